@@ -1,0 +1,18 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the benchmark.
+
+This package holds mesh generators, a counter-free splitmix64 stream, and
+purely structural index-set builders (cluster trees, block partitions and
+seeded pivot subsets).  It contains none of the quadrature arithmetic of the
+method: no rules, no kernels, no integrals.
+"""
+from .rng import SplitMix64
+from .meshes import (Mesh, icosphere, octasphere, cube_surface, torus,
+                     jitter, icosahedron, octahedron, two_triangles,
+                     mean_edge_length)
+from .structure import (ClusterTree, build_cluster_tree, build_block_partition,
+                        seeded_pivots, BlockPartition)
+
+__all__ = ["SplitMix64", "Mesh", "icosphere", "octasphere", "cube_surface",
+           "torus", "jitter", "icosahedron", "octahedron", "two_triangles",
+           "mean_edge_length", "ClusterTree", "build_cluster_tree",
+           "build_block_partition", "seeded_pivots", "BlockPartition"]
