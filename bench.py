@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark: Galerkin entries/s of the near field + coupling (pivot) blocks.
+
+Workload (one step): the 20480-triangle icosphere with the piecewise-linear
+basis, H2 block partition (leaf 32, eta 2, at most 16 pivots per cluster);
+the Laplace single- and double-layer near-field blocks (Sauter-Schwab order
+5, Duffy order 3) and coupling blocks, FP64.  Inputs are resident on the
+device before the timed region; L2 is flushed (256 MiB write) between timed
+steps.  `e2e` repeats the step through the same C ABI from host buffers:
+mesh upload, block lists host->device, outputs device->host.
+
+--impl reference runs the plain FP64 CPU oracle on a bounded sample of the
+same workload's entries (the slow baseline arm).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Galerkin entries/s (near SS + far pivots) at ≤1e-6 rel err vs plain FP64 form"
+UNIT = "entries/s"
+
+# FP64 operations per quadrature point (FMA = 2, rsqrt = 1, sincos = 2), as the
+# block kernels evaluate them: difference vector 3, r^2 5, rsqrt 1, weight and
+# accumulation 2; double layer + (x-y).n 5, r^-3 2, product 1; Helmholtz +
+# kappa r 1, sincos 2, two products and a second accumulation 5; piecewise
+# linear + three basis-weighted accumulations 6 and the x-side 3x3 update
+# 18 / (points per axis pair).
+def flops_per_point(kernel: str, basis: str, np_axis: int) -> float:
+    f = 11.0
+    if kernel == "laplace_dlp":
+        f += 8.0
+    elif kernel == "helmholtz_slp":
+        f += 8.0
+    if basis == "p1":
+        f += 6.0 + 18.0 / np_axis
+    return f
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pair_counts(w):
+    """Host-side accounting of the work one step performs (for the roofline):
+    regular triangle pairs evaluated by the block kernel per block set, and the
+    touching pairs per case."""
+    import scipy.sparse as sp
+    mesh = w.mesh
+    nt, nv = mesh.nt, mesh.nv
+    tri = mesh.tris
+    # vertex -> triangle incidence
+    VT = sp.csr_matrix((np.ones(3 * nt), (tri.ravel(), np.repeat(np.arange(nt), 3))),
+                       shape=(nv, nt))
+    # touching incidence: triangles sharing a vertex
+    TT = (VT.T @ VT).tocsr()
+    TT.data[:] = 1.0
+
+    def block_pairs(bs):
+        ncl = len(bs.row_ptr) - 1
+        rows = np.repeat(np.arange(ncl), np.diff(bs.row_ptr))
+        CV = sp.csr_matrix((np.ones(len(bs.row_idx)), (rows, bs.row_idx)), shape=(ncl, nv))
+        CT = (CV @ VT).tocsr()
+        CT.data[:] = 1.0          # Ta(c): triangles touching cluster c
+        size = np.asarray(CT.sum(axis=1)).ravel()
+        touch = (CT @ TT @ CT.T).tocsr()
+        t, s = bs.blk_row, bs.blk_col
+        total = float(np.sum(size[t] * size[s]))
+        tp = float(np.asarray(touch[t, s]).ravel().sum())
+        return total - tp, tp
+
+    near_reg, near_touch = block_pairs(w.near)
+    far_reg, far_touch = block_pairs(w.far)
+    return {"near_regular_pairs": near_reg, "near_touching_lookups": near_touch,
+            "far_regular_pairs": far_reg, "far_touching_lookups": far_touch}
+
+
+def build_device_inputs(torch, pkg, w, dev):
+    def t32(a):
+        return torch.as_tensor(np.ascontiguousarray(a, np.int32)).to(dev)
+
+    def t64(a):
+        return torch.as_tensor(np.ascontiguousarray(a, np.int64)).to(dev)
+
+    sets = {}
+    for name, bs in (("near", w.near), ("far", w.far)):
+        sets[name] = dict(row_ptr=t32(bs.row_ptr), row_idx=t32(bs.row_idx), col_ptr=t32(bs.col_ptr),
+                          col_idx=t32(bs.col_idx), blk_row=t32(bs.blk_row), blk_col=t32(bs.blk_col),
+                          blk_off=t64(bs.blk_off), n=bs.n_entries)
+    return sets
+
+
+def make_jobs(torch, pkg, mid, w, sets, outs):
+    quad = pkg.quad_desc(**w.quad.kw())
+    jobs = {"near": [], "far": []}
+    for op in w.operators:
+        kd = pkg.kernel_desc(op.kernel, op.kappa)
+        for name in ("near", "far"):
+            s = sets[name]
+            jobs[name].append(pkg.BlockJob(mid, s["row_ptr"], s["row_idx"], s["col_ptr"], s["col_idx"],
+                                           s["blk_row"], s["blk_col"], s["blk_off"],
+                                           outs[(op.kernel, name)], kd, quad))
+    return jobs
+
+
+def run_ours(args):
+    import torch
+    import synth
+    import paper_1510_07244_gb300 as pkg
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    w = synth.workloads.config2(args.levels)
+    stream = torch.cuda.current_stream(dev)
+    ctx = pkg.Context(local, stream)
+    mid = ctx.bem_mesh_upload(w.mesh.verts, w.mesh.tris, w.basis)
+    sets = build_device_inputs(torch, pkg, w, dev)
+    outs = {}
+    for op in w.operators:
+        dt = torch.complex128 if op.kernel == "helmholtz_slp" else torch.float64
+        for name in ("near", "far"):
+            outs[(op.kernel, name)] = torch.empty(sets[name]["n"], dtype=dt, device=dev)
+    jobs = make_jobs(torch, pkg, mid, w, sets, outs)
+    entries_per_step = len(w.operators) * (w.near.n_entries + w.far.n_entries)
+
+    def step():
+        ctx.bem_near_field(jobs["near"])
+        ctx.bem_coupling_blocks(jobs["far"])
+
+    for _ in range(args.warmup):
+        step()
+    ctx.bem_sync()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    ctx.bem_profile_reset()
+    ctx.bem_profile_enable(True)
+    clocks = Clocks(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.bem_sync()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    prof = ctx.bem_profile_read()
+    ctx.bem_profile_enable(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = entries_per_step * ws * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (longest total time in the timed region)
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    counts = pair_counts(w)
+    q = w.quad
+    npts_reg = (q.q_regular ** 2) ** 2 if q.regular_rule == "duffy" else 49
+    np_axis = q.q_regular ** 2 if q.regular_rule == "duffy" else 7
+    ops = {op.kernel: op for op in w.operators}
+    roof = None
+    peak_fp64 = 152 * 2.07e9 * 4.0 / 1e12      # TFLOP/s, derived in the design doc
+    if dom[0] in ("block_p1", "block_p0"):
+        flops = 0.0
+        for kname in ops:
+            f = flops_per_point(kname, w.basis, np_axis)
+            flops += (counts["near_regular_pairs"] + counts["far_regular_pairs"]) * npts_reg * f
+        flops *= args.steps
+        achieved = flops / (dom[1][1] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom[0], "achieved": round(achieved, 4),
+                "peak": round(peak_fp64, 4), "unit": "TFLOP/s", "frac": round(achieved / peak_fp64, 4),
+                "traffic": None, "peak_source": "derived FP64 vector rate: 152 SM x 4 flop/clk x 2.07 GHz",
+                "avg_launch_ms": round(dom[1][1] / dom[1][0], 4), "launches": dom[1][0]}
+    else:
+        roof = {"bound": "alu", "kernel": dom[0], "achieved": None, "peak": round(peak_fp64, 4),
+                "unit": "TFLOP/s", "frac": None, "traffic": None}
+    launches = int(sum(v[0] for v in prof.values()))
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = {}
+        for name in ("near", "far"):
+            bs = w.near if name == "near" else w.far
+            pin[name] = {k: torch.from_numpy(np.ascontiguousarray(getattr(bs, k),
+                                                                  np.int64 if k == "blk_off" else np.int32)).pin_memory()
+                         for k in ("row_ptr", "row_idx", "col_ptr", "col_idx", "blk_row", "blk_col", "blk_off")}
+        host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
+        h2d = sum(t.numel() * t.element_size() for d in pin.values() for t in d.values())
+        h2d += w.mesh.verts.nbytes + w.mesh.tris.nbytes
+        d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+        times = []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            mid2 = ctx.bem_mesh_upload(w.mesh.verts, w.mesh.tris, w.basis)
+            for name in ("near", "far"):
+                for key, t in pin[name].items():
+                    sets[name][key].copy_(t, non_blocking=True)
+            jobs2 = make_jobs(torch, pkg, mid2, w, sets, outs)
+            ctx.bem_near_field(jobs2["near"])
+            ctx.bem_coupling_blocks(jobs2["far"])
+            for key, t in outs.items():
+                host_out[key].copy_(t, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            ctx.bem_sync()
+            t1 = time.perf_counter()
+            ctx.bem_mesh_free(mid2)
+            if k > 0:
+                times.append(t1 - t0)
+        e2e = {"value": entries_per_step / statistics.mean(times), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": len(times), "includes": "mesh upload + host planning, block lists H2D, "
+                                                "all kernels, outputs D2H"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": w.name, "triangles": w.mesh.nt, "vertices": w.mesh.nv,
+                           "basis": w.basis, "operators": [o.kernel for o in w.operators],
+                           "entries_per_step": entries_per_step,
+                           "near_entries": w.near.n_entries, "far_entries": w.far.n_entries,
+                           "near_blocks": len(w.near.blk_row), "far_blocks": len(w.far.blk_row),
+                           "quadrature": w.quad.kw(), "precision": "fp64", "order_mode": "fixed",
+                           "l2": "flushed between timed steps (256 MiB write, untimed)",
+                           "pairs_per_step_per_operator": counts},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "kernel_ms": {k: round(v[1], 3) for k, v in prof.items()},
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def sample_entries(w, n, seed):
+    """Seeded uniform sample of (operator, row, col) over the step's entries."""
+    import synth
+    rng = synth.SplitMix64(seed)
+    nr, nf = w.near.n_entries, w.far.n_entries
+    tot = nr + nf
+    pick = rng.integers(n, tot * len(w.operators))
+    op = pick // tot
+    k = pick % tot
+    rn, cn = w.near.entry_indices()
+    rf, cf = w.far.entry_indices()
+    R = np.where(k < nr, rn[np.minimum(k, nr - 1)], rf[np.maximum(k - nr, 0)])
+    C = np.where(k < nr, cn[np.minimum(k, nr - 1)], cf[np.maximum(k - nr, 0)])
+    return op, R, C
+
+
+def time_oracle(w, n, seed):
+    import oracle
+    op, R, C = sample_entries(w, n, seed)
+    t0 = time.perf_counter()
+    for i, o in enumerate(w.operators):
+        sel = op == i
+        if sel.any():
+            oracle.entries(w.mesh.verts, w.mesh.tris, R[sel], C[sel], kernel=o.kernel, kappa=o.kappa,
+                           basis=w.basis, **w.quad.kw())
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(w, budget_s):
+    import oracle
+    oracle.build()
+    n0 = 2000
+    t0 = time_oracle(w, n0, 1)
+    n = int(max(n0, min(5_000_000, n0 * budget_s / max(t0, 1e-3))))
+    t = time_oracle(w, n, 2)
+    return {"value": n / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} entries drawn uniformly (seeded) from the step's near-field and coupling "
+                      f"entries of both operators; {t:.1f} s on {os.cpu_count()} OpenMP threads"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import synth
+    import oracle
+    oracle.build()
+    w = synth.workloads.config2(args.levels)
+    entries_per_step = len(w.operators) * (w.near.n_entries + w.far.n_entries)
+    t0 = time_oracle(w, 1000, 3)
+    per_step = args.ref_seconds_per_step
+    n = int(max(1000, 1000 * per_step / max(t0, 1e-3)))
+    times = []
+    for k in range(args.warmup + args.steps):
+        t = time_oracle(w, n, 100 + k)
+        if k >= args.warmup:
+            times.append(t)
+    value = n * len(times) / sum(times)
+    sample = (f"each step: {n} of the {entries_per_step} entries of the workload, drawn uniformly "
+              f"(seeded) from near-field and coupling entries of both operators")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "entries_per_step": entries_per_step, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds-per-step", type=float, default=4.0)
+    ap.add_argument("--levels", type=int, default=5,
+                    help="icosphere refinement levels (5 = the 20480-triangle workload; "
+                         "smaller values only for profiling captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

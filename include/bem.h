@@ -1,0 +1,207 @@
+/*
+ * bem.h -- C ABI of the GB300 Galerkin boundary-element quadrature library.
+ *
+ * The library computes entries of Galerkin boundary-element matrices
+ * (Section 2.1, Eq. 1)
+ *
+ *     g_ij = int_Gamma phi_i(x) int_Gamma k(x, y) psi_j(y) dy dx
+ *
+ * on flat-triangle surface meshes, as sums over triangle pairs of integrals on
+ * the reference triangle D = {(s,t): 0 <= t <= s <= 1} (Section 2.2), with
+ *   - kernels (Eq. 2, Section 4): Laplace single layer 1/(4 pi |x-y|),
+ *     Laplace double layer (x-y).n_y / (4 pi |x-y|^3) (outward n_y),
+ *     Helmholtz single layer exp(i kappa |x-y|) / (4 pi |x-y|);
+ *   - bases: piecewise constant (index = triangle) or continuous piecewise
+ *     linear (index = vertex), the same space for test and trial functions;
+ *   - quadrature (Section 2.2): tensor Gauss-Legendre after the Duffy map for
+ *     disjoint triangles (or the 7-point Radon rule on each triangle), and
+ *     Sauter-Schwab subdomain rules for identical, common-edge and
+ *     common-vertex pairs.  "Touching" means sharing a vertex index.
+ *
+ * Conventions for every call:
+ *   - Every call returns an int status: BEM_OK (0) or a negative BEM_ERR_*.
+ *     bem_last_error() returns a message for the last failure on a context.
+ *   - Bulk data pointers (index lists, outputs) are DEVICE pointers owned by
+ *     the caller, except bem_mesh_upload, which takes HOST arrays and keeps
+ *     its own device copy until bem_mesh_free / bem_destroy.
+ *   - Index arrays are int32 and 0-based.  Output matrices are column-major.
+ *     Real kernels write double; the Helmholtz kernel writes interleaved
+ *     complex (re, im) double pairs (16 bytes per entry, 16-byte aligned).
+ *     The mixed-precision mode still writes double.
+ *   - Compute calls are asynchronous on the context's CUDA stream.  Errors
+ *     detected on the device (an index out of range, a touching pair inside a
+ *     block that must be disjoint) are recorded in a device status word that
+ *     bem_sync() returns; the entries concerned are left unwritten.
+ *   - A context serves one thread at a time.
+ */
+#ifndef BEM_GB300_H
+#define BEM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define BEM_OK               0
+#define BEM_ERR_INVALID_ARG (-1)  /* bad argument or index (host or device check) */
+#define BEM_ERR_CUDA        (-2)  /* a CUDA runtime call failed                  */
+#define BEM_ERR_OOM         (-3)  /* device allocation failed                    */
+#define BEM_ERR_TIMEOUT     (-4)  /* a bounded device wait gave up               */
+#define BEM_ERR_DEGENERATE  (-5)  /* zero-area triangle / repeated vertex        */
+#define BEM_ERR_UNSUPPORTED (-6)  /* option combination not implemented          */
+
+/* ---- enumerations -------------------------------------------------------- */
+enum { BEM_LAPLACE_SLP = 0, BEM_LAPLACE_DLP = 1, BEM_HELMHOLTZ_SLP = 2 };
+enum { BEM_P0 = 0, BEM_P1 = 1 };
+enum { BEM_RULE_DUFFY = 0, BEM_RULE_TRI7 = 1 };
+enum { BEM_FP64 = 0, BEM_MIXED = 1 };
+enum { BEM_ORDER_FIXED = 0, BEM_ORDER_LEARNED = 1 };
+
+typedef struct bem_ctx bem_ctx;
+
+/* Kernel function (Eq. 2).  kappa: wave number, used by BEM_HELMHOLTZ_SLP. */
+typedef struct {
+    int32_t kind;
+    double kappa;
+} bem_kernel_desc;
+
+/* Quadrature orders (Section 2.2 and the "higher quadrature orders" study of
+ * Section 4): q_* = Gauss-Legendre points per axis of [0,1]^4.  The paper's
+ * default is 3 for disjoint pairs and 5 for the singular cases.
+ *   regular_rule: BEM_RULE_DUFFY (q_regular^4 points) or BEM_RULE_TRI7
+ *                 (7 x 7 = 49 points, q_regular ignored).
+ *   precision:    BEM_FP64, or BEM_MIXED (regular and common-vertex pairs in
+ *                 FP32 arithmetic with compensated sums; identical and
+ *                 common-edge pairs stay FP64).
+ *   order_mode:   BEM_ORDER_FIXED (the orders above) or BEM_ORDER_LEARNED. */
+typedef struct {
+    int32_t q_regular;
+    int32_t regular_rule;
+    int32_t q_identical;
+    int32_t q_edge;
+    int32_t q_vertex;
+    int32_t precision;
+    int32_t order_mode;
+} bem_quad_desc;
+
+/* A list of matrix blocks G|_{t x s} of one mesh (Section 2.3: blocks of the
+ * block tree; near-field blocks t x s, coupling blocks t~ x s~).
+ *   Row clusters: cluster c holds indices row_idx[row_ptr[c] .. row_ptr[c+1]).
+ *   Column clusters: likewise with col_ptr / col_idx.
+ *   Block b is G restricted to (row cluster blk_row[b]) x (column cluster
+ *   blk_col[b]) and is written column-major (leading dimension = number of
+ *   rows of the block) at element offset blk_off[b] of `out`.
+ * All arrays are device arrays.  Blocks must not overlap in `out`. */
+typedef struct {
+    int32_t mesh_id;
+    bem_kernel_desc kernel;
+    bem_quad_desc quad;
+    const int32_t *row_ptr;      /* n_row_clusters + 1 */
+    const int32_t *row_idx;
+    int32_t n_row_clusters;
+    const int32_t *col_ptr;      /* n_col_clusters + 1 */
+    const int32_t *col_idx;
+    int32_t n_col_clusters;
+    const int32_t *blk_row;      /* n_blocks */
+    const int32_t *blk_col;      /* n_blocks */
+    const int64_t *blk_off;      /* n_blocks */
+    int64_t n_blocks;
+    void *out;                   /* double or (re,im) double pairs */
+} bem_block_job;
+
+/* Counters of an uploaded mesh (filled by bem_mesh_info). */
+typedef struct {
+    int64_t n_vertices;
+    int64_t n_triangles;
+    int64_t n_identical;    /* ordered touching pairs per case */
+    int64_t n_edge;
+    int64_t n_vertex;
+    int32_t max_vertex_degree;
+    int32_t basis;
+} bem_mesh_stats;
+
+/* ---- context --------------------------------------------------------------
+ * bem_create: context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The stream is not
+ * owned.  bem_destroy frees everything the context allocated (meshes,
+ * rules, scratch) after synchronising its stream. */
+int bem_create(bem_ctx **ctx, int device, void *cuda_stream);
+int bem_destroy(bem_ctx *ctx);
+/* Message of the last failure on this context ("" if none).  Owned by ctx. */
+const char *bem_last_error(bem_ctx *ctx);
+/* Waits for all work on the context's stream; returns the first error
+ * recorded by a kernel since the previous bem_sync (and clears it), a CUDA
+ * error, or BEM_OK. */
+int bem_sync(bem_ctx *ctx);
+
+/* ---- mesh (a1: per-triangle precompute; a2: touching-pair classification) --
+ * Copies a flat-triangle mesh to the device and precomputes per triangle the
+ * vertices, the edge vectors of the affine map Phi(s,t) = v0 + s (v1 - v0) +
+ * t (v2 - v1) (Section 2.2), the Gram factor sqrt(g) = |(v1-v0) x (v2-v1)|
+ * and the unit normal (v1-v0) x (v2-v1) / sqrt(g) (outward for outward-
+ * oriented meshes: the double layer uses it).  It also classifies every pair
+ * of triangles that share a vertex index into identical / common edge /
+ * common vertex (Section 2.2) with the vertex orders the Sauter-Schwab maps
+ * expect, and builds the vertex-to-triangle adjacency the piecewise-linear
+ * basis needs.
+ *   verts: HOST double[nv][3];  tris: HOST int32[nt][3].
+ *   basis: BEM_P0 or BEM_P1 (index space of every call on this mesh).
+ * Errors: BEM_ERR_INVALID_ARG (vertex index out of range, nv or nt < 1),
+ * BEM_ERR_DEGENERATE (zero-area triangle, repeated vertex in a triangle),
+ * BEM_ERR_OOM. */
+int bem_mesh_upload(bem_ctx *ctx, const double *verts, int64_t nv, const int32_t *tris,
+                    int64_t nt, int32_t basis, int32_t *mesh_id);
+int bem_mesh_free(bem_ctx *ctx, int32_t mesh_id);
+int bem_mesh_info(bem_ctx *ctx, int32_t mesh_id, bem_mesh_stats *stats);
+
+/* ---- matrix entries ------------------------------------------------------- */
+
+/* Near-field blocks (Section 2.3: inadmissible leaves of the block tree), the
+ * paper's per-case work lists (Section 3) formed on the device: every triangle
+ * pair of every block is classified by its shared vertex indices; disjoint
+ * pairs use the regular rule, touching pairs the Sauter-Schwab rules.
+ * n_jobs jobs (any meshes, kernels and orders) run in one call. */
+int bem_near_field(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs);
+
+/* Coupling blocks G|_{t~ x s~} of admissible blocks (Section 2.4): the same
+ * block layout as bem_near_field, with the pivot sets t~, s~ as clusters.
+ * Admissible blocks contain only disjoint pairs; a touching pair found in a
+ * coupling block is a caller error, recorded as BEM_ERR_INVALID_ARG in the
+ * device status word, and that block is left unwritten. */
+int bem_coupling_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs);
+
+/* Arbitrary entries (pivot rows / columns, Section 2.3-2.4):
+ * out[k] = g_{rows[k], cols[k]} for k < n.  rows, cols, out: device arrays. */
+int bem_pivot_entries(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
+                      const bem_quad_desc *quad, const int32_t *rows, const int32_t *cols,
+                      int64_t n, void *out);
+
+/* Full dense matrix, n x n column-major (n = triangles for P0, vertices for
+ * P1).  lower_only != 0 writes only entries with row >= column (the single
+ * layer is symmetric, Section 4); the rest of `out` is not touched. */
+int bem_assemble_dense(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
+                       const bem_quad_desc *quad, int32_t lower_only, void *out);
+
+/* ---- launch profiling (tracing) ------------------------------------------
+ * When enabled, every kernel launch of the context is bracketed by CUDA
+ * events recorded on the context's stream.  bem_profile_read waits for the
+ * stream, adds the elapsed times of all finished launches to per-kernel
+ * totals and copies up to `cap` totals to `out` (*n_out = number of kernel
+ * classes).  bem_profile_enable(ctx, 0) stops recording; bem_profile_reset
+ * clears the totals.  No effect on results. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} bem_kernel_time;
+
+int bem_profile_enable(bem_ctx *ctx, int32_t on);
+int bem_profile_reset(bem_ctx *ctx);
+int bem_profile_read(bem_ctx *ctx, bem_kernel_time *out, int32_t cap, int32_t *n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BEM_GB300_H */

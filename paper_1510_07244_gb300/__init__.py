@@ -1,0 +1,12 @@
+"""GB300 (sm_103a) Galerkin boundary-element quadrature: Sauter-Schwab near
+field and H2 coupling/pivot entries behind the C ABI of include/bem.h.
+
+The compute path is the CUDA library built by ``paper_1510_07244_gb300.build``;
+this package only marshals arguments to it (``_binding``) and, in
+``workloads``, assembles the synthetic benchmark inputs.
+"""
+from ._binding import (Context, BlockJob, BemError, kernel_desc, quad_desc, load, LIB_PATH,
+                       EXPORTS, KERNELS, BASES, RULES)
+
+__all__ = ["Context", "BlockJob", "BemError", "kernel_desc", "quad_desc", "load", "LIB_PATH",
+           "EXPORTS", "KERNELS", "BASES", "RULES"]

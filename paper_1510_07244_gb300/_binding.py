@@ -1,0 +1,259 @@
+"""ctypes binding of libbem_gb300.so (the C ABI in include/bem.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch CUDA tensors (int32 index lists, float64
+or complex128 outputs); the stream is torch's current stream unless given.
+If the shared library is missing this module raises instead of computing
+anything another way.
+"""
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libbem_gb300.so")
+
+BEM_OK = 0
+ERRORS = {-1: "BEM_ERR_INVALID_ARG", -2: "BEM_ERR_CUDA", -3: "BEM_ERR_OOM",
+          -4: "BEM_ERR_TIMEOUT", -5: "BEM_ERR_DEGENERATE", -6: "BEM_ERR_UNSUPPORTED"}
+KERNELS = {"laplace_slp": 0, "laplace_dlp": 1, "helmholtz_slp": 2}
+BASES = {"p0": 0, "p1": 1}
+RULES = {"duffy": 0, "tri7": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+ORDER_MODES = {"fixed": 0, "learned": 1}
+EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_upload",
+           "bem_mesh_free", "bem_mesh_info", "bem_near_field", "bem_coupling_blocks",
+           "bem_pivot_entries", "bem_assemble_dense", "bem_profile_enable",
+           "bem_profile_reset", "bem_profile_read"]
+
+
+class BemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class bem_kernel_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("kappa", ctypes.c_double)]
+
+
+class bem_quad_desc(ctypes.Structure):
+    _fields_ = [("q_regular", ctypes.c_int32), ("regular_rule", ctypes.c_int32),
+                ("q_identical", ctypes.c_int32), ("q_edge", ctypes.c_int32),
+                ("q_vertex", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("order_mode", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+
+
+class bem_block_job(ctypes.Structure):
+    _fields_ = [("mesh_id", ctypes.c_int32), ("kernel", bem_kernel_desc),
+                ("quad", bem_quad_desc),
+                ("row_ptr", _vp), ("row_idx", _vp), ("n_row_clusters", ctypes.c_int32),
+                ("col_ptr", _vp), ("col_idx", _vp), ("n_col_clusters", ctypes.c_int32),
+                ("blk_row", _vp), ("blk_col", _vp), ("blk_off", _vp),
+                ("n_blocks", ctypes.c_int64), ("out", _vp)]
+
+
+class bem_mesh_stats(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("n_identical", ctypes.c_int64), ("n_edge", ctypes.c_int64),
+                ("n_vertex", ctypes.c_int64), ("max_vertex_degree", ctypes.c_int32),
+                ("basis", ctypes.c_int32)]
+
+
+class bem_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_1510_07244_gb300.build` (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    lib.bem_create.argtypes = [P(_vp), ctypes.c_int, _vp]
+    lib.bem_destroy.argtypes = [_vp]
+    lib.bem_last_error.argtypes = [_vp]
+    lib.bem_last_error.restype = ctypes.c_char_p
+    lib.bem_sync.argtypes = [_vp]
+    lib.bem_mesh_upload.argtypes = [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int64,
+                                    ctypes.c_int32, P(ctypes.c_int32)]
+    lib.bem_mesh_free.argtypes = [_vp, ctypes.c_int32]
+    lib.bem_mesh_info.argtypes = [_vp, ctypes.c_int32, P(bem_mesh_stats)]
+    lib.bem_near_field.argtypes = [_vp, P(bem_block_job), ctypes.c_int32]
+    lib.bem_coupling_blocks.argtypes = [_vp, P(bem_block_job), ctypes.c_int32]
+    lib.bem_pivot_entries.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc),
+                                      P(bem_quad_desc), _vp, _vp, ctypes.c_int64, _vp]
+    lib.bem_assemble_dense.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc),
+                                       P(bem_quad_desc), ctypes.c_int32, _vp]
+    lib.bem_profile_enable.argtypes = [_vp, ctypes.c_int32]
+    lib.bem_profile_reset.argtypes = [_vp]
+    lib.bem_profile_read.argtypes = [_vp, P(bem_kernel_time), ctypes.c_int32,
+                                     P(ctypes.c_int32)]
+    for name in EXPORTS:
+        if name != "bem_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def kernel_desc(kind="laplace_slp", kappa=0.0) -> bem_kernel_desc:
+    return bem_kernel_desc(KERNELS[kind], float(kappa))
+
+
+def quad_desc(q_regular=3, regular_rule="duffy", q_identical=5, q_edge=5, q_vertex=5,
+              precision="fp64", order_mode="fixed") -> bem_quad_desc:
+    return bem_quad_desc(int(q_regular), RULES[regular_rule], int(q_identical), int(q_edge),
+                         int(q_vertex), PRECISIONS[precision], ORDER_MODES[order_mode])
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_dev(t, dtype, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+
+
+@dataclass
+class BlockJob:
+    """Blocks of one mesh in cluster-CSR form (all CUDA tensors)."""
+    mesh_id: int
+    row_ptr: object
+    row_idx: object
+    col_ptr: object
+    col_idx: object
+    blk_row: object
+    blk_col: object
+    blk_off: object
+    out: object
+    kernel: bem_kernel_desc = field(default_factory=kernel_desc)
+    quad: bem_quad_desc = field(default_factory=quad_desc)
+
+    def to_c(self) -> bem_block_job:
+        import torch
+        for n in ("row_ptr", "row_idx", "col_ptr", "col_idx", "blk_row", "blk_col"):
+            _check_dev(getattr(self, n), torch.int32, n)
+        _check_dev(self.blk_off, torch.int64, "blk_off")
+        cplx = self.kernel.kind == KERNELS["helmholtz_slp"]
+        _check_dev(self.out, torch.complex128 if cplx else torch.float64, "out")
+        return bem_block_job(self.mesh_id, self.kernel, self.quad,
+                             _ptr(self.row_ptr), _ptr(self.row_idx), self.row_ptr.numel() - 1,
+                             _ptr(self.col_ptr), _ptr(self.col_idx), self.col_ptr.numel() - 1,
+                             _ptr(self.blk_row), _ptr(self.blk_col), _ptr(self.blk_off),
+                             self.blk_row.numel(), _ptr(self.out))
+
+
+class Context:
+    """Owns a bem_ctx.  Methods mirror the C entry points."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self.lib.bem_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream))
+        if rc != BEM_OK:
+            raise BemError(rc, "bem_create failed")
+        self.h = h
+
+    def _check(self, rc):
+        if rc != BEM_OK:
+            raise BemError(rc, self.lib.bem_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bem_last_error(self) -> str:
+        return self.lib.bem_last_error(self.h).decode()
+
+    def bem_sync(self):
+        self._check(self.lib.bem_sync(self.h))
+
+    def bem_mesh_upload(self, verts, tris, basis="p0") -> int:
+        v = np.ascontiguousarray(verts, np.float64)
+        t = np.ascontiguousarray(tris, np.int32)
+        mid = ctypes.c_int32(0)
+        self._check(self.lib.bem_mesh_upload(self.h, v.ctypes.data_as(_vp), v.shape[0],
+                                             t.ctypes.data_as(_vp), t.shape[0], BASES[basis],
+                                             ctypes.byref(mid)))
+        return mid.value
+
+    def bem_mesh_free(self, mesh_id: int):
+        self._check(self.lib.bem_mesh_free(self.h, mesh_id))
+
+    def bem_mesh_info(self, mesh_id: int) -> dict:
+        s = bem_mesh_stats()
+        self._check(self.lib.bem_mesh_info(self.h, mesh_id, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def bem_near_field(self, jobs):
+        arr = (bem_block_job * len(jobs))(*[j.to_c() for j in jobs])
+        self._check(self.lib.bem_near_field(self.h, arr, len(jobs)))
+
+    def bem_coupling_blocks(self, jobs):
+        arr = (bem_block_job * len(jobs))(*[j.to_c() for j in jobs])
+        self._check(self.lib.bem_coupling_blocks(self.h, arr, len(jobs)))
+
+    def bem_pivot_entries(self, mesh_id, kernel, quad, rows, cols, out):
+        import torch
+        _check_dev(rows, torch.int32, "rows")
+        _check_dev(cols, torch.int32, "cols")
+        cplx = kernel.kind == KERNELS["helmholtz_slp"]
+        _check_dev(out, torch.complex128 if cplx else torch.float64, "out")
+        if rows.numel() != cols.numel() or out.numel() < rows.numel():
+            raise ValueError("rows/cols/out size mismatch")
+        self._check(self.lib.bem_pivot_entries(self.h, mesh_id, ctypes.byref(kernel),
+                                               ctypes.byref(quad), _ptr(rows), _ptr(cols),
+                                               rows.numel(), _ptr(out)))
+
+    def bem_assemble_dense(self, mesh_id, kernel, quad, lower_only, out):
+        import torch
+        cplx = kernel.kind == KERNELS["helmholtz_slp"]
+        _check_dev(out, torch.complex128 if cplx else torch.float64, "out")
+        info = self.bem_mesh_info(mesh_id)
+        n = info["n_triangles"] if info["basis"] == 0 else info["n_vertices"]
+        if out.numel() < n * n:
+            raise ValueError(f"out must hold {n} x {n} entries")
+        self._check(self.lib.bem_assemble_dense(self.h, mesh_id, ctypes.byref(kernel),
+                                                ctypes.byref(quad), int(lower_only), _ptr(out)))
+
+    def bem_profile_enable(self, on: bool = True):
+        self._check(self.lib.bem_profile_enable(self.h, 1 if on else 0))
+
+    def bem_profile_reset(self):
+        self._check(self.lib.bem_profile_reset(self.h))
+
+    def bem_profile_read(self) -> dict:
+        """{kernel class: (launches, total_ms)} of all finished profiled launches."""
+        cap = 32
+        arr = (bem_kernel_time * cap)()
+        n = ctypes.c_int32(0)
+        self._check(self.lib.bem_profile_read(self.h, arr, cap, ctypes.byref(n)))
+        return {arr[k].name.decode(): (arr[k].launches, arr[k].total_ms)
+                for k in range(min(cap, n.value))}

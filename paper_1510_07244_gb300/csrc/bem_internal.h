@@ -1,0 +1,136 @@
+// Internal declarations shared by the host planner (bem_api.cpp), the rule
+// generator (bem_rules.cpp) and the device code (bem_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "bem.h"
+
+namespace bem {
+
+constexpr int kGeomStride = 16;      // doubles per triangle record (128 bytes)
+// record layout: v0[3] v1[3] v2[3] n[3] sqrt_g pad[3]
+constexpr int kMaxDegP1 = 16;        // vertex degree bound of the P1 block engine
+constexpr int kTile = 32;            // rows / columns of one block tile
+constexpr int kMaxNp = 25;           // points of a 2D regular rule (Duffy q <= 5)
+
+enum Case { kRegular = 0, kVertex = 1, kEdge = 2, kIdentical = 3 };
+
+// The six permutations of (0,1,2); a code c in [0,6) names kPerm[c].
+// Canonical orders are stored as (code_a * 6 + code_b).
+extern const int kPerm[6][3];
+
+// 2D rule on the reference triangle D, passed by value to the kernels.
+struct Rule2D {
+    int np;
+    double s[kMaxNp], t[kMaxNp], w[kMaxNp];
+};
+
+// 4D rule on D x D, device SoA: x1 | x2 | y1 | y2 | w, n each.
+struct Rule4D {
+    int n = 0;
+    double *d = nullptr;   // device, 5 n doubles
+};
+
+// Device view of an uploaded mesh.
+struct MeshView {
+    int64_t nv, nt;
+    int basis;
+    int maxdeg;
+    const double *geom;        // nt * kGeomStride
+    const int4 *tvid;          // nt (v0, v1, v2, 0)
+    const int *vt_ptr;         // nv + 1
+    const int *vt_tri;         // 3 nt, ascending triangle ids per vertex
+    const int *nb_ptr;         // nt + 1: touching neighbours of each triangle
+    const int *nb_tri;         // ntouch, ascending per triangle
+    const int *nb_src;         // ntouch: the triangle a of entry k (b = nb_tri[k])
+    const unsigned char *nb_case;   // ntouch
+    const unsigned char *nb_perm;   // ntouch: code_a * 6 + code_b
+    double2 *table;            // ntouch * (1 or 9): touching-pair integrals
+    int64_t ntouch;
+};
+
+struct Mesh {
+    MeshView v{};
+    bem_mesh_stats stats{};
+    std::vector<void *> allocs;
+    int *list[4] = {nullptr, nullptr, nullptr, nullptr};   // touching indices per case
+    int64_t nlist[4] = {0, 0, 0, 0};
+    int *iota = nullptr;       // 0 .. n-1 (dense calls)
+    int *dense_csr = nullptr;  // {0, n} and the block {0, 0, off 0}
+};
+
+}  // namespace bem
+
+struct bem_prof_rec {
+    std::string name;
+    cudaEvent_t a, b;
+};
+
+struct bem_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int *status = nullptr;                 // device status word
+    int64_t *tile_prefix = nullptr;        // scratch: per-block tile prefix sums
+    int64_t tile_prefix_cap = 0;
+    int num_sms = 0;
+    std::map<int, bem::Mesh *> meshes;
+    int next_mesh = 1;
+    std::map<std::tuple<int, int, int>, bem::Rule4D> rules4;   // (case, rule, q)
+    bool profile = false;
+    std::vector<bem_prof_rec> prof_pending;
+    std::vector<cudaEvent_t> prof_free;
+    std::map<std::string, std::pair<int64_t, double>> prof_total;
+};
+
+namespace bem {
+// Brackets one launch with profiling events when the context profiles.
+struct ProfScope {
+    bem_ctx *ctx;
+    bem_prof_rec rec;
+    bool on;
+    ProfScope(bem_ctx *c, const char *name);
+    ~ProfScope();
+};
+}  // namespace bem
+
+namespace bem {
+
+// bem_rules.cpp
+bool gauss_legendre_unit(int q, std::vector<double> &x, std::vector<double> &w);
+bool make_rule2d(int regular_rule, int q, Rule2D &out);
+bool make_rule4d_host(int cas, int regular_rule, int q, std::vector<double> &soa);
+
+// bem_kernels.cu: launchers (return a cudaError_t of the launch)
+struct BlockLaunch {
+    const int32_t *row_ptr, *row_idx, *col_ptr, *col_idx;
+    int32_t n_row_clusters, n_col_clusters;
+    const int32_t *blk_row, *blk_col;
+    const int64_t *blk_off;
+    int64_t n_blocks;
+    void *out;
+    int kind;
+    double kappa;
+    int lower_only;
+    int allow_touching;
+};
+
+cudaError_t launch_tile_prefix(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
+                               int *status, cudaStream_t st);
+cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
+                            const Rule4D &rule, int kind, double kappa, cudaStream_t st);
+cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const Rule2D &rule,
+                                const int64_t *prefix, int *status, int grid, cudaStream_t st);
+size_t p1_smem_bytes(bool cplx);
+cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const int32_t *cols,
+                                 int64_t n, void *out, const Rule4D *rules /*[4]*/, int kind,
+                                 double kappa, int *status, cudaStream_t st);
+
+}  // namespace bem

@@ -1,0 +1,801 @@
+// sm_103a kernels of the Galerkin quadrature path, FP64 form.
+//
+//  k_touching      one warp per touching triangle pair (Sauter-Schwab rules,
+//                  Section 2.2): lanes stride the q^4 * n_sub points of the
+//                  case's rule, warp-shuffle reduction, result stored in the
+//                  mesh's touching table in the ORIGINAL local vertex order.
+//  k_block_p0/p1   block engine for near-field, coupling and dense blocks
+//                  (Section 2.3 blocks t x s; Section 3 per-case lists are
+//                  replaced by classifying each pair on the fly): one CTA per
+//                  tile of a block, one thread per disjoint triangle pair
+//                  (product rule of a 2D triangle rule, Section 2.2 Duffy),
+//                  touching pairs read from the touching table.
+//  k_pivot         one warp per requested entry g_ij (pivot rows/columns).
+//
+// Kernel values (Eq. 2): laplace 1/(4 pi r), double layer (x-y).n_y/(4 pi r^3),
+// helmholtz exp(i kappa r)/(4 pi r).  sqrt(g_a g_b)/(4 pi) is applied once per
+// pair.
+#include <cuda_runtime.h>
+
+#include "bem_internal.h"
+
+namespace bem {
+
+__constant__ int c_perm[6][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {0, 2, 1}, {1, 0, 2}, {2, 1, 0}};
+
+constexpr double kInv4Pi = 0.079577471545947667884441881686257181;
+
+__device__ __forceinline__ void set_status(int *st, int code) { atomicCAS(st, 0, code); }
+
+struct Tri {
+    double v[3][3];
+    double n[3];
+    double sg;
+};
+
+__device__ __forceinline__ void load_tri(const double *__restrict__ geom, int64_t t, Tri &o)
+{
+    const double *g = geom + t * kGeomStride;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        o.v[k][0] = __ldg(g + 3 * k + 0);
+        o.v[k][1] = __ldg(g + 3 * k + 1);
+        o.v[k][2] = __ldg(g + 3 * k + 2);
+    }
+    o.n[0] = __ldg(g + 9);
+    o.n[1] = __ldg(g + 10);
+    o.n[2] = __ldg(g + 11);
+    o.sg = __ldg(g + 12);
+}
+
+// Kernel value without the 1/(4 pi) factor; d = x - y, nb = trial normal.
+template <int KIND>
+__device__ __forceinline__ void kval(double dx, double dy, double dz, const double *nb,
+                                     double kappa, double &re, double &im)
+{
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double ri = rsqrt(r2);
+    if (KIND == BEM_LAPLACE_SLP) {
+        re = ri;
+        im = 0.0;
+    } else if (KIND == BEM_LAPLACE_DLP) {
+        const double dn = dx * nb[0] + dy * nb[1] + dz * nb[2];
+        re = dn * ri * ri * ri;
+        im = 0.0;
+    } else {
+        double s, c;
+        sincos(kappa * (r2 * ri), &s, &c);
+        re = c * ri;
+        im = s * ri;
+    }
+}
+
+// Touching table index of the pair (a, b), or -1 if b is not a touching neighbour of a.
+__device__ __forceinline__ int find_touching(const MeshView &m, int a, int b)
+{
+    const int lo = __ldg(m.nb_ptr + a), hi = __ldg(m.nb_ptr + a + 1);
+    for (int k = lo; k < hi; ++k)
+        if (__ldg(m.nb_tri + k) == b) return k;
+    return -1;
+}
+
+__device__ __forceinline__ bool touching(int4 A, int4 B)
+{
+    return A.x == B.x || A.x == B.y || A.x == B.z || A.y == B.x || A.y == B.y || A.y == B.z ||
+           A.z == B.x || A.z == B.y || A.z == B.z;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Touching pairs: one warp per pair.
+// ---------------------------------------------------------------------------
+template <int KIND, int BASIS>
+__global__ void __launch_bounds__(256) k_touching(MeshView m, const int *__restrict__ list,
+                                                  int64_t n, const double *__restrict__ rule,
+                                                  int np, double kappa)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= n) return;
+    const int idx = __ldg(list + wid);
+    const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);
+    const int pc = __ldg(m.nb_perm + idx);
+    const int *pa = c_perm[pc / 6], *pb = c_perm[pc % 6];
+    Tri A, B;
+    load_tri(m.geom, a, A);
+    load_tri(m.geom, b, B);
+    double e1a[3], e2a[3], e1b[3], e2b[3], d0[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        e1a[c] = A.v[pa[1]][c] - A.v[pa[0]][c];
+        e2a[c] = A.v[pa[2]][c] - A.v[pa[1]][c];
+        e1b[c] = B.v[pb[1]][c] - B.v[pb[0]][c];
+        e2b[c] = B.v[pb[2]][c] - B.v[pb[1]][c];
+        d0[c] = A.v[pa[0]][c] - B.v[pb[0]][c];
+    }
+    constexpr int NACC = BASIS == BEM_P0 ? 1 : 9;
+    double accr[NACC], acci[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) accr[k] = acci[k] = 0.0;
+    const double *X1 = rule, *X2 = rule + np, *Y1 = rule + 2 * np, *Y2 = rule + 3 * np,
+                 *W = rule + 4 * np;
+    for (int p = lane; p < np; p += 32) {
+        const double x1 = __ldg(X1 + p), x2 = __ldg(X2 + p), y1 = __ldg(Y1 + p),
+                     y2 = __ldg(Y2 + p), w = __ldg(W + p);
+        const double dx = d0[0] + x1 * e1a[0] + x2 * e2a[0] - y1 * e1b[0] - y2 * e2b[0];
+        const double dy = d0[1] + x1 * e1a[1] + x2 * e2a[1] - y1 * e1b[1] - y2 * e2b[1];
+        const double dz = d0[2] + x1 * e1a[2] + x2 * e2a[2] - y1 * e1b[2] - y2 * e2b[2];
+        double kr, ki;
+        kval<KIND>(dx, dy, dz, B.n, kappa, kr, ki);
+        if (BASIS == BEM_P0) {
+            accr[0] += w * kr;
+            if (KIND == BEM_HELMHOLTZ_SLP) acci[0] += w * ki;
+        } else {
+            const double la[3] = {1.0 - x1, x1 - x2, x2};
+            const double lb[3] = {1.0 - y1, y1 - y2, y2};
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double fr = w * kr * la[i];
+                const double fi = w * ki * la[i];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    accr[i * 3 + j] += fr * lb[j];
+                    if (KIND == BEM_HELMHOLTZ_SLP) acci[i * 3 + j] += fi * lb[j];
+                }
+            }
+        }
+    }
+    const double scale = A.sg * B.sg * kInv4Pi;
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) {
+        accr[k] = warp_sum(accr[k]);
+        if (KIND == BEM_HELMHOLTZ_SLP) acci[k] = warp_sum(acci[k]);
+    }
+    if (lane == 0) {
+        if (BASIS == BEM_P0) {
+            m.table[idx] = make_double2(accr[0] * scale, acci[0] * scale);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    m.table[(int64_t)idx * 9 + pa[i] * 3 + pb[j]] =
+                        make_double2(accr[i * 3 + j] * scale, acci[i * 3 + j] * scale);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Regular pair integrals in one thread (product of a 2D rule with itself).
+// ---------------------------------------------------------------------------
+template <int KIND, int NP>
+__device__ __forceinline__ void regular_p0(const Tri &A, const Tri &B, const Rule2D &R,
+                                           double kappa, double &out_re, double &out_im)
+{
+    double e1a[3], e2a[3], d0[3], yx[NP], yy[NP], yz[NP];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        e1a[c] = A.v[1][c] - A.v[0][c];
+        e2a[c] = A.v[2][c] - A.v[1][c];
+        d0[c] = A.v[0][c] - B.v[0][c];
+    }
+    {
+        const double e1b0 = B.v[1][0] - B.v[0][0], e1b1 = B.v[1][1] - B.v[0][1],
+                     e1b2 = B.v[1][2] - B.v[0][2];
+        const double e2b0 = B.v[2][0] - B.v[1][0], e2b1 = B.v[2][1] - B.v[1][1],
+                     e2b2 = B.v[2][2] - B.v[1][2];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            yx[j] = R.s[j] * e1b0 + R.t[j] * e2b0;
+            yy[j] = R.s[j] * e1b1 + R.t[j] * e2b1;
+            yz[j] = R.s[j] * e1b2 + R.t[j] * e2b2;
+        }
+    }
+    double sr = 0.0, si = 0.0;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const double xx = d0[0] + R.s[i] * e1a[0] + R.t[i] * e2a[0];
+        const double xy = d0[1] + R.s[i] * e1a[1] + R.t[i] * e2a[1];
+        const double xz = d0[2] + R.s[i] * e1a[2] + R.t[i] * e2a[2];
+        double ir = 0.0, ii = 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            double kr, ki;
+            kval<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], B.n, kappa, kr, ki);
+            ir += R.w[j] * kr;
+            if (KIND == BEM_HELMHOLTZ_SLP) ii += R.w[j] * ki;
+        }
+        sr += R.w[i] * ir;
+        if (KIND == BEM_HELMHOLTZ_SLP) si += R.w[i] * ii;
+    }
+    const double scale = A.sg * B.sg * kInv4Pi;
+    out_re = sr * scale;
+    out_im = si * scale;
+}
+
+template <int KIND, int NP>
+__device__ __forceinline__ void regular_p1(const Tri &A, const Tri &B, const Rule2D &R,
+                                           double kappa, double *accr, double *acci)
+{
+    double e1a[3], e2a[3], d0[3], yx[NP], yy[NP], yz[NP];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        e1a[c] = A.v[1][c] - A.v[0][c];
+        e2a[c] = A.v[2][c] - A.v[1][c];
+        d0[c] = A.v[0][c] - B.v[0][c];
+    }
+    {
+        const double e1b0 = B.v[1][0] - B.v[0][0], e1b1 = B.v[1][1] - B.v[0][1],
+                     e1b2 = B.v[1][2] - B.v[0][2];
+        const double e2b0 = B.v[2][0] - B.v[1][0], e2b1 = B.v[2][1] - B.v[1][1],
+                     e2b2 = B.v[2][2] - B.v[1][2];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            yx[j] = R.s[j] * e1b0 + R.t[j] * e2b0;
+            yy[j] = R.s[j] * e1b1 + R.t[j] * e2b1;
+            yz[j] = R.s[j] * e1b2 + R.t[j] * e2b2;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) accr[k] = acci[k] = 0.0;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const double xx = d0[0] + R.s[i] * e1a[0] + R.t[i] * e2a[0];
+        const double xy = d0[1] + R.s[i] * e1a[1] + R.t[i] * e2a[1];
+        const double xz = d0[2] + R.s[i] * e1a[2] + R.t[i] * e2a[2];
+        double ir[3] = {0.0, 0.0, 0.0}, ii[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            double kr, ki;
+            kval<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], B.n, kappa, kr, ki);
+            const double lb[3] = {1.0 - R.s[j], R.s[j] - R.t[j], R.t[j]};
+            const double wr = R.w[j] * kr;
+            const double wi = R.w[j] * ki;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                ir[q] += wr * lb[q];
+                if (KIND == BEM_HELMHOLTZ_SLP) ii[q] += wi * lb[q];
+            }
+        }
+        const double la[3] = {1.0 - R.s[i], R.s[i] - R.t[i], R.t[i]};
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const double f = R.w[i] * la[p];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                accr[p * 3 + q] += f * ir[q];
+                if (KIND == BEM_HELMHOLTZ_SLP) acci[p * 3 + q] += f * ii[q];
+            }
+        }
+    }
+    const double scale = A.sg * B.sg * kInv4Pi;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        accr[k] *= scale;
+        acci[k] *= scale;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block bookkeeping
+// ---------------------------------------------------------------------------
+struct BlockInfo {
+    int ok;
+    int r_lo, nr, c_lo, nc;
+    int64_t off;
+    int tile_in_blk;
+};
+
+__device__ __forceinline__ int64_t find_block(const int64_t *prefix, int64_t nb, int64_t tile)
+{
+    // first b with prefix[b] > tile (prefix = inclusive sums of tiles per block)
+    int64_t lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (prefix[mid] > tile) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ BlockInfo block_info(const BlockLaunch &L, const int64_t *prefix,
+                                                int64_t tile, int *status)
+{
+    BlockInfo bi;
+    const int64_t b = find_block(prefix, L.n_blocks, tile);
+    const int t = L.blk_row[b], s = L.blk_col[b];
+    bi.ok = 0;
+    if (t < 0 || t >= L.n_row_clusters || s < 0 || s >= L.n_col_clusters) {
+        set_status(status, BEM_ERR_INVALID_ARG);
+        return bi;
+    }
+    bi.r_lo = L.row_ptr[t];
+    bi.nr = L.row_ptr[t + 1] - bi.r_lo;
+    bi.c_lo = L.col_ptr[s];
+    bi.nc = L.col_ptr[s + 1] - bi.c_lo;
+    bi.off = L.blk_off[b];
+    bi.tile_in_blk = (int)(tile - (b > 0 ? prefix[b - 1] : 0));
+    bi.ok = (bi.nr > 0 && bi.nc > 0);
+    return bi;
+}
+
+// Tiles per block -> inclusive prefix sums (single CTA, chunked).
+__global__ void __launch_bounds__(1024) k_tile_prefix(BlockLaunch L, int tr, int tc,
+                                                      int64_t *prefix, int *status)
+{
+    __shared__ int64_t part[1024];
+    const int64_t n = L.n_blocks;
+    const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = threadIdx.x * chunk, hi = min(n, lo + chunk);
+    int64_t sum = 0;
+    for (int64_t b = lo; b < hi; ++b) {
+        const int t = L.blk_row[b], s = L.blk_col[b];
+        int64_t tiles = 0;
+        if (t >= 0 && t < L.n_row_clusters && s >= 0 && s < L.n_col_clusters) {
+            const int nr = L.row_ptr[t + 1] - L.row_ptr[t];
+            const int nc = L.col_ptr[s + 1] - L.col_ptr[s];
+            if (nr < 0 || nc < 0) set_status(status, BEM_ERR_INVALID_ARG);
+            else tiles = (int64_t)((nr + tr - 1) / tr) * ((nc + tc - 1) / tc);
+        } else {
+            set_status(status, BEM_ERR_INVALID_ARG);
+        }
+        sum += tiles;
+        prefix[b] = sum;   // local inclusive sum, fixed below
+    }
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        int64_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const int64_t base = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
+    for (int64_t b = lo; b < hi; ++b) prefix[b] += base;
+}
+
+// ---------------------------------------------------------------------------
+// Block engine, piecewise constant: tile = 32 rows x 8 columns, one thread per entry.
+// ---------------------------------------------------------------------------
+constexpr int kP0Cols = 8;
+
+template <int KIND, int NP>
+__global__ void __launch_bounds__(256) k_block_p0(MeshView m, BlockLaunch L, Rule2D R,
+                                                  const int64_t *__restrict__ prefix,
+                                                  int *status)
+{
+    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
+    const int lr = threadIdx.x & 31, lc = threadIdx.x >> 5;
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const BlockInfo bi = block_info(L, prefix, tile, status);
+        if (!bi.ok) continue;
+        const int ntr = (bi.nr + kTile - 1) / kTile;
+        const int r = (bi.tile_in_blk % ntr) * kTile + lr;
+        const int c = (bi.tile_in_blk / ntr) * kP0Cols + lc;
+        if (r >= bi.nr || c >= bi.nc) continue;
+        const int a = L.row_idx[bi.r_lo + r], b = L.col_idx[bi.c_lo + c];
+        if (a < 0 || a >= m.nt || b < 0 || b >= m.nt) {
+            set_status(status, BEM_ERR_INVALID_ARG);
+            continue;
+        }
+        if (L.lower_only && a < b) continue;
+        double re, im;
+        const int4 va = __ldg(m.tvid + a), vb = __ldg(m.tvid + b);
+        if (touching(va, vb)) {
+            const int k = L.allow_touching ? find_touching(m, a, b) : -1;
+            if (k < 0) {
+                set_status(status, BEM_ERR_INVALID_ARG);
+                continue;
+            }
+            const double2 v = m.table[k];
+            re = v.x;
+            im = v.y;
+        } else {
+            Tri A, B;
+            load_tri(m.geom, a, A);
+            load_tri(m.geom, b, B);
+            regular_p0<KIND, NP>(A, B, R, L.kappa, re, im);
+        }
+        const int64_t o = bi.off + (int64_t)r + (int64_t)c * bi.nr;
+        if (KIND == BEM_HELMHOLTZ_SLP) reinterpret_cast<double2 *>(L.out)[o] = make_double2(re, im);
+        else reinterpret_cast<double *>(L.out)[o] = re;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block engine, piecewise linear: tile = 32 x 32 vertices.  The triangles
+// touching the tile's rows (Ta) and columns (Tb) are collected in shared
+// memory; the 3x3 local matrices of all pairs Ta x Tb are computed chunk by
+// chunk (one thread per pair) into shared memory and gathered by the owner
+// thread of each entry in a fixed order (deterministic sums).
+// ---------------------------------------------------------------------------
+constexpr int kP1Cap = 512;                 // pairs per chunk
+constexpr int kP1MaxTri = kTile * kMaxDegP1;
+
+struct P1Smem {
+    int rows[kTile], cols[kTile];
+    int ta[kP1MaxTri], tb[kP1MaxTri];
+    int rl[kTile][kMaxDegP1], cl[kTile][kMaxDegP1];
+    int rl_n[kTile], cl_n[kTile];
+    int cnt_r[kTile], off_r[kTile], cnt_c[kTile], off_c[kTile];
+    int nta, ntb;
+};
+
+__device__ __forceinline__ int pos_in(const int *set, int n, int v)
+{
+    for (int k = 0; k < n; ++k)
+        if (set[k] == v) return k;
+    return -1;
+}
+
+__device__ __forceinline__ int owner_pos(const MeshView &m, int T, const int *set, int n)
+{
+    const int4 tv = __ldg(m.tvid + T);
+    int p = pos_in(set, n, tv.x);
+    int q = pos_in(set, n, tv.y);
+    int r = pos_in(set, n, tv.z);
+    int best = 1 << 30;
+    if (p >= 0) best = min(best, p);
+    if (q >= 0) best = min(best, q);
+    if (r >= 0) best = min(best, r);
+    return best;
+}
+
+// Collect the triangles touching the vertex set `set` (n <= 32): deterministic
+// order (by owner position, then adjacency order), and per vertex the list of
+// (triangle slot << 2 | local index).
+__device__ void p1_support(const MeshView &m, const int *set, int n, int *tri, int *cnt,
+                           int *off, int (*lists)[kMaxDegP1], int *list_n, int *ntri,
+                           int *status)
+{
+    const int tid = threadIdx.x;
+    if (tid < n) {
+        const int v = set[tid];
+        const int lo = __ldg(m.vt_ptr + v), hi = __ldg(m.vt_ptr + v + 1);
+        int c = 0;
+        for (int k = lo; k < hi; ++k)
+            if (owner_pos(m, __ldg(m.vt_tri + k), set, n) == tid) ++c;
+        cnt[tid] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int s = 0;
+        for (int k = 0; k < n; ++k) {
+            off[k] = s;
+            s += cnt[k];
+        }
+        *ntri = s;
+    }
+    __syncthreads();
+    if (tid < n) {
+        const int v = set[tid];
+        const int lo = __ldg(m.vt_ptr + v), hi = __ldg(m.vt_ptr + v + 1);
+        int c = off[tid];
+        for (int k = lo; k < hi; ++k) {
+            const int T = __ldg(m.vt_tri + k);
+            if (owner_pos(m, T, set, n) == tid) tri[c++] = T;
+        }
+    }
+    __syncthreads();
+    if (tid < n) {
+        const int v = set[tid];
+        const int lo = __ldg(m.vt_ptr + v), hi = __ldg(m.vt_ptr + v + 1);
+        for (int k = lo; k < hi; ++k) {
+            const int T = __ldg(m.vt_tri + k);
+            const int q = owner_pos(m, T, set, n);
+            int slot = -1;
+            for (int u = off[q]; u < off[q] + cnt[q]; ++u)
+                if (tri[u] == T) slot = u;
+            const int4 tv = __ldg(m.tvid + T);
+            const int loc = tv.x == v ? 0 : (tv.y == v ? 1 : 2);
+            lists[tid][k - lo] = (slot << 2) | loc;
+        }
+        list_n[tid] = hi - lo;
+    }
+    __syncthreads();
+}
+
+template <int KIND, int NP>
+__global__ void __launch_bounds__(256) k_block_p1(MeshView m, BlockLaunch L, Rule2D R,
+                                                  const int64_t *__restrict__ prefix,
+                                                  int *status)
+{
+    constexpr bool CPLX = KIND == BEM_HELMHOLTZ_SLP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P1Smem &S = *reinterpret_cast<P1Smem *>(smem_raw);
+    double *buf_r = reinterpret_cast<double *>(smem_raw + ((sizeof(P1Smem) + 15) & ~size_t(15)));
+    double *buf_i = buf_r + kP1Cap * 9;
+    const int tid = threadIdx.x;
+    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
+
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const BlockInfo bi = block_info(L, prefix, tile, status);
+        if (!bi.ok) continue;   // uniform across the CTA
+        const int ntr = (bi.nr + kTile - 1) / kTile;
+        const int r0 = (bi.tile_in_blk % ntr) * kTile, c0 = (bi.tile_in_blk / ntr) * kTile;
+        const int tr = min(kTile, bi.nr - r0), tc = min(kTile, bi.nc - c0);
+        __shared__ int bad;
+        if (tid == 0) bad = 0;
+        __syncthreads();
+        if (tid < tr) {
+            const int v = L.row_idx[bi.r_lo + r0 + tid];
+            if (v < 0 || v >= m.nv) bad = 1;
+            S.rows[tid] = v;
+        }
+        if (tid >= 64 && tid - 64 < tc) {
+            const int v = L.col_idx[bi.c_lo + c0 + tid - 64];
+            if (v < 0 || v >= m.nv) bad = 1;
+            S.cols[tid - 64] = v;
+        }
+        __syncthreads();
+        if (bad) {
+            if (tid == 0) set_status(status, BEM_ERR_INVALID_ARG);
+            __syncthreads();
+            continue;
+        }
+        p1_support(m, S.rows, tr, S.ta, S.cnt_r, S.off_r, S.rl, S.rl_n, &S.nta, status);
+        p1_support(m, S.cols, tc, S.tb, S.cnt_c, S.off_c, S.cl, S.cl_n, &S.ntb, status);
+        const int nta = S.nta, ntb = S.ntb;
+        const int ia_step = max(1, kP1Cap / max(ntb, 1));
+        double accr[4] = {0, 0, 0, 0}, acci[4] = {0, 0, 0, 0};
+        const int er = tid & 31;
+        for (int ia0 = 0; ia0 < nta; ia0 += ia_step) {
+            const int ia1 = min(nta, ia0 + ia_step);
+            const int npairs = (ia1 - ia0) * ntb;
+            for (int p = tid; p < npairs; p += blockDim.x) {
+                const int a = S.ta[ia0 + p / ntb], b = S.tb[p % ntb];
+                const int4 va = __ldg(m.tvid + a), vb = __ldg(m.tvid + b);
+                double vr[9], vi[9];
+                if (touching(va, vb)) {
+                    const int k = L.allow_touching ? find_touching(m, a, b) : -1;
+                    if (k < 0) {
+                        set_status(status, BEM_ERR_INVALID_ARG);
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) vr[q] = vi[q] = 0.0;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) {
+                            const double2 t = m.table[(int64_t)k * 9 + q];
+                            vr[q] = t.x;
+                            vi[q] = t.y;
+                        }
+                    }
+                } else {
+                    Tri A, B;
+                    load_tri(m.geom, a, A);
+                    load_tri(m.geom, b, B);
+                    regular_p1<KIND, NP>(A, B, R, L.kappa, vr, vi);
+                }
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    buf_r[p * 9 + q] = vr[q];
+                    if (CPLX) buf_i[p * 9 + q] = vi[q];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int ec = (tid >> 5) + 8 * e;
+                if (er < tr && ec < tc) {
+                    for (int u = 0; u < S.rl_n[er]; ++u) {
+                        const int ia = S.rl[er][u] >> 2, la = S.rl[er][u] & 3;
+                        if (ia < ia0 || ia >= ia1) continue;
+                        const int rowbase = (ia - ia0) * ntb;
+                        for (int v = 0; v < S.cl_n[ec]; ++v) {
+                            const int ib = S.cl[ec][v] >> 2, lb = S.cl[ec][v] & 3;
+                            const int q = (rowbase + ib) * 9 + la * 3 + lb;
+                            accr[e] += buf_r[q];
+                            if (CPLX) acci[e] += buf_i[q];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int ec = (tid >> 5) + 8 * e;
+            if (er < tr && ec < tc) {
+                if (L.lower_only && S.rows[er] < S.cols[ec]) continue;
+                const int64_t o = bi.off + (int64_t)(r0 + er) + (int64_t)(c0 + ec) * bi.nr;
+                if (CPLX) reinterpret_cast<double2 *>(L.out)[o] = make_double2(accr[e], acci[e]);
+                else reinterpret_cast<double *>(L.out)[o] = accr[e];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+size_t p1_smem_bytes(bool cplx)
+{
+    return ((sizeof(P1Smem) + 15) & ~size_t(15)) + (size_t)kP1Cap * 9 * sizeof(double) * (cplx ? 2 : 1);
+}
+
+// ---------------------------------------------------------------------------
+// Arbitrary entries: one warp per entry, lanes stride the points of each pair's rule.
+// ---------------------------------------------------------------------------
+struct RuleSet {
+    const double *d[4];
+    int n[4];
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_pivot(MeshView m, const int32_t *__restrict__ rows,
+                                               const int32_t *__restrict__ cols, int64_t n,
+                                               void *out, RuleSet rs, double kappa, int *status)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= n) return;
+    const int i = rows[wid], j = cols[wid];
+    const int64_t lim = m.basis == BEM_P0 ? m.nt : m.nv;
+    if (i < 0 || i >= lim || j < 0 || j >= lim) {
+        if (lane == 0) set_status(status, BEM_ERR_INVALID_ARG);
+        return;
+    }
+    int alo, ahi, blo, bhi;
+    if (m.basis == BEM_P0) {
+        alo = 0; ahi = 1; blo = 0; bhi = 1;
+    } else {
+        alo = __ldg(m.vt_ptr + i); ahi = __ldg(m.vt_ptr + i + 1);
+        blo = __ldg(m.vt_ptr + j); bhi = __ldg(m.vt_ptr + j + 1);
+    }
+    double sr = 0.0, si = 0.0;
+    for (int ka = alo; ka < ahi; ++ka) {
+        const int a = m.basis == BEM_P0 ? i : __ldg(m.vt_tri + ka);
+        const int4 va = __ldg(m.tvid + a);
+        const int la = m.basis == BEM_P0 ? -1 : (va.x == i ? 0 : (va.y == i ? 1 : 2));
+        Tri A;
+        load_tri(m.geom, a, A);
+        for (int kb = blo; kb < bhi; ++kb) {
+            const int b = m.basis == BEM_P0 ? j : __ldg(m.vt_tri + kb);
+            const int4 vb = __ldg(m.tvid + b);
+            const int lb = m.basis == BEM_P0 ? -1 : (vb.x == j ? 0 : (vb.y == j ? 1 : 2));
+            int cas = kRegular, pc = 0;
+            if (touching(va, vb)) {
+                const int k = find_touching(m, a, b);
+                cas = __ldg(m.nb_case + k);
+                pc = __ldg(m.nb_perm + k);
+            }
+            const int *pa = c_perm[pc / 6], *pb = c_perm[pc % 6];
+            int ca = -1, cb = -1;   // canonical positions of the basis vertices
+            for (int q = 0; q < 3; ++q) {
+                if (pa[q] == la) ca = q;
+                if (pb[q] == lb) cb = q;
+            }
+            Tri B;
+            load_tri(m.geom, b, B);
+            double e1a[3], e2a[3], e1b[3], e2b[3], d0[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                e1a[c] = A.v[pa[1]][c] - A.v[pa[0]][c];
+                e2a[c] = A.v[pa[2]][c] - A.v[pa[1]][c];
+                e1b[c] = B.v[pb[1]][c] - B.v[pb[0]][c];
+                e2b[c] = B.v[pb[2]][c] - B.v[pb[1]][c];
+                d0[c] = A.v[pa[0]][c] - B.v[pb[0]][c];
+            }
+            const double *rule = rs.d[cas];
+            const int np = rs.n[cas];
+            double pr = 0.0, pi = 0.0;
+            for (int p = lane; p < np; p += 32) {
+                const double x1 = __ldg(rule + p), x2 = __ldg(rule + np + p),
+                             y1 = __ldg(rule + 2 * np + p), y2 = __ldg(rule + 3 * np + p),
+                             w = __ldg(rule + 4 * np + p);
+                const double dx = d0[0] + x1 * e1a[0] + x2 * e2a[0] - y1 * e1b[0] - y2 * e2b[0];
+                const double dy = d0[1] + x1 * e1a[1] + x2 * e2a[1] - y1 * e1b[1] - y2 * e2b[1];
+                const double dz = d0[2] + x1 * e1a[2] + x2 * e2a[2] - y1 * e1b[2] - y2 * e2b[2];
+                double kr, ki;
+                kval<KIND>(dx, dy, dz, B.n, kappa, kr, ki);
+                double f = w;
+                if (ca >= 0) f *= (ca == 0 ? 1.0 - x1 : (ca == 1 ? x1 - x2 : x2));
+                if (cb >= 0) f *= (cb == 0 ? 1.0 - y1 : (cb == 1 ? y1 - y2 : y2));
+                pr += f * kr;
+                if (KIND == BEM_HELMHOLTZ_SLP) pi += f * ki;
+            }
+            const double scale = A.sg * B.sg * kInv4Pi;
+            sr += pr * scale;
+            si += pi * scale;
+        }
+    }
+    sr = warp_sum(sr);
+    if (KIND == BEM_HELMHOLTZ_SLP) si = warp_sum(si);
+    if (lane == 0) {
+        if (KIND == BEM_HELMHOLTZ_SLP) reinterpret_cast<double2 *>(out)[wid] = make_double2(sr, si);
+        else reinterpret_cast<double *>(out)[wid] = sr;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_tile_prefix(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
+                               int *status, cudaStream_t st)
+{
+    if (L.n_blocks <= 0) return cudaSuccess;
+    k_tile_prefix<<<1, 1024, 0, st>>>(L, tr, tc, prefix, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
+                            const Rule4D &rule, int kind, double kappa, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = (n + 7) / 8;
+    const bool p1 = m.basis == BEM_P1;
+#define BEM_TOUCH(K, B) k_touching<K, B><<<(unsigned)blocks, 256, 0, st>>>(m, list, n, rule.d, rule.n, kappa)
+    switch (kind) {
+    case BEM_LAPLACE_SLP: if (p1) BEM_TOUCH(BEM_LAPLACE_SLP, BEM_P1); else BEM_TOUCH(BEM_LAPLACE_SLP, BEM_P0); break;
+    case BEM_LAPLACE_DLP: if (p1) BEM_TOUCH(BEM_LAPLACE_DLP, BEM_P1); else BEM_TOUCH(BEM_LAPLACE_DLP, BEM_P0); break;
+    default: if (p1) BEM_TOUCH(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TOUCH(BEM_HELMHOLTZ_SLP, BEM_P0); break;
+    }
+#undef BEM_TOUCH
+    (void)cas;
+    return cudaGetLastError();
+}
+
+template <int KIND, int NP>
+static cudaError_t block_np(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
+                            const int64_t *prefix, int *status, int grid, cudaStream_t st)
+{
+    if (m.basis == BEM_P0) {
+        k_block_p0<KIND, NP><<<grid, 256, 0, st>>>(m, L, R, prefix, status);
+    } else {
+        const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP);
+        cudaError_t e = cudaFuncSetAttribute(k_block_p1<KIND, NP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_block_p1<KIND, NP><<<grid, 256, sm, st>>>(m, L, R, prefix, status);
+    }
+    return cudaGetLastError();
+}
+
+template <int KIND>
+static cudaError_t block_kind(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
+                              const int64_t *prefix, int *status, int grid, cudaStream_t st)
+{
+    switch (R.np) {
+    case 4: return block_np<KIND, 4>(m, L, R, prefix, status, grid, st);
+    case 7: return block_np<KIND, 7>(m, L, R, prefix, status, grid, st);
+    case 9: return block_np<KIND, 9>(m, L, R, prefix, status, grid, st);
+    case 16: return block_np<KIND, 16>(m, L, R, prefix, status, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
+                                const int64_t *prefix, int *status, int grid, cudaStream_t st)
+{
+    if (L.n_blocks <= 0) return cudaSuccess;
+    switch (L.kind) {
+    case BEM_LAPLACE_SLP: return block_kind<BEM_LAPLACE_SLP>(m, L, R, prefix, status, grid, st);
+    case BEM_LAPLACE_DLP: return block_kind<BEM_LAPLACE_DLP>(m, L, R, prefix, status, grid, st);
+    default: return block_kind<BEM_HELMHOLTZ_SLP>(m, L, R, prefix, status, grid, st);
+    }
+}
+
+cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const int32_t *cols,
+                                 int64_t n, void *out, const Rule4D *rules, int kind,
+                                 double kappa, int *status, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    RuleSet rs;
+    for (int c = 0; c < 4; ++c) {
+        rs.d[c] = rules[c].d;
+        rs.n[c] = rules[c].n;
+    }
+    const int64_t blocks = (n + 7) / 8;
+    switch (kind) {
+    case BEM_LAPLACE_SLP: k_pivot<BEM_LAPLACE_SLP><<<(unsigned)blocks, 256, 0, st>>>(m, rows, cols, n, out, rs, kappa, status); break;
+    case BEM_LAPLACE_DLP: k_pivot<BEM_LAPLACE_DLP><<<(unsigned)blocks, 256, 0, st>>>(m, rows, cols, n, out, rs, kappa, status); break;
+    default: k_pivot<BEM_HELMHOLTZ_SLP><<<(unsigned)blocks, 256, 0, st>>>(m, rows, cols, n, out, rs, kappa, status); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace bem

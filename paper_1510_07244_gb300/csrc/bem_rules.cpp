@@ -1,0 +1,201 @@
+// Quadrature rules of the library (host side; uploaded once per context).
+//
+//  * Gauss-Legendre on [0,1]: Newton iteration in long double on P_q with a
+//    Tricomi-type initial guess for each root.
+//  * Regular (disjoint) pairs (Section 2.2): the Duffy map T(s,t) = (s, s t)
+//    on each triangle turns D into [0,1]^2 with Jacobian s, so the 4D rule
+//    is the product of two copies of a 2D triangle rule (q^2 points); the
+//    alternative 2D rule is Radon's 7-point degree-5 formula.
+//  * Touching pairs (Section 2.2, Sauter-Schwab): [0,1]^4 rules obtained by
+//    splitting D x D into subdomains on which a Duffy-type map collapses the
+//    singular set.  Our own derivation, with R+ = {y1 <= x1} and the
+//    scaling x1 = xi (x = xi (1, a), y = xi (b, c), Jacobian xi^3):
+//      common vertex (shared vertex = local vertex 0 of both triangles):
+//        b = eta2, c = eta2 eta3                      J = xi^3 eta2
+//      common edge (shared edge = local edge v0 -> v1 of both), u = 1 - b:
+//        cone over {a = 1}:    (a,u,c) = eta1 (1, eta2 (1-eta3), eta2 eta3),
+//                                                    J = xi^3 eta1^2 eta2
+//        cone over {u + c = 1}: (a,u,c) = eta1 (eta2, eta3, 1-eta3),
+//                                                    J = xi^3 eta1^2
+//      identical (u = 1 - b, w = a - c; three Duffy triangles of the (u,w)
+//        quadrilateral around the singular line u = w = 0):
+//        (u, w) = eta1 (eta2, 1),         a = eta1 + (1-eta1) eta3
+//        (u, w) = eta1 (1, eta2),         a = eta1 eta2 + (1-eta1) eta3
+//        (u, w) = eta1 (1-eta2, -eta2),   a = (1-eta1) eta3
+//                                                    J = xi^3 eta1 (1-eta1)
+//    Every piece is used as is and with x and y exchanged (R- = swap of R+):
+//    2, 4 and 6 subdomains with q^4 points each.
+#include <cmath>
+#include <functional>
+#include <vector>
+
+#include "bem_internal.h"
+
+namespace bem {
+
+const int kPerm[6][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {0, 2, 1}, {1, 0, 2}, {2, 1, 0}};
+
+bool gauss_legendre_unit(int q, std::vector<double> &x, std::vector<double> &w)
+{
+    if (q < 1 || q > 64) return false;
+    x.assign(q, 0.0);
+    w.assign(q, 0.0);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int i = 1; i <= q; ++i) {
+        // Tricomi: theta = pi (4i - 1) / (4q + 2), z ~ (1 - (q-1)/(8 q^3)) cos theta
+        long double th = pi * (4.0L * i - 1.0L) / (4.0L * q + 2.0L);
+        long double z = (1.0L - (q - 1.0L) / (8.0L * q * q * q)) * std::cos(th);
+        long double pq = 0, pqm1 = 0;
+        for (int it = 0; it < 60; ++it) {
+            long double a = 1.0L, b = z;      // P_0, P_1
+            if (q == 1) { pq = z; pqm1 = 1.0L; }
+            else {
+                for (int k = 2; k <= q; ++k) {
+                    long double c = ((2.0L * k - 1.0L) * z * b - (k - 1.0L) * a) / k;
+                    a = b;
+                    b = c;
+                }
+                pq = b;
+                pqm1 = a;
+            }
+            long double dp = q * (pqm1 - z * pq) / (1.0L - z * z);
+            long double step = pq / dp;
+            z -= step;
+            if (std::fabs((double)step) < 1e-19) break;
+        }
+        long double a = 1.0L, b = z;
+        if (q == 1) { pq = z; pqm1 = 1.0L; }
+        else {
+            for (int k = 2; k <= q; ++k) {
+                long double c = ((2.0L * k - 1.0L) * z * b - (k - 1.0L) * a) / k;
+                a = b;
+                b = c;
+            }
+            pq = b;
+            pqm1 = a;
+        }
+        long double dp = q * (pqm1 - z * pq) / (1.0L - z * z);
+        // roots come out in descending z; store ascending on [0,1]
+        x[i - 1] = (double)((1.0L - z) / 2.0L);
+        w[i - 1] = (double)(1.0L / ((1.0L - z * z) * dp * dp));
+    }
+    return true;
+}
+
+bool make_rule2d(int regular_rule, int q, Rule2D &out)
+{
+    if (regular_rule == BEM_RULE_TRI7) {
+        const double r = std::sqrt(15.0);
+        const double p1 = (6.0 - r) / 21.0, p2 = (6.0 + r) / 21.0;
+        const double w0 = 9.0 / 80.0;                 // 9/40 * |D|
+        const double w1 = (155.0 - r) / 2400.0, w2 = (155.0 + r) / 2400.0;
+        // barycentric (l0, l1, l2) -> (s, t) = (l1 + l2, l2)
+        const double L[7][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3},
+                                {1 - 2 * p1, p1, p1}, {p1, 1 - 2 * p1, p1}, {p1, p1, 1 - 2 * p1},
+                                {1 - 2 * p2, p2, p2}, {p2, 1 - 2 * p2, p2}, {p2, p2, 1 - 2 * p2}};
+        const double W[7] = {w0, w1, w1, w1, w2, w2, w2};
+        out.np = 7;
+        for (int k = 0; k < 7; ++k) {
+            out.s[k] = L[k][1] + L[k][2];
+            out.t[k] = L[k][2];
+            out.w[k] = W[k];
+        }
+        return true;
+    }
+    if (regular_rule != BEM_RULE_DUFFY || q < 1 || q * q > kMaxNp) return false;
+    std::vector<double> g, gw;
+    gauss_legendre_unit(q, g, gw);
+    out.np = q * q;
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) {
+            out.s[i * q + j] = g[i];
+            out.t[i * q + j] = g[i] * g[j];
+            out.w[i * q + j] = gw[i] * gw[j] * g[i];
+        }
+    return true;
+}
+
+namespace {
+
+struct Pt {
+    double x1, x2, y1, y2, w;
+};
+
+// One piece of R+: maps (xi, e1, e2, e3) to (x, y) and its Jacobian.
+using Piece = std::function<Pt(double, double, double, double)>;
+
+std::vector<Piece> pieces(int cas)
+{
+    std::vector<Piece> P;
+    if (cas == kVertex) {
+        P.push_back([](double xi, double e1, double e2, double e3) {
+            return Pt{xi, xi * e1, xi * e2, xi * e2 * e3, xi * xi * xi * e2};
+        });
+    } else if (cas == kEdge) {
+        P.push_back([](double xi, double e1, double e2, double e3) {
+            double a = e1, u = e1 * e2 * (1.0 - e3), c = e1 * e2 * e3;
+            return Pt{xi, xi * a, xi * (1.0 - u), xi * c, xi * xi * xi * e1 * e1 * e2};
+        });
+        P.push_back([](double xi, double e1, double e2, double e3) {
+            double a = e1 * e2, u = e1 * e3, c = e1 * (1.0 - e3);
+            return Pt{xi, xi * a, xi * (1.0 - u), xi * c, xi * xi * xi * e1 * e1};
+        });
+    } else if (cas == kIdentical) {
+        auto mk = [](double u, double w, double a, double xi, double e1) {
+            return Pt{xi, xi * a, xi * (1.0 - u), xi * (a - w), xi * xi * xi * e1 * (1.0 - e1)};
+        };
+        P.push_back([mk](double xi, double e1, double e2, double e3) {
+            return mk(e1 * e2, e1, e1 + (1.0 - e1) * e3, xi, e1);
+        });
+        P.push_back([mk](double xi, double e1, double e2, double e3) {
+            return mk(e1, e1 * e2, e1 * e2 + (1.0 - e1) * e3, xi, e1);
+        });
+        P.push_back([mk](double xi, double e1, double e2, double e3) {
+            return mk(e1 * (1.0 - e2), -e1 * e2, (1.0 - e1) * e3, xi, e1);
+        });
+    }
+    return P;
+}
+
+}  // namespace
+
+bool make_rule4d_host(int cas, int regular_rule, int q, std::vector<double> &soa)
+{
+    std::vector<Pt> pts;
+    if (cas == kRegular) {
+        Rule2D r;
+        if (!make_rule2d(regular_rule, q, r)) return false;
+        for (int i = 0; i < r.np; ++i)
+            for (int j = 0; j < r.np; ++j)
+                pts.push_back(Pt{r.s[i], r.t[i], r.s[j], r.t[j], r.w[i] * r.w[j]});
+    } else {
+        std::vector<double> g, gw;
+        if (!gauss_legendre_unit(q, g, gw)) return false;
+        for (const Piece &f : pieces(cas))
+            for (int swap = 0; swap < 2; ++swap)
+                for (int i = 0; i < q; ++i)
+                    for (int j = 0; j < q; ++j)
+                        for (int k = 0; k < q; ++k)
+                            for (int l = 0; l < q; ++l) {
+                                Pt p = f(g[i], g[j], g[k], g[l]);
+                                p.w *= gw[i] * gw[j] * gw[k] * gw[l];
+                                if (swap) {
+                                    std::swap(p.x1, p.y1);
+                                    std::swap(p.x2, p.y2);
+                                }
+                                pts.push_back(p);
+                            }
+    }
+    const size_t n = pts.size();
+    soa.assign(5 * n, 0.0);
+    for (size_t k = 0; k < n; ++k) {
+        soa[k] = pts[k].x1;
+        soa[n + k] = pts[k].x2;
+        soa[2 * n + k] = pts[k].y1;
+        soa[3 * n + k] = pts[k].y2;
+        soa[4 * n + k] = pts[k].w;
+    }
+    return true;
+}
+
+}  // namespace bem

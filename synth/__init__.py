@@ -9,10 +9,11 @@ from .rng import SplitMix64
 from .meshes import (Mesh, icosphere, octasphere, cube_surface, torus,
                      jitter, icosahedron, octahedron, two_triangles,
                      mean_edge_length)
+from . import workloads
 from .structure import (ClusterTree, build_cluster_tree, build_block_partition,
                         seeded_pivots, BlockPartition)
 
 __all__ = ["SplitMix64", "Mesh", "icosphere", "octasphere", "cube_surface",
            "torus", "jitter", "icosahedron", "octahedron", "two_triangles",
            "mean_edge_length", "ClusterTree", "build_cluster_tree",
-           "build_block_partition", "seeded_pivots", "BlockPartition"]
+           "build_block_partition", "seeded_pivots", "BlockPartition", "workloads"]

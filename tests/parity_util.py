@@ -1,0 +1,40 @@
+"""Helpers of the GPU parity tests: device upload of block sets, the relative
+error measure, and oracle evaluation of sampled entries."""
+import numpy as np
+
+import oracle
+
+
+def rel_err(got, ref, row_ids):
+    """|got - ref| / max(|ref|, 1e-3 * max |ref| over the same row), elementwise.
+
+    Entries can be exactly zero (coplanar double layer), so each entry is
+    measured against the largest entry of its row among the compared ones."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    row_ids = np.asarray(row_ids)
+    scale = np.zeros(row_ids.max() + 1 if len(row_ids) else 1)
+    np.maximum.at(scale, row_ids, np.abs(ref))
+    den = np.maximum(np.abs(ref), 1e-3 * scale[row_ids])
+    den = np.where(den > 0, den, 1.0)
+    return np.abs(got - ref) / den
+
+
+def to_dev(a, dtype):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def block_job(pkg, mesh_id, bs, kernel, kappa, quad, out):
+    import torch
+    return pkg.BlockJob(mesh_id, to_dev(bs.row_ptr, torch.int32), to_dev(bs.row_idx, torch.int32),
+                        to_dev(bs.col_ptr, torch.int32), to_dev(bs.col_idx, torch.int32),
+                        to_dev(bs.blk_row, torch.int32), to_dev(bs.blk_col, torch.int32),
+                        to_dev(bs.blk_off, torch.int64), out,
+                        pkg.kernel_desc(kernel, kappa), pkg.quad_desc(**quad))
+
+
+def oracle_entries(mesh, basis, rows, cols, kernel, kappa, quad):
+    z = oracle.entries(mesh.verts, mesh.tris, rows, cols, kernel=kernel, kappa=kappa,
+                       basis=basis, **quad)
+    return z if kernel == "helmholtz_slp" else z.real

@@ -1,0 +1,262 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle,
+element by element on the same seeded inputs.
+
+Tolerance: relative error <= 1e-10 per entry for the FP64 form (measured as
+in parity_util.rel_err).  Both sides evaluate the same rule with the same
+canonical vertex orders; only the summation order differs (warp trees and a
+per-pair scaling on the GPU, plain nested sums in the oracle).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth.workloads import BlockSet, h2_blocks
+from parity_util import block_job, oracle_entries, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+KERNELS = [("laplace_slp", 0.0), ("laplace_dlp", 0.0), ("helmholtz_slp", 4.0)]
+QUADS = {"paper": dict(q_regular=3, regular_rule="duffy", q_identical=5, q_edge=5, q_vertex=5),
+         "c1": dict(q_regular=3, regular_rule="tri7", q_identical=4, q_edge=4, q_vertex=4),
+         "q4": dict(q_regular=4, regular_rule="duffy", q_identical=6, q_edge=6, q_vertex=6),
+         "low": dict(q_regular=2, regular_rule="duffy", q_identical=2, q_edge=3, q_vertex=2)}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1510_07244_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def ctx(pkg):
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+def _out(n, kernel):
+    import torch
+    dt = torch.complex128 if kernel == "helmholtz_slp" else torch.float64
+    return torch.full((max(n, 1),), float("nan"), dtype=dt, device="cuda")
+
+
+def _dense(ctx, pkg, mesh, basis, kernel, kappa, quad, lower=0):
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, basis)
+    n = mesh.nt if basis == "p0" else mesh.nv
+    out = _out(n * n, kernel)
+    ctx.bem_assemble_dense(mid, pkg.kernel_desc(kernel, kappa), pkg.quad_desc(**quad), lower, out)
+    ctx.bem_sync()
+    ctx.bem_mesh_free(mid)
+    return out.cpu().numpy()[: n * n].reshape(n, n).T, n
+
+
+MESHES = {
+    "octahedron": lambda: synth.octahedron(),
+    "ico2": lambda: synth.jitter(synth.icosphere(2), 0.05, 11),
+    "cube3": lambda: synth.jitter(synth.cube_surface(3), 0.05, 12),
+    "torus": lambda: synth.jitter(synth.torus(13, 5), 0.05, 13),
+}
+
+
+@pytest.mark.parametrize("meshname", ["octahedron", "ico2", "cube3", "torus"])
+@pytest.mark.parametrize("kernel,kappa", KERNELS)
+@pytest.mark.parametrize("basis", ["p0", "p1"])
+def test_dense_matches_oracle(ctx, pkg, meshname, kernel, kappa, basis):
+    mesh = MESHES[meshname]()
+    quad = QUADS["paper"]
+    got, n = _dense(ctx, pkg, mesh, basis, kernel, kappa, quad)
+    rows = np.repeat(np.arange(n), n)
+    cols = np.tile(np.arange(n), n)
+    ref = oracle_entries(mesh, basis, rows, cols, kernel, kappa, quad).reshape(n, n)
+    assert np.isfinite(got).all()
+    assert rel_err(got.ravel(), ref.ravel(), rows).max() <= TOL
+
+
+@pytest.mark.parametrize("qname", ["c1", "q4", "low"])
+@pytest.mark.parametrize("basis", ["p0", "p1"])
+def test_dense_other_orders(ctx, pkg, qname, basis):
+    mesh = MESHES["cube3"]()
+    quad = QUADS[qname]
+    for kernel, kappa in KERNELS:
+        got, n = _dense(ctx, pkg, mesh, basis, kernel, kappa, quad)
+        rows = np.repeat(np.arange(n), n)
+        cols = np.tile(np.arange(n), n)
+        ref = oracle_entries(mesh, basis, rows, cols, kernel, kappa, quad).reshape(n, n)
+        assert rel_err(got.ravel(), ref.ravel(), rows).max() <= TOL, kernel
+
+
+def test_dense_lower_only(ctx, pkg):
+    import torch
+    mesh = MESHES["ico2"]()
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p0")
+    n = mesh.nt
+    out = torch.full((n * n,), -7.0, dtype=torch.float64, device="cuda")
+    ctx.bem_assemble_dense(mid, pkg.kernel_desc("laplace_slp"), pkg.quad_desc(**QUADS["c1"]),
+                           1, out)
+    ctx.bem_sync()
+    full, _ = _dense(ctx, pkg, mesh, "p0", "laplace_slp", 0.0, QUADS["c1"])
+    got = out.cpu().numpy().reshape(n, n).T
+    il = np.tril_indices(n)
+    iu = np.triu_indices(n, 1)
+    assert np.array_equal(got[il], full[il])
+    assert np.all(got[iu] == -7.0)
+
+
+@pytest.mark.parametrize("basis", ["p0", "p1"])
+@pytest.mark.parametrize("kernel,kappa", KERNELS)
+def test_near_field_and_coupling(ctx, pkg, basis, kernel, kappa):
+    quad = QUADS["paper"]
+    if basis == "p0":
+        mesh = synth.jitter(synth.icosphere(2), 0.05, 21)
+        part, near, far = h2_blocks(mesh, basis, leaf_size=12, eta=1.0, rank=6, pivot_seed=5)
+    else:
+        mesh = synth.jitter(synth.icosphere(3), 0.05, 21)
+        part, near, far = h2_blocks(mesh, basis, leaf_size=16, eta=2.0, rank=6, pivot_seed=5)
+    assert len(near.blk_row) > 4 and len(far.blk_row) > 4
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, basis)
+    out_n = _out(near.n_entries, kernel)
+    out_f = _out(far.n_entries, kernel)
+    ctx.bem_near_field([block_job(pkg, mid, near, kernel, kappa, quad, out_n)])
+    ctx.bem_coupling_blocks([block_job(pkg, mid, far, kernel, kappa, quad, out_f)])
+    ctx.bem_sync()
+    for bs, out in ((near, out_n), (far, out_f)):
+        r, c = bs.entry_indices()
+        got = out.cpu().numpy()[: bs.n_entries]
+        ref = oracle_entries(mesh, basis, r, c, kernel, kappa, quad)
+        assert np.isfinite(got).all()
+        assert rel_err(got, ref, r).max() <= TOL
+    ctx.bem_mesh_free(mid)
+
+
+@pytest.mark.parametrize("basis", ["p0", "p1"])
+@pytest.mark.parametrize("kernel,kappa", KERNELS)
+def test_pivot_entries(ctx, pkg, basis, kernel, kappa):
+    import torch
+    mesh = synth.jitter(synth.cube_surface(4), 0.05, 31)
+    quad = QUADS["paper"]
+    n = mesh.nt if basis == "p0" else mesh.nv
+    rng = synth.SplitMix64(77)
+    rows = rng.integers(400, n)
+    cols = rng.integers(400, n)
+    # include every touching configuration explicitly
+    t = mesh.tris
+    if basis == "p0":
+        extra_r = [0, 0, 0, 1]
+        extra_c = [0, 1, int(np.where((t == t[0, 0]).any(1))[0][-1]), 1]
+    else:
+        extra_r = [t[0, 0], t[0, 0], t[0, 1]]
+        extra_c = [t[0, 0], t[0, 1], t[0, 1]]
+    rows = np.concatenate([rows, extra_r]).astype(np.int32)
+    cols = np.concatenate([cols, extra_c]).astype(np.int32)
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, basis)
+    out = _out(len(rows), kernel)
+    ctx.bem_pivot_entries(mid, pkg.kernel_desc(kernel, kappa), pkg.quad_desc(**quad),
+                          to_dev(rows, torch.int32), to_dev(cols, torch.int32), out)
+    ctx.bem_sync()
+    got = out.cpu().numpy()[: len(rows)]
+    ref = oracle_entries(mesh, basis, rows, cols, kernel, kappa, quad)
+    assert rel_err(got, ref, rows).max() <= TOL
+    ctx.bem_mesh_free(mid)
+
+
+def test_results_are_deterministic(ctx, pkg):
+    mesh = synth.jitter(synth.icosphere(2), 0.05, 41)
+    a, _ = _dense(ctx, pkg, mesh, "p1", "helmholtz_slp", 3.0, QUADS["paper"])
+    b, _ = _dense(ctx, pkg, mesh, "p1", "helmholtz_slp", 3.0, QUADS["paper"])
+    assert np.array_equal(a, b)
+
+
+def test_empty_and_ragged_inputs(ctx, pkg):
+    import torch
+    mesh = synth.octahedron()
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p0")
+    kd, qd = pkg.kernel_desc("laplace_slp"), pkg.quad_desc(**QUADS["paper"])
+    # zero entries / zero blocks are no-ops
+    e = torch.zeros(0, dtype=torch.int32, device="cuda")
+    ctx.bem_pivot_entries(mid, kd, qd, e, e, torch.zeros(1, dtype=torch.float64, device="cuda"))
+    # clusters of sizes 1, 3 and 8 (ragged tiles), a block with an empty cluster
+    bs = BlockSet(np.array([0, 1, 4, 12, 12]), np.array([5, 0, 2, 7] + list(range(8))),
+                  np.array([0, 1, 4, 12, 12]), np.array([5, 0, 2, 7] + list(range(8))),
+                  np.array([0, 1, 2, 2, 3]), np.array([2, 1, 0, 2, 1]),
+                  np.array([0, 8, 17, 25, 89]), 89)
+    out = torch.full((89,), float("nan"), dtype=torch.float64, device="cuda")
+    ctx.bem_near_field([block_job(pkg, mid, bs, "laplace_slp", 0.0, QUADS["paper"], out)])
+    ctx.bem_sync()
+    r, c = bs.entry_indices()
+    ref = oracle_entries(mesh, "p0", r, c, "laplace_slp", 0.0, QUADS["paper"])
+    got = out.cpu().numpy()
+    assert rel_err(got, ref, r).max() <= TOL
+    ctx.bem_mesh_free(mid)
+
+
+def test_device_detected_errors(ctx, pkg):
+    import torch
+    mesh = synth.octahedron()
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p0")
+    kd, qd = pkg.kernel_desc("laplace_slp"), pkg.quad_desc(**QUADS["paper"])
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    bad = torch.tensor([0, 99], dtype=torch.int32, device="cuda")
+    ctx.bem_pivot_entries(mid, kd, qd, bad, bad, out)
+    with pytest.raises(pkg.BemError) as ei:
+        ctx.bem_sync()
+    assert ei.value.code == -1
+    ctx.bem_sync()   # the status word was cleared
+    # a touching pair inside a coupling block is rejected
+    bs = BlockSet(np.array([0, 2]), np.array([0, 1]), np.array([0, 2]), np.array([0, 1]),
+                  np.array([0]), np.array([0]), np.array([0]), 4)
+    ctx.bem_coupling_blocks([block_job(pkg, mid, bs, "laplace_slp", 0.0, QUADS["paper"], out)])
+    with pytest.raises(pkg.BemError):
+        ctx.bem_sync()
+    ctx.bem_mesh_free(mid)
+
+
+def test_host_detected_errors(ctx, pkg):
+    mesh = synth.octahedron()
+    with pytest.raises(pkg.BemError) as ei:
+        bad = mesh.tris.copy()
+        bad[0] = [0, 0, 1]
+        ctx.bem_mesh_upload(mesh.verts, bad, "p0")
+    assert ei.value.code == -5
+    with pytest.raises(pkg.BemError):
+        ctx.bem_mesh_upload(mesh.verts, mesh.tris + 100, "p0")
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p0")
+    import torch
+    out = torch.zeros(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.BemError) as ei:
+        ctx.bem_assemble_dense(mid, pkg.kernel_desc("laplace_slp"),
+                               pkg.quad_desc(q_regular=7), 0, out)
+    assert ei.value.code == -6
+    ctx.bem_mesh_free(mid)
+
+
+def test_c2_full_size_sampled(ctx, pkg):
+    """The benchmark's 20480-triangle P1 workload in its launch configuration:
+    all near-field and coupling entries on the GPU, a seeded sample of each
+    checked against the oracle."""
+    w = synth.workloads.config2()
+    quad = w.quad.kw()
+    mid = ctx.bem_mesh_upload(w.mesh.verts, w.mesh.tris, w.basis)
+    rng = synth.SplitMix64(99)
+    for op in w.operators:
+        out_n = _out(w.near.n_entries, op.kernel)
+        out_f = _out(w.far.n_entries, op.kernel)
+        ctx.bem_near_field([block_job(pkg, mid, w.near, op.kernel, op.kappa, quad, out_n)])
+        ctx.bem_coupling_blocks([block_job(pkg, mid, w.far, op.kernel, op.kappa, quad, out_f)])
+        ctx.bem_sync()
+        for bs, out in ((w.near, out_n), (w.far, out_f)):
+            got_all = out.cpu().numpy()[: bs.n_entries]
+            assert np.isfinite(got_all).all()
+            r, c = bs.entry_indices()
+            pick = rng.integers(1500, bs.n_entries)
+            ref = oracle_entries(w.mesh, w.basis, r[pick], c[pick], op.kernel, op.kappa, quad)
+            # row scale from the full row set of the sample
+            assert rel_err(got_all[pick], ref, r[pick]).max() <= TOL
+    ctx.bem_mesh_free(mid)
