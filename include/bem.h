@@ -184,6 +184,31 @@ int bem_pivot_entries(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kern
 int bem_assemble_dense(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
                        const bem_quad_desc *quad, int32_t lower_only, void *out);
 
+/* ---- allocation-free near field --------------------------------------------
+ * The paper has no counterpart of this call; it exists for callers that must
+ * not allocate device memory (a service whose device memory belongs to its own
+ * pool allocator, a loop that cannot afford the implicit device-wide
+ * synchronisation cudaMalloc/cudaFree may cause, a host program that has
+ * handed out all device memory before assembling).
+ *
+ * Computes the same near-field blocks as bem_near_field for ONE job, with the
+ * same kernels, but calls no cudaMalloc, cudaFree or other allocating routine.
+ * Its scratch (singular-case rule tables and per-block tile sums) is a static
+ * device array of 1,302,336 bytes inside the library, present on every GPU
+ * that loads the library until the process exits.  Limits: at most 65536
+ * blocks and singular orders q_vertex, q_edge, q_identical <= 6; larger
+ * requests fail with BEM_ERR_INVALID_ARG and a message naming the limit.
+ * The mesh, the context's status word and the outputs are the ones set up
+ * by earlier calls (bem_create, bem_mesh_upload) and by the caller.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array and the mesh's touching table, and
+ *     leaves its contents behind: calls on the same stream are ordered, but
+ *     calls that overlap on the GPU (other streams or contexts on the same
+ *     device) race and may produce wrong entries. */
+int bem_near_field_noalloc(bem_ctx *ctx, const bem_block_job *job);
+
 /* ---- launch profiling (tracing) ------------------------------------------
  * When enabled, every kernel launch of the context is bracketed by CUDA
  * events recorded on the context's stream.  bem_profile_read waits for the

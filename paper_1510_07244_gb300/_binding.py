@@ -26,7 +26,7 @@ ORDER_MODES = {"fixed": 0, "learned": 1}
 EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_upload",
            "bem_mesh_free", "bem_mesh_info", "bem_near_field", "bem_coupling_blocks",
            "bem_pivot_entries", "bem_assemble_dense", "bem_profile_enable",
-           "bem_profile_reset", "bem_profile_read"]
+           "bem_profile_reset", "bem_profile_read", "bem_near_field_noalloc"]
 
 
 class BemError(RuntimeError):
@@ -98,6 +98,7 @@ def load():
                                       P(bem_quad_desc), _vp, _vp, ctypes.c_int64, _vp]
     lib.bem_assemble_dense.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc),
                                        P(bem_quad_desc), ctypes.c_int32, _vp]
+    lib.bem_near_field_noalloc.argtypes = [_vp, P(bem_block_job)]
     lib.bem_profile_enable.argtypes = [_vp, ctypes.c_int32]
     lib.bem_profile_reset.argtypes = [_vp]
     lib.bem_profile_read.argtypes = [_vp, P(bem_kernel_time), ctypes.c_int32,
@@ -215,6 +216,11 @@ class Context:
     def bem_near_field(self, jobs):
         arr = (bem_block_job * len(jobs))(*[j.to_c() for j in jobs])
         self._check(self.lib.bem_near_field(self.h, arr, len(jobs)))
+
+    def bem_near_field_noalloc(self, job):
+        """Near field of one job without any device allocation (static scratch)."""
+        c = job.to_c()
+        self._check(self.lib.bem_near_field_noalloc(self.h, ctypes.byref(c)))
 
     def bem_coupling_blocks(self, jobs):
         arr = (bem_block_job * len(jobs))(*[j.to_c() for j in jobs])
