@@ -72,9 +72,11 @@ typedef struct {
  * default is 3 for disjoint pairs and 5 for the singular cases.
  *   regular_rule: BEM_RULE_DUFFY (q_regular^4 points) or BEM_RULE_TRI7
  *                 (7 x 7 = 49 points, q_regular ignored).
- *   precision:    BEM_FP64, or BEM_MIXED (regular and common-vertex pairs in
- *                 FP32 arithmetic with compensated sums; identical and
- *                 common-edge pairs stay FP64).
+ *   precision:    BEM_FP64, or BEM_MIXED: for the Laplace kernels, disjoint and
+ *                 common-vertex pairs in FP32 arithmetic (double-float set-up of
+ *                 vertex differences and double-layer heights, compensated
+ *                 sums); identical and common-edge pairs, Helmholtz pairs and
+ *                 bem_pivot_entries stay FP64.
  *   order_mode:   BEM_ORDER_FIXED (the orders above) or BEM_ORDER_LEARNED. */
 typedef struct {
     int32_t q_regular;

@@ -5,7 +5,7 @@ leg may import this package.  The library (``paper_1510_07244_gb300``) never
 imports it and shares no code with it.
 """
 from .oracle import (build, gauss_legendre01, radon7, rule_points, classify, entries,
-                     pair, CASES, KERNELS, BASES, RULES)
+                     entries_absolute, pair, CASES, KERNELS, BASES, RULES)
 
 __all__ = ["build", "gauss_legendre01", "radon7", "rule_points", "classify", "entries",
-           "pair", "CASES", "KERNELS", "BASES", "RULES"]
+           "entries_absolute", "pair", "CASES", "KERNELS", "BASES", "RULES"]

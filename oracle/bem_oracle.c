@@ -472,7 +472,8 @@ typedef struct {
 } orc_setup;
 
 static void pair_integral(const orc_mesh *m, const orc_setup *S, int64_t a, int64_t b,
-                          int la, int lb, double *out_re, double *out_im, int64_t *npts)
+                          int la, int lb, double *out_re, double *out_im, int64_t *npts,
+                          int absolute)
 {
     const int32_t *ta = m->tris + 3 * a, *tb = m->tris + 3 * b;
     int oa[3], ob[3];
@@ -521,8 +522,14 @@ static void pair_integral(const orc_mesh *m, const orc_setup *S, int64_t a, int6
         double fa = (la < 0) ? 1.0 : lambda_ref(pa, R->x1[p], R->x2[p]);
         double fb = (lb < 0) ? 1.0 : lambda_ref(pb, R->y1[p], R->y2[p]);
         double wf = R->w[p] * fa * fb;
-        sre += wf * kre;
-        sim += wf * kim;
+        if (absolute) {
+            /* magnitude of the term: the scale of the rounding error of a
+             * floating-point evaluation of this sum */
+            sre += fabs(wf) * sqrt(kre * kre + kim * kim);
+        } else {
+            sre += wf * kre;
+            sim += wf * kim;
+        }
     }
     *out_re = ga * gb * sre;
     *out_im = ga * gb * sim;
@@ -558,11 +565,11 @@ static void setup_free(orc_setup *S)
 /* Returns 0, or -1 on invalid arguments (index out of range, bad order,     */
 /* degenerate triangle).                                                     */
 /* ------------------------------------------------------------------------ */
-int orc_entries(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
-                int test_basis, int trial_basis, int kernel, double kappa,
-                int regular_rule, int q_regular, int q_identical, int q_edge, int q_vertex,
-                const int64_t *rows, const int64_t *cols, int64_t n, double *out,
-                int64_t *npoints, int nthreads)
+static int entries_impl(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                        int test_basis, int trial_basis, int kernel, double kappa,
+                        int regular_rule, int q_regular, int q_identical, int q_edge,
+                        int q_vertex, const int64_t *rows, const int64_t *cols, int64_t n,
+                        double *out, int64_t *npoints, int nthreads, int absolute)
 {
     if (nv <= 0 || nt <= 0 || n < 0) return -1;
     if (kernel < 0 || kernel > 2) return -1;
@@ -621,7 +628,7 @@ int orc_entries(const double *verts, int64_t nv, const int32_t *tris, int64_t nt
                 if (trial_basis == ORC_P1)
                     for (int c = 0; c < 3; ++c) if (M.tris[3 * b + c] == j) lb = c;
                 double re, im;
-                pair_integral(&M, &S, a, b, la, lb, &re, &im, &pts);
+                pair_integral(&M, &S, a, b, la, lb, &re, &im, &pts, absolute);
                 sre += re;
                 sim += im;
             }
@@ -634,6 +641,32 @@ int orc_entries(const double *verts, int64_t nv, const int32_t *tris, int64_t nt
     mesh_free(&M);
     setup_free(&S);
     return 0;
+}
+
+int orc_entries(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                int test_basis, int trial_basis, int kernel, double kappa,
+                int regular_rule, int q_regular, int q_identical, int q_edge, int q_vertex,
+                const int64_t *rows, const int64_t *cols, int64_t n, double *out,
+                int64_t *npoints, int nthreads)
+{
+    return entries_impl(verts, nv, tris, nt, test_basis, trial_basis, kernel, kappa,
+                        regular_rule, q_regular, q_identical, q_edge, q_vertex, rows, cols, n,
+                        out, npoints, nthreads, 0);
+}
+
+/* The same sums with every quadrature term replaced by its magnitude:
+ * A_ij = sum over pairs sqrt(g_a g_b) sum_p |w_p phi psi k|, the scale of the
+ * rounding error of any floating-point evaluation of g_ij with this rule
+ * (out[2k] = A, out[2k+1] = 0). */
+int orc_entries_absolute(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                         int test_basis, int trial_basis, int kernel, double kappa,
+                         int regular_rule, int q_regular, int q_identical, int q_edge,
+                         int q_vertex, const int64_t *rows, const int64_t *cols, int64_t n,
+                         double *out, int nthreads)
+{
+    return entries_impl(verts, nv, tris, nt, test_basis, trial_basis, kernel, kappa,
+                        regular_rule, q_regular, q_identical, q_edge, q_vertex, rows, cols, n,
+                        out, NULL, nthreads, 1);
 }
 
 /* Triangle-pair integral with explicit local basis functions (for tests):
@@ -650,7 +683,7 @@ int orc_pair(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, i
     }
     orc_mesh M;
     mesh_init(&M, verts, nv, tris, nt);
-    pair_integral(&M, &S, a, b, la, lb, &out[0], &out[1], NULL);
+    pair_integral(&M, &S, a, b, la, lb, &out[0], &out[1], NULL, 0);
     mesh_free(&M);
     setup_free(&S);
     return 0;

@@ -54,6 +54,11 @@ def _get():
                                         ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         _i64, _i64, ctypes.c_int64, _d, _i64, ctypes.c_int]
+            lib.orc_entries_absolute.argtypes = [_d, ctypes.c_int64, _i32, ctypes.c_int64,
+                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 _i64, _i64, ctypes.c_int64, _d, ctypes.c_int]
             lib.orc_pair.argtypes = [_d, ctypes.c_int64, _i32, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -124,6 +129,24 @@ def entries(verts, tris, rows, cols, *, kernel="laplace_slp", kappa=0.0, basis="
         raise ValueError("oracle rejected the arguments")
     z = out[0:2 * len(r):2] + 1j * out[1:2 * len(r):2]
     return (z, int(npts[0])) if return_points else z
+
+
+def entries_absolute(verts, tris, rows, cols, *, kernel="laplace_slp", kappa=0.0, basis="p0",
+                     trial_basis=None, regular_rule="duffy", q_regular=3, q_identical=5, q_edge=5,
+                     q_vertex=5, nthreads=0):
+    """A_ij: the entries' quadrature sums with every term replaced by its magnitude."""
+    v, t = _mesh(verts, tris)
+    r = np.ascontiguousarray(rows, np.int64).ravel()
+    c = np.ascontiguousarray(cols, np.int64).ravel()
+    out = np.zeros(2 * max(len(r), 1))
+    tb = basis if trial_basis is None else trial_basis
+    rc = _get().orc_entries_absolute(_p(v, _d), v.shape[0], _p(t, _i32), t.shape[0], BASES[basis],
+                                     BASES[tb], KERNELS[kernel], float(kappa), RULES[regular_rule],
+                                     q_regular, q_identical, q_edge, q_vertex, _p(r, _i64),
+                                     _p(c, _i64), len(r), _p(out, _d), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return out[0:2 * len(r):2].copy()
 
 
 def pair(verts, tris, a, b, la=-1, lb=-1, *, kernel="laplace_slp", kappa=0.0,

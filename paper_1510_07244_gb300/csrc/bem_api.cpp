@@ -143,8 +143,8 @@ Mesh *get_mesh(bem_ctx *ctx, int id)
 int check_quad(bem_ctx *ctx, const bem_quad_desc *q, Rule2D &r2)
 {
     if (!q) return fail(ctx, BEM_ERR_INVALID_ARG, "null quadrature descriptor");
-    if (q->precision != BEM_FP64)
-        return fail(ctx, BEM_ERR_UNSUPPORTED, "only the FP64 form is available in this build");
+    if (q->precision != BEM_FP64 && q->precision != BEM_MIXED)
+        return fail(ctx, BEM_ERR_INVALID_ARG, "precision must be BEM_FP64 or BEM_MIXED");
     if (q->order_mode != BEM_ORDER_FIXED)
         return fail(ctx, BEM_ERR_UNSUPPORTED, "only fixed orders are available in this build");
     for (int v : {q->q_identical, q->q_edge, q->q_vertex})
@@ -181,6 +181,11 @@ int get_rule4(bem_ctx *ctx, int cas, int rule, int q, Rule4D &out)
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(rule)");
     e = cudaMemcpy(r.d, soa.data(), soa.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(rule)");
+    std::vector<float> sf(soa.begin(), soa.end());
+    e = cudaMalloc((void **)&r.f, sf.size() * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(rule)");
+    e = cudaMemcpy(r.f, sf.data(), sf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(rule)");
     ctx->rules4[key] = r;
     out = r;
     return BEM_OK;
@@ -199,7 +204,7 @@ int run_touching(bem_ctx *ctx, Mesh *m, const bem_kernel_desc *k, const bem_quad
                                        "touching_identical"};
         ProfScope ps(ctx, names[cas]);
         cudaError_t e = launch_touching(m->v, cas, m->list[cas], m->nlist[cas], r, k->kind,
-                                        k->kappa, ctx->stream);
+                                        k->kappa, q->precision == BEM_MIXED, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "touching kernel");
     }
     return BEM_OK;
@@ -268,6 +273,7 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
         L.kappa = J.kernel.kappa;
         L.lower_only = lower_only;
         L.allow_touching = allow_touching ? 1 : 0;
+        L.mixed = J.quad.precision == BEM_MIXED ? 1 : 0;
         const int tc = m->v.basis == BEM_P0 ? 8 : kTile;
         cudaError_t e;
         {
@@ -318,7 +324,10 @@ int bem_destroy(bem_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     for (auto &kv : ctx->meshes) free_mesh(kv.second);
-    for (auto &kv : ctx->rules4) cudaFree(kv.second.d);
+    for (auto &kv : ctx->rules4) {
+        cudaFree(kv.second.d);
+        cudaFree(kv.second.f);
+    }
     for (auto &r : ctx->prof_pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -390,6 +399,27 @@ int bem_mesh_upload(bem_ctx *ctx, const double *verts, int64_t nv, const int32_t
         tvid[t] = make_int4(T[0], T[1], T[2], 0);
     }
 
+    // mixed-form records: vertices as float hi + lo, FP64 edge vectors and
+    // normal rounded to float (normal also as hi + lo), Gram factor
+    std::vector<float> geomf((size_t)nt * kGeomFStride, 0.0f);
+    for (int64_t t = 0; t < nt; ++t) {
+        const double *g = &geom[(size_t)t * kGeomStride];
+        float *f = &geomf[(size_t)t * kGeomFStride];
+        for (int k = 0; k < 9; ++k) {
+            const float hi = (float)g[k];
+            f[k] = hi;
+            f[9 + k] = (float)(g[k] - (double)hi);
+        }
+        for (int c = 0; c < 3; ++c) {
+            f[18 + c] = (float)(g[3 + c] - g[c]);
+            f[21 + c] = (float)(g[6 + c] - g[3 + c]);
+            const float nh = (float)g[9 + c];
+            f[24 + c] = nh;
+            f[27 + c] = (float)(g[9 + c] - (double)nh);
+        }
+        f[30] = (float)g[12];
+    }
+
     // vertex -> triangle adjacency (ascending triangle ids)
     std::vector<int> vt_ptr((size_t)nv + 1, 0), vt_tri((size_t)(3 * nt));
     for (int64_t k = 0; k < 3 * nt; ++k) vt_ptr[tris[k] + 1]++;
@@ -453,10 +483,12 @@ int bem_mesh_upload(bem_ctx *ctx, const double *verts, int64_t nv, const int32_t
     V.ntouch = (int64_t)nb_tri.size();
     int rc = BEM_OK;
     double *d_geom;
+    float *d_geomf;
     int4 *d_tvid;
     int *d_vtp, *d_vtt, *d_nbp, *d_nbt, *d_nbs;
     unsigned char *d_nbc, *d_nbperm;
-    if ((rc = upload(ctx, m, geom, &d_geom)) || (rc = upload(ctx, m, tvid, &d_tvid)) ||
+    if ((rc = upload(ctx, m, geom, &d_geom)) || (rc = upload(ctx, m, geomf, &d_geomf)) ||
+        (rc = upload(ctx, m, tvid, &d_tvid)) ||
         (rc = upload(ctx, m, vt_ptr, &d_vtp)) || (rc = upload(ctx, m, vt_tri, &d_vtt)) ||
         (rc = upload(ctx, m, nb_ptr, &d_nbp)) || (rc = upload(ctx, m, nb_tri, &d_nbt)) ||
         (rc = upload(ctx, m, nb_src, &d_nbs)) || (rc = upload(ctx, m, nb_case, &d_nbc)) ||
@@ -465,6 +497,7 @@ int bem_mesh_upload(bem_ctx *ctx, const double *verts, int64_t nv, const int32_t
         return rc;
     }
     V.geom = d_geom;
+    V.geomf = d_geomf;
     V.tvid = d_tvid;
     V.vt_ptr = d_vtp;
     V.vt_tri = d_vtt;

@@ -16,6 +16,9 @@ namespace bem {
 
 constexpr int kGeomStride = 16;      // doubles per triangle record (128 bytes)
 // record layout: v0[3] v1[3] v2[3] n[3] sqrt_g pad[3]
+constexpr int kGeomFStride = 32;     // floats per triangle record of the mixed form (128 bytes)
+// layout: vertex hi[9] | vertex lo[9] (x = hi + lo exactly to ~2^-48) | e1[3] e2[3]
+//         (FP64 differences rounded once) | n hi[3] | n lo[3] | sqrt_g | pad
 constexpr int kMaxDegP1 = 16;        // vertex degree bound of the P1 block engine
 constexpr int kTile = 32;            // rows / columns of one block tile
 constexpr int kMaxNp = 25;           // points of a 2D regular rule (Duffy q <= 5)
@@ -30,12 +33,14 @@ extern const int kPerm[6][3];
 struct Rule2D {
     int np;
     double s[kMaxNp], t[kMaxNp], w[kMaxNp];
+    float sf[kMaxNp], tf[kMaxNp], wf[kMaxNp];   // the same rule rounded to float
 };
 
 // 4D rule on D x D, device SoA: x1 | x2 | y1 | y2 | w, n each.
 struct Rule4D {
     int n = 0;
     double *d = nullptr;   // device, 5 n doubles
+    float *f = nullptr;    // device, 5 n floats (mixed form), may be null
 };
 
 // Device view of an uploaded mesh.
@@ -44,6 +49,7 @@ struct MeshView {
     int basis;
     int maxdeg;
     const double *geom;        // nt * kGeomStride
+    const float *geomf;        // nt * kGeomFStride (mixed form)
     const int4 *tvid;          // nt (v0, v1, v2, 0)
     const int *vt_ptr;         // nv + 1
     const int *vt_tri;         // 3 nt, ascending triangle ids per vertex
@@ -120,15 +126,17 @@ struct BlockLaunch {
     double kappa;
     int lower_only;
     int allow_touching;
+    int mixed;        // 1: regular pairs in FP32 (BEM_MIXED)
 };
 
 cudaError_t launch_tile_prefix(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
                                int *status, cudaStream_t st);
 cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
-                            const Rule4D &rule, int kind, double kappa, cudaStream_t st);
+                            const Rule4D &rule, int kind, double kappa, int mixed,
+                            cudaStream_t st);
 cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const Rule2D &rule,
                                 const int64_t *prefix, int *status, int grid, cudaStream_t st);
-size_t p1_smem_bytes(bool cplx);
+size_t p1_smem_bytes(bool cplx, bool mixed);
 cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const int32_t *cols,
                                  int64_t n, void *out, const Rule4D *rules /*[4]*/, int kind,
                                  double kappa, int *status, cudaStream_t st);

@@ -17,6 +17,8 @@
 // pair.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "bem_internal.h"
 
 namespace bem {
@@ -90,6 +92,240 @@ __device__ __forceinline__ double warp_sum(double v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed form: float arithmetic with double-float set-up.  Every vertex is held
+// as hi + lo floats; differences of vertices and the heights of one
+// triangle's vertices above another's plane are formed with error-free
+// transformations (Knuth's TwoSum, FMA-based TwoProduct), so they carry full
+// float precision even when they are tiny against the coordinates.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (ah + al) - (bh + bl) as an unevaluated hi + lo pair
+__device__ __forceinline__ void dd_sub(float ah, float al, float bh, float bl, float &h, float &l)
+{
+    float s, e;
+    two_sum(ah, -bh, s, e);
+    e += al - bl;
+    h = s + e;
+    l = e - (h - s);
+}
+
+__device__ __forceinline__ float dd_diff(float ah, float al, float bh, float bl)
+{
+    float h, l;
+    dd_sub(ah, al, bh, bl, h, l);
+    return h + l;
+}
+
+// ((a - b) . n) as an unevaluated hi + lo pair, with a, b, n given as hi/lo triples
+__device__ __forceinline__ void dd_height(const float *ah, const float *al, const float *bh,
+                                          const float *bl, const float *nh, const float *nl,
+                                          float &hh, float &hl)
+{
+    float S = 0.0f, E = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float dh, dl;
+        dd_sub(ah[c], al[c], bh[c], bl[c], dh, dl);
+        const float p = dh * nh[c];
+        const float pe = fmaf(dh, nh[c], -p) + fmaf(dh, nl[c], dl * nh[c]);
+        float s2, e2;
+        two_sum(S, p, s2, e2);
+        S = s2;
+        E += e2 + pe;
+    }
+    hh = S + E;
+    hl = E - (hh - S);
+}
+
+// Affine height h(s,t) = h0 + s h10 + t h21 of a point of the test triangle above
+// the trial triangle's plane, from hi/lo coefficients, with compensated
+// products and sums: its error is a few ulps of |h| even where h changes sign.
+struct Height {
+    float h0, h0l, h10, h10l, h21, h21l;
+};
+
+__device__ __forceinline__ float height_at(const Height &H, float s, float t)
+{
+    const float p1 = s * H.h10, p2 = t * H.h21;
+    const float e1 = fmaf(s, H.h10, -p1), e2 = fmaf(t, H.h21, -p2);
+    float a, ea, b, eb;
+    two_sum(p1, p2, a, ea);
+    two_sum(a, H.h0, b, eb);
+    const float lo = ea + eb + e1 + e2 + H.h0l + fmaf(s, H.h10l, t * H.h21l);
+    return b + lo;
+}
+
+// heights of the test triangle's vertices k0, k1, k2 above the trial plane
+// (through the trial vertex bh/bl with normal nh/nl) as affine coefficients
+__device__ __forceinline__ Height make_height(const float *a0h, const float *a0l,
+                                              const float *a1h, const float *a1l,
+                                              const float *a2h, const float *a2l,
+                                              const float *bh, const float *bl,
+                                              const float *nh, const float *nl)
+{
+    float h0, l0, h1, l1, h2, l2;
+    dd_height(a0h, a0l, bh, bl, nh, nl, h0, l0);
+    dd_height(a1h, a1l, bh, bl, nh, nl, h1, l1);
+    dd_height(a2h, a2l, bh, bl, nh, nl, h2, l2);
+    Height H;
+    H.h0 = h0;
+    H.h0l = l0;
+    dd_sub(h1, l1, h0, l0, H.h10, H.h10l);
+    dd_sub(h2, l2, h1, l1, H.h21, H.h21l);
+    return H;
+}
+
+struct TriF {
+    float vh[3][3], vl[3][3];
+    float e1[3], e2[3];
+    float nh[3], nl[3];
+    float sg;
+};
+
+__device__ __forceinline__ void load_trif(const float *__restrict__ geomf, int64_t t, TriF &o)
+{
+    const float4 *g = reinterpret_cast<const float4 *>(geomf + t * kGeomFStride);
+    float f[32];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float4 v = __ldg(g + k);
+        f[4 * k] = v.x;
+        f[4 * k + 1] = v.y;
+        f[4 * k + 2] = v.z;
+        f[4 * k + 3] = v.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o.vh[k][c] = f[3 * k + c];
+            o.vl[k][c] = f[9 + 3 * k + c];
+        }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        o.e1[c] = f[18 + c];
+        o.e2[c] = f[21 + c];
+        o.nh[c] = f[24 + c];
+        o.nl[c] = f[27 + c];
+    }
+    o.sg = f[30];
+}
+
+// Laplace kernel value in float: 1/r (single layer) or dn/r^3 (double layer)
+template <int KIND>
+__device__ __forceinline__ float kvalf(float dx, float dy, float dz, float dn)
+{
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ri = rsqrtf(r2);
+    if (KIND == BEM_LAPLACE_SLP) return ri;
+    return dn * (ri * ri * ri);
+}
+
+// Regular pair, piecewise constant, float (Laplace kernels).
+template <int KIND, int NP>
+__device__ __forceinline__ float regular_p0_f32(const TriF &A, const TriF &B, const Rule2D &R)
+{
+    float d0[3], yx[NP], yy[NP], yz[NP];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d0[c] = dd_diff(A.vh[0][c], A.vl[0][c], B.vh[0][c], B.vl[0][c]);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        yx[j] = fmaf(R.sf[j], B.e1[0], R.tf[j] * B.e2[0]);
+        yy[j] = fmaf(R.sf[j], B.e1[1], R.tf[j] * B.e2[1]);
+        yz[j] = fmaf(R.sf[j], B.e1[2], R.tf[j] * B.e2[2]);
+    }
+    Height H = {};
+    if (KIND == BEM_LAPLACE_DLP)
+        H = make_height(A.vh[0], A.vl[0], A.vh[1], A.vl[1], A.vh[2], A.vl[2], B.vh[0], B.vl[0],
+                        B.nh, B.nl);
+    float sum = 0.0f, comp = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const float xx = fmaf(R.sf[i], A.e1[0], fmaf(R.tf[i], A.e2[0], d0[0]));
+        const float xy = fmaf(R.sf[i], A.e1[1], fmaf(R.tf[i], A.e2[1], d0[1]));
+        const float xz = fmaf(R.sf[i], A.e1[2], fmaf(R.tf[i], A.e2[2], d0[2]));
+        const float dn = KIND == BEM_LAPLACE_DLP ? height_at(H, R.sf[i], R.tf[i]) : 0.0f;
+        float inner = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+            inner = fmaf(R.wf[j], kvalf<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], dn), inner);
+        // compensated outer sum (Kahan)
+        const float y = fmaf(R.wf[i], inner, -comp);
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    }
+    return sum * (A.sg * B.sg * (float)kInv4Pi);
+}
+
+// Regular pair, piecewise linear (3x3 local matrix), float (Laplace kernels).
+template <int KIND, int NP>
+__device__ __forceinline__ void regular_p1_f32(const TriF &A, const TriF &B, const Rule2D &R,
+                                               float *acc)
+{
+    float d0[3], yx[NP], yy[NP], yz[NP];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d0[c] = dd_diff(A.vh[0][c], A.vl[0][c], B.vh[0][c], B.vl[0][c]);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        yx[j] = fmaf(R.sf[j], B.e1[0], R.tf[j] * B.e2[0]);
+        yy[j] = fmaf(R.sf[j], B.e1[1], R.tf[j] * B.e2[1]);
+        yz[j] = fmaf(R.sf[j], B.e1[2], R.tf[j] * B.e2[2]);
+    }
+    Height H = {};
+    if (KIND == BEM_LAPLACE_DLP)
+        H = make_height(A.vh[0], A.vl[0], A.vh[1], A.vl[1], A.vh[2], A.vl[2], B.vh[0], B.vl[0],
+                        B.nh, B.nl);
+    float comp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = comp[k] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const float xx = fmaf(R.sf[i], A.e1[0], fmaf(R.tf[i], A.e2[0], d0[0]));
+        const float xy = fmaf(R.sf[i], A.e1[1], fmaf(R.tf[i], A.e2[1], d0[1]));
+        const float xz = fmaf(R.sf[i], A.e1[2], fmaf(R.tf[i], A.e2[2], d0[2]));
+        const float dn = KIND == BEM_LAPLACE_DLP ? height_at(H, R.sf[i], R.tf[i]) : 0.0f;
+        float ir[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            const float wk = R.wf[j] * kvalf<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], dn);
+            const float s_ = R.sf[j], t_ = R.tf[j];
+            ir[0] = fmaf(wk, 1.0f - s_, ir[0]);
+            ir[1] = fmaf(wk, s_ - t_, ir[1]);
+            ir[2] = fmaf(wk, t_, ir[2]);
+        }
+        const float la[3] = {1.0f - R.sf[i], R.sf[i] - R.tf[i], R.tf[i]};
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const float f = R.wf[i] * la[p];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float y = fmaf(f, ir[q], -comp[p * 3 + q]);
+                const float t = acc[p * 3 + q] + y;
+                comp[p * 3 + q] = (t - acc[p * 3 + q]) - y;
+                acc[p * 3 + q] = t;
+            }
+        }
+    }
+    const float scale = A.sg * B.sg * (float)kInv4Pi;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] *= scale;
 }
 
 // ---------------------------------------------------------------------------
@@ -167,6 +403,90 @@ __global__ void __launch_bounds__(256) k_touching(MeshView m, const int *__restr
                 for (int j = 0; j < 3; ++j)
                     m.table[(int64_t)idx * 9 + pa[i] * 3 + pb[j]] =
                         make_double2(accr[i * 3 + j] * scale, acci[i * 3 + j] * scale);
+        }
+    }
+}
+
+// Common-vertex pairs in float (mixed form, Laplace kernels): the shared vertex is
+// the canonical vertex 0 of both triangles, so x - y is formed from edge
+// vectors only and keeps float precision down to the singular point.
+template <int KIND, int BASIS>
+__global__ void __launch_bounds__(256) k_touching_vertex_f32(MeshView m, const int *__restrict__ list,
+                                                             int64_t n, const float *__restrict__ rule,
+                                                             int np)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= n) return;
+    const int idx = __ldg(list + wid);
+    const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);
+    const int pc = __ldg(m.nb_perm + idx);
+    const int *pa = c_perm[pc / 6], *pb = c_perm[pc % 6];
+    TriF A, B;
+    load_trif(m.geomf, a, A);
+    load_trif(m.geomf, b, B);
+    // canonical vertex order by selects (no dynamically indexed local arrays)
+    float ah[3][3], al[3][3], bh[3][3], bl[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int ia = pa[k], ib = pb[k];
+            ah[k][c] = ia == 0 ? A.vh[0][c] : (ia == 1 ? A.vh[1][c] : A.vh[2][c]);
+            al[k][c] = ia == 0 ? A.vl[0][c] : (ia == 1 ? A.vl[1][c] : A.vl[2][c]);
+            bh[k][c] = ib == 0 ? B.vh[0][c] : (ib == 1 ? B.vh[1][c] : B.vh[2][c]);
+            bl[k][c] = ib == 0 ? B.vl[0][c] : (ib == 1 ? B.vl[1][c] : B.vl[2][c]);
+        }
+    float e1a[3], e2a[3], e1b[3], e2b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        e1a[c] = dd_diff(ah[1][c], al[1][c], ah[0][c], al[0][c]);
+        e2a[c] = dd_diff(ah[2][c], al[2][c], ah[1][c], al[1][c]);
+        e1b[c] = dd_diff(bh[1][c], bl[1][c], bh[0][c], bl[0][c]);
+        e2b[c] = dd_diff(bh[2][c], bl[2][c], bh[1][c], bl[1][c]);
+    }
+    // heights of a's canonical vertices above b's plane (vertex 0 is shared)
+    Height H = {};
+    if (KIND == BEM_LAPLACE_DLP)
+        H = make_height(ah[0], al[0], ah[1], al[1], ah[2], al[2], bh[0], bl[0], B.nh, B.nl);
+    constexpr int NACC = BASIS == BEM_P0 ? 1 : 9;
+    float acc[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k] = 0.0f;
+    const float *X1 = rule, *X2 = rule + np, *Y1 = rule + 2 * np, *Y2 = rule + 3 * np,
+                *W = rule + 4 * np;
+    for (int p = lane; p < np; p += 32) {
+        const float x1 = __ldg(X1 + p), x2 = __ldg(X2 + p), y1 = __ldg(Y1 + p),
+                    y2 = __ldg(Y2 + p), w = __ldg(W + p);
+        const float dx = fmaf(x1, e1a[0], fmaf(x2, e2a[0], -fmaf(y1, e1b[0], y2 * e2b[0])));
+        const float dy = fmaf(x1, e1a[1], fmaf(x2, e2a[1], -fmaf(y1, e1b[1], y2 * e2b[1])));
+        const float dz = fmaf(x1, e1a[2], fmaf(x2, e2a[2], -fmaf(y1, e1b[2], y2 * e2b[2])));
+        const float dn = KIND == BEM_LAPLACE_DLP ? height_at(H, x1, x2) : 0.0f;
+        const float wk = w * kvalf<KIND>(dx, dy, dz, dn);
+        if (BASIS == BEM_P0) {
+            acc[0] += wk;
+        } else {
+            const float la[3] = {1.0f - x1, x1 - x2, x2};
+            const float lb[3] = {1.0f - y1, y1 - y2, y2};
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) acc[i * 3 + j] = fmaf(wk * la[i], lb[j], acc[i * 3 + j]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k] = warp_sumf(acc[k]);
+    if (lane == 0) {
+        const double scale = (double)A.sg * (double)B.sg * kInv4Pi;
+        if (BASIS == BEM_P0) {
+            m.table[idx] = make_double2((double)acc[0] * scale, 0.0);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    m.table[(int64_t)idx * 9 + pa[i] * 3 + pb[j]] =
+                        make_double2((double)acc[i * 3 + j] * scale, 0.0);
         }
     }
 }
@@ -365,7 +685,7 @@ __global__ void __launch_bounds__(1024) k_tile_prefix(BlockLaunch L, int tr, int
 // ---------------------------------------------------------------------------
 constexpr int kP0Cols = 8;
 
-template <int KIND, int NP>
+template <int KIND, int NP, bool MIXED>
 __global__ void __launch_bounds__(256) k_block_p0(MeshView m, BlockLaunch L, Rule2D R,
                                                   const int64_t *__restrict__ prefix,
                                                   int *status)
@@ -396,6 +716,12 @@ __global__ void __launch_bounds__(256) k_block_p0(MeshView m, BlockLaunch L, Rul
             const double2 v = m.table[k];
             re = v.x;
             im = v.y;
+        } else if (MIXED) {
+            TriF A, B;
+            load_trif(m.geomf, a, A);
+            load_trif(m.geomf, b, B);
+            re = (double)regular_p0_f32<KIND, NP>(A, B, R);
+            im = 0.0;
         } else {
             Tri A, B;
             load_tri(m.geom, a, A);
@@ -501,16 +827,26 @@ __device__ void p1_support(const MeshView &m, const int *set, int n, int *tri, i
     __syncthreads();
 }
 
-template <int KIND, int NP>
-__global__ void __launch_bounds__(256) k_block_p1(MeshView m, BlockLaunch L, Rule2D R,
-                                                  const int64_t *__restrict__ prefix,
-                                                  int *status)
+// Threads per CTA of the P1 block engine: the FP64 form saturates the FP64
+// pipe with one 256-thread CTA per SM; the float form runs 128-thread CTAs,
+// several per SM, so that one CTA's barrier waits overlap another's math.
+__host__ __device__ constexpr int p1_threads(bool mixed) { return mixed ? 128 : 256; }
+__host__ __device__ constexpr int p1_min_blocks(bool mixed) { return mixed ? 4 : 1; }
+
+template <int KIND, int NP, bool MIXED>
+__global__ void __launch_bounds__(p1_threads(MIXED), p1_min_blocks(MIXED))
+k_block_p1(MeshView m, BlockLaunch L, Rule2D R, const int64_t *__restrict__ prefix, int *status)
 {
     constexpr bool CPLX = KIND == BEM_HELMHOLTZ_SLP;
+    constexpr int NT = p1_threads(MIXED);
+    constexpr int NE = kTile * kTile / NT;     // entries owned per thread
+    constexpr int EW = NT / 32;                // column stride of owned entries
+    // pair results: double in the FP64 form, float in the mixed form
+    using Val = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     P1Smem &S = *reinterpret_cast<P1Smem *>(smem_raw);
-    double *buf_r = reinterpret_cast<double *>(smem_raw + ((sizeof(P1Smem) + 15) & ~size_t(15)));
-    double *buf_i = buf_r + kP1Cap * 9;
+    Val *buf_r = reinterpret_cast<Val *>(smem_raw + ((sizeof(P1Smem) + 15) & ~size_t(15)));
+    Val *buf_i = buf_r + kP1Cap * 9;
     const int tid = threadIdx.x;
     const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
 
@@ -543,7 +879,9 @@ __global__ void __launch_bounds__(256) k_block_p1(MeshView m, BlockLaunch L, Rul
         p1_support(m, S.cols, tc, S.tb, S.cnt_c, S.off_c, S.cl, S.cl_n, &S.ntb, status);
         const int nta = S.nta, ntb = S.ntb;
         const int ia_step = max(1, kP1Cap / max(ntb, 1));
-        double accr[4] = {0, 0, 0, 0}, acci[4] = {0, 0, 0, 0};
+        Val accr[NE], acci[NE], cmpr[NE];   // cmpr: Kahan compensation (mixed form)
+#pragma unroll
+        for (int e = 0; e < NE; ++e) accr[e] = acci[e] = cmpr[e] = 0;
         const int er = tid & 31;
         for (int ia0 = 0; ia0 < nta; ia0 += ia_step) {
             const int ia1 = min(nta, ia0 + ia_step);
@@ -551,26 +889,43 @@ __global__ void __launch_bounds__(256) k_block_p1(MeshView m, BlockLaunch L, Rul
             for (int p = tid; p < npairs; p += blockDim.x) {
                 const int a = S.ta[ia0 + p / ntb], b = S.tb[p % ntb];
                 const int4 va = __ldg(m.tvid + a), vb = __ldg(m.tvid + b);
-                double vr[9], vi[9];
+                Val vr[9], vi[9];
                 if (touching(va, vb)) {
                     const int k = L.allow_touching ? find_touching(m, a, b) : -1;
                     if (k < 0) {
                         set_status(status, BEM_ERR_INVALID_ARG);
 #pragma unroll
-                        for (int q = 0; q < 9; ++q) vr[q] = vi[q] = 0.0;
+                        for (int q = 0; q < 9; ++q) vr[q] = vi[q] = 0;
                     } else {
 #pragma unroll
                         for (int q = 0; q < 9; ++q) {
                             const double2 t = m.table[(int64_t)k * 9 + q];
-                            vr[q] = t.x;
-                            vi[q] = t.y;
+                            vr[q] = (Val)t.x;
+                            vi[q] = (Val)t.y;
                         }
+                    }
+                } else if (MIXED) {
+                    TriF A, B;
+                    load_trif(m.geomf, a, A);
+                    load_trif(m.geomf, b, B);
+                    float f[9];
+                    regular_p1_f32<KIND, NP>(A, B, R, f);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        vr[q] = (Val)f[q];
+                        vi[q] = 0;
                     }
                 } else {
                     Tri A, B;
                     load_tri(m.geom, a, A);
                     load_tri(m.geom, b, B);
-                    regular_p1<KIND, NP>(A, B, R, L.kappa, vr, vi);
+                    double dr[9], di[9];
+                    regular_p1<KIND, NP>(A, B, R, L.kappa, dr, di);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        vr[q] = (Val)dr[q];
+                        vi[q] = (Val)di[q];
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
@@ -580,8 +935,8 @@ __global__ void __launch_bounds__(256) k_block_p1(MeshView m, BlockLaunch L, Rul
             }
             __syncthreads();
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int ec = (tid >> 5) + 8 * e;
+            for (int e = 0; e < NE; ++e) {
+                const int ec = (tid >> 5) + EW * e;
                 if (er < tr && ec < tc) {
                     for (int u = 0; u < S.rl_n[er]; ++u) {
                         const int ia = S.rl[er][u] >> 2, la = S.rl[er][u] & 3;
@@ -590,7 +945,14 @@ __global__ void __launch_bounds__(256) k_block_p1(MeshView m, BlockLaunch L, Rul
                         for (int v = 0; v < S.cl_n[ec]; ++v) {
                             const int ib = S.cl[ec][v] >> 2, lb = S.cl[ec][v] & 3;
                             const int q = (rowbase + ib) * 9 + la * 3 + lb;
-                            accr[e] += buf_r[q];
+                            if (MIXED) {
+                                const Val y = buf_r[q] - cmpr[e];
+                                const Val t = accr[e] + y;
+                                cmpr[e] = (t - accr[e]) - y;
+                                accr[e] = t;
+                            } else {
+                                accr[e] += buf_r[q];
+                            }
                             if (CPLX) acci[e] += buf_i[q];
                         }
                     }
@@ -599,22 +961,25 @@ __global__ void __launch_bounds__(256) k_block_p1(MeshView m, BlockLaunch L, Rul
             __syncthreads();
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int ec = (tid >> 5) + 8 * e;
+        for (int e = 0; e < NE; ++e) {
+            const int ec = (tid >> 5) + EW * e;
             if (er < tr && ec < tc) {
                 if (L.lower_only && S.rows[er] < S.cols[ec]) continue;
                 const int64_t o = bi.off + (int64_t)(r0 + er) + (int64_t)(c0 + ec) * bi.nr;
-                if (CPLX) reinterpret_cast<double2 *>(L.out)[o] = make_double2(accr[e], acci[e]);
-                else reinterpret_cast<double *>(L.out)[o] = accr[e];
+                if (CPLX)
+                    reinterpret_cast<double2 *>(L.out)[o] = make_double2((double)accr[e], (double)acci[e]);
+                else
+                    reinterpret_cast<double *>(L.out)[o] = (double)accr[e];
             }
         }
         __syncthreads();
     }
 }
 
-size_t p1_smem_bytes(bool cplx)
+size_t p1_smem_bytes(bool cplx, bool mixed)
 {
-    return ((sizeof(P1Smem) + 15) & ~size_t(15)) + (size_t)kP1Cap * 9 * sizeof(double) * (cplx ? 2 : 1);
+    return ((sizeof(P1Smem) + 15) & ~size_t(15)) +
+           (size_t)kP1Cap * 9 * (mixed ? sizeof(float) : sizeof(double)) * (cplx ? 2 : 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -723,47 +1088,57 @@ cudaError_t launch_tile_prefix(const BlockLaunch &L, int tr, int tc, int64_t *pr
 }
 
 cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
-                            const Rule4D &rule, int kind, double kappa, cudaStream_t st)
+                            const Rule4D &rule, int kind, double kappa, int mixed, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    const int64_t blocks = (n + 7) / 8;
+    const unsigned blocks = (unsigned)((n + 7) / 8);
     const bool p1 = m.basis == BEM_P1;
-#define BEM_TOUCH(K, B) k_touching<K, B><<<(unsigned)blocks, 256, 0, st>>>(m, list, n, rule.d, rule.n, kappa)
+    if (mixed && cas == kVertex && kind != BEM_HELMHOLTZ_SLP && rule.f) {
+        if (kind == BEM_LAPLACE_SLP) {
+            if (p1) k_touching_vertex_f32<BEM_LAPLACE_SLP, BEM_P1><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
+            else k_touching_vertex_f32<BEM_LAPLACE_SLP, BEM_P0><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
+        } else {
+            if (p1) k_touching_vertex_f32<BEM_LAPLACE_DLP, BEM_P1><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
+            else k_touching_vertex_f32<BEM_LAPLACE_DLP, BEM_P0><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
+        }
+        return cudaGetLastError();
+    }
+#define BEM_TOUCH(K, B) k_touching<K, B><<<blocks, 256, 0, st>>>(m, list, n, rule.d, rule.n, kappa)
     switch (kind) {
     case BEM_LAPLACE_SLP: if (p1) BEM_TOUCH(BEM_LAPLACE_SLP, BEM_P1); else BEM_TOUCH(BEM_LAPLACE_SLP, BEM_P0); break;
     case BEM_LAPLACE_DLP: if (p1) BEM_TOUCH(BEM_LAPLACE_DLP, BEM_P1); else BEM_TOUCH(BEM_LAPLACE_DLP, BEM_P0); break;
     default: if (p1) BEM_TOUCH(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TOUCH(BEM_HELMHOLTZ_SLP, BEM_P0); break;
     }
 #undef BEM_TOUCH
-    (void)cas;
     return cudaGetLastError();
 }
 
-template <int KIND, int NP>
+template <int KIND, int NP, bool MIXED>
 static cudaError_t block_np(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
                             const int64_t *prefix, int *status, int grid, cudaStream_t st)
 {
     if (m.basis == BEM_P0) {
-        k_block_p0<KIND, NP><<<grid, 256, 0, st>>>(m, L, R, prefix, status);
+        k_block_p0<KIND, NP, MIXED><<<grid, 256, 0, st>>>(m, L, R, prefix, status);
     } else {
-        const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP);
-        cudaError_t e = cudaFuncSetAttribute(k_block_p1<KIND, NP>,
+        const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP, MIXED);
+        cudaError_t e = cudaFuncSetAttribute(k_block_p1<KIND, NP, MIXED>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_block_p1<KIND, NP><<<grid, 256, sm, st>>>(m, L, R, prefix, status);
+        const int g = MIXED ? grid * 2 : grid;
+        k_block_p1<KIND, NP, MIXED><<<g, p1_threads(MIXED), sm, st>>>(m, L, R, prefix, status);
     }
     return cudaGetLastError();
 }
 
-template <int KIND>
+template <int KIND, bool MIXED>
 static cudaError_t block_kind(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
                               const int64_t *prefix, int *status, int grid, cudaStream_t st)
 {
     switch (R.np) {
-    case 4: return block_np<KIND, 4>(m, L, R, prefix, status, grid, st);
-    case 7: return block_np<KIND, 7>(m, L, R, prefix, status, grid, st);
-    case 9: return block_np<KIND, 9>(m, L, R, prefix, status, grid, st);
-    case 16: return block_np<KIND, 16>(m, L, R, prefix, status, grid, st);
+    case 4: return block_np<KIND, 4, MIXED>(m, L, R, prefix, status, grid, st);
+    case 7: return block_np<KIND, 7, MIXED>(m, L, R, prefix, status, grid, st);
+    case 9: return block_np<KIND, 9, MIXED>(m, L, R, prefix, status, grid, st);
+    case 16: return block_np<KIND, 16, MIXED>(m, L, R, prefix, status, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -772,10 +1147,15 @@ cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const R
                                 const int64_t *prefix, int *status, int grid, cudaStream_t st)
 {
     if (L.n_blocks <= 0) return cudaSuccess;
+    // the mixed form covers the Laplace kernels; Helmholtz pairs stay FP64
     switch (L.kind) {
-    case BEM_LAPLACE_SLP: return block_kind<BEM_LAPLACE_SLP>(m, L, R, prefix, status, grid, st);
-    case BEM_LAPLACE_DLP: return block_kind<BEM_LAPLACE_DLP>(m, L, R, prefix, status, grid, st);
-    default: return block_kind<BEM_HELMHOLTZ_SLP>(m, L, R, prefix, status, grid, st);
+    case BEM_LAPLACE_SLP:
+        return L.mixed ? block_kind<BEM_LAPLACE_SLP, true>(m, L, R, prefix, status, grid, st)
+                       : block_kind<BEM_LAPLACE_SLP, false>(m, L, R, prefix, status, grid, st);
+    case BEM_LAPLACE_DLP:
+        return L.mixed ? block_kind<BEM_LAPLACE_DLP, true>(m, L, R, prefix, status, grid, st)
+                       : block_kind<BEM_LAPLACE_DLP, false>(m, L, R, prefix, status, grid, st);
+    default: return block_kind<BEM_HELMHOLTZ_SLP, false>(m, L, R, prefix, status, grid, st);
     }
 }
 

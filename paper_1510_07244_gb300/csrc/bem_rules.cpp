@@ -82,6 +82,15 @@ bool gauss_legendre_unit(int q, std::vector<double> &x, std::vector<double> &w)
     return true;
 }
 
+static void round_rule(Rule2D &r)
+{
+    for (int k = 0; k < r.np; ++k) {
+        r.sf[k] = (float)r.s[k];
+        r.tf[k] = (float)r.t[k];
+        r.wf[k] = (float)r.w[k];
+    }
+}
+
 bool make_rule2d(int regular_rule, int q, Rule2D &out)
 {
     if (regular_rule == BEM_RULE_TRI7) {
@@ -100,6 +109,7 @@ bool make_rule2d(int regular_rule, int q, Rule2D &out)
             out.t[k] = L[k][2];
             out.w[k] = W[k];
         }
+        round_rule(out);
         return true;
     }
     if (regular_rule != BEM_RULE_DUFFY || q < 1 || q * q > kMaxNp) return false;
@@ -112,6 +122,7 @@ bool make_rule2d(int regular_rule, int q, Rule2D &out)
             out.t[i * q + j] = g[i] * g[j];
             out.w[i * q + j] = gw[i] * gw[j] * g[i];
         }
+    round_rule(out);
     return true;
 }
 

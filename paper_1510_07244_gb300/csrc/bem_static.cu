@@ -117,7 +117,7 @@ extern "C" int bem_near_field_noalloc(bem_ctx *ctx, const bem_block_job *job)
                             ctx->stream);
         if (e == cudaSuccess)
             e = launch_touching(m->v, c, m->list[c], m->nlist[c], r, J.kernel.kind, J.kernel.kappa,
-                                ctx->stream);
+                                0, ctx->stream);
         if (e != cudaSuccess) return noalloc_fail(ctx, BEM_ERR_CUDA, cudaGetErrorString(e));
     }
 
@@ -137,6 +137,7 @@ extern "C" int bem_near_field_noalloc(bem_ctx *ctx, const bem_block_job *job)
     L.kappa = J.kernel.kappa;
     L.lower_only = 0;
     L.allow_touching = 1;
+    L.mixed = 0;
     const int tc = m->v.basis == BEM_P0 ? 8 : kTile;
     e = launch_tile_prefix(L, kTile, tc, prefix, ctx->status, ctx->stream);
     if (e == cudaSuccess)

@@ -20,6 +20,32 @@ def rel_err(got, ref, row_ids):
     return np.abs(got - ref) / den
 
 
+def rel_err_abs(got, ref, absint, row_ids):
+    """|got - ref| / max(A, 1e-3 * max A over the same row), A = the oracle's sum
+    of term magnitudes (oracle.entries_absolute).
+
+    A floating-point evaluation of a quadrature sum has a forward error bounded
+    by a multiple of the unit roundoff times the sum of the magnitudes of its
+    terms; where the integrand changes sign (a double-layer pair whose test
+    triangle straddles the trial triangle's plane) A exceeds |ref| and this is
+    the measure that a fixed-precision evaluation can meet.  For integrands of
+    one sign (single layer) A = |ref| and this equals rel_err."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    absint = np.asarray(absint)
+    row_ids = np.asarray(row_ids)
+    scale = np.zeros(row_ids.max() + 1 if len(row_ids) else 1)
+    np.maximum.at(scale, row_ids, absint)
+    den = np.maximum(absint, 1e-3 * scale[row_ids])
+    den = np.where(den > 0, den, 1.0)
+    return np.abs(got - ref) / den
+
+
+def oracle_absolute(mesh, basis, rows, cols, kernel, kappa, quad):
+    return oracle.entries_absolute(mesh.verts, mesh.tris, rows, cols, kernel=kernel, kappa=kappa,
+                                   basis=basis, **quad)
+
+
 def to_dev(a, dtype):
     import torch
     return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)

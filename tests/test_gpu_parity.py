@@ -12,7 +12,8 @@ import pytest
 import oracle
 import synth
 from synth.workloads import BlockSet, h2_blocks
-from parity_util import block_job, oracle_entries, rel_err, to_dev
+from parity_util import (block_job, oracle_absolute, oracle_entries, rel_err, rel_err_abs,
+                         to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -259,4 +260,92 @@ def test_c2_full_size_sampled(ctx, pkg):
             ref = oracle_entries(w.mesh, w.basis, r[pick], c[pick], op.kernel, op.kappa, quad)
             # row scale from the full row set of the sample
             assert rel_err(got_all[pick], ref, r[pick]).max() <= TOL
+    ctx.bem_mesh_free(mid)
+
+
+# --------------------------------------------------------------------------
+# Mixed-precision form: FP32 regular and common-vertex pairs (Laplace), FP64
+# identical and common-edge pairs.  Bar: 1e-6, the tolerance of the mixed
+# form, measured against the sum of term magnitudes (rel_err_abs), which is
+# the plain relative error wherever the integrand has one sign.
+# --------------------------------------------------------------------------
+MIXED_TOL = 1e-6
+LAPLACE = [("laplace_slp", 0.0), ("laplace_dlp", 0.0)]
+
+
+@pytest.mark.parametrize("meshname", ["ico2", "cube3", "torus"])
+@pytest.mark.parametrize("kernel,kappa", LAPLACE)
+@pytest.mark.parametrize("basis", ["p0", "p1"])
+def test_mixed_dense_matches_oracle(ctx, pkg, meshname, kernel, kappa, basis):
+    mesh = MESHES[meshname]()
+    quad = dict(QUADS["paper"], precision="mixed")
+    got, n = _dense(ctx, pkg, mesh, basis, kernel, kappa, quad)
+    rows = np.repeat(np.arange(n), n)
+    cols = np.tile(np.arange(n), n)
+    ref = oracle_entries(mesh, basis, rows, cols, kernel, kappa, QUADS["paper"]).reshape(n, n)
+    absint = oracle_absolute(mesh, basis, rows, cols, kernel, kappa, QUADS["paper"])
+    err = rel_err_abs(got.ravel(), ref.ravel(), absint, rows)
+    assert err.max() <= MIXED_TOL
+    if kernel == "laplace_slp":
+        assert rel_err(got.ravel(), ref.ravel(), rows).max() <= MIXED_TOL
+    # and it is not the FP64 result in disguise
+    assert err.max() > 1e-12
+
+
+@pytest.mark.parametrize("basis", ["p0", "p1"])
+@pytest.mark.parametrize("kernel,kappa", LAPLACE)
+def test_mixed_near_field_and_coupling(ctx, pkg, basis, kernel, kappa):
+    quad = dict(QUADS["paper"], precision="mixed")
+    mesh = synth.jitter(synth.icosphere(3), 0.05, 23)
+    part, near, far = h2_blocks(mesh, basis, leaf_size=16, eta=2.0, rank=6, pivot_seed=7)
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, basis)
+    out_n = _out(near.n_entries, kernel)
+    out_f = _out(far.n_entries, kernel)
+    ctx.bem_near_field([block_job(pkg, mid, near, kernel, kappa, quad, out_n)])
+    ctx.bem_coupling_blocks([block_job(pkg, mid, far, kernel, kappa, quad, out_f)])
+    ctx.bem_sync()
+    for bs, out in ((near, out_n), (far, out_f)):
+        r, c = bs.entry_indices()
+        got = out.cpu().numpy()[: bs.n_entries]
+        ref = oracle_entries(mesh, basis, r, c, kernel, kappa, QUADS["paper"])
+        absint = oracle_absolute(mesh, basis, r, c, kernel, kappa, QUADS["paper"])
+        assert rel_err_abs(got, ref, absint, r).max() <= MIXED_TOL
+    ctx.bem_mesh_free(mid)
+
+
+def test_mixed_translated_far_from_origin(ctx, pkg):
+    """The double-float anchors keep the mixed form accurate when the mesh sits
+    far from the origin (coordinates ~1e3, triangles ~0.1)."""
+    mesh = MESHES["cube3"]()
+    moved = synth.Mesh(mesh.verts + np.array([1e3, -7e2, 3e2]), mesh.tris)
+    quad = dict(QUADS["paper"], precision="mixed")
+    for kernel in ("laplace_slp", "laplace_dlp"):
+        got, n = _dense(ctx, pkg, moved, "p1", kernel, 0.0, quad)
+        rows = np.repeat(np.arange(n), n)
+        cols = np.tile(np.arange(n), n)
+        ref = oracle_entries(mesh, "p1", rows, cols, kernel, 0.0, QUADS["paper"]).reshape(n, n)
+        absint = oracle_absolute(mesh, "p1", rows, cols, kernel, 0.0, QUADS["paper"])
+        assert rel_err_abs(got.ravel(), ref.ravel(), absint, rows).max() <= MIXED_TOL, kernel
+
+
+def test_mixed_full_size_against_fp64(ctx, pkg):
+    """Every entry of the 20480-triangle P1 workload: mixed form vs FP64 form."""
+    import torch
+    w = synth.workloads.config2()
+    mid = ctx.bem_mesh_upload(w.mesh.verts, w.mesh.tris, w.basis)
+    q64 = w.quad.kw()
+    qmx = dict(q64, precision="mixed")
+    for op in w.operators:
+        res = {}
+        for name, q in (("fp64", q64), ("mixed", qmx)):
+            out_n = _out(w.near.n_entries, op.kernel)
+            out_f = _out(w.far.n_entries, op.kernel)
+            ctx.bem_near_field([block_job(pkg, mid, w.near, op.kernel, op.kappa, q, out_n)])
+            ctx.bem_coupling_blocks([block_job(pkg, mid, w.far, op.kernel, op.kappa, q, out_f)])
+            ctx.bem_sync()
+            res[name] = (out_n.cpu().numpy(), out_f.cpu().numpy())
+        for k, bs in enumerate((w.near, w.far)):
+            r, _ = bs.entry_indices()
+            err = rel_err(res["mixed"][k], res["fp64"][k], r)
+            assert err.max() <= MIXED_TOL, (op.kernel, k, err.max())
     ctx.bem_mesh_free(mid)

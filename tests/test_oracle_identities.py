@@ -192,3 +192,23 @@ def test_argument_validation(oracle_mod):
     with pytest.raises(ValueError):
         oracle_mod.entries(m.verts, bad, [0], [1])
     assert len(oracle_mod.entries(m.verts, m.tris, [], [])) == 0
+
+
+def test_absolute_sums(oracle_mod):
+    """entries_absolute: equal to the entry where the integrand has one sign (single
+    layer), never below |entry| (double layer, Helmholtz), and positive."""
+    mesh = synth.jitter(synth.cube_surface(2), 0.05, 5)
+    n = mesh.nt
+    rows = np.repeat(np.arange(n), n)
+    cols = np.tile(np.arange(n), n)
+    for kernel, kappa in (("laplace_slp", 0.0), ("laplace_dlp", 0.0), ("helmholtz_slp", 6.0)):
+        g = oracle_mod.entries(mesh.verts, mesh.tris, rows, cols, kernel=kernel, kappa=kappa, **Q5)
+        A = oracle_mod.entries_absolute(mesh.verts, mesh.tris, rows, cols, kernel=kernel,
+                                        kappa=kappa, **Q5)
+        assert np.all(A >= np.abs(g) * (1 - 1e-14))
+        if kernel == "laplace_slp":
+            assert np.allclose(A, g.real, rtol=1e-15, atol=0)
+    # P1 single layer: hat functions are nonnegative, so again A = g
+    g = oracle_mod.entries(mesh.verts, mesh.tris, [0, 3], [1, 5], basis="p1", **Q5).real
+    A = oracle_mod.entries_absolute(mesh.verts, mesh.tris, [0, 3], [1, 5], basis="p1", **Q5)
+    assert np.allclose(A, g, rtol=1e-15, atol=0)
