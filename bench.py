@@ -45,15 +45,23 @@ def flops_per_point(kernel: str, basis: str, np_axis: int) -> float:
     return f
 
 
-def flops_per_point_ss(kernel: str, basis: str) -> float:
-    """Per point of a 4D singular rule (no product structure): the map of both
-    points 24, r^2 5, rsqrt 1, weight and accumulation 2; P1 adds the hat
-    functions 4, three weights 3 and nine accumulations 18 - 2."""
-    f = 32.0
-    if kernel in ("laplace_dlp", "helmholtz_slp"):
-        f += 8.0
+def flops_per_point_ss(case: str, kernel: str, basis: str) -> float:
+    """Per point of a singular rule, as the touching kernels evaluate it: the
+    difference vector from 2 / 3 / 4 scaled edge vectors (identical / edge /
+    vertex: 9 / 15 / 21), r^2 5, rsqrt 1, weight 1 and accumulation 1; the
+    double layer's height costs 1 for a common edge (x2 H) and 5 for a common
+    vertex, plus r^-3 2 and a product 1, and vanishes for identical (flat)
+    pairs; Helmholtz adds kappa r 1, sincos 2, products 3; P1 replaces the
+    accumulation by three products and nine FMAs on the moments (+20)."""
+    if kernel == "laplace_dlp" and case == "identical":
+        return 0.0
+    f = {"identical": 9.0, "edge": 15.0, "vertex": 21.0}[case] + 8.0
+    if kernel == "laplace_dlp":
+        f += (1.0 if case == "edge" else 5.0) + 3.0
+    elif kernel == "helmholtz_slp":
+        f += 6.0 + 2.0
     if basis == "p1":
-        f += 23.0
+        f += 20.0
     return f
 
 
@@ -76,7 +84,7 @@ def kernel_flops(w, counts, stats, precision):
     for cas, nsub, qq, key in (("touching_vertex", 2, q.q_vertex, "n_vertex"),
                                ("touching_edge", 4, q.q_edge, "n_edge"),
                                ("touching_identical", 6, q.q_identical, "n_identical")):
-        f = sum(stats[key] * nsub * qq ** 4 * flops_per_point_ss(o.kernel, w.basis)
+        f = sum(stats[key] * nsub * qq ** 4 * flops_per_point_ss(cas.split("_")[1], o.kernel, w.basis)
                 for o in w.operators)
         p = "fp32" if (mixed and cas == "touching_vertex" and pipe == "fp32") else "fp64"
         out[cas] = (f, p)

@@ -186,6 +186,18 @@ int bem_pivot_entries(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kern
 int bem_assemble_dense(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
                        const bem_quad_desc *quad, int32_t lower_only, void *out);
 
+/* ---- quadrature rules ------------------------------------------------------
+ * Copies the library's 4D rule on D x D for a case (Section 2.2; case 0 =
+ * disjoint pairs with regular_rule BEM_RULE_DUFFY / BEM_RULE_TRI7, 1 = common
+ * vertex, 2 = common edge, 3 = identical; q = Gauss points per axis) into the
+ * HOST array `out` as 7 columns of n values: x1, x2, y1, y2, w, x1-y1,
+ * x2-y2 (x in the test triangle's reference domain, y in the trial's, w the
+ * weight including the Jacobian; the differences are formed from each
+ * subdomain map's own factors).  Returns n, or a negative BEM_ERR_* for an
+ * unknown case or order.  If out is NULL or cap < 7 n, only n is returned.
+ * Needs no device and no context. */
+int64_t bem_rule_points(int32_t cas, int32_t regular_rule, int32_t q, double *out, int64_t cap);
+
 /* ---- allocation-free near field --------------------------------------------
  * The paper has no counterpart of this call; it exists for callers that must
  * not allocate device memory (a service whose device memory belongs to its own
@@ -196,7 +208,7 @@ int bem_assemble_dense(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *ker
  * Computes the same near-field blocks as bem_near_field for ONE job, with the
  * same kernels, but calls no cudaMalloc, cudaFree or other allocating routine.
  * Its scratch (singular-case rule tables and per-block tile sums) is a static
- * device array of 1,302,336 bytes inside the library, present on every GPU
+ * device array of 1,395,200 bytes inside the library, present on every GPU
  * that loads the library until the process exits.  Limits: at most 65536
  * blocks and singular orders q_vertex, q_edge, q_identical <= 6; larger
  * requests fail with BEM_ERR_INVALID_ARG and a message naming the limit.

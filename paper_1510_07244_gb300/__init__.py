@@ -6,7 +6,7 @@ this package only marshals arguments to it (``_binding``) and, in
 ``workloads``, assembles the synthetic benchmark inputs.
 """
 from ._binding import (Context, BlockJob, BemError, kernel_desc, quad_desc, load, LIB_PATH,
-                       EXPORTS, KERNELS, BASES, RULES)
+                       EXPORTS, KERNELS, BASES, RULES, bem_rule_points)
 
 __all__ = ["Context", "BlockJob", "BemError", "kernel_desc", "quad_desc", "load", "LIB_PATH",
-           "EXPORTS", "KERNELS", "BASES", "RULES"]
+           "EXPORTS", "KERNELS", "BASES", "RULES", "bem_rule_points"]

@@ -26,7 +26,7 @@ ORDER_MODES = {"fixed": 0, "learned": 1}
 EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_upload",
            "bem_mesh_free", "bem_mesh_info", "bem_near_field", "bem_coupling_blocks",
            "bem_pivot_entries", "bem_assemble_dense", "bem_profile_enable",
-           "bem_profile_reset", "bem_profile_read", "bem_near_field_noalloc"]
+           "bem_profile_reset", "bem_profile_read", "bem_near_field_noalloc", "bem_rule_points"]
 
 
 class BemError(RuntimeError):
@@ -99,15 +99,33 @@ def load():
     lib.bem_assemble_dense.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc),
                                        P(bem_quad_desc), ctypes.c_int32, _vp]
     lib.bem_near_field_noalloc.argtypes = [_vp, P(bem_block_job)]
+    lib.bem_rule_points.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
+                                    ctypes.c_int64]
     lib.bem_profile_enable.argtypes = [_vp, ctypes.c_int32]
     lib.bem_profile_reset.argtypes = [_vp]
     lib.bem_profile_read.argtypes = [_vp, P(bem_kernel_time), ctypes.c_int32,
                                      P(ctypes.c_int32)]
     for name in EXPORTS:
-        if name != "bem_last_error":
+        if name not in ("bem_last_error", "bem_rule_points"):
             getattr(lib, name).restype = ctypes.c_int
+    lib.bem_rule_points.restype = ctypes.c_int64
     _lib = lib
     return lib
+
+
+CASES = {"regular": 0, "vertex": 1, "edge": 2, "identical": 3}
+
+
+def bem_rule_points(case: str, q: int, regular_rule: str = "duffy"):
+    """The library's 4D rule for a case: dict of numpy columns x1, x2, y1, y2, w, d1, d2."""
+    lib = load()
+    n = lib.bem_rule_points(CASES[case], RULES[regular_rule], q, None, 0)
+    if n < 0:
+        raise BemError(int(n), "bad rule")
+    out = np.zeros(7 * n)
+    lib.bem_rule_points(CASES[case], RULES[regular_rule], q, out.ctypes.data_as(_vp), out.size)
+    cols = out.reshape(7, n)
+    return dict(zip(("x1", "x2", "y1", "y2", "w", "d1", "d2"), cols))
 
 
 def kernel_desc(kind="laplace_slp", kappa=0.0) -> bem_kernel_desc:

@@ -176,7 +176,7 @@ int get_rule4(bem_ctx *ctx, int cas, int rule, int q, Rule4D &out)
     std::vector<double> soa;
     if (!make_rule4d_host(cas, rule, q, soa)) return fail(ctx, BEM_ERR_INVALID_ARG, "bad rule");
     Rule4D r;
-    r.n = (int)(soa.size() / 5);
+    r.n = (int)(soa.size() / kRuleCols);
     cudaError_t e = cudaMalloc((void **)&r.d, soa.size() * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(rule)");
     e = cudaMemcpy(r.d, soa.data(), soa.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -685,6 +685,16 @@ int bem_profile_read(bem_ctx *ctx, bem_kernel_time *out, int32_t cap, int32_t *n
     }
     if (n_out) *n_out = k;
     return BEM_OK;
+}
+
+int64_t bem_rule_points(int32_t cas, int32_t regular_rule, int32_t q, double *out, int64_t cap)
+{
+    if (cas < kRegular || cas > kIdentical || q < 1 || q > 20) return BEM_ERR_INVALID_ARG;
+    std::vector<double> soa;
+    if (!make_rule4d_host(cas, regular_rule, q, soa)) return BEM_ERR_INVALID_ARG;
+    const int64_t n = (int64_t)(soa.size() / kRuleCols);
+    if (out && cap >= (int64_t)soa.size()) std::memcpy(out, soa.data(), soa.size() * sizeof(double));
+    return n;
 }
 
 }  // extern "C"

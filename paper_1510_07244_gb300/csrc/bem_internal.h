@@ -36,11 +36,14 @@ struct Rule2D {
     float sf[kMaxNp], tf[kMaxNp], wf[kMaxNp];   // the same rule rounded to float
 };
 
-// 4D rule on D x D, device SoA: x1 | x2 | y1 | y2 | w, n each.
+// 4D rule on D x D, device SoA with kRuleCols columns of n values:
+// x1 | x2 | y1 | y2 | w | x1-y1 | x2-y2 (the differences are formed from each
+// subdomain map's own factors, so they keep full precision near the singular set).
+constexpr int kRuleCols = 7;
 struct Rule4D {
     int n = 0;
-    double *d = nullptr;   // device, 5 n doubles
-    float *f = nullptr;    // device, 5 n floats (mixed form), may be null
+    double *d = nullptr;   // device, kRuleCols n doubles
+    float *f = nullptr;    // device, kRuleCols n floats (mixed form), may be null
 };
 
 // Device view of an uploaded mesh.

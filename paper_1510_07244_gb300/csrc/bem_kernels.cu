@@ -329,9 +329,39 @@ __device__ __forceinline__ void regular_p1_f32(const TriF &A, const TriF &B, con
 }
 
 // ---------------------------------------------------------------------------
-// Touching pairs: one warp per pair.
+// Touching pairs: one warp per pair, FP64.
+//
+// In the canonical vertex orders the shared vertices come first, so
+//   identical:  x - y = (x1-y1) e1 + (x2-y2) e2          (both maps equal)
+//   edge:       x - y = (x1-y1) e1 + x2 e2a - y2 e2b      (shared edge e1)
+//   vertex:     x - y = x1 e1a + x2 e2a - y1 e1b - y2 e2b
+// with the differences x1-y1, x2-y2 read from the rule (formed from each
+// subdomain map's factors).  The double layer (x-y).n_b is the height of x
+// above the trial plane: zero for identical (flat) pairs, x2 (e2a . n_b) for
+// common edges.  The piecewise-linear local matrix is accumulated as the
+// nine moments of (1, x1, x2) x (1, y1, y2) and mapped to the hat functions
+// lambda = (1-s, s-t, t) once per pair.
 // ---------------------------------------------------------------------------
-template <int KIND, int BASIS>
+template <class T>
+__device__ __forceinline__ void moments_to_hats(const T M[9], T out[9])
+{
+    // hats = A m with A = [[1,-1,0],[0,1,-1],[0,0,1]] on both sides: out = A M A^T
+    T R[9];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        R[0 * 3 + b] = M[0 * 3 + b] - M[1 * 3 + b];
+        R[1 * 3 + b] = M[1 * 3 + b] - M[2 * 3 + b];
+        R[2 * 3 + b] = M[2 * 3 + b];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        out[a * 3 + 0] = R[a * 3 + 0] - R[a * 3 + 1];
+        out[a * 3 + 1] = R[a * 3 + 1] - R[a * 3 + 2];
+        out[a * 3 + 2] = R[a * 3 + 2];
+    }
+}
+
+template <int KIND, int BASIS, int CAS>
 __global__ void __launch_bounds__(256) k_touching(MeshView m, const int *__restrict__ list,
                                                   int64_t n, const double *__restrict__ rule,
                                                   int np, double kappa)
@@ -343,66 +373,118 @@ __global__ void __launch_bounds__(256) k_touching(MeshView m, const int *__restr
     const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);
     const int pc = __ldg(m.nb_perm + idx);
     const int *pa = c_perm[pc / 6], *pb = c_perm[pc % 6];
-    Tri A, B;
-    load_tri(m.geom, a, A);
-    load_tri(m.geom, b, B);
-    double e1a[3], e2a[3], e1b[3], e2b[3], d0[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        e1a[c] = A.v[pa[1]][c] - A.v[pa[0]][c];
-        e2a[c] = A.v[pa[2]][c] - A.v[pa[1]][c];
-        e1b[c] = B.v[pb[1]][c] - B.v[pb[0]][c];
-        e2b[c] = B.v[pb[2]][c] - B.v[pb[1]][c];
-        d0[c] = A.v[pa[0]][c] - B.v[pb[0]][c];
-    }
     constexpr int NACC = BASIS == BEM_P0 ? 1 : 9;
+    constexpr bool CPLX = KIND == BEM_HELMHOLTZ_SLP;
+    constexpr bool ZERO = KIND == BEM_LAPLACE_DLP && CAS == kIdentical;   // flat pair
     double accr[NACC], acci[NACC];
 #pragma unroll
     for (int k = 0; k < NACC; ++k) accr[k] = acci[k] = 0.0;
-    const double *X1 = rule, *X2 = rule + np, *Y1 = rule + 2 * np, *Y2 = rule + 3 * np,
-                 *W = rule + 4 * np;
-    for (int p = lane; p < np; p += 32) {
-        const double x1 = __ldg(X1 + p), x2 = __ldg(X2 + p), y1 = __ldg(Y1 + p),
-                     y2 = __ldg(Y2 + p), w = __ldg(W + p);
-        const double dx = d0[0] + x1 * e1a[0] + x2 * e2a[0] - y1 * e1b[0] - y2 * e2b[0];
-        const double dy = d0[1] + x1 * e1a[1] + x2 * e2a[1] - y1 * e1b[1] - y2 * e2b[1];
-        const double dz = d0[2] + x1 * e1a[2] + x2 * e2a[2] - y1 * e1b[2] - y2 * e2b[2];
-        double kr, ki;
-        kval<KIND>(dx, dy, dz, B.n, kappa, kr, ki);
-        if (BASIS == BEM_P0) {
-            accr[0] += w * kr;
-            if (KIND == BEM_HELMHOLTZ_SLP) acci[0] += w * ki;
-        } else {
-            const double la[3] = {1.0 - x1, x1 - x2, x2};
-            const double lb[3] = {1.0 - y1, y1 - y2, y2};
+    const double *g_a = m.geom + (int64_t)a * kGeomStride;
+    const double *g_b = m.geom + (int64_t)b * kGeomStride;
+    if (!ZERO) {
+        double va[3][3], vb[3][3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const double fr = w * kr * la[i];
-                const double fi = w * ki * la[i];
+        for (int k = 0; k < 3; ++k) {
+            const int ia = pa[k], ib = pb[k];
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    accr[i * 3 + j] += fr * lb[j];
-                    if (KIND == BEM_HELMHOLTZ_SLP) acci[i * 3 + j] += fi * lb[j];
+            for (int c = 0; c < 3; ++c) {
+                va[k][c] = __ldg(g_a + 3 * ia + c);
+                vb[k][c] = __ldg(g_b + 3 * ib + c);
+            }
+        }
+        double e1a[3], e2a[3], e1b[3], e2b[3], nb[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            e1a[c] = va[1][c] - va[0][c];
+            e2a[c] = va[2][c] - va[1][c];
+            e1b[c] = vb[1][c] - vb[0][c];
+            e2b[c] = vb[2][c] - vb[1][c];
+            nb[c] = __ldg(g_b + 9 + c);
+        }
+        // edge: height of x above the trial plane is x2 (e2a . n_b)
+        const double H = e2a[0] * nb[0] + e2a[1] * nb[1] + e2a[2] * nb[2];
+        const double *X1 = rule, *X2 = rule + np, *Y1 = rule + 2 * np, *Y2 = rule + 3 * np,
+                     *W = rule + 4 * np, *D1 = rule + 5 * np, *D2 = rule + 6 * np;
+        for (int p = lane; p < np; p += 32) {
+            const double w = __ldg(W + p);
+            double x1 = 0.0, x2 = __ldg(X2 + p), y1 = 0.0, y2 = 0.0;
+            double dx, dy, dz;
+            if (CAS == kIdentical) {
+                const double d1 = __ldg(D1 + p), d2 = __ldg(D2 + p);
+                dx = d1 * e1a[0] + d2 * e2a[0];
+                dy = d1 * e1a[1] + d2 * e2a[1];
+                dz = d1 * e1a[2] + d2 * e2a[2];
+            } else if (CAS == kEdge) {
+                const double d1 = __ldg(D1 + p);
+                y2 = __ldg(Y2 + p);
+                dx = d1 * e1a[0] + x2 * e2a[0] - y2 * e2b[0];
+                dy = d1 * e1a[1] + x2 * e2a[1] - y2 * e2b[1];
+                dz = d1 * e1a[2] + x2 * e2a[2] - y2 * e2b[2];
+            } else {
+                x1 = __ldg(X1 + p);
+                y1 = __ldg(Y1 + p);
+                y2 = __ldg(Y2 + p);
+                dx = x1 * e1a[0] + x2 * e2a[0] - y1 * e1b[0] - y2 * e2b[0];
+                dy = x1 * e1a[1] + x2 * e2a[1] - y1 * e1b[1] - y2 * e2b[1];
+                dz = x1 * e1a[2] + x2 * e2a[2] - y1 * e1b[2] - y2 * e2b[2];
+            }
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            const double ri = rsqrt(r2);
+            double kr, ki = 0.0;
+            if (KIND == BEM_LAPLACE_SLP) {
+                kr = ri;
+            } else if (KIND == BEM_LAPLACE_DLP) {
+                const double dn = CAS == kEdge ? x2 * H : dx * nb[0] + dy * nb[1] + dz * nb[2];
+                kr = dn * ri * ri * ri;
+            } else {
+                double sn, cs;
+                sincos(kappa * (r2 * ri), &sn, &cs);
+                kr = cs * ri;
+                ki = sn * ri;
+            }
+            const double wr = w * kr, wi = w * ki;
+            if (BASIS == BEM_P0) {
+                accr[0] += wr;
+                if (CPLX) acci[0] += wi;
+            } else {
+                if (CAS != kVertex) {
+                    x1 = __ldg(X1 + p);
+                    y1 = __ldg(Y1 + p);
+                    if (CAS == kIdentical) y2 = __ldg(Y2 + p);
+                }
+                const double mx[3] = {1.0, x1, x2}, my[3] = {1.0, y1, y2};
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const double fr = wr * mx[i];
+                    const double fi = wi * mx[i];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        accr[i * 3 + j] += fr * my[j];
+                        if (CPLX) acci[i * 3 + j] += fi * my[j];
+                    }
                 }
             }
         }
-    }
-    const double scale = A.sg * B.sg * kInv4Pi;
 #pragma unroll
-    for (int k = 0; k < NACC; ++k) {
-        accr[k] = warp_sum(accr[k]);
-        if (KIND == BEM_HELMHOLTZ_SLP) acci[k] = warp_sum(acci[k]);
+        for (int k = 0; k < NACC; ++k) {
+            accr[k] = warp_sum(accr[k]);
+            if (CPLX) acci[k] = warp_sum(acci[k]);
+        }
     }
     if (lane == 0) {
+        const double scale = __ldg(g_a + 12) * __ldg(g_b + 12) * kInv4Pi;
         if (BASIS == BEM_P0) {
             m.table[idx] = make_double2(accr[0] * scale, acci[0] * scale);
         } else {
+            double hr[9], hi[9];
+            moments_to_hats(accr, hr);
+            moments_to_hats(acci, hi);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
                     m.table[(int64_t)idx * 9 + pa[i] * 3 + pb[j]] =
-                        make_double2(accr[i * 3 + j] * scale, acci[i * 3 + j] * scale);
+                        make_double2(hr[i * 3 + j] * scale, hi[i * 3 + j] * scale);
         }
     }
 }
@@ -454,7 +536,7 @@ __global__ void __launch_bounds__(256) k_touching_vertex_f32(MeshView m, const i
 #pragma unroll
     for (int k = 0; k < NACC; ++k) acc[k] = 0.0f;
     const float *X1 = rule, *X2 = rule + np, *Y1 = rule + 2 * np, *Y2 = rule + 3 * np,
-                *W = rule + 4 * np;
+                *W = rule + 4 * np;   // columns 5, 6 (differences) are not needed here
     for (int p = lane; p < np; p += 32) {
         const float x1 = __ldg(X1 + p), x2 = __ldg(X2 + p), y1 = __ldg(Y1 + p),
                     y2 = __ldg(Y2 + p), w = __ldg(W + p);
@@ -466,12 +548,13 @@ __global__ void __launch_bounds__(256) k_touching_vertex_f32(MeshView m, const i
         if (BASIS == BEM_P0) {
             acc[0] += wk;
         } else {
-            const float la[3] = {1.0f - x1, x1 - x2, x2};
-            const float lb[3] = {1.0f - y1, y1 - y2, y2};
+            const float mx[3] = {1.0f, x1, x2}, my[3] = {1.0f, y1, y2};
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < 3; ++i) {
+                const float f = wk * mx[i];
 #pragma unroll
-                for (int j = 0; j < 3; ++j) acc[i * 3 + j] = fmaf(wk * la[i], lb[j], acc[i * 3 + j]);
+                for (int j = 0; j < 3; ++j) acc[i * 3 + j] = fmaf(f, my[j], acc[i * 3 + j]);
+            }
         }
     }
 #pragma unroll
@@ -481,12 +564,15 @@ __global__ void __launch_bounds__(256) k_touching_vertex_f32(MeshView m, const i
         if (BASIS == BEM_P0) {
             m.table[idx] = make_double2((double)acc[0] * scale, 0.0);
         } else {
+            double M[9], hat[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) M[k] = (double)acc[k];
+            moments_to_hats(M, hat);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
-                    m.table[(int64_t)idx * 9 + pa[i] * 3 + pb[j]] =
-                        make_double2((double)acc[i * 3 + j] * scale, 0.0);
+                    m.table[(int64_t)idx * 9 + pa[i] * 3 + pb[j]] = make_double2(hat[i * 3 + j] * scale, 0.0);
         }
     }
 }
@@ -1103,12 +1189,19 @@ cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t
         }
         return cudaGetLastError();
     }
-#define BEM_TOUCH(K, B) k_touching<K, B><<<blocks, 256, 0, st>>>(m, list, n, rule.d, rule.n, kappa)
+#define BEM_TOUCH(K, B, C) k_touching<K, B, C><<<blocks, 256, 0, st>>>(m, list, n, rule.d, rule.n, kappa)
+#define BEM_TOUCH_CASE(K, B)                                   \
+    do {                                                       \
+        if (cas == kIdentical) BEM_TOUCH(K, B, kIdentical);    \
+        else if (cas == kEdge) BEM_TOUCH(K, B, kEdge);         \
+        else BEM_TOUCH(K, B, kVertex);                         \
+    } while (0)
     switch (kind) {
-    case BEM_LAPLACE_SLP: if (p1) BEM_TOUCH(BEM_LAPLACE_SLP, BEM_P1); else BEM_TOUCH(BEM_LAPLACE_SLP, BEM_P0); break;
-    case BEM_LAPLACE_DLP: if (p1) BEM_TOUCH(BEM_LAPLACE_DLP, BEM_P1); else BEM_TOUCH(BEM_LAPLACE_DLP, BEM_P0); break;
-    default: if (p1) BEM_TOUCH(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TOUCH(BEM_HELMHOLTZ_SLP, BEM_P0); break;
+    case BEM_LAPLACE_SLP: if (p1) BEM_TOUCH_CASE(BEM_LAPLACE_SLP, BEM_P1); else BEM_TOUCH_CASE(BEM_LAPLACE_SLP, BEM_P0); break;
+    case BEM_LAPLACE_DLP: if (p1) BEM_TOUCH_CASE(BEM_LAPLACE_DLP, BEM_P1); else BEM_TOUCH_CASE(BEM_LAPLACE_DLP, BEM_P0); break;
+    default: if (p1) BEM_TOUCH_CASE(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TOUCH_CASE(BEM_HELMHOLTZ_SLP, BEM_P0); break;
     }
+#undef BEM_TOUCH_CASE
 #undef BEM_TOUCH
     return cudaGetLastError();
 }

@@ -130,6 +130,7 @@ namespace {
 
 struct Pt {
     double x1, x2, y1, y2, w;
+    double d1, d2;   // x1 - y1, x2 - y2 formed from the map's own factors
 };
 
 // One piece of R+: maps (xi, e1, e2, e3) to (x, y) and its Jacobian.
@@ -140,20 +141,24 @@ std::vector<Piece> pieces(int cas)
     std::vector<Piece> P;
     if (cas == kVertex) {
         P.push_back([](double xi, double e1, double e2, double e3) {
-            return Pt{xi, xi * e1, xi * e2, xi * e2 * e3, xi * xi * xi * e2};
+            return Pt{xi, xi * e1, xi * e2, xi * e2 * e3, xi * xi * xi * e2,
+                      xi * (1.0 - e2), xi * (e1 - e2 * e3)};
         });
     } else if (cas == kEdge) {
         P.push_back([](double xi, double e1, double e2, double e3) {
             double a = e1, u = e1 * e2 * (1.0 - e3), c = e1 * e2 * e3;
-            return Pt{xi, xi * a, xi * (1.0 - u), xi * c, xi * xi * xi * e1 * e1 * e2};
+            return Pt{xi, xi * a, xi * (1.0 - u), xi * c, xi * xi * xi * e1 * e1 * e2,
+                      xi * u, xi * (a - c)};
         });
         P.push_back([](double xi, double e1, double e2, double e3) {
             double a = e1 * e2, u = e1 * e3, c = e1 * (1.0 - e3);
-            return Pt{xi, xi * a, xi * (1.0 - u), xi * c, xi * xi * xi * e1 * e1};
+            return Pt{xi, xi * a, xi * (1.0 - u), xi * c, xi * xi * xi * e1 * e1,
+                      xi * u, xi * (a - c)};
         });
     } else if (cas == kIdentical) {
         auto mk = [](double u, double w, double a, double xi, double e1) {
-            return Pt{xi, xi * a, xi * (1.0 - u), xi * (a - w), xi * xi * xi * e1 * (1.0 - e1)};
+            return Pt{xi, xi * a, xi * (1.0 - u), xi * (a - w), xi * xi * xi * e1 * (1.0 - e1),
+                      xi * u, xi * w};
         };
         P.push_back([mk](double xi, double e1, double e2, double e3) {
             return mk(e1 * e2, e1, e1 + (1.0 - e1) * e3, xi, e1);
@@ -178,7 +183,8 @@ bool make_rule4d_host(int cas, int regular_rule, int q, std::vector<double> &soa
         if (!make_rule2d(regular_rule, q, r)) return false;
         for (int i = 0; i < r.np; ++i)
             for (int j = 0; j < r.np; ++j)
-                pts.push_back(Pt{r.s[i], r.t[i], r.s[j], r.t[j], r.w[i] * r.w[j]});
+                pts.push_back(Pt{r.s[i], r.t[i], r.s[j], r.t[j], r.w[i] * r.w[j],
+                                 r.s[i] - r.s[j], r.t[i] - r.t[j]});
     } else {
         std::vector<double> g, gw;
         if (!gauss_legendre_unit(q, g, gw)) return false;
@@ -193,18 +199,22 @@ bool make_rule4d_host(int cas, int regular_rule, int q, std::vector<double> &soa
                                 if (swap) {
                                     std::swap(p.x1, p.y1);
                                     std::swap(p.x2, p.y2);
+                                    p.d1 = -p.d1;
+                                    p.d2 = -p.d2;
                                 }
                                 pts.push_back(p);
                             }
     }
     const size_t n = pts.size();
-    soa.assign(5 * n, 0.0);
+    soa.assign(kRuleCols * n, 0.0);
     for (size_t k = 0; k < n; ++k) {
         soa[k] = pts[k].x1;
         soa[n + k] = pts[k].x2;
         soa[2 * n + k] = pts[k].y1;
         soa[3 * n + k] = pts[k].y2;
         soa[4 * n + k] = pts[k].w;
+        soa[5 * n + k] = pts[k].d1;
+        soa[6 * n + k] = pts[k].d2;
     }
     return true;
 }

@@ -21,9 +21,9 @@ namespace {
 
 constexpr int64_t kMaxBlocks = 65536;   // tile prefix slots (int64 each)
 constexpr int kMaxOrder = 6;            // singular orders q <= 6
-// vertex 2 q^4 + edge 4 q^4 + identical 6 q^4 points, 5 doubles per point
-constexpr int64_t kRuleDoubles = 5LL * 12 * kMaxOrder * kMaxOrder * kMaxOrder * kMaxOrder;
-constexpr int64_t kScratchDoubles = kMaxBlocks + kRuleDoubles;   // 1,302,336 B in all
+// vertex 2 q^4 + edge 4 q^4 + identical 6 q^4 points, 7 doubles per point
+constexpr int64_t kRuleDoubles = 7LL * 12 * kMaxOrder * kMaxOrder * kMaxOrder * kMaxOrder;
+constexpr int64_t kScratchDoubles = kMaxBlocks + kRuleDoubles;   // 1,395,200 B in all
 
 // One copy per device of every process that loads the library.  In host code
 // this name is only a host-side stand-in: the device address comes from
@@ -110,7 +110,7 @@ extern "C" int bem_near_field_noalloc(bem_ctx *ctx, const bem_block_job *job)
         std::vector<double> soa;
         if (!make_rule4d_host(c, 0, qs[c], soa)) return noalloc_fail(ctx, BEM_ERR_INVALID_ARG, "bad rule");
         Rule4D r;
-        r.n = (int)(soa.size() / 5);
+        r.n = (int)(soa.size() / kRuleCols);
         r.d = rules + at;
         at += (int64_t)soa.size();
         e = cudaMemcpyAsync(r.d, soa.data(), soa.size() * sizeof(double), cudaMemcpyHostToDevice,
