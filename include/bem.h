@@ -186,6 +186,44 @@ int bem_pivot_entries(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kern
 int bem_assemble_dense(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
                        const bem_quad_desc *quad, int32_t lower_only, void *out);
 
+/* ---- persistent batched driver ---------------------------------------------
+ * A plan replaces the paper's CPU-side list machinery (Section 3, Algorithms
+ * 1-4: per-case lists, list-size limit, worker threads, result scatter) for a
+ * fixed set of jobs: the near-field jobs (as bem_near_field) and coupling
+ * jobs (as bem_coupling_blocks) of any meshes and kernels.  Jobs that share
+ * a kernel instantiation (basis, kernel, regular rule and order, precision)
+ * form one bucket, and each bucket is drained by ONE persistent launch over
+ * the tiles of all its jobs; touching pairs are likewise batched per (case,
+ * order).  Each near-field job gets its own touching table inside the plan.
+ *   flags: BEM_PLAN_GRAPH     capture the whole launch sequence into a CUDA
+ *                             graph at creation; bem_plan_run replays it;
+ *          BEM_PLAN_AUTOTUNE  time candidate grid sizes per bucket on the
+ *                             plan's data at creation and keep the fastest
+ *                             (cached in the context);
+ *          BEM_PLAN_PROFILE   record launch-profiling events in the plan
+ *                             (read with bem_profile_read while profiling is
+ *                             enabled).
+ * The plan keeps the jobs' device pointers (index lists, outputs) and uses
+ * the meshes' device data: both must stay valid until bem_plan_destroy; the
+ * index lists' contents are read at every run.
+ * bem_plan_create runs the plan's kernels once (or several times when
+ * autotuning), so outputs are written at creation too.  Results are the
+ * same, bit for bit, as those of bem_near_field / bem_coupling_blocks.
+ * Errors as bem_near_field; BEM_ERR_CUDA if graph capture fails. */
+typedef struct bem_plan bem_plan;
+#define BEM_PLAN_GRAPH    1
+#define BEM_PLAN_AUTOTUNE 2
+#define BEM_PLAN_PROFILE  4
+int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near,
+                    const bem_block_job *coupling_jobs, int32_t n_coupling, int32_t flags,
+                    bem_plan **plan);
+int bem_plan_run(bem_ctx *ctx, bem_plan *plan);
+int bem_plan_destroy(bem_ctx *ctx, bem_plan *plan);
+/* Launch counts of a plan (touching buckets, block buckets) and the chosen
+ * CTAs per SM of up to `cap` block buckets. */
+int bem_plan_info(bem_ctx *ctx, bem_plan *plan, int32_t *n_touch_launches,
+                  int32_t *n_block_launches, int32_t *grid_mult, int32_t cap);
+
 /* ---- quadrature rules ------------------------------------------------------
  * Copies the library's 4D rule on D x D for a case (Section 2.2; case 0 =
  * disjoint pairs with regular_rule BEM_RULE_DUFFY / BEM_RULE_TRI7, 1 = common

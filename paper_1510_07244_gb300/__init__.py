@@ -6,7 +6,9 @@ this package only marshals arguments to it (``_binding``) and, in
 ``workloads``, assembles the synthetic benchmark inputs.
 """
 from ._binding import (Context, BlockJob, BemError, kernel_desc, quad_desc, load, LIB_PATH,
-                       EXPORTS, KERNELS, BASES, RULES, bem_rule_points)
+                       EXPORTS, KERNELS, BASES, RULES, bem_rule_points, PLAN_GRAPH,
+                       PLAN_AUTOTUNE, PLAN_PROFILE)
 
 __all__ = ["Context", "BlockJob", "BemError", "kernel_desc", "quad_desc", "load", "LIB_PATH",
-           "EXPORTS", "KERNELS", "BASES", "RULES", "bem_rule_points"]
+           "EXPORTS", "KERNELS", "BASES", "RULES", "bem_rule_points",
+           "PLAN_GRAPH", "PLAN_AUTOTUNE", "PLAN_PROFILE"]

@@ -26,7 +26,9 @@ ORDER_MODES = {"fixed": 0, "learned": 1}
 EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_upload",
            "bem_mesh_free", "bem_mesh_info", "bem_near_field", "bem_coupling_blocks",
            "bem_pivot_entries", "bem_assemble_dense", "bem_profile_enable",
-           "bem_profile_reset", "bem_profile_read", "bem_near_field_noalloc", "bem_rule_points"]
+           "bem_profile_reset", "bem_profile_read", "bem_near_field_noalloc", "bem_rule_points",
+           "bem_plan_create", "bem_plan_run", "bem_plan_destroy", "bem_plan_info"]
+PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE = 1, 2, 4
 
 
 class BemError(RuntimeError):
@@ -99,6 +101,12 @@ def load():
     lib.bem_assemble_dense.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc),
                                        P(bem_quad_desc), ctypes.c_int32, _vp]
     lib.bem_near_field_noalloc.argtypes = [_vp, P(bem_block_job)]
+    lib.bem_plan_create.argtypes = [_vp, P(bem_block_job), ctypes.c_int32, P(bem_block_job),
+                                    ctypes.c_int32, ctypes.c_int32, P(_vp)]
+    lib.bem_plan_run.argtypes = [_vp, _vp]
+    lib.bem_plan_destroy.argtypes = [_vp, _vp]
+    lib.bem_plan_info.argtypes = [_vp, _vp, P(ctypes.c_int32), P(ctypes.c_int32),
+                                  P(ctypes.c_int32), ctypes.c_int32]
     lib.bem_rule_points.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
                                     ctypes.c_int64]
     lib.bem_profile_enable.argtypes = [_vp, ctypes.c_int32]
@@ -281,3 +289,29 @@ class Context:
         self._check(self.lib.bem_profile_read(self.h, arr, cap, ctypes.byref(n)))
         return {arr[k].name.decode(): (arr[k].launches, arr[k].total_ms)
                 for k in range(min(cap, n.value))}
+
+    def bem_plan_create(self, near_jobs, coupling_jobs, flags=PLAN_GRAPH):
+        """Plan over near-field and coupling jobs; returns an opaque handle.  The
+        jobs' tensors must stay alive until bem_plan_destroy."""
+        nj = (bem_block_job * max(1, len(near_jobs)))(*[j.to_c() for j in near_jobs])
+        cj = (bem_block_job * max(1, len(coupling_jobs)))(*[j.to_c() for j in coupling_jobs])
+        h = ctypes.c_void_p()
+        self._check(self.lib.bem_plan_create(self.h, nj, len(near_jobs), cj, len(coupling_jobs),
+                                             int(flags), ctypes.byref(h)))
+        self._plans = getattr(self, "_plans", {})
+        self._plans[h.value] = (near_jobs, coupling_jobs)   # keep the tensors alive
+        return h
+
+    def bem_plan_run(self, plan):
+        self._check(self.lib.bem_plan_run(self.h, plan))
+
+    def bem_plan_destroy(self, plan):
+        self._check(self.lib.bem_plan_destroy(self.h, plan))
+        getattr(self, "_plans", {}).pop(plan.value, None)
+
+    def bem_plan_info(self, plan):
+        nt, nb = ctypes.c_int32(0), ctypes.c_int32(0)
+        g = (ctypes.c_int32 * 64)()
+        self._check(self.lib.bem_plan_info(self.h, plan, ctypes.byref(nt), ctypes.byref(nb), g, 64))
+        return {"touch_launches": nt.value, "block_launches": nb.value,
+                "grid_mult": [g[k] for k in range(min(64, nb.value))]}

@@ -293,6 +293,47 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
 
 }  // namespace
 
+namespace bem {
+
+int api_fail(bem_ctx *ctx, int code, const char *msg) { return fail(ctx, code, msg); }
+int api_cuda_fail(bem_ctx *ctx, cudaError_t e, const char *where) { return cuda_fail(ctx, e, where); }
+int api_get_rule4(bem_ctx *ctx, int cas, int rule, int q, Rule4D &out)
+{
+    return get_rule4(ctx, cas, rule, q, out);
+}
+
+int api_check_job(bem_ctx *ctx, const bem_block_job &J, Rule2D &r2, Mesh **mesh)
+{
+    Mesh *m = get_mesh(ctx, J.mesh_id);
+    if (!m) return fail(ctx, BEM_ERR_INVALID_ARG, "unknown mesh id");
+    int rc = check_kernel(ctx, &J.kernel);
+    if (rc) return rc;
+    rc = check_quad(ctx, &J.quad, r2);
+    if (rc) return rc;
+    if (J.n_blocks < 0) return fail(ctx, BEM_ERR_INVALID_ARG, "negative block count");
+    if (J.n_blocks > 0 &&
+        (!J.row_ptr || !J.row_idx || !J.col_ptr || !J.col_idx || !J.blk_row || !J.blk_col ||
+         !J.blk_off || !J.out || J.n_row_clusters < 1 || J.n_col_clusters < 1))
+        return fail(ctx, BEM_ERR_INVALID_ARG, "null pointer or empty cluster list");
+    if (J.kernel.kind == BEM_HELMHOLTZ_SLP && (reinterpret_cast<uintptr_t>(J.out) & 15))
+        return fail(ctx, BEM_ERR_INVALID_ARG, "complex output must be 16-byte aligned");
+    if (m->v.basis == BEM_P1 && m->v.maxdeg > kMaxDegP1)
+        return fail(ctx, BEM_ERR_UNSUPPORTED, "vertex degree above 16 (piecewise linear)");
+    *mesh = m;
+    return BEM_OK;
+}
+
+void prof_accumulate(bem_ctx *ctx, const bem_prof_rec &r)
+{
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    auto &t = ctx->prof_total[r.name];
+    t.first += 1;
+    t.second += ms;
+}
+
+}  // namespace bem
+
 extern "C" {
 
 int bem_create(bem_ctx **out, int device, void *cuda_stream)
@@ -323,6 +364,7 @@ int bem_destroy(bem_ctx *ctx)
     if (!ctx) return BEM_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    plan_forget(ctx);
     for (auto &kv : ctx->meshes) free_mesh(kv.second);
     for (auto &kv : ctx->rules4) {
         cudaFree(kv.second.d);
@@ -508,6 +550,7 @@ int bem_mesh_upload(bem_ctx *ctx, const double *verts, int64_t nv, const int32_t
     V.nb_perm = d_nbperm;
     for (int c = kVertex; c <= kIdentical; ++c) {
         m->nlist[c] = (int64_t)lists[c].size();
+        m->hlist[c] = lists[c];
         if ((rc = upload(ctx, m, lists[c], &m->list[c]))) {
             free_mesh(m);
             return rc;
@@ -673,6 +716,7 @@ int bem_profile_read(bem_ctx *ctx, bem_kernel_time *out, int32_t cap, int32_t *n
         ctx->prof_free.push_back(r.b);
     }
     ctx->prof_pending.clear();
+    plan_drain_profile(ctx);
     int k = 0;
     for (auto &kv : ctx->prof_total) {
         if (k < cap) {

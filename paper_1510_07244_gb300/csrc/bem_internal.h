@@ -71,6 +71,7 @@ struct Mesh {
     std::vector<void *> allocs;
     int *list[4] = {nullptr, nullptr, nullptr, nullptr};   // touching indices per case
     int64_t nlist[4] = {0, 0, 0, 0};
+    std::vector<int> hlist[4];                              // host copies of the lists
     int *iota = nullptr;       // 0 .. n-1 (dense calls)
     int *dense_csr = nullptr;  // {0, n} and the block {0, 0, off 0}
 };
@@ -97,6 +98,8 @@ struct bem_ctx {
     std::vector<bem_prof_rec> prof_pending;
     std::vector<cudaEvent_t> prof_free;
     std::map<std::string, std::pair<int64_t, double>> prof_total;
+    std::vector<struct bem_plan *> prof_plans;   // plans whose last run's events are unread
+    std::map<std::string, int> tuned;            // autotuner cache: bucket key -> CTAs per SM
 };
 
 namespace bem {
@@ -111,6 +114,16 @@ struct ProfScope {
 }  // namespace bem
 
 namespace bem {
+
+// bem_api.cpp helpers shared with the plan driver
+int api_fail(bem_ctx *ctx, int code, const char *msg);
+int api_cuda_fail(bem_ctx *ctx, cudaError_t e, const char *where);
+int api_check_job(bem_ctx *ctx, const bem_block_job &J, Rule2D &r2, Mesh **mesh);
+int api_get_rule4(bem_ctx *ctx, int cas, int rule, int q, Rule4D &out);
+void prof_accumulate(bem_ctx *ctx, const bem_prof_rec &r);
+// bem_plan.cpp: adds the unread launch times of plans run since the last read
+void plan_drain_profile(bem_ctx *ctx);
+void plan_forget(bem_ctx *ctx);   // context teardown
 
 // bem_rules.cpp
 bool gauss_legendre_unit(int q, std::vector<double> &x, std::vector<double> &w);
@@ -132,6 +145,24 @@ struct BlockLaunch {
     int mixed;        // 1: regular pairs in FP32 (BEM_MIXED)
 };
 
+// One block list of a batched launch (device table entry).
+struct BatchJob {
+    MeshView m;
+    BlockLaunch L;
+    const int64_t *prefix;     // per-block tile prefix sums of this list
+};
+
+// One mesh / kernel of a batched touching launch.
+struct TouchJob {
+    MeshView m;                // m.table = this job's touching table
+    double kappa;
+};
+
+// Launch shape of a block-engine bucket (autotuned).
+struct Shape {
+    int grid_mult;             // CTAs per SM
+};
+
 cudaError_t launch_tile_prefix(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
                                int *status, cudaStream_t st);
 cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
@@ -140,6 +171,13 @@ cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t
 cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const Rule2D &rule,
                                 const int64_t *prefix, int *status, int grid, cudaStream_t st);
 size_t p1_smem_bytes(bool cplx, bool mixed);
+cudaError_t launch_tile_prefix_batch(BatchJob *jobs, int n_jobs, int tr, int tc, int64_t *job_total,
+                                     int64_t *job_end, int *status, cudaStream_t st);
+cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int cas, int mixed,
+                                  const int2 *items, int64_t n, const Rule4D &rule, cudaStream_t st);
+cudaError_t launch_block_batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end, int basis,
+                               int kind, int mixed, const Rule2D &R, int *status, int grid,
+                               cudaStream_t st);
 cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const int32_t *cols,
                                  int64_t n, void *out, const Rule4D *rules /*[4]*/, int kind,
                                  double kappa, int *status, cudaStream_t st);

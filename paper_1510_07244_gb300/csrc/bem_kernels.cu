@@ -362,14 +362,9 @@ __device__ __forceinline__ void moments_to_hats(const T M[9], T out[9])
 }
 
 template <int KIND, int BASIS, int CAS>
-__global__ void __launch_bounds__(256) k_touching(MeshView m, const int *__restrict__ list,
-                                                  int64_t n, const double *__restrict__ rule,
-                                                  int np, double kappa)
+__device__ __forceinline__ void touch_pair(const MeshView &m, int idx, const double *__restrict__ rule,
+                                           int np, double kappa, int lane)
 {
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wid >= n) return;
-    const int idx = __ldg(list + wid);
     const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);
     const int pc = __ldg(m.nb_perm + idx);
     const int *pa = c_perm[pc / 6], *pb = c_perm[pc % 6];
@@ -489,18 +484,35 @@ __global__ void __launch_bounds__(256) k_touching(MeshView m, const int *__restr
     }
 }
 
+template <int KIND, int BASIS, int CAS>
+__global__ void __launch_bounds__(256) k_touching(MeshView m, const int *__restrict__ list,
+                                                  int64_t n, const double *__restrict__ rule,
+                                                  int np, double kappa)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= n) return;
+    touch_pair<KIND, BASIS, CAS>(m, __ldg(list + wid), rule, np, kappa, threadIdx.x & 31);
+}
+
+// Batched: items[k] = (job, touching index) over many meshes / kernels.
+template <int KIND, int BASIS, int CAS>
+__global__ void __launch_bounds__(256) k_touching_batch(const TouchJob *__restrict__ jobs,
+                                                        const int2 *__restrict__ items, int64_t n,
+                                                        const double *__restrict__ rule, int np)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= n) return;
+    const int2 it = items[wid];
+    touch_pair<KIND, BASIS, CAS>(jobs[it.x].m, it.y, rule, np, jobs[it.x].kappa, threadIdx.x & 31);
+}
+
 // Common-vertex pairs in float (mixed form, Laplace kernels): the shared vertex is
 // the canonical vertex 0 of both triangles, so x - y is formed from edge
 // vectors only and keeps float precision down to the singular point.
 template <int KIND, int BASIS>
-__global__ void __launch_bounds__(256) k_touching_vertex_f32(MeshView m, const int *__restrict__ list,
-                                                             int64_t n, const float *__restrict__ rule,
-                                                             int np)
+__device__ __forceinline__ void touch_vertex_f32(const MeshView &m, int idx,
+                                                 const float *__restrict__ rule, int np, int lane)
 {
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wid >= n) return;
-    const int idx = __ldg(list + wid);
     const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);
     const int pc = __ldg(m.nb_perm + idx);
     const int *pa = c_perm[pc / 6], *pb = c_perm[pc % 6];
@@ -575,6 +587,29 @@ __global__ void __launch_bounds__(256) k_touching_vertex_f32(MeshView m, const i
                     m.table[(int64_t)idx * 9 + pa[i] * 3 + pb[j]] = make_double2(hat[i * 3 + j] * scale, 0.0);
         }
     }
+}
+
+template <int KIND, int BASIS>
+__global__ void __launch_bounds__(256) k_touching_vertex_f32(MeshView m, const int *__restrict__ list,
+                                                             int64_t n, const float *__restrict__ rule,
+                                                             int np)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= n) return;
+    touch_vertex_f32<KIND, BASIS>(m, __ldg(list + wid), rule, np, threadIdx.x & 31);
+}
+
+template <int KIND, int BASIS>
+__global__ void __launch_bounds__(256) k_touching_vertex_f32_batch(const TouchJob *__restrict__ jobs,
+                                                                   const int2 *__restrict__ items,
+                                                                   int64_t n,
+                                                                   const float *__restrict__ rule,
+                                                                   int np)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= n) return;
+    const int2 it = items[wid];
+    touch_vertex_f32<KIND, BASIS>(jobs[it.x].m, it.y, rule, np, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -732,8 +767,8 @@ __device__ __forceinline__ BlockInfo block_info(const BlockLaunch &L, const int6
 }
 
 // Tiles per block -> inclusive prefix sums (single CTA, chunked).
-__global__ void __launch_bounds__(1024) k_tile_prefix(BlockLaunch L, int tr, int tc,
-                                                      int64_t *prefix, int *status)
+__device__ void tile_prefix_cta(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
+                                int *status, int64_t *total)
 {
     __shared__ int64_t part[1024];
     const int64_t n = L.n_blocks;
@@ -764,6 +799,45 @@ __global__ void __launch_bounds__(1024) k_tile_prefix(BlockLaunch L, int tr, int
     }
     const int64_t base = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
     for (int64_t b = lo; b < hi; ++b) prefix[b] += base;
+    if (total && threadIdx.x == blockDim.x - 1) *total = part[threadIdx.x];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_tile_prefix(BlockLaunch L, int tr, int tc,
+                                                      int64_t *prefix, int *status)
+{
+    tile_prefix_cta(L, tr, tc, prefix, status, nullptr);
+}
+
+// one CTA per job: per-job block prefix sums and the job's tile total
+__global__ void __launch_bounds__(1024) k_tile_prefix_batch(BatchJob *jobs, int tr, int tc,
+                                                            int64_t *job_total, int *status)
+{
+    BatchJob &J = jobs[blockIdx.x];
+    tile_prefix_cta(J.L, tr, tc, const_cast<int64_t *>(J.prefix), status, job_total + blockIdx.x);
+}
+
+// inclusive scan of the job totals (single CTA)
+__global__ void __launch_bounds__(1024) k_job_scan(const int64_t *job_total, int n, int64_t *job_end)
+{
+    __shared__ int64_t part[1024];
+    const int chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * chunk, hi = min(n, lo + chunk);
+    int64_t sum = 0;
+    for (int k = lo; k < hi; ++k) {
+        sum += job_total[k];
+        job_end[k] = sum;
+    }
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        int64_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const int64_t base = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
+    for (int k = lo; k < hi; ++k) job_end[k] += base;
 }
 
 // ---------------------------------------------------------------------------
@@ -771,33 +845,33 @@ __global__ void __launch_bounds__(1024) k_tile_prefix(BlockLaunch L, int tr, int
 // ---------------------------------------------------------------------------
 constexpr int kP0Cols = 8;
 
+// One tile (32 rows x 8 columns) of one block list; `tile` indexes the list's tiles.
 template <int KIND, int NP, bool MIXED>
-__global__ void __launch_bounds__(256) k_block_p0(MeshView m, BlockLaunch L, Rule2D R,
-                                                  const int64_t *__restrict__ prefix,
-                                                  int *status)
+__device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
+                                        const int64_t *__restrict__ prefix, int64_t tile,
+                                        int *status)
 {
-    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
     const int lr = threadIdx.x & 31, lc = threadIdx.x >> 5;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    {
         const BlockInfo bi = block_info(L, prefix, tile, status);
-        if (!bi.ok) continue;
+        if (!bi.ok) return;
         const int ntr = (bi.nr + kTile - 1) / kTile;
         const int r = (bi.tile_in_blk % ntr) * kTile + lr;
         const int c = (bi.tile_in_blk / ntr) * kP0Cols + lc;
-        if (r >= bi.nr || c >= bi.nc) continue;
+        if (r >= bi.nr || c >= bi.nc) return;
         const int a = L.row_idx[bi.r_lo + r], b = L.col_idx[bi.c_lo + c];
         if (a < 0 || a >= m.nt || b < 0 || b >= m.nt) {
             set_status(status, BEM_ERR_INVALID_ARG);
-            continue;
+            return;
         }
-        if (L.lower_only && a < b) continue;
+        if (L.lower_only && a < b) return;
         double re, im;
         const int4 va = __ldg(m.tvid + a), vb = __ldg(m.tvid + b);
         if (touching(va, vb)) {
             const int k = L.allow_touching ? find_touching(m, a, b) : -1;
             if (k < 0) {
                 set_status(status, BEM_ERR_INVALID_ARG);
-                continue;
+                return;
             }
             const double2 v = m.table[k];
             re = v.x;
@@ -820,6 +894,16 @@ __global__ void __launch_bounds__(256) k_block_p0(MeshView m, BlockLaunch L, Rul
     }
 }
 
+template <int KIND, int NP, bool MIXED>
+__global__ void __launch_bounds__(256) k_block_p0(MeshView m, BlockLaunch L, Rule2D R,
+                                                  const int64_t *__restrict__ prefix,
+                                                  int *status)
+{
+    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x)
+        p0_tile<KIND, NP, MIXED>(m, L, R, prefix, tile, status);
+}
+
 // ---------------------------------------------------------------------------
 // Block engine, piecewise linear: tile = 32 x 32 vertices.  The triangles
 // touching the tile's rows (Ta) and columns (Tb) are collected in shared
@@ -833,7 +917,9 @@ constexpr int kP1MaxTri = kTile * kMaxDegP1;
 struct P1Smem {
     int rows[kTile], cols[kTile];
     int ta[kP1MaxTri], tb[kP1MaxTri];
-    int rl[kTile][kMaxDegP1], cl[kTile][kMaxDegP1];
+    // per-vertex support lists, stored [k][vertex] so that the 32 lanes of a
+    // warp (one vertex each) read consecutive words (no bank conflicts)
+    int rl[kMaxDegP1][kTile], cl[kMaxDegP1][kTile];
     int rl_n[kTile], cl_n[kTile];
     int cnt_r[kTile], off_r[kTile], cnt_c[kTile], off_c[kTile];
     int nta, ntb;
@@ -863,7 +949,7 @@ __device__ __forceinline__ int owner_pos(const MeshView &m, int T, const int *se
 // order (by owner position, then adjacency order), and per vertex the list of
 // (triangle slot << 2 | local index).
 __device__ void p1_support(const MeshView &m, const int *set, int n, int *tri, int *cnt,
-                           int *off, int (*lists)[kMaxDegP1], int *list_n, int *ntri,
+                           int *off, int (*lists)[kTile], int *list_n, int *ntri,
                            int *status)
 {
     const int tid = threadIdx.x;
@@ -906,7 +992,7 @@ __device__ void p1_support(const MeshView &m, const int *set, int n, int *tri, i
                 if (tri[u] == T) slot = u;
             const int4 tv = __ldg(m.tvid + T);
             const int loc = tv.x == v ? 0 : (tv.y == v ? 1 : 2);
-            lists[tid][k - lo] = (slot << 2) | loc;
+            lists[k - lo][tid] = (slot << 2) | loc;
         }
         list_n[tid] = hi - lo;
     }
@@ -919,9 +1005,11 @@ __device__ void p1_support(const MeshView &m, const int *set, int n, int *tri, i
 __host__ __device__ constexpr int p1_threads(bool mixed) { return mixed ? 128 : 256; }
 __host__ __device__ constexpr int p1_min_blocks(bool mixed) { return mixed ? 4 : 1; }
 
+// One 32 x 32 tile of one block list (called by every thread of the CTA).
 template <int KIND, int NP, bool MIXED>
-__global__ void __launch_bounds__(p1_threads(MIXED), p1_min_blocks(MIXED))
-k_block_p1(MeshView m, BlockLaunch L, Rule2D R, const int64_t *__restrict__ prefix, int *status)
+__device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
+                                        const int64_t *__restrict__ prefix, int64_t tile,
+                                        int *status, unsigned char *smem_raw)
 {
     constexpr bool CPLX = KIND == BEM_HELMHOLTZ_SLP;
     constexpr int NT = p1_threads(MIXED);
@@ -929,16 +1017,13 @@ k_block_p1(MeshView m, BlockLaunch L, Rule2D R, const int64_t *__restrict__ pref
     constexpr int EW = NT / 32;                // column stride of owned entries
     // pair results: double in the FP64 form, float in the mixed form
     using Val = typename std::conditional<MIXED, float, double>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     P1Smem &S = *reinterpret_cast<P1Smem *>(smem_raw);
     Val *buf_r = reinterpret_cast<Val *>(smem_raw + ((sizeof(P1Smem) + 15) & ~size_t(15)));
     Val *buf_i = buf_r + kP1Cap * 9;
     const int tid = threadIdx.x;
-    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
-
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    {
         const BlockInfo bi = block_info(L, prefix, tile, status);
-        if (!bi.ok) continue;   // uniform across the CTA
+        if (!bi.ok) return;   // uniform across the CTA
         const int ntr = (bi.nr + kTile - 1) / kTile;
         const int r0 = (bi.tile_in_blk % ntr) * kTile, c0 = (bi.tile_in_blk / ntr) * kTile;
         const int tr = min(kTile, bi.nr - r0), tc = min(kTile, bi.nc - c0);
@@ -959,7 +1044,7 @@ k_block_p1(MeshView m, BlockLaunch L, Rule2D R, const int64_t *__restrict__ pref
         if (bad) {
             if (tid == 0) set_status(status, BEM_ERR_INVALID_ARG);
             __syncthreads();
-            continue;
+            return;
         }
         p1_support(m, S.rows, tr, S.ta, S.cnt_r, S.off_r, S.rl, S.rl_n, &S.nta, status);
         p1_support(m, S.cols, tc, S.tb, S.cnt_c, S.off_c, S.cl, S.cl_n, &S.ntb, status);
@@ -1025,11 +1110,11 @@ k_block_p1(MeshView m, BlockLaunch L, Rule2D R, const int64_t *__restrict__ pref
                 const int ec = (tid >> 5) + EW * e;
                 if (er < tr && ec < tc) {
                     for (int u = 0; u < S.rl_n[er]; ++u) {
-                        const int ia = S.rl[er][u] >> 2, la = S.rl[er][u] & 3;
+                        const int ia = S.rl[u][er] >> 2, la = S.rl[u][er] & 3;
                         if (ia < ia0 || ia >= ia1) continue;
                         const int rowbase = (ia - ia0) * ntb;
                         for (int v = 0; v < S.cl_n[ec]; ++v) {
-                            const int ib = S.cl[ec][v] >> 2, lb = S.cl[ec][v] & 3;
+                            const int ib = S.cl[v][ec] >> 2, lb = S.cl[v][ec] & 3;
                             const int q = (rowbase + ib) * 9 + la * 3 + lb;
                             if (MIXED) {
                                 const Val y = buf_r[q] - cmpr[e];
@@ -1059,6 +1144,63 @@ k_block_p1(MeshView m, BlockLaunch L, Rule2D R, const int64_t *__restrict__ pref
             }
         }
         __syncthreads();
+    }
+}
+
+template <int KIND, int NP, bool MIXED>
+__global__ void __launch_bounds__(p1_threads(MIXED), p1_min_blocks(MIXED))
+k_block_p1(MeshView m, BlockLaunch L, Rule2D R, const int64_t *__restrict__ prefix, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x)
+        p1_tile<KIND, NP, MIXED>(m, L, R, prefix, tile, status, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Batched (persistent) block engine: one launch drains the tiles of many
+// block lists (jobs) that share kernel, basis, rule and precision, e.g. the
+// near-field and coupling blocks of many meshes.  job_end[j] = tiles of jobs
+// 0..j (inclusive); every tile finds its job by binary search and runs the
+// same tile body as the single-list kernels, so the results are identical.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_job(const int64_t *job_end, int n_jobs, int64_t tile)
+{
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (job_end[mid] > tile) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+template <int KIND, int NP, bool MIXED>
+__global__ void __launch_bounds__(256) k_batch_p0(const BatchJob *__restrict__ jobs, int n_jobs,
+                                                  const int64_t *__restrict__ job_end, Rule2D R,
+                                                  int *status)
+{
+    const int64_t total = n_jobs > 0 ? job_end[n_jobs - 1] : 0;
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int j = find_job(job_end, n_jobs, tile);
+        const int64_t local = tile - (j > 0 ? job_end[j - 1] : 0);
+        const BatchJob &J = jobs[j];
+        p0_tile<KIND, NP, MIXED>(J.m, J.L, R, J.prefix, local, status);
+    }
+}
+
+template <int KIND, int NP, bool MIXED>
+__global__ void __launch_bounds__(p1_threads(MIXED), p1_min_blocks(MIXED))
+k_batch_p1(const BatchJob *__restrict__ jobs, int n_jobs, const int64_t *__restrict__ job_end,
+           Rule2D R, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t total = n_jobs > 0 ? job_end[n_jobs - 1] : 0;
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int j = find_job(job_end, n_jobs, tile);
+        const int64_t local = tile - (j > 0 ? job_end[j - 1] : 0);
+        const BatchJob &J = jobs[j];
+        p1_tile<KIND, NP, MIXED>(J.m, J.L, R, J.prefix, local, status, smem_raw);
     }
 }
 
@@ -1269,6 +1411,102 @@ cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const i
     default: k_pivot<BEM_HELMHOLTZ_SLP><<<(unsigned)blocks, 256, 0, st>>>(m, rows, cols, n, out, rs, kappa, status); break;
     }
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_tile_prefix_batch(BatchJob *jobs, int n_jobs, int tr, int tc, int64_t *job_total,
+                                     int64_t *job_end, int *status, cudaStream_t st)
+{
+    if (n_jobs <= 0) return cudaSuccess;
+    k_tile_prefix_batch<<<n_jobs, 1024, 0, st>>>(jobs, tr, tc, job_total, status);
+    k_job_scan<<<1, 1024, 0, st>>>(job_total, n_jobs, job_end);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int cas, int mixed,
+                                  const int2 *items, int64_t n, const Rule4D &rule, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n + 7) / 8);
+    const bool p1 = basis == BEM_P1;
+    if (mixed && cas == kVertex && kind != BEM_HELMHOLTZ_SLP && rule.f) {
+        if (kind == BEM_LAPLACE_SLP) {
+            if (p1) k_touching_vertex_f32_batch<BEM_LAPLACE_SLP, BEM_P1><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
+            else k_touching_vertex_f32_batch<BEM_LAPLACE_SLP, BEM_P0><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
+        } else {
+            if (p1) k_touching_vertex_f32_batch<BEM_LAPLACE_DLP, BEM_P1><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
+            else k_touching_vertex_f32_batch<BEM_LAPLACE_DLP, BEM_P0><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
+        }
+        return cudaGetLastError();
+    }
+#define BEM_TB(K, B, C) k_touching_batch<K, B, C><<<blocks, 256, 0, st>>>(jobs, items, n, rule.d, rule.n)
+#define BEM_TB_CASE(K, B)                                  \
+    do {                                                   \
+        if (cas == kIdentical) BEM_TB(K, B, kIdentical);   \
+        else if (cas == kEdge) BEM_TB(K, B, kEdge);        \
+        else BEM_TB(K, B, kVertex);                        \
+    } while (0)
+    switch (kind) {
+    case BEM_LAPLACE_SLP: if (p1) BEM_TB_CASE(BEM_LAPLACE_SLP, BEM_P1); else BEM_TB_CASE(BEM_LAPLACE_SLP, BEM_P0); break;
+    case BEM_LAPLACE_DLP: if (p1) BEM_TB_CASE(BEM_LAPLACE_DLP, BEM_P1); else BEM_TB_CASE(BEM_LAPLACE_DLP, BEM_P0); break;
+    default: if (p1) BEM_TB_CASE(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TB_CASE(BEM_HELMHOLTZ_SLP, BEM_P0); break;
+    }
+#undef BEM_TB_CASE
+#undef BEM_TB
+    return cudaGetLastError();
+}
+
+template <int KIND, int NP, bool MIXED>
+static cudaError_t batch_np(const BatchJob *jobs, int n_jobs, const int64_t *job_end, int basis,
+                            const Rule2D &R, int *status, int grid, cudaStream_t st)
+{
+    if (basis == BEM_P0) {
+        k_batch_p0<KIND, NP, MIXED><<<grid, 256, 0, st>>>(jobs, n_jobs, job_end, R, status);
+    } else {
+        const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP, MIXED);
+        // set once (outside any stream capture: plans issue once before capturing)
+        static bool attr_done = false;
+        if (!attr_done) {
+            cudaError_t e = cudaFuncSetAttribute(k_batch_p1<KIND, NP, MIXED>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            attr_done = true;
+        }
+        k_batch_p1<KIND, NP, MIXED><<<grid, p1_threads(MIXED), sm, st>>>(jobs, n_jobs, job_end, R, status);
+    }
+    return cudaGetLastError();
+}
+
+template <int KIND, bool MIXED>
+static cudaError_t batch_kind(const BatchJob *jobs, int n_jobs, const int64_t *job_end, int basis,
+                              const Rule2D &R, int *status, int grid, cudaStream_t st)
+{
+    switch (R.np) {
+    case 4: return batch_np<KIND, 4, MIXED>(jobs, n_jobs, job_end, basis, R, status, grid, st);
+    case 7: return batch_np<KIND, 7, MIXED>(jobs, n_jobs, job_end, basis, R, status, grid, st);
+    case 9: return batch_np<KIND, 9, MIXED>(jobs, n_jobs, job_end, basis, R, status, grid, st);
+    case 16: return batch_np<KIND, 16, MIXED>(jobs, n_jobs, job_end, basis, R, status, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_block_batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end, int basis,
+                               int kind, int mixed, const Rule2D &R, int *status, int grid,
+                               cudaStream_t st)
+{
+    if (n_jobs <= 0) return cudaSuccess;
+    switch (kind) {
+    case BEM_LAPLACE_SLP:
+        return mixed ? batch_kind<BEM_LAPLACE_SLP, true>(jobs, n_jobs, job_end, basis, R, status, grid, st)
+                     : batch_kind<BEM_LAPLACE_SLP, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
+    case BEM_LAPLACE_DLP:
+        return mixed ? batch_kind<BEM_LAPLACE_DLP, true>(jobs, n_jobs, job_end, basis, R, status, grid, st)
+                     : batch_kind<BEM_LAPLACE_DLP, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
+    default:
+        return batch_kind<BEM_HELMHOLTZ_SLP, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
+    }
 }
 
 }  // namespace bem

@@ -1,0 +1,453 @@
+// Persistent batched driver: a plan gathers many block lists (near-field and
+// coupling jobs of any meshes and kernels), groups them into buckets that
+// share one kernel instantiation (basis, kernel, regular rule, precision; for
+// touching pairs also the case and its order), and issues one launch per
+// bucket: every bucket's kernel drains the tiles of all its jobs.  The launch
+// sequence can be captured once into a CUDA graph and replayed per step, and
+// each bucket's grid can be picked by an autotuner that times candidates on
+// the plan's own data.  This replaces the paper's CPU list building, list
+// size tuning and worker threads (Section 3, Algorithms 1-4) by device-side
+// lists and one graph launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "bem_internal.h"
+
+using namespace bem;
+
+namespace {
+
+struct TouchBucket {
+    int basis, kind, cas, mixed;
+    Rule4D rule;
+    int2 *items = nullptr;
+    int64_t n = 0;
+    std::string name;
+};
+
+struct BlockBucket {
+    int basis, kind, mixed;
+    Rule2D r2;
+    std::vector<BatchJob> host_jobs;
+    BatchJob *jobs = nullptr;
+    int64_t *job_total = nullptr, *job_end = nullptr;
+    int grid_mult = 0;
+    std::string key, name;
+};
+
+}  // namespace
+
+struct bem_plan {
+    int flags = 0;
+    cudaStream_t cap = nullptr;
+    std::vector<void *> allocs;
+    TouchJob *touch_jobs = nullptr;
+    std::vector<TouchBucket> tb;
+    std::vector<BlockBucket> bb;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<bem_prof_rec> prof;   // event pairs recorded around each launch
+    bool prof_outstanding = false;
+};
+
+namespace {
+
+template <class T>
+cudaError_t plan_alloc(bem_plan *p, T **ptr, size_t count)
+{
+    cudaError_t e = cudaMalloc((void **)ptr, std::max<size_t>(1, count) * sizeof(T));
+    if (e == cudaSuccess) p->allocs.push_back(*ptr);
+    return e;
+}
+
+template <class T>
+cudaError_t plan_upload(bem_plan *p, T **ptr, const std::vector<T> &h)
+{
+    cudaError_t e = plan_alloc(p, ptr, h.size());
+    if (e == cudaSuccess && !h.empty())
+        e = cudaMemcpy(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+void plan_free(bem_plan *p)
+{
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (auto &r : p->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (void *a : p->allocs) cudaFree(a);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    delete p;
+}
+
+int default_mult(int basis, int mixed) { return basis == BEM_P0 ? 8 : (mixed ? 4 : 2); }
+
+std::vector<int> candidates(int basis, int mixed)
+{
+    if (basis == BEM_P0) return {4, 8, 16};
+    return mixed ? std::vector<int>{4, 8, 12} : std::vector<int>{1, 2, 3};
+}
+
+// Issues the plan's launches on stream st (profiling events when prof != null).
+// Events recorded while the stream is being captured must be external record
+// nodes, or the graph only uses them for ordering and never records them.
+cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
+                  bool capturing = false)
+{
+    cudaError_t e = cudaSuccess;
+    size_t pi = 0;
+    auto rec = [&](cudaEvent_t ev) {
+        if (capturing) cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+        else cudaEventRecord(ev, st);
+    };
+    auto ev_begin = [&](void) {
+        if (record_prof) rec(p->prof[pi].a);
+    };
+    auto ev_end = [&](void) {
+        if (record_prof) rec(p->prof[pi].b);
+        ++pi;
+    };
+    for (auto &t : p->tb) {
+        ev_begin();
+        e = launch_touching_batch(p->touch_jobs, t.basis, t.kind, t.cas, t.mixed, t.items, t.n, t.rule, st);
+        ev_end();
+        if (e != cudaSuccess) return e;
+    }
+    for (auto &b : p->bb) {
+        ev_begin();
+        e = launch_tile_prefix_batch(b.jobs, (int)b.host_jobs.size(), kTile,
+                                     b.basis == BEM_P0 ? 8 : kTile, b.job_total, b.job_end,
+                                     ctx->status, st);
+        ev_end();
+        if (e != cudaSuccess) return e;
+    }
+    for (auto &b : p->bb) {
+        ev_begin();
+        e = launch_block_batch(b.jobs, (int)b.host_jobs.size(), b.job_end, b.basis, b.kind, b.mixed,
+                               b.r2, ctx->status, ctx->num_sms * b.grid_mult, st);
+        ev_end();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int autotune(bem_ctx *ctx, bem_plan *p)
+{
+    cudaStream_t st = p->cap;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    // prerequisites once: touching tables and tile prefix sums
+    for (auto &t : p->tb)
+        launch_touching_batch(p->touch_jobs, t.basis, t.kind, t.cas, t.mixed, t.items, t.n, t.rule, st);
+    for (auto &bk : p->bb)
+        launch_tile_prefix_batch(bk.jobs, (int)bk.host_jobs.size(), kTile,
+                                 bk.basis == BEM_P0 ? 8 : kTile, bk.job_total, bk.job_end,
+                                 ctx->status, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    for (auto &bk : p->bb) {
+        if (e != cudaSuccess) break;
+        auto it = ctx->tuned.find(bk.key);
+        if (it != ctx->tuned.end()) {
+            bk.grid_mult = it->second;
+            continue;
+        }
+        float best = 1e30f;
+        int best_m = bk.grid_mult;
+        for (int mult : candidates(bk.basis, bk.mixed)) {
+            float t_min = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(a, st);
+                e = launch_block_batch(bk.jobs, (int)bk.host_jobs.size(), bk.job_end, bk.basis,
+                                       bk.kind, bk.mixed, bk.r2, ctx->status, ctx->num_sms * mult, st);
+                cudaEventRecord(b, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                if (e != cudaSuccess) break;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, a, b);
+                t_min = std::min(t_min, ms);
+            }
+            if (e != cudaSuccess) break;
+            if (t_min < best) {
+                best = t_min;
+                best_m = mult;
+            }
+        }
+        bk.grid_mult = best_m;
+        ctx->tuned[bk.key] = best_m;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "autotune");
+    return BEM_OK;
+}
+
+}  // namespace
+
+namespace bem {
+
+void plan_drain_profile(bem_ctx *ctx)
+{
+    for (bem_plan *p : ctx->prof_plans) {
+        if (!p->prof_outstanding || p->prof.empty()) continue;
+        cudaEventSynchronize(p->prof.back().b);
+        for (auto &r : p->prof) prof_accumulate(ctx, r);
+        p->prof_outstanding = false;
+    }
+    ctx->prof_plans.clear();
+}
+
+void plan_forget(bem_ctx *ctx) { ctx->prof_plans.clear(); }
+
+}  // namespace bem
+
+extern "C" {
+
+int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near,
+                    const bem_block_job *coupling_jobs, int32_t n_coupling, int32_t flags,
+                    bem_plan **out)
+{
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (!out || n_near < 0 || n_coupling < 0 || (n_near > 0 && !near_jobs) ||
+        (n_coupling > 0 && !coupling_jobs))
+        return api_fail(ctx, BEM_ERR_INVALID_ARG, "bad plan arguments");
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    bem_plan *p = new bem_plan();
+    p->flags = flags;
+    cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        plan_free(p);
+        return api_cuda_fail(ctx, e, "cudaStreamCreate");
+    }
+
+    struct JobInfo {
+        const bem_block_job *J;
+        Mesh *m;
+        Rule2D r2;
+        bool near;
+        int touch_job;   // index into touch_jobs (near jobs), -1 otherwise
+    };
+    std::vector<JobInfo> jobs;
+    for (int k = 0; k < n_near + n_coupling; ++k) {
+        const bem_block_job &J = k < n_near ? near_jobs[k] : coupling_jobs[k - n_near];
+        JobInfo ji;
+        ji.J = &J;
+        ji.near = k < n_near;
+        ji.touch_job = -1;
+        int rc = api_check_job(ctx, J, ji.r2, &ji.m);
+        if (rc) {
+            plan_free(p);
+            return rc;
+        }
+        jobs.push_back(ji);
+    }
+
+    // touching work of the near jobs: one table per job, items bucketed
+    std::vector<TouchJob> tj;
+    std::map<std::tuple<int, int, int, int, int>, std::vector<int2>> titems;   // basis,kind,case,mixed,q
+    for (auto &ji : jobs) {
+        if (!ji.near || ji.J->n_blocks == 0) continue;
+        const MeshView &mv = ji.m->v;
+        const size_t per = mv.basis == BEM_P0 ? 1 : 9;
+        double2 *table = nullptr;
+        if ((e = plan_alloc(p, &table, (size_t)mv.ntouch * per)) != cudaSuccess) {
+            plan_free(p);
+            return api_cuda_fail(ctx, e, "cudaMalloc(plan touching table)");
+        }
+        TouchJob t;
+        t.m = mv;
+        t.m.table = table;
+        t.kappa = ji.J->kernel.kappa;
+        ji.touch_job = (int)tj.size();
+        tj.push_back(t);
+        const int mixed = ji.J->quad.precision == BEM_MIXED;
+        const int qs[4] = {0, ji.J->quad.q_vertex, ji.J->quad.q_edge, ji.J->quad.q_identical};
+        for (int c = kVertex; c <= kIdentical; ++c) {
+            auto &v = titems[std::make_tuple(mv.basis, ji.J->kernel.kind, c,
+                                             (c == kVertex) ? mixed : 0, qs[c])];
+            for (int idx : ji.m->hlist[c]) v.push_back(make_int2(ji.touch_job, idx));
+        }
+    }
+    if ((e = plan_upload(p, &p->touch_jobs, tj)) != cudaSuccess) {
+        plan_free(p);
+        return api_cuda_fail(ctx, e, "plan upload");
+    }
+    static const char *cname[4] = {"", "vertex", "edge", "identical"};
+    for (auto &kv : titems) {
+        if (kv.second.empty()) continue;
+        TouchBucket t;
+        std::tie(t.basis, t.kind, t.cas, t.mixed, std::ignore) = kv.first;
+        const int q = std::get<4>(kv.first);
+        int rc = api_get_rule4(ctx, t.cas, 0, q, t.rule);
+        if (rc) {
+            plan_free(p);
+            return rc;
+        }
+        t.n = (int64_t)kv.second.size();
+        if ((e = plan_upload(p, &t.items, kv.second)) != cudaSuccess) {
+            plan_free(p);
+            return api_cuda_fail(ctx, e, "plan upload");
+        }
+        t.name = std::string("touching_") + cname[t.cas];
+        p->tb.push_back(t);
+    }
+
+    // block buckets
+    std::map<std::string, int> bindex;
+    for (auto &ji : jobs) {
+        const bem_block_job &J = *ji.J;
+        if (J.n_blocks == 0) continue;
+        const int mixed = J.quad.precision == BEM_MIXED && J.kernel.kind != BEM_HELMHOLTZ_SLP;
+        char key[96];
+        std::snprintf(key, sizeof key, "b%d k%d np%d m%d r%d q%d", ji.m->v.basis, J.kernel.kind,
+                      ji.r2.np, mixed, J.quad.regular_rule, J.quad.q_regular);
+        auto it = bindex.find(key);
+        if (it == bindex.end()) {
+            BlockBucket b;
+            b.basis = ji.m->v.basis;
+            b.kind = J.kernel.kind;
+            b.mixed = mixed;
+            b.r2 = ji.r2;
+            b.key = key;
+            b.name = b.basis == BEM_P0 ? "block_p0" : "block_p1";
+            b.grid_mult = default_mult(b.basis, mixed);
+            bindex[key] = (int)p->bb.size();
+            p->bb.push_back(b);
+            it = bindex.find(key);
+        }
+        BlockBucket &b = p->bb[it->second];
+        BatchJob bj;
+        bj.m = ji.m->v;
+        bj.m.table = ji.touch_job >= 0 ? tj[ji.touch_job].m.table : nullptr;
+        BlockLaunch &L = bj.L;
+        L.row_ptr = J.row_ptr;
+        L.row_idx = J.row_idx;
+        L.col_ptr = J.col_ptr;
+        L.col_idx = J.col_idx;
+        L.n_row_clusters = J.n_row_clusters;
+        L.n_col_clusters = J.n_col_clusters;
+        L.blk_row = J.blk_row;
+        L.blk_col = J.blk_col;
+        L.blk_off = J.blk_off;
+        L.n_blocks = J.n_blocks;
+        L.out = J.out;
+        L.kind = J.kernel.kind;
+        L.kappa = J.kernel.kappa;
+        L.lower_only = 0;
+        L.allow_touching = ji.near ? 1 : 0;
+        L.mixed = mixed;
+        int64_t *prefix = nullptr;
+        if ((e = plan_alloc(p, &prefix, (size_t)J.n_blocks)) != cudaSuccess) {
+            plan_free(p);
+            return api_cuda_fail(ctx, e, "cudaMalloc(plan prefix)");
+        }
+        bj.prefix = prefix;
+        b.host_jobs.push_back(bj);
+    }
+    for (auto &b : p->bb) {
+        const size_t nj = b.host_jobs.size();
+        if ((e = plan_upload(p, &b.jobs, b.host_jobs)) != cudaSuccess ||
+            (e = plan_alloc(p, &b.job_total, nj)) != cudaSuccess ||
+            (e = plan_alloc(p, &b.job_end, nj)) != cudaSuccess) {
+            plan_free(p);
+            return api_cuda_fail(ctx, e, "plan upload");
+        }
+    }
+    // profiling events: one pair per launch of issue()
+    const size_t nlaunch = p->tb.size() + 2 * p->bb.size();
+    for (size_t k = 0; k < nlaunch; ++k) {
+        bem_prof_rec r;
+        cudaEventCreate(&r.a);
+        cudaEventCreate(&r.b);
+        if (k < p->tb.size()) r.name = p->tb[k].name;
+        else if (k < p->tb.size() + p->bb.size()) r.name = "tile_prefix";
+        else r.name = p->bb[k - p->tb.size() - p->bb.size()].name;
+        p->prof.push_back(r);
+    }
+
+    if (flags & BEM_PLAN_AUTOTUNE) {
+        int rc = autotune(ctx, p);
+        if (rc) {
+            plan_free(p);
+            return rc;
+        }
+    } else {
+        // one direct issue sets the kernels' shared-memory attributes before any capture
+        e = issue(ctx, p, p->cap, false);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->cap);
+        if (e != cudaSuccess) {
+            plan_free(p);
+            return api_cuda_fail(ctx, e, "plan warm-up");
+        }
+    }
+    if (flags & BEM_PLAN_GRAPH) {
+        e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = issue(ctx, p, p->cap, (flags & BEM_PLAN_PROFILE) != 0, true);
+            e = cudaStreamEndCapture(p->cap, &p->graph);
+            if (e2 != cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+        if (e != cudaSuccess) {
+            plan_free(p);
+            return api_cuda_fail(ctx, e, "graph capture");
+        }
+    }
+    *out = p;
+    return BEM_OK;
+}
+
+int bem_plan_run(bem_ctx *ctx, bem_plan *p)
+{
+    if (!ctx || !p) return BEM_ERR_INVALID_ARG;
+    const bool prof = (p->flags & BEM_PLAN_PROFILE) && ctx->profile && !p->prof.empty();
+    if (p->prof_outstanding && !p->prof.empty()) {
+        // the previous run's launch times are added before the events are reused
+        cudaEventSynchronize(p->prof.back().b);
+        for (auto &r : p->prof) prof_accumulate(ctx, r);
+        p->prof_outstanding = false;
+    }
+    cudaError_t e;
+    if (p->exec) e = cudaGraphLaunch(p->exec, ctx->stream);
+    else e = issue(ctx, p, ctx->stream, prof);
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "plan run");
+    if (prof) {
+        p->prof_outstanding = true;
+        if (std::find(ctx->prof_plans.begin(), ctx->prof_plans.end(), p) == ctx->prof_plans.end())
+            ctx->prof_plans.push_back(p);
+    }
+    return BEM_OK;
+}
+
+int bem_plan_destroy(bem_ctx *ctx, bem_plan *p)
+{
+    if (!ctx || !p) return BEM_ERR_INVALID_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    cudaStreamSynchronize(p->cap);
+    ctx->prof_plans.erase(std::remove(ctx->prof_plans.begin(), ctx->prof_plans.end(), p),
+                          ctx->prof_plans.end());
+    plan_free(p);
+    return BEM_OK;
+}
+
+int bem_plan_info(bem_ctx *ctx, bem_plan *p, int32_t *n_touch_launches, int32_t *n_block_launches,
+                  int32_t *grid_mult, int32_t cap)
+{
+    if (!ctx || !p) return BEM_ERR_INVALID_ARG;
+    if (n_touch_launches) *n_touch_launches = (int32_t)p->tb.size();
+    if (n_block_launches) *n_block_launches = (int32_t)p->bb.size();
+    for (int k = 0; grid_mult && k < cap && k < (int)p->bb.size(); ++k) grid_mult[k] = p->bb[k].grid_mult;
+    return BEM_OK;
+}
+
+}  // extern "C"

@@ -6,14 +6,14 @@ seeded pivot subsets).  It contains none of the quadrature arithmetic of the
 method: no rules, no kernels, no integrals.
 """
 from .rng import SplitMix64
-from .meshes import (Mesh, icosphere, octasphere, cube_surface, torus,
+from .meshes import (Mesh, icosphere, icosphere_n, octasphere, cube_surface, torus,
                      jitter, icosahedron, octahedron, two_triangles,
                      mean_edge_length)
 from . import workloads
 from .structure import (ClusterTree, build_cluster_tree, build_block_partition,
                         seeded_pivots, BlockPartition)
 
-__all__ = ["SplitMix64", "Mesh", "icosphere", "octasphere", "cube_surface",
+__all__ = ["SplitMix64", "Mesh", "icosphere", "icosphere_n", "octasphere", "cube_surface",
            "torus", "jitter", "icosahedron", "octahedron", "two_triangles",
            "mean_edge_length", "ClusterTree", "build_cluster_tree",
            "build_block_partition", "seeded_pivots", "BlockPartition", "workloads"]

@@ -132,6 +132,46 @@ def octasphere(n: int) -> Mesh:
     return Mesh(verts, _orient_outward(verts, tris, lambda c: 0.0 * c), f"octasphere{n}")
 
 
+def subdivided_sphere(base: Mesh, n: int, name: str) -> Mesh:
+    """Each face of a convex polyhedron inscribed in the unit sphere split
+    regularly into n^2 triangles, vertices projected to the unit sphere."""
+    index = {}
+    verts = []
+
+    def vid(key, p):
+        if key not in index:
+            index[key] = len(verts)
+            verts.append(p / np.linalg.norm(p))
+        return index[key]
+
+    def key_of(face, i, j):
+        # a point (i, j, n-i-j) on a face, made canonical across shared edges by
+        # its exact barycentric weights on the sorted vertex ids
+        a, b, c = face
+        w = {a: n - i - j, b: i, c: j}
+        return tuple(sorted((v, k) for v, k in w.items() if k > 0))
+
+    tris = []
+    for face in base.tris:
+        A, B, C = (base.verts[v] for v in face)
+
+        def P(i, j):
+            return vid(key_of(face, i, j), (A * (n - i - j) + B * i + C * j) / n)
+        for i in range(n):
+            for j in range(n - i):
+                tris.append((P(i, j), P(i + 1, j), P(i, j + 1)))
+                if i + j + 1 < n:
+                    tris.append((P(i + 1, j), P(i + 1, j + 1), P(i, j + 1)))
+    verts = np.array(verts, dtype=np.float64)
+    tris = np.array(tris, dtype=np.int32)
+    return Mesh(verts, _orient_outward(verts, tris, lambda c: 0.0 * c), name)
+
+
+def icosphere_n(n: int) -> Mesh:
+    """Icosahedron with every face split into n^2 triangles (20 n^2 triangles)."""
+    return subdivided_sphere(icosahedron(), n, f"icosphere_n{n}")
+
+
 def cube_surface(n: int) -> Mesh:
     index = {}
     verts = []

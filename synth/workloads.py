@@ -111,3 +111,67 @@ def config2(levels: int = 5) -> Workload:
                     near=near, far=far,
                     meta={"leaf_size": 32, "eta": 2.0, "rank": 16,
                           "n_near_blocks": len(near.blk_row), "n_far_blocks": len(far.blk_row)})
+
+
+@dataclass
+class BatchItem:
+    """One mesh of a batched workload with its operators and block sets."""
+    mesh: meshes.Mesh
+    operators: list
+    near: BlockSet
+    far: BlockSet
+
+
+@dataclass
+class BatchWorkload:
+    name: str
+    basis: str
+    quad: Quad
+    items: list
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_entries(self):
+        return sum(len(it.operators) * (it.near.n_entries + it.far.n_entries) for it in self.items)
+
+
+def _nearest(target, sizes):
+    """(n, size) minimising |log size - log target| over the candidates."""
+    best = min(sizes, key=lambda ns: abs(np.log(ns[1]) - np.log(target)))
+    return best
+
+
+def config4(count: int = 48, lo: float = 500.0, hi: float = 30000.0, leaf_size: int = 32,
+            eta: float = 2.0, rank: int = 16) -> BatchWorkload:
+    """48 closed meshes of uneven size (16 spheres, 16 cubes, 16 tori with radii
+    1 and 0.3), target sizes log-uniform in [500, 30000] triangles (seeded),
+    jitter 5%; per mesh the Laplace double layer and the Helmholtz single layer
+    with kappa ~ U[1, 10]; P0, H2 blocks (leaf 32, eta 2, <= 16 pivots)."""
+    from .rng import SplitMix64
+    rng = SplitMix64(seed(4))
+    targets = np.exp(rng.uniform(count, np.log(lo), np.log(hi)))
+    kappas = rng.uniform(count, 1.0, 10.0)
+    items = []
+    for k in range(count):
+        kind = ("sphere", "cube", "torus")[k % 3]
+        t = targets[k]
+        if kind == "sphere":
+            n, _ = _nearest(t, [(n, 20 * n * n) for n in range(3, 40)])
+            mesh = meshes.icosphere_n(n)
+        elif kind == "cube":
+            n, _ = _nearest(t, [(n, 12 * n * n) for n in range(3, 51)])
+            mesh = meshes.cube_surface(n)
+        else:
+            cands = []
+            for nv_ in range(4, 60):
+                nu_ = max(6, int(round(3.3 * nv_)))
+                cands.append(((nu_, nv_), 2 * nu_ * nv_))
+            (nu_, nv_), _ = _nearest(t, cands)
+            mesh = meshes.torus(nu_, nv_)
+        mesh = meshes.jitter(mesh, 0.05, seed(4, k))
+        _, near, far = h2_blocks(mesh, "p0", leaf_size, eta, rank, seed(4, 100 + k))
+        items.append(BatchItem(mesh, [Operator("laplace_dlp"),
+                                      Operator("helmholtz_slp", float(kappas[k]))], near, far))
+    return BatchWorkload(f"C4 {count} meshes (spheres/cubes/tori) laplace_dlp+helmholtz_slp p0 h2",
+                         "p0", Quad(3, "duffy", 5, 5, 5), items,
+                         meta={"triangles": int(sum(it.mesh.nt for it in items))})

@@ -46,6 +46,19 @@ def oracle_absolute(mesh, basis, rows, cols, kernel, kappa, quad):
                                    basis=basis, **quad)
 
 
+def sample_block_entries(bs, n_blocks, rng):
+    """Output positions of every entry of n_blocks seeded random blocks of a
+    block set (whole blocks, so each row's scale is that of its block row)."""
+    nb = len(bs.blk_row)
+    picks = np.unique(rng.integers(min(n_blocks, nb), nb))
+    pos = []
+    for b in picks:
+        t, s = bs.blk_row[b], bs.blk_col[b]
+        n = (bs.row_ptr[t + 1] - bs.row_ptr[t]) * (bs.col_ptr[s + 1] - bs.col_ptr[s])
+        pos.append(bs.blk_off[b] + np.arange(n))
+    return np.concatenate(pos) if pos else np.zeros(0, np.int64)
+
+
 def to_dev(a, dtype):
     import torch
     return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)

@@ -1,0 +1,142 @@
+"""Persistent batched driver (bem_plan_*): one launch per kernel bucket over
+many meshes and kernels, optionally captured in a CUDA graph and autotuned.
+Its results must equal those of the per-job calls bit for bit (the same tile
+bodies run in both), and sampled entries must match the oracle."""
+import numpy as np
+import pytest
+
+import synth
+from parity_util import block_job, oracle_entries, rel_err, sample_block_entries
+
+pytestmark = pytest.mark.gpu
+
+QUAD = dict(q_regular=3, regular_rule="duffy", q_identical=5, q_edge=5, q_vertex=5)
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1510_07244_gb300 as pkg
+    ctx = pkg.Context(0)
+    yield pkg, ctx
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    return synth.workloads.config4(count=6, lo=200.0, hi=1200.0, leaf_size=16, eta=2.0, rank=6)
+
+
+def _jobs(pkg, ctx, w, precision):
+    import torch
+    mids, near, far, outs = [], [], [], []
+    q = dict(QUAD, precision=precision)
+    for it in w.items:
+        mid = ctx.bem_mesh_upload(it.mesh.verts, it.mesh.tris, w.basis)
+        mids.append(mid)
+        for op in it.operators:
+            dt = torch.complex128 if op.kernel == "helmholtz_slp" else torch.float64
+            on = torch.full((max(1, it.near.n_entries),), float("nan"), dtype=dt, device="cuda")
+            of = torch.full((max(1, it.far.n_entries),), float("nan"), dtype=dt, device="cuda")
+            near.append(block_job(pkg, mid, it.near, op.kernel, op.kappa, q, on))
+            far.append(block_job(pkg, mid, it.far, op.kernel, op.kappa, q, of))
+            outs.append((it, op, on, of))
+    return mids, near, far, outs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("flags", [0, 1, 3, 7])
+def test_plan_equals_per_job_calls(env, small_batch, precision, flags):
+    pkg, ctx = env
+    mids, near, far, outs = _jobs(pkg, ctx, small_batch, precision)
+    for j in near:
+        ctx.bem_near_field([j])
+    for j in far:
+        ctx.bem_coupling_blocks([j])
+    ctx.bem_sync()
+    ref = [(on.clone(), of.clone()) for _, _, on, of in outs]
+    for _, _, on, of in outs:
+        on.fill_(float("nan"))
+        of.fill_(float("nan"))
+    plan = ctx.bem_plan_create(near, far, flags)
+    ctx.bem_plan_run(plan)
+    ctx.bem_plan_run(plan)
+    ctx.bem_sync()
+    info = ctx.bem_plan_info(plan)
+    # one launch per (kernel, precision) bucket: far fewer than one per job
+    assert info["block_launches"] <= 2 < len(near) + len(far)
+    for (r_on, r_of), (_, _, on, of) in zip(ref, outs):
+        assert torch_equal(on, r_on) and torch_equal(of, r_of)
+    ctx.bem_plan_destroy(plan)
+    for m in mids:
+        ctx.bem_mesh_free(m)
+
+
+def torch_equal(a, b):
+    import torch
+    return bool(torch.equal(a, b))
+
+
+def test_plan_matches_oracle(env, small_batch):
+    pkg, ctx = env
+    mids, near, far, outs = _jobs(pkg, ctx, small_batch, "fp64")
+    plan = ctx.bem_plan_create(near, far, 3)
+    ctx.bem_plan_run(plan)
+    ctx.bem_sync()
+    rng = synth.SplitMix64(17)
+    for it, op, on, of in outs:
+        for bs, out in ((it.near, on), (it.far, of)):
+            if bs.n_entries == 0:
+                continue
+            r, c = bs.entry_indices()
+            pick = sample_block_entries(bs, 12, rng)
+            got = out.cpu().numpy()[pick]
+            ref = oracle_entries(it.mesh, "p0", r[pick], c[pick], op.kernel, op.kappa, QUAD)
+            assert rel_err(got, ref, r[pick]).max() <= 1e-10
+    ctx.bem_plan_destroy(plan)
+    for m in mids:
+        ctx.bem_mesh_free(m)
+
+
+def test_plan_p1_and_profile(env):
+    """Piecewise-linear jobs of two meshes in one plan; the launch profile
+    counts every bucket launch of every run."""
+    import torch
+    pkg, ctx = env
+    jobs_n, jobs_f, outs, mids = [], [], [], []
+    for lv, seed in ((2, 3), (3, 4)):
+        mesh = synth.jitter(synth.icosphere(lv), 0.05, seed)
+        _, near, far = synth.workloads.h2_blocks(mesh, "p1", 16, 2.0, 6, seed)
+        mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p1")
+        mids.append(mid)
+        for kernel in ("laplace_slp", "laplace_dlp"):
+            on = torch.zeros(max(1, near.n_entries), dtype=torch.float64, device="cuda")
+            of = torch.zeros(max(1, far.n_entries), dtype=torch.float64, device="cuda")
+            jobs_n.append(block_job(pkg, mid, near, kernel, 0.0, QUAD, on))
+            jobs_f.append(block_job(pkg, mid, far, kernel, 0.0, QUAD, of))
+            outs.append((on, of))
+    for j in jobs_n:
+        ctx.bem_near_field([j])
+    for j in jobs_f:
+        ctx.bem_coupling_blocks([j])
+    ctx.bem_sync()
+    ref = [(a.clone(), b.clone()) for a, b in outs]
+    plan = ctx.bem_plan_create(jobs_n, jobs_f, 7)
+    ctx.bem_profile_reset()
+    ctx.bem_profile_enable(True)
+    for _ in range(3):
+        ctx.bem_plan_run(plan)
+    prof = ctx.bem_profile_read()
+    ctx.bem_profile_enable(False)
+    for (ra, rb), (a, b) in zip(ref, outs):
+        assert torch.equal(a, ra) and torch.equal(b, rb)
+    info = ctx.bem_plan_info(plan)
+    assert prof["block_p1"][0] == 3 * info["block_launches"]
+    assert all(v[1] > 0 for v in prof.values())
+    ctx.bem_plan_destroy(plan)
+    for m in mids:
+        ctx.bem_mesh_free(m)
