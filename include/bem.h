@@ -77,7 +77,12 @@ typedef struct {
  *                 vertex differences and double-layer heights, compensated
  *                 sums); identical and common-edge pairs, Helmholtz pairs and
  *                 bem_pivot_entries stay FP64.
- *   order_mode:   BEM_ORDER_FIXED (the orders above) or BEM_ORDER_LEARNED. */
+ *   order_mode:   BEM_ORDER_FIXED (the orders above) or BEM_ORDER_LEARNED: for
+ *                 bem_near_field on piecewise-constant meshes, every disjoint
+ *                 pair gets the rule class the context's order model
+ *                 (bem_set_order_model) predicts; touching pairs keep the
+ *                 fixed singular orders above.  Such a call reads one value
+ *                 back from the device to size its scratch (it synchronises). */
 typedef struct {
     int32_t q_regular;
     int32_t regular_rule;
@@ -175,7 +180,9 @@ int bem_near_field(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs);
 int bem_coupling_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs);
 
 /* Arbitrary entries (pivot rows / columns, Section 2.3-2.4):
- * out[k] = g_{rows[k], cols[k]} for k < n.  rows, cols, out: device arrays. */
+ * out[k] = g_{rows[k], cols[k]} for k < n.  rows, cols, out: device arrays.
+ * Here the regular rule may be any Duffy order 1..20 (the block calls take
+ * Duffy 2..4 or TRI7). */
 int bem_pivot_entries(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
                       const bem_quad_desc *quad, const int32_t *rows, const int32_t *cols,
                       int64_t n, void *out);
@@ -185,6 +192,59 @@ int bem_pivot_entries(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kern
  * layer is symmetric, Section 4); the rest of `out` is not touched. */
 int bem_assemble_dense(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
                        const bem_quad_desc *quad, int32_t lower_only, void *out);
+
+/* Sum of the magnitudes of the quadrature terms of each requested entry,
+ * A_k = sum over pairs sqrt(g_a g_b)/(4 pi) sum_p |w_p phi psi k|, with the
+ * same rules as bem_pivot_entries (real double output for every kernel).
+ * A_k bounds the rounding error of any floating-point evaluation of the
+ * entry's sum (up to a multiple of the unit roundoff); it is the error scale
+ * used to label rule classes for the order model. */
+int bem_pivot_entries_absolute(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
+                               const bem_quad_desc *quad, const int32_t *rows, const int32_t *cols,
+                               int64_t n, double *out);
+
+/* ---- learned quadrature orders ----------------------------------------------
+ * The paper fixes one rule per case (Section 2.2; Section 4 compares fixed
+ * orders 3/5 and 4/6).  The order model is a small multilayer perceptron,
+ * 8 pair features -> 64 -> 64 -> 6 classes (ReLU), that predicts, for a
+ * disjoint pair, the cheapest of six rules meeting an error target, on a
+ * ladder of increasing accuracy and cost:
+ *   class 0: Duffy q=2 (16 points)  1: Radon 7x7 (49)   2: Duffy q=4 (256)
+ *   class 3: Duffy q=5 (625)        4: Duffy q=6 (1296) 5: Duffy q=8 (4096).
+ * Features (bem_pair_features, normalised by the model's mean / std):
+ * log2 centroid distance / D, log2 closest-vertex distance / D, cos of the
+ * normals' angle, log2 area ratio, test centroid height above the trial
+ * plane / distance, kernel id / 2, kappa D, log2 aspect ratio; D = larger
+ * triangle diameter.  Training runs on the device (FP32 forward, backward
+ * and Adam, deterministic); inference uses BF16 weights on the tensor cores.
+ * Parameters: W1[64][8] b1[64] W2[64][64] b2[64] W3[6][64] b3[6] (floats);
+ * normalisation: mean[8] then 1/std[8]. All X / y / grads / logits pointers
+ * are device arrays (X: n x 8 floats row-major, y: n int32 classes). */
+typedef struct bem_mlp bem_mlp;
+int bem_mlp_create(bem_ctx *ctx, uint64_t seed, bem_mlp **mlp);
+int bem_mlp_destroy(bem_ctx *ctx, bem_mlp *mlp);
+int bem_mlp_num_params(void);
+int bem_mlp_set_params(bem_ctx *ctx, bem_mlp *mlp, const float *host_params, const float *host_norm);
+int bem_mlp_get_params(bem_ctx *ctx, bem_mlp *mlp, float *host_params, float *host_norm);
+/* gradients of the mean cross-entropy over the n rows (grads: device, num_params floats) */
+int bem_mlp_gradients(bem_ctx *ctx, bem_mlp *mlp, const float *X, const int32_t *y, int32_t n,
+                      float *grads, float *loss);
+/* one Adam step (beta 0.9 / 0.999) on the n rows; loss = mean loss before the step */
+int bem_mlp_train_step(bem_ctx *ctx, bem_mlp *mlp, const float *X, const int32_t *y, int32_t n,
+                       float lr, float *loss);
+/* logits (n x 6, device) of the BF16 tensor-core inference */
+int bem_mlp_infer(bem_ctx *ctx, bem_mlp *mlp, const float *X, int64_t n, float *logits);
+/* features of pairs (a[k], b[k]) of a piecewise-constant mesh (normalised by the
+ * model when mlp != NULL, raw otherwise) */
+int bem_pair_features(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel, bem_mlp *mlp,
+                      const int32_t *a, const int32_t *b, int64_t n, float *X);
+/* model used by BEM_ORDER_LEARNED calls (NULL to clear); every disjoint pair
+ * gets the cheapest class whose cumulative predicted probability (classes 0..c)
+ * reaches `confidence`, so an uncertain prediction moves up the ladder (the
+ * most accurate class is the fallback).  The model must outlive the calls. */
+int bem_set_order_model(bem_ctx *ctx, bem_mlp *mlp, float confidence);
+/* number of disjoint pairs per class of the last BEM_ORDER_LEARNED job */
+int bem_learned_counts(bem_ctx *ctx, int64_t *counts /* [6] */);
 
 /* ---- persistent batched driver ---------------------------------------------
  * A plan replaces the paper's CPU-side list machinery (Section 3, Algorithms

@@ -27,7 +27,12 @@ EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_
            "bem_mesh_free", "bem_mesh_info", "bem_near_field", "bem_coupling_blocks",
            "bem_pivot_entries", "bem_assemble_dense", "bem_profile_enable",
            "bem_profile_reset", "bem_profile_read", "bem_near_field_noalloc", "bem_rule_points",
-           "bem_plan_create", "bem_plan_run", "bem_plan_destroy", "bem_plan_info"]
+           "bem_plan_create", "bem_plan_run", "bem_plan_destroy", "bem_plan_info",
+           "bem_pivot_entries_absolute", "bem_mlp_create", "bem_mlp_destroy", "bem_mlp_num_params",
+           "bem_mlp_set_params", "bem_mlp_get_params", "bem_mlp_gradients", "bem_mlp_train_step",
+           "bem_mlp_infer", "bem_pair_features", "bem_set_order_model", "bem_learned_counts"]
+ORDER_CLASSES = [("duffy", 2), ("tri7", 1), ("duffy", 4), ("duffy", 5), ("duffy", 6), ("duffy", 8)]
+ORDER_CLASS_POINTS = [16, 49, 256, 625, 1296, 4096]
 PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE = 1, 2, 4
 
 
@@ -101,6 +106,21 @@ def load():
     lib.bem_assemble_dense.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc),
                                        P(bem_quad_desc), ctypes.c_int32, _vp]
     lib.bem_near_field_noalloc.argtypes = [_vp, P(bem_block_job)]
+    lib.bem_pivot_entries_absolute.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc),
+                                               P(bem_quad_desc), _vp, _vp, ctypes.c_int64, _vp]
+    lib.bem_mlp_create.argtypes = [_vp, ctypes.c_uint64, P(_vp)]
+    lib.bem_mlp_destroy.argtypes = [_vp, _vp]
+    lib.bem_mlp_num_params.argtypes = []
+    lib.bem_mlp_set_params.argtypes = [_vp, _vp, _vp, _vp]
+    lib.bem_mlp_get_params.argtypes = [_vp, _vp, _vp, _vp]
+    lib.bem_mlp_gradients.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, _vp, P(ctypes.c_float)]
+    lib.bem_mlp_train_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_float,
+                                       P(ctypes.c_float)]
+    lib.bem_mlp_infer.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp]
+    lib.bem_pair_features.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc), _vp, _vp, _vp,
+                                      ctypes.c_int64, _vp]
+    lib.bem_set_order_model.argtypes = [_vp, _vp, ctypes.c_float]
+    lib.bem_learned_counts.argtypes = [_vp, P(ctypes.c_int64)]
     lib.bem_plan_create.argtypes = [_vp, P(bem_block_job), ctypes.c_int32, P(bem_block_job),
                                     ctypes.c_int32, ctypes.c_int32, P(_vp)]
     lib.bem_plan_run.argtypes = [_vp, _vp]
@@ -315,3 +335,76 @@ class Context:
         self._check(self.lib.bem_plan_info(self.h, plan, ctypes.byref(nt), ctypes.byref(nb), g, 64))
         return {"touch_launches": nt.value, "block_launches": nb.value,
                 "grid_mult": [g[k] for k in range(min(64, nb.value))]}
+
+    # ---- pivots (absolute sums) and the order model --------------------------
+    def bem_pivot_entries_absolute(self, mesh_id, kernel, quad, rows, cols, out):
+        import torch
+        _check_dev(rows, torch.int32, "rows")
+        _check_dev(cols, torch.int32, "cols")
+        _check_dev(out, torch.float64, "out")
+        self._check(self.lib.bem_pivot_entries_absolute(self.h, mesh_id, ctypes.byref(kernel),
+                                                        ctypes.byref(quad), _ptr(rows), _ptr(cols),
+                                                        rows.numel(), _ptr(out)))
+
+    def bem_mlp_create(self, seed=0):
+        h = ctypes.c_void_p()
+        self._check(self.lib.bem_mlp_create(self.h, ctypes.c_uint64(seed), ctypes.byref(h)))
+        return h
+
+    def bem_mlp_destroy(self, mlp):
+        self._check(self.lib.bem_mlp_destroy(self.h, mlp))
+
+    def bem_mlp_num_params(self):
+        return int(self.lib.bem_mlp_num_params())
+
+    def bem_mlp_set_params(self, mlp, params=None, norm=None):
+        p = None if params is None else np.ascontiguousarray(params, np.float32)
+        q = None if norm is None else np.ascontiguousarray(norm, np.float32)
+        self._check(self.lib.bem_mlp_set_params(self.h, mlp, None if p is None else p.ctypes.data_as(_vp),
+                                                None if q is None else q.ctypes.data_as(_vp)))
+
+    def bem_mlp_get_params(self, mlp):
+        p = np.zeros(self.bem_mlp_num_params(), np.float32)
+        q = np.zeros(16, np.float32)
+        self._check(self.lib.bem_mlp_get_params(self.h, mlp, p.ctypes.data_as(_vp), q.ctypes.data_as(_vp)))
+        return p, q
+
+    def bem_mlp_gradients(self, mlp, X, y, grads=None):
+        import torch
+        _check_dev(X, torch.float32, "X")
+        _check_dev(y, torch.int32, "y")
+        loss = ctypes.c_float(0.0)
+        self._check(self.lib.bem_mlp_gradients(self.h, mlp, _ptr(X), _ptr(y), y.numel(), _ptr(grads),
+                                               ctypes.byref(loss)))
+        return loss.value
+
+    def bem_mlp_train_step(self, mlp, X, y, lr):
+        import torch
+        _check_dev(X, torch.float32, "X")
+        _check_dev(y, torch.int32, "y")
+        loss = ctypes.c_float(0.0)
+        self._check(self.lib.bem_mlp_train_step(self.h, mlp, _ptr(X), _ptr(y), y.numel(),
+                                                ctypes.c_float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def bem_mlp_infer(self, mlp, X, logits):
+        import torch
+        _check_dev(X, torch.float32, "X")
+        _check_dev(logits, torch.float32, "logits")
+        self._check(self.lib.bem_mlp_infer(self.h, mlp, _ptr(X), X.shape[0], _ptr(logits)))
+
+    def bem_pair_features(self, mesh_id, kernel, mlp, a, b, X):
+        import torch
+        _check_dev(a, torch.int32, "a")
+        _check_dev(b, torch.int32, "b")
+        _check_dev(X, torch.float32, "X")
+        self._check(self.lib.bem_pair_features(self.h, mesh_id, ctypes.byref(kernel), mlp, _ptr(a),
+                                               _ptr(b), a.numel(), _ptr(X)))
+
+    def bem_set_order_model(self, mlp, confidence=0.9):
+        self._check(self.lib.bem_set_order_model(self.h, mlp, ctypes.c_float(confidence)))
+
+    def bem_learned_counts(self):
+        c = (ctypes.c_int64 * 6)()
+        self._check(self.lib.bem_learned_counts(self.h, c))
+        return [int(v) for v in c]

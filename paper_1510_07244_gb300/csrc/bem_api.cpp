@@ -140,15 +140,22 @@ Mesh *get_mesh(bem_ctx *ctx, int id)
     return it == ctx->meshes.end() ? nullptr : it->second;
 }
 
-int check_quad(bem_ctx *ctx, const bem_quad_desc *q, Rule2D &r2)
+int check_quad(bem_ctx *ctx, const bem_quad_desc *q, Rule2D &r2, bool block_rule = true)
 {
     if (!q) return fail(ctx, BEM_ERR_INVALID_ARG, "null quadrature descriptor");
     if (q->precision != BEM_FP64 && q->precision != BEM_MIXED)
         return fail(ctx, BEM_ERR_INVALID_ARG, "precision must be BEM_FP64 or BEM_MIXED");
-    if (q->order_mode != BEM_ORDER_FIXED)
-        return fail(ctx, BEM_ERR_UNSUPPORTED, "only fixed orders are available in this build");
+    if (q->order_mode != BEM_ORDER_FIXED && q->order_mode != BEM_ORDER_LEARNED)
+        return fail(ctx, BEM_ERR_INVALID_ARG, "order_mode must be BEM_ORDER_FIXED or BEM_ORDER_LEARNED");
     for (int v : {q->q_identical, q->q_edge, q->q_vertex})
         if (v < 1 || v > 20) return fail(ctx, BEM_ERR_INVALID_ARG, "singular order must be in [1, 20]");
+    if (!block_rule) {
+        // entries evaluated with 4D tables: any Duffy order up to 20, or TRI7
+        if (q->regular_rule != BEM_RULE_TRI7 &&
+            (q->regular_rule != BEM_RULE_DUFFY || q->q_regular < 1 || q->q_regular > 20))
+            return fail(ctx, BEM_ERR_INVALID_ARG, "regular rule must be TRI7 or DUFFY with q in [1, 20]");
+        return BEM_OK;
+    }
     if (!make_rule2d(q->regular_rule, q->q_regular, r2))
         return fail(ctx, BEM_ERR_UNSUPPORTED, "regular rule must be TRI7 or DUFFY with q in [2, 4]");
     if (r2.np != 4 && r2.np != 7 && r2.np != 9 && r2.np != 16)
@@ -281,6 +288,16 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
             e = launch_tile_prefix(L, kTile, tc, ctx->tile_prefix, ctx->status, ctx->stream);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "tile prefix kernel");
+        if (J.quad.order_mode == BEM_ORDER_LEARNED) {
+            if (m->v.basis != BEM_P0)
+                return fail(ctx, BEM_ERR_UNSUPPORTED, "learned orders need the piecewise-constant basis");
+            if (!allow_touching || lower_only)
+                return fail(ctx, BEM_ERR_UNSUPPORTED, "learned orders are available for bem_near_field");
+            ProfScope ps(ctx, "learned_p0");
+            rc = run_learned_p0(ctx, m->v, L, ctx->tile_prefix, J.quad.precision);
+            if (rc) return rc;
+            continue;
+        }
         const int grid = ctx->num_sms * (m->v.basis == BEM_P0 ? 8 : 2);
         {
             ProfScope ps(ctx, m->v.basis == BEM_P0 ? "block_p0" : "block_p1");
@@ -377,6 +394,9 @@ int bem_destroy(bem_ctx *ctx)
     for (cudaEvent_t e : ctx->prof_free) cudaEventDestroy(e);
     cudaFree(ctx->status);
     cudaFree(ctx->tile_prefix);
+    cudaFree(ctx->learned_cls);
+    cudaFree(ctx->learned_rec);
+    cudaFree(ctx->learned_small);
     delete ctx;
     return BEM_OK;
 }
@@ -619,9 +639,9 @@ int bem_coupling_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs)
     return run_blocks(ctx, jobs, n_jobs, false, 0);
 }
 
-int bem_pivot_entries(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
+static int pivot_impl(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
                       const bem_quad_desc *quad, const int32_t *rows, const int32_t *cols,
-                      int64_t n, void *out)
+                      int64_t n, void *out, bool absolute)
 {
     if (!ctx) return BEM_ERR_INVALID_ARG;
     Mesh *m = get_mesh(ctx, mesh_id);
@@ -629,12 +649,12 @@ int bem_pivot_entries(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kern
     int rc = check_kernel(ctx, kernel);
     if (rc) return rc;
     Rule2D r2;
-    rc = check_quad(ctx, quad, r2);
+    rc = check_quad(ctx, quad, r2, false);
     if (rc) return rc;
     if (n < 0) return fail(ctx, BEM_ERR_INVALID_ARG, "negative entry count");
     if (n == 0) return BEM_OK;
     if (!rows || !cols || !out) return fail(ctx, BEM_ERR_INVALID_ARG, "null pointer");
-    if (kernel->kind == BEM_HELMHOLTZ_SLP && (reinterpret_cast<uintptr_t>(out) & 15))
+    if (!absolute && kernel->kind == BEM_HELMHOLTZ_SLP && (reinterpret_cast<uintptr_t>(out) & 15))
         return fail(ctx, BEM_ERR_INVALID_ARG, "complex output must be 16-byte aligned");
     Rule4D rules[4];
     if ((rc = get_rule4(ctx, kRegular, quad->regular_rule, quad->q_regular, rules[kRegular])) ||
@@ -646,10 +666,24 @@ int bem_pivot_entries(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kern
     {
         ProfScope ps(ctx, "pivot");
         e = launch_pivot_entries(m->v, rows, cols, n, out, rules, kernel->kind, kernel->kappa,
-                                 ctx->status, ctx->stream);
+                                 ctx->status, ctx->stream, absolute);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pivot kernel");
     return BEM_OK;
+}
+
+int bem_pivot_entries(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
+                      const bem_quad_desc *quad, const int32_t *rows, const int32_t *cols,
+                      int64_t n, void *out)
+{
+    return pivot_impl(ctx, mesh_id, kernel, quad, rows, cols, n, out, false);
+}
+
+int bem_pivot_entries_absolute(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
+                               const bem_quad_desc *quad, const int32_t *rows, const int32_t *cols,
+                               int64_t n, double *out)
+{
+    return pivot_impl(ctx, mesh_id, kernel, quad, rows, cols, n, out, true);
 }
 
 int bem_assemble_dense(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,

@@ -1,20 +1,8 @@
-// sm_103a kernels of the Galerkin quadrature path, FP64 form.
-//
-//  k_touching      one warp per touching triangle pair (Sauter-Schwab rules,
-//                  Section 2.2): lanes stride the q^4 * n_sub points of the
-//                  case's rule, warp-shuffle reduction, result stored in the
-//                  mesh's touching table in the ORIGINAL local vertex order.
-//  k_block_p0/p1   block engine for near-field, coupling and dense blocks
-//                  (Section 2.3 blocks t x s; Section 3 per-case lists are
-//                  replaced by classifying each pair on the fly): one CTA per
-//                  tile of a block, one thread per disjoint triangle pair
-//                  (product rule of a 2D triangle rule, Section 2.2 Duffy),
-//                  touching pairs read from the touching table.
-//  k_pivot         one warp per requested entry g_ij (pivot rows/columns).
-//
-// Kernel values (Eq. 2): laplace 1/(4 pi r), double layer (x-y).n_y/(4 pi r^3),
-// helmholtz exp(i kappa r)/(4 pi r).  sqrt(g_a g_b)/(4 pi) is applied once per
-// pair.
+// Device-side building blocks shared by the kernel translation units:
+// geometry records, kernel functions, double-float helpers, the regular
+// pair integrals, and the tile bodies of the block engine.
+#pragma once
+
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -23,7 +11,7 @@
 
 namespace bem {
 
-__constant__ int c_perm[6][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {0, 2, 1}, {1, 0, 2}, {2, 1, 0}};
+static __constant__ int c_perm[6][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {0, 2, 1}, {1, 0, 2}, {2, 1, 0}};
 
 constexpr double kInv4Pi = 0.079577471545947667884441881686257181;
 
@@ -484,28 +472,6 @@ __device__ __forceinline__ void touch_pair(const MeshView &m, int idx, const dou
     }
 }
 
-template <int KIND, int BASIS, int CAS>
-__global__ void __launch_bounds__(256) k_touching(MeshView m, const int *__restrict__ list,
-                                                  int64_t n, const double *__restrict__ rule,
-                                                  int np, double kappa)
-{
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (wid >= n) return;
-    touch_pair<KIND, BASIS, CAS>(m, __ldg(list + wid), rule, np, kappa, threadIdx.x & 31);
-}
-
-// Batched: items[k] = (job, touching index) over many meshes / kernels.
-template <int KIND, int BASIS, int CAS>
-__global__ void __launch_bounds__(256) k_touching_batch(const TouchJob *__restrict__ jobs,
-                                                        const int2 *__restrict__ items, int64_t n,
-                                                        const double *__restrict__ rule, int np)
-{
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (wid >= n) return;
-    const int2 it = items[wid];
-    touch_pair<KIND, BASIS, CAS>(jobs[it.x].m, it.y, rule, np, jobs[it.x].kappa, threadIdx.x & 31);
-}
-
 // Common-vertex pairs in float (mixed form, Laplace kernels): the shared vertex is
 // the canonical vertex 0 of both triangles, so x - y is formed from edge
 // vectors only and keeps float precision down to the singular point.
@@ -587,29 +553,6 @@ __device__ __forceinline__ void touch_vertex_f32(const MeshView &m, int idx,
                     m.table[(int64_t)idx * 9 + pa[i] * 3 + pb[j]] = make_double2(hat[i * 3 + j] * scale, 0.0);
         }
     }
-}
-
-template <int KIND, int BASIS>
-__global__ void __launch_bounds__(256) k_touching_vertex_f32(MeshView m, const int *__restrict__ list,
-                                                             int64_t n, const float *__restrict__ rule,
-                                                             int np)
-{
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (wid >= n) return;
-    touch_vertex_f32<KIND, BASIS>(m, __ldg(list + wid), rule, np, threadIdx.x & 31);
-}
-
-template <int KIND, int BASIS>
-__global__ void __launch_bounds__(256) k_touching_vertex_f32_batch(const TouchJob *__restrict__ jobs,
-                                                                   const int2 *__restrict__ items,
-                                                                   int64_t n,
-                                                                   const float *__restrict__ rule,
-                                                                   int np)
-{
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (wid >= n) return;
-    const int2 it = items[wid];
-    touch_vertex_f32<KIND, BASIS>(jobs[it.x].m, it.y, rule, np, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -766,80 +709,6 @@ __device__ __forceinline__ BlockInfo block_info(const BlockLaunch &L, const int6
     return bi;
 }
 
-// Tiles per block -> inclusive prefix sums (single CTA, chunked).
-__device__ void tile_prefix_cta(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
-                                int *status, int64_t *total)
-{
-    __shared__ int64_t part[1024];
-    const int64_t n = L.n_blocks;
-    const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
-    const int64_t lo = threadIdx.x * chunk, hi = min(n, lo + chunk);
-    int64_t sum = 0;
-    for (int64_t b = lo; b < hi; ++b) {
-        const int t = L.blk_row[b], s = L.blk_col[b];
-        int64_t tiles = 0;
-        if (t >= 0 && t < L.n_row_clusters && s >= 0 && s < L.n_col_clusters) {
-            const int nr = L.row_ptr[t + 1] - L.row_ptr[t];
-            const int nc = L.col_ptr[s + 1] - L.col_ptr[s];
-            if (nr < 0 || nc < 0) set_status(status, BEM_ERR_INVALID_ARG);
-            else tiles = (int64_t)((nr + tr - 1) / tr) * ((nc + tc - 1) / tc);
-        } else {
-            set_status(status, BEM_ERR_INVALID_ARG);
-        }
-        sum += tiles;
-        prefix[b] = sum;   // local inclusive sum, fixed below
-    }
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        int64_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    const int64_t base = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
-    for (int64_t b = lo; b < hi; ++b) prefix[b] += base;
-    if (total && threadIdx.x == blockDim.x - 1) *total = part[threadIdx.x];
-    __syncthreads();
-}
-
-__global__ void __launch_bounds__(1024) k_tile_prefix(BlockLaunch L, int tr, int tc,
-                                                      int64_t *prefix, int *status)
-{
-    tile_prefix_cta(L, tr, tc, prefix, status, nullptr);
-}
-
-// one CTA per job: per-job block prefix sums and the job's tile total
-__global__ void __launch_bounds__(1024) k_tile_prefix_batch(BatchJob *jobs, int tr, int tc,
-                                                            int64_t *job_total, int *status)
-{
-    BatchJob &J = jobs[blockIdx.x];
-    tile_prefix_cta(J.L, tr, tc, const_cast<int64_t *>(J.prefix), status, job_total + blockIdx.x);
-}
-
-// inclusive scan of the job totals (single CTA)
-__global__ void __launch_bounds__(1024) k_job_scan(const int64_t *job_total, int n, int64_t *job_end)
-{
-    __shared__ int64_t part[1024];
-    const int chunk = (n + blockDim.x - 1) / blockDim.x;
-    const int lo = threadIdx.x * chunk, hi = min(n, lo + chunk);
-    int64_t sum = 0;
-    for (int k = lo; k < hi; ++k) {
-        sum += job_total[k];
-        job_end[k] = sum;
-    }
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        int64_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    const int64_t base = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
-    for (int k = lo; k < hi; ++k) job_end[k] += base;
-}
-
 // ---------------------------------------------------------------------------
 // Block engine, piecewise constant: tile = 32 rows x 8 columns, one thread per entry.
 // ---------------------------------------------------------------------------
@@ -894,16 +763,6 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
     }
 }
 
-template <int KIND, int NP, bool MIXED>
-__global__ void __launch_bounds__(256) k_block_p0(MeshView m, BlockLaunch L, Rule2D R,
-                                                  const int64_t *__restrict__ prefix,
-                                                  int *status)
-{
-    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x)
-        p0_tile<KIND, NP, MIXED>(m, L, R, prefix, tile, status);
-}
-
 // ---------------------------------------------------------------------------
 // Block engine, piecewise linear: tile = 32 x 32 vertices.  The triangles
 // touching the tile's rows (Ta) and columns (Tb) are collected in shared
@@ -948,7 +807,7 @@ __device__ __forceinline__ int owner_pos(const MeshView &m, int T, const int *se
 // Collect the triangles touching the vertex set `set` (n <= 32): deterministic
 // order (by owner position, then adjacency order), and per vertex the list of
 // (triangle slot << 2 | local index).
-__device__ void p1_support(const MeshView &m, const int *set, int n, int *tri, int *cnt,
+__device__ __forceinline__ void p1_support(const MeshView &m, const int *set, int n, int *tri, int *cnt,
                            int *off, int (*lists)[kTile], int *list_n, int *ntri,
                            int *status)
 {
@@ -1147,23 +1006,6 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
     }
 }
 
-template <int KIND, int NP, bool MIXED>
-__global__ void __launch_bounds__(p1_threads(MIXED), p1_min_blocks(MIXED))
-k_block_p1(MeshView m, BlockLaunch L, Rule2D R, const int64_t *__restrict__ prefix, int *status)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x)
-        p1_tile<KIND, NP, MIXED>(m, L, R, prefix, tile, status, smem_raw);
-}
-
-// ---------------------------------------------------------------------------
-// Batched (persistent) block engine: one launch drains the tiles of many
-// block lists (jobs) that share kernel, basis, rule and precision, e.g. the
-// near-field and coupling blocks of many meshes.  job_end[j] = tiles of jobs
-// 0..j (inclusive); every tile finds its job by binary search and runs the
-// same tile body as the single-list kernels, so the results are identical.
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ int find_job(const int64_t *job_end, int n_jobs, int64_t tile)
 {
     int lo = 0, hi = n_jobs - 1;
@@ -1175,338 +1017,9 @@ __device__ __forceinline__ int find_job(const int64_t *job_end, int n_jobs, int6
     return lo;
 }
 
-template <int KIND, int NP, bool MIXED>
-__global__ void __launch_bounds__(256) k_batch_p0(const BatchJob *__restrict__ jobs, int n_jobs,
-                                                  const int64_t *__restrict__ job_end, Rule2D R,
-                                                  int *status)
-{
-    const int64_t total = n_jobs > 0 ? job_end[n_jobs - 1] : 0;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        const int j = find_job(job_end, n_jobs, tile);
-        const int64_t local = tile - (j > 0 ? job_end[j - 1] : 0);
-        const BatchJob &J = jobs[j];
-        p0_tile<KIND, NP, MIXED>(J.m, J.L, R, J.prefix, local, status);
-    }
-}
-
-template <int KIND, int NP, bool MIXED>
-__global__ void __launch_bounds__(p1_threads(MIXED), p1_min_blocks(MIXED))
-k_batch_p1(const BatchJob *__restrict__ jobs, int n_jobs, const int64_t *__restrict__ job_end,
-           Rule2D R, int *status)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int64_t total = n_jobs > 0 ? job_end[n_jobs - 1] : 0;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        const int j = find_job(job_end, n_jobs, tile);
-        const int64_t local = tile - (j > 0 ? job_end[j - 1] : 0);
-        const BatchJob &J = jobs[j];
-        p1_tile<KIND, NP, MIXED>(J.m, J.L, R, J.prefix, local, status, smem_raw);
-    }
-}
-
-size_t p1_smem_bytes(bool cplx, bool mixed)
-{
-    return ((sizeof(P1Smem) + 15) & ~size_t(15)) +
-           (size_t)kP1Cap * 9 * (mixed ? sizeof(float) : sizeof(double)) * (cplx ? 2 : 1);
-}
-
-// ---------------------------------------------------------------------------
-// Arbitrary entries: one warp per entry, lanes stride the points of each pair's rule.
-// ---------------------------------------------------------------------------
 struct RuleSet {
     const double *d[4];
     int n[4];
 };
-
-template <int KIND>
-__global__ void __launch_bounds__(256) k_pivot(MeshView m, const int32_t *__restrict__ rows,
-                                               const int32_t *__restrict__ cols, int64_t n,
-                                               void *out, RuleSet rs, double kappa, int *status)
-{
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wid >= n) return;
-    const int i = rows[wid], j = cols[wid];
-    const int64_t lim = m.basis == BEM_P0 ? m.nt : m.nv;
-    if (i < 0 || i >= lim || j < 0 || j >= lim) {
-        if (lane == 0) set_status(status, BEM_ERR_INVALID_ARG);
-        return;
-    }
-    int alo, ahi, blo, bhi;
-    if (m.basis == BEM_P0) {
-        alo = 0; ahi = 1; blo = 0; bhi = 1;
-    } else {
-        alo = __ldg(m.vt_ptr + i); ahi = __ldg(m.vt_ptr + i + 1);
-        blo = __ldg(m.vt_ptr + j); bhi = __ldg(m.vt_ptr + j + 1);
-    }
-    double sr = 0.0, si = 0.0;
-    for (int ka = alo; ka < ahi; ++ka) {
-        const int a = m.basis == BEM_P0 ? i : __ldg(m.vt_tri + ka);
-        const int4 va = __ldg(m.tvid + a);
-        const int la = m.basis == BEM_P0 ? -1 : (va.x == i ? 0 : (va.y == i ? 1 : 2));
-        Tri A;
-        load_tri(m.geom, a, A);
-        for (int kb = blo; kb < bhi; ++kb) {
-            const int b = m.basis == BEM_P0 ? j : __ldg(m.vt_tri + kb);
-            const int4 vb = __ldg(m.tvid + b);
-            const int lb = m.basis == BEM_P0 ? -1 : (vb.x == j ? 0 : (vb.y == j ? 1 : 2));
-            int cas = kRegular, pc = 0;
-            if (touching(va, vb)) {
-                const int k = find_touching(m, a, b);
-                cas = __ldg(m.nb_case + k);
-                pc = __ldg(m.nb_perm + k);
-            }
-            const int *pa = c_perm[pc / 6], *pb = c_perm[pc % 6];
-            int ca = -1, cb = -1;   // canonical positions of the basis vertices
-            for (int q = 0; q < 3; ++q) {
-                if (pa[q] == la) ca = q;
-                if (pb[q] == lb) cb = q;
-            }
-            Tri B;
-            load_tri(m.geom, b, B);
-            double e1a[3], e2a[3], e1b[3], e2b[3], d0[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                e1a[c] = A.v[pa[1]][c] - A.v[pa[0]][c];
-                e2a[c] = A.v[pa[2]][c] - A.v[pa[1]][c];
-                e1b[c] = B.v[pb[1]][c] - B.v[pb[0]][c];
-                e2b[c] = B.v[pb[2]][c] - B.v[pb[1]][c];
-                d0[c] = A.v[pa[0]][c] - B.v[pb[0]][c];
-            }
-            const double *rule = rs.d[cas];
-            const int np = rs.n[cas];
-            double pr = 0.0, pi = 0.0;
-            for (int p = lane; p < np; p += 32) {
-                const double x1 = __ldg(rule + p), x2 = __ldg(rule + np + p),
-                             y1 = __ldg(rule + 2 * np + p), y2 = __ldg(rule + 3 * np + p),
-                             w = __ldg(rule + 4 * np + p);
-                const double dx = d0[0] + x1 * e1a[0] + x2 * e2a[0] - y1 * e1b[0] - y2 * e2b[0];
-                const double dy = d0[1] + x1 * e1a[1] + x2 * e2a[1] - y1 * e1b[1] - y2 * e2b[1];
-                const double dz = d0[2] + x1 * e1a[2] + x2 * e2a[2] - y1 * e1b[2] - y2 * e2b[2];
-                double kr, ki;
-                kval<KIND>(dx, dy, dz, B.n, kappa, kr, ki);
-                double f = w;
-                if (ca >= 0) f *= (ca == 0 ? 1.0 - x1 : (ca == 1 ? x1 - x2 : x2));
-                if (cb >= 0) f *= (cb == 0 ? 1.0 - y1 : (cb == 1 ? y1 - y2 : y2));
-                pr += f * kr;
-                if (KIND == BEM_HELMHOLTZ_SLP) pi += f * ki;
-            }
-            const double scale = A.sg * B.sg * kInv4Pi;
-            sr += pr * scale;
-            si += pi * scale;
-        }
-    }
-    sr = warp_sum(sr);
-    if (KIND == BEM_HELMHOLTZ_SLP) si = warp_sum(si);
-    if (lane == 0) {
-        if (KIND == BEM_HELMHOLTZ_SLP) reinterpret_cast<double2 *>(out)[wid] = make_double2(sr, si);
-        else reinterpret_cast<double *>(out)[wid] = sr;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Launchers
-// ---------------------------------------------------------------------------
-cudaError_t launch_tile_prefix(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
-                               int *status, cudaStream_t st)
-{
-    if (L.n_blocks <= 0) return cudaSuccess;
-    k_tile_prefix<<<1, 1024, 0, st>>>(L, tr, tc, prefix, status);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
-                            const Rule4D &rule, int kind, double kappa, int mixed, cudaStream_t st)
-{
-    if (n <= 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((n + 7) / 8);
-    const bool p1 = m.basis == BEM_P1;
-    if (mixed && cas == kVertex && kind != BEM_HELMHOLTZ_SLP && rule.f) {
-        if (kind == BEM_LAPLACE_SLP) {
-            if (p1) k_touching_vertex_f32<BEM_LAPLACE_SLP, BEM_P1><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
-            else k_touching_vertex_f32<BEM_LAPLACE_SLP, BEM_P0><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
-        } else {
-            if (p1) k_touching_vertex_f32<BEM_LAPLACE_DLP, BEM_P1><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
-            else k_touching_vertex_f32<BEM_LAPLACE_DLP, BEM_P0><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
-        }
-        return cudaGetLastError();
-    }
-#define BEM_TOUCH(K, B, C) k_touching<K, B, C><<<blocks, 256, 0, st>>>(m, list, n, rule.d, rule.n, kappa)
-#define BEM_TOUCH_CASE(K, B)                                   \
-    do {                                                       \
-        if (cas == kIdentical) BEM_TOUCH(K, B, kIdentical);    \
-        else if (cas == kEdge) BEM_TOUCH(K, B, kEdge);         \
-        else BEM_TOUCH(K, B, kVertex);                         \
-    } while (0)
-    switch (kind) {
-    case BEM_LAPLACE_SLP: if (p1) BEM_TOUCH_CASE(BEM_LAPLACE_SLP, BEM_P1); else BEM_TOUCH_CASE(BEM_LAPLACE_SLP, BEM_P0); break;
-    case BEM_LAPLACE_DLP: if (p1) BEM_TOUCH_CASE(BEM_LAPLACE_DLP, BEM_P1); else BEM_TOUCH_CASE(BEM_LAPLACE_DLP, BEM_P0); break;
-    default: if (p1) BEM_TOUCH_CASE(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TOUCH_CASE(BEM_HELMHOLTZ_SLP, BEM_P0); break;
-    }
-#undef BEM_TOUCH_CASE
-#undef BEM_TOUCH
-    return cudaGetLastError();
-}
-
-template <int KIND, int NP, bool MIXED>
-static cudaError_t block_np(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
-                            const int64_t *prefix, int *status, int grid, cudaStream_t st)
-{
-    if (m.basis == BEM_P0) {
-        k_block_p0<KIND, NP, MIXED><<<grid, 256, 0, st>>>(m, L, R, prefix, status);
-    } else {
-        const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP, MIXED);
-        cudaError_t e = cudaFuncSetAttribute(k_block_p1<KIND, NP, MIXED>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        const int g = MIXED ? grid * 2 : grid;
-        k_block_p1<KIND, NP, MIXED><<<g, p1_threads(MIXED), sm, st>>>(m, L, R, prefix, status);
-    }
-    return cudaGetLastError();
-}
-
-template <int KIND, bool MIXED>
-static cudaError_t block_kind(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
-                              const int64_t *prefix, int *status, int grid, cudaStream_t st)
-{
-    switch (R.np) {
-    case 4: return block_np<KIND, 4, MIXED>(m, L, R, prefix, status, grid, st);
-    case 7: return block_np<KIND, 7, MIXED>(m, L, R, prefix, status, grid, st);
-    case 9: return block_np<KIND, 9, MIXED>(m, L, R, prefix, status, grid, st);
-    case 16: return block_np<KIND, 16, MIXED>(m, L, R, prefix, status, grid, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
-                                const int64_t *prefix, int *status, int grid, cudaStream_t st)
-{
-    if (L.n_blocks <= 0) return cudaSuccess;
-    // the mixed form covers the Laplace kernels; Helmholtz pairs stay FP64
-    switch (L.kind) {
-    case BEM_LAPLACE_SLP:
-        return L.mixed ? block_kind<BEM_LAPLACE_SLP, true>(m, L, R, prefix, status, grid, st)
-                       : block_kind<BEM_LAPLACE_SLP, false>(m, L, R, prefix, status, grid, st);
-    case BEM_LAPLACE_DLP:
-        return L.mixed ? block_kind<BEM_LAPLACE_DLP, true>(m, L, R, prefix, status, grid, st)
-                       : block_kind<BEM_LAPLACE_DLP, false>(m, L, R, prefix, status, grid, st);
-    default: return block_kind<BEM_HELMHOLTZ_SLP, false>(m, L, R, prefix, status, grid, st);
-    }
-}
-
-cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const int32_t *cols,
-                                 int64_t n, void *out, const Rule4D *rules, int kind,
-                                 double kappa, int *status, cudaStream_t st)
-{
-    if (n <= 0) return cudaSuccess;
-    RuleSet rs;
-    for (int c = 0; c < 4; ++c) {
-        rs.d[c] = rules[c].d;
-        rs.n[c] = rules[c].n;
-    }
-    const int64_t blocks = (n + 7) / 8;
-    switch (kind) {
-    case BEM_LAPLACE_SLP: k_pivot<BEM_LAPLACE_SLP><<<(unsigned)blocks, 256, 0, st>>>(m, rows, cols, n, out, rs, kappa, status); break;
-    case BEM_LAPLACE_DLP: k_pivot<BEM_LAPLACE_DLP><<<(unsigned)blocks, 256, 0, st>>>(m, rows, cols, n, out, rs, kappa, status); break;
-    default: k_pivot<BEM_HELMHOLTZ_SLP><<<(unsigned)blocks, 256, 0, st>>>(m, rows, cols, n, out, rs, kappa, status); break;
-    }
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Batched launchers
-// ---------------------------------------------------------------------------
-cudaError_t launch_tile_prefix_batch(BatchJob *jobs, int n_jobs, int tr, int tc, int64_t *job_total,
-                                     int64_t *job_end, int *status, cudaStream_t st)
-{
-    if (n_jobs <= 0) return cudaSuccess;
-    k_tile_prefix_batch<<<n_jobs, 1024, 0, st>>>(jobs, tr, tc, job_total, status);
-    k_job_scan<<<1, 1024, 0, st>>>(job_total, n_jobs, job_end);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int cas, int mixed,
-                                  const int2 *items, int64_t n, const Rule4D &rule, cudaStream_t st)
-{
-    if (n <= 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((n + 7) / 8);
-    const bool p1 = basis == BEM_P1;
-    if (mixed && cas == kVertex && kind != BEM_HELMHOLTZ_SLP && rule.f) {
-        if (kind == BEM_LAPLACE_SLP) {
-            if (p1) k_touching_vertex_f32_batch<BEM_LAPLACE_SLP, BEM_P1><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
-            else k_touching_vertex_f32_batch<BEM_LAPLACE_SLP, BEM_P0><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
-        } else {
-            if (p1) k_touching_vertex_f32_batch<BEM_LAPLACE_DLP, BEM_P1><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
-            else k_touching_vertex_f32_batch<BEM_LAPLACE_DLP, BEM_P0><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
-        }
-        return cudaGetLastError();
-    }
-#define BEM_TB(K, B, C) k_touching_batch<K, B, C><<<blocks, 256, 0, st>>>(jobs, items, n, rule.d, rule.n)
-#define BEM_TB_CASE(K, B)                                  \
-    do {                                                   \
-        if (cas == kIdentical) BEM_TB(K, B, kIdentical);   \
-        else if (cas == kEdge) BEM_TB(K, B, kEdge);        \
-        else BEM_TB(K, B, kVertex);                        \
-    } while (0)
-    switch (kind) {
-    case BEM_LAPLACE_SLP: if (p1) BEM_TB_CASE(BEM_LAPLACE_SLP, BEM_P1); else BEM_TB_CASE(BEM_LAPLACE_SLP, BEM_P0); break;
-    case BEM_LAPLACE_DLP: if (p1) BEM_TB_CASE(BEM_LAPLACE_DLP, BEM_P1); else BEM_TB_CASE(BEM_LAPLACE_DLP, BEM_P0); break;
-    default: if (p1) BEM_TB_CASE(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TB_CASE(BEM_HELMHOLTZ_SLP, BEM_P0); break;
-    }
-#undef BEM_TB_CASE
-#undef BEM_TB
-    return cudaGetLastError();
-}
-
-template <int KIND, int NP, bool MIXED>
-static cudaError_t batch_np(const BatchJob *jobs, int n_jobs, const int64_t *job_end, int basis,
-                            const Rule2D &R, int *status, int grid, cudaStream_t st)
-{
-    if (basis == BEM_P0) {
-        k_batch_p0<KIND, NP, MIXED><<<grid, 256, 0, st>>>(jobs, n_jobs, job_end, R, status);
-    } else {
-        const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP, MIXED);
-        // set once (outside any stream capture: plans issue once before capturing)
-        static bool attr_done = false;
-        if (!attr_done) {
-            cudaError_t e = cudaFuncSetAttribute(k_batch_p1<KIND, NP, MIXED>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
-            attr_done = true;
-        }
-        k_batch_p1<KIND, NP, MIXED><<<grid, p1_threads(MIXED), sm, st>>>(jobs, n_jobs, job_end, R, status);
-    }
-    return cudaGetLastError();
-}
-
-template <int KIND, bool MIXED>
-static cudaError_t batch_kind(const BatchJob *jobs, int n_jobs, const int64_t *job_end, int basis,
-                              const Rule2D &R, int *status, int grid, cudaStream_t st)
-{
-    switch (R.np) {
-    case 4: return batch_np<KIND, 4, MIXED>(jobs, n_jobs, job_end, basis, R, status, grid, st);
-    case 7: return batch_np<KIND, 7, MIXED>(jobs, n_jobs, job_end, basis, R, status, grid, st);
-    case 9: return batch_np<KIND, 9, MIXED>(jobs, n_jobs, job_end, basis, R, status, grid, st);
-    case 16: return batch_np<KIND, 16, MIXED>(jobs, n_jobs, job_end, basis, R, status, grid, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-cudaError_t launch_block_batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end, int basis,
-                               int kind, int mixed, const Rule2D &R, int *status, int grid,
-                               cudaStream_t st)
-{
-    if (n_jobs <= 0) return cudaSuccess;
-    switch (kind) {
-    case BEM_LAPLACE_SLP:
-        return mixed ? batch_kind<BEM_LAPLACE_SLP, true>(jobs, n_jobs, job_end, basis, R, status, grid, st)
-                     : batch_kind<BEM_LAPLACE_SLP, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
-    case BEM_LAPLACE_DLP:
-        return mixed ? batch_kind<BEM_LAPLACE_DLP, true>(jobs, n_jobs, job_end, basis, R, status, grid, st)
-                     : batch_kind<BEM_LAPLACE_DLP, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
-    default:
-        return batch_kind<BEM_HELMHOLTZ_SLP, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
-    }
-}
 
 }  // namespace bem

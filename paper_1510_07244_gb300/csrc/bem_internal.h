@@ -100,6 +100,14 @@ struct bem_ctx {
     std::map<std::string, std::pair<int64_t, double>> prof_total;
     std::vector<struct bem_plan *> prof_plans;   // plans whose last run's events are unread
     std::map<std::string, int> tuned;            // autotuner cache: bucket key -> CTAs per SM
+    // learned order selection
+    struct bem_mlp *order_model = nullptr;
+    float order_conf = 0.0f;
+    unsigned char *learned_cls = nullptr;        // scratch: class per tile slot
+    void *learned_rec = nullptr;                 // scratch: records grouped by class
+    int64_t learned_cap = 0;
+    int64_t *learned_small = nullptr;            // counters / offsets
+    int64_t learned_counts[6] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace bem {
@@ -171,6 +179,19 @@ cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t
 cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const Rule2D &rule,
                                 const int64_t *prefix, int *status, int grid, cudaStream_t st);
 size_t p1_smem_bytes(bool cplx, bool mixed);
+// bem_block_p1_{fp64,mixed}.cu: piecewise-linear block engine per precision
+cudaError_t launch_p1_single_fp64(int kind, int np, const MeshView &m, const BlockLaunch &L,
+                                  const Rule2D &R, const int64_t *prefix, int *status, int grid,
+                                  cudaStream_t st);
+cudaError_t launch_p1_single_mixed(int kind, int np, const MeshView &m, const BlockLaunch &L,
+                                   const Rule2D &R, const int64_t *prefix, int *status, int grid,
+                                   cudaStream_t st);
+cudaError_t launch_p1_batch_fp64(int kind, int np, const BatchJob *jobs, int n_jobs,
+                                 const int64_t *job_end, const Rule2D &R, int *status, int grid,
+                                 cudaStream_t st);
+cudaError_t launch_p1_batch_mixed(int kind, int np, const BatchJob *jobs, int n_jobs,
+                                  const int64_t *job_end, const Rule2D &R, int *status, int grid,
+                                  cudaStream_t st);
 cudaError_t launch_tile_prefix_batch(BatchJob *jobs, int n_jobs, int tr, int tc, int64_t *job_total,
                                      int64_t *job_end, int *status, cudaStream_t st);
 cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int cas, int mixed,
@@ -180,6 +201,10 @@ cudaError_t launch_block_batch(const BatchJob *jobs, int n_jobs, const int64_t *
                                cudaStream_t st);
 cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const int32_t *cols,
                                  int64_t n, void *out, const Rule4D *rules /*[4]*/, int kind,
-                                 double kappa, int *status, cudaStream_t st);
+                                 double kappa, int *status, cudaStream_t st, bool absolute);
+
+// bem_order.cu: learned-order near field of one piecewise-constant job
+int run_learned_p0(bem_ctx *ctx, const MeshView &mv, const BlockLaunch &L, const int64_t *prefix,
+                   int precision);
 
 }  // namespace bem

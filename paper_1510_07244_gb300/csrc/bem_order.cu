@@ -1,0 +1,951 @@
+// Learned quadrature-order selection for disjoint (regular) triangle pairs.
+//
+// The paper uses one fixed rule per Sauter-Schwab case (Section 2.2 and the
+// "higher quadrature orders" study of Section 4).  Here a small MLP,
+// 8 pair features -> 64 -> 64 -> 6 rule classes (ReLU), predicts for every
+// disjoint pair the cheapest rule that meets an error target; the classes
+// form a ladder of increasing accuracy and cost:
+//     0: Duffy q=2 (16 points)   1: Radon 7x7 (49)   2: Duffy q=4 (256)
+//     3: Duffy q=5 (625)         4: Duffy q=6 (1296) 5: Duffy q=8 (4096).
+// A pair gets the cheapest class whose cumulative predicted probability
+// reaches the confidence level (so uncertainty moves it up the ladder).
+//
+// Training runs on the GPU with the kernels below (FP32 forward, backward and
+// Adam, batch sums in a fixed order, so a training step is deterministic);
+// inference uses BF16 weights and activations on the tensor cores
+// (mma.sync m16n8k16, FP32 accumulation).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "bem_device.cuh"
+
+namespace bem {
+
+// ---------------------------------------------------------------------------
+// Pair features (8): log2(centroid distance / D), log2(closest vertex
+// distance / D), cos(angle between normals), log2(area ratio), height of the
+// test centroid above the trial plane / centroid distance, kernel id / 2,
+// kappa D, log2(aspect ratio); D = the larger triangle diameter.  Normalised
+// by the model's mean and standard deviation.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pair_features(const MeshView &m, int a, int b, int kind,
+                                              double kappa, const float *mean, const float *inv_std,
+                                              float *f)
+{
+    const double *ga = m.geom + (int64_t)a * kGeomStride;
+    const double *gb = m.geom + (int64_t)b * kGeomStride;
+    double va[3][3], vb[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            va[k][c] = __ldg(ga + 3 * k + c);
+            vb[k][c] = __ldg(gb + 3 * k + c);
+        }
+    double ca[3], cb[3], da = 0.0, db = 0.0, dmin = 1e300;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ca[c] = (va[0][c] + va[1][c] + va[2][c]) / 3.0;
+        cb[c] = (vb[0][c] + vb[1][c] + vb[2][c]) / 3.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3;
+        double ea = 0.0, eb = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ea += (va[i][c] - va[j][c]) * (va[i][c] - va[j][c]);
+            eb += (vb[i][c] - vb[j][c]) * (vb[i][c] - vb[j][c]);
+        }
+        da = fmax(da, ea);
+        db = fmax(db, eb);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double dd = 0.0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dd += (va[i][c] - vb[k][c]) * (va[i][c] - vb[k][c]);
+            dmin = fmin(dmin, dd);
+        }
+    }
+    da = sqrt(da);
+    db = sqrt(db);
+    const double D = fmax(da, db);
+    double dc = 0.0, h = 0.0, cosang = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        dc += (ca[c] - cb[c]) * (ca[c] - cb[c]);
+        h += (ca[c] - cb[c]) * __ldg(gb + 9 + c);
+        cosang += __ldg(ga + 9 + c) * __ldg(gb + 9 + c);
+    }
+    dc = sqrt(dc);
+    const double area_a = 0.5 * __ldg(ga + 12), area_b = 0.5 * __ldg(gb + 12);
+    const double ar = fmax(da * da / (2.0 * area_a), db * db / (2.0 * area_b));
+    float raw[8];
+    raw[0] = (float)log2(fmax(dc / D, 1e-6));
+    raw[1] = (float)log2(fmax(sqrt(dmin) / D, 1e-6));
+    raw[2] = (float)cosang;
+    raw[3] = (float)log2(area_a / area_b);
+    raw[4] = (float)(h / fmax(dc, 1e-300));
+    raw[5] = 0.5f * (float)kind;
+    raw[6] = kind == BEM_HELMHOLTZ_SLP ? (float)(kappa * D) : 0.0f;
+    raw[7] = (float)log2(ar);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = (raw[k] - mean[k]) * inv_std[k];
+}
+
+__global__ void k_features(MeshView m, const int32_t *__restrict__ a_idx,
+                           const int32_t *__restrict__ b_idx, int64_t n, int kind, double kappa,
+                           const float *mean, const float *inv_std, float *X)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    pair_features(m, a_idx[i], b_idx[i], kind, kappa, mean, inv_std, X + 8 * i);
+}
+
+// ---------------------------------------------------------------------------
+// Training kernels (FP32).  Parameter layout (floats): W1[64][8] b1[64]
+// W2[64][64] b2[64] W3[6][64] b3[6].
+// ---------------------------------------------------------------------------
+constexpr int kIn = 8, kHid = 64, kOut = 6;
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
+              kOffB2 = kOffW2 + kHid * kHid, kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kOut * kHid,
+              kNParams = kOffB3 + kOut;
+
+// z = in W^T + b (rows x outd), optional ReLU copy
+__global__ void k_dense(const float *in, int rows, int ind, const float *W, const float *b, int outd,
+                        float *z, float *h)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)rows * outd) return;
+    const int64_t i = t / outd;
+    const int o = (int)(t % outd);
+    float s = b[o];
+    for (int k = 0; k < ind; ++k) s = fmaf(in[i * ind + k], W[o * ind + k], s);
+    z[t] = s;
+    if (h) h[t] = fmaxf(s, 0.0f);
+}
+
+// softmax cross entropy: dz = (p - onehot) / n, per-row loss
+__global__ void k_softmax_ce(const float *logits, const int32_t *y, int n, float *dz, float *loss)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float mx = -1e30f;
+    for (int o = 0; o < kOut; ++o) mx = fmaxf(mx, logits[i * kOut + o]);
+    float se = 0.0f;
+    for (int o = 0; o < kOut; ++o) se += expf(logits[i * kOut + o] - mx);
+    const int yi = y[i];
+    for (int o = 0; o < kOut; ++o) {
+        const float p = expf(logits[i * kOut + o] - mx) / se;
+        dz[i * kOut + o] = (p - (o == yi ? 1.0f : 0.0f)) / (float)n;
+    }
+    loss[i] = -(logits[i * kOut + yi] - mx - logf(se));
+}
+
+// dW[o][k] = sum_i dz[i][o] in[i][k], db[o] = sum_i dz[i][o]  (fixed order over i)
+__global__ void k_weight_grad(const float *dz, const float *in, int rows, int outd, int ind,
+                              float *dW, float *db)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < outd * ind) {
+        const int o = t / ind, k = t % ind;
+        float s = 0.0f;
+        for (int i = 0; i < rows; ++i) s = fmaf(dz[(int64_t)i * outd + o], in[(int64_t)i * ind + k], s);
+        dW[t] = s;
+    } else if (t < outd * ind + outd) {
+        const int o = t - outd * ind;
+        float s = 0.0f;
+        for (int i = 0; i < rows; ++i) s += dz[(int64_t)i * outd + o];
+        db[o] = s;
+    }
+}
+
+// dprev[i][k] = (sum_o dz[i][o] W[o][k]) * (zprev[i][k] > 0)
+__global__ void k_back_act(const float *dz, const float *W, const float *zprev, int rows, int outd,
+                           int ind, float *dprev)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)rows * ind) return;
+    const int64_t i = t / ind;
+    const int k = (int)(t % ind);
+    float s = 0.0f;
+    for (int o = 0; o < outd; ++o) s = fmaf(dz[i * outd + o], W[o * ind + k], s);
+    dprev[t] = zprev[t] > 0.0f ? s : 0.0f;
+}
+
+__global__ void k_adam(float *p, const float *g, float *m1, float *m2, int n, float lr, float b1,
+                       float b2, float eps, float c1, float c2)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    m1[t] = b1 * m1[t] + (1.0f - b1) * g[t];
+    m2[t] = b2 * m2[t] + (1.0f - b2) * g[t] * g[t];
+    p[t] -= lr * (m1[t] / c1) / (sqrtf(m2[t] / c2) + eps);
+}
+
+__global__ void k_sum_fixed(const float *x, int n, float *out)
+{
+    // one CTA, fixed-order strided partial sums then a tree
+    __shared__ float part[256];
+    float s = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0];
+}
+
+__global__ void k_to_bf16(const float *p, int n, __nv_bfloat16 *q)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) q[t] = __float2bfloat16_rn(p[t]);
+}
+
+// ---------------------------------------------------------------------------
+// Inference on the tensor cores: one warp evaluates 16 feature rows per
+// mma.sync.m16n8k16 (BF16 inputs, FP32 accumulators).  Fragment layouts of
+// m16n8k16 (PTX ISA): A row-major 16x16, thread t holds rows t/4 and t/4+8,
+// columns 2(t%4)+{0,1} and +8; B col-major 16x8, thread t holds k = 2(t%4)+{0,1}
+// and +8 of column t/4; C 16x8, rows t/4 and t/4+8, columns 2(t%4)+{0,1}.
+// The C fragments of two neighbouring 8-column tiles form the A fragment of
+// the next layer's 16-wide k tile, so activations stay in registers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<unsigned *>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float *c, const unsigned *a, const unsigned *b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// B fragment of W (out x in, row-major BF16) for output tile n0 (8 columns)
+// and k tile k0 (16 inputs); inputs beyond `ind` and outputs beyond `outd` are 0.
+__device__ __forceinline__ void load_b(const __nv_bfloat16 *W, int outd, int ind, int n0, int k0,
+                                       int lane, unsigned *b)
+{
+    const int n = n0 + lane / 4, k = k0 + 2 * (lane % 4);
+    __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+    auto at = [&](int kk) { return (n < outd && kk < ind) ? W[n * ind + kk] : z; };
+    __nv_bfloat162 v0, v1;
+    v0.x = at(k);
+    v0.y = at(k + 1);
+    v1.x = at(k + 8);
+    v1.y = at(k + 9);
+    b[0] = *reinterpret_cast<unsigned *>(&v0);
+    b[1] = *reinterpret_cast<unsigned *>(&v1);
+}
+
+struct MlpDev {
+    const __nv_bfloat16 *W1, *W2, *W3;
+    const float *b1, *b2, *b3;
+};
+
+// 16 rows (features in X16, row-major 16 x 8 float) -> logits of rows t/4 and
+// t/4 + 8 for this lane's two classes 2(t%4), 2(t%4)+1 (classes < 8).
+__device__ __forceinline__ void mlp_tile(const MlpDev &P, const float (*X16)[8], int lane,
+                                         float *out_lo, float *out_hi)
+{
+    const int r = lane / 4, cq = 2 * (lane % 4);
+    // layer 1: K = 8 (padded to 16)
+    unsigned a[4];
+    a[0] = pack_bf16(X16[r][cq], X16[r][cq + 1]);
+    a[1] = pack_bf16(X16[r + 8][cq], X16[r + 8][cq + 1]);
+    a[2] = 0u;   // columns 8..15 are padding
+    a[3] = 0u;
+    float h1[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        unsigned b[2];
+        load_b(P.W1, kHid, kIn, nt * 8, 0, lane, b);
+        const int col = nt * 8 + cq;
+        h1[nt][0] = P.b1[col];
+        h1[nt][1] = P.b1[col + 1];
+        h1[nt][2] = P.b1[col];
+        h1[nt][3] = P.b1[col + 1];
+        mma_bf16(h1[nt], a, b);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h1[nt][q] = fmaxf(h1[nt][q], 0.0f);
+    }
+    // layer 2: K = 64 (4 k tiles), N = 64 (8 n tiles)
+    float h2[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int col = nt * 8 + cq;
+        h2[nt][0] = P.b2[col];
+        h2[nt][1] = P.b2[col + 1];
+        h2[nt][2] = P.b2[col];
+        h2[nt][3] = P.b2[col + 1];
+    }
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+        unsigned ak[4];
+        ak[0] = pack_bf16(h1[2 * kt][0], h1[2 * kt][1]);
+        ak[1] = pack_bf16(h1[2 * kt][2], h1[2 * kt][3]);
+        ak[2] = pack_bf16(h1[2 * kt + 1][0], h1[2 * kt + 1][1]);
+        ak[3] = pack_bf16(h1[2 * kt + 1][2], h1[2 * kt + 1][3]);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            unsigned b[2];
+            load_b(P.W2, kHid, kHid, nt * 8, kt * 16, lane, b);
+            mma_bf16(h2[nt], ak, b);
+        }
+    }
+    // layer 3: K = 64, N = 6 (one 8-column tile)
+    float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (cq < kOut) {
+        o[0] = P.b3[cq];
+        o[2] = P.b3[cq];
+    }
+    if (cq + 1 < kOut) {
+        o[1] = P.b3[cq + 1];
+        o[3] = P.b3[cq + 1];
+    }
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+        unsigned ak[4];
+        ak[0] = pack_bf16(fmaxf(h2[2 * kt][0], 0.0f), fmaxf(h2[2 * kt][1], 0.0f));
+        ak[1] = pack_bf16(fmaxf(h2[2 * kt][2], 0.0f), fmaxf(h2[2 * kt][3], 0.0f));
+        ak[2] = pack_bf16(fmaxf(h2[2 * kt + 1][0], 0.0f), fmaxf(h2[2 * kt + 1][1], 0.0f));
+        ak[3] = pack_bf16(fmaxf(h2[2 * kt + 1][2], 0.0f), fmaxf(h2[2 * kt + 1][3], 0.0f));
+        unsigned b[2];
+        load_b(P.W3, kOut, kHid, 0, kt * 16, lane, b);
+        mma_bf16(o, ak, b);
+    }
+    out_lo[0] = o[0];
+    out_lo[1] = o[1];
+    out_hi[0] = o[2];
+    out_hi[1] = o[3];
+}
+
+// Logits of n feature rows (n padded inside to multiples of 16): one warp per 16 rows.
+__global__ void k_mlp_infer(MlpDev P, const float *__restrict__ X, int64_t n, float *logits)
+{
+    __shared__ float xs[8][16][8];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + w) * 16;
+    if (row0 >= n) return;
+    for (int k = lane; k < 128; k += 32) {
+        const int rr = k / 8, cc = k % 8;
+        xs[w][rr][cc] = row0 + rr < n ? X[(row0 + rr) * 8 + cc] : 0.0f;
+    }
+    __syncwarp();
+    float lo[2], hi[2];
+    mlp_tile(P, xs[w], lane, lo, hi);
+    const int r = lane / 4, cq = 2 * (lane % 4);
+    for (int q = 0; q < 2; ++q) {
+        const int c = cq + q;
+        if (c >= kOut) continue;
+        if (row0 + r < n) logits[(row0 + r) * kOut + c] = lo[q];
+        if (row0 + r + 8 < n) logits[(row0 + r + 8) * kOut + c] = hi[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Learned-order near field (piecewise constant).
+//   select:  per tile entry (32 x 8 tiles as in the block engine): touching
+//            pairs are written from the touching table; disjoint pairs get
+//            features, the warp's 32 pairs go through the MLP on the tensor
+//            cores (two 16-row tiles), and the class (argmax; the most
+//            accurate class when the top softmax probability is below the
+//            confidence threshold) is stored per entry and counted.
+//   compact: a second walk writes (output position, a, b) records grouped by
+//            class (within a class in any order; each record owns its output).
+//   eval:    one warp per record with the class's rule.
+// ---------------------------------------------------------------------------
+constexpr int kClasses = 6;
+
+__device__ __forceinline__ void select_entry(const MeshView &m, const BlockLaunch &L,
+                                             const int64_t *prefix, int64_t tile, int *status,
+                                             int &a, int &b, int64_t &pos, int &state)
+{
+    // state: 0 = no entry, 1 = done (touching, written), 2 = regular pair
+    state = 0;
+    const BlockInfo bi = block_info(L, prefix, tile, status);
+    if (!bi.ok) return;
+    const int lr = threadIdx.x & 31, lc = threadIdx.x >> 5;
+    const int ntr = (bi.nr + kTile - 1) / kTile;
+    const int r = (bi.tile_in_blk % ntr) * kTile + lr;
+    const int c = (bi.tile_in_blk / ntr) * 8 + lc;
+    if (r >= bi.nr || c >= bi.nc) return;
+    a = L.row_idx[bi.r_lo + r];
+    b = L.col_idx[bi.c_lo + c];
+    if (a < 0 || a >= m.nt || b < 0 || b >= m.nt) {
+        set_status(status, BEM_ERR_INVALID_ARG);
+        return;
+    }
+    pos = bi.off + (int64_t)r + (int64_t)c * bi.nr;
+    const int4 va = __ldg(m.tvid + a), vb = __ldg(m.tvid + b);
+    if (touching(va, vb)) {
+        const int k = find_touching(m, a, b);
+        const double2 v = m.table[k];
+        if (L.kind == BEM_HELMHOLTZ_SLP) reinterpret_cast<double2 *>(L.out)[pos] = v;
+        else reinterpret_cast<double *>(L.out)[pos] = v.x;
+        state = 1;
+        return;
+    }
+    state = 2;
+}
+
+struct LearnedArgs {
+    MlpDev P;
+    const float *mean, *inv_std;
+    float conf;                  // confidence level of the cumulative class probability
+    unsigned char *cls;          // per tile slot: class (255 = no regular pair)
+    int *counts;                 // [kClasses]
+    int *fill;                   // [kClasses]
+    int64_t *offs;               // [kClasses + 1]
+    int4 *rec;                   // records: (pos lo, pos hi, a, b)
+};
+
+__global__ void __launch_bounds__(256) k_learned_select(MeshView m, BlockLaunch L,
+                                                        const int64_t *__restrict__ prefix,
+                                                        LearnedArgs A, int *status)
+{
+    __shared__ float xs[8][2][16][8];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        int a = 0, b = 0, state = 0;
+        int64_t pos = 0;
+        select_entry(m, L, prefix, tile, status, a, b, pos, state);
+        float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (state == 2) pair_features(m, a, b, L.kind, L.kappa, A.mean, A.inv_std, f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) xs[w][lane / 16][lane % 16][k] = f[k];
+        __syncwarp();
+        // logits of the warp's 32 rows: two 16-row tiles
+        float lo[2][2], hi[2][2];
+        mlp_tile(A.P, xs[w][0], lane, lo[0], hi[0]);
+        mlp_tile(A.P, xs[w][1], lane, lo[1], hi[1]);
+        __syncwarp();
+        // gather this lane's row logits: row = lane; tile = lane / 16, r = lane % 16
+        float logit[kClasses];
+        {
+            const int my_t = lane / 16, my_r = lane % 16;
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+                // class cc of row my_r in tile my_t lives in lane 4 * (my_r % 8) + cc / 2,
+                // register lo (rows < 8) or hi (rows >= 8), element cc % 2
+                const int src = 4 * (my_r % 8) + cc / 2;
+                float v0 = __shfl_sync(0xffffffffu, lo[0][cc % 2], src);
+                float v1 = __shfl_sync(0xffffffffu, hi[0][cc % 2], src);
+                float v2 = __shfl_sync(0xffffffffu, lo[1][cc % 2], src);
+                float v3 = __shfl_sync(0xffffffffu, hi[1][cc % 2], src);
+                const float v = my_t == 0 ? (my_r < 8 ? v0 : v1) : (my_r < 8 ? v2 : v3);
+                if (cc < kClasses) logit[cc] = v;
+            }
+        }
+        int cls = 255;
+        if (state == 2) {
+            float mx = logit[0];
+#pragma unroll
+            for (int cc = 1; cc < kClasses; ++cc) mx = fmaxf(mx, logit[cc]);
+            float e[kClasses], se = 0.0f;
+#pragma unroll
+            for (int cc = 0; cc < kClasses; ++cc) {
+                e[cc] = __expf(logit[cc] - mx);
+                se += e[cc];
+            }
+            // cheapest class whose cumulative probability reaches the confidence
+            cls = kClasses - 1;
+            float cum = 0.0f;
+#pragma unroll
+            for (int cc = 0; cc < kClasses; ++cc) {
+                cum += e[cc];
+                if (cum >= A.conf * se) {
+                    cls = cc;
+                    break;
+                }
+            }
+            atomicAdd(&A.counts[cls], 1);
+        }
+        A.cls[tile * 256 + threadIdx.x] = (unsigned char)cls;
+    }
+}
+
+__global__ void k_learned_offsets(LearnedArgs A)
+{
+    if (threadIdx.x == 0) {
+        int64_t s = 0;
+        for (int c = 0; c < kClasses; ++c) {
+            A.offs[c] = s;
+            s += A.counts[c];
+            A.fill[c] = 0;
+        }
+        A.offs[kClasses] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_learned_compact(MeshView m, BlockLaunch L,
+                                                         const int64_t *__restrict__ prefix,
+                                                         LearnedArgs A)
+{
+    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int cls = A.cls[tile * 256 + threadIdx.x];
+        if (cls >= kClasses) continue;
+        const BlockInfo bi = block_info(L, prefix, tile, nullptr);
+        const int lr = threadIdx.x & 31, lc = threadIdx.x >> 5;
+        const int ntr = (bi.nr + kTile - 1) / kTile;
+        const int r = (bi.tile_in_blk % ntr) * kTile + lr;
+        const int c = (bi.tile_in_blk / ntr) * 8 + lc;
+        const int64_t pos = bi.off + (int64_t)r + (int64_t)c * bi.nr;
+        const int k = atomicAdd(&A.fill[cls], 1);
+        A.rec[A.offs[cls] + k] = make_int4((int)(pos & 0xffffffff), (int)(pos >> 32),
+                                           L.row_idx[bi.r_lo + r], L.col_idx[bi.c_lo + c]);
+    }
+}
+
+// One warp per record of one class: disjoint pair with the class's 4D rule.
+template <int KIND, bool MIXED>
+__global__ void __launch_bounds__(256) k_learned_eval(MeshView m, const int4 *__restrict__ rec,
+                                                      const int64_t *__restrict__ offs, int cls,
+                                                      const double *__restrict__ rule,
+                                                      const float *__restrict__ rulef, int np,
+                                                      double kappa, void *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t lo = offs[cls], hi = offs[cls + 1];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = lo + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < hi; k += nw) {
+        const int4 R = rec[k];
+        const int64_t pos = (int64_t)(unsigned)R.x | ((int64_t)R.y << 32);
+        const int a = R.z, b = R.w;
+        double sr = 0.0, si = 0.0;
+        if (MIXED) {
+            TriF A, B;
+            load_trif(m.geomf, a, A);
+            load_trif(m.geomf, b, B);
+            float d0[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) d0[c] = dd_diff(A.vh[0][c], A.vl[0][c], B.vh[0][c], B.vl[0][c]);
+            Height H = {};
+            if (KIND == BEM_LAPLACE_DLP)
+                H = make_height(A.vh[0], A.vl[0], A.vh[1], A.vl[1], A.vh[2], A.vl[2], B.vh[0], B.vl[0],
+                                B.nh, B.nl);
+            float acc = 0.0f;
+            for (int p = lane; p < np; p += 32) {
+                const float x1 = __ldg(rulef + p), x2 = __ldg(rulef + np + p),
+                            y1 = __ldg(rulef + 2 * np + p), y2 = __ldg(rulef + 3 * np + p),
+                            w = __ldg(rulef + 4 * np + p);
+                const float dx = fmaf(x1, A.e1[0], fmaf(x2, A.e2[0], d0[0])) - fmaf(y1, B.e1[0], y2 * B.e2[0]);
+                const float dy = fmaf(x1, A.e1[1], fmaf(x2, A.e2[1], d0[1])) - fmaf(y1, B.e1[1], y2 * B.e2[1]);
+                const float dz = fmaf(x1, A.e1[2], fmaf(x2, A.e2[2], d0[2])) - fmaf(y1, B.e1[2], y2 * B.e2[2]);
+                const float dn = KIND == BEM_LAPLACE_DLP ? height_at(H, x1, x2) : 0.0f;
+                acc = fmaf(w, kvalf<KIND>(dx, dy, dz, dn), acc);
+            }
+            acc = warp_sumf(acc);
+            sr = (double)acc * (double)A.sg * (double)B.sg * kInv4Pi;
+        } else {
+            Tri A, B;
+            load_tri(m.geom, a, A);
+            load_tri(m.geom, b, B);
+            double e1a[3], e2a[3], e1b[3], e2b[3], d0[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                e1a[c] = A.v[1][c] - A.v[0][c];
+                e2a[c] = A.v[2][c] - A.v[1][c];
+                e1b[c] = B.v[1][c] - B.v[0][c];
+                e2b[c] = B.v[2][c] - B.v[1][c];
+                d0[c] = A.v[0][c] - B.v[0][c];
+            }
+            double pr = 0.0, pi = 0.0;
+            for (int p = lane; p < np; p += 32) {
+                const double x1 = __ldg(rule + p), x2 = __ldg(rule + np + p), y1 = __ldg(rule + 2 * np + p),
+                             y2 = __ldg(rule + 3 * np + p), w = __ldg(rule + 4 * np + p);
+                const double dx = d0[0] + x1 * e1a[0] + x2 * e2a[0] - y1 * e1b[0] - y2 * e2b[0];
+                const double dy = d0[1] + x1 * e1a[1] + x2 * e2a[1] - y1 * e1b[1] - y2 * e2b[1];
+                const double dz = d0[2] + x1 * e1a[2] + x2 * e2a[2] - y1 * e1b[2] - y2 * e2b[2];
+                double kr, ki;
+                kval<KIND>(dx, dy, dz, B.n, kappa, kr, ki);
+                pr += w * kr;
+                pi += w * ki;
+            }
+            pr = warp_sum(pr);
+            if (KIND == BEM_HELMHOLTZ_SLP) pi = warp_sum(pi);
+            const double sc = A.sg * B.sg * kInv4Pi;
+            sr = pr * sc;
+            si = pi * sc;
+        }
+        if (lane == 0) {
+            if (KIND == BEM_HELMHOLTZ_SLP) reinterpret_cast<double2 *>(out)[pos] = make_double2(sr, si);
+            else reinterpret_cast<double *>(out)[pos] = sr;
+        }
+    }
+}
+
+}  // namespace bem
+
+// ---------------------------------------------------------------------------
+// Host side: the model object and its C entry points
+// ---------------------------------------------------------------------------
+using namespace bem;
+
+struct bem_mlp {
+    int device;
+    float *params = nullptr, *grads = nullptr, *m1 = nullptr, *m2 = nullptr;
+    __nv_bfloat16 *pbf = nullptr;
+    float *norm = nullptr;     // mean[8], inv_std[8]
+    int64_t step = 0;
+    // training scratch
+    int64_t cap = 0;
+    float *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *z3 = nullptr, *dz3 = nullptr,
+          *dz2 = nullptr, *dz1 = nullptr, *loss = nullptr, *loss_sum = nullptr;
+};
+
+namespace {
+
+void mlp_free_scratch(bem_mlp *m)
+{
+    for (float *p : {m->z1, m->h1, m->z2, m->h2, m->z3, m->dz3, m->dz2, m->dz1, m->loss})
+        cudaFree(p);
+    m->z1 = m->h1 = m->z2 = m->h2 = m->z3 = m->dz3 = m->dz2 = m->dz1 = m->loss = nullptr;
+    m->cap = 0;
+}
+
+cudaError_t mlp_scratch(bem_mlp *m, int64_t n)
+{
+    if (n <= m->cap) return cudaSuccess;
+    mlp_free_scratch(m);
+    cudaError_t e = cudaSuccess;
+    auto al = [&](float **p, int64_t cnt) {
+        if (e == cudaSuccess) e = cudaMalloc((void **)p, sizeof(float) * std::max<int64_t>(1, cnt));
+    };
+    al(&m->z1, n * kHid);
+    al(&m->h1, n * kHid);
+    al(&m->z2, n * kHid);
+    al(&m->h2, n * kHid);
+    al(&m->z3, n * kOut);
+    al(&m->dz3, n * kOut);
+    al(&m->dz2, n * kHid);
+    al(&m->dz1, n * kHid);
+    al(&m->loss, n);
+    if (e == cudaSuccess) m->cap = n;
+    return e;
+}
+
+unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// forward (training precision) + loss + gradients into m->grads
+cudaError_t mlp_forward_backward(bem_mlp *m, const float *X, const int32_t *y, int n, cudaStream_t st)
+{
+    cudaError_t e = mlp_scratch(m, n);
+    if (e != cudaSuccess) return e;
+    const float *P = m->params;
+    float *G = m->grads;
+    k_dense<<<nblk((int64_t)n * kHid), 256, 0, st>>>(X, n, kIn, P + kOffW1, P + kOffB1, kHid, m->z1, m->h1);
+    k_dense<<<nblk((int64_t)n * kHid), 256, 0, st>>>(m->h1, n, kHid, P + kOffW2, P + kOffB2, kHid, m->z2, m->h2);
+    k_dense<<<nblk((int64_t)n * kOut), 256, 0, st>>>(m->h2, n, kHid, P + kOffW3, P + kOffB3, kOut, m->z3, nullptr);
+    k_softmax_ce<<<nblk(n), 256, 0, st>>>(m->z3, y, n, m->dz3, m->loss);
+    k_sum_fixed<<<1, 256, 0, st>>>(m->loss, n, m->loss_sum);
+    k_weight_grad<<<nblk(kOut * kHid + kOut), 256, 0, st>>>(m->dz3, m->h2, n, kOut, kHid, G + kOffW3, G + kOffB3);
+    k_back_act<<<nblk((int64_t)n * kHid), 256, 0, st>>>(m->dz3, P + kOffW3, m->z2, n, kOut, kHid, m->dz2);
+    k_weight_grad<<<nblk(kHid * kHid + kHid), 256, 0, st>>>(m->dz2, m->h1, n, kHid, kHid, G + kOffW2, G + kOffB2);
+    k_back_act<<<nblk((int64_t)n * kHid), 256, 0, st>>>(m->dz2, P + kOffW2, m->z1, n, kHid, kHid, m->dz1);
+    k_weight_grad<<<nblk(kHid * kIn + kHid), 256, 0, st>>>(m->dz1, X, n, kHid, kIn, G + kOffW1, G + kOffB1);
+    return cudaGetLastError();
+}
+
+MlpDev mlp_dev(const bem_mlp *m)
+{
+    MlpDev d;
+    d.W1 = m->pbf + kOffW1;
+    d.W2 = m->pbf + kOffW2;
+    d.W3 = m->pbf + kOffW3;
+    d.b1 = m->params + kOffB1;
+    d.b2 = m->params + kOffB2;
+    d.b3 = m->params + kOffB3;
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bem_mlp_create(bem_ctx *ctx, uint64_t seed, bem_mlp **out)
+{
+    if (!ctx || !out) return BEM_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    bem_mlp *m = new bem_mlp();
+    m->device = ctx->device;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    al((void **)&m->params, sizeof(float) * kNParams);
+    al((void **)&m->grads, sizeof(float) * kNParams);
+    al((void **)&m->m1, sizeof(float) * kNParams);
+    al((void **)&m->m2, sizeof(float) * kNParams);
+    al((void **)&m->pbf, sizeof(__nv_bfloat16) * kNParams);
+    al((void **)&m->norm, sizeof(float) * 16);
+    al((void **)&m->loss_sum, sizeof(float));
+    if (e != cudaSuccess) {
+        delete m;
+        return api_cuda_fail(ctx, e, "cudaMalloc(mlp)");
+    }
+    // He-style uniform init from a splitmix64 stream
+    std::vector<float> h(kNParams, 0.0f);
+    uint64_t s = seed;
+    auto next = [&]() {
+        s += 0x9E3779B97F4A7C15ull;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    auto fill = [&](int off, int cnt, int fan_in) {
+        const double a = std::sqrt(6.0 / fan_in);
+        for (int k = 0; k < cnt; ++k) h[off + k] = (float)((2.0 * next() - 1.0) * a);
+    };
+    fill(kOffW1, kHid * kIn, kIn);
+    fill(kOffW2, kHid * kHid, kHid);
+    fill(kOffW3, kOut * kHid, kHid);
+    std::vector<float> norm(16, 0.0f);
+    for (int k = 0; k < 8; ++k) norm[8 + k] = 1.0f;
+    cudaMemcpy(m->params, h.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice);
+    cudaMemset(m->m1, 0, sizeof(float) * kNParams);
+    cudaMemset(m->m2, 0, sizeof(float) * kNParams);
+    cudaMemcpy(m->norm, norm.data(), sizeof(float) * 16, cudaMemcpyHostToDevice);
+    k_to_bf16<<<nblk(kNParams), 256>>>(m->params, kNParams, m->pbf);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        delete m;
+        return api_cuda_fail(ctx, e, "mlp init");
+    }
+    *out = m;
+    return BEM_OK;
+}
+
+int bem_mlp_destroy(bem_ctx *ctx, bem_mlp *m)
+{
+    if (!ctx || !m) return BEM_ERR_INVALID_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    mlp_free_scratch(m);
+    for (void *p : {(void *)m->params, (void *)m->grads, (void *)m->m1, (void *)m->m2, (void *)m->pbf,
+                    (void *)m->norm, (void *)m->loss_sum})
+        cudaFree(p);
+    delete m;
+    return BEM_OK;
+}
+
+int bem_mlp_num_params(void) { return kNParams; }
+
+int bem_mlp_set_params(bem_ctx *ctx, bem_mlp *m, const float *host_params, const float *host_norm)
+{
+    if (!ctx || !m) return BEM_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    if (host_params) e = cudaMemcpy(m->params, host_params, sizeof(float) * kNParams, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && host_norm) e = cudaMemcpy(m->norm, host_norm, sizeof(float) * 16, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "mlp set");
+    k_to_bf16<<<nblk(kNParams), 256, 0, ctx->stream>>>(m->params, kNParams, m->pbf);
+    return BEM_OK;
+}
+
+int bem_mlp_get_params(bem_ctx *ctx, bem_mlp *m, float *host_params, float *host_norm)
+{
+    if (!ctx || !m) return BEM_ERR_INVALID_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    cudaError_t e = cudaSuccess;
+    if (host_params) e = cudaMemcpy(host_params, m->params, sizeof(float) * kNParams, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && host_norm) e = cudaMemcpy(host_norm, m->norm, sizeof(float) * 16, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "mlp get");
+    return BEM_OK;
+}
+
+int bem_mlp_gradients(bem_ctx *ctx, bem_mlp *m, const float *X, const int32_t *y, int32_t n,
+                      float *grads, float *loss)
+{
+    if (!ctx || !m || !X || !y || n < 1) return BEM_ERR_INVALID_ARG;
+    cudaError_t e = mlp_forward_backward(m, X, y, n, ctx->stream);
+    if (e == cudaSuccess && grads)
+        e = cudaMemcpyAsync(grads, m->grads, sizeof(float) * kNParams, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess && loss) {
+        float s = 0.0f;
+        e = cudaMemcpyAsync(&s, m->loss_sum, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        *loss = s / (float)n;
+    }
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "mlp gradients");
+    return BEM_OK;
+}
+
+int bem_mlp_train_step(bem_ctx *ctx, bem_mlp *m, const float *X, const int32_t *y, int32_t n,
+                       float lr, float *loss)
+{
+    if (!ctx || !m || !X || !y || n < 1) return BEM_ERR_INVALID_ARG;
+    cudaError_t e = mlp_forward_backward(m, X, y, n, ctx->stream);
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "mlp step");
+    m->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - std::pow(b1, (float)m->step), c2 = 1.0f - std::pow(b2, (float)m->step);
+    k_adam<<<nblk(kNParams), 256, 0, ctx->stream>>>(m->params, m->grads, m->m1, m->m2, kNParams, lr,
+                                                    b1, b2, 1e-8f, c1, c2);
+    k_to_bf16<<<nblk(kNParams), 256, 0, ctx->stream>>>(m->params, kNParams, m->pbf);
+    if (loss) {
+        float s = 0.0f;
+        e = cudaMemcpyAsync(&s, m->loss_sum, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        *loss = s / (float)n;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "mlp step");
+    return BEM_OK;
+}
+
+int bem_mlp_infer(bem_ctx *ctx, bem_mlp *m, const float *X, int64_t n, float *logits)
+{
+    if (!ctx || !m || (n > 0 && (!X || !logits)) || n < 0) return BEM_ERR_INVALID_ARG;
+    if (n == 0) return BEM_OK;
+    const int64_t tiles = (n + 15) / 16;
+    k_mlp_infer<<<(unsigned)((tiles + 7) / 8), 256, 0, ctx->stream>>>(mlp_dev(m), X, n, logits);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "mlp infer");
+    return BEM_OK;
+}
+
+int bem_set_order_model(bem_ctx *ctx, bem_mlp *m, float confidence)
+{
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (m && !(confidence >= 0.0f && confidence <= 1.0f))
+        return api_fail(ctx, BEM_ERR_INVALID_ARG, "confidence must be in [0, 1]");
+    ctx->order_model = m;
+    ctx->order_conf = confidence;
+    return BEM_OK;
+}
+
+int bem_learned_counts(bem_ctx *ctx, int64_t *counts)
+{
+    if (!ctx || !counts) return BEM_ERR_INVALID_ARG;
+    for (int c = 0; c < kClasses; ++c) counts[c] = ctx->learned_counts[c];
+    return BEM_OK;
+}
+
+int bem_pair_features(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel, bem_mlp *m,
+                      const int32_t *a, const int32_t *b, int64_t n, float *X)
+{
+    if (!ctx || !kernel || n < 0) return BEM_ERR_INVALID_ARG;
+    auto it = ctx->meshes.find(mesh_id);
+    if (it == ctx->meshes.end()) return api_fail(ctx, BEM_ERR_INVALID_ARG, "unknown mesh id");
+    if (it->second->v.basis != BEM_P0) return api_fail(ctx, BEM_ERR_UNSUPPORTED, "pair features need a P0 mesh");
+    if (n == 0) return BEM_OK;
+    if (!a || !b || !X) return api_fail(ctx, BEM_ERR_INVALID_ARG, "null pointer");
+    static float *ident = nullptr;   // mean 0, inv_std 1 when no model is given
+    const float *mean, *inv;
+    if (m) {
+        mean = m->norm;
+        inv = m->norm + 8;
+    } else {
+        if (!ident) {
+            std::vector<float> h(16, 0.0f);
+            for (int k = 0; k < 8; ++k) h[8 + k] = 1.0f;
+            cudaMalloc((void **)&ident, 16 * sizeof(float));
+            cudaMemcpy(ident, h.data(), 16 * sizeof(float), cudaMemcpyHostToDevice);
+        }
+        mean = ident;
+        inv = ident + 8;
+    }
+    k_features<<<nblk(n), 256, 0, ctx->stream>>>(it->second->v, a, b, n, kernel->kind, kernel->kappa,
+                                                mean, inv, X);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "features");
+    return BEM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned near-field job (called by bem_near_field for order_mode LEARNED;
+// the touching table and the tile prefix sums are already on the stream).
+// ---------------------------------------------------------------------------
+namespace bem {
+
+// the classes' regular rules: (rule, q)
+static const int kClassRule[kClasses][2] = {{BEM_RULE_DUFFY, 2}, {BEM_RULE_TRI7, 1},
+                                            {BEM_RULE_DUFFY, 4}, {BEM_RULE_DUFFY, 5},
+                                            {BEM_RULE_DUFFY, 6}, {BEM_RULE_DUFFY, 8}};
+
+int run_learned_p0(bem_ctx *ctx, const MeshView &mv, const BlockLaunch &L, const int64_t *prefix,
+                   int precision)
+{
+    bem_mlp *model = ctx->order_model;
+    if (!model) return api_fail(ctx, BEM_ERR_INVALID_ARG, "order_mode LEARNED needs bem_set_order_model");
+    // the number of tiles sizes the scratch: one read back per call
+    int64_t tiles = 0;
+    cudaError_t e = cudaMemcpyAsync(&tiles, prefix + (L.n_blocks - 1), sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned: tile count");
+    const int64_t slots = std::max<int64_t>(1, tiles * 256);
+    if (slots > ctx->learned_cap) {
+        cudaFree(ctx->learned_cls);
+        cudaFree(ctx->learned_rec);
+        ctx->learned_cls = nullptr;
+        ctx->learned_rec = nullptr;
+        ctx->learned_cap = 0;
+        e = cudaMalloc((void **)&ctx->learned_cls, slots);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->learned_rec, slots * sizeof(int4));
+        if (e != cudaSuccess) return api_cuda_fail(ctx, e, "cudaMalloc(learned scratch)");
+        ctx->learned_cap = slots;
+    }
+    if (!ctx->learned_small) {
+        e = cudaMalloc((void **)&ctx->learned_small, 64 * sizeof(int64_t));
+        if (e != cudaSuccess) return api_cuda_fail(ctx, e, "cudaMalloc(learned counters)");
+    }
+    LearnedArgs A;
+    A.P = mlp_dev(model);
+    A.mean = model->norm;
+    A.inv_std = model->norm + 8;
+    A.conf = ctx->order_conf;
+    A.cls = ctx->learned_cls;
+    A.counts = reinterpret_cast<int *>(ctx->learned_small);
+    A.fill = A.counts + 8;
+    A.offs = ctx->learned_small + 8;
+    A.rec = reinterpret_cast<int4 *>(ctx->learned_rec);
+    cudaMemsetAsync(A.counts, 0, 16 * sizeof(int), ctx->stream);
+    const int grid = ctx->num_sms * 8;
+    k_learned_select<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A, ctx->status);
+    k_learned_offsets<<<1, 32, 0, ctx->stream>>>(A);
+    k_learned_compact<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A);
+    const bool mixed = precision == BEM_MIXED && L.kind != BEM_HELMHOLTZ_SLP;
+    for (int c = 0; c < kClasses; ++c) {
+        Rule4D r;
+        int rc = api_get_rule4(ctx, kRegular, kClassRule[c][0], kClassRule[c][1], r);
+        if (rc) return rc;
+        switch (L.kind) {
+        case BEM_LAPLACE_SLP:
+            if (mixed) k_learned_eval<BEM_LAPLACE_SLP, true><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+            else k_learned_eval<BEM_LAPLACE_SLP, false><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+            break;
+        case BEM_LAPLACE_DLP:
+            if (mixed) k_learned_eval<BEM_LAPLACE_DLP, true><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+            else k_learned_eval<BEM_LAPLACE_DLP, false><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+            break;
+        default:
+            k_learned_eval<BEM_HELMHOLTZ_SLP, false><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+        }
+    }
+    // class counts of this call (for reports): read after the launches
+    int counts[8] = {0};
+    e = cudaMemcpyAsync(counts, A.counts, 8 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned path");
+    for (int c = 0; c < kClasses; ++c) ctx->learned_counts[c] = counts[c];
+    return BEM_OK;
+}
+
+}  // namespace bem

@@ -179,12 +179,27 @@ bool make_rule4d_host(int cas, int regular_rule, int q, std::vector<double> &soa
 {
     std::vector<Pt> pts;
     if (cas == kRegular) {
-        Rule2D r;
-        if (!make_rule2d(regular_rule, q, r)) return false;
-        for (int i = 0; i < r.np; ++i)
-            for (int j = 0; j < r.np; ++j)
-                pts.push_back(Pt{r.s[i], r.t[i], r.s[j], r.t[j], r.w[i] * r.w[j],
-                                 r.s[i] - r.s[j], r.t[i] - r.t[j]});
+        // 2D rule on D (any Duffy order here; the block engine's Rule2D holds <= 25 points)
+        std::vector<double> S, T, W;
+        if (regular_rule == BEM_RULE_TRI7) {
+            Rule2D r;
+            make_rule2d(BEM_RULE_TRI7, 1, r);
+            S.assign(r.s, r.s + r.np);
+            T.assign(r.t, r.t + r.np);
+            W.assign(r.w, r.w + r.np);
+        } else {
+            std::vector<double> g, gw;
+            if (regular_rule != BEM_RULE_DUFFY || !gauss_legendre_unit(q, g, gw)) return false;
+            for (int i = 0; i < q; ++i)
+                for (int j = 0; j < q; ++j) {
+                    S.push_back(g[i]);
+                    T.push_back(g[i] * g[j]);
+                    W.push_back(gw[i] * gw[j] * g[i]);
+                }
+        }
+        for (size_t i = 0; i < S.size(); ++i)
+            for (size_t j = 0; j < S.size(); ++j)
+                pts.push_back(Pt{S[i], T[i], S[j], T[j], W[i] * W[j], S[i] - S[j], T[i] - T[j]});
     } else {
         std::vector<double> g, gw;
         if (!gauss_legendre_unit(q, g, gw)) return false;

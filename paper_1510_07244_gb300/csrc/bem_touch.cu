@@ -1,0 +1,120 @@
+// Touching-pair kernels (Sauter-Schwab rules, Section 2.2): one warp per pair,
+// single-mesh and batched forms, FP64 and the mixed-form common-vertex kernel.
+#include <cuda_runtime.h>
+
+#include "bem_device.cuh"
+
+namespace bem {
+
+template <int KIND, int BASIS, int CAS>
+__global__ void __launch_bounds__(256) k_touching(MeshView m, const int *__restrict__ list,
+                                                  int64_t n, const double *__restrict__ rule,
+                                                  int np, double kappa)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= n) return;
+    touch_pair<KIND, BASIS, CAS>(m, __ldg(list + wid), rule, np, kappa, threadIdx.x & 31);
+}
+
+// Batched: items[k] = (job, touching index) over many meshes / kernels.
+template <int KIND, int BASIS, int CAS>
+__global__ void __launch_bounds__(256) k_touching_batch(const TouchJob *__restrict__ jobs,
+                                                        const int2 *__restrict__ items, int64_t n,
+                                                        const double *__restrict__ rule, int np)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= n) return;
+    const int2 it = items[wid];
+    touch_pair<KIND, BASIS, CAS>(jobs[it.x].m, it.y, rule, np, jobs[it.x].kappa, threadIdx.x & 31);
+}
+
+template <int KIND, int BASIS>
+__global__ void __launch_bounds__(256) k_touching_vertex_f32(MeshView m, const int *__restrict__ list,
+                                                             int64_t n, const float *__restrict__ rule,
+                                                             int np)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= n) return;
+    touch_vertex_f32<KIND, BASIS>(m, __ldg(list + wid), rule, np, threadIdx.x & 31);
+}
+
+template <int KIND, int BASIS>
+__global__ void __launch_bounds__(256) k_touching_vertex_f32_batch(const TouchJob *__restrict__ jobs,
+                                                                   const int2 *__restrict__ items,
+                                                                   int64_t n,
+                                                                   const float *__restrict__ rule,
+                                                                   int np)
+{
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (wid >= n) return;
+    const int2 it = items[wid];
+    touch_vertex_f32<KIND, BASIS>(jobs[it.x].m, it.y, rule, np, threadIdx.x & 31);
+}
+
+cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
+                            const Rule4D &rule, int kind, double kappa, int mixed, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n + 7) / 8);
+    const bool p1 = m.basis == BEM_P1;
+    if (mixed && cas == kVertex && kind != BEM_HELMHOLTZ_SLP && rule.f) {
+        if (kind == BEM_LAPLACE_SLP) {
+            if (p1) k_touching_vertex_f32<BEM_LAPLACE_SLP, BEM_P1><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
+            else k_touching_vertex_f32<BEM_LAPLACE_SLP, BEM_P0><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
+        } else {
+            if (p1) k_touching_vertex_f32<BEM_LAPLACE_DLP, BEM_P1><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
+            else k_touching_vertex_f32<BEM_LAPLACE_DLP, BEM_P0><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
+        }
+        return cudaGetLastError();
+    }
+#define BEM_TOUCH(K, B, C) k_touching<K, B, C><<<blocks, 256, 0, st>>>(m, list, n, rule.d, rule.n, kappa)
+#define BEM_TOUCH_CASE(K, B)                                   \
+    do {                                                       \
+        if (cas == kIdentical) BEM_TOUCH(K, B, kIdentical);    \
+        else if (cas == kEdge) BEM_TOUCH(K, B, kEdge);         \
+        else BEM_TOUCH(K, B, kVertex);                         \
+    } while (0)
+    switch (kind) {
+    case BEM_LAPLACE_SLP: if (p1) BEM_TOUCH_CASE(BEM_LAPLACE_SLP, BEM_P1); else BEM_TOUCH_CASE(BEM_LAPLACE_SLP, BEM_P0); break;
+    case BEM_LAPLACE_DLP: if (p1) BEM_TOUCH_CASE(BEM_LAPLACE_DLP, BEM_P1); else BEM_TOUCH_CASE(BEM_LAPLACE_DLP, BEM_P0); break;
+    default: if (p1) BEM_TOUCH_CASE(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TOUCH_CASE(BEM_HELMHOLTZ_SLP, BEM_P0); break;
+    }
+#undef BEM_TOUCH_CASE
+#undef BEM_TOUCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int cas, int mixed,
+                                  const int2 *items, int64_t n, const Rule4D &rule, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n + 7) / 8);
+    const bool p1 = basis == BEM_P1;
+    if (mixed && cas == kVertex && kind != BEM_HELMHOLTZ_SLP && rule.f) {
+        if (kind == BEM_LAPLACE_SLP) {
+            if (p1) k_touching_vertex_f32_batch<BEM_LAPLACE_SLP, BEM_P1><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
+            else k_touching_vertex_f32_batch<BEM_LAPLACE_SLP, BEM_P0><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
+        } else {
+            if (p1) k_touching_vertex_f32_batch<BEM_LAPLACE_DLP, BEM_P1><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
+            else k_touching_vertex_f32_batch<BEM_LAPLACE_DLP, BEM_P0><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
+        }
+        return cudaGetLastError();
+    }
+#define BEM_TB(K, B, C) k_touching_batch<K, B, C><<<blocks, 256, 0, st>>>(jobs, items, n, rule.d, rule.n)
+#define BEM_TB_CASE(K, B)                                  \
+    do {                                                   \
+        if (cas == kIdentical) BEM_TB(K, B, kIdentical);   \
+        else if (cas == kEdge) BEM_TB(K, B, kEdge);        \
+        else BEM_TB(K, B, kVertex);                        \
+    } while (0)
+    switch (kind) {
+    case BEM_LAPLACE_SLP: if (p1) BEM_TB_CASE(BEM_LAPLACE_SLP, BEM_P1); else BEM_TB_CASE(BEM_LAPLACE_SLP, BEM_P0); break;
+    case BEM_LAPLACE_DLP: if (p1) BEM_TB_CASE(BEM_LAPLACE_DLP, BEM_P1); else BEM_TB_CASE(BEM_LAPLACE_DLP, BEM_P0); break;
+    default: if (p1) BEM_TB_CASE(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TB_CASE(BEM_HELMHOLTZ_SLP, BEM_P0); break;
+    }
+#undef BEM_TB_CASE
+#undef BEM_TB
+    return cudaGetLastError();
+}
+
+}  // namespace bem

@@ -59,3 +59,16 @@ def test_library_rules_match_oracle(oracle_mod, case, q, rule):
 def test_library_rule_rejects_bad_orders():
     with pytest.raises(pkg.BemError):
         pkg.bem_rule_points("edge", 0)
+
+
+@pytest.mark.parametrize("q", [1, 5, 10])
+def test_library_high_order_regular_rule(q):
+    """Duffy orders beyond the block engine's product-rule limit (used by pivot
+    entries and by the order model's reference values)."""
+    r = pkg.bem_rule_points("regular", q)
+    assert len(r["w"]) == q ** 4
+    for a, b, c, d in itertools.product(range(4), repeat=4):
+        if a + b + 1 > 2 * q - 1 or c + d + 1 > 2 * q - 1:
+            continue
+        got = np.sum(r["w"] * r["x1"] ** a * r["x2"] ** b * r["y1"] ** c * r["y2"] ** d)
+        assert abs(got - tri_moment(a, b) * tri_moment(c, d)) < 1e-14
