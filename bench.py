@@ -91,6 +91,31 @@ def kernel_flops(w, counts, stats, precision):
     return {k: (f, p, PEAK_FP32 if p == "fp32" else PEAK_FP64) for k, (f, p) in out.items()}
 
 
+def block_costs(bs):
+    """Cost of each block of a block set: its number of entries."""
+    rs = np.diff(bs.row_ptr)[bs.blk_row]
+    cs = np.diff(bs.col_ptr)[bs.blk_col]
+    return (rs * cs).astype(np.int64)
+
+
+def shard_range(bs, rank, ws):
+    """This rank's contiguous block range (lo, hi) of a block set (strong scaling)."""
+    import paper_1510_07244_gb300 as pkg
+    b = pkg.bem_shard_blocks(block_costs(bs), ws)
+    return int(b[rank]), int(b[rank + 1])
+
+
+def reduce_over_ranks(x, op, device=None):
+    """x reduced over all ranks (MAX or SUM); x itself when not distributed."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX if op == "max" else tdist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -174,7 +199,9 @@ def pair_counts(w):
             "far_regular_pairs": far_reg, "far_touching_lookups": far_touch}
 
 
-def build_device_inputs(torch, pkg, w, dev):
+def build_device_inputs(torch, pkg, w, dev, ranges=None):
+    """Device copies of the block sets; with ranges = {"near": (lo, hi), ...} only
+    those blocks (outputs keep the full layout, so shards write disjoint parts)."""
     def t32(a):
         return torch.as_tensor(np.ascontiguousarray(a, np.int32)).to(dev)
 
@@ -183,9 +210,12 @@ def build_device_inputs(torch, pkg, w, dev):
 
     sets = {}
     for name, bs in (("near", w.near), ("far", w.far)):
+        lo, hi = ranges[name] if ranges else (0, len(bs.blk_row))
+        costs = block_costs(bs)[lo:hi]
         sets[name] = dict(row_ptr=t32(bs.row_ptr), row_idx=t32(bs.row_idx), col_ptr=t32(bs.col_ptr),
-                          col_idx=t32(bs.col_idx), blk_row=t32(bs.blk_row), blk_col=t32(bs.blk_col),
-                          blk_off=t64(bs.blk_off), n=bs.n_entries)
+                          col_idx=t32(bs.col_idx), blk_row=t32(bs.blk_row[lo:hi]),
+                          blk_col=t32(bs.blk_col[lo:hi]), blk_off=t64(bs.blk_off[lo:hi]),
+                          n=bs.n_entries, mine=int(costs.sum()))
     return sets
 
 
@@ -217,8 +247,13 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     ctx = pkg.Context(local, stream)
     mid = ctx.bem_mesh_upload(w.mesh.verts, w.mesh.tris, w.basis)
-    sets = build_device_inputs(torch, pkg, w, dev)
-    entries_per_step = len(w.operators) * (w.near.n_entries + w.far.n_entries)
+    ranges = None
+    if args.split and ws > 1:
+        ranges = {"near": shard_range(w.near, rank, ws), "far": shard_range(w.far, rank, ws)}
+    sets = build_device_inputs(torch, pkg, w, dev, ranges)
+    # entries this rank produces per step, and over all ranks
+    entries_per_step = len(w.operators) * (sets["near"]["mine"] + sets["far"]["mine"])
+    entries_all = reduce_over_ranks(entries_per_step, "sum", dev) if ws > 1 else entries_per_step
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     counts = pair_counts(w)
     stats = ctx.bem_mesh_info(mid)
@@ -257,11 +292,7 @@ def run_ours(args):
         ctx.bem_profile_enable(False)
         info = ctx.bem_plan_info(plan)
         ctx.bem_plan_destroy(plan)
-        total = float(sum(a.elapsed_time(b) for a, b in evs))
-        if ws > 1:
-            t = torch.tensor([total], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
+        total = reduce_over_ranks(float(sum(a.elapsed_time(b) for a, b in evs)), "max", dev)
         # kernels per replay: one per touching bucket, prefix + scan + engine per block bucket
         info["kernels_per_step"] = info["touch_launches"] + 3 * info["block_launches"]
         return total, prof, info
@@ -287,7 +318,7 @@ def run_ours(args):
         for op in w.operators:
             dt = torch.complex128 if op.kernel == "helmholtz_slp" else torch.float64
             for name in ("near", "far"):
-                o[(op.kernel, name)] = torch.empty(sets[name]["n"], dtype=dt, device=dev)
+                o[(op.kernel, name)] = torch.zeros(sets[name]["n"], dtype=dt, device=dev)
         return o
 
     outs64, outsmx = alloc_outs(), alloc_outs()
@@ -311,9 +342,10 @@ def run_ours(args):
             den = torch.where(den > 0, den, torch.ones_like(den))
             e = ((outsmx[(op.kernel, name)] - outs64[(op.kernel, name)]).abs() / den).max().item()
             maxerr = max(maxerr, e)
+    maxerr = reduce_over_ranks(maxerr, "max", dev)
     chosen_ok = maxerr <= 1e-6
-    value64 = entries_per_step * ws * args.fp64_steps / (ms64 / 1e3)
-    valuemx = entries_per_step * ws * args.steps / (msmx / 1e3)
+    value64 = entries_all * args.fp64_steps / (ms64 / 1e3)
+    valuemx = entries_all * args.steps / (msmx / 1e3)
     value = valuemx if chosen_ok else value64
     steps_used = args.steps if chosen_ok else args.fp64_steps
     total_ms = msmx if chosen_ok else ms64
@@ -367,7 +399,7 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / steps_used, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None,
+                "scaling": "strong" if ranges else "weak", "vs_baseline": None,
                 "dtype": "f32+f64 (mixed)" if chosen_ok else "f64", "data": "synthetic",
                 "config": {"workload": w.name, "triangles": w.mesh.nt, "vertices": w.mesh.nv,
                            "basis": w.basis, "operators": [o.kernel for o in w.operators],
@@ -478,6 +510,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds-per-step", type=float, default=4.0)
+    ap.add_argument("--split", action="store_true",
+                    help="under torchrun: shard one workload's blocks across the ranks (strong "
+                         "scaling) instead of one workload per rank (weak scaling)")
     ap.add_argument("--levels", type=int, default=5,
                     help="icosphere refinement levels (5 = the 20480-triangle workload; "
                          "smaller values only for profiling captures)")

@@ -284,6 +284,15 @@ int bem_plan_destroy(bem_ctx *ctx, bem_plan *plan);
 int bem_plan_info(bem_ctx *ctx, bem_plan *plan, int32_t *n_touch_launches,
                   int32_t *n_block_launches, int32_t *grid_mult, int32_t cap);
 
+/* ---- sharding (multi-GPU) ----------------------------------------------------
+ * Every matrix entry is independent (Section 3: the work lists need no
+ * exchange), so block lists shard across GPUs without communication.  Splits
+ * blocks 0..n_blocks-1 (HOST array cost[b] >= 0, e.g. quadrature points of
+ * the block) into n_shards contiguous ranges of nearly equal total cost:
+ * shard k owns blocks bounds[k] .. bounds[k+1]-1 (bounds: HOST, n_shards+1).
+ * Whole blocks, so every output block has one owner.  Needs no device. */
+int bem_shard_blocks(const int64_t *cost, int64_t n_blocks, int32_t n_shards, int64_t *bounds);
+
 /* ---- quadrature rules ------------------------------------------------------
  * Copies the library's 4D rule on D x D for a case (Section 2.2; case 0 =
  * disjoint pairs with regular_rule BEM_RULE_DUFFY / BEM_RULE_TRI7, 1 = common

@@ -30,7 +30,8 @@ EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_
            "bem_plan_create", "bem_plan_run", "bem_plan_destroy", "bem_plan_info",
            "bem_pivot_entries_absolute", "bem_mlp_create", "bem_mlp_destroy", "bem_mlp_num_params",
            "bem_mlp_set_params", "bem_mlp_get_params", "bem_mlp_gradients", "bem_mlp_train_step",
-           "bem_mlp_infer", "bem_pair_features", "bem_set_order_model", "bem_learned_counts"]
+           "bem_mlp_infer", "bem_pair_features", "bem_set_order_model", "bem_learned_counts",
+           "bem_shard_blocks"]
 ORDER_CLASSES = [("duffy", 2), ("tri7", 1), ("duffy", 4), ("duffy", 5), ("duffy", 6), ("duffy", 8)]
 ORDER_CLASS_POINTS = [16, 49, 256, 625, 1296, 4096]
 PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE = 1, 2, 4
@@ -120,6 +121,7 @@ def load():
     lib.bem_pair_features.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc), _vp, _vp, _vp,
                                       ctypes.c_int64, _vp]
     lib.bem_set_order_model.argtypes = [_vp, _vp, ctypes.c_float]
+    lib.bem_shard_blocks.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, _vp]
     lib.bem_learned_counts.argtypes = [_vp, P(ctypes.c_int64)]
     lib.bem_plan_create.argtypes = [_vp, P(bem_block_job), ctypes.c_int32, P(bem_block_job),
                                     ctypes.c_int32, ctypes.c_int32, P(_vp)]
@@ -154,6 +156,17 @@ def bem_rule_points(case: str, q: int, regular_rule: str = "duffy"):
     lib.bem_rule_points(CASES[case], RULES[regular_rule], q, out.ctypes.data_as(_vp), out.size)
     cols = out.reshape(7, n)
     return dict(zip(("x1", "x2", "y1", "y2", "w", "d1", "d2"), cols))
+
+
+def bem_shard_blocks(cost, n_shards: int) -> np.ndarray:
+    """Contiguous block ranges of nearly equal cost (host only): bounds (n_shards + 1)."""
+    c = np.ascontiguousarray(cost, np.int64)
+    bounds = np.zeros(n_shards + 1, np.int64)
+    rc = load().bem_shard_blocks(c.ctypes.data_as(_vp), len(c), int(n_shards),
+                                 bounds.ctypes.data_as(_vp))
+    if rc != BEM_OK:
+        raise BemError(rc, "bad shard arguments")
+    return bounds
 
 
 def kernel_desc(kind="laplace_slp", kappa=0.0) -> bem_kernel_desc:

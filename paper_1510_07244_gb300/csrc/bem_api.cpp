@@ -775,4 +775,27 @@ int64_t bem_rule_points(int32_t cas, int32_t regular_rule, int32_t q, double *ou
     return n;
 }
 
+int bem_shard_blocks(const int64_t *cost, int64_t n_blocks, int32_t n_shards, int64_t *bounds)
+{
+    if (!bounds || n_shards < 1 || n_blocks < 0 || (n_blocks > 0 && !cost)) return BEM_ERR_INVALID_ARG;
+    long double total = 0.0L;
+    for (int64_t b = 0; b < n_blocks; ++b) {
+        if (cost[b] < 0) return BEM_ERR_INVALID_ARG;
+        total += (long double)cost[b];
+    }
+    // shard k ends at the first block whose inclusive prefix reaches (k+1)/n of the total
+    bounds[0] = 0;
+    long double acc = 0.0L;
+    int64_t b = 0;
+    for (int k = 1; k < n_shards; ++k) {
+        const long double target = total * k / n_shards;
+        while (b < n_blocks && acc + (long double)cost[b] <= target) acc += (long double)cost[b++];
+        // take the block that crosses the target if that lands closer to it
+        if (b < n_blocks && target - acc > acc + (long double)cost[b] - target) acc += (long double)cost[b++];
+        bounds[k] = b;
+    }
+    bounds[n_shards] = n_blocks;
+    return BEM_OK;
+}
+
 }  // extern "C"

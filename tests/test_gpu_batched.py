@@ -140,3 +140,29 @@ def test_plan_p1_and_profile(env):
     ctx.bem_plan_destroy(plan)
     for m in mids:
         ctx.bem_mesh_free(m)
+
+
+def test_shards_reproduce_unsharded_run(env):
+    """Multi-GPU sharding rehearsed on one GPU: the block lists cut into three
+    cost-balanced shards, run one after another into one output, give the
+    unsharded FP64 result bit for bit (whole blocks, no exchange)."""
+    import torch
+    import bench
+    from synth.workloads import BlockSet
+    pkg, ctx = env
+    w = synth.workloads.config2(levels=3)
+    mid = ctx.bem_mesh_upload(w.mesh.verts, w.mesh.tris, w.basis)
+    for bs, call in ((w.near, ctx.bem_near_field), (w.far, ctx.bem_coupling_blocks)):
+        full = torch.zeros(bs.n_entries, dtype=torch.float64, device="cuda")
+        call([block_job(pkg, mid, bs, "laplace_dlp", 0.0, QUAD, full)])
+        sharded = torch.zeros_like(full)
+        bounds = pkg.bem_shard_blocks(bench.block_costs(bs), 3)
+        for k in range(3):
+            lo, hi = int(bounds[k]), int(bounds[k + 1])
+            part = BlockSet(bs.row_ptr, bs.row_idx, bs.col_ptr, bs.col_idx, bs.blk_row[lo:hi],
+                            bs.blk_col[lo:hi], bs.blk_off[lo:hi], bs.n_entries)
+            if hi > lo:
+                call([block_job(pkg, mid, part, "laplace_dlp", 0.0, QUAD, sharded)])
+        ctx.bem_sync()
+        assert torch.equal(full, sharded)
+    ctx.bem_mesh_free(mid)
