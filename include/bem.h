@@ -72,11 +72,13 @@ typedef struct {
  * default is 3 for disjoint pairs and 5 for the singular cases.
  *   regular_rule: BEM_RULE_DUFFY (q_regular^4 points) or BEM_RULE_TRI7
  *                 (7 x 7 = 49 points, q_regular ignored).
- *   precision:    BEM_FP64, or BEM_MIXED: for the Laplace kernels, disjoint and
- *                 common-vertex pairs in FP32 arithmetic (double-float set-up of
- *                 vertex differences and double-layer heights, compensated
- *                 sums); identical and common-edge pairs, Helmholtz pairs and
- *                 bem_pivot_entries stay FP64.
+ *   precision:    BEM_FP64, or BEM_MIXED: disjoint and common-vertex pairs in
+ *                 FP32 arithmetic (double-float set-up of vertex differences,
+ *                 double-layer heights and the Helmholtz reference phase
+ *                 kappa |c_a - c_b| of the centroids, compensated sums);
+ *                 identical and common-edge pairs stay FP64, and so do the
+ *                 disjoint Helmholtz pairs of the piecewise-linear basis and
+ *                 bem_pivot_entries.
  *   order_mode:   BEM_ORDER_FIXED (the orders above) or BEM_ORDER_LEARNED: for
  *                 bem_near_field on piecewise-constant meshes, every disjoint
  *                 pair gets the rule class the context's order model

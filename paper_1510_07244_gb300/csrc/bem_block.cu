@@ -273,7 +273,11 @@ cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const R
     case BEM_LAPLACE_DLP:
         return L.mixed ? block_kind<BEM_LAPLACE_DLP, true>(m, L, R, prefix, status, grid, st)
                        : block_kind<BEM_LAPLACE_DLP, false>(m, L, R, prefix, status, grid, st);
-    default: return block_kind<BEM_HELMHOLTZ_SLP, false>(m, L, R, prefix, status, grid, st);
+    default:
+        // the mixed Helmholtz form covers piecewise-constant pairs
+        return (L.mixed && m.basis == BEM_P0)
+                   ? block_kind<BEM_HELMHOLTZ_SLP, true>(m, L, R, prefix, status, grid, st)
+                   : block_kind<BEM_HELMHOLTZ_SLP, false>(m, L, R, prefix, status, grid, st);
     }
 }
 
@@ -346,7 +350,9 @@ cudaError_t launch_block_batch(const BatchJob *jobs, int n_jobs, const int64_t *
         return mixed ? batch_kind<BEM_LAPLACE_DLP, true>(jobs, n_jobs, job_end, basis, R, status, grid, st)
                      : batch_kind<BEM_LAPLACE_DLP, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
     default:
-        return batch_kind<BEM_HELMHOLTZ_SLP, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
+        return (mixed && basis == BEM_P0)
+                   ? batch_kind<BEM_HELMHOLTZ_SLP, true>(jobs, n_jobs, job_end, basis, R, status, grid, st)
+                   : batch_kind<BEM_HELMHOLTZ_SLP, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
     }
 }
 

@@ -225,6 +225,150 @@ __device__ __forceinline__ float kvalf(float dx, float dy, float dz, float dn)
     return dn * (ri * ri * ri);
 }
 
+// ---------------------------------------------------------------------------
+// Helmholtz in the mixed form.  exp(i kappa r) = exp(i kappa r0) exp(i kappa
+// (r - r0)) with r0 = the distance of the two centroids: r0, kappa r0 and its
+// reduction modulo 2 pi are formed in double-float arithmetic once per pair;
+// per point only the small offset r - r0 = ((2 d_c + e) . e) / (r + r0), with
+// e = (x - x_c) - (y - y_c) from centroid-relative offsets, is evaluated in
+// float, so the phase keeps ~1e-7 absolute accuracy for kappa r of order 10^2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void dd_add(float ah, float al, float bh, float bl, float &h, float &l)
+{
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e += al + bl;
+    h = s + e;
+    l = e - (h - s);
+}
+
+__device__ __forceinline__ void dd_mul(float ah, float al, float bh, float bl, float &h, float &l)
+{
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p) + fmaf(ah, bl, al * bh);
+    h = p + e;
+    l = e - (h - p);
+}
+
+// phase data of a pair: cos/sin of kappa r0 and the float quantities per point
+struct HelmPhase {
+    float dcx, dcy, dcz;   // centroid difference d_c (float)
+    float r0, r0sq;        // r0 and r0^2 (float)
+    float c0, s0;          // cos, sin of kappa r0
+    float kap;
+};
+
+__device__ __forceinline__ HelmPhase helm_phase(const TriF &A, const TriF &B, double kappa)
+{
+    // centroid difference in double-float: (sum of vertices of A - of B) / 3
+    float dh[3], dl[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float h = 0.0f, l = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dd_add(h, l, A.vh[k][c], A.vl[k][c], h, l);
+            dd_add(h, l, -B.vh[k][c], -B.vl[k][c], h, l);
+        }
+        // divide by 3: multiply by 1/3 in double-float
+        const float th = 0.333333343267f, tl = -9.93410748e-09f;
+        dd_mul(h, l, th, tl, dh[c], dl[c]);
+    }
+    // r0^2 = |d_c|^2 and r0 in double-float
+    float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float ph, pl;
+        dd_mul(dh[c], dl[c], dh[c], dl[c], ph, pl);
+        dd_add(sh, sl, ph, pl, sh, sl);
+    }
+    const float rh0 = sqrtf(sh);
+    // one Newton step in double-float: r = rh0 + (s - rh0^2) / (2 rh0)
+    float qh, ql;
+    dd_mul(rh0, 0.0f, rh0, 0.0f, qh, ql);
+    float dh2, dl2;
+    dd_add(sh, sl, -qh, -ql, dh2, dl2);
+    const float corr = (dh2 + dl2) / (2.0f * rh0);
+    float r0h, r0l;
+    two_sum(rh0, corr, r0h, r0l);
+    // kappa r0 in double-float, reduced modulo 2 pi
+    const float kh = (float)kappa, kl = (float)(kappa - (double)kh);
+    float ph, pl;
+    dd_mul(kh, kl, r0h, r0l, ph, pl);
+    const float n = rintf(ph * 0.159154943092f);
+    const float two_pi_h = 6.28318548202514648f, two_pi_l = -1.74845553e-07f;
+    float t = fmaf(-n, two_pi_h, ph);
+    t = fmaf(-n, two_pi_l, t) + pl;
+    HelmPhase P;
+    sincosf(t, &P.s0, &P.c0);
+    P.dcx = dh[0] + dl[0];
+    P.dcy = dh[1] + dl[1];
+    P.dcz = dh[2] + dl[2];
+    P.r0 = r0h + r0l;
+    P.r0sq = sh + sl;
+    P.kap = kh;
+    return P;
+}
+
+// exp(i kappa r) / r (times nothing else) at offset e = d - d_c
+__device__ __forceinline__ void helm_value(const HelmPhase &P, float ex, float ey, float ez,
+                                           float &re, float &im)
+{
+    const float q = fmaf(fmaf(2.0f, P.dcx, ex), ex,
+                         fmaf(fmaf(2.0f, P.dcy, ey), ey, fmaf(2.0f, P.dcz, ez) * ez));
+    const float r2 = P.r0sq + q;
+    const float ri = rsqrtf(r2);
+    const float delta = __fdividef(q, fmaf(r2, ri, P.r0));
+    float s, c;
+    __sincosf(P.kap * delta, &s, &c);
+    re = (P.c0 * c - P.s0 * s) * ri;
+    im = (P.s0 * c + P.c0 * s) * ri;
+}
+
+// Regular pair, piecewise constant, Helmholtz single layer, float.
+template <int NP>
+__device__ __forceinline__ void regular_p0_f32_helm(const TriF &A, const TriF &B, const Rule2D &R,
+                                                    double kappa, float &out_re, float &out_im)
+{
+    const HelmPhase P = helm_phase(A, B, kappa);
+    // centroid-relative offsets of the y points: y - y_c = (s - 2/3) e1 + (t - 1/3) e2
+    float yx[NP], yy[NP], yz[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const float a = R.sf[j] - 0.666666687f, b = R.tf[j] - 0.333333343f;
+        yx[j] = fmaf(a, B.e1[0], b * B.e2[0]);
+        yy[j] = fmaf(a, B.e1[1], b * B.e2[1]);
+        yz[j] = fmaf(a, B.e1[2], b * B.e2[2]);
+    }
+    float sr = 0.0f, si = 0.0f, cr = 0.0f, ci = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const float a = R.sf[i] - 0.666666687f, b = R.tf[i] - 0.333333343f;
+        const float xx = fmaf(a, A.e1[0], b * A.e2[0]);
+        const float xy = fmaf(a, A.e1[1], b * A.e2[1]);
+        const float xz = fmaf(a, A.e1[2], b * A.e2[2]);
+        float ir = 0.0f, ii = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            float kr, ki;
+            helm_value(P, xx - yx[j], xy - yy[j], xz - yz[j], kr, ki);
+            ir = fmaf(R.wf[j], kr, ir);
+            ii = fmaf(R.wf[j], ki, ii);
+        }
+        // compensated outer sums
+        float y = fmaf(R.wf[i], ir, -cr), t = sr + y;
+        cr = (t - sr) - y;
+        sr = t;
+        y = fmaf(R.wf[i], ii, -ci);
+        t = si + y;
+        ci = (t - si) - y;
+        si = t;
+    }
+    const float sc = A.sg * B.sg * (float)kInv4Pi;
+    out_re = sr * sc;
+    out_im = si * sc;
+}
+
 // Regular pair, piecewise constant, float (Laplace kernels).
 template <int KIND, int NP>
 __device__ __forceinline__ float regular_p0_f32(const TriF &A, const TriF &B, const Rule2D &R)
@@ -477,8 +621,10 @@ __device__ __forceinline__ void touch_pair(const MeshView &m, int idx, const dou
 // vectors only and keeps float precision down to the singular point.
 template <int KIND, int BASIS>
 __device__ __forceinline__ void touch_vertex_f32(const MeshView &m, int idx,
-                                                 const float *__restrict__ rule, int np, int lane)
+                                                 const float *__restrict__ rule, int np, int lane,
+                                                 float kappa = 0.0f)
 {
+    constexpr bool CPLX = KIND == BEM_HELMHOLTZ_SLP;
     const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);
     const int pc = __ldg(m.nb_perm + idx);
     const int *pa = c_perm[pc / 6], *pb = c_perm[pc % 6];
@@ -510,9 +656,9 @@ __device__ __forceinline__ void touch_vertex_f32(const MeshView &m, int idx,
     if (KIND == BEM_LAPLACE_DLP)
         H = make_height(ah[0], al[0], ah[1], al[1], ah[2], al[2], bh[0], bl[0], B.nh, B.nl);
     constexpr int NACC = BASIS == BEM_P0 ? 1 : 9;
-    float acc[NACC];
+    float acc[NACC], acci[NACC];
 #pragma unroll
-    for (int k = 0; k < NACC; ++k) acc[k] = 0.0f;
+    for (int k = 0; k < NACC; ++k) acc[k] = acci[k] = 0.0f;
     const float *X1 = rule, *X2 = rule + np, *Y1 = rule + 2 * np, *Y2 = rule + 3 * np,
                 *W = rule + 4 * np;   // columns 5, 6 (differences) are not needed here
     for (int p = lane; p < np; p += 32) {
@@ -522,35 +668,58 @@ __device__ __forceinline__ void touch_vertex_f32(const MeshView &m, int idx,
         const float dy = fmaf(x1, e1a[1], fmaf(x2, e2a[1], -fmaf(y1, e1b[1], y2 * e2b[1])));
         const float dz = fmaf(x1, e1a[2], fmaf(x2, e2a[2], -fmaf(y1, e1b[2], y2 * e2b[2])));
         const float dn = KIND == BEM_LAPLACE_DLP ? height_at(H, x1, x2) : 0.0f;
-        const float wk = w * kvalf<KIND>(dx, dy, dz, dn);
+        float wk, wki = 0.0f;
+        if (CPLX) {
+            // the pair shares a vertex: kappa r stays below kappa times two diameters
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = rsqrtf(r2);
+            float sn, cs;
+            sincosf(kappa * (r2 * ri), &sn, &cs);
+            wk = w * cs * ri;
+            wki = w * sn * ri;
+        } else {
+            wk = w * kvalf<KIND>(dx, dy, dz, dn);
+        }
         if (BASIS == BEM_P0) {
             acc[0] += wk;
+            if (CPLX) acci[0] += wki;
         } else {
             const float mx[3] = {1.0f, x1, x2}, my[3] = {1.0f, y1, y2};
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const float f = wk * mx[i];
+                const float f = wk * mx[i], fi = wki * mx[i];
 #pragma unroll
-                for (int j = 0; j < 3; ++j) acc[i * 3 + j] = fmaf(f, my[j], acc[i * 3 + j]);
+                for (int j = 0; j < 3; ++j) {
+                    acc[i * 3 + j] = fmaf(f, my[j], acc[i * 3 + j]);
+                    if (CPLX) acci[i * 3 + j] = fmaf(fi, my[j], acci[i * 3 + j]);
+                }
             }
         }
     }
 #pragma unroll
-    for (int k = 0; k < NACC; ++k) acc[k] = warp_sumf(acc[k]);
+    for (int k = 0; k < NACC; ++k) {
+        acc[k] = warp_sumf(acc[k]);
+        if (CPLX) acci[k] = warp_sumf(acci[k]);
+    }
     if (lane == 0) {
         const double scale = (double)A.sg * (double)B.sg * kInv4Pi;
         if (BASIS == BEM_P0) {
-            m.table[idx] = make_double2((double)acc[0] * scale, 0.0);
+            m.table[idx] = make_double2((double)acc[0] * scale, (double)acci[0] * scale);
         } else {
-            double M[9], hat[9];
+            double M[9], Mi[9], hat[9], hati[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) M[k] = (double)acc[k];
+            for (int k = 0; k < 9; ++k) {
+                M[k] = (double)acc[k];
+                Mi[k] = (double)acci[k];
+            }
             moments_to_hats(M, hat);
+            moments_to_hats(Mi, hati);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
-                    m.table[(int64_t)idx * 9 + pa[i] * 3 + pb[j]] = make_double2(hat[i * 3 + j] * scale, 0.0);
+                    m.table[(int64_t)idx * 9 + pa[i] * 3 + pb[j]] =
+                        make_double2(hat[i * 3 + j] * scale, hati[i * 3 + j] * scale);
         }
     }
 }
@@ -749,8 +918,15 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
             TriF A, B;
             load_trif(m.geomf, a, A);
             load_trif(m.geomf, b, B);
-            re = (double)regular_p0_f32<KIND, NP>(A, B, R);
-            im = 0.0;
+            if (KIND == BEM_HELMHOLTZ_SLP) {
+                float fr, fi;
+                regular_p0_f32_helm<NP>(A, B, R, L.kappa, fr, fi);
+                re = (double)fr;
+                im = (double)fi;
+            } else {
+                re = (double)regular_p0_f32<KIND, NP>(A, B, R);
+                im = 0.0;
+            }
         } else {
             Tri A, B;
             load_tri(m.geom, a, A);

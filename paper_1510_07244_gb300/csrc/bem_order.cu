@@ -537,19 +537,36 @@ __global__ void __launch_bounds__(256) k_learned_eval(MeshView m, const int4 *__
             if (KIND == BEM_LAPLACE_DLP)
                 H = make_height(A.vh[0], A.vl[0], A.vh[1], A.vl[1], A.vh[2], A.vl[2], B.vh[0], B.vl[0],
                                 B.nh, B.nl);
-            float acc = 0.0f;
+            float acc = 0.0f, acci = 0.0f;
+            HelmPhase P;
+            if (KIND == BEM_HELMHOLTZ_SLP) P = helm_phase(A, B, kappa);
             for (int p = lane; p < np; p += 32) {
                 const float x1 = __ldg(rulef + p), x2 = __ldg(rulef + np + p),
                             y1 = __ldg(rulef + 2 * np + p), y2 = __ldg(rulef + 3 * np + p),
                             w = __ldg(rulef + 4 * np + p);
-                const float dx = fmaf(x1, A.e1[0], fmaf(x2, A.e2[0], d0[0])) - fmaf(y1, B.e1[0], y2 * B.e2[0]);
-                const float dy = fmaf(x1, A.e1[1], fmaf(x2, A.e2[1], d0[1])) - fmaf(y1, B.e1[1], y2 * B.e2[1]);
-                const float dz = fmaf(x1, A.e1[2], fmaf(x2, A.e2[2], d0[2])) - fmaf(y1, B.e1[2], y2 * B.e2[2]);
-                const float dn = KIND == BEM_LAPLACE_DLP ? height_at(H, x1, x2) : 0.0f;
-                acc = fmaf(w, kvalf<KIND>(dx, dy, dz, dn), acc);
+                if (KIND == BEM_HELMHOLTZ_SLP) {
+                    // centroid-relative offsets (see helm_phase)
+                    const float ax = x1 - 0.666666687f, at = x2 - 0.333333343f;
+                    const float bx = y1 - 0.666666687f, bt = y2 - 0.333333343f;
+                    float kr, ki;
+                    helm_value(P, fmaf(ax, A.e1[0], at * A.e2[0]) - fmaf(bx, B.e1[0], bt * B.e2[0]),
+                               fmaf(ax, A.e1[1], at * A.e2[1]) - fmaf(bx, B.e1[1], bt * B.e2[1]),
+                               fmaf(ax, A.e1[2], at * A.e2[2]) - fmaf(bx, B.e1[2], bt * B.e2[2]), kr, ki);
+                    acc = fmaf(w, kr, acc);
+                    acci = fmaf(w, ki, acci);
+                } else {
+                    const float dx = fmaf(x1, A.e1[0], fmaf(x2, A.e2[0], d0[0])) - fmaf(y1, B.e1[0], y2 * B.e2[0]);
+                    const float dy = fmaf(x1, A.e1[1], fmaf(x2, A.e2[1], d0[1])) - fmaf(y1, B.e1[1], y2 * B.e2[1]);
+                    const float dz = fmaf(x1, A.e1[2], fmaf(x2, A.e2[2], d0[2])) - fmaf(y1, B.e1[2], y2 * B.e2[2]);
+                    const float dn = KIND == BEM_LAPLACE_DLP ? height_at(H, x1, x2) : 0.0f;
+                    acc = fmaf(w, kvalf<KIND>(dx, dy, dz, dn), acc);
+                }
             }
             acc = warp_sumf(acc);
-            sr = (double)acc * (double)A.sg * (double)B.sg * kInv4Pi;
+            if (KIND == BEM_HELMHOLTZ_SLP) acci = warp_sumf(acci);
+            const double sc = (double)A.sg * (double)B.sg * kInv4Pi;
+            sr = (double)acc * sc;
+            si = (double)acci * sc;
         } else {
             Tri A, B;
             load_tri(m.geom, a, A);
@@ -921,7 +938,7 @@ int run_learned_p0(bem_ctx *ctx, const MeshView &mv, const BlockLaunch &L, const
     k_learned_select<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A, ctx->status);
     k_learned_offsets<<<1, 32, 0, ctx->stream>>>(A);
     k_learned_compact<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A);
-    const bool mixed = precision == BEM_MIXED && L.kind != BEM_HELMHOLTZ_SLP;
+    const bool mixed = precision == BEM_MIXED;
     for (int c = 0; c < kClasses; ++c) {
         Rule4D r;
         int rc = api_get_rule4(ctx, kRegular, kClassRule[c][0], kClassRule[c][1], r);
@@ -936,7 +953,8 @@ int run_learned_p0(bem_ctx *ctx, const MeshView &mv, const BlockLaunch &L, const
             else k_learned_eval<BEM_LAPLACE_DLP, false><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
             break;
         default:
-            k_learned_eval<BEM_HELMHOLTZ_SLP, false><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+            if (mixed) k_learned_eval<BEM_HELMHOLTZ_SLP, true><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+            else k_learned_eval<BEM_HELMHOLTZ_SLP, false><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
         }
     }
     // class counts of this call (for reports): read after the launches

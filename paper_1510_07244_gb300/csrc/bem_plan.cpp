@@ -307,7 +307,8 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
     for (auto &ji : jobs) {
         const bem_block_job &J = *ji.J;
         if (J.n_blocks == 0) continue;
-        const int mixed = J.quad.precision == BEM_MIXED && J.kernel.kind != BEM_HELMHOLTZ_SLP;
+        const int mixed = J.quad.precision == BEM_MIXED &&
+                          !(J.kernel.kind == BEM_HELMHOLTZ_SLP && ji.m->v.basis == BEM_P1);
         char key[96];
         std::snprintf(key, sizeof key, "b%d k%d np%d m%d r%d q%d", ji.m->v.basis, J.kernel.kind,
                       ji.r2.np, mixed, J.quad.regular_rule, J.quad.q_regular);

@@ -31,11 +31,11 @@ __global__ void __launch_bounds__(256) k_touching_batch(const TouchJob *__restri
 template <int KIND, int BASIS>
 __global__ void __launch_bounds__(256) k_touching_vertex_f32(MeshView m, const int *__restrict__ list,
                                                              int64_t n, const float *__restrict__ rule,
-                                                             int np)
+                                                             int np, float kappa)
 {
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wid >= n) return;
-    touch_vertex_f32<KIND, BASIS>(m, __ldg(list + wid), rule, np, threadIdx.x & 31);
+    touch_vertex_f32<KIND, BASIS>(m, __ldg(list + wid), rule, np, threadIdx.x & 31, kappa);
 }
 
 template <int KIND, int BASIS>
@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(256) k_touching_vertex_f32_batch(const TouchJo
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wid >= n) return;
     const int2 it = items[wid];
-    touch_vertex_f32<KIND, BASIS>(jobs[it.x].m, it.y, rule, np, threadIdx.x & 31);
+    touch_vertex_f32<KIND, BASIS>(jobs[it.x].m, it.y, rule, np, threadIdx.x & 31,
+                                  (float)jobs[it.x].kappa);
 }
 
 cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
@@ -57,14 +58,13 @@ cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t
     if (n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + 7) / 8);
     const bool p1 = m.basis == BEM_P1;
-    if (mixed && cas == kVertex && kind != BEM_HELMHOLTZ_SLP && rule.f) {
-        if (kind == BEM_LAPLACE_SLP) {
-            if (p1) k_touching_vertex_f32<BEM_LAPLACE_SLP, BEM_P1><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
-            else k_touching_vertex_f32<BEM_LAPLACE_SLP, BEM_P0><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
-        } else {
-            if (p1) k_touching_vertex_f32<BEM_LAPLACE_DLP, BEM_P1><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
-            else k_touching_vertex_f32<BEM_LAPLACE_DLP, BEM_P0><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n);
-        }
+    if (mixed && cas == kVertex && rule.f) {
+        const float kf = (float)kappa;
+#define BEM_TV(K, B) k_touching_vertex_f32<K, B><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n, kf)
+        if (kind == BEM_LAPLACE_SLP) { if (p1) BEM_TV(BEM_LAPLACE_SLP, BEM_P1); else BEM_TV(BEM_LAPLACE_SLP, BEM_P0); }
+        else if (kind == BEM_LAPLACE_DLP) { if (p1) BEM_TV(BEM_LAPLACE_DLP, BEM_P1); else BEM_TV(BEM_LAPLACE_DLP, BEM_P0); }
+        else { if (p1) BEM_TV(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TV(BEM_HELMHOLTZ_SLP, BEM_P0); }
+#undef BEM_TV
         return cudaGetLastError();
     }
 #define BEM_TOUCH(K, B, C) k_touching<K, B, C><<<blocks, 256, 0, st>>>(m, list, n, rule.d, rule.n, kappa)
@@ -90,14 +90,12 @@ cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int
     if (n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + 7) / 8);
     const bool p1 = basis == BEM_P1;
-    if (mixed && cas == kVertex && kind != BEM_HELMHOLTZ_SLP && rule.f) {
-        if (kind == BEM_LAPLACE_SLP) {
-            if (p1) k_touching_vertex_f32_batch<BEM_LAPLACE_SLP, BEM_P1><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
-            else k_touching_vertex_f32_batch<BEM_LAPLACE_SLP, BEM_P0><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
-        } else {
-            if (p1) k_touching_vertex_f32_batch<BEM_LAPLACE_DLP, BEM_P1><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
-            else k_touching_vertex_f32_batch<BEM_LAPLACE_DLP, BEM_P0><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);
-        }
+    if (mixed && cas == kVertex && rule.f) {
+#define BEM_TVB(K, B) k_touching_vertex_f32_batch<K, B><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n)
+        if (kind == BEM_LAPLACE_SLP) { if (p1) BEM_TVB(BEM_LAPLACE_SLP, BEM_P1); else BEM_TVB(BEM_LAPLACE_SLP, BEM_P0); }
+        else if (kind == BEM_LAPLACE_DLP) { if (p1) BEM_TVB(BEM_LAPLACE_DLP, BEM_P1); else BEM_TVB(BEM_LAPLACE_DLP, BEM_P0); }
+        else { if (p1) BEM_TVB(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TVB(BEM_HELMHOLTZ_SLP, BEM_P0); }
+#undef BEM_TVB
         return cudaGetLastError();
     }
 #define BEM_TB(K, B, C) k_touching_batch<K, B, C><<<blocks, 256, 0, st>>>(jobs, items, n, rule.d, rule.n)

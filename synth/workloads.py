@@ -113,6 +113,19 @@ def config2(levels: int = 5) -> Workload:
                           "n_near_blocks": len(near.blk_row), "n_far_blocks": len(far.blk_row)})
 
 
+def config3(n: int = 64) -> Workload:
+    """Helmholtz single layer, kappa = 8, P0, surface of the unit cube with n x n
+    squares per face (12 n^2 triangles; n = 64: 49152), vertices jittered by 5%
+    of the mean edge length (seeded); H2 blocks (leaf 32, eta 2, <= 16 pivots);
+    SS q=5, Duffy q=3; mixed precision."""
+    mesh = meshes.jitter(meshes.cube_surface(n), 0.05, seed(3))
+    part, near, far = h2_blocks(mesh, "p0", 32, 2.0, 16, seed(3, 1))
+    return Workload(f"C3 cube{mesh.nt} helmholtz_slp k8 p0 h2 mixed", mesh, "p0",
+                    [Operator("helmholtz_slp", 8.0)], Quad(3, "duffy", 5, 5, 5),
+                    near=near, far=far,
+                    meta={"leaf_size": 32, "eta": 2.0, "rank": 16, "precision": "mixed"})
+
+
 @dataclass
 class BatchItem:
     """One mesh of a batched workload with its operators and block sets."""

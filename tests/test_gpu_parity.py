@@ -349,3 +349,55 @@ def test_mixed_full_size_against_fp64(ctx, pkg):
             err = rel_err(res["mixed"][k], res["fp64"][k], r)
             assert err.max() <= MIXED_TOL, (op.kernel, k, err.max())
     ctx.bem_mesh_free(mid)
+
+
+@pytest.mark.parametrize("meshname,kappa", [("cube3", 4.0), ("torus", 8.0), ("ico2", 16.0)])
+def test_mixed_helmholtz_p0(ctx, pkg, meshname, kappa):
+    """Mixed Helmholtz (P0): FP32 disjoint and common-vertex pairs with the
+    double-float reference phase; within 1e-6 of the oracle."""
+    mesh = MESHES[meshname]()
+    quad = dict(QUADS["paper"], precision="mixed")
+    got, n = _dense(ctx, pkg, mesh, "p0", "helmholtz_slp", kappa, quad)
+    rows = np.repeat(np.arange(n), n)
+    cols = np.tile(np.arange(n), n)
+    ref = oracle_entries(mesh, "p0", rows, cols, "helmholtz_slp", kappa, QUADS["paper"]).reshape(n, n)
+    absint = oracle_absolute(mesh, "p0", rows, cols, "helmholtz_slp", kappa, QUADS["paper"])
+    err = rel_err_abs(got.ravel(), ref.ravel(), absint, rows)
+    assert 1e-12 < err.max() <= MIXED_TOL
+
+
+def test_mixed_helmholtz_far_phase(ctx, pkg):
+    """kappa = 16 on a 2048-triangle sphere: far pairs with kappa r up to 32."""
+    mesh = synth.jitter(synth.octasphere(16), 0.05, 77)
+    quad = dict(QUADS["paper"], precision="mixed")
+    got, n = _dense(ctx, pkg, mesh, "p0", "helmholtz_slp", 16.0, quad)
+    rng = synth.SplitMix64(5)
+    rows = rng.integers(3000, n)
+    cols = rng.integers(3000, n)
+    ref = oracle_entries(mesh, "p0", rows, cols, "helmholtz_slp", 16.0, QUADS["paper"])
+    absint = oracle_absolute(mesh, "p0", rows, cols, "helmholtz_slp", 16.0, QUADS["paper"])
+    assert rel_err_abs(got[rows, cols], ref, absint, rows).max() <= MIXED_TOL
+
+
+def test_c3_full_size_sampled(ctx, pkg):
+    """The 49152-triangle jittered cube, Helmholtz kappa = 8, mixed form: all
+    near-field and coupling blocks on the GPU, whole sampled blocks checked
+    against the FP64 oracle (the error of the mixed form on this workload)."""
+    from parity_util import sample_block_entries
+    w = synth.workloads.config3()
+    op = w.operators[0]
+    q = w.quad.kw()
+    mid = ctx.bem_mesh_upload(w.mesh.verts, w.mesh.tris, w.basis)
+    rng = synth.SplitMix64(31)
+    for bs, call in ((w.near, ctx.bem_near_field), (w.far, ctx.bem_coupling_blocks)):
+        out = _out(bs.n_entries, op.kernel)
+        call([block_job(pkg, mid, bs, op.kernel, op.kappa, dict(q, precision="mixed"), out)])
+        ctx.bem_sync()
+        got_all = out.cpu().numpy()
+        assert np.isfinite(got_all).all()
+        pos = sample_block_entries(bs, 8, rng)
+        r, c = bs.entry_indices()
+        ref = oracle_entries(w.mesh, "p0", r[pos], c[pos], op.kernel, op.kappa, q)
+        A = oracle_absolute(w.mesh, "p0", r[pos], c[pos], op.kernel, op.kappa, q)
+        assert rel_err_abs(got_all[pos], ref, A, r[pos]).max() <= MIXED_TOL
+    ctx.bem_mesh_free(mid)
