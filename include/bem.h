@@ -295,6 +295,41 @@ int bem_plan_info(bem_ctx *ctx, bem_plan *plan, int32_t *n_touch_launches,
  * Whole blocks, so every output block has one owner.  Needs no device. */
 int bem_shard_blocks(const int64_t *cost, int64_t n_blocks, int32_t n_shards, int64_t *bounds);
 
+/* ---- GCA pivots (host) -------------------------------------------------------
+ * Pivot rows t~ of every cluster for the H^2 coupling matrices G|t~ x s~
+ * (Sections 2.3-2.4).  For a cluster t: B_t = bounding box of the supports
+ * of its basis functions, delta_t = diam(B_t), omega_t = B_t grown by
+ * delta_t / 2 on every side; a gauss_per_face x gauss_per_face Gauss rule on
+ * each of the six faces of omega_t (m = 6 gauss_per_face^2 points z_nu,
+ * weights w_nu) gives the matrix A_t = (A_t+, A_t-) of Green's representation
+ * formula, a_{t+,i nu} = sqrt(w_nu) int phi_i g(., z_nu) and
+ * a_{t-,i nu} = sqrt(w_nu) delta_t int phi_i dg/dn(z_nu)(., z_nu) (g the
+ * Laplace Green function for kappa = 0, exp(i kappa r)/(4 pi r) otherwise).
+ * Cross approximation with complete pivoting on A_t chooses at most max_rank
+ * rows, stopping once the largest remaining entry is <= eps times the first
+ * pivot.  A cluster with sons restricts A_t to the rows t^ = t~_1 u t~_2 of
+ * its sons' pivots (nested bases), so its pivots are a subset of theirs.
+ *   verts   HOST double[nv][3]; tris HOST int32[nt][3] (as bem_mesh_upload)
+ *   basis   BEM_P0 (indices are triangles) or BEM_P1 (vertices)
+ *   cl_ptr, cl_idx  HOST cluster CSR: cluster c holds the indices
+ *                   cl_idx[cl_ptr[c] .. cl_ptr[c+1]-1] (cl_ptr[0] = 0)
+ *   cl_son  HOST int32[n_clusters][2]: the sons of c, -1 where absent; every
+ *           cluster has at most one parent, and the sons' index sets make up
+ *           the father's
+ *   n_threads  host threads (0 = all hardware threads); the result does not
+ *              depend on it
+ *   piv_ptr, piv_idx  HOST outputs: pivots of c (sorted ascending) are
+ *           piv_idx[piv_ptr[c] .. piv_ptr[c+1]-1]; piv_ptr holds n_clusters+1
+ *           entries, piv_idx `cap` (n_clusters * max_rank always suffices).
+ * Returns BEM_OK, or BEM_ERR_INVALID_ARG for bad arguments, an index out of
+ * range, a cluster with two parents or a cycle, or cap too small.  Needs no
+ * device and no context; all arrays stay the caller's. */
+int bem_gca_pivots(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, int32_t basis,
+                   double kappa, const int32_t *cl_ptr, const int32_t *cl_idx,
+                   const int32_t *cl_son, int32_t n_clusters, int32_t gauss_per_face, double eps,
+                   int32_t max_rank, int32_t n_threads, int32_t *piv_ptr, int32_t *piv_idx,
+                   int64_t cap);
+
 /* ---- quadrature rules ------------------------------------------------------
  * Copies the library's 4D rule on D x D for a case (Section 2.2; case 0 =
  * disjoint pairs with regular_rule BEM_RULE_DUFFY / BEM_RULE_TRI7, 1 = common

@@ -31,7 +31,7 @@ EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_
            "bem_pivot_entries_absolute", "bem_mlp_create", "bem_mlp_destroy", "bem_mlp_num_params",
            "bem_mlp_set_params", "bem_mlp_get_params", "bem_mlp_gradients", "bem_mlp_train_step",
            "bem_mlp_infer", "bem_pair_features", "bem_set_order_model", "bem_learned_counts",
-           "bem_shard_blocks"]
+           "bem_shard_blocks", "bem_gca_pivots"]
 ORDER_CLASSES = [("duffy", 2), ("tri7", 1), ("duffy", 4), ("duffy", 5), ("duffy", 6), ("duffy", 8)]
 ORDER_CLASS_POINTS = [16, 49, 256, 625, 1296, 4096]
 PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE = 1, 2, 4
@@ -122,6 +122,10 @@ def load():
                                       ctypes.c_int64, _vp]
     lib.bem_set_order_model.argtypes = [_vp, _vp, ctypes.c_float]
     lib.bem_shard_blocks.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, _vp]
+    lib.bem_gca_pivots.argtypes = [_vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
+                                   ctypes.c_double, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
+                                   ctypes.c_int64]
     lib.bem_learned_counts.argtypes = [_vp, P(ctypes.c_int64)]
     lib.bem_plan_create.argtypes = [_vp, P(bem_block_job), ctypes.c_int32, P(bem_block_job),
                                     ctypes.c_int32, ctypes.c_int32, P(_vp)]
@@ -167,6 +171,31 @@ def bem_shard_blocks(cost, n_shards: int) -> np.ndarray:
     if rc != BEM_OK:
         raise BemError(rc, "bad shard arguments")
     return bounds
+
+
+def bem_gca_pivots(verts, tris, basis: str, cl_ptr, cl_idx, cl_son, kappa: float = 0.0,
+                   gauss_per_face: int = 4, eps: float = 1e-6, max_rank: int = 16,
+                   n_threads: int = 0):
+    """GCA pivots of every cluster (host only): cluster CSR (piv_ptr, piv_idx) int32."""
+    v = np.ascontiguousarray(verts, np.float64)
+    t = np.ascontiguousarray(tris, np.int32)
+    ptr = np.ascontiguousarray(cl_ptr, np.int32)
+    idx = np.ascontiguousarray(cl_idx, np.int32)
+    son = np.ascontiguousarray(cl_son, np.int32)
+    nc = len(ptr) - 1
+    if son.shape != (nc, 2):
+        raise BemError(-1, "cl_son must be (n_clusters, 2)")
+    piv_ptr = np.zeros(nc + 1, np.int32)
+    piv_idx = np.zeros(max(1, nc * max_rank), np.int32)
+    rc = load().bem_gca_pivots(v.ctypes.data_as(_vp), len(v), t.ctypes.data_as(_vp), len(t),
+                               BASES[basis], float(kappa), ptr.ctypes.data_as(_vp),
+                               idx.ctypes.data_as(_vp), son.ctypes.data_as(_vp), nc,
+                               int(gauss_per_face), float(eps), int(max_rank), int(n_threads),
+                               piv_ptr.ctypes.data_as(_vp), piv_idx.ctypes.data_as(_vp),
+                               piv_idx.size)
+    if rc != BEM_OK:
+        raise BemError(rc, "bad GCA arguments")
+    return piv_ptr, piv_idx[: piv_ptr[-1]].copy()
 
 
 def kernel_desc(kind="laplace_slp", kappa=0.0) -> bem_kernel_desc:

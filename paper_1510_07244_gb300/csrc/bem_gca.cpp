@@ -1,0 +1,325 @@
+// Green cross approximation (GCA) pivots on the host (Sections 2.3-2.4).
+//
+// The coupling matrices of the H^2 form are the Galerkin entries at pivot rows
+// t~ x pivot columns s~ of every admissible block.  The pivots come from the
+// cluster's own geometry alone:
+//   * B_t = bounding box of the supports of the cluster's basis functions,
+//     delta_t = diam(B_t), and omega_t = B_t grown by delta_t / 2 on every
+//     side, so dist(B_t, boundary of omega_t) = delta_t / 2;
+//   * a tensor Gauss rule (points z_nu, weights w_nu) on the six faces of
+//     omega_t discretises Green's representation formula, which gives
+//     A_t = (A_t+, A_t-) with, for i in t,
+//         a_{t+, i nu} = sqrt(w_nu)         int phi_i(x) g(x, z_nu) dx
+//         a_{t-, i nu} = sqrt(w_nu) delta_t int phi_i(x) d/dn(z_nu) g(x, z_nu) dx
+//     (outward face normals; the integrands are smooth because z_nu stays
+//     delta_t / 2 away from the supports, so Radon's 7-point rule on each
+//     support triangle evaluates them);
+//   * cross approximation with complete pivoting on A_t picks the pivot rows
+//     t~ (at most max_rank, stopping when the largest remaining entry falls
+//     below eps times the first pivot);
+//   * nested bases: a cluster with sons runs the same cross approximation on
+//     the rows t^ = t~_1 u t~_2 of A_t only, so its pivots are a subset of
+//     its sons' pivots.
+// g is the kernel's Green function: 1/(4 pi r) (Laplace, kappa = 0) or
+// exp(i kappa r)/(4 pi r) (Helmholtz).  Every cluster of one tree level is
+// independent, so the levels run bottom-up with the clusters of a level
+// spread over host threads; the result does not depend on the thread count.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <thread>
+#include <vector>
+
+#include "bem_internal.h"
+
+namespace {
+
+using cplx = std::complex<double>;
+constexpr double kPi = 3.14159265358979323846;
+
+struct HostMesh {
+    const double *v;
+    const int32_t *t;
+    int64_t nv, nt;
+    int basis;
+    double kappa;
+    std::vector<int64_t> vt_ptr;   // triangles around each vertex (P1)
+    std::vector<int32_t> vt_tri;
+    double S[7], T[7], W[7];       // Radon's 7-point rule on the reference triangle
+};
+
+void radon7(HostMesh &M)
+{
+    const double r = std::sqrt(15.0);
+    const double p1 = (6.0 - r) / 21.0, p2 = (6.0 + r) / 21.0;
+    const double L[7][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3},
+                            {1 - 2 * p1, p1, p1}, {p1, 1 - 2 * p1, p1}, {p1, p1, 1 - 2 * p1},
+                            {1 - 2 * p2, p2, p2}, {p2, 1 - 2 * p2, p2}, {p2, p2, 1 - 2 * p2}};
+    const double w1 = (155.0 - r) / 2400.0, w2 = (155.0 + r) / 2400.0;
+    const double W[7] = {9.0 / 80.0, w1, w1, w1, w2, w2, w2};
+    for (int k = 0; k < 7; ++k) {
+        M.S[k] = L[k][1] + L[k][2];
+        M.T[k] = L[k][2];
+        M.W[k] = W[k];
+    }
+}
+
+// int phi_i(x) g(x, z) dx and int phi_i(x) d/dn(z) g(x, z) dx.
+void basis_integrals(const HostMesh &M, int index, const double *z, const double *nz, cplx &gp,
+                     cplx &gm)
+{
+    gp = gm = 0.0;
+    auto tri = [&](int64_t tr, int local) {
+        const int32_t *tv = M.t + 3 * tr;
+        const double *v0 = M.v + 3 * (int64_t)tv[0], *v1 = M.v + 3 * (int64_t)tv[1],
+                     *v2 = M.v + 3 * (int64_t)tv[2];
+        double e1[3], e2[3];
+        for (int c = 0; c < 3; ++c) {
+            e1[c] = v1[c] - v0[c];
+            e2[c] = v2[c] - v1[c];
+        }
+        const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                     cz = e1[0] * e2[1] - e1[1] * e2[0];
+        const double sg = std::sqrt(cx * cx + cy * cy + cz * cz);
+        for (int k = 0; k < 7; ++k) {
+            double d[3];
+            for (int c = 0; c < 3; ++c) d[c] = v0[c] + M.S[k] * e1[c] + M.T[k] * e2[c] - z[c];
+            const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            const double lam = local < 0 ? 1.0
+                                         : (local == 0 ? 1.0 - M.S[k]
+                                                       : (local == 1 ? M.S[k] - M.T[k] : M.T[k]));
+            const double f = M.W[k] * sg * lam / (4.0 * kPi * r);
+            // n(z) . grad_z of exp(i kappa r)/r with r = |x - z|:
+            //   (x - z).n / r^2 * (1 - i kappa r) exp(i kappa r) / r
+            const double dn = (d[0] * nz[0] + d[1] * nz[1] + d[2] * nz[2]) / (r * r);
+            if (M.kappa == 0.0) {
+                gp += f;
+                gm += f * dn;
+            } else {
+                const cplx e = std::polar(1.0, M.kappa * r);
+                gp += f * e;
+                gm += f * dn * cplx(1.0, -M.kappa * r) * e;
+            }
+        }
+    };
+    if (M.basis == BEM_P0) {
+        tri(index, -1);
+    } else {
+        for (int64_t k = M.vt_ptr[index]; k < M.vt_ptr[index + 1]; ++k) {
+            const int64_t tr = M.vt_tri[k];
+            const int32_t *tv = M.t + 3 * tr;
+            tri(tr, tv[0] == index ? 0 : (tv[1] == index ? 1 : 2));
+        }
+    }
+}
+
+void grow_box(const HostMesh &M, int index, double *lo, double *hi)
+{
+    auto add_tri = [&](int64_t tr) {
+        for (int k = 0; k < 3; ++k)
+            for (int c = 0; c < 3; ++c) {
+                const double x = M.v[3 * (int64_t)M.t[3 * tr + k] + c];
+                lo[c] = std::min(lo[c], x);
+                hi[c] = std::max(hi[c], x);
+            }
+    };
+    if (M.basis == BEM_P0) add_tri(index);
+    else
+        for (int64_t k = M.vt_ptr[index]; k < M.vt_ptr[index + 1]; ++k) add_tri(M.vt_tri[k]);
+}
+
+// Cross approximation with complete pivoting of the rows x cols matrix A
+// (row-major, overwritten by its residual); returns the pivot rows in the
+// order they were chosen.
+std::vector<int> aca_complete(std::vector<cplx> &A, int rows, int cols, double eps, int max_rank)
+{
+    std::vector<int> piv;
+    double first = 0.0;
+    std::vector<cplx> colv(rows), rowv(cols);
+    for (int k = 0; k < std::min(max_rank, std::min(rows, cols)); ++k) {
+        int bi = -1, bj = -1;
+        double best = 0.0;
+        for (int i = 0; i < rows; ++i)
+            for (int j = 0; j < cols; ++j) {
+                const double a = std::abs(A[(size_t)i * cols + j]);
+                if (a > best) {
+                    best = a;
+                    bi = i;
+                    bj = j;
+                }
+            }
+        if (bi < 0) break;
+        if (k == 0) first = best;
+        else if (best <= eps * first) break;
+        piv.push_back(bi);
+        const cplx p = A[(size_t)bi * cols + bj];
+        for (int i = 0; i < rows; ++i) colv[i] = A[(size_t)i * cols + bj] / p;
+        for (int j = 0; j < cols; ++j) rowv[j] = A[(size_t)bi * cols + j];
+        for (int i = 0; i < rows; ++i) {
+            if (colv[i] == 0.0) continue;
+            for (int j = 0; j < cols; ++j) A[(size_t)i * cols + j] -= colv[i] * rowv[j];
+        }
+    }
+    return piv;
+}
+
+struct Tree {
+    const int32_t *ptr, *idx, *son;
+};
+
+// Pivots of cluster c, given its sons' pivots.
+std::vector<int32_t> cluster_pivots(const HostMesh &M, const Tree &T, int c,
+                                    const std::vector<std::vector<int32_t>> &piv,
+                                    const std::vector<double> &g, const std::vector<double> &gw,
+                                    double eps, int max_rank)
+{
+    std::vector<int32_t> rows;
+    const int s0 = T.son[2 * c], s1 = T.son[2 * c + 1];
+    if (s0 < 0 && s1 < 0) rows.assign(T.idx + T.ptr[c], T.idx + T.ptr[c + 1]);
+    else
+        for (int s : {s0, s1})
+            if (s >= 0) rows.insert(rows.end(), piv[s].begin(), piv[s].end());
+    if (rows.empty()) return rows;
+
+    double lo[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL}, hi[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
+    for (int32_t k = T.ptr[c]; k < T.ptr[c + 1]; ++k) grow_box(M, T.idx[k], lo, hi);
+    const double delta = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) +
+                                   (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                   (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    double wlo[3], whi[3];
+    for (int d = 0; d < 3; ++d) {
+        wlo[d] = lo[d] - 0.5 * delta;
+        whi[d] = hi[d] + 0.5 * delta;
+    }
+    const int q = (int)g.size();
+    std::vector<double> Z, N, Wq;
+    for (int ax = 0; ax < 3; ++ax)
+        for (int side = 0; side < 2; ++side) {
+            const int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
+            const double len1 = whi[a1] - wlo[a1], len2 = whi[a2] - wlo[a2];
+            for (int i = 0; i < q; ++i)
+                for (int j = 0; j < q; ++j) {
+                    double z[3], n[3] = {0.0, 0.0, 0.0};
+                    z[ax] = side ? whi[ax] : wlo[ax];
+                    z[a1] = wlo[a1] + g[i] * len1;
+                    z[a2] = wlo[a2] + g[j] * len2;
+                    n[ax] = side ? 1.0 : -1.0;
+                    Z.insert(Z.end(), z, z + 3);
+                    N.insert(N.end(), n, n + 3);
+                    Wq.push_back(gw[i] * gw[j] * len1 * len2);
+                }
+        }
+    const int m = (int)Wq.size(), rn = (int)rows.size();
+    std::vector<cplx> A((size_t)rn * 2 * m);
+    for (int i = 0; i < rn; ++i)
+        for (int nu = 0; nu < m; ++nu) {
+            cplx gp, gm;
+            basis_integrals(M, rows[i], &Z[3 * nu], &N[3 * nu], gp, gm);
+            const double sw = std::sqrt(Wq[nu]);
+            A[(size_t)i * 2 * m + nu] = sw * gp;
+            A[(size_t)i * 2 * m + m + nu] = sw * delta * gm;
+        }
+    std::vector<int32_t> out;
+    for (int r : aca_complete(A, rn, 2 * m, eps, max_rank)) out.push_back(rows[r]);
+    std::sort(out.begin(), out.end());
+    return out;
+}
+
+}  // namespace
+
+extern "C" int bem_gca_pivots(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                              int32_t basis, double kappa, const int32_t *cl_ptr,
+                              const int32_t *cl_idx, const int32_t *cl_son, int32_t n_clusters,
+                              int32_t gauss_per_face, double eps, int32_t max_rank,
+                              int32_t n_threads, int32_t *piv_ptr, int32_t *piv_idx, int64_t cap)
+{
+    if (!verts || !tris || nv < 1 || nt < 1 || (basis != BEM_P0 && basis != BEM_P1) ||
+        !std::isfinite(kappa) || kappa < 0.0 || !cl_ptr || !cl_idx || !cl_son || n_clusters < 1 ||
+        gauss_per_face < 1 || gauss_per_face > 16 || !(eps > 0.0) || max_rank < 1 ||
+        n_threads < 0 || !piv_ptr || !piv_idx || cap < 0)
+        return BEM_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < 3 * nt; ++k)
+        if (tris[k] < 0 || tris[k] >= nv) return BEM_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < 3 * nv; ++k)
+        if (!std::isfinite(verts[k])) return BEM_ERR_INVALID_ARG;
+    const int64_t nidx = basis == BEM_P0 ? nt : nv;
+    if (cl_ptr[0] != 0) return BEM_ERR_INVALID_ARG;
+    for (int c = 0; c < n_clusters; ++c) {
+        if (cl_ptr[c + 1] < cl_ptr[c]) return BEM_ERR_INVALID_ARG;
+        for (int s = 0; s < 2; ++s)
+            if (cl_son[2 * c + s] >= n_clusters || cl_son[2 * c + s] == c ||
+                cl_son[2 * c + s] < -1)
+                return BEM_ERR_INVALID_ARG;
+    }
+    for (int64_t k = 0; k < cl_ptr[n_clusters]; ++k)
+        if (cl_idx[k] < 0 || cl_idx[k] >= nidx) return BEM_ERR_INVALID_ARG;
+
+    // depth of every cluster; a cluster with two parents or a cycle is an error
+    std::vector<int> depth(n_clusters, -1), parent(n_clusters, -1);
+    for (int c = 0; c < n_clusters; ++c)
+        for (int s = 0; s < 2; ++s) {
+            const int x = cl_son[2 * c + s];
+            if (x < 0) continue;
+            if (parent[x] >= 0) return BEM_ERR_INVALID_ARG;
+            parent[x] = c;
+        }
+    int max_depth = 0;
+    for (int c = 0; c < n_clusters; ++c) {
+        int d = 0, x = c;
+        while (parent[x] >= 0) {
+            x = parent[x];
+            if (++d > n_clusters) return BEM_ERR_INVALID_ARG;
+        }
+        depth[c] = d;
+        max_depth = std::max(max_depth, d);
+    }
+
+    HostMesh M;
+    M.v = verts;
+    M.t = tris;
+    M.nv = nv;
+    M.nt = nt;
+    M.basis = basis;
+    M.kappa = kappa;
+    radon7(M);
+    if (basis == BEM_P1) {
+        M.vt_ptr.assign(nv + 1, 0);
+        M.vt_tri.resize(3 * nt);
+        for (int64_t k = 0; k < 3 * nt; ++k) M.vt_ptr[tris[k] + 1]++;
+        for (int64_t v = 0; v < nv; ++v) M.vt_ptr[v + 1] += M.vt_ptr[v];
+        std::vector<int64_t> fill(M.vt_ptr.begin(), M.vt_ptr.end() - 1);
+        for (int64_t t = 0; t < nt; ++t)
+            for (int k = 0; k < 3; ++k) M.vt_tri[fill[tris[3 * t + k]]++] = (int32_t)t;
+    }
+    std::vector<double> g, gw;
+    bem::gauss_legendre_unit(gauss_per_face, g, gw);
+
+    const Tree T{cl_ptr, cl_idx, cl_son};
+    std::vector<std::vector<int32_t>> piv(n_clusters);
+    const int nthr =
+        n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+    for (int d = max_depth; d >= 0; --d) {
+        std::vector<int> level;
+        for (int c = 0; c < n_clusters; ++c)
+            if (depth[c] == d) level.push_back(c);
+        std::atomic<size_t> next(0);
+        auto work = [&]() {
+            for (size_t k; (k = next.fetch_add(1)) < level.size();)
+                piv[level[k]] = cluster_pivots(M, T, level[k], piv, g, gw, eps, max_rank);
+        };
+        const int n_level = std::min<int>(nthr, (int)level.size());
+        std::vector<std::thread> pool;
+        for (int k = 1; k < n_level; ++k) pool.emplace_back(work);
+        work();
+        for (auto &th : pool) th.join();
+    }
+    int64_t at = 0;
+    piv_ptr[0] = 0;
+    for (int c = 0; c < n_clusters; ++c) {
+        if (at + (int64_t)piv[c].size() > cap) return BEM_ERR_INVALID_ARG;
+        for (int32_t v : piv[c]) piv_idx[at++] = v;
+        piv_ptr[c + 1] = (int32_t)at;
+    }
+    return BEM_OK;
+}

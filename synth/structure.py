@@ -111,6 +111,15 @@ class BlockPartition:
         idx = np.concatenate([t.indices(c) for c in range(t.n_clusters)]).astype(np.int32)
         return ptr, idx
 
+    def son_array(self):
+        """int32 (n_clusters, 2): the sons of every cluster, -1 where absent."""
+        t = self.tree
+        out = np.full((t.n_clusters, 2), -1, np.int32)
+        for c in range(t.n_clusters):
+            for k, s in enumerate(t.sons[c]):
+                out[c, k] = s
+        return out
+
     def near_blocks(self):
         """(blk_row, blk_col, blk_off, total) for the near blocks, column-major |t| x |s|."""
         return _blocks(self.near, lambda c: self.tree.end[c] - self.tree.start[c])

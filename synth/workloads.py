@@ -72,6 +72,7 @@ class Workload:
     near: BlockSet = None
     far: BlockSet = None
     meta: dict = field(default_factory=dict)
+    partition: object = None         # structure.BlockPartition of the H2 blocks
 
     @property
     def n_entries_per_operator(self):
@@ -108,7 +109,7 @@ def config2(levels: int = 5) -> Workload:
     part, near, far = h2_blocks(mesh, "p1", 32, 2.0, 16, seed(2))
     return Workload(f"C2 icosphere{mesh.nt} laplace_slp+dlp p1 h2", mesh, "p1",
                     [Operator("laplace_slp"), Operator("laplace_dlp")], Quad(3, "duffy", 5, 5, 5),
-                    near=near, far=far,
+                    near=near, far=far, partition=part,
                     meta={"leaf_size": 32, "eta": 2.0, "rank": 16,
                           "n_near_blocks": len(near.blk_row), "n_far_blocks": len(far.blk_row)})
 
@@ -122,7 +123,7 @@ def config3(n: int = 64) -> Workload:
     part, near, far = h2_blocks(mesh, "p0", 32, 2.0, 16, seed(3, 1))
     return Workload(f"C3 cube{mesh.nt} helmholtz_slp k8 p0 h2 mixed", mesh, "p0",
                     [Operator("helmholtz_slp", 8.0)], Quad(3, "duffy", 5, 5, 5),
-                    near=near, far=far,
+                    near=near, far=far, partition=part,
                     meta={"leaf_size": 32, "eta": 2.0, "rank": 16, "precision": "mixed"})
 
 
