@@ -76,7 +76,7 @@ def kernel_flops(w, counts, stats, precision):
     npts_reg = (q.q_regular ** 2) ** 2 if q.regular_rule == "duffy" else 49
     np_axis = q.q_regular ** 2 if q.regular_rule == "duffy" else 7
     reg = counts["near_regular_pairs"] + counts["far_regular_pairs"]
-    mixed = precision == "mixed"
+    mixed = precision in ("mixed", "mixed_full")
     out = {}
     laplace_ops = [o for o in w.operators if o.kernel != "helmholtz_slp"]
     f_blk = sum(reg * npts_reg * flops_per_point(o.kernel, w.basis, np_axis) for o in w.operators)
@@ -87,7 +87,8 @@ def kernel_flops(w, counts, stats, precision):
                                ("touching_identical", 6, q.q_identical, "n_identical")):
         f = sum(stats[key] * nsub * qq ** 4 * flops_per_point_ss(cas.split("_")[1], o.kernel, w.basis)
                 for o in w.operators)
-        p = "fp32" if (mixed and cas == "touching_vertex" and pipe == "fp32") else "fp64"
+        f32 = precision == "mixed_full" or (mixed and cas == "touching_vertex")
+        p = "fp32" if f32 else "fp64"
         out[cas] = (f, p)
     return {k: (f, p, PEAK_FP32 if p == "fp32" else PEAK_FP64) for k, (f, p) in out.items()}
 
@@ -342,39 +343,58 @@ def run_ours(args):
                 o[(op.kernel, name)] = torch.zeros(sets[name]["n"], dtype=dt, device=dev)
         return o
 
-    outs64, outsmx = alloc_outs(), alloc_outs()
+    def max_rel_err(outs, outs64):
+        """Largest |g - g64| / max(|g64|, 1e-3 row max) over every entry."""
+        maxerr = 0.0
+        for name, bs in (("near", w.near), ("far", w.far)):
+            rows = torch.as_tensor(bs.entry_indices()[0]).to(dev)
+            for op in w.operators:
+                a64 = outs64[(op.kernel, name)].abs()
+                scale = torch.zeros(int(rows.max().item()) + 1, dtype=a64.dtype, device=dev)
+                scale = scale.scatter_reduce(0, rows, a64, reduce="amax")
+                den = torch.maximum(a64, 1e-3 * scale[rows])
+                den = torch.where(den > 0, den, torch.ones_like(den))
+                e = ((outs[(op.kernel, name)] - outs64[(op.kernel, name)]).abs() / den).max().item()
+                maxerr = max(maxerr, e)
+        return reduce_over_ranks(maxerr, "max", dev)
+
+    # the FP64 form, then the two mixed forms; the headline is the fastest form
+    # within 1e-6 of the FP64 form on every entry
+    mixed_forms = ["mixed_full", "mixed"] if args.form == "auto" else [args.form]
+    outs64 = alloc_outs()
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
     ms64, prof64, info64 = run_form("fp64", outs64, args.fp64_steps)
-    msmx, profmx, infomx = run_form("mixed", outsmx, args.steps)
+    forms = {}
+    for f in mixed_forms:
+        o = alloc_outs()
+        ms, prof, info = run_form(f, o, args.steps)
+        forms[f] = {"ms": ms, "prof": prof, "info": info, "outs": o,
+                    "max_rel_err": max_rel_err(o, outs64),
+                    "value": entries_all * args.steps / (ms / 1e3)}
     clk = clocks.stop()
-    outs = outsmx
-
-    # the chosen (mixed) form must stay within 1e-6 of the FP64 form on every entry
-    maxerr = 0.0
-    for name, bs in (("near", w.near), ("far", w.far)):
-        rows = torch.as_tensor(bs.entry_indices()[0]).to(dev)
-        for op in w.operators:
-            a64 = outs64[(op.kernel, name)].abs()
-            scale = torch.zeros(int(rows.max().item()) + 1, dtype=a64.dtype, device=dev)
-            scale = scale.scatter_reduce(0, rows, a64, reduce="amax")
-            den = torch.maximum(a64, 1e-3 * scale[rows])
-            den = torch.where(den > 0, den, torch.ones_like(den))
-            e = ((outsmx[(op.kernel, name)] - outs64[(op.kernel, name)]).abs() / den).max().item()
-            maxerr = max(maxerr, e)
-    maxerr = reduce_over_ranks(maxerr, "max", dev)
-    chosen_ok = maxerr <= 1e-6
+    ok = [f for f in mixed_forms if forms[f]["max_rel_err"] <= 1e-6]
+    chosen = max(ok, key=lambda f: forms[f]["value"]) if ok else "fp64"
+    chosen_ok = chosen != "fp64"
     value64 = entries_all * args.fp64_steps / (ms64 / 1e3)
-    valuemx = entries_all * args.steps / (msmx / 1e3)
-    value = valuemx if chosen_ok else value64
-    steps_used = args.steps if chosen_ok else args.fp64_steps
-    total_ms = msmx if chosen_ok else ms64
-    prof = profmx if chosen_ok else prof64
-    roof, per_kernel = roofline(prof, "mixed" if chosen_ok else "fp64", steps_used)
+    if chosen_ok:
+        F = forms[chosen]
+        value, steps_used, total_ms, prof, info = F["value"], args.steps, F["ms"], F["prof"], F["info"]
+        outs, maxerr = F["outs"], F["max_rel_err"]
+    else:
+        value, steps_used, total_ms, prof, info = value64, args.fp64_steps, ms64, prof64, info64
+        outs, maxerr = outs64, 0.0
+    roof, per_kernel = roofline(prof, chosen, steps_used)
     roof64, per64 = roofline(prof64, "fp64", args.fp64_steps)
-    info = infomx if chosen_ok else info64
     launches = int(info["kernels_per_step"] * steps_used)
+    other_forms = {f: {"value": F["value"], "ms_per_step": F["ms"] / args.steps,
+                       "max_rel_err_vs_fp64_form": F["max_rel_err"],
+                       "kernels": roofline(F["prof"], f, args.steps)[1]}
+                   for f, F in forms.items() if f != chosen}
+    for f in list(forms):
+        if f != chosen:
+            del forms[f]["outs"]
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -397,7 +417,7 @@ def run_ours(args):
             for name in ("near", "far"):
                 for key, t in pin[name].items():
                     sets[name][key].copy_(t, non_blocking=True)
-            jobs2 = make_jobs(torch, pkg, mid2, w, sets, outs, "mixed" if chosen_ok else "fp64")
+            jobs2 = make_jobs(torch, pkg, mid2, w, sets, outs, chosen)
             ctx.bem_near_field(jobs2["near"])
             ctx.bem_coupling_blocks(jobs2["far"])
             for key, t in outs.items():
@@ -431,7 +451,7 @@ def run_ours(args):
                                       "eps 1e-6, rank <= 16" if gca_s is not None
                                       else "seeded, rank <= 16"),
                            "gca_setup_s": gca_s,
-                           "quadrature": w.quad.kw(), "precision": "mixed" if chosen_ok else "fp64",
+                           "quadrature": w.quad.kw(), "precision": chosen,
                            "order_mode": "fixed",
                            "l2": "flushed between timed steps (256 MiB write, untimed)",
                            "pairs_per_step_per_operator": counts},
@@ -445,6 +465,7 @@ def run_ours(args):
                              "entries_compared": entries_per_step},
                 "fp64_form": {"value": value64, "ms_per_step": ms64 / args.fp64_steps,
                               "steps": args.fp64_steps, "roofline": roof64, "kernels": per64},
+                "other_forms": other_forms,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -539,6 +560,9 @@ def main():
     ap.add_argument("--split", action="store_true",
                     help="under torchrun: shard one workload's blocks across the ranks (strong "
                          "scaling) instead of one workload per rank (weak scaling)")
+    ap.add_argument("--form", default="auto", choices=["auto", "mixed_full", "mixed"],
+                    help="mixed form(s) timed beside the FP64 form; auto times both and "
+                         "reports the fastest within 1e-6 of the FP64 form")
     ap.add_argument("--pivots", default="gca", choices=["gca", "seeded"],
                     help="coupling pivots from the host GCA (default) or seeded per cluster")
     ap.add_argument("--levels", type=int, default=5,

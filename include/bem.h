@@ -56,7 +56,7 @@ extern "C" {
 enum { BEM_LAPLACE_SLP = 0, BEM_LAPLACE_DLP = 1, BEM_HELMHOLTZ_SLP = 2 };
 enum { BEM_P0 = 0, BEM_P1 = 1 };
 enum { BEM_RULE_DUFFY = 0, BEM_RULE_TRI7 = 1 };
-enum { BEM_FP64 = 0, BEM_MIXED = 1 };
+enum { BEM_FP64 = 0, BEM_MIXED = 1, BEM_MIXED_FULL = 2 };
 enum { BEM_ORDER_FIXED = 0, BEM_ORDER_LEARNED = 1 };
 
 typedef struct bem_ctx bem_ctx;
@@ -79,6 +79,10 @@ typedef struct {
  *                 identical and common-edge pairs stay FP64, and so do the
  *                 disjoint Helmholtz pairs of the piecewise-linear basis and
  *                 bem_pivot_entries.
+ *                 BEM_MIXED_FULL: as BEM_MIXED, and identical and common-edge
+ *                 pairs in FP32 too (x - y from the rule's difference columns
+ *                 and float edge vectors, double-layer numerators from
+ *                 double-float plane heights, Kahan-compensated sums).
  *   order_mode:   BEM_ORDER_FIXED (the orders above) or BEM_ORDER_LEARNED: for
  *                 bem_near_field on piecewise-constant meshes, every disjoint
  *                 pair gets the rule class the context's order model

@@ -21,7 +21,7 @@ ERRORS = {-1: "BEM_ERR_INVALID_ARG", -2: "BEM_ERR_CUDA", -3: "BEM_ERR_OOM",
 KERNELS = {"laplace_slp": 0, "laplace_dlp": 1, "helmholtz_slp": 2}
 BASES = {"p0": 0, "p1": 1}
 RULES = {"duffy": 0, "tri7": 1}
-PRECISIONS = {"fp64": 0, "mixed": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_full": 2}
 ORDER_MODES = {"fixed": 0, "learned": 1}
 EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_upload",
            "bem_mesh_free", "bem_mesh_info", "bem_near_field", "bem_coupling_blocks",

@@ -143,8 +143,9 @@ Mesh *get_mesh(bem_ctx *ctx, int id)
 int check_quad(bem_ctx *ctx, const bem_quad_desc *q, Rule2D &r2, bool block_rule = true)
 {
     if (!q) return fail(ctx, BEM_ERR_INVALID_ARG, "null quadrature descriptor");
-    if (q->precision != BEM_FP64 && q->precision != BEM_MIXED)
-        return fail(ctx, BEM_ERR_INVALID_ARG, "precision must be BEM_FP64 or BEM_MIXED");
+    if (q->precision != BEM_FP64 && !is_mixed(q->precision))
+        return fail(ctx, BEM_ERR_INVALID_ARG,
+                    "precision must be BEM_FP64, BEM_MIXED or BEM_MIXED_FULL");
     if (q->order_mode != BEM_ORDER_FIXED && q->order_mode != BEM_ORDER_LEARNED)
         return fail(ctx, BEM_ERR_INVALID_ARG, "order_mode must be BEM_ORDER_FIXED or BEM_ORDER_LEARNED");
     for (int v : {q->q_identical, q->q_edge, q->q_vertex})
@@ -211,7 +212,7 @@ int run_touching(bem_ctx *ctx, Mesh *m, const bem_kernel_desc *k, const bem_quad
                                        "touching_identical"};
         ProfScope ps(ctx, names[cas]);
         cudaError_t e = launch_touching(m->v, cas, m->list[cas], m->nlist[cas], r, k->kind,
-                                        k->kappa, q->precision == BEM_MIXED, ctx->stream);
+                                        k->kappa, touch_in_float(q->precision, cas), ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "touching kernel");
     }
     return BEM_OK;
@@ -280,7 +281,7 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
         L.kappa = J.kernel.kappa;
         L.lower_only = lower_only;
         L.allow_touching = allow_touching ? 1 : 0;
-        L.mixed = J.quad.precision == BEM_MIXED ? 1 : 0;
+        L.mixed = is_mixed(J.quad.precision) ? 1 : 0;
         const int tc = m->v.basis == BEM_P0 ? 8 : kTile;
         cudaError_t e;
         {

@@ -616,13 +616,20 @@ __device__ __forceinline__ void touch_pair(const MeshView &m, int idx, const dou
     }
 }
 
-// Common-vertex pairs in float (mixed form, Laplace kernels): the shared vertex is
-// the canonical vertex 0 of both triangles, so x - y is formed from edge
-// vectors only and keeps float precision down to the singular point.
-template <int KIND, int BASIS>
-__device__ __forceinline__ void touch_vertex_f32(const MeshView &m, int idx,
-                                                 const float *__restrict__ rule, int np, int lane,
-                                                 float kappa = 0.0f)
+// Touching pairs in float (mixed form).  The canonical vertex order puts the
+// shared vertices first, so x - y is formed from edge vectors and the rule's
+// difference columns only and keeps float precision down to the singular set:
+//   common vertex: x - y = x1 e1a + x2 e2a - y1 e1b - y2 e2b
+//   common edge:   x - y = (x1 - y1) e1 + x2 e2a - y2 e2b   (e1 shared)
+//   identical:     x - y = (x1 - y1) e1 + (x2 - y2) e2
+// The double-layer numerator (x - y) . n_y is the height of x above the trial
+// plane, an affine function on the test triangle whose vertex heights come
+// from the double-float vertex records: h(x) for a common vertex, x2 h(a2) for
+// a common edge (the shared vertices lie in the plane), 0 for identical
+// pairs.  Every lane sums its points with Kahan compensation.
+template <int CAS, int KIND, int BASIS>
+__device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const float *__restrict__ rule,
+                                          int np, int lane, float kappa = 0.0f)
 {
     constexpr bool CPLX = KIND == BEM_HELMHOLTZ_SLP;
     const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);
@@ -651,26 +658,47 @@ __device__ __forceinline__ void touch_vertex_f32(const MeshView &m, int idx,
         e1b[c] = dd_diff(bh[1][c], bl[1][c], bh[0][c], bl[0][c]);
         e2b[c] = dd_diff(bh[2][c], bl[2][c], bh[1][c], bl[1][c]);
     }
-    // heights of a's canonical vertices above b's plane (vertex 0 is shared)
     Height H = {};
-    if (KIND == BEM_LAPLACE_DLP)
+    float h2 = 0.0f;
+    if (KIND == BEM_LAPLACE_DLP && CAS == kVertex)
         H = make_height(ah[0], al[0], ah[1], al[1], ah[2], al[2], bh[0], bl[0], B.nh, B.nl);
+    if (KIND == BEM_LAPLACE_DLP && CAS == kEdge) {
+        float hh, hl;
+        dd_height(ah[2], al[2], bh[0], bl[0], B.nh, B.nl, hh, hl);
+        h2 = hh + hl;
+    }
     constexpr int NACC = BASIS == BEM_P0 ? 1 : 9;
-    float acc[NACC], acci[NACC];
+    float acc[NACC], cmp[NACC], acci[NACC], cmpi[NACC];
 #pragma unroll
-    for (int k = 0; k < NACC; ++k) acc[k] = acci[k] = 0.0f;
+    for (int k = 0; k < NACC; ++k) acc[k] = cmp[k] = acci[k] = cmpi[k] = 0.0f;
+    // an in-plane double layer vanishes identically on identical pairs
+    const bool zero = KIND == BEM_LAPLACE_DLP && CAS == kIdentical;
     const float *X1 = rule, *X2 = rule + np, *Y1 = rule + 2 * np, *Y2 = rule + 3 * np,
-                *W = rule + 4 * np;   // columns 5, 6 (differences) are not needed here
-    for (int p = lane; p < np; p += 32) {
+                *W = rule + 4 * np, *D1 = rule + 5 * np, *D2 = rule + 6 * np;
+    for (int p = lane; p < np && !zero; p += 32) {
         const float x1 = __ldg(X1 + p), x2 = __ldg(X2 + p), y1 = __ldg(Y1 + p),
                     y2 = __ldg(Y2 + p), w = __ldg(W + p);
-        const float dx = fmaf(x1, e1a[0], fmaf(x2, e2a[0], -fmaf(y1, e1b[0], y2 * e2b[0])));
-        const float dy = fmaf(x1, e1a[1], fmaf(x2, e2a[1], -fmaf(y1, e1b[1], y2 * e2b[1])));
-        const float dz = fmaf(x1, e1a[2], fmaf(x2, e2a[2], -fmaf(y1, e1b[2], y2 * e2b[2])));
-        const float dn = KIND == BEM_LAPLACE_DLP ? height_at(H, x1, x2) : 0.0f;
+        float dx, dy, dz, dn = 0.0f;
+        if (CAS == kVertex) {
+            dx = fmaf(x1, e1a[0], fmaf(x2, e2a[0], -fmaf(y1, e1b[0], y2 * e2b[0])));
+            dy = fmaf(x1, e1a[1], fmaf(x2, e2a[1], -fmaf(y1, e1b[1], y2 * e2b[1])));
+            dz = fmaf(x1, e1a[2], fmaf(x2, e2a[2], -fmaf(y1, e1b[2], y2 * e2b[2])));
+            if (KIND == BEM_LAPLACE_DLP) dn = height_at(H, x1, x2);
+        } else if (CAS == kEdge) {
+            const float d1 = __ldg(D1 + p);
+            dx = fmaf(d1, e1a[0], fmaf(x2, e2a[0], -y2 * e2b[0]));
+            dy = fmaf(d1, e1a[1], fmaf(x2, e2a[1], -y2 * e2b[1]));
+            dz = fmaf(d1, e1a[2], fmaf(x2, e2a[2], -y2 * e2b[2]));
+            if (KIND == BEM_LAPLACE_DLP) dn = x2 * h2;
+        } else {
+            const float d1 = __ldg(D1 + p), d2 = __ldg(D2 + p);
+            dx = fmaf(d1, e1a[0], d2 * e2a[0]);
+            dy = fmaf(d1, e1a[1], d2 * e2a[1]);
+            dz = fmaf(d1, e1a[2], d2 * e2a[2]);
+        }
         float wk, wki = 0.0f;
         if (CPLX) {
-            // the pair shares a vertex: kappa r stays below kappa times two diameters
+            // the pair touches: kappa r stays below kappa times two diameters
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float ri = rsqrtf(r2);
             float sn, cs;
@@ -680,40 +708,41 @@ __device__ __forceinline__ void touch_vertex_f32(const MeshView &m, int idx,
         } else {
             wk = w * kvalf<KIND>(dx, dy, dz, dn);
         }
-        if (BASIS == BEM_P0) {
-            acc[0] += wk;
-            if (CPLX) acci[0] += wki;
-        } else {
-            const float mx[3] = {1.0f, x1, x2}, my[3] = {1.0f, y1, y2};
+        const float mx[3] = {1.0f, x1, x2}, my[3] = {1.0f, y1, y2};
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const float f = wk * mx[i], fi = wki * mx[i];
+        for (int i = 0; i < (BASIS == BEM_P0 ? 1 : 3); ++i)
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    acc[i * 3 + j] = fmaf(f, my[j], acc[i * 3 + j]);
-                    if (CPLX) acci[i * 3 + j] = fmaf(fi, my[j], acci[i * 3 + j]);
+            for (int j = 0; j < (BASIS == BEM_P0 ? 1 : 3); ++j) {
+                const int k = BASIS == BEM_P0 ? 0 : i * 3 + j;
+                const float f = BASIS == BEM_P0 ? wk : wk * mx[i] * my[j];
+                const float yv = f - cmp[k];
+                const float t = acc[k] + yv;
+                cmp[k] = (t - acc[k]) - yv;
+                acc[k] = t;
+                if (CPLX) {
+                    const float fi = BASIS == BEM_P0 ? wki : wki * mx[i] * my[j];
+                    const float yi = fi - cmpi[k];
+                    const float ti = acci[k] + yi;
+                    cmpi[k] = (ti - acci[k]) - yi;
+                    acci[k] = ti;
                 }
             }
-        }
     }
+    // lane partial sums (with their compensations) reduced in double
+    double sr[NACC], si[NACC];
 #pragma unroll
     for (int k = 0; k < NACC; ++k) {
-        acc[k] = warp_sumf(acc[k]);
-        if (CPLX) acci[k] = warp_sumf(acci[k]);
+        sr[k] = warp_sum((double)acc[k] - (double)cmp[k]);
+        si[k] = CPLX ? warp_sum((double)acci[k] - (double)cmpi[k]) : 0.0;
     }
     if (lane == 0) {
         const double scale = (double)A.sg * (double)B.sg * kInv4Pi;
         if (BASIS == BEM_P0) {
-            m.table[idx] = make_double2((double)acc[0] * scale, (double)acci[0] * scale);
+            m.table[idx] = make_double2(sr[0] * scale, si[0] * scale);
         } else {
-            double M[9], Mi[9], hat[9], hati[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                M[k] = (double)acc[k];
-                Mi[k] = (double)acci[k];
-            }
-            moments_to_hats(M, hat);
-            moments_to_hats(Mi, hati);
+            double hat[9], hati[9];
+            moments_to_hats(sr, hat);
+            moments_to_hats(si, hati);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll

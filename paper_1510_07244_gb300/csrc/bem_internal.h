@@ -150,8 +150,16 @@ struct BlockLaunch {
     double kappa;
     int lower_only;
     int allow_touching;
-    int mixed;        // 1: regular pairs in FP32 (BEM_MIXED)
+    int mixed;        // 1: regular pairs in FP32 (BEM_MIXED, BEM_MIXED_FULL)
 };
+
+// Precision forms: float arithmetic for disjoint pairs, and for the touching
+// pairs of case `cas`.
+inline bool is_mixed(int precision) { return precision == BEM_MIXED || precision == BEM_MIXED_FULL; }
+inline int touch_in_float(int precision, int cas)
+{
+    return precision == BEM_MIXED_FULL || (precision == BEM_MIXED && cas == kVertex);
+}
 
 // One block list of a batched launch (device table entry).
 struct BatchJob {
@@ -174,7 +182,7 @@ struct Shape {
 cudaError_t launch_tile_prefix(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
                                int *status, cudaStream_t st);
 cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
-                            const Rule4D &rule, int kind, double kappa, int mixed,
+                            const Rule4D &rule, int kind, double kappa, int f32,
                             cudaStream_t st);
 cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const Rule2D &rule,
                                 const int64_t *prefix, int *status, int grid, cudaStream_t st);

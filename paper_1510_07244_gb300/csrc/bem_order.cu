@@ -938,7 +938,7 @@ int run_learned_p0(bem_ctx *ctx, const MeshView &mv, const BlockLaunch &L, const
     k_learned_select<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A, ctx->status);
     k_learned_offsets<<<1, 32, 0, ctx->stream>>>(A);
     k_learned_compact<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A);
-    const bool mixed = precision == BEM_MIXED;
+    const bool mixed = is_mixed(precision);
     for (int c = 0; c < kClasses; ++c) {
         Rule4D r;
         int rc = api_get_rule4(ctx, kRegular, kClassRule[c][0], kClassRule[c][1], r);

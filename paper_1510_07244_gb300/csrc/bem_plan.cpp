@@ -270,11 +270,10 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         t.kappa = ji.J->kernel.kappa;
         ji.touch_job = (int)tj.size();
         tj.push_back(t);
-        const int mixed = ji.J->quad.precision == BEM_MIXED;
         const int qs[4] = {0, ji.J->quad.q_vertex, ji.J->quad.q_edge, ji.J->quad.q_identical};
         for (int c = kVertex; c <= kIdentical; ++c) {
             auto &v = titems[std::make_tuple(mv.basis, ji.J->kernel.kind, c,
-                                             (c == kVertex) ? mixed : 0, qs[c])];
+                                             touch_in_float(ji.J->quad.precision, c), qs[c])];
             for (int idx : ji.m->hlist[c]) v.push_back(make_int2(ji.touch_job, idx));
         }
     }
@@ -307,7 +306,7 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
     for (auto &ji : jobs) {
         const bem_block_job &J = *ji.J;
         if (J.n_blocks == 0) continue;
-        const int mixed = J.quad.precision == BEM_MIXED &&
+        const int mixed = is_mixed(J.quad.precision) &&
                           !(J.kernel.kind == BEM_HELMHOLTZ_SLP && ji.m->v.basis == BEM_P1);
         char key[96];
         std::snprintf(key, sizeof key, "b%d k%d np%d m%d r%d q%d", ji.m->v.basis, J.kernel.kind,

@@ -1,5 +1,5 @@
 // Touching-pair kernels (Sauter-Schwab rules, Section 2.2): one warp per pair,
-// single-mesh and batched forms, FP64 and the mixed-form common-vertex kernel.
+// single-mesh and batched forms, FP64 and the float kernels of the mixed forms.
 #include <cuda_runtime.h>
 
 #include "bem_device.cuh"
@@ -28,39 +28,43 @@ __global__ void __launch_bounds__(256) k_touching_batch(const TouchJob *__restri
     touch_pair<KIND, BASIS, CAS>(jobs[it.x].m, it.y, rule, np, jobs[it.x].kappa, threadIdx.x & 31);
 }
 
-template <int KIND, int BASIS>
-__global__ void __launch_bounds__(256) k_touching_vertex_f32(MeshView m, const int *__restrict__ list,
-                                                             int64_t n, const float *__restrict__ rule,
-                                                             int np, float kappa)
+template <int CAS, int KIND, int BASIS>
+__global__ void __launch_bounds__(256) k_touching_f32(MeshView m, const int *__restrict__ list,
+                                                      int64_t n, const float *__restrict__ rule,
+                                                      int np, float kappa)
 {
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wid >= n) return;
-    touch_vertex_f32<KIND, BASIS>(m, __ldg(list + wid), rule, np, threadIdx.x & 31, kappa);
+    touch_f32<CAS, KIND, BASIS>(m, __ldg(list + wid), rule, np, threadIdx.x & 31, kappa);
 }
 
-template <int KIND, int BASIS>
-__global__ void __launch_bounds__(256) k_touching_vertex_f32_batch(const TouchJob *__restrict__ jobs,
-                                                                   const int2 *__restrict__ items,
-                                                                   int64_t n,
-                                                                   const float *__restrict__ rule,
-                                                                   int np)
+template <int CAS, int KIND, int BASIS>
+__global__ void __launch_bounds__(256) k_touching_f32_batch(const TouchJob *__restrict__ jobs,
+                                                            const int2 *__restrict__ items,
+                                                            int64_t n,
+                                                            const float *__restrict__ rule, int np)
 {
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wid >= n) return;
     const int2 it = items[wid];
-    touch_vertex_f32<KIND, BASIS>(jobs[it.x].m, it.y, rule, np, threadIdx.x & 31,
-                                  (float)jobs[it.x].kappa);
+    touch_f32<CAS, KIND, BASIS>(jobs[it.x].m, it.y, rule, np, threadIdx.x & 31,
+                                (float)jobs[it.x].kappa);
 }
 
 cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
-                            const Rule4D &rule, int kind, double kappa, int mixed, cudaStream_t st)
+                            const Rule4D &rule, int kind, double kappa, int f32, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + 7) / 8);
     const bool p1 = m.basis == BEM_P1;
-    if (mixed && cas == kVertex && rule.f) {
+    if (f32 && rule.f) {
         const float kf = (float)kappa;
-#define BEM_TV(K, B) k_touching_vertex_f32<K, B><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n, kf)
+#define BEM_TV(K, B)                                                                          \
+    do {                                                                                      \
+        if (cas == kIdentical) k_touching_f32<kIdentical, K, B><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n, kf); \
+        else if (cas == kEdge) k_touching_f32<kEdge, K, B><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n, kf);      \
+        else k_touching_f32<kVertex, K, B><<<blocks, 256, 0, st>>>(m, list, n, rule.f, rule.n, kf);                      \
+    } while (0)
         if (kind == BEM_LAPLACE_SLP) { if (p1) BEM_TV(BEM_LAPLACE_SLP, BEM_P1); else BEM_TV(BEM_LAPLACE_SLP, BEM_P0); }
         else if (kind == BEM_LAPLACE_DLP) { if (p1) BEM_TV(BEM_LAPLACE_DLP, BEM_P1); else BEM_TV(BEM_LAPLACE_DLP, BEM_P0); }
         else { if (p1) BEM_TV(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TV(BEM_HELMHOLTZ_SLP, BEM_P0); }
@@ -84,14 +88,19 @@ cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int cas, int mixed,
+cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int cas, int f32,
                                   const int2 *items, int64_t n, const Rule4D &rule, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + 7) / 8);
     const bool p1 = basis == BEM_P1;
-    if (mixed && cas == kVertex && rule.f) {
-#define BEM_TVB(K, B) k_touching_vertex_f32_batch<K, B><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n)
+    if (f32 && rule.f) {
+#define BEM_TVB(K, B)                                                                          \
+    do {                                                                                       \
+        if (cas == kIdentical) k_touching_f32_batch<kIdentical, K, B><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n); \
+        else if (cas == kEdge) k_touching_f32_batch<kEdge, K, B><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);      \
+        else k_touching_f32_batch<kVertex, K, B><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n);                      \
+    } while (0)
         if (kind == BEM_LAPLACE_SLP) { if (p1) BEM_TVB(BEM_LAPLACE_SLP, BEM_P1); else BEM_TVB(BEM_LAPLACE_SLP, BEM_P0); }
         else if (kind == BEM_LAPLACE_DLP) { if (p1) BEM_TVB(BEM_LAPLACE_DLP, BEM_P1); else BEM_TVB(BEM_LAPLACE_DLP, BEM_P0); }
         else { if (p1) BEM_TVB(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TVB(BEM_HELMHOLTZ_SLP, BEM_P0); }

@@ -48,7 +48,7 @@ def _jobs(pkg, ctx, w, precision):
     return mids, near, far, outs
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_full"])
 @pytest.mark.parametrize("flags", [0, 1, 3, 7])
 def test_plan_equals_per_job_calls(env, small_batch, precision, flags):
     pkg, ctx = env

@@ -271,14 +271,17 @@ def test_c2_full_size_sampled(ctx, pkg):
 # --------------------------------------------------------------------------
 MIXED_TOL = 1e-6
 LAPLACE = [("laplace_slp", 0.0), ("laplace_dlp", 0.0)]
+# "mixed": FP64 identical and common-edge pairs; "mixed_full": those in FP32 too
+MIXED_FORMS = ["mixed", "mixed_full"]
 
 
+@pytest.mark.parametrize("form", MIXED_FORMS)
 @pytest.mark.parametrize("meshname", ["ico2", "cube3", "torus"])
 @pytest.mark.parametrize("kernel,kappa", LAPLACE)
 @pytest.mark.parametrize("basis", ["p0", "p1"])
-def test_mixed_dense_matches_oracle(ctx, pkg, meshname, kernel, kappa, basis):
+def test_mixed_dense_matches_oracle(ctx, pkg, meshname, kernel, kappa, basis, form):
     mesh = MESHES[meshname]()
-    quad = dict(QUADS["paper"], precision="mixed")
+    quad = dict(QUADS["paper"], precision=form)
     got, n = _dense(ctx, pkg, mesh, basis, kernel, kappa, quad)
     rows = np.repeat(np.arange(n), n)
     cols = np.tile(np.arange(n), n)
@@ -292,10 +295,11 @@ def test_mixed_dense_matches_oracle(ctx, pkg, meshname, kernel, kappa, basis):
     assert err.max() > 1e-12
 
 
+@pytest.mark.parametrize("form", MIXED_FORMS)
 @pytest.mark.parametrize("basis", ["p0", "p1"])
 @pytest.mark.parametrize("kernel,kappa", LAPLACE)
-def test_mixed_near_field_and_coupling(ctx, pkg, basis, kernel, kappa):
-    quad = dict(QUADS["paper"], precision="mixed")
+def test_mixed_near_field_and_coupling(ctx, pkg, basis, kernel, kappa, form):
+    quad = dict(QUADS["paper"], precision=form)
     mesh = synth.jitter(synth.icosphere(3), 0.05, 23)
     part, near, far = h2_blocks(mesh, basis, leaf_size=16, eta=2.0, rank=6, pivot_seed=7)
     mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, basis)
@@ -313,12 +317,13 @@ def test_mixed_near_field_and_coupling(ctx, pkg, basis, kernel, kappa):
     ctx.bem_mesh_free(mid)
 
 
-def test_mixed_translated_far_from_origin(ctx, pkg):
+@pytest.mark.parametrize("form", MIXED_FORMS)
+def test_mixed_translated_far_from_origin(ctx, pkg, form):
     """The double-float anchors keep the mixed form accurate when the mesh sits
     far from the origin (coordinates ~1e3, triangles ~0.1)."""
     mesh = MESHES["cube3"]()
     moved = synth.Mesh(mesh.verts + np.array([1e3, -7e2, 3e2]), mesh.tris)
-    quad = dict(QUADS["paper"], precision="mixed")
+    quad = dict(QUADS["paper"], precision=form)
     for kernel in ("laplace_slp", "laplace_dlp"):
         got, n = _dense(ctx, pkg, moved, "p1", kernel, 0.0, quad)
         rows = np.repeat(np.arange(n), n)
@@ -329,15 +334,13 @@ def test_mixed_translated_far_from_origin(ctx, pkg):
 
 
 def test_mixed_full_size_against_fp64(ctx, pkg):
-    """Every entry of the 20480-triangle P1 workload: mixed form vs FP64 form."""
-    import torch
+    """Every entry of the 20480-triangle P1 workload: both mixed forms vs FP64 form."""
     w = synth.workloads.config2()
     mid = ctx.bem_mesh_upload(w.mesh.verts, w.mesh.tris, w.basis)
     q64 = w.quad.kw()
-    qmx = dict(q64, precision="mixed")
     for op in w.operators:
         res = {}
-        for name, q in (("fp64", q64), ("mixed", qmx)):
+        for name, q in [("fp64", q64)] + [(f, dict(q64, precision=f)) for f in MIXED_FORMS]:
             out_n = _out(w.near.n_entries, op.kernel)
             out_f = _out(w.far.n_entries, op.kernel)
             ctx.bem_near_field([block_job(pkg, mid, w.near, op.kernel, op.kappa, q, out_n)])
@@ -346,17 +349,19 @@ def test_mixed_full_size_against_fp64(ctx, pkg):
             res[name] = (out_n.cpu().numpy(), out_f.cpu().numpy())
         for k, bs in enumerate((w.near, w.far)):
             r, _ = bs.entry_indices()
-            err = rel_err(res["mixed"][k], res["fp64"][k], r)
-            assert err.max() <= MIXED_TOL, (op.kernel, k, err.max())
+            for f in MIXED_FORMS:
+                err = rel_err(res[f][k], res["fp64"][k], r)
+                assert err.max() <= MIXED_TOL, (op.kernel, f, k, err.max())
     ctx.bem_mesh_free(mid)
 
 
+@pytest.mark.parametrize("form", MIXED_FORMS)
 @pytest.mark.parametrize("meshname,kappa", [("cube3", 4.0), ("torus", 8.0), ("ico2", 16.0)])
-def test_mixed_helmholtz_p0(ctx, pkg, meshname, kappa):
+def test_mixed_helmholtz_p0(ctx, pkg, meshname, kappa, form):
     """Mixed Helmholtz (P0): FP32 disjoint and common-vertex pairs with the
     double-float reference phase; within 1e-6 of the oracle."""
     mesh = MESHES[meshname]()
-    quad = dict(QUADS["paper"], precision="mixed")
+    quad = dict(QUADS["paper"], precision=form)
     got, n = _dense(ctx, pkg, mesh, "p0", "helmholtz_slp", kappa, quad)
     rows = np.repeat(np.arange(n), n)
     cols = np.tile(np.arange(n), n)
