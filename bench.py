@@ -79,8 +79,19 @@ def kernel_flops(w, counts, stats, precision):
     mixed = precision in ("mixed", "mixed_full")
     out = {}
     laplace_ops = [o for o in w.operators if o.kernel != "helmholtz_slp"]
-    f_blk = sum(reg * npts_reg * flops_per_point(o.kernel, w.basis, np_axis) for o in w.operators)
     pipe = "fp32" if mixed and len(laplace_ops) == len(w.operators) else "fp64"
+    coupling = mixed and w.basis == "p1" and pipe == "fp32"
+    if coupling:
+        # coupling blocks run one entry per lane: deg(i) deg(j) pairs per entry,
+        # per point the piecewise-constant count (the trial basis value is
+        # folded into the trial weight), per test point 10 more (x 6, basis
+        # value and weight 2, accumulation 2)
+        reg = counts["near_regular_pairs"]
+        f_cpl = sum(counts["far_entry_pairs"] * npts_reg *
+                    (flops_per_point(o.kernel, "p0", np_axis) + 10.0 / np_axis)
+                    for o in w.operators)
+        out["coupling_p1"] = (f_cpl, "fp32")
+    f_blk = sum(reg * npts_reg * flops_per_point(o.kernel, w.basis, np_axis) for o in w.operators)
     out["block_p1" if w.basis == "p1" else "block_p0"] = (f_blk, pipe)
     for cas, nsub, qq, key in (("touching_vertex", 2, q.q_vertex, "n_vertex"),
                                ("touching_edge", 4, q.q_edge, "n_edge"),
@@ -195,10 +206,20 @@ def pair_counts(w):
         tp = float(np.asarray(touch[t, s]).ravel().sum())
         return total - tp, tp
 
+    def entry_pairs(bs):
+        # pairs summed entry by entry: sum over blocks of (sum deg i)(sum deg j)
+        deg = np.bincount(w.mesh.tris.ravel(), minlength=nv).astype(np.float64)
+        sdeg = np.add.reduceat(deg[bs.row_idx], bs.row_ptr[:-1]) if len(bs.row_idx) else np.zeros(0)
+        sdeg[np.diff(bs.row_ptr) == 0] = 0.0
+        return float(np.sum(sdeg[bs.blk_row] * sdeg[bs.blk_col]))
+
     near_reg, near_touch = block_pairs(w.near)
     far_reg, far_touch = block_pairs(w.far)
-    return {"near_regular_pairs": near_reg, "near_touching_lookups": near_touch,
-            "far_regular_pairs": far_reg, "far_touching_lookups": far_touch}
+    out = {"near_regular_pairs": near_reg, "near_touching_lookups": near_touch,
+           "far_regular_pairs": far_reg, "far_touching_lookups": far_touch}
+    if w.basis == "p1":
+        out["far_entry_pairs"] = entry_pairs(w.far)
+    return out
 
 
 def build_device_inputs(torch, pkg, w, dev, ranges=None):

@@ -282,11 +282,14 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
         L.lower_only = lower_only;
         L.allow_touching = allow_touching ? 1 : 0;
         L.mixed = is_mixed(J.quad.precision) ? 1 : 0;
-        const int tc = m->v.basis == BEM_P0 ? 8 : kTile;
+        const bool coupling = J.quad.order_mode == BEM_ORDER_FIXED &&
+                              use_coupling_engine(m->v.basis, L.kind, L.mixed, L.allow_touching);
+        const int tr = coupling ? kCouplingRows : kTile;
+        const int tc = coupling ? kCouplingCols : (m->v.basis == BEM_P0 ? 8 : kTile);
         cudaError_t e;
         {
             ProfScope ps(ctx, "tile_prefix");
-            e = launch_tile_prefix(L, kTile, tc, ctx->tile_prefix, ctx->status, ctx->stream);
+            e = launch_tile_prefix(L, tr, tc, ctx->tile_prefix, ctx->status, ctx->stream);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "tile prefix kernel");
         if (J.quad.order_mode == BEM_ORDER_LEARNED) {
@@ -297,6 +300,13 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
             ProfScope ps(ctx, "learned_p0");
             rc = run_learned_p0(ctx, m->v, L, ctx->tile_prefix, J.quad.precision);
             if (rc) return rc;
+            continue;
+        }
+        if (coupling) {
+            ProfScope ps(ctx, "coupling_p1");
+            e = launch_coupling_p1(m->v, L, r2, ctx->tile_prefix, ctx->status, ctx->num_sms * 4,
+                                   ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "coupling kernel");
             continue;
         }
         const int grid = ctx->num_sms * (m->v.basis == BEM_P0 ? 8 : 2);

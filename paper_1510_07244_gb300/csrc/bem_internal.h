@@ -202,6 +202,15 @@ cudaError_t launch_p1_batch_mixed(int kind, int np, const BatchJob *jobs, int n_
                                   cudaStream_t st);
 cudaError_t launch_tile_prefix_batch(BatchJob *jobs, int n_jobs, int tr, int tc, int64_t *job_total,
                                      int64_t *job_end, int *status, cudaStream_t st);
+// bem_coupling.cu: coupling blocks of the piecewise-linear basis, mixed form
+// (Laplace kernels), one entry per lane in warp tiles of 16 rows x 2 columns.
+constexpr int kCouplingRows = 16, kCouplingCols = 2;
+bool use_coupling_engine(int basis, int kind, int mixed, int allow_touching);
+cudaError_t launch_coupling_p1(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
+                               const int64_t *prefix, int *status, int grid, cudaStream_t st);
+cudaError_t launch_coupling_p1_batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end,
+                                     int kind, const Rule2D &R, int *status, int grid,
+                                     cudaStream_t st);
 cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int cas, int mixed,
                                   const int2 *items, int64_t n, const Rule4D &rule, cudaStream_t st);
 cudaError_t launch_block_batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end, int basis,

@@ -34,6 +34,7 @@ struct TouchBucket {
 
 struct BlockBucket {
     int basis, kind, mixed;
+    bool coupling = false;   // coupling engine (16 x 2 entry tiles) instead of the tile engine
     Rule2D r2;
     std::vector<BatchJob> host_jobs;
     BatchJob *jobs = nullptr;
@@ -89,12 +90,29 @@ void plan_free(bem_plan *p)
     delete p;
 }
 
-int default_mult(int basis, int mixed) { return basis == BEM_P0 ? 8 : (mixed ? 4 : 2); }
-
-std::vector<int> candidates(int basis, int mixed)
+int default_mult(const BlockBucket &b)
 {
-    if (basis == BEM_P0) return {4, 8, 16};
-    return mixed ? std::vector<int>{4, 8, 12} : std::vector<int>{1, 2, 3};
+    if (b.coupling) return 4;
+    return b.basis == BEM_P0 ? 8 : (b.mixed ? 4 : 2);
+}
+
+std::vector<int> candidates(const BlockBucket &b)
+{
+    if (b.coupling) return {3, 4, 6};
+    if (b.basis == BEM_P0) return {4, 8, 16};
+    return b.mixed ? std::vector<int>{4, 8, 12} : std::vector<int>{1, 2, 3};
+}
+
+int tile_rows(const BlockBucket &b) { return b.coupling ? kCouplingRows : kTile; }
+int tile_cols(const BlockBucket &b) { return b.coupling ? kCouplingCols : (b.basis == BEM_P0 ? 8 : kTile); }
+
+cudaError_t launch_bucket(bem_ctx *ctx, const BlockBucket &b, int mult, cudaStream_t st)
+{
+    if (b.coupling)
+        return launch_coupling_p1_batch(b.jobs, (int)b.host_jobs.size(), b.job_end, b.kind, b.r2,
+                                        ctx->status, ctx->num_sms * mult, st);
+    return launch_block_batch(b.jobs, (int)b.host_jobs.size(), b.job_end, b.basis, b.kind, b.mixed,
+                              b.r2, ctx->status, ctx->num_sms * mult, st);
 }
 
 // Issues the plan's launches on stream st (profiling events when prof != null).
@@ -124,16 +142,14 @@ cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
     }
     for (auto &b : p->bb) {
         ev_begin();
-        e = launch_tile_prefix_batch(b.jobs, (int)b.host_jobs.size(), kTile,
-                                     b.basis == BEM_P0 ? 8 : kTile, b.job_total, b.job_end,
-                                     ctx->status, st);
+        e = launch_tile_prefix_batch(b.jobs, (int)b.host_jobs.size(), tile_rows(b), tile_cols(b),
+                                     b.job_total, b.job_end, ctx->status, st);
         ev_end();
         if (e != cudaSuccess) return e;
     }
     for (auto &b : p->bb) {
         ev_begin();
-        e = launch_block_batch(b.jobs, (int)b.host_jobs.size(), b.job_end, b.basis, b.kind, b.mixed,
-                               b.r2, ctx->status, ctx->num_sms * b.grid_mult, st);
+        e = launch_bucket(ctx, b, b.grid_mult, st);
         ev_end();
         if (e != cudaSuccess) return e;
     }
@@ -150,9 +166,8 @@ int autotune(bem_ctx *ctx, bem_plan *p)
     for (auto &t : p->tb)
         launch_touching_batch(p->touch_jobs, t.basis, t.kind, t.cas, t.mixed, t.items, t.n, t.rule, st);
     for (auto &bk : p->bb)
-        launch_tile_prefix_batch(bk.jobs, (int)bk.host_jobs.size(), kTile,
-                                 bk.basis == BEM_P0 ? 8 : kTile, bk.job_total, bk.job_end,
-                                 ctx->status, st);
+        launch_tile_prefix_batch(bk.jobs, (int)bk.host_jobs.size(), tile_rows(bk), tile_cols(bk),
+                                 bk.job_total, bk.job_end, ctx->status, st);
     cudaError_t e = cudaStreamSynchronize(st);
     for (auto &bk : p->bb) {
         if (e != cudaSuccess) break;
@@ -163,12 +178,11 @@ int autotune(bem_ctx *ctx, bem_plan *p)
         }
         float best = 1e30f;
         int best_m = bk.grid_mult;
-        for (int mult : candidates(bk.basis, bk.mixed)) {
+        for (int mult : candidates(bk)) {
             float t_min = 1e30f;
             for (int rep = 0; rep < 2; ++rep) {
                 cudaEventRecord(a, st);
-                e = launch_block_batch(bk.jobs, (int)bk.host_jobs.size(), bk.job_end, bk.basis,
-                                       bk.kind, bk.mixed, bk.r2, ctx->status, ctx->num_sms * mult, st);
+                e = launch_bucket(ctx, bk, mult, st);
                 cudaEventRecord(b, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(b);
                 if (e != cudaSuccess) break;
@@ -308,19 +322,21 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         if (J.n_blocks == 0) continue;
         const int mixed = is_mixed(J.quad.precision) &&
                           !(J.kernel.kind == BEM_HELMHOLTZ_SLP && ji.m->v.basis == BEM_P1);
+        const bool coupling = use_coupling_engine(ji.m->v.basis, J.kernel.kind, mixed, ji.near ? 1 : 0);
         char key[96];
-        std::snprintf(key, sizeof key, "b%d k%d np%d m%d r%d q%d", ji.m->v.basis, J.kernel.kind,
-                      ji.r2.np, mixed, J.quad.regular_rule, J.quad.q_regular);
+        std::snprintf(key, sizeof key, "b%d k%d np%d m%d r%d q%d c%d", ji.m->v.basis, J.kernel.kind,
+                      ji.r2.np, mixed, J.quad.regular_rule, J.quad.q_regular, coupling ? 1 : 0);
         auto it = bindex.find(key);
         if (it == bindex.end()) {
             BlockBucket b;
             b.basis = ji.m->v.basis;
             b.kind = J.kernel.kind;
             b.mixed = mixed;
+            b.coupling = coupling;
             b.r2 = ji.r2;
             b.key = key;
-            b.name = b.basis == BEM_P0 ? "block_p0" : "block_p1";
-            b.grid_mult = default_mult(b.basis, mixed);
+            b.name = coupling ? "coupling_p1" : (b.basis == BEM_P0 ? "block_p0" : "block_p1");
+            b.grid_mult = default_mult(b);
             bindex[key] = (int)p->bb.size();
             p->bb.push_back(b);
             it = bindex.find(key);

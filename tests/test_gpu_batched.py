@@ -102,11 +102,14 @@ def test_plan_matches_oracle(env, small_batch):
         ctx.bem_mesh_free(m)
 
 
-def test_plan_p1_and_profile(env):
+@pytest.mark.parametrize("precision", ["fp64", "mixed_full"])
+def test_plan_p1_and_profile(env, precision):
     """Piecewise-linear jobs of two meshes in one plan; the launch profile
-    counts every bucket launch of every run."""
+    counts every bucket launch of every run.  In the mixed form the coupling
+    jobs run in their own bucket (coupling engine)."""
     import torch
     pkg, ctx = env
+    quad = dict(QUAD, precision=precision)
     jobs_n, jobs_f, outs, mids = [], [], [], []
     for lv, seed in ((2, 3), (3, 4)):
         mesh = synth.jitter(synth.icosphere(lv), 0.05, seed)
@@ -116,8 +119,8 @@ def test_plan_p1_and_profile(env):
         for kernel in ("laplace_slp", "laplace_dlp"):
             on = torch.zeros(max(1, near.n_entries), dtype=torch.float64, device="cuda")
             of = torch.zeros(max(1, far.n_entries), dtype=torch.float64, device="cuda")
-            jobs_n.append(block_job(pkg, mid, near, kernel, 0.0, QUAD, on))
-            jobs_f.append(block_job(pkg, mid, far, kernel, 0.0, QUAD, of))
+            jobs_n.append(block_job(pkg, mid, near, kernel, 0.0, quad, on))
+            jobs_f.append(block_job(pkg, mid, far, kernel, 0.0, quad, of))
             outs.append((on, of))
     for j in jobs_n:
         ctx.bem_near_field([j])
@@ -135,7 +138,9 @@ def test_plan_p1_and_profile(env):
     for (ra, rb), (a, b) in zip(ref, outs):
         assert torch.equal(a, ra) and torch.equal(b, rb)
     info = ctx.bem_plan_info(plan)
-    assert prof["block_p1"][0] == 3 * info["block_launches"]
+    engines = ["block_p1"] + (["coupling_p1"] if precision != "fp64" else [])
+    assert sum(prof[k][0] for k in engines) == 3 * info["block_launches"]
+    assert info["block_launches"] == len(engines) * 2      # per engine: SLP and DLP buckets
     assert all(v[1] > 0 for v in prof.values())
     ctx.bem_plan_destroy(plan)
     for m in mids:

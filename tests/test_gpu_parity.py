@@ -317,6 +317,50 @@ def test_mixed_near_field_and_coupling(ctx, pkg, basis, kernel, kappa, form):
     ctx.bem_mesh_free(mid)
 
 
+@pytest.mark.parametrize("kernel", ["laplace_slp", "laplace_dlp"])
+def test_coupling_engine_ragged_and_errors(ctx, pkg, kernel):
+    """Piecewise-linear coupling blocks of the mixed form (one entry per lane,
+    16 x 2 warp tiles): pivot sets of 1, 3, 17 (two row tiles) and 0 entries,
+    against the oracle; a touching pair or an index out of range sets the
+    status word and zeroes the entry."""
+    import torch
+    mesh = synth.jitter(synth.icosphere(3), 0.05, 29)
+    quad = dict(QUADS["paper"], precision="mixed_full")
+    rng = synth.SplitMix64(3)
+    # four clusters of far-apart vertices: around the poles +-z and +-x
+    v = mesh.verts
+    groups = [np.where(v[:, 2] > 0.97)[0][:1], np.where(v[:, 2] < -0.9)[0][:3],
+              np.where(v[:, 0] > 0.7)[0][:17], np.zeros(0, np.int64)]
+    ptr = np.concatenate([[0], np.cumsum([len(g) for g in groups])])
+    idx = np.concatenate(groups)
+    pairs = [(0, 1), (1, 0), (2, 1), (1, 2), (0, 2), (2, 3), (3, 0)]
+    sizes = [len(groups[a]) * len(groups[b]) for a, b in pairs]
+    off = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    bs = BlockSet(ptr, idx, ptr, idx, np.array([p[0] for p in pairs]),
+                  np.array([p[1] for p in pairs]), off, int(sum(sizes)))
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p1")
+    out = torch.full((bs.n_entries,), float("nan"), dtype=torch.float64, device="cuda")
+    ctx.bem_coupling_blocks([block_job(pkg, mid, bs, kernel, 0.0, quad, out)])
+    ctx.bem_sync()
+    r, c = bs.entry_indices()
+    ref = oracle_entries(mesh, "p1", r, c, kernel, 0.0, QUADS["paper"])
+    absint = oracle_absolute(mesh, "p1", r, c, kernel, 0.0, QUADS["paper"])
+    got = out.cpu().numpy()
+    assert rel_err_abs(got, ref, absint, r).max() <= MIXED_TOL
+    # a block whose supports touch (vertex 0 against its neighbour) is not admissible
+    nb = int(mesh.tris[np.where((mesh.tris == 0).any(axis=1))[0][0]][1:].max())
+    for pair in ([0, nb], [0, mesh.nv + 5]):
+        bad = BlockSet(np.array([0, 1, 2]), np.array(pair), np.array([0, 1, 2]), np.array(pair),
+                       np.array([0]), np.array([1]), np.array([0]), 1)
+        one = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        ctx.bem_coupling_blocks([block_job(pkg, mid, bad, kernel, 0.0, quad, one)])
+        with pytest.raises(pkg.BemError) as ei:
+            ctx.bem_sync()
+        assert ei.value.code == -1
+        assert one.item() == 0.0
+    ctx.bem_mesh_free(mid)
+
+
 @pytest.mark.parametrize("form", MIXED_FORMS)
 def test_mixed_translated_far_from_origin(ctx, pkg, form):
     """The double-float anchors keep the mixed form accurate when the mesh sits
