@@ -51,8 +51,8 @@ __device__ __forceinline__ float coupling_pair(const TriF &A, const TriF &B, int
 #pragma unroll
         for (int j = 0; j < NP; ++j)
             inner = fmaf(wy[j], kvalf<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], dn), inner);
-        const float lam = la == 0 ? 1.0f - s : (la == 1 ? s - t : t);
-        sum = fmaf(R.wf[i] * lam, inner, sum);
+        const float wx = la == 0 ? R.wl[0][i] : (la == 1 ? R.wl[1][i] : R.wl[2][i]);
+        sum = fmaf(wx, inner, sum);
     }
     return sum;
 }
@@ -96,7 +96,7 @@ __device__ __forceinline__ void coupling_tile(const MeshView &m, const BlockLaun
             yx[q] = fmaf(s, B.e1[0], t * B.e2[0]);
             yy[q] = fmaf(s, B.e1[1], t * B.e2[1]);
             yz[q] = fmaf(s, B.e1[2], t * B.e2[2]);
-            wy[q] = R.wf[q] * (lb == 0 ? 1.0f - s : (lb == 1 ? s - t : t));
+            wy[q] = lb == 0 ? R.wl[0][q] : (lb == 1 ? R.wl[1][q] : R.wl[2][q]);
         }
         for (int ka = alo; ka < ahi; ++ka) {
             const int a = __ldg(m.vt_tri + ka);

@@ -89,6 +89,17 @@ __device__ __forceinline__ float warp_sumf(float v)
     return v;
 }
 
+// 1/sqrt(x) in float as the single hardware approximation PTX calls
+// rsqrt.approx.ftz.f32 (relative error about 2^-23).  Every argument here is a
+// squared distance far above the subnormal range, so the flush changes
+// nothing and the subnormal fix-up of rsqrtf is not needed.
+__device__ __forceinline__ float rsqrt_fast(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---------------------------------------------------------------------------
 // Mixed form: float arithmetic with double-float set-up.  Every vertex is held
 // as hi + lo floats; differences of vertices and the heights of one
@@ -159,6 +170,21 @@ __device__ __forceinline__ float height_at(const Height &H, float s, float t)
     return b + lo;
 }
 
+// Sum over the warp of the unevaluated pairs hi + lo of every lane: TwoSum at
+// each butterfly level keeps the rounding error of the float additions.
+__device__ __forceinline__ void warp_sum2f(float &hi, float &lo)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        float sh, e;
+        two_sum(hi, h2, sh, e);
+        hi = sh;
+        lo = (lo + l2) + e;
+    }
+}
+
 // heights of the test triangle's vertices k0, k1, k2 above the trial plane
 // (through the trial vertex bh/bl with normal nh/nl) as affine coefficients
 __device__ __forceinline__ Height make_height(const float *a0h, const float *a0l,
@@ -220,7 +246,7 @@ template <int KIND>
 __device__ __forceinline__ float kvalf(float dx, float dy, float dz, float dn)
 {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float ri = rsqrtf(r2);
+    const float ri = rsqrt_fast(r2);
     if (KIND == BEM_LAPLACE_SLP) return ri;
     return dn * (ri * ri * ri);
 }
@@ -317,7 +343,7 @@ __device__ __forceinline__ void helm_value(const HelmPhase &P, float ex, float e
     const float q = fmaf(fmaf(2.0f, P.dcx, ex), ex,
                          fmaf(fmaf(2.0f, P.dcy, ey), ey, fmaf(2.0f, P.dcz, ez) * ez));
     const float r2 = P.r0sq + q;
-    const float ri = rsqrtf(r2);
+    const float ri = rsqrt_fast(r2);
     const float delta = __fdividef(q, fmaf(r2, ri, P.r0));
     float s, c;
     __sincosf(P.kap * delta, &s, &c);
@@ -433,19 +459,18 @@ __device__ __forceinline__ void regular_p1_f32(const TriF &A, const TriF &B, con
         const float xy = fmaf(R.sf[i], A.e1[1], fmaf(R.tf[i], A.e2[1], d0[1]));
         const float xz = fmaf(R.sf[i], A.e1[2], fmaf(R.tf[i], A.e2[2], d0[2]));
         const float dn = KIND == BEM_LAPLACE_DLP ? height_at(H, R.sf[i], R.tf[i]) : 0.0f;
+        // trial moments: sum_j w_j lambda_q(y_j) k(x_i, y_j), weights from the rule
         float ir[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            const float wk = R.wf[j] * kvalf<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], dn);
-            const float s_ = R.sf[j], t_ = R.tf[j];
-            ir[0] = fmaf(wk, 1.0f - s_, ir[0]);
-            ir[1] = fmaf(wk, s_ - t_, ir[1]);
-            ir[2] = fmaf(wk, t_, ir[2]);
+            const float k = kvalf<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], dn);
+            ir[0] = fmaf(R.wl[0][j], k, ir[0]);
+            ir[1] = fmaf(R.wl[1][j], k, ir[1]);
+            ir[2] = fmaf(R.wl[2][j], k, ir[2]);
         }
-        const float la[3] = {1.0f - R.sf[i], R.sf[i] - R.tf[i], R.tf[i]};
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            const float f = R.wf[i] * la[p];
+            const float f = R.wl[p][i];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const float y = fmaf(f, ir[q], -comp[p * 3 + q]);
@@ -700,7 +725,7 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
         if (CPLX) {
             // the pair touches: kappa r stays below kappa times two diameters
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ri = rsqrtf(r2);
+            const float ri = rsqrt_fast(r2);
             float sn, cs;
             sincosf(kappa * (r2 * ri), &sn, &cs);
             wk = w * cs * ri;
@@ -728,12 +753,19 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
                 }
             }
     }
-    // lane partial sums (with their compensations) reduced in double
+    // lane partial sums with their compensations, reduced as float pairs
     double sr[NACC], si[NACC];
 #pragma unroll
     for (int k = 0; k < NACC; ++k) {
-        sr[k] = warp_sum((double)acc[k] - (double)cmp[k]);
-        si[k] = CPLX ? warp_sum((double)acci[k] - (double)cmpi[k]) : 0.0;
+        float h = acc[k], l = -cmp[k];
+        warp_sum2f(h, l);
+        sr[k] = (double)h + (double)l;
+        si[k] = 0.0;
+        if (CPLX) {
+            float hi_ = acci[k], li_ = -cmpi[k];
+            warp_sum2f(hi_, li_);
+            si[k] = (double)hi_ + (double)li_;
+        }
     }
     if (lane == 0) {
         const double scale = (double)A.sg * (double)B.sg * kInv4Pi;
@@ -1011,7 +1043,8 @@ __device__ __forceinline__ int owner_pos(const MeshView &m, int T, const int *se
 
 // Collect the triangles touching the vertex set `set` (n <= 32): deterministic
 // order (by owner position, then adjacency order), and per vertex the list of
-// (triangle slot << 2 | local index).
+// (triangle slot << 2 | local index), sorted by slot so that the gather can
+// walk it once across the chunks of triangle rows.
 __device__ __forceinline__ void p1_support(const MeshView &m, const int *set, int n, int *tri, int *cnt,
                            int *off, int (*lists)[kTile], int *list_n, int *ntri,
                            int *status)
@@ -1056,7 +1089,14 @@ __device__ __forceinline__ void p1_support(const MeshView &m, const int *set, in
                 if (tri[u] == T) slot = u;
             const int4 tv = __ldg(m.tvid + T);
             const int loc = tv.x == v ? 0 : (tv.y == v ? 1 : 2);
-            lists[k - lo][tid] = (slot << 2) | loc;
+            // insertion into the slot-sorted list (slots are distinct)
+            int u = k - lo;
+            const int key = (slot << 2) | loc;
+            while (u > 0 && lists[u - 1][tid] > key) {
+                lists[u][tid] = lists[u - 1][tid];
+                --u;
+            }
+            lists[u][tid] = key;
         }
         list_n[tid] = hi - lo;
     }
@@ -1118,6 +1158,10 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
 #pragma unroll
         for (int e = 0; e < NE; ++e) accr[e] = acci[e] = cmpr[e] = 0;
         const int er = tid & 31;
+        // this thread's row vertex: its support list is sorted by triangle
+        // slot, so the rows of each chunk are the next run of the list
+        const int nrl = er < tr ? S.rl_n[er] : 0;
+        int u_end = 0;
         for (int ia0 = 0; ia0 < nta; ia0 += ia_step) {
             const int ia1 = min(nta, ia0 + ia_step);
             const int npairs = (ia1 - ia0) * ntb;
@@ -1169,13 +1213,14 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
                 }
             }
             __syncthreads();
+            const int u_beg = u_end;
+            while (u_end < nrl && (S.rl[u_end][er] >> 2) < ia1) ++u_end;
 #pragma unroll
             for (int e = 0; e < NE; ++e) {
                 const int ec = (tid >> 5) + EW * e;
                 if (er < tr && ec < tc) {
-                    for (int u = 0; u < S.rl_n[er]; ++u) {
+                    for (int u = u_beg; u < u_end; ++u) {
                         const int ia = S.rl[u][er] >> 2, la = S.rl[u][er] & 3;
-                        if (ia < ia0 || ia >= ia1) continue;
                         const int rowbase = (ia - ia0) * ntb;
                         for (int v = 0; v < S.cl_n[ec]; ++v) {
                             const int ib = S.cl[v][ec] >> 2, lb = S.cl[v][ec] & 3;

@@ -34,6 +34,9 @@ struct Rule2D {
     int np;
     double s[kMaxNp], t[kMaxNp], w[kMaxNp];
     float sf[kMaxNp], tf[kMaxNp], wf[kMaxNp];   // the same rule rounded to float
+    // w_k lambda_q(s_k, t_k) in float: the weights times the three linear
+    // basis functions of the reference triangle, lambda = (1 - s, s - t, t)
+    float wl[3][kMaxNp];
 };
 
 // 4D rule on D x D, device SoA with kRuleCols columns of n values:

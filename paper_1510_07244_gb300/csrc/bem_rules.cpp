@@ -88,6 +88,9 @@ static void round_rule(Rule2D &r)
         r.sf[k] = (float)r.s[k];
         r.tf[k] = (float)r.t[k];
         r.wf[k] = (float)r.w[k];
+        r.wl[0][k] = (float)(r.w[k] * (1.0 - r.s[k]));
+        r.wl[1][k] = (float)(r.w[k] * (r.s[k] - r.t[k]));
+        r.wl[2][k] = (float)(r.w[k] * r.t[k]);
     }
 }
 
