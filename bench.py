@@ -235,8 +235,13 @@ def build_device_inputs(torch, pkg, w, dev, ranges=None):
     for name, bs in (("near", w.near), ("far", w.far)):
         lo, hi = ranges[name] if ranges else (0, len(bs.blk_row))
         costs = block_costs(bs)[lo:hi]
-        sets[name] = dict(row_ptr=t32(bs.row_ptr), row_idx=t32(bs.row_idx), col_ptr=t32(bs.col_ptr),
-                          col_idx=t32(bs.col_idx), blk_row=t32(bs.blk_row[lo:hi]),
+        # rows and columns from the same arrays share one device copy (and one
+        # support table in the plan)
+        rp, ri = t32(bs.row_ptr), t32(bs.row_idx)
+        cp = rp if bs.col_ptr is bs.row_ptr else t32(bs.col_ptr)
+        ci = ri if bs.col_idx is bs.row_idx else t32(bs.col_idx)
+        sets[name] = dict(row_ptr=rp, row_idx=ri, col_ptr=cp,
+                          col_idx=ci, blk_row=t32(bs.blk_row[lo:hi]),
                           blk_col=t32(bs.blk_col[lo:hi]), blk_off=t64(bs.blk_off[lo:hi]),
                           n=bs.n_entries, mine=int(costs.sum()))
     return sets
@@ -336,8 +341,9 @@ def run_ours(args):
         info = ctx.bem_plan_info(plan)
         ctx.bem_plan_destroy(plan)
         total = reduce_over_ranks(float(sum(a.elapsed_time(b) for a, b in evs)), "max", dev)
-        # kernels per replay: one per touching bucket, prefix + scan + engine per block bucket
-        info["kernels_per_step"] = info["touch_launches"] + 3 * info["block_launches"]
+        # kernels per replay: touching buckets, block engines, prefix sums and support builds
+        info["kernels_per_step"] = (info["touch_launches"] + info["block_launches"] +
+                                    info["aux_launches"])
         return total, prof, info
 
     def roofline(prof, precision, steps):
@@ -423,9 +429,12 @@ def run_ours(args):
         pin = {}
         for name in ("near", "far"):
             bs = w.near if name == "near" else w.far
+            keys = ["row_ptr", "row_idx", "blk_row", "blk_col", "blk_off"]
+            if sets[name]["col_ptr"] is not sets[name]["row_ptr"]:
+                keys += ["col_ptr", "col_idx"]      # columns not shared with the rows
             pin[name] = {k: torch.from_numpy(np.ascontiguousarray(getattr(bs, k),
                                                                   np.int64 if k == "blk_off" else np.int32)).pin_memory()
-                         for k in ("row_ptr", "row_idx", "col_ptr", "col_idx", "blk_row", "blk_col", "blk_off")}
+                         for k in keys}
         host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
         h2d = sum(t.numel() * t.element_size() for d in pin.values() for t in d.values())
         h2d += w.mesh.verts.nbytes + w.mesh.tris.nbytes

@@ -275,6 +275,11 @@ int bem_learned_counts(bem_ctx *ctx, int64_t *counts /* [6] */);
  * bem_plan_create runs the plan's kernels once (or several times when
  * autotuning), so outputs are written at creation too.  Results are the
  * same, bit for bit, as those of bem_near_field / bem_coupling_blocks.
+ * Piecewise-linear near-field jobs read support records (the triangles
+ * around each 32-index slice of a cluster), built once per run for every
+ * distinct cluster list; their storage is sized from the lists' total length
+ * at creation (one device read), and a later run whose lists need more
+ * records reports BEM_ERR_INVALID_ARG through the status word.
  * Errors as bem_near_field; BEM_ERR_CUDA if graph capture fails. */
 typedef struct bem_plan bem_plan;
 #define BEM_PLAN_GRAPH    1
@@ -285,10 +290,13 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
                     bem_plan **plan);
 int bem_plan_run(bem_ctx *ctx, bem_plan *plan);
 int bem_plan_destroy(bem_ctx *ctx, bem_plan *plan);
-/* Launch counts of a plan (touching buckets, block buckets) and the chosen
- * CTAs per SM of up to `cap` block buckets. */
+/* Kernel launches of one plan run: touching buckets, block buckets, and the
+ * auxiliary launches (per block bucket its tile prefix sums, per distinct
+ * piecewise-linear cluster list its support records); the chosen CTAs per SM
+ * of up to `cap` block buckets.  Any pointer may be NULL. */
 int bem_plan_info(bem_ctx *ctx, bem_plan *plan, int32_t *n_touch_launches,
-                  int32_t *n_block_launches, int32_t *grid_mult, int32_t cap);
+                  int32_t *n_block_launches, int32_t *n_aux_launches, int32_t *grid_mult,
+                  int32_t cap);
 
 /* ---- sharding (multi-GPU) ----------------------------------------------------
  * Every matrix entry is independent (Section 3: the work lists need no

@@ -132,7 +132,7 @@ def load():
     lib.bem_plan_run.argtypes = [_vp, _vp]
     lib.bem_plan_destroy.argtypes = [_vp, _vp]
     lib.bem_plan_info.argtypes = [_vp, _vp, P(ctypes.c_int32), P(ctypes.c_int32),
-                                  P(ctypes.c_int32), ctypes.c_int32]
+                                  P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int32]
     lib.bem_rule_points.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
                                     ctypes.c_int64]
     lib.bem_profile_enable.argtypes = [_vp, ctypes.c_int32]
@@ -372,10 +372,11 @@ class Context:
         getattr(self, "_plans", {}).pop(plan.value, None)
 
     def bem_plan_info(self, plan):
-        nt, nb = ctypes.c_int32(0), ctypes.c_int32(0)
+        nt, nb, na = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
         g = (ctypes.c_int32 * 64)()
-        self._check(self.lib.bem_plan_info(self.h, plan, ctypes.byref(nt), ctypes.byref(nb), g, 64))
-        return {"touch_launches": nt.value, "block_launches": nb.value,
+        self._check(self.lib.bem_plan_info(self.h, plan, ctypes.byref(nt), ctypes.byref(nb),
+                                           ctypes.byref(na), g, 64))
+        return {"touch_launches": nt.value, "block_launches": nb.value, "aux_launches": na.value,
                 "grid_mult": [g[k] for k in range(min(64, nb.value))]}
 
     # ---- pivots (absolute sums) and the order model --------------------------

@@ -126,10 +126,112 @@ __global__ void __launch_bounds__(256) k_batch_p0(const BatchJob *__restrict__ j
     }
 }
 
+// ---------------------------------------------------------------------------
+// Support records of the piecewise-linear tile engine, built once per run for
+// every 32-index slice of a cluster list with the same p1_support the tiles
+// run otherwise (identical records, so identical results).
+// ---------------------------------------------------------------------------
+// slice[c] = sum over clusters before c of ceil(|c| / 32); slice[n] = total
+__global__ void __launch_bounds__(1024) k_slice_prefix(const int32_t *__restrict__ ptr, int32_t n,
+                                                       int32_t *slice, int *status)
+{
+    __shared__ int32_t part[1024];
+    const int32_t chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int32_t lo = min(n, (int32_t)threadIdx.x * chunk), hi = min(n, lo + chunk);
+    int32_t sum = 0;
+    for (int32_t c = lo; c < hi; ++c) {
+        const int32_t size = ptr[c + 1] - ptr[c];
+        if (size < 0) set_status(status, BEM_ERR_INVALID_ARG);
+        slice[c] = sum;   // local exclusive sum, offset below
+        sum += size > 0 ? (size + kTile - 1) / kTile : 0;
+    }
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const int32_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const int32_t base = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
+    for (int32_t c = lo; c < hi; ++c) slice[c] += base;
+    if (threadIdx.x == blockDim.x - 1) slice[n] = part[threadIdx.x];
+}
+
+struct SupBuildSmem {
+    int rows[kTile];
+    int tri[kP1MaxTri];
+    int cnt[kTile], off[kTile];
+    int lists[kMaxDegP1][kTile];
+    int list_n[kTile];
+    int ntri, bad;
+};
+
+__global__ void __launch_bounds__(128) k_build_supports(MeshView m, const int32_t *__restrict__ ptr,
+                                                        const int32_t *__restrict__ idx,
+                                                        int32_t n_clusters,
+                                                        const int32_t *__restrict__ slice,
+                                                        int32_t *sup, int64_t cap, int *status)
+{
+    __shared__ SupBuildSmem S;
+    const int tid = threadIdx.x;
+    const int64_t total = slice[n_clusters];
+    for (int64_t sl = blockIdx.x; sl < total; sl += gridDim.x) {
+        if (sl >= cap) {
+            if (tid == 0) set_status(status, BEM_ERR_INVALID_ARG);
+            break;
+        }
+        // cluster of this slice: the last c with slice[c] <= sl
+        int lo = 0, hi = n_clusters - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (slice[mid] <= sl) lo = mid;
+            else hi = mid - 1;
+        }
+        const int c = lo;
+        const int r0 = (int)(sl - slice[c]) * kTile;
+        const int n = min(kTile, ptr[c + 1] - ptr[c] - r0);
+        int32_t *rec = sup + sl * kSupInts;
+        if (tid == 0) S.bad = 0;
+        __syncthreads();
+        if (tid < n) {
+            const int v = idx[ptr[c] + r0 + tid];
+            if (v < 0 || v >= m.nv) S.bad = 1;
+            S.rows[tid] = v;
+        }
+        __syncthreads();
+        if (S.bad) {
+            if (tid == 0) {
+                rec[kSupCount] = -1;
+                set_status(status, BEM_ERR_INVALID_ARG);
+            }
+            __syncthreads();
+            continue;
+        }
+        p1_support(m, S.rows, n, S.tri, S.cnt, S.off, S.lists, S.list_n, &S.ntri, status);
+        for (int k = tid; k < kTile; k += blockDim.x) rec[kSupListN + k] = k < n ? S.list_n[k] : 0;
+        for (int k = tid; k < kMaxDegP1 * kTile; k += blockDim.x)
+            rec[kSupLists + k] = (&S.lists[0][0])[k];
+        for (int k = tid; k < S.ntri; k += blockDim.x) rec[kSupTris + k] = S.tri[k];
+        if (tid == 0) rec[kSupCount] = S.ntri;
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_build_supports(const MeshView &m, const int32_t *ptr, const int32_t *idx,
+                                  int32_t n_clusters, int32_t *slice, int32_t *sup, int64_t cap,
+                                  int *status, int grid, cudaStream_t st)
+{
+    if (n_clusters <= 0) return cudaSuccess;
+    k_slice_prefix<<<1, 1024, 0, st>>>(ptr, n_clusters, slice, status);
+    k_build_supports<<<grid, 128, 0, st>>>(m, ptr, idx, n_clusters, slice, sup, cap, status);
+    return cudaGetLastError();
+}
+
 size_t p1_smem_bytes(bool cplx, bool mixed)
 {
     return ((sizeof(P1Smem) + 15) & ~size_t(15)) +
-           (size_t)kP1Cap * 9 * (mixed ? sizeof(float) : sizeof(double)) * (cplx ? 2 : 1);
+           (size_t)p1_cap(mixed) * 9 * (mixed ? sizeof(float) : sizeof(double)) * (cplx ? 2 : 1);
 }
 
 // ---------------------------------------------------------------------------

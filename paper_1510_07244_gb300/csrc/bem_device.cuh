@@ -450,10 +450,11 @@ __device__ __forceinline__ void regular_p1_f32(const TriF &A, const TriF &B, con
     if (KIND == BEM_LAPLACE_DLP)
         H = make_height(A.vh[0], A.vl[0], A.vh[1], A.vl[1], A.vh[2], A.vl[2], B.vh[0], B.vl[0],
                         B.nh, B.nl);
-    float comp[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] = comp[k] = 0.0f;
-#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+    // outer points not unrolled: the unrolled inner loop alone keeps enough
+    // independent work, and the loop body stays small in the instruction cache
+#pragma unroll 1
     for (int i = 0; i < NP; ++i) {
         const float xx = fmaf(R.sf[i], A.e1[0], fmaf(R.tf[i], A.e2[0], d0[0]));
         const float xy = fmaf(R.sf[i], A.e1[1], fmaf(R.tf[i], A.e2[1], d0[1]));
@@ -473,10 +474,7 @@ __device__ __forceinline__ void regular_p1_f32(const TriF &A, const TriF &B, con
             const float f = R.wl[p][i];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const float y = fmaf(f, ir[q], -comp[p * 3 + q]);
-                const float t = acc[p * 3 + q] + y;
-                comp[p * 3 + q] = (t - acc[p * 3 + q]) - y;
-                acc[p * 3 + q] = t;
+                acc[p * 3 + q] = fmaf(f, ir[q], acc[p * 3 + q]);
             }
         }
     }
@@ -901,6 +899,7 @@ __device__ __forceinline__ void regular_p1(const Tri &A, const Tri &B, const Rul
 // ---------------------------------------------------------------------------
 struct BlockInfo {
     int ok;
+    int t, s;            // row and column cluster
     int r_lo, nr, c_lo, nc;
     int64_t off;
     int tile_in_blk;
@@ -925,6 +924,8 @@ __device__ __forceinline__ BlockInfo block_info(const BlockLaunch &L, const int6
     const int64_t b = find_block(prefix, L.n_blocks, tile);
     const int t = L.blk_row[b], s = L.blk_col[b];
     bi.ok = 0;
+    bi.t = t;
+    bi.s = s;
     if (t < 0 || t >= L.n_row_clusters || s < 0 || s >= L.n_col_clusters) {
         set_status(status, BEM_ERR_INVALID_ARG);
         return bi;
@@ -1007,7 +1008,9 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
 // chunk (one thread per pair) into shared memory and gathered by the owner
 // thread of each entry in a fixed order (deterministic sums).
 // ---------------------------------------------------------------------------
-constexpr int kP1Cap = 512;                 // pairs per chunk
+// pairs per chunk: float results (36 KB per chunk) leave room for four CTAs
+// per SM; double results stay at 512 pairs so that complex chunks fit too
+__host__ __device__ constexpr int p1_cap(bool mixed) { return mixed ? 1024 : 512; }
 constexpr int kP1MaxTri = kTile * kMaxDegP1;
 
 struct P1Smem {
@@ -1103,6 +1106,30 @@ __device__ __forceinline__ void p1_support(const MeshView &m, const int *set, in
     __syncthreads();
 }
 
+static_assert(kSupCount + 1 <= kSupInts && kSupLists % 4 == 0 && kSupTris % 4 == 0 &&
+                  kSupInts % 4 == 0,
+              "support records must be int4-aligned");
+
+// Copies one support record (built by k_build_supports) into shared memory;
+// returns the triangle count, or -1 for a record marked invalid.
+__device__ __forceinline__ int p1_load_support(const int32_t *__restrict__ rec, int *tri,
+                                               int (*lists)[kTile], int *list_n)
+{
+    const int nt = __ldg(rec + kSupCount);
+    const int4 *src = reinterpret_cast<const int4 *>(rec);
+    for (int k = threadIdx.x; k < kSupCount / 4; k += blockDim.x) {
+        const int w = 4 * k;
+        if (w < kSupLists) {
+            *reinterpret_cast<int4 *>(list_n + w) = __ldg(src + k);
+        } else if (w < kSupTris) {
+            *reinterpret_cast<int4 *>(&lists[0][0] + (w - kSupLists)) = __ldg(src + k);
+        } else if (w - kSupTris < nt) {
+            *reinterpret_cast<int4 *>(tri + (w - kSupTris)) = __ldg(src + k);
+        }
+    }
+    return nt;
+}
+
 // Threads per CTA of the P1 block engine: the FP64 form saturates the FP64
 // pipe with one 256-thread CTA per SM; the float form runs 128-thread CTAs,
 // several per SM, so that one CTA's barrier waits overlap another's math.
@@ -1123,7 +1150,7 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
     using Val = typename std::conditional<MIXED, float, double>::type;
     P1Smem &S = *reinterpret_cast<P1Smem *>(smem_raw);
     Val *buf_r = reinterpret_cast<Val *>(smem_raw + ((sizeof(P1Smem) + 15) & ~size_t(15)));
-    Val *buf_i = buf_r + kP1Cap * 9;
+    Val *buf_i = buf_r + p1_cap(MIXED) * 9;
     const int tid = threadIdx.x;
     {
         const BlockInfo bi = block_info(L, prefix, tile, status);
@@ -1150,10 +1177,30 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
             __syncthreads();
             return;
         }
-        p1_support(m, S.rows, tr, S.ta, S.cnt_r, S.off_r, S.rl, S.rl_n, &S.nta, status);
-        p1_support(m, S.cols, tc, S.tb, S.cnt_c, S.off_c, S.cl, S.cl_n, &S.ntb, status);
-        const int nta = S.nta, ntb = S.ntb;
-        const int ia_step = max(1, kP1Cap / max(ntb, 1));
+        int nta, ntb;
+        if (L.sup_r) {
+            // supports built once per run for every cluster slice
+            const int64_t sr = (int64_t)__ldg(L.slice_r + bi.t) + r0 / kTile;
+            const int64_t sc = (int64_t)__ldg(L.slice_c + bi.s) + c0 / kTile;
+            if (sr >= L.cap_r || sc >= L.cap_c) {
+                if (tid == 0) set_status(status, BEM_ERR_INVALID_ARG);
+                return;   // uniform across the CTA
+            }
+            nta = p1_load_support(L.sup_r + sr * kSupInts, S.ta, S.rl, S.rl_n);
+            ntb = p1_load_support(L.sup_c + sc * kSupInts, S.tb, S.cl, S.cl_n);
+            __syncthreads();
+            if (nta < 0 || ntb < 0) {
+                if (tid == 0) set_status(status, BEM_ERR_INVALID_ARG);
+                __syncthreads();
+                return;
+            }
+        } else {
+            p1_support(m, S.rows, tr, S.ta, S.cnt_r, S.off_r, S.rl, S.rl_n, &S.nta, status);
+            p1_support(m, S.cols, tc, S.tb, S.cnt_c, S.off_c, S.cl, S.cl_n, &S.ntb, status);
+            nta = S.nta;
+            ntb = S.ntb;
+        }
+        const int ia_step = max(1, p1_cap(MIXED) / max(ntb, 1));
         Val accr[NE], acci[NE], cmpr[NE];   // cmpr: Kahan compensation (mixed form)
 #pragma unroll
         for (int e = 0; e < NE; ++e) accr[e] = acci[e] = cmpr[e] = 0;

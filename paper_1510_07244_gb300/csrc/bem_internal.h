@@ -154,7 +154,21 @@ struct BlockLaunch {
     int lower_only;
     int allow_touching;
     int mixed;        // 1: regular pairs in FP32 (BEM_MIXED, BEM_MIXED_FULL)
+    // piecewise-linear tile engine: support records of the 32-index slices of
+    // the row / column clusters, built once per run (null: built per tile);
+    // slice_*[c] = first record of cluster c, cap_* = records allocated
+    const int32_t *sup_r = nullptr, *sup_c = nullptr;
+    const int32_t *slice_r = nullptr, *slice_c = nullptr;
+    int64_t cap_r = 0, cap_c = 0;
 };
+
+// One support record (int32 words, 16-byte multiple): list lengths [kTile],
+// per-vertex lists [kMaxDegP1][kTile], triangles [kTile * kMaxDegP1], count.
+constexpr int kSupListN = 0;
+constexpr int kSupLists = kTile;
+constexpr int kSupTris = kSupLists + kMaxDegP1 * kTile;
+constexpr int kSupCount = kSupTris + kTile * kMaxDegP1;
+constexpr int kSupInts = (kSupCount + 1 + 3) & ~3;
 
 // Precision forms: float arithmetic for disjoint pairs, and for the touching
 // pairs of case `cas`.
@@ -214,6 +228,12 @@ cudaError_t launch_coupling_p1(const MeshView &m, const BlockLaunch &L, const Ru
 cudaError_t launch_coupling_p1_batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end,
                                      int kind, const Rule2D &R, int *status, int grid,
                                      cudaStream_t st);
+// bem_block.cu: support records of all 32-index slices of a cluster list
+// (ptr, idx, n_clusters) into sup (cap records); slice gets n_clusters + 1
+// entries (exclusive prefix of the slice counts).
+cudaError_t launch_build_supports(const MeshView &m, const int32_t *ptr, const int32_t *idx,
+                                  int32_t n_clusters, int32_t *slice, int32_t *sup, int64_t cap,
+                                  int *status, int grid, cudaStream_t st);
 cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int cas, int mixed,
                                   const int2 *items, int64_t n, const Rule4D &rule, cudaStream_t st);
 cudaError_t launch_block_batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end, int basis,

@@ -43,6 +43,16 @@ struct BlockBucket {
     std::string key, name;
 };
 
+// Support records of one cluster list of one mesh, shared by every P1 tile
+// engine job that uses the list (rows or columns).
+struct SupTable {
+    MeshView m;
+    const int32_t *ptr, *idx;
+    int32_t n;
+    int32_t *slice = nullptr, *sup = nullptr;
+    int64_t cap = 0;
+};
+
 }  // namespace
 
 struct bem_plan {
@@ -52,6 +62,7 @@ struct bem_plan {
     TouchJob *touch_jobs = nullptr;
     std::vector<TouchBucket> tb;
     std::vector<BlockBucket> bb;
+    std::vector<SupTable> sup;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<bem_prof_rec> prof;   // event pairs recorded around each launch
@@ -103,6 +114,35 @@ std::vector<int> candidates(const BlockBucket &b)
     return b.mixed ? std::vector<int>{4, 8, 12} : std::vector<int>{1, 2, 3};
 }
 
+// The support table of (mesh, cluster list), created on first use.  Its size
+// comes from the list's current total length (one read from the device):
+// sum ceil(|c| / 32) <= total / 32 + n records.
+cudaError_t plan_support(bem_plan *p, const MeshView &m, const int32_t *ptr, const int32_t *idx,
+                         int32_t n, int *out)
+{
+    for (size_t k = 0; k < p->sup.size(); ++k) {
+        const SupTable &s = p->sup[k];
+        if (s.m.geom == m.geom && s.ptr == ptr && s.idx == idx && s.n == n) {
+            *out = (int)k;
+            return cudaSuccess;
+        }
+    }
+    int32_t total = 0;
+    cudaError_t e = cudaMemcpy(&total, ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    SupTable s;
+    s.m = m;
+    s.ptr = ptr;
+    s.idx = idx;
+    s.n = n;
+    s.cap = (int64_t)std::max(total, 0) / kTile + n + 1;
+    if ((e = plan_alloc(p, &s.slice, (size_t)n + 1)) != cudaSuccess) return e;
+    if ((e = plan_alloc(p, &s.sup, (size_t)s.cap * kSupInts)) != cudaSuccess) return e;
+    *out = (int)p->sup.size();
+    p->sup.push_back(s);
+    return cudaSuccess;
+}
+
 int tile_rows(const BlockBucket &b) { return b.coupling ? kCouplingRows : kTile; }
 int tile_cols(const BlockBucket &b) { return b.coupling ? kCouplingCols : (b.basis == BEM_P0 ? 8 : kTile); }
 
@@ -140,6 +180,13 @@ cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
         ev_end();
         if (e != cudaSuccess) return e;
     }
+    for (auto &s : p->sup) {
+        ev_begin();
+        e = launch_build_supports(s.m, s.ptr, s.idx, s.n, s.slice, s.sup, s.cap, ctx->status,
+                                  ctx->num_sms * 4, st);
+        ev_end();
+        if (e != cudaSuccess) return e;
+    }
     for (auto &b : p->bb) {
         ev_begin();
         e = launch_tile_prefix_batch(b.jobs, (int)b.host_jobs.size(), tile_rows(b), tile_cols(b),
@@ -165,6 +212,9 @@ int autotune(bem_ctx *ctx, bem_plan *p)
     // prerequisites once: touching tables and tile prefix sums
     for (auto &t : p->tb)
         launch_touching_batch(p->touch_jobs, t.basis, t.kind, t.cas, t.mixed, t.items, t.n, t.rule, st);
+    for (auto &s : p->sup)
+        launch_build_supports(s.m, s.ptr, s.idx, s.n, s.slice, s.sup, s.cap, ctx->status,
+                              ctx->num_sms * 4, st);
     for (auto &bk : p->bb)
         launch_tile_prefix_batch(bk.jobs, (int)bk.host_jobs.size(), tile_rows(bk), tile_cols(bk),
                                  bk.job_total, bk.job_end, ctx->status, st);
@@ -362,6 +412,23 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         L.lower_only = 0;
         L.allow_touching = ji.near ? 1 : 0;
         L.mixed = mixed;
+        if (b.basis == BEM_P1 && !b.coupling) {
+            // the tile engine reads per-slice support records built once per run
+            int rows = -1, cols = -1;
+            cudaError_t es = plan_support(p, ji.m->v, J.row_ptr, J.row_idx, J.n_row_clusters, &rows);
+            if (es == cudaSuccess)
+                es = plan_support(p, ji.m->v, J.col_ptr, J.col_idx, J.n_col_clusters, &cols);
+            if (es != cudaSuccess) {
+                plan_free(p);
+                return api_cuda_fail(ctx, es, "plan support tables");
+            }
+            L.sup_r = p->sup[rows].sup;
+            L.slice_r = p->sup[rows].slice;
+            L.cap_r = p->sup[rows].cap;
+            L.sup_c = p->sup[cols].sup;
+            L.slice_c = p->sup[cols].slice;
+            L.cap_c = p->sup[cols].cap;
+        }
         int64_t *prefix = nullptr;
         if ((e = plan_alloc(p, &prefix, (size_t)J.n_blocks)) != cudaSuccess) {
             plan_free(p);
@@ -380,14 +447,15 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         }
     }
     // profiling events: one pair per launch of issue()
-    const size_t nlaunch = p->tb.size() + 2 * p->bb.size();
-    for (size_t k = 0; k < nlaunch; ++k) {
+    const size_t nt = p->tb.size(), ns = p->sup.size(), nb = p->bb.size();
+    for (size_t k = 0; k < nt + ns + 2 * nb; ++k) {
         bem_prof_rec r;
         cudaEventCreate(&r.a);
         cudaEventCreate(&r.b);
-        if (k < p->tb.size()) r.name = p->tb[k].name;
-        else if (k < p->tb.size() + p->bb.size()) r.name = "tile_prefix";
-        else r.name = p->bb[k - p->tb.size() - p->bb.size()].name;
+        if (k < nt) r.name = p->tb[k].name;
+        else if (k < nt + ns) r.name = "supports";
+        else if (k < nt + ns + nb) r.name = "tile_prefix";
+        else r.name = p->bb[k - nt - ns - nb].name;
         p->prof.push_back(r);
     }
 
@@ -457,11 +525,14 @@ int bem_plan_destroy(bem_ctx *ctx, bem_plan *p)
 }
 
 int bem_plan_info(bem_ctx *ctx, bem_plan *p, int32_t *n_touch_launches, int32_t *n_block_launches,
-                  int32_t *grid_mult, int32_t cap)
+                  int32_t *n_aux_launches, int32_t *grid_mult, int32_t cap)
 {
     if (!ctx || !p) return BEM_ERR_INVALID_ARG;
     if (n_touch_launches) *n_touch_launches = (int32_t)p->tb.size();
     if (n_block_launches) *n_block_launches = (int32_t)p->bb.size();
+    // per block bucket: tile prefix sums and job scan; per support table:
+    // slice prefix and record build
+    if (n_aux_launches) *n_aux_launches = (int32_t)(2 * p->bb.size() + 2 * p->sup.size());
     for (int k = 0; grid_mult && k < cap && k < (int)p->bb.size(); ++k) grid_mult[k] = p->bb[k].grid_mult;
     return BEM_OK;
 }

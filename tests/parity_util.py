@@ -65,9 +65,13 @@ def to_dev(a, dtype):
 
 
 def block_job(pkg, mesh_id, bs, kernel, kappa, quad, out):
+    """A job over a block set; row and column clusters given by the same host
+    arrays share one device copy (and so one support table in a plan)."""
     import torch
-    return pkg.BlockJob(mesh_id, to_dev(bs.row_ptr, torch.int32), to_dev(bs.row_idx, torch.int32),
-                        to_dev(bs.col_ptr, torch.int32), to_dev(bs.col_idx, torch.int32),
+    rp, ri = to_dev(bs.row_ptr, torch.int32), to_dev(bs.row_idx, torch.int32)
+    cp = rp if bs.col_ptr is bs.row_ptr else to_dev(bs.col_ptr, torch.int32)
+    ci = ri if bs.col_idx is bs.row_idx else to_dev(bs.col_idx, torch.int32)
+    return pkg.BlockJob(mesh_id, rp, ri, cp, ci,
                         to_dev(bs.blk_row, torch.int32), to_dev(bs.blk_col, torch.int32),
                         to_dev(bs.blk_off, torch.int64), out,
                         pkg.kernel_desc(kernel, kappa), pkg.quad_desc(**quad))

@@ -102,18 +102,21 @@ def test_plan_matches_oracle(env, small_batch):
         ctx.bem_mesh_free(m)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed_full"])
-def test_plan_p1_and_profile(env, precision):
+@pytest.mark.parametrize("precision,leaf", [("fp64", 16), ("mixed_full", 16), ("mixed_full", 64)])
+def test_plan_p1_and_profile(env, precision, leaf):
     """Piecewise-linear jobs of two meshes in one plan; the launch profile
     counts every bucket launch of every run.  In the mixed form the coupling
-    jobs run in their own bucket (coupling engine)."""
+    jobs run in their own bucket (coupling engine).  The plan's near-field
+    tiles read support records built once per run (clusters of up to 64
+    indices: several 32-index slices each), the per-job calls build them per
+    tile: the results agree bit for bit."""
     import torch
     pkg, ctx = env
     quad = dict(QUAD, precision=precision)
     jobs_n, jobs_f, outs, mids = [], [], [], []
     for lv, seed in ((2, 3), (3, 4)):
         mesh = synth.jitter(synth.icosphere(lv), 0.05, seed)
-        _, near, far = synth.workloads.h2_blocks(mesh, "p1", 16, 2.0, 6, seed)
+        _, near, far = synth.workloads.h2_blocks(mesh, "p1", leaf, 2.0, 6, seed)
         mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p1")
         mids.append(mid)
         for kernel in ("laplace_slp", "laplace_dlp"):
@@ -138,9 +141,15 @@ def test_plan_p1_and_profile(env, precision):
     for (ra, rb), (a, b) in zip(ref, outs):
         assert torch.equal(a, ra) and torch.equal(b, rb)
     info = ctx.bem_plan_info(plan)
-    engines = ["block_p1"] + (["coupling_p1"] if precision != "fp64" else [])
+    engines = [k for k in ("block_p1", "coupling_p1") if k in prof]
+    assert "block_p1" in engines and (precision != "fp64" or len(engines) == 1)
     assert sum(prof[k][0] for k in engines) == 3 * info["block_launches"]
     assert info["block_launches"] == len(engines) * 2      # per engine: SLP and DLP buckets
+    # one support build per distinct cluster list (rows = columns here) per run
+    # (jobs without blocks need none)
+    tables = info["aux_launches"] // 2 - info["block_launches"]
+    assert 2 <= tables <= len(jobs_n) + len(jobs_f)
+    assert prof["supports"][0] == 3 * tables
     assert all(v[1] > 0 for v in prof.values())
     ctx.bem_plan_destroy(plan)
     for m in mids:
