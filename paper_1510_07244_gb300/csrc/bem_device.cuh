@@ -516,6 +516,17 @@ __device__ __forceinline__ void moments_to_hats(const T M[9], T out[9])
     }
 }
 
+// float-float value (unevaluated hi + lo) for moments_to_hats in the float kernels
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ FF operator-(FF a, FF b)
+{
+    FF r;
+    dd_sub(a.h, a.l, b.h, b.l, r.h, r.l);
+    return r;
+}
+
 template <int KIND, int BASIS, int CAS>
 __device__ __forceinline__ void touch_pair(const MeshView &m, int idx, const double *__restrict__ rule,
                                            int np, double kappa, int lane)
@@ -751,34 +762,42 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
                 }
             }
     }
-    // lane partial sums with their compensations, reduced as float pairs
-    double sr[NACC], si[NACC];
+    // lane partial sums with their compensations, reduced as float pairs;
+    // the hats are formed in float-float as well, and lane q < 9 converts and
+    // stores hat q, so the few double operations run once per pair
+    FF mr[NACC], mi[NACC];
 #pragma unroll
     for (int k = 0; k < NACC; ++k) {
-        float h = acc[k], l = -cmp[k];
-        warp_sum2f(h, l);
-        sr[k] = (double)h + (double)l;
-        si[k] = 0.0;
+        mr[k] = FF{acc[k], -cmp[k]};
+        warp_sum2f(mr[k].h, mr[k].l);
+        mi[k] = FF{0.0f, 0.0f};
         if (CPLX) {
-            float hi_ = acci[k], li_ = -cmpi[k];
-            warp_sum2f(hi_, li_);
-            si[k] = (double)hi_ + (double)li_;
+            mi[k] = FF{acci[k], -cmpi[k]};
+            warp_sum2f(mi[k].h, mi[k].l);
         }
     }
-    if (lane == 0) {
-        const double scale = (double)A.sg * (double)B.sg * kInv4Pi;
-        if (BASIS == BEM_P0) {
-            m.table[idx] = make_double2(sr[0] * scale, si[0] * scale);
-        } else {
-            double hat[9], hati[9];
-            moments_to_hats(sr, hat);
-            moments_to_hats(si, hati);
+    if (BASIS == BEM_P0) {
+        if (lane == 0) {
+            const double scale = (double)A.sg * (double)B.sg * kInv4Pi;
+            m.table[idx] = make_double2(((double)mr[0].h + (double)mr[0].l) * scale,
+                                        ((double)mi[0].h + (double)mi[0].l) * scale);
+        }
+    } else {
+        FF hr[9], hi[9];
+        moments_to_hats(mr, hr);
+        if (CPLX) moments_to_hats(mi, hi);
+        FF vr = hr[0], vi = CPLX ? hi[0] : FF{0.0f, 0.0f};
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    m.table[(int64_t)idx * 9 + pa[i] * 3 + pb[j]] =
-                        make_double2(hat[i * 3 + j] * scale, hati[i * 3 + j] * scale);
+        for (int q = 1; q < 9; ++q)
+            if (lane == q) {
+                vr = hr[q];
+                if (CPLX) vi = hi[q];
+            }
+        if (lane < 9) {
+            const double scale = (double)A.sg * (double)B.sg * kInv4Pi;
+            m.table[(int64_t)idx * 9 + pa[lane / 3] * 3 + pb[lane % 3]] =
+                make_double2(((double)vr.h + (double)vr.l) * scale,
+                             ((double)vi.h + (double)vi.l) * scale);
         }
     }
 }
