@@ -692,14 +692,38 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
         e1b[c] = dd_diff(bh[1][c], bl[1][c], bh[0][c], bl[0][c]);
         e2b[c] = dd_diff(bh[2][c], bl[2][c], bh[1][c], bl[1][c]);
     }
+    // Double-layer heights of a's canonical vertices 1, 2 above b's plane (the
+    // shared vertex 0 lies in it).  Neighbours can be nearly coplanar, and then
+    // the height is a tiny difference of edge-sized terms: the 48-bit hi + lo
+    // vertices are too coarse for it, so lane 0 takes it from the FP64 records
+    // (the precision of the input) and broadcasts it.
     Height H = {};
     float h2 = 0.0f;
-    if (KIND == BEM_LAPLACE_DLP && CAS == kVertex)
-        H = make_height(ah[0], al[0], ah[1], al[1], ah[2], al[2], bh[0], bl[0], B.nh, B.nl);
-    if (KIND == BEM_LAPLACE_DLP && CAS == kEdge) {
-        float hh, hl;
-        dd_height(ah[2], al[2], bh[0], bl[0], B.nh, B.nl, hh, hl);
-        h2 = hh + hl;
+    if (KIND == BEM_LAPLACE_DLP && CAS != kIdentical) {
+        double d1 = 0.0, d2 = 0.0;
+        if (lane == 0) {
+            const double *ga = m.geom + (int64_t)a * kGeomStride;
+            const double *gb = m.geom + (int64_t)b * kGeomStride;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double b0 = __ldg(gb + 3 * pb[0] + c), n = __ldg(gb + 9 + c);
+                d1 = fma(__ldg(ga + 3 * pa[1] + c) - b0, n, d1);
+                d2 = fma(__ldg(ga + 3 * pa[2] + c) - b0, n, d2);
+            }
+        }
+        d1 = __shfl_sync(0xffffffffu, d1, 0);
+        d2 = __shfl_sync(0xffffffffu, d2, 0);
+        if (CAS == kEdge) {
+            h2 = (float)d2;
+        } else {
+            const double d21 = d2 - d1;
+            H.h0 = 0.0f;
+            H.h0l = 0.0f;
+            H.h10 = (float)d1;
+            H.h10l = (float)(d1 - (double)H.h10);
+            H.h21 = (float)d21;
+            H.h21l = (float)(d21 - (double)H.h21);
+        }
     }
     constexpr int NACC = BASIS == BEM_P0 ? 1 : 9;
     float acc[NACC], cmp[NACC], acci[NACC], cmpi[NACC];

@@ -134,6 +134,7 @@ class BatchItem:
     operators: list
     near: BlockSet
     far: BlockSet
+    partition: object = None         # structure.BlockPartition of the H2 blocks
 
 
 @dataclass
@@ -183,9 +184,10 @@ def config4(count: int = 48, lo: float = 500.0, hi: float = 30000.0, leaf_size: 
             (nu_, nv_), _ = _nearest(t, cands)
             mesh = meshes.torus(nu_, nv_)
         mesh = meshes.jitter(mesh, 0.05, seed(4, k))
-        _, near, far = h2_blocks(mesh, "p0", leaf_size, eta, rank, seed(4, 100 + k))
+        part, near, far = h2_blocks(mesh, "p0", leaf_size, eta, rank, seed(4, 100 + k))
         items.append(BatchItem(mesh, [Operator("laplace_dlp"),
-                                      Operator("helmholtz_slp", float(kappas[k]))], near, far))
+                                      Operator("helmholtz_slp", float(kappas[k]))], near, far,
+                               part))
     return BatchWorkload(f"C4 {count} meshes (spheres/cubes/tori) laplace_dlp+helmholtz_slp p0 h2",
                          "p0", Quad(3, "duffy", 5, 5, 5), items,
                          meta={"triangles": int(sum(it.mesh.nt for it in items))})
