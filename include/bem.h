@@ -84,10 +84,10 @@ typedef struct {
  *                 and float edge vectors, double-layer numerators from
  *                 double-float plane heights, Kahan-compensated sums).
  *   order_mode:   BEM_ORDER_FIXED (the orders above) or BEM_ORDER_LEARNED: for
- *                 bem_near_field on piecewise-constant meshes, every disjoint
- *                 pair gets the rule class the context's order model
- *                 (bem_set_order_model) predicts; touching pairs keep the
- *                 fixed singular orders above.  Such a call reads one value
+ *                 bem_near_field and bem_coupling_blocks on piecewise-constant
+ *                 meshes, every disjoint pair gets the rule class the context's
+ *                 order model (bem_set_order_model) predicts; touching pairs
+ *                 keep the fixed singular orders above.  Such a call reads one value
  *                 back from the device to size its scratch (it synchronises). */
 typedef struct {
     int32_t q_regular;

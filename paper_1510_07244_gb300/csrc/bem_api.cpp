@@ -295,8 +295,9 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
         if (J.quad.order_mode == BEM_ORDER_LEARNED) {
             if (m->v.basis != BEM_P0)
                 return fail(ctx, BEM_ERR_UNSUPPORTED, "learned orders need the piecewise-constant basis");
-            if (!allow_touching || lower_only)
-                return fail(ctx, BEM_ERR_UNSUPPORTED, "learned orders are available for bem_near_field");
+            if (lower_only)
+                return fail(ctx, BEM_ERR_UNSUPPORTED,
+                            "learned orders are available for bem_near_field and bem_coupling_blocks");
             ProfScope ps(ctx, "learned_p0");
             rc = run_learned_p0(ctx, m->v, L, ctx->tile_prefix, J.quad.precision);
             if (rc) return rc;

@@ -367,8 +367,7 @@ __device__ __forceinline__ void regular_p0_f32_helm(const TriF &A, const TriF &B
         yz[j] = fmaf(a, B.e1[2], b * B.e2[2]);
     }
     float sr = 0.0f, si = 0.0f, cr = 0.0f, ci = 0.0f;
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
+    auto outer = [&](int i) {
         const float a = R.sf[i] - 0.666666687f, b = R.tf[i] - 0.333333343f;
         const float xx = fmaf(a, A.e1[0], b * A.e2[0]);
         const float xy = fmaf(a, A.e1[1], b * A.e2[1]);
@@ -389,6 +388,14 @@ __device__ __forceinline__ void regular_p0_f32_helm(const TriF &A, const TriF &B
         t = si + y;
         ci = (t - si) - y;
         si = t;
+    };
+    // larger rules keep the outer loop rolled (code size)
+    if (NP > 9) {
+#pragma unroll 1
+        for (int i = 0; i < NP; ++i) outer(i);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) outer(i);
     }
     const float sc = A.sg * B.sg * (float)kInv4Pi;
     out_re = sr * sc;
@@ -413,8 +420,7 @@ __device__ __forceinline__ float regular_p0_f32(const TriF &A, const TriF &B, co
         H = make_height(A.vh[0], A.vl[0], A.vh[1], A.vl[1], A.vh[2], A.vl[2], B.vh[0], B.vl[0],
                         B.nh, B.nl);
     float sum = 0.0f, comp = 0.0f;
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
+    auto outer = [&](int i) {
         const float xx = fmaf(R.sf[i], A.e1[0], fmaf(R.tf[i], A.e2[0], d0[0]));
         const float xy = fmaf(R.sf[i], A.e1[1], fmaf(R.tf[i], A.e2[1], d0[1]));
         const float xz = fmaf(R.sf[i], A.e1[2], fmaf(R.tf[i], A.e2[2], d0[2]));
@@ -428,6 +434,14 @@ __device__ __forceinline__ float regular_p0_f32(const TriF &A, const TriF &B, co
         const float t = sum + y;
         comp = (t - sum) - y;
         sum = t;
+    };
+    // larger rules keep the outer loop rolled (code size)
+    if (NP > 9) {
+#pragma unroll 1
+        for (int i = 0; i < NP; ++i) outer(i);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) outer(i);
     }
     return sum * (A.sg * B.sg * (float)kInv4Pi);
 }

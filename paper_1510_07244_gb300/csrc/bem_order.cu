@@ -30,69 +30,76 @@ namespace bem {
 // distance / D), cos(angle between normals), log2(area ratio), height of the
 // test centroid above the trial plane / centroid distance, kernel id / 2,
 // kappa D, log2(aspect ratio); D = the larger triangle diameter.  Normalised
-// by the model's mean and standard deviation.
+// by the model's mean and standard deviation.  Float arithmetic (a feature
+// only has to place the pair among the classes).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void pair_features(const MeshView &m, int a, int b, int kind,
                                               double kappa, const float *mean, const float *inv_std,
                                               float *f)
 {
-    const double *ga = m.geom + (int64_t)a * kGeomStride;
-    const double *gb = m.geom + (int64_t)b * kGeomStride;
-    double va[3][3], vb[3][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            va[k][c] = __ldg(ga + 3 * k + c);
-            vb[k][c] = __ldg(gb + 3 * k + c);
-        }
-    double ca[3], cb[3], da = 0.0, db = 0.0, dmin = 1e300;
+    // float arithmetic on the double-float records: vertex offsets from each
+    // triangle's vertex 0, and the offset between the two vertices 0 formed from
+    // the hi + lo pairs, so every difference keeps float precision
+    TriF A, B;
+    load_trif(m.geomf, a, A);
+    load_trif(m.geomf, b, B);
+    float oa[3][3], ob[3][3], d0[3], na[3], nb[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        ca[c] = (va[0][c] + va[1][c] + va[2][c]) / 3.0;
-        cb[c] = (vb[0][c] + vb[1][c] + vb[2][c]) / 3.0;
+        oa[0][c] = 0.0f;
+        oa[1][c] = A.e1[c];
+        oa[2][c] = A.e1[c] + A.e2[c];
+        ob[0][c] = 0.0f;
+        ob[1][c] = B.e1[c];
+        ob[2][c] = B.e1[c] + B.e2[c];
+        d0[c] = dd_diff(A.vh[0][c], A.vl[0][c], B.vh[0][c], B.vl[0][c]);
+        na[c] = A.nh[c] + A.nl[c];
+        nb[c] = B.nh[c] + B.nl[c];
     }
+    float da2 = 0.0f, db2 = 0.0f, dmin2 = 3.0e38f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const int j = (i + 1) % 3;
-        double ea = 0.0, eb = 0.0;
+        float ea = 0.0f, eb = 0.0f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            ea += (va[i][c] - va[j][c]) * (va[i][c] - va[j][c]);
-            eb += (vb[i][c] - vb[j][c]) * (vb[i][c] - vb[j][c]);
+            ea = fmaf(oa[i][c] - oa[j][c], oa[i][c] - oa[j][c], ea);
+            eb = fmaf(ob[i][c] - ob[j][c], ob[i][c] - ob[j][c], eb);
         }
-        da = fmax(da, ea);
-        db = fmax(db, eb);
+        da2 = fmaxf(da2, ea);
+        db2 = fmaxf(db2, eb);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double dd = 0.0;
+            float dd = 0.0f;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dd += (va[i][c] - vb[k][c]) * (va[i][c] - vb[k][c]);
-            dmin = fmin(dmin, dd);
+            for (int c = 0; c < 3; ++c) {
+                const float x = d0[c] + oa[i][c] - ob[k][c];
+                dd = fmaf(x, x, dd);
+            }
+            dmin2 = fminf(dmin2, dd);
         }
     }
-    da = sqrt(da);
-    db = sqrt(db);
-    const double D = fmax(da, db);
-    double dc = 0.0, h = 0.0, cosang = 0.0;
+    const float D = sqrtf(fmaxf(da2, db2));
+    float dc2 = 0.0f, h = 0.0f, cosang = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        dc += (ca[c] - cb[c]) * (ca[c] - cb[c]);
-        h += (ca[c] - cb[c]) * __ldg(gb + 9 + c);
-        cosang += __ldg(ga + 9 + c) * __ldg(gb + 9 + c);
+        const float dcv = d0[c] + (oa[1][c] + oa[2][c] - ob[1][c] - ob[2][c]) * (1.0f / 3.0f);
+        dc2 = fmaf(dcv, dcv, dc2);
+        h = fmaf(dcv, nb[c], h);
+        cosang = fmaf(na[c], nb[c], cosang);
     }
-    dc = sqrt(dc);
-    const double area_a = 0.5 * __ldg(ga + 12), area_b = 0.5 * __ldg(gb + 12);
-    const double ar = fmax(da * da / (2.0 * area_a), db * db / (2.0 * area_b));
+    const float dc = sqrtf(dc2);
+    const float area_a = 0.5f * A.sg, area_b = 0.5f * B.sg;
+    const float ar = fmaxf(da2 / (2.0f * area_a), db2 / (2.0f * area_b));
     float raw[8];
-    raw[0] = (float)log2(fmax(dc / D, 1e-6));
-    raw[1] = (float)log2(fmax(sqrt(dmin) / D, 1e-6));
-    raw[2] = (float)cosang;
-    raw[3] = (float)log2(area_a / area_b);
-    raw[4] = (float)(h / fmax(dc, 1e-300));
+    raw[0] = __log2f(fmaxf(dc / D, 1e-6f));
+    raw[1] = __log2f(fmaxf(sqrtf(dmin2) / D, 1e-6f));
+    raw[2] = cosang;
+    raw[3] = __log2f(area_a / area_b);
+    raw[4] = h / fmaxf(dc, 1e-30f);
     raw[5] = 0.5f * (float)kind;
-    raw[6] = kind == BEM_HELMHOLTZ_SLP ? (float)(kappa * D) : 0.0f;
-    raw[7] = (float)log2(ar);
+    raw[6] = kind == BEM_HELMHOLTZ_SLP ? (float)kappa * D : 0.0f;
+    raw[7] = __log2f(ar);
 #pragma unroll
     for (int k = 0; k < 8; ++k) f[k] = (raw[k] - mean[k]) * inv_std[k];
 }
@@ -390,8 +397,11 @@ __device__ __forceinline__ void select_entry(const MeshView &m, const BlockLaunc
     pos = bi.off + (int64_t)r + (int64_t)c * bi.nr;
     const int4 va = __ldg(m.tvid + a), vb = __ldg(m.tvid + b);
     if (touching(va, vb)) {
-        const int k = find_touching(m, a, b);
-        const double2 v = m.table[k];
+        // near field: the touching table's value; a touching pair in a coupling
+        // block (no table) means the block was not admissible
+        const int k = L.allow_touching ? find_touching(m, a, b) : -1;
+        const double2 v = k >= 0 ? m.table[k] : make_double2(0.0, 0.0);
+        if (k < 0) set_status(status, BEM_ERR_INVALID_ARG);
         if (L.kind == BEM_HELMHOLTZ_SLP) reinterpret_cast<double2 *>(L.out)[pos] = v;
         else reinterpret_cast<double *>(L.out)[pos] = v.x;
         state = 1;
@@ -471,7 +481,12 @@ __global__ void __launch_bounds__(256) k_learned_select(MeshView m, BlockLaunch 
                     break;
                 }
             }
-            atomicAdd(&A.counts[cls], 1);
+        }
+        // class counts: one atomic per class and warp
+#pragma unroll
+        for (int cc = 0; cc < kClasses; ++cc) {
+            const unsigned mk = __ballot_sync(0xffffffffu, cls == cc);
+            if (mk && lane == 0) atomicAdd(&A.counts[cc], __popc(mk));
         }
         A.cls[tile * 256 + threadIdx.x] = (unsigned char)cls;
     }
@@ -495,19 +510,73 @@ __global__ void __launch_bounds__(256) k_learned_compact(MeshView m, BlockLaunch
                                                          LearnedArgs A)
 {
     const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
+    const int lane = threadIdx.x & 31;
     for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        // the loop is uniform across the CTA: every warp takes part in the ballots
         const int cls = A.cls[tile * 256 + threadIdx.x];
-        if (cls >= kClasses) continue;
+        const unsigned any = __ballot_sync(0xffffffffu, cls < kClasses);
+        if (!any) continue;
         const BlockInfo bi = block_info(L, prefix, tile, nullptr);
         const int lr = threadIdx.x & 31, lc = threadIdx.x >> 5;
         const int ntr = (bi.nr + kTile - 1) / kTile;
         const int r = (bi.tile_in_blk % ntr) * kTile + lr;
         const int c = (bi.tile_in_blk / ntr) * 8 + lc;
-        const int64_t pos = bi.off + (int64_t)r + (int64_t)c * bi.nr;
-        const int k = atomicAdd(&A.fill[cls], 1);
-        A.rec[A.offs[cls] + k] = make_int4((int)(pos & 0xffffffff), (int)(pos >> 32),
-                                           L.row_idx[bi.r_lo + r], L.col_idx[bi.c_lo + c]);
+        // slots within the class: one atomic per class and warp, lanes in order
+#pragma unroll
+        for (int cc = 0; cc < kClasses; ++cc) {
+            const unsigned mk = __ballot_sync(0xffffffffu, cls == cc);
+            if (!mk) continue;
+            const int leader = __ffs(mk) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&A.fill[cc], __popc(mk));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (cls == cc) {
+                const int64_t pos = bi.off + (int64_t)r + (int64_t)c * bi.nr;
+                const int k = base + __popc(mk & ((1u << lane) - 1u));
+                A.rec[A.offs[cc] + k] = make_int4((int)(pos & 0xffffffff), (int)(pos >> 32),
+                                                  L.row_idx[bi.r_lo + r], L.col_idx[bi.c_lo + c]);
+            }
+        }
     }
+}
+
+// Float form, classes whose rule is a product of a 2D rule with at most 25
+// points: one thread per pair with the block engine's pair integrals.
+template <int KIND, int NP>
+__global__ void __launch_bounds__(256) k_learned_eval_tp(MeshView m, const int4 *__restrict__ rec,
+                                                         const int64_t *__restrict__ offs, int cls,
+                                                         Rule2D R, double kappa, void *out)
+{
+    const int64_t lo = offs[cls], hi = offs[cls + 1];
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < hi; k += nt) {
+        const int4 Rk = rec[k];
+        const int64_t pos = (int64_t)(unsigned)Rk.x | ((int64_t)Rk.y << 32);
+        TriF A, B;
+        load_trif(m.geomf, Rk.z, A);
+        load_trif(m.geomf, Rk.w, B);
+        if (KIND == BEM_HELMHOLTZ_SLP) {
+            float fr, fi;
+            regular_p0_f32_helm<NP>(A, B, R, kappa, fr, fi);
+            reinterpret_cast<double2 *>(out)[pos] = make_double2((double)fr, (double)fi);
+        } else {
+            reinterpret_cast<double *>(out)[pos] = (double)regular_p0_f32<KIND, NP>(A, B, R);
+        }
+    }
+}
+
+template <int KIND>
+cudaError_t launch_learned_tp(const MeshView &m, const int4 *rec, const int64_t *offs, int cls,
+                              const Rule2D &R, double kappa, void *out, int grid, cudaStream_t st)
+{
+    switch (R.np) {
+    case 4: k_learned_eval_tp<KIND, 4><<<grid, 256, 0, st>>>(m, rec, offs, cls, R, kappa, out); break;
+    case 7: k_learned_eval_tp<KIND, 7><<<grid, 256, 0, st>>>(m, rec, offs, cls, R, kappa, out); break;
+    case 16: k_learned_eval_tp<KIND, 16><<<grid, 256, 0, st>>>(m, rec, offs, cls, R, kappa, out); break;
+    case 25: k_learned_eval_tp<KIND, 25><<<grid, 256, 0, st>>>(m, rec, offs, cls, R, kappa, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // One warp per record of one class: disjoint pair with the class's 4D rule.
@@ -935,11 +1004,30 @@ int run_learned_p0(bem_ctx *ctx, const MeshView &mv, const BlockLaunch &L, const
     A.rec = reinterpret_cast<int4 *>(ctx->learned_rec);
     cudaMemsetAsync(A.counts, 0, 16 * sizeof(int), ctx->stream);
     const int grid = ctx->num_sms * 8;
-    k_learned_select<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A, ctx->status);
-    k_learned_offsets<<<1, 32, 0, ctx->stream>>>(A);
-    k_learned_compact<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A);
+    {
+        ProfScope ps(ctx, "learned_select");
+        k_learned_select<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A, ctx->status);
+        k_learned_offsets<<<1, 32, 0, ctx->stream>>>(A);
+        k_learned_compact<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A);
+    }
+    static const char *kEvalName[kClasses] = {"learned_eval_duffy2", "learned_eval_tri7",
+                                              "learned_eval_duffy4", "learned_eval_duffy5",
+                                              "learned_eval_duffy6", "learned_eval_duffy8"};
     const bool mixed = is_mixed(precision);
     for (int c = 0; c < kClasses; ++c) {
+        ProfScope ps(ctx, kEvalName[c]);
+        Rule2D r2;
+        if (mixed && make_rule2d(kClassRule[c][0], kClassRule[c][1], r2) &&
+            (r2.np == 4 || r2.np == 7 || r2.np == 16 || r2.np == 25)) {
+            // thread per pair on the 2D product rule
+            e = L.kind == BEM_LAPLACE_SLP
+                    ? launch_learned_tp<BEM_LAPLACE_SLP>(mv, A.rec, A.offs, c, r2, L.kappa, L.out, grid, ctx->stream)
+                    : L.kind == BEM_LAPLACE_DLP
+                          ? launch_learned_tp<BEM_LAPLACE_DLP>(mv, A.rec, A.offs, c, r2, L.kappa, L.out, grid, ctx->stream)
+                          : launch_learned_tp<BEM_HELMHOLTZ_SLP>(mv, A.rec, A.offs, c, r2, L.kappa, L.out, grid, ctx->stream);
+            if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned evaluation");
+            continue;
+        }
         Rule4D r;
         int rc = api_get_rule4(ctx, kRegular, kClassRule[c][0], kClassRule[c][1], r);
         if (rc) return rc;

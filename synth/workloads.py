@@ -127,6 +127,26 @@ def config3(n: int = 64) -> Workload:
                     meta={"leaf_size": 32, "eta": 2.0, "rank": 16, "precision": "mixed"})
 
 
+def config5(n: int = 128) -> Workload:
+    """Learned quadrature orders: the paper's octahedral sphere with 8 n^2 triangles
+    (n = 128: 131072), vertices jittered by 5% of the mean edge length (seeded);
+    Laplace double layer and Helmholtz single layer with kappa = 16, P0, H2 blocks
+    (leaf 32, eta 2, <= 16 pivots); SS q=5, Duffy q=3 as the fixed orders."""
+    mesh = meshes.jitter(meshes.octasphere(n), 0.05, seed(5))
+    part, near, far = h2_blocks(mesh, "p0", 32, 2.0, 16, seed(5, 1))
+    return Workload(f"C5 octasphere{mesh.nt} laplace_dlp+helmholtz_slp k16 p0 h2 learned", mesh,
+                    "p0", [Operator("laplace_dlp"), Operator("helmholtz_slp", 16.0)],
+                    Quad(3, "duffy", 5, 5, 5), near=near, far=far, partition=part,
+                    meta={"leaf_size": 32, "eta": 2.0, "rank": 16, "order_mode": "learned"})
+
+
+def order_training_meshes():
+    """Smaller meshes of the same family on which the order model's labels are
+    generated: jittered octahedral spheres with 2048, 4608 and 8192 triangles."""
+    return [meshes.jitter(meshes.octasphere(n), 0.05, seed(5, 10 + k))
+            for k, n in enumerate((16, 24, 32))]
+
+
 @dataclass
 class BatchItem:
     """One mesh of a batched workload with its operators and block sets."""

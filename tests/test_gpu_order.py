@@ -121,10 +121,13 @@ def trained(env):
     ctx.bem_mlp_destroy(mlp)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed_full"])
 @pytest.mark.parametrize("kernel,kappa", KERNELS)
-def test_learned_near_field_meets_target_with_gain(env, trained, kernel, kappa):
+def test_learned_near_field_meets_target_with_gain(env, trained, kernel, kappa, precision):
     """Held-out 8192-triangle jittered sphere: learned orders vs the oracle at
-    Duffy order 10 (same singular rules) on whole sampled blocks."""
+    Duffy order 10 (same singular rules) on whole sampled blocks, in the FP64
+    form (one warp per pair) and the float form (one thread per pair for the
+    classes whose rule is a product of a 2D rule)."""
     import torch
     pkg, ctx, om = env
     mlp, losses = trained
@@ -135,7 +138,7 @@ def test_learned_near_field_meets_target_with_gain(env, trained, kernel, kappa):
     mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p0")
     from parity_util import block_job
     q = dict(q_regular=3, regular_rule="duffy", q_identical=5, q_edge=5, q_vertex=5,
-             order_mode="learned")
+             order_mode="learned", precision=precision)
     dt = torch.complex128 if kernel == "helmholtz_slp" else torch.float64
     out = torch.full((near.n_entries,), float("nan"), dtype=dt, device="cuda")
     ctx.bem_near_field([block_job(pkg, mid, near, kernel, kappa, q, out)])
@@ -150,6 +153,17 @@ def test_learned_near_field_meets_target_with_gain(env, trained, kernel, kappa):
     A = oracle_absolute(mesh, "p0", r[pos], c[pos], kernel, kappa, qref)
     err = rel_err_abs(got_all[pos], ref, A, r[pos]).max()
     assert err <= 1e-6, err
+    # coupling blocks take learned orders too (no touching pairs there)
+    _, _, far = synth.workloads.h2_blocks(mesh, "p0", 32, 2.0, 16, 9)
+    outf = torch.full((far.n_entries,), float("nan"), dtype=dt, device="cuda")
+    ctx.bem_coupling_blocks([block_job(pkg, mid, far, kernel, kappa, q, outf)])
+    ctx.bem_sync()
+    posf = sample_block_entries(far, 10, synth.SplitMix64(4))
+    rf, cf = far.entry_indices()
+    reff = oracle_entries(mesh, "p0", rf[posf], cf[posf], kernel, kappa, qref)
+    Af = oracle_absolute(mesh, "p0", rf[posf], cf[posf], kernel, kappa, qref)
+    errf = rel_err_abs(outf.cpu().numpy()[posf], reff, Af, rf[posf]).max()
+    assert errf <= 1e-6, errf
     # gain: points per disjoint pair against the cheapest fixed rule meeting the
     # target on every pair of the training data (Duffy q=6: 1296 points)
     pts = np.dot(counts, pkg.ORDER_CLASS_POINTS) / max(1, sum(counts))
