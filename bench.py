@@ -35,6 +35,22 @@ UNIT = "entries/s"
 # kappa r 1, sincos 2, two products and a second accumulation 5; piecewise
 # linear + three basis-weighted accumulations 6 and the x-side 3x3 update
 # 18 / (points per axis pair).
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` on the default workload, from the ncu
+    summary committed under profiles/ (None if there is none)."""
+    import glob
+    import re
+    key = f"traffic_bytes_per_launch[{kernel}]:"
+    for path in sorted(glob.glob(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                              "profiles", "*.md"))):
+        for line in open(path):
+            if line.startswith(key):
+                m = re.search(r"(\d+)", line[len(key):])
+                if m:
+                    return int(m.group(1))
+    return None
+
+
 def flops_per_point(kernel: str, basis: str, np_axis: int) -> float:
     f = 11.0
     if kernel == "laplace_dlp":
@@ -406,7 +422,10 @@ def run_ours(args):
                              "launches": launches, "avg_launch_ms": round(ms / launches, 4)}
         dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
         r = dict(per.get(dom, {}))
-        r.update({"bound": "alu", "kernel": dom, "traffic": None,
+        # DRAM bytes per launch from the committed ncu capture of the full-size
+        # default workload (null for other sizes)
+        traffic = profiled_traffic(dom) if args.levels == 5 and not args.split else None
+        r.update({"bound": "alu", "kernel": dom, "traffic": traffic,
                   "peak_source": "derived: 152 SM x (2 FP64 | 128 FP32) FMA/clk x 2.07 GHz"})
         return r, per
 
