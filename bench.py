@@ -834,7 +834,7 @@ def run_c5(args):
 
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
-    w = synth.workloads.config5()
+    w = synth.workloads.config5(args.c5_n)
     stream = torch.cuda.current_stream(dev)
     ctx = pkg.Context(0, stream)
 
@@ -1061,6 +1061,9 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2 (default): the 20480-triangle P1 benchmark line; c3 / c4: the "
                          "49152-triangle Helmholtz cube / the 48-mesh batch, measured the same way")
+    ap.add_argument("--c5-n", type=int, default=128,
+                    help="C5 sphere subdivision (8 n^2 triangles; 128 = the 131072-triangle "
+                         "workload, smaller values only for profiling captures)")
     ap.add_argument("--levels", type=int, default=5,
                     help="icosphere refinement levels (5 = the 20480-triangle workload; "
                          "smaller values only for profiling captures)")

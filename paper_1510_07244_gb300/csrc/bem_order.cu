@@ -261,9 +261,45 @@ struct MlpDev {
     const float *b1, *b2, *b3;
 };
 
+// The B operands of all three layers in mma fragment order, staged once per CTA
+// in shared memory: each lane loads its fragment with one 8-byte read.
+struct MlpFrag {
+    uint2 w1[8][32];       // [n tile][lane]        (K = 8, padded to one 16-wide k tile)
+    uint2 w2[8][4][32];    // [n tile][k tile][lane]
+    uint2 w3[4][32];       // [k tile][lane]         (N = 6, padded to one 8-wide n tile)
+    float b1[kHid], b2[kHid], b3[8];
+};
+
+// Called by every thread of the CTA (contains a barrier).
+__device__ __forceinline__ void mlp_stage(const MlpDev &P, MlpFrag &F)
+{
+    for (int i = threadIdx.x; i < 8 * 32; i += blockDim.x) {
+        unsigned b[2];
+        load_b(P.W1, kHid, kIn, (i / 32) * 8, 0, i % 32, b);
+        F.w1[i / 32][i % 32] = make_uint2(b[0], b[1]);
+    }
+    for (int i = threadIdx.x; i < 8 * 4 * 32; i += blockDim.x) {
+        const int nt = i / 128, kt = (i / 32) % 4, ln = i % 32;
+        unsigned b[2];
+        load_b(P.W2, kHid, kHid, nt * 8, kt * 16, ln, b);
+        F.w2[nt][kt][ln] = make_uint2(b[0], b[1]);
+    }
+    for (int i = threadIdx.x; i < 4 * 32; i += blockDim.x) {
+        unsigned b[2];
+        load_b(P.W3, kOut, kHid, 0, (i / 32) * 16, i % 32, b);
+        F.w3[i / 32][i % 32] = make_uint2(b[0], b[1]);
+    }
+    for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+        F.b1[i] = P.b1[i];
+        F.b2[i] = P.b2[i];
+    }
+    if (threadIdx.x < 8) F.b3[threadIdx.x] = threadIdx.x < kOut ? P.b3[threadIdx.x] : 0.0f;
+    __syncthreads();
+}
+
 // 16 rows (features in X16, row-major 16 x 8 float) -> logits of rows t/4 and
 // t/4 + 8 for this lane's two classes 2(t%4), 2(t%4)+1 (classes < 8).
-__device__ __forceinline__ void mlp_tile(const MlpDev &P, const float (*X16)[8], int lane,
+__device__ __forceinline__ void mlp_tile(const MlpFrag &F, const float (*X16)[8], int lane,
                                          float *out_lo, float *out_hi)
 {
     const int r = lane / 4, cq = 2 * (lane % 4);
@@ -276,13 +312,13 @@ __device__ __forceinline__ void mlp_tile(const MlpDev &P, const float (*X16)[8],
     float h1[8][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-        unsigned b[2];
-        load_b(P.W1, kHid, kIn, nt * 8, 0, lane, b);
+        const uint2 bw = F.w1[nt][lane];
+        const unsigned b[2] = {bw.x, bw.y};
         const int col = nt * 8 + cq;
-        h1[nt][0] = P.b1[col];
-        h1[nt][1] = P.b1[col + 1];
-        h1[nt][2] = P.b1[col];
-        h1[nt][3] = P.b1[col + 1];
+        h1[nt][0] = F.b1[col];
+        h1[nt][1] = F.b1[col + 1];
+        h1[nt][2] = F.b1[col];
+        h1[nt][3] = F.b1[col + 1];
         mma_bf16(h1[nt], a, b);
 #pragma unroll
         for (int q = 0; q < 4; ++q) h1[nt][q] = fmaxf(h1[nt][q], 0.0f);
@@ -292,10 +328,10 @@ __device__ __forceinline__ void mlp_tile(const MlpDev &P, const float (*X16)[8],
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const int col = nt * 8 + cq;
-        h2[nt][0] = P.b2[col];
-        h2[nt][1] = P.b2[col + 1];
-        h2[nt][2] = P.b2[col];
-        h2[nt][3] = P.b2[col + 1];
+        h2[nt][0] = F.b2[col];
+        h2[nt][1] = F.b2[col + 1];
+        h2[nt][2] = F.b2[col];
+        h2[nt][3] = F.b2[col + 1];
     }
 #pragma unroll
     for (int kt = 0; kt < 4; ++kt) {
@@ -306,21 +342,13 @@ __device__ __forceinline__ void mlp_tile(const MlpDev &P, const float (*X16)[8],
         ak[3] = pack_bf16(h1[2 * kt + 1][2], h1[2 * kt + 1][3]);
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
-            unsigned b[2];
-            load_b(P.W2, kHid, kHid, nt * 8, kt * 16, lane, b);
+            const uint2 bw = F.w2[nt][kt][lane];
+            const unsigned b[2] = {bw.x, bw.y};
             mma_bf16(h2[nt], ak, b);
         }
     }
     // layer 3: K = 64, N = 6 (one 8-column tile)
-    float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (cq < kOut) {
-        o[0] = P.b3[cq];
-        o[2] = P.b3[cq];
-    }
-    if (cq + 1 < kOut) {
-        o[1] = P.b3[cq + 1];
-        o[3] = P.b3[cq + 1];
-    }
+    float o[4] = {F.b3[cq], F.b3[cq + 1], F.b3[cq], F.b3[cq + 1]};   // zero beyond kOut
 #pragma unroll
     for (int kt = 0; kt < 4; ++kt) {
         unsigned ak[4];
@@ -328,8 +356,8 @@ __device__ __forceinline__ void mlp_tile(const MlpDev &P, const float (*X16)[8],
         ak[1] = pack_bf16(fmaxf(h2[2 * kt][2], 0.0f), fmaxf(h2[2 * kt][3], 0.0f));
         ak[2] = pack_bf16(fmaxf(h2[2 * kt + 1][0], 0.0f), fmaxf(h2[2 * kt + 1][1], 0.0f));
         ak[3] = pack_bf16(fmaxf(h2[2 * kt + 1][2], 0.0f), fmaxf(h2[2 * kt + 1][3], 0.0f));
-        unsigned b[2];
-        load_b(P.W3, kOut, kHid, 0, kt * 16, lane, b);
+        const uint2 bw = F.w3[kt][lane];
+        const unsigned b[2] = {bw.x, bw.y};
         mma_bf16(o, ak, b);
     }
     out_lo[0] = o[0];
@@ -342,6 +370,8 @@ __device__ __forceinline__ void mlp_tile(const MlpDev &P, const float (*X16)[8],
 __global__ void k_mlp_infer(MlpDev P, const float *__restrict__ X, int64_t n, float *logits)
 {
     __shared__ float xs[8][16][8];
+    __shared__ MlpFrag F;
+    mlp_stage(P, F);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + w) * 16;
     if (row0 >= n) return;
@@ -351,7 +381,7 @@ __global__ void k_mlp_infer(MlpDev P, const float *__restrict__ X, int64_t n, fl
     }
     __syncwarp();
     float lo[2], hi[2];
-    mlp_tile(P, xs[w], lane, lo, hi);
+    mlp_tile(F, xs[w], lane, lo, hi);
     const int r = lane / 4, cq = 2 * (lane % 4);
     for (int q = 0; q < 2; ++q) {
         const int c = cq + q;
@@ -421,11 +451,13 @@ struct LearnedArgs {
     int4 *rec;                   // records: (pos lo, pos hi, a, b)
 };
 
-__global__ void __launch_bounds__(256) k_learned_select(MeshView m, BlockLaunch L,
-                                                        const int64_t *__restrict__ prefix,
-                                                        LearnedArgs A, int *status)
+__global__ void __launch_bounds__(256, 2) k_learned_select(MeshView m, BlockLaunch L,
+                                                           const int64_t *__restrict__ prefix,
+                                                           LearnedArgs A, int *status)
 {
     __shared__ float xs[8][2][16][8];
+    __shared__ MlpFrag F;
+    mlp_stage(A.P, F);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
     for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
@@ -439,8 +471,8 @@ __global__ void __launch_bounds__(256) k_learned_select(MeshView m, BlockLaunch 
         __syncwarp();
         // logits of the warp's 32 rows: two 16-row tiles
         float lo[2][2], hi[2][2];
-        mlp_tile(A.P, xs[w][0], lane, lo[0], hi[0]);
-        mlp_tile(A.P, xs[w][1], lane, lo[1], hi[1]);
+        mlp_tile(F, xs[w][0], lane, lo[0], hi[0]);
+        mlp_tile(F, xs[w][1], lane, lo[1], hi[1]);
         __syncwarp();
         // gather this lane's row logits: row = lane; tile = lane / 16, r = lane % 16
         float logit[kClasses];
