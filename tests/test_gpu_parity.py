@@ -428,10 +428,11 @@ def test_mixed_helmholtz_far_phase(ctx, pkg):
     assert rel_err_abs(got[rows, cols], ref, absint, rows).max() <= MIXED_TOL
 
 
-def test_c3_full_size_sampled(ctx, pkg):
-    """The 49152-triangle jittered cube, Helmholtz kappa = 8, mixed form: all
-    near-field and coupling blocks on the GPU, whole sampled blocks checked
-    against the FP64 oracle (the error of the mixed form on this workload)."""
+@pytest.mark.parametrize("form", MIXED_FORMS)
+def test_c3_full_size_sampled(ctx, pkg, form):
+    """The 49152-triangle jittered cube, Helmholtz kappa = 8, both float forms:
+    all near-field and coupling blocks on the GPU, whole sampled blocks checked
+    against the FP64 oracle (the error of the float forms on this workload)."""
     from parity_util import sample_block_entries
     w = synth.workloads.config3()
     op = w.operators[0]
@@ -440,7 +441,7 @@ def test_c3_full_size_sampled(ctx, pkg):
     rng = synth.SplitMix64(31)
     for bs, call in ((w.near, ctx.bem_near_field), (w.far, ctx.bem_coupling_blocks)):
         out = _out(bs.n_entries, op.kernel)
-        call([block_job(pkg, mid, bs, op.kernel, op.kappa, dict(q, precision="mixed"), out)])
+        call([block_job(pkg, mid, bs, op.kernel, op.kappa, dict(q, precision=form), out)])
         ctx.bem_sync()
         got_all = out.cpu().numpy()
         assert np.isfinite(got_all).all()
