@@ -597,6 +597,127 @@ __global__ void __launch_bounds__(256) k_learned_eval_tp(MeshView m, const int4 
     }
 }
 
+// Float form, the larger product rules (Duffy q = 6, 8: 36, 64 points per
+// triangle): one thread per pair, trial points taken CH at a time so that their
+// coordinates fit in registers; the test-point loop stays rolled.
+template <int NP>
+struct RuleF {
+    float s[NP], t[NP], w[NP];
+};
+
+template <int KIND, int NP, int CH>
+__global__ void __launch_bounds__(256) k_learned_eval_big(MeshView m, const int4 *__restrict__ rec,
+                                                          const int64_t *__restrict__ offs, int cls,
+                                                          RuleF<NP> R, double kappa, void *out)
+{
+    static_assert(NP % CH == 0, "chunks must tile the rule");
+    constexpr bool CPLX = KIND == BEM_HELMHOLTZ_SLP;
+    const int64_t lo = offs[cls], hi = offs[cls + 1];
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < hi; k += nt) {
+        const int4 Rk = rec[k];
+        const int64_t pos = (int64_t)(unsigned)Rk.x | ((int64_t)Rk.y << 32);
+        TriF A, B;
+        load_trif(m.geomf, Rk.z, A);
+        load_trif(m.geomf, Rk.w, B);
+        // Laplace: positions relative to B's vertex 0; Helmholtz: to the centroids
+        float d0[3] = {0.0f, 0.0f, 0.0f};
+        Height H = {};
+        HelmPhase P;
+        if (CPLX) {
+            P = helm_phase(A, B, kappa);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                d0[c] = dd_diff(A.vh[0][c], A.vl[0][c], B.vh[0][c], B.vl[0][c]);
+            if (KIND == BEM_LAPLACE_DLP)
+                H = make_height(A.vh[0], A.vl[0], A.vh[1], A.vl[1], A.vh[2], A.vl[2], B.vh[0],
+                                B.vl[0], B.nh, B.nl);
+        }
+        const float sh = CPLX ? 0.666666687f : 0.0f, th = CPLX ? 0.333333343f : 0.0f;
+        float sr = 0.0f, cr = 0.0f, si = 0.0f, ci = 0.0f;
+#pragma unroll 1
+        for (int jc = 0; jc < NP; jc += CH) {
+            float yx[CH], yy[CH], yz[CH];
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+                const float a = R.s[jc + j] - sh, b = R.t[jc + j] - th;
+                yx[j] = fmaf(a, B.e1[0], b * B.e2[0]);
+                yy[j] = fmaf(a, B.e1[1], b * B.e2[1]);
+                yz[j] = fmaf(a, B.e1[2], b * B.e2[2]);
+            }
+#pragma unroll 1
+            for (int i = 0; i < NP; ++i) {
+                const float a = R.s[i] - sh, b = R.t[i] - th;
+                const float xx = fmaf(a, A.e1[0], fmaf(b, A.e2[0], d0[0]));
+                const float xy = fmaf(a, A.e1[1], fmaf(b, A.e2[1], d0[1]));
+                const float xz = fmaf(a, A.e1[2], fmaf(b, A.e2[2], d0[2]));
+                const float dn = KIND == BEM_LAPLACE_DLP ? height_at(H, R.s[i], R.t[i]) : 0.0f;
+                float ir = 0.0f, ii = 0.0f;
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    if (CPLX) {
+                        float kr, ki;
+                        helm_value(P, xx - yx[j], xy - yy[j], xz - yz[j], kr, ki);
+                        ir = fmaf(R.w[jc + j], kr, ir);
+                        ii = fmaf(R.w[jc + j], ki, ii);
+                    } else {
+                        ir = fmaf(R.w[jc + j], kvalf<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], dn), ir);
+                    }
+                }
+                // Kahan sums over the (test point, chunk) partial sums
+                float y = fmaf(R.w[i], ir, -cr), t = sr + y;
+                cr = (t - sr) - y;
+                sr = t;
+                if (CPLX) {
+                    y = fmaf(R.w[i], ii, -ci);
+                    t = si + y;
+                    ci = (t - si) - y;
+                    si = t;
+                }
+            }
+        }
+        const float sc = A.sg * B.sg * (float)kInv4Pi;
+        if (CPLX)
+            reinterpret_cast<double2 *>(out)[pos] = make_double2((double)(sr * sc), (double)(si * sc));
+        else
+            reinterpret_cast<double *>(out)[pos] = (double)(sr * sc);
+    }
+}
+
+// Duffy product rule with q points per axis (q^2 points): s = x, t = x y, w = wx wy x
+template <int NP>
+bool duffy_rule_f(int q, RuleF<NP> &R)
+{
+    std::vector<double> g, gw;
+    if (q * q != NP || !gauss_legendre_unit(q, g, gw)) return false;
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) {
+            R.s[i * q + j] = (float)g[i];
+            R.t[i * q + j] = (float)(g[i] * g[j]);
+            R.w[i * q + j] = (float)(gw[i] * gw[j] * g[i]);
+        }
+    return true;
+}
+
+template <int KIND>
+cudaError_t launch_learned_big(const MeshView &m, const int4 *rec, const int64_t *offs, int cls,
+                               int q, double kappa, void *out, int grid, cudaStream_t st)
+{
+    if (q == 6) {
+        RuleF<36> R;
+        if (!duffy_rule_f(6, R)) return cudaErrorInvalidValue;
+        k_learned_eval_big<KIND, 36, 12><<<grid, 256, 0, st>>>(m, rec, offs, cls, R, kappa, out);
+    } else if (q == 8) {
+        RuleF<64> R;
+        if (!duffy_rule_f(8, R)) return cudaErrorInvalidValue;
+        k_learned_eval_big<KIND, 64, 16><<<grid, 256, 0, st>>>(m, rec, offs, cls, R, kappa, out);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <int KIND>
 cudaError_t launch_learned_tp(const MeshView &m, const int4 *rec, const int64_t *offs, int cls,
                               const Rule2D &R, double kappa, void *out, int grid, cudaStream_t st)
@@ -1057,6 +1178,18 @@ int run_learned_p0(bem_ctx *ctx, const MeshView &mv, const BlockLaunch &L, const
                     : L.kind == BEM_LAPLACE_DLP
                           ? launch_learned_tp<BEM_LAPLACE_DLP>(mv, A.rec, A.offs, c, r2, L.kappa, L.out, grid, ctx->stream)
                           : launch_learned_tp<BEM_HELMHOLTZ_SLP>(mv, A.rec, A.offs, c, r2, L.kappa, L.out, grid, ctx->stream);
+            if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned evaluation");
+            continue;
+        }
+        if (mixed && kClassRule[c][0] == BEM_RULE_DUFFY &&
+            (kClassRule[c][1] == 6 || kClassRule[c][1] == 8)) {
+            // thread per pair, trial points in chunks
+            const int q = kClassRule[c][1];
+            e = L.kind == BEM_LAPLACE_SLP
+                    ? launch_learned_big<BEM_LAPLACE_SLP>(mv, A.rec, A.offs, c, q, L.kappa, L.out, grid, ctx->stream)
+                    : L.kind == BEM_LAPLACE_DLP
+                          ? launch_learned_big<BEM_LAPLACE_DLP>(mv, A.rec, A.offs, c, q, L.kappa, L.out, grid, ctx->stream)
+                          : launch_learned_big<BEM_HELMHOLTZ_SLP>(mv, A.rec, A.offs, c, q, L.kappa, L.out, grid, ctx->stream);
             if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned evaluation");
             continue;
         }
