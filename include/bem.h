@@ -280,6 +280,8 @@ int bem_learned_counts(bem_ctx *ctx, int64_t *counts /* [6] */);
  * distinct cluster list; their storage is sized from the lists' total length
  * at creation (one device read), and a later run whose lists need more
  * records reports BEM_ERR_INVALID_ARG through the status word.
+ * Plans run the fixed orders of each job's bem_quad_desc: a job with
+ * order_mode BEM_ORDER_LEARNED is rejected with BEM_ERR_UNSUPPORTED.
  * Errors as bem_near_field; BEM_ERR_CUDA if graph capture fails. */
 typedef struct bem_plan bem_plan;
 #define BEM_PLAN_GRAPH    1

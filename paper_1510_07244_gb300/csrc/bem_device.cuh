@@ -672,9 +672,9 @@ __device__ __forceinline__ void touch_pair(const MeshView &m, int idx, const dou
 //   identical:     x - y = (x1 - y1) e1 + (x2 - y2) e2
 // The double-layer numerator (x - y) . n_y is the height of x above the trial
 // plane, an affine function on the test triangle whose vertex heights come
-// from the double-float vertex records: h(x) for a common vertex, x2 h(a2) for
-// a common edge (the shared vertices lie in the plane), 0 for identical
-// pairs.  Every lane sums its points with Kahan compensation.
+// from the FP64 records (neighbours can be nearly coplanar): h(x) for a common
+// vertex, x2 h(a2) for a common edge (the shared vertices lie in the plane), 0
+// for identical pairs.  Every lane sums its points with Kahan compensation.
 template <int CAS, int KIND, int BASIS>
 __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const float *__restrict__ rule,
                                           int np, int lane, float kappa = 0.0f)
@@ -1060,10 +1060,12 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
 
 // ---------------------------------------------------------------------------
 // Block engine, piecewise linear: tile = 32 x 32 vertices.  The triangles
-// touching the tile's rows (Ta) and columns (Tb) are collected in shared
-// memory; the 3x3 local matrices of all pairs Ta x Tb are computed chunk by
-// chunk (one thread per pair) into shared memory and gathered by the owner
-// thread of each entry in a fixed order (deterministic sums).
+// touching the tile's rows (Ta) and columns (Tb) come to shared memory from the
+// per-run support records (plans) or are collected by the tile itself (single
+// calls; same function, same result); the 3x3 local matrices of all pairs
+// Ta x Tb are computed chunk by chunk (one thread per pair) into shared memory
+// and gathered by the owner thread of each entry in a fixed order
+// (deterministic sums).
 // ---------------------------------------------------------------------------
 // pairs per chunk: float results (36 KB per chunk) leave room for four CTAs
 // per SM; double results stay at 512 pairs so that complex chunks fit too

@@ -309,6 +309,10 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         ji.near = k < n_near;
         ji.touch_job = -1;
         int rc = api_check_job(ctx, J, ji.r2, &ji.m);
+        if (rc == BEM_OK && J.quad.order_mode != BEM_ORDER_FIXED)
+            rc = api_fail(ctx, BEM_ERR_UNSUPPORTED,
+                          "plans run fixed orders; learned orders go through bem_near_field / "
+                          "bem_coupling_blocks");
         if (rc) {
             plan_free(p);
             return rc;
