@@ -160,6 +160,9 @@ struct BlockLaunch {
     const int32_t *sup_r = nullptr, *sup_c = nullptr;
     const int32_t *slice_r = nullptr, *slice_c = nullptr;
     int64_t cap_r = 0, cap_c = 0;
+    // fused coupling jobs: the double-layer output of the same blocks (the
+    // single-layer one is `out`), null otherwise
+    void *out2 = nullptr;
 };
 
 // One support record (int32 words, 16-byte multiple): list lengths [kTile],
@@ -228,6 +231,11 @@ cudaError_t launch_coupling_p1(const MeshView &m, const BlockLaunch &L, const Ru
 cudaError_t launch_coupling_p1_batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end,
                                      int kind, const Rule2D &R, int *status, int grid,
                                      cudaStream_t st);
+// Single and double layer of the same coupling blocks in one pass (the
+// distance and its reciprocal square root are shared): jobs carry both outputs.
+cudaError_t launch_coupling_p1_fused_batch(const BatchJob *jobs, int n_jobs,
+                                           const int64_t *job_end, const Rule2D &R, int *status,
+                                           int grid, cudaStream_t st);
 // bem_block.cu: support records of all 32-index slices of a cluster list
 // (ptr, idx, n_clusters) into sup (cap records); slice gets n_clusters + 1
 // entries (exclusive prefix of the slice counts).

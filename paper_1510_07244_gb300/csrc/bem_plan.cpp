@@ -35,6 +35,7 @@ struct TouchBucket {
 struct BlockBucket {
     int basis, kind, mixed;
     bool coupling = false;   // coupling engine (16 x 2 entry tiles) instead of the tile engine
+    bool fused = false;      // coupling engine, single and double layer of the same blocks
     Rule2D r2;
     std::vector<BatchJob> host_jobs;
     BatchJob *jobs = nullptr;
@@ -148,6 +149,9 @@ int tile_cols(const BlockBucket &b) { return b.coupling ? kCouplingCols : (b.bas
 
 cudaError_t launch_bucket(bem_ctx *ctx, const BlockBucket &b, int mult, cudaStream_t st)
 {
+    if (b.fused)
+        return launch_coupling_p1_fused_batch(b.jobs, (int)b.host_jobs.size(), b.job_end, b.r2,
+                                              ctx->status, ctx->num_sms * mult, st);
     if (b.coupling)
         return launch_coupling_p1_batch(b.jobs, (int)b.host_jobs.size(), b.job_end, b.kind, b.r2,
                                         ctx->status, ctx->num_sms * mult, st);
@@ -369,17 +373,49 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         p->tb.push_back(t);
     }
 
+    // coupling jobs of the single and the double layer over the same blocks of
+    // the same mesh (same device arrays, same rule) run fused: the double-layer
+    // job's output rides on the single-layer job, which then computes both
+    std::vector<void *> out2(jobs.size(), nullptr);
+    std::vector<char> absorbed(jobs.size(), 0);
+    auto same_blocks = [](const bem_block_job &x, const bem_block_job &y) {
+        return x.mesh_id == y.mesh_id && x.row_ptr == y.row_ptr && x.row_idx == y.row_idx &&
+               x.col_ptr == y.col_ptr && x.col_idx == y.col_idx && x.blk_row == y.blk_row &&
+               x.blk_col == y.blk_col && x.blk_off == y.blk_off && x.n_blocks == y.n_blocks &&
+               x.n_row_clusters == y.n_row_clusters && x.n_col_clusters == y.n_col_clusters &&
+               x.quad.precision == y.quad.precision && x.quad.regular_rule == y.quad.regular_rule &&
+               x.quad.q_regular == y.quad.q_regular;
+    };
+    for (size_t x = 0; x < jobs.size(); ++x) {
+        const bem_block_job &Jx = *jobs[x].J;
+        if (jobs[x].near || Jx.n_blocks == 0 || Jx.kernel.kind != BEM_LAPLACE_SLP || out2[x]) continue;
+        if (!use_coupling_engine(jobs[x].m->v.basis, Jx.kernel.kind, is_mixed(Jx.quad.precision), 0))
+            continue;
+        for (size_t y = 0; y < jobs.size(); ++y) {
+            const bem_block_job &Jy = *jobs[y].J;
+            if (y == x || jobs[y].near || absorbed[y] || Jy.kernel.kind != BEM_LAPLACE_DLP ||
+                !same_blocks(Jx, Jy) || Jy.out == Jx.out)
+                continue;
+            out2[x] = Jy.out;
+            absorbed[y] = 1;
+            break;
+        }
+    }
+
     // block buckets
     std::map<std::string, int> bindex;
-    for (auto &ji : jobs) {
+    for (size_t jx = 0; jx < jobs.size(); ++jx) {
+        auto &ji = jobs[jx];
         const bem_block_job &J = *ji.J;
-        if (J.n_blocks == 0) continue;
+        if (J.n_blocks == 0 || absorbed[jx]) continue;
         const int mixed = is_mixed(J.quad.precision) &&
                           !(J.kernel.kind == BEM_HELMHOLTZ_SLP && ji.m->v.basis == BEM_P1);
         const bool coupling = use_coupling_engine(ji.m->v.basis, J.kernel.kind, mixed, ji.near ? 1 : 0);
+        const bool fused = out2[jx] != nullptr;
         char key[96];
-        std::snprintf(key, sizeof key, "b%d k%d np%d m%d r%d q%d c%d", ji.m->v.basis, J.kernel.kind,
-                      ji.r2.np, mixed, J.quad.regular_rule, J.quad.q_regular, coupling ? 1 : 0);
+        std::snprintf(key, sizeof key, "b%d k%d np%d m%d r%d q%d c%d f%d", ji.m->v.basis,
+                      J.kernel.kind, ji.r2.np, mixed, J.quad.regular_rule, J.quad.q_regular,
+                      coupling ? 1 : 0, fused ? 1 : 0);
         auto it = bindex.find(key);
         if (it == bindex.end()) {
             BlockBucket b;
@@ -387,6 +423,7 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
             b.kind = J.kernel.kind;
             b.mixed = mixed;
             b.coupling = coupling;
+            b.fused = fused;
             b.r2 = ji.r2;
             b.key = key;
             b.name = coupling ? "coupling_p1" : (b.basis == BEM_P0 ? "block_p0" : "block_p1");
@@ -411,6 +448,7 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         L.blk_off = J.blk_off;
         L.n_blocks = J.n_blocks;
         L.out = J.out;
+        L.out2 = out2[jx];
         L.kind = J.kernel.kind;
         L.kappa = J.kernel.kappa;
         L.lower_only = 0;

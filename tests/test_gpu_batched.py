@@ -193,3 +193,46 @@ def test_plan_rejects_learned_orders(env, small_batch):
     assert ei.value.code == -6
     for m in mids:
         ctx.bem_mesh_free(m)
+
+
+def test_plan_fuses_single_and_double_layer_coupling(env):
+    """Coupling jobs of both layers over the same device block arrays run as one
+    fused launch (shared distances) and give the per-job results bit for bit."""
+    import torch
+    from parity_util import oracle_absolute, rel_err_abs, to_dev
+    pkg, ctx = env
+    mesh = synth.jitter(synth.icosphere(3), 0.05, 5)
+    _, near, far = synth.workloads.h2_blocks(mesh, "p1", 16, 2.0, 6, 5)
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p1")
+    quad = dict(QUAD, precision="mixed_full")
+    arr = [to_dev(a, torch.int32) for a in (far.row_ptr, far.row_idx, far.blk_row, far.blk_col)]
+    off = to_dev(far.blk_off, torch.int64)
+    jobs, outs = [], []
+    for kernel in ("laplace_slp", "laplace_dlp"):
+        o = torch.full((far.n_entries,), float("nan"), dtype=torch.float64, device="cuda")
+        jobs.append(pkg.BlockJob(mid, arr[0], arr[1], arr[0], arr[1], arr[2], arr[3], off, o,
+                                 pkg.kernel_desc(kernel), pkg.quad_desc(**quad)))
+        outs.append(o)
+    for j in jobs:
+        ctx.bem_coupling_blocks([j])
+    ctx.bem_sync()
+    ref = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(float("nan"))
+    plan = ctx.bem_plan_create([], jobs, pkg.PLAN_GRAPH | pkg.PLAN_PROFILE)
+    ctx.bem_profile_reset()
+    ctx.bem_profile_enable(True)
+    ctx.bem_plan_run(plan)
+    prof = ctx.bem_profile_read()
+    ctx.bem_profile_enable(False)
+    assert ctx.bem_plan_info(plan)["block_launches"] == 1
+    assert prof["coupling_p1"][0] == 1
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+    r, c = far.entry_indices()
+    for kernel, o in zip(("laplace_slp", "laplace_dlp"), outs):
+        want = oracle_entries(mesh, "p1", r, c, kernel, 0.0, QUAD)
+        A = oracle_absolute(mesh, "p1", r, c, kernel, 0.0, QUAD)
+        assert rel_err_abs(o.cpu().numpy(), want, A, r).max() <= 1e-6
+    ctx.bem_plan_destroy(plan)
+    ctx.bem_mesh_free(mid)
