@@ -98,6 +98,12 @@ def kernel_flops(w, counts, stats, precision):
     # the float forms cover the Laplace kernels, and Helmholtz on the P0 basis
     pipe = "fp32" if mixed and (w.basis == "p0" or len(laplace_ops) == len(w.operators)) else "fp64"
     coupling = mixed and w.basis == "p1" and pipe == "fp32"
+    # plans fuse the single and double layer of the same P1 blocks in the float
+    # forms: one launch evaluates both, so the work they share per point (the
+    # difference 3, r^2 5, rsqrt 1) and, in the coupling engine, per test point
+    # (x 6) counts once
+    kinds = sorted(o.kernel for o in w.operators)
+    fused = mixed and w.basis == "p1" and kinds == ["laplace_dlp", "laplace_slp"]
     if coupling:
         # coupling blocks run one entry per lane: deg(i) deg(j) pairs per entry,
         # per point the piecewise-constant count (the trial basis value is
@@ -107,8 +113,12 @@ def kernel_flops(w, counts, stats, precision):
         f_cpl = sum(counts["far_entry_pairs"] * npts_reg *
                     (flops_per_point(o.kernel, "p0", np_axis) + 10.0 / np_axis)
                     for o in w.operators)
+        if fused:
+            f_cpl -= counts["far_entry_pairs"] * npts_reg * (9.0 + 6.0 / np_axis)
         out["coupling_p1"] = (f_cpl, "fp32")
     f_blk = sum(reg * npts_reg * flops_per_point(o.kernel, w.basis, np_axis) for o in w.operators)
+    if fused:
+        f_blk -= reg * npts_reg * 9.0
     out["block_p1" if w.basis == "p1" else "block_p0"] = (f_blk, pipe)
     for cas, nsub, qq, key in (("touching_vertex", 2, q.q_vertex, "n_vertex"),
                                ("touching_edge", 4, q.q_edge, "n_edge"),

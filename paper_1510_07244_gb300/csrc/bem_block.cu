@@ -228,10 +228,11 @@ cudaError_t launch_build_supports(const MeshView &m, const int32_t *ptr, const i
     return cudaGetLastError();
 }
 
-size_t p1_smem_bytes(bool cplx, bool mixed)
+size_t p1_smem_bytes(bool cplx, bool mixed, bool fused)
 {
     return ((sizeof(P1Smem) + 15) & ~size_t(15)) +
-           (size_t)p1_cap(mixed) * 9 * (mixed ? sizeof(float) : sizeof(double)) * (cplx ? 2 : 1);
+           (size_t)p1_cap(mixed, fused) * 9 * (mixed ? sizeof(float) : sizeof(double)) *
+               (cplx || fused ? 2 : 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -444,6 +445,10 @@ cudaError_t launch_block_batch(const BatchJob *jobs, int n_jobs, const int64_t *
                                cudaStream_t st)
 {
     if (n_jobs <= 0) return cudaSuccess;
+    if (kind == kFusedLaplace)   // piecewise-linear float form only
+        return (basis == BEM_P1 && mixed)
+                   ? launch_p1_batch_mixed(kFusedLaplace, R.np, jobs, n_jobs, job_end, R, status, grid, st)
+                   : cudaErrorInvalidValue;
     switch (kind) {
     case BEM_LAPLACE_SLP:
         return mixed ? batch_kind<BEM_LAPLACE_SLP, true>(jobs, n_jobs, job_end, basis, R, status, grid, st)

@@ -43,7 +43,7 @@ cudaError_t single(const MeshView &m, const BlockLaunch &L, const Rule2D &R, con
                    int *status, int grid, cudaStream_t st)
 {
     constexpr bool MIXED = BEM_P1_MIXED;
-    const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP, MIXED);
+    const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP, MIXED, KIND == kFusedLaplace);
     cudaError_t e = cudaFuncSetAttribute(k_block_p1<KIND, NP, MIXED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -56,7 +56,7 @@ cudaError_t batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end, cons
                   int *status, int grid, cudaStream_t st)
 {
     constexpr bool MIXED = BEM_P1_MIXED;
-    const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP, MIXED);
+    const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP, MIXED, KIND == kFusedLaplace);
     // set once (outside any stream capture: plans issue once before capturing)
     static bool attr_done = false;
     if (!attr_done) {
@@ -91,6 +91,7 @@ cudaError_t batch_kind(int kind, const BatchJob *jobs, int n_jobs, const int64_t
 #if !BEM_P1_MIXED
     return batch<BEM_HELMHOLTZ_SLP, NP>(jobs, n_jobs, job_end, R, status, grid, st);
 #else
+    if (kind == kFusedLaplace) return batch<kFusedLaplace, NP>(jobs, n_jobs, job_end, R, status, grid, st);
     return cudaErrorInvalidValue;
 #endif
 }

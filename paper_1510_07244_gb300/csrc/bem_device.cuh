@@ -664,6 +664,63 @@ __device__ __forceinline__ void touch_pair(const MeshView &m, int idx, const dou
     }
 }
 
+// Both Laplace layers of a regular pair (two 3x3 local matrices): each is formed
+// exactly as regular_p1_f32 forms it, sharing the points, distances and
+// reciprocal square roots.
+template <int NP>
+__device__ __forceinline__ void regular_p1_f32_fused(const TriF &A, const TriF &B, const Rule2D &R,
+                                                     float *acc_s, float *acc_d)
+{
+    float d0[3], yx[NP], yy[NP], yz[NP];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d0[c] = dd_diff(A.vh[0][c], A.vl[0][c], B.vh[0][c], B.vl[0][c]);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        yx[j] = fmaf(R.sf[j], B.e1[0], R.tf[j] * B.e2[0]);
+        yy[j] = fmaf(R.sf[j], B.e1[1], R.tf[j] * B.e2[1]);
+        yz[j] = fmaf(R.sf[j], B.e1[2], R.tf[j] * B.e2[2]);
+    }
+    const Height H = make_height(A.vh[0], A.vl[0], A.vh[1], A.vl[1], A.vh[2], A.vl[2], B.vh[0],
+                                 B.vl[0], B.nh, B.nl);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc_s[k] = acc_d[k] = 0.0f;
+#pragma unroll 1
+    for (int i = 0; i < NP; ++i) {
+        const float xx = fmaf(R.sf[i], A.e1[0], fmaf(R.tf[i], A.e2[0], d0[0]));
+        const float xy = fmaf(R.sf[i], A.e1[1], fmaf(R.tf[i], A.e2[1], d0[1]));
+        const float xz = fmaf(R.sf[i], A.e1[2], fmaf(R.tf[i], A.e2[2], d0[2]));
+        const float dn = height_at(H, R.sf[i], R.tf[i]);
+        float is[3] = {0.0f, 0.0f, 0.0f}, id[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            const float dx = xx - yx[j], dy = xy - yy[j], dz = xz - yz[j];
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = rsqrt_fast(r2);
+            const float kd = dn * (ri * ri * ri);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                is[q] = fmaf(R.wl[q][j], ri, is[q]);
+                id[q] = fmaf(R.wl[q][j], kd, id[q]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const float f = R.wl[p][i];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                acc_s[p * 3 + q] = fmaf(f, is[q], acc_s[p * 3 + q]);
+                acc_d[p * 3 + q] = fmaf(f, id[q], acc_d[p * 3 + q]);
+            }
+        }
+    }
+    const float scale = A.sg * B.sg * (float)kInv4Pi;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        acc_s[k] *= scale;
+        acc_d[k] *= scale;
+    }
+}
+
 // Touching pairs in float (mixed form).  The canonical vertex order puts the
 // shared vertices first, so x - y is formed from edge vectors and the rule's
 // difference columns only and keeps float precision down to the singular set:
@@ -1069,7 +1126,10 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
 // ---------------------------------------------------------------------------
 // pairs per chunk: float results (36 KB per chunk) leave room for four CTAs
 // per SM; double results stay at 512 pairs so that complex chunks fit too
-__host__ __device__ constexpr int p1_cap(bool mixed) { return mixed ? 1024 : 512; }
+__host__ __device__ constexpr int p1_cap(bool mixed, bool fused = false)
+{
+    return mixed && !fused ? 1024 : 512;   // fused: two float results per pair, same bytes
+}
 constexpr int kP1MaxTri = kTile * kMaxDegP1;
 
 struct P1Smem {
@@ -1202,14 +1262,18 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
                                         int *status, unsigned char *smem_raw)
 {
     constexpr bool CPLX = KIND == BEM_HELMHOLTZ_SLP;
+    // fused: single layer in the real slots, double layer in the second ones
+    constexpr bool FUSED = KIND == kFusedLaplace;
+    constexpr bool TWO = CPLX || FUSED;
     constexpr int NT = p1_threads(MIXED);
     constexpr int NE = kTile * kTile / NT;     // entries owned per thread
     constexpr int EW = NT / 32;                // column stride of owned entries
+    constexpr int CAP = p1_cap(MIXED, FUSED);
     // pair results: double in the FP64 form, float in the mixed form
     using Val = typename std::conditional<MIXED, float, double>::type;
     P1Smem &S = *reinterpret_cast<P1Smem *>(smem_raw);
     Val *buf_r = reinterpret_cast<Val *>(smem_raw + ((sizeof(P1Smem) + 15) & ~size_t(15)));
-    Val *buf_i = buf_r + p1_cap(MIXED) * 9;
+    Val *buf_i = buf_r + CAP * 9;
     const int tid = threadIdx.x;
     {
         const BlockInfo bi = block_info(L, prefix, tile, status);
@@ -1259,10 +1323,11 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
             nta = S.nta;
             ntb = S.ntb;
         }
-        const int ia_step = max(1, p1_cap(MIXED) / max(ntb, 1));
-        Val accr[NE], acci[NE], cmpr[NE];   // cmpr: Kahan compensation (mixed form)
+        const int ia_step = max(1, CAP / max(ntb, 1));
+        // cmpr, cmpi: Kahan compensations (mixed form)
+        Val accr[NE], acci[NE], cmpr[NE], cmpi[NE];
 #pragma unroll
-        for (int e = 0; e < NE; ++e) accr[e] = acci[e] = cmpr[e] = 0;
+        for (int e = 0; e < NE; ++e) accr[e] = acci[e] = cmpr[e] = cmpi[e] = 0;
         const int er = tid & 31;
         // this thread's row vertex: its support list is sorted by triangle
         // slot, so the rows of each chunk are the next run of the list
@@ -1286,8 +1351,19 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
                         for (int q = 0; q < 9; ++q) {
                             const double2 t = m.table[(int64_t)k * 9 + q];
                             vr[q] = (Val)t.x;
-                            vi[q] = (Val)t.y;
+                            vi[q] = FUSED ? (Val)L.table2[(int64_t)k * 9 + q].x : (Val)t.y;
                         }
+                    }
+                } else if (FUSED) {
+                    TriF A, B;
+                    load_trif(m.geomf, a, A);
+                    load_trif(m.geomf, b, B);
+                    float fs[9], fd[9];
+                    regular_p1_f32_fused<NP>(A, B, R, fs, fd);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        vr[q] = (Val)fs[q];
+                        vi[q] = (Val)fd[q];
                     }
                 } else if (MIXED) {
                     TriF A, B;
@@ -1315,7 +1391,7 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
                     buf_r[p * 9 + q] = vr[q];
-                    if (CPLX) buf_i[p * 9 + q] = vi[q];
+                    if (TWO) buf_i[p * 9 + q] = vi[q];
                 }
             }
             __syncthreads();
@@ -1336,6 +1412,12 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
                                 const Val t = accr[e] + y;
                                 cmpr[e] = (t - accr[e]) - y;
                                 accr[e] = t;
+                                if (FUSED) {
+                                    const Val y2 = buf_i[q] - cmpi[e];
+                                    const Val t2 = acci[e] + y2;
+                                    cmpi[e] = (t2 - acci[e]) - y2;
+                                    acci[e] = t2;
+                                }
                             } else {
                                 accr[e] += buf_r[q];
                             }
@@ -1352,10 +1434,12 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
             if (er < tr && ec < tc) {
                 if (L.lower_only && S.rows[er] < S.cols[ec]) continue;
                 const int64_t o = bi.off + (int64_t)(r0 + er) + (int64_t)(c0 + ec) * bi.nr;
-                if (CPLX)
+                if (CPLX) {
                     reinterpret_cast<double2 *>(L.out)[o] = make_double2((double)accr[e], (double)acci[e]);
-                else
+                } else {
                     reinterpret_cast<double *>(L.out)[o] = (double)accr[e];
+                    if (FUSED) reinterpret_cast<double *>(L.out2)[o] = (double)acci[e];
+                }
             }
         }
         __syncthreads();

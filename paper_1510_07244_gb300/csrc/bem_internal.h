@@ -160,10 +160,15 @@ struct BlockLaunch {
     const int32_t *sup_r = nullptr, *sup_c = nullptr;
     const int32_t *slice_r = nullptr, *slice_c = nullptr;
     int64_t cap_r = 0, cap_c = 0;
-    // fused coupling jobs: the double-layer output of the same blocks (the
-    // single-layer one is `out`), null otherwise
+    // fused jobs (single and double layer of the same blocks): the double-layer
+    // output (the single-layer one is `out`) and, for the near field, the
+    // double layer's touching table (the single layer's is the mesh view's)
     void *out2 = nullptr;
+    const double2 *table2 = nullptr;
 };
+
+// Internal kernel id of the fused single + double layer (never a public kind).
+constexpr int kFusedLaplace = 3;
 
 // One support record (int32 words, 16-byte multiple): list lengths [kTile],
 // per-vertex lists [kMaxDegP1][kTile], triangles [kTile * kMaxDegP1], count.
@@ -206,7 +211,7 @@ cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t
                             cudaStream_t st);
 cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const Rule2D &rule,
                                 const int64_t *prefix, int *status, int grid, cudaStream_t st);
-size_t p1_smem_bytes(bool cplx, bool mixed);
+size_t p1_smem_bytes(bool cplx, bool mixed, bool fused = false);
 // bem_block_p1_{fp64,mixed}.cu: piecewise-linear block engine per precision
 cudaError_t launch_p1_single_fp64(int kind, int np, const MeshView &m, const BlockLaunch &L,
                                   const Rule2D &R, const int64_t *prefix, int *status, int grid,

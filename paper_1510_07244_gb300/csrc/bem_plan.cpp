@@ -149,9 +149,12 @@ int tile_cols(const BlockBucket &b) { return b.coupling ? kCouplingCols : (b.bas
 
 cudaError_t launch_bucket(bem_ctx *ctx, const BlockBucket &b, int mult, cudaStream_t st)
 {
-    if (b.fused)
+    if (b.fused && b.coupling)
         return launch_coupling_p1_fused_batch(b.jobs, (int)b.host_jobs.size(), b.job_end, b.r2,
                                               ctx->status, ctx->num_sms * mult, st);
+    if (b.fused)
+        return launch_block_batch(b.jobs, (int)b.host_jobs.size(), b.job_end, b.basis, kFusedLaplace,
+                                  b.mixed, b.r2, ctx->status, ctx->num_sms * mult, st);
     if (b.coupling)
         return launch_coupling_p1_batch(b.jobs, (int)b.host_jobs.size(), b.job_end, b.kind, b.r2,
                                         ctx->status, ctx->num_sms * mult, st);
@@ -373,10 +376,13 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         p->tb.push_back(t);
     }
 
-    // coupling jobs of the single and the double layer over the same blocks of
-    // the same mesh (same device arrays, same rule) run fused: the double-layer
-    // job's output rides on the single-layer job, which then computes both
+    // jobs of the single and the double layer over the same blocks of the same
+    // mesh (same device arrays, same regular rule, both near field or both
+    // coupling) run fused in the float forms of the piecewise-linear basis: the
+    // double-layer job's output (and touching table) ride on the single-layer
+    // job, which then computes both
     std::vector<void *> out2(jobs.size(), nullptr);
+    std::vector<const double2 *> table2(jobs.size(), nullptr);
     std::vector<char> absorbed(jobs.size(), 0);
     auto same_blocks = [](const bem_block_job &x, const bem_block_job &y) {
         return x.mesh_id == y.mesh_id && x.row_ptr == y.row_ptr && x.row_idx == y.row_idx &&
@@ -388,15 +394,16 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
     };
     for (size_t x = 0; x < jobs.size(); ++x) {
         const bem_block_job &Jx = *jobs[x].J;
-        if (jobs[x].near || Jx.n_blocks == 0 || Jx.kernel.kind != BEM_LAPLACE_SLP || out2[x]) continue;
-        if (!use_coupling_engine(jobs[x].m->v.basis, Jx.kernel.kind, is_mixed(Jx.quad.precision), 0))
+        if (Jx.n_blocks == 0 || Jx.kernel.kind != BEM_LAPLACE_SLP || out2[x] ||
+            jobs[x].m->v.basis != BEM_P1 || !is_mixed(Jx.quad.precision))
             continue;
         for (size_t y = 0; y < jobs.size(); ++y) {
             const bem_block_job &Jy = *jobs[y].J;
-            if (y == x || jobs[y].near || absorbed[y] || Jy.kernel.kind != BEM_LAPLACE_DLP ||
-                !same_blocks(Jx, Jy) || Jy.out == Jx.out)
+            if (y == x || jobs[y].near != jobs[x].near || absorbed[y] ||
+                Jy.kernel.kind != BEM_LAPLACE_DLP || !same_blocks(Jx, Jy) || Jy.out == Jx.out)
                 continue;
             out2[x] = Jy.out;
+            if (jobs[x].near) table2[x] = tj[jobs[y].touch_job].m.table;
             absorbed[y] = 1;
             break;
         }
@@ -449,6 +456,7 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         L.n_blocks = J.n_blocks;
         L.out = J.out;
         L.out2 = out2[jx];
+        L.table2 = table2[jx];
         L.kind = J.kernel.kind;
         L.kappa = J.kernel.kappa;
         L.lower_only = 0;

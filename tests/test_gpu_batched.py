@@ -195,9 +195,10 @@ def test_plan_rejects_learned_orders(env, small_batch):
         ctx.bem_mesh_free(m)
 
 
-def test_plan_fuses_single_and_double_layer_coupling(env):
-    """Coupling jobs of both layers over the same device block arrays run as one
-    fused launch (shared distances) and give the per-job results bit for bit."""
+def test_plan_fuses_single_and_double_layer(env):
+    """Jobs of both layers over the same device block arrays run fused (near
+    field: one tile engine launch; coupling: one coupling launch), sharing the
+    distances, and give the per-job results bit for bit."""
     import torch
     from parity_util import oracle_absolute, rel_err_abs, to_dev
     pkg, ctx = env
@@ -205,34 +206,35 @@ def test_plan_fuses_single_and_double_layer_coupling(env):
     _, near, far = synth.workloads.h2_blocks(mesh, "p1", 16, 2.0, 6, 5)
     mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p1")
     quad = dict(QUAD, precision="mixed_full")
-    arr = [to_dev(a, torch.int32) for a in (far.row_ptr, far.row_idx, far.blk_row, far.blk_col)]
-    off = to_dev(far.blk_off, torch.int64)
-    jobs, outs = [], []
-    for kernel in ("laplace_slp", "laplace_dlp"):
-        o = torch.full((far.n_entries,), float("nan"), dtype=torch.float64, device="cuda")
-        jobs.append(pkg.BlockJob(mid, arr[0], arr[1], arr[0], arr[1], arr[2], arr[3], off, o,
-                                 pkg.kernel_desc(kernel), pkg.quad_desc(**quad)))
-        outs.append(o)
-    for j in jobs:
-        ctx.bem_coupling_blocks([j])
+    jobs = {"near": [], "far": []}
+    outs = []
+    for name, bs in (("near", near), ("far", far)):
+        arr = [to_dev(a, torch.int32) for a in (bs.row_ptr, bs.row_idx, bs.blk_row, bs.blk_col)]
+        off = to_dev(bs.blk_off, torch.int64)
+        for kernel in ("laplace_slp", "laplace_dlp"):
+            o = torch.full((bs.n_entries,), float("nan"), dtype=torch.float64, device="cuda")
+            jobs[name].append(pkg.BlockJob(mid, arr[0], arr[1], arr[0], arr[1], arr[2], arr[3], off,
+                                           o, pkg.kernel_desc(kernel), pkg.quad_desc(**quad)))
+            outs.append((name, kernel, bs, o))
+    ctx.bem_near_field(jobs["near"])
+    ctx.bem_coupling_blocks(jobs["far"])
     ctx.bem_sync()
-    ref = [o.clone() for o in outs]
-    for o in outs:
+    ref = [o.clone() for *_, o in outs]
+    for *_, o in outs:
         o.fill_(float("nan"))
-    plan = ctx.bem_plan_create([], jobs, pkg.PLAN_GRAPH | pkg.PLAN_PROFILE)
+    plan = ctx.bem_plan_create(jobs["near"], jobs["far"], pkg.PLAN_GRAPH | pkg.PLAN_PROFILE)
     ctx.bem_profile_reset()
     ctx.bem_profile_enable(True)
     ctx.bem_plan_run(plan)
     prof = ctx.bem_profile_read()
     ctx.bem_profile_enable(False)
-    assert ctx.bem_plan_info(plan)["block_launches"] == 1
-    assert prof["coupling_p1"][0] == 1
-    for o, r in zip(outs, ref):
-        assert torch.equal(o, r)
-    r, c = far.entry_indices()
-    for kernel, o in zip(("laplace_slp", "laplace_dlp"), outs):
-        want = oracle_entries(mesh, "p1", r, c, kernel, 0.0, QUAD)
-        A = oracle_absolute(mesh, "p1", r, c, kernel, 0.0, QUAD)
-        assert rel_err_abs(o.cpu().numpy(), want, A, r).max() <= 1e-6
+    assert ctx.bem_plan_info(plan)["block_launches"] == 2
+    assert prof["coupling_p1"][0] == 1 and prof["block_p1"][0] == 1
+    for (name, kernel, bs, o), r in zip(outs, ref):
+        assert torch.equal(o, r), (name, kernel)
+        rows, cols = bs.entry_indices()
+        want = oracle_entries(mesh, "p1", rows, cols, kernel, 0.0, QUAD)
+        A = oracle_absolute(mesh, "p1", rows, cols, kernel, 0.0, QUAD)
+        assert rel_err_abs(o.cpu().numpy(), want, A, rows).max() <= 1e-6, (name, kernel)
     ctx.bem_plan_destroy(plan)
     ctx.bem_mesh_free(mid)
