@@ -27,8 +27,19 @@ k_batch_p1(const BatchJob *__restrict__ jobs, int n_jobs, const int64_t *__restr
            Rule2D R, int *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int64_t next_tile;
     const int64_t total = n_jobs > 0 ? job_end[n_jobs - 1] : 0;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    // tiles differ in cost (cluster and support sizes): each CTA takes the
+    // next tile from the counter job_end[n_jobs] (zeroed before the launch)
+    // instead of a fixed stride, so that all SMs finish together
+    unsigned long long *counter =
+        reinterpret_cast<unsigned long long *>(const_cast<int64_t *>(job_end + n_jobs));
+    for (;;) {
+        if (threadIdx.x == 0) next_tile = (int64_t)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t tile = next_tile;
+        __syncthreads();
+        if (tile >= total) break;
         const int j = find_job(job_end, n_jobs, tile);
         const int64_t local = tile - (j > 0 ? job_end[j - 1] : 0);
         const BatchJob &J = jobs[j];
@@ -65,6 +76,8 @@ cudaError_t batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end, cons
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
+    cudaError_t e = cudaMemsetAsync(const_cast<int64_t *>(job_end) + n_jobs, 0, sizeof(int64_t), st);
+    if (e != cudaSuccess) return e;
     k_batch_p1<KIND, NP, MIXED><<<grid, p1_threads(MIXED), sm, st>>>(jobs, n_jobs, job_end, R, status);
     return cudaGetLastError();
 }

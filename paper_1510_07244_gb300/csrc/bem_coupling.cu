@@ -50,7 +50,8 @@ __device__ __forceinline__ float coupling_pair(const TriF &A, const TriF &B, int
         float inner = 0.0f;
 #pragma unroll
         for (int j = 0; j < NP; ++j)
-            inner = fmaf(wy[j], kvalf<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], dn), inner);
+            inner = fmaf(wy[j], kvalf_r<KIND>(xx - yx[j], xy - yy[j], xz - yz[j]), inner);
+        if (KIND == BEM_LAPLACE_DLP) inner *= dn;
         const float wx = la == 0 ? R.wl[0][i] : (la == 1 ? R.wl[1][i] : R.wl[2][i]);
         sum = fmaf(wx, inner, sum);
     }
@@ -85,8 +86,9 @@ __device__ __forceinline__ void coupling_pair2(const TriF &A, const TriF &B, int
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float ri = rsqrt_fast(r2);
             in_s = fmaf(wy[j], ri, in_s);
-            in_d = fmaf(wy[j], dn * (ri * ri * ri), in_d);
+            in_d = fmaf(wy[j], ri * ri * ri, in_d);
         }
+        in_d *= dn;
         const float wx = la == 0 ? R.wl[0][i] : (la == 1 ? R.wl[1][i] : R.wl[2][i]);
         sum_s = fmaf(wx, in_s, sum_s);
         sum_d = fmaf(wx, in_d, sum_d);

@@ -251,6 +251,18 @@ __device__ __forceinline__ float kvalf(float dx, float dy, float dz, float dn)
     return dn * (ri * ri * ri);
 }
 
+// The same without the double layer's height factor: 1/r (single layer) or
+// 1/r^3 (double layer).  Product rules whose inner loop runs over trial points
+// at one test point x multiply the inner sum by the height of x once instead.
+template <int KIND>
+__device__ __forceinline__ float kvalf_r(float dx, float dy, float dz)
+{
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ri = rsqrt_fast(r2);
+    if (KIND == BEM_LAPLACE_SLP) return ri;
+    return ri * ri * ri;
+}
+
 // ---------------------------------------------------------------------------
 // Helmholtz in the mixed form.  exp(i kappa r) = exp(i kappa r0) exp(i kappa
 // (r - r0)) with r0 = the distance of the two centroids: r0, kappa r0 and its
@@ -428,7 +440,8 @@ __device__ __forceinline__ float regular_p0_f32(const TriF &A, const TriF &B, co
         float inner = 0.0f;
 #pragma unroll
         for (int j = 0; j < NP; ++j)
-            inner = fmaf(R.wf[j], kvalf<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], dn), inner);
+            inner = fmaf(R.wf[j], kvalf_r<KIND>(xx - yx[j], xy - yy[j], xz - yz[j]), inner);
+        if (KIND == BEM_LAPLACE_DLP) inner *= dn;
         // compensated outer sum (Kahan)
         const float y = fmaf(R.wf[i], inner, -comp);
         const float t = sum + y;
@@ -478,10 +491,14 @@ __device__ __forceinline__ void regular_p1_f32(const TriF &A, const TriF &B, con
         float ir[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            const float k = kvalf<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], dn);
+            const float k = kvalf_r<KIND>(xx - yx[j], xy - yy[j], xz - yz[j]);
             ir[0] = fmaf(R.wl[0][j], k, ir[0]);
             ir[1] = fmaf(R.wl[1][j], k, ir[1]);
             ir[2] = fmaf(R.wl[2][j], k, ir[2]);
+        }
+        if (KIND == BEM_LAPLACE_DLP) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) ir[q] *= dn;
         }
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
@@ -696,13 +713,15 @@ __device__ __forceinline__ void regular_p1_f32_fused(const TriF &A, const TriF &
             const float dx = xx - yx[j], dy = xy - yy[j], dz = xz - yz[j];
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float ri = rsqrt_fast(r2);
-            const float kd = dn * (ri * ri * ri);
+            const float r3 = ri * ri * ri;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 is[q] = fmaf(R.wl[q][j], ri, is[q]);
-                id[q] = fmaf(R.wl[q][j], kd, id[q]);
+                id[q] = fmaf(R.wl[q][j], r3, id[q]);
             }
         }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) id[q] *= dn;
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
             const float f = R.wl[p][i];

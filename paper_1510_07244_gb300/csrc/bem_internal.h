@@ -249,6 +249,9 @@ cudaError_t launch_build_supports(const MeshView &m, const int32_t *ptr, const i
                                   int *status, int grid, cudaStream_t st);
 cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int cas, int mixed,
                                   const int2 *items, int64_t n, const Rule4D &rule, cudaStream_t st);
+// Block buckets of many jobs: job_end[j] = tiles of jobs 0..j (inclusive
+// prefix); job_end holds n_jobs + 1 entries, the last one the tile counter of
+// the piecewise-linear tile engine (reset by the launch).
 cudaError_t launch_block_batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end, int basis,
                                int kind, int mixed, const Rule2D &R, int *status, int grid,
                                cudaStream_t st);

@@ -662,9 +662,10 @@ __global__ void __launch_bounds__(256) k_learned_eval_big(MeshView m, const int4
                         ir = fmaf(R.w[jc + j], kr, ir);
                         ii = fmaf(R.w[jc + j], ki, ii);
                     } else {
-                        ir = fmaf(R.w[jc + j], kvalf<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], dn), ir);
+                        ir = fmaf(R.w[jc + j], kvalf_r<KIND>(xx - yx[j], xy - yy[j], xz - yz[j]), ir);
                     }
                 }
+                if (KIND == BEM_LAPLACE_DLP) ir *= dn;
                 // Kahan sums over the (test point, chunk) partial sums
                 float y = fmaf(R.w[i], ir, -cr), t = sr + y;
                 cr = (t - sr) - y;

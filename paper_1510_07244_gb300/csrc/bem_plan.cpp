@@ -491,7 +491,7 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         const size_t nj = b.host_jobs.size();
         if ((e = plan_upload(p, &b.jobs, b.host_jobs)) != cudaSuccess ||
             (e = plan_alloc(p, &b.job_total, nj)) != cudaSuccess ||
-            (e = plan_alloc(p, &b.job_end, nj)) != cudaSuccess) {
+            (e = plan_alloc(p, &b.job_end, nj + 1)) != cudaSuccess) {   // + tile counter
             plan_free(p);
             return api_cuda_fail(ctx, e, "plan upload");
         }
