@@ -230,9 +230,10 @@ cudaError_t launch_build_supports(const MeshView &m, const int32_t *ptr, const i
 
 size_t p1_smem_bytes(bool cplx, bool mixed, bool fused)
 {
+    // header, pair results of one chunk, staging sums (one or two results each)
     return ((sizeof(P1Smem) + 15) & ~size_t(15)) +
-           (size_t)p1_cap(mixed, fused) * 9 * (mixed ? sizeof(float) : sizeof(double)) *
-               (cplx || fused ? 2 : 1);
+           ((size_t)p1_cap(mixed, fused) * 9 + (size_t)p1_chunk_rows(mixed, fused) * kP1StageLd * 3) *
+               (mixed ? sizeof(float) : sizeof(double)) * (cplx || fused ? 2 : 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -1140,8 +1140,9 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
 // per-run support records (plans) or are collected by the tile itself (single
 // calls; same function, same result); the 3x3 local matrices of all pairs
 // Ta x Tb are computed chunk by chunk (one thread per pair) into shared memory
-// and gathered by the owner thread of each entry in a fixed order
-// (deterministic sums).
+// and gathered in two fixed-order stages (deterministic sums): per (row
+// triangle, column vertex) over the column's support, then by the owner
+// thread of each entry over its row's support.
 // ---------------------------------------------------------------------------
 // pairs per chunk: float results (36 KB per chunk) leave room for four CTAs
 // per SM; double results stay at 512 pairs so that complex chunks fit too
@@ -1149,6 +1150,14 @@ __host__ __device__ constexpr int p1_cap(bool mixed, bool fused = false)
 {
     return mixed && !fused ? 1024 : 512;   // fused: two float results per pair, same bytes
 }
+// Row triangles per chunk at most: the gather first sums each (row triangle,
+// column vertex) over the column's support into a staging array of this many
+// rows x (kTile + 1) columns x 3 local test indices (6.3 KB per result).
+__host__ __device__ constexpr int p1_chunk_rows(bool mixed, bool fused = false)
+{
+    return mixed && !fused ? 16 : 8;
+}
+constexpr int kP1StageLd = kTile + 1;   // padded column stride of the staging array
 constexpr int kP1MaxTri = kTile * kMaxDegP1;
 
 struct P1Smem {
@@ -1288,11 +1297,15 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
     constexpr int NE = kTile * kTile / NT;     // entries owned per thread
     constexpr int EW = NT / 32;                // column stride of owned entries
     constexpr int CAP = p1_cap(MIXED, FUSED);
+    constexpr int CR = p1_chunk_rows(MIXED, FUSED);
+    constexpr int TN = CR * kP1StageLd * 3;    // staging values per result
     // pair results: double in the FP64 form, float in the mixed form
     using Val = typename std::conditional<MIXED, float, double>::type;
     P1Smem &S = *reinterpret_cast<P1Smem *>(smem_raw);
     Val *buf_r = reinterpret_cast<Val *>(smem_raw + ((sizeof(P1Smem) + 15) & ~size_t(15)));
     Val *buf_i = buf_r + CAP * 9;
+    Val *stg_r = buf_r + CAP * 9 * (TWO ? 2 : 1);
+    Val *stg_i = stg_r + TN;
     const int tid = threadIdx.x;
     {
         const BlockInfo bi = block_info(L, prefix, tile, status);
@@ -1342,7 +1355,7 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
             nta = S.nta;
             ntb = S.ntb;
         }
-        const int ia_step = max(1, CAP / max(ntb, 1));
+        const int ia_step = max(1, min(CR, CAP / max(ntb, 1)));
         // cmpr, cmpi: Kahan compensations (mixed form)
         Val accr[NE], acci[NE], cmpr[NE], cmpi[NE];
 #pragma unroll
@@ -1414,6 +1427,36 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
                 }
             }
             __syncthreads();
+            // gather, stage 1: per (row triangle a of the chunk, column vertex
+            // j) the sums over the triangles b of j's support, for the three
+            // local indices of a (consecutive threads take the row triangles
+            // of one column, so they walk the same support list)
+            const int na = ia1 - ia0;
+            for (int it = tid; it < na * tc; it += NT) {
+                const int al = it % na, jc = it / na;
+                Val sr[3] = {0, 0, 0}, si[3] = {0, 0, 0};
+                const int rowbase = al * ntb;
+                const int nv = S.cl_n[jc];
+                for (int v = 0; v < nv; ++v) {
+                    const int key = S.cl[v][jc];
+                    const int q = (rowbase + (key >> 2)) * 9 + (key & 3);
+#pragma unroll
+                    for (int la = 0; la < 3; ++la) {
+                        sr[la] += buf_r[q + la * 3];
+                        if (TWO) si[la] += buf_i[q + la * 3];
+                    }
+                }
+                const int o = (al * kP1StageLd + jc) * 3;
+#pragma unroll
+                for (int la = 0; la < 3; ++la) {
+                    stg_r[o + la] = sr[la];
+                    if (TWO) stg_i[o + la] = si[la];
+                }
+            }
+            __syncthreads();
+            // stage 2: each entry's owner adds the staged sums of its row
+            // vertex's support triangles in this chunk (the next run of its
+            // slot-sorted list), compensated in the float forms
             const int u_beg = u_end;
             while (u_end < nrl && (S.rl[u_end][er] >> 2) < ia1) ++u_end;
 #pragma unroll
@@ -1421,27 +1464,23 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
                 const int ec = (tid >> 5) + EW * e;
                 if (er < tr && ec < tc) {
                     for (int u = u_beg; u < u_end; ++u) {
-                        const int ia = S.rl[u][er] >> 2, la = S.rl[u][er] & 3;
-                        const int rowbase = (ia - ia0) * ntb;
-                        for (int v = 0; v < S.cl_n[ec]; ++v) {
-                            const int ib = S.cl[v][ec] >> 2, lb = S.cl[v][ec] & 3;
-                            const int q = (rowbase + ib) * 9 + la * 3 + lb;
-                            if (MIXED) {
-                                const Val y = buf_r[q] - cmpr[e];
-                                const Val t = accr[e] + y;
-                                cmpr[e] = (t - accr[e]) - y;
-                                accr[e] = t;
-                                if (FUSED) {
-                                    const Val y2 = buf_i[q] - cmpi[e];
-                                    const Val t2 = acci[e] + y2;
-                                    cmpi[e] = (t2 - acci[e]) - y2;
-                                    acci[e] = t2;
-                                }
-                            } else {
-                                accr[e] += buf_r[q];
+                        const int key = S.rl[u][er];
+                        const int q = (((key >> 2) - ia0) * kP1StageLd + ec) * 3 + (key & 3);
+                        if (MIXED) {
+                            const Val y = stg_r[q] - cmpr[e];
+                            const Val t = accr[e] + y;
+                            cmpr[e] = (t - accr[e]) - y;
+                            accr[e] = t;
+                            if (FUSED) {
+                                const Val y2 = stg_i[q] - cmpi[e];
+                                const Val t2 = acci[e] + y2;
+                                cmpi[e] = (t2 - acci[e]) - y2;
+                                acci[e] = t2;
                             }
-                            if (CPLX) acci[e] += buf_i[q];
+                        } else {
+                            accr[e] += stg_r[q];
                         }
+                        if (CPLX) acci[e] += stg_i[q];
                     }
                 }
             }
