@@ -46,7 +46,7 @@ __device__ __forceinline__ float coupling_pair(const TriF &A, const TriF &B, int
         const float xx = fmaf(s, A.e1[0], fmaf(t, A.e2[0], d0[0]));
         const float xy = fmaf(s, A.e1[1], fmaf(t, A.e2[1], d0[1]));
         const float xz = fmaf(s, A.e1[2], fmaf(t, A.e2[2], d0[2]));
-        const float dn = KIND == BEM_LAPLACE_DLP ? height_at(H, s, t) : 0.0f;
+        const float dn = KIND == BEM_LAPLACE_DLP ? height_at_far(H, s, t) : 0.0f;
         float inner = 0.0f;
 #pragma unroll
         for (int j = 0; j < NP; ++j)
@@ -78,7 +78,7 @@ __device__ __forceinline__ void coupling_pair2(const TriF &A, const TriF &B, int
         const float xx = fmaf(s, A.e1[0], fmaf(t, A.e2[0], d0[0]));
         const float xy = fmaf(s, A.e1[1], fmaf(t, A.e2[1], d0[1]));
         const float xz = fmaf(s, A.e1[2], fmaf(t, A.e2[2], d0[2]));
-        const float dn = height_at(H, s, t);
+        const float dn = height_at_far(H, s, t);
         float in_s = 0.0f, in_d = 0.0f;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {

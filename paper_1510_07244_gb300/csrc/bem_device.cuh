@@ -170,6 +170,19 @@ __device__ __forceinline__ float height_at(const Height &H, float s, float t)
     return b + lo;
 }
 
+// The same height in plain float from the rounded coefficients, for pairs of
+// an admissible (far-field) block: the coefficients keep the precision of the
+// double-float set-up (tiny for nearly coplanar triangles), and the rounding
+// of the evaluation, a few ulps of |h0| + |h10| + |h21|, stays within a few
+// ulps of the largest term of the pair's sum because the triangles lie at
+// least a multiple of their size apart, so 1/r^3 varies by a bounded factor
+// over the pair.  Near-field pairs, where the test triangle can cross the
+// trial plane close to the trial triangle, use height_at.
+__device__ __forceinline__ float height_at_far(const Height &H, float s, float t)
+{
+    return fmaf(s, H.h10, fmaf(t, H.h21, H.h0));
+}
+
 // Sum over the warp of the unevaluated pairs hi + lo of every lane: TwoSum at
 // each butterfly level keeps the rounding error of the float additions.
 __device__ __forceinline__ void warp_sum2f(float &hi, float &lo)
