@@ -836,58 +836,75 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
     const bool zero = KIND == BEM_LAPLACE_DLP && CAS == kIdentical;
     const float *X1 = rule, *X2 = rule + np, *Y1 = rule + 2 * np, *Y2 = rule + 3 * np,
                 *W = rule + 4 * np, *D1 = rule + 5 * np, *D2 = rule + 6 * np;
-    for (int p = lane; p < np && !zero; p += 32) {
-        const float x1 = __ldg(X1 + p), x2 = __ldg(X2 + p), y1 = __ldg(Y1 + p),
-                    y2 = __ldg(Y2 + p), w = __ldg(W + p);
-        float dx, dy, dz, dn = 0.0f;
-        if (CAS == kVertex) {
-            dx = fmaf(x1, e1a[0], fmaf(x2, e2a[0], -fmaf(y1, e1b[0], y2 * e2b[0])));
-            dy = fmaf(x1, e1a[1], fmaf(x2, e2a[1], -fmaf(y1, e1b[1], y2 * e2b[1])));
-            dz = fmaf(x1, e1a[2], fmaf(x2, e2a[2], -fmaf(y1, e1b[2], y2 * e2b[2])));
-            if (KIND == BEM_LAPLACE_DLP) dn = height_at(H, x1, x2);
-        } else if (CAS == kEdge) {
-            const float d1 = __ldg(D1 + p);
-            dx = fmaf(d1, e1a[0], fmaf(x2, e2a[0], -y2 * e2b[0]));
-            dy = fmaf(d1, e1a[1], fmaf(x2, e2a[1], -y2 * e2b[1]));
-            dz = fmaf(d1, e1a[2], fmaf(x2, e2a[2], -y2 * e2b[2]));
-            if (KIND == BEM_LAPLACE_DLP) dn = x2 * h2;
-        } else {
-            const float d1 = __ldg(D1 + p), d2 = __ldg(D2 + p);
-            dx = fmaf(d1, e1a[0], d2 * e2a[0]);
-            dy = fmaf(d1, e1a[1], d2 * e2a[1]);
-            dz = fmaf(d1, e1a[2], d2 * e2a[2]);
-        }
-        float wk, wki = 0.0f;
-        if (CPLX) {
-            // the pair touches: kappa r stays below kappa times two diameters
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ri = rsqrt_fast(r2);
-            float sn, cs;
-            sincosf(kappa * (r2 * ri), &sn, &cs);
-            wk = w * cs * ri;
-            wki = w * sn * ri;
-        } else {
-            wk = w * kvalf<KIND>(dx, dy, dz, dn);
-        }
-        const float mx[3] = {1.0f, x1, x2}, my[3] = {1.0f, y1, y2};
+    // Each lane takes its points in blocks of KB (stride 32): the terms of a
+    // block are added plainly (error at most KB - 1 ulps of the block's
+    // magnitudes) and each block sum enters the lane's sums with Kahan
+    // compensation, which keeps the compensated accuracy at a quarter of the
+    // additions.
+    constexpr int KB = 4;
+    for (int p0 = lane; p0 < np && !zero; p0 += 32 * KB) {
+        float br[NACC], bi[NACC];
 #pragma unroll
-        for (int i = 0; i < (BASIS == BEM_P0 ? 1 : 3); ++i)
+        for (int k = 0; k < NACC; ++k) br[k] = bi[k] = 0.0f;
 #pragma unroll
-            for (int j = 0; j < (BASIS == BEM_P0 ? 1 : 3); ++j) {
-                const int k = BASIS == BEM_P0 ? 0 : i * 3 + j;
-                const float f = BASIS == BEM_P0 ? wk : wk * mx[i] * my[j];
-                const float yv = f - cmp[k];
-                const float t = acc[k] + yv;
-                cmp[k] = (t - acc[k]) - yv;
-                acc[k] = t;
-                if (CPLX) {
-                    const float fi = BASIS == BEM_P0 ? wki : wki * mx[i] * my[j];
-                    const float yi = fi - cmpi[k];
-                    const float ti = acci[k] + yi;
-                    cmpi[k] = (ti - acci[k]) - yi;
-                    acci[k] = ti;
-                }
+        for (int u = 0; u < KB; ++u) {
+            const int p = p0 + 32 * u;
+            if (p >= np) break;
+            const float x1 = __ldg(X1 + p), x2 = __ldg(X2 + p), y1 = __ldg(Y1 + p),
+                        y2 = __ldg(Y2 + p), w = __ldg(W + p);
+            float dx, dy, dz, dn = 0.0f;
+            if (CAS == kVertex) {
+                dx = fmaf(x1, e1a[0], fmaf(x2, e2a[0], -fmaf(y1, e1b[0], y2 * e2b[0])));
+                dy = fmaf(x1, e1a[1], fmaf(x2, e2a[1], -fmaf(y1, e1b[1], y2 * e2b[1])));
+                dz = fmaf(x1, e1a[2], fmaf(x2, e2a[2], -fmaf(y1, e1b[2], y2 * e2b[2])));
+                if (KIND == BEM_LAPLACE_DLP) dn = height_at(H, x1, x2);
+            } else if (CAS == kEdge) {
+                const float d1 = __ldg(D1 + p);
+                dx = fmaf(d1, e1a[0], fmaf(x2, e2a[0], -y2 * e2b[0]));
+                dy = fmaf(d1, e1a[1], fmaf(x2, e2a[1], -y2 * e2b[1]));
+                dz = fmaf(d1, e1a[2], fmaf(x2, e2a[2], -y2 * e2b[2]));
+                if (KIND == BEM_LAPLACE_DLP) dn = x2 * h2;
+            } else {
+                const float d1 = __ldg(D1 + p), d2 = __ldg(D2 + p);
+                dx = fmaf(d1, e1a[0], d2 * e2a[0]);
+                dy = fmaf(d1, e1a[1], d2 * e2a[1]);
+                dz = fmaf(d1, e1a[2], d2 * e2a[2]);
             }
+            float wk, wki = 0.0f;
+            if (CPLX) {
+                // the pair touches: kappa r stays below kappa times two diameters
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float ri = rsqrt_fast(r2);
+                float sn, cs;
+                sincosf(kappa * (r2 * ri), &sn, &cs);
+                wk = w * cs * ri;
+                wki = w * sn * ri;
+            } else {
+                wk = w * kvalf<KIND>(dx, dy, dz, dn);
+            }
+            const float mx[3] = {1.0f, x1, x2}, my[3] = {1.0f, y1, y2};
+#pragma unroll
+            for (int i = 0; i < (BASIS == BEM_P0 ? 1 : 3); ++i)
+#pragma unroll
+                for (int j = 0; j < (BASIS == BEM_P0 ? 1 : 3); ++j) {
+                    const int k = BASIS == BEM_P0 ? 0 : i * 3 + j;
+                    br[k] += BASIS == BEM_P0 ? wk : wk * mx[i] * my[j];
+                    if (CPLX) bi[k] += BASIS == BEM_P0 ? wki : wki * mx[i] * my[j];
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) {
+            const float yv = br[k] - cmp[k];
+            const float t = acc[k] + yv;
+            cmp[k] = (t - acc[k]) - yv;
+            acc[k] = t;
+            if (CPLX) {
+                const float yi = bi[k] - cmpi[k];
+                const float ti = acci[k] + yi;
+                cmpi[k] = (ti - acci[k]) - yi;
+                acci[k] = ti;
+            }
+        }
     }
     // lane partial sums with their compensations, reduced as float pairs;
     // the hats are formed in float-float as well, and lane q < 9 converts and
