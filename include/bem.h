@@ -282,6 +282,13 @@ int bem_learned_counts(bem_ctx *ctx, int64_t *counts /* [6] */);
  * records reports BEM_ERR_INVALID_ARG through the status word.
  * Plans run the fixed orders of each job's bem_quad_desc: a job with
  * order_mode BEM_ORDER_LEARNED is rejected with BEM_ERR_UNSUPPORTED.
+ * In the float forms a piecewise-linear Laplace single-layer job and a
+ * double-layer job of the same kind (both near field or both coupling) with
+ * the same mesh, the same block-list pointers and the same regular rule,
+ * order and precision run fused: one launch evaluates both layers and shares
+ * the points, distances and reciprocal square roots (Eq. 1 for both kernels
+ * over the same pairs); the results are unchanged.  The outputs of a plan's
+ * jobs must not overlap.
  * Errors as bem_near_field; BEM_ERR_CUDA if graph capture fails. */
 typedef struct bem_plan bem_plan;
 #define BEM_PLAN_GRAPH    1
