@@ -232,6 +232,8 @@ def pair_counts(w):
         size = np.asarray(CT.sum(axis=1)).ravel()
         touch = (CT @ TT @ CT.T).tocsr()
         t, s = bs.blk_row, bs.blk_col
+        if len(t) == 0:
+            return 0.0, 0.0
         total = float(np.sum(size[t] * size[s]))
         tp = float(np.asarray(touch[t, s]).ravel().sum())
         return total - tp, tp

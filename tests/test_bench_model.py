@@ -1,0 +1,65 @@
+"""Host-side accounting of the benchmark: the algorithmic operation counts
+per kernel (fused launches count the work both layers share once) and the
+committed DRAM-traffic figures it reports."""
+import pytest
+
+import bench
+import synth
+
+
+@pytest.fixture(scope="module")
+def small_c2():
+    w = synth.workloads.config2(levels=3)
+    counts = bench.pair_counts(w)
+    assert counts["near_regular_pairs"] > 0 and counts["far_entry_pairs"] > 0
+    return w, counts
+
+
+STATS = {"n_vertex": 0, "n_edge": 0, "n_identical": 0}
+
+
+def test_fused_launches_count_shared_work_once(small_c2):
+    w, counts = small_c2
+    npts, npa = 81, 9
+    slp = bench.flops_per_point("laplace_slp", "p1", npa)
+    dlp = bench.flops_per_point("laplace_dlp", "p1", npa)
+    f64 = bench.kernel_flops(w, counts, STATS, "fp64")
+    mix = bench.kernel_flops(w, counts, STATS, "mixed_full")
+    reg_all = counts["near_regular_pairs"] + counts["far_regular_pairs"]
+    # FP64 form: one tile engine for near and coupling blocks, layers separate
+    assert set(f64) >= {"block_p1"} and "coupling_p1" not in f64
+    assert f64["block_p1"][0] == pytest.approx(reg_all * npts * (slp + dlp))
+    assert f64["block_p1"][1] == "fp64"
+    # float forms: near field in the fused tile engine, coupling blocks in the
+    # fused coupling engine; the difference, r^2 and rsqrt (9) count once
+    assert mix["block_p1"][0] == pytest.approx(
+        counts["near_regular_pairs"] * npts * (slp + dlp - 9.0))
+    p0s = bench.flops_per_point("laplace_slp", "p0", npa)
+    p0d = bench.flops_per_point("laplace_dlp", "p0", npa)
+    want = counts["far_entry_pairs"] * npts * (p0s + p0d + 20.0 / npa - 9.0 - 6.0 / npa)
+    assert mix["coupling_p1"][0] == pytest.approx(want)
+    assert mix["coupling_p1"][1] == mix["block_p1"][1] == "fp32"
+    assert mix["block_p1"][2] == pytest.approx(bench.PEAK_FP32)
+
+
+def test_single_operator_is_not_fused(small_c2):
+    w, counts = small_c2
+    w1 = synth.workloads.Workload(**{**w.__dict__,
+                                     "operators": [o for o in w.operators
+                                                   if o.kernel == "laplace_dlp"]})
+    mix = bench.kernel_flops(w1, counts, STATS, "mixed_full")
+    dlp = bench.flops_per_point("laplace_dlp", "p1", 9)
+    assert mix["block_p1"][0] == pytest.approx(counts["near_regular_pairs"] * 81 * dlp)
+
+
+def test_empty_block_set_counts_nothing():
+    w = synth.workloads.config2(levels=2)    # 320 triangles: no admissible blocks
+    assert len(w.far.blk_row) == 0
+    counts = bench.pair_counts(w)
+    assert counts["far_regular_pairs"] == counts["far_entry_pairs"] == 0
+
+
+def test_committed_traffic_figures():
+    t = bench.profiled_traffic("coupling_p1")
+    assert isinstance(t, int) and 1_000_000 < t < 100_000_000
+    assert bench.profiled_traffic("no_such_kernel") is None
