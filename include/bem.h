@@ -316,6 +316,28 @@ int bem_plan_info(bem_ctx *ctx, bem_plan *plan, int32_t *n_touch_launches,
  * Whole blocks, so every output block has one owner.  Needs no device. */
 int bem_shard_blocks(const int64_t *cost, int64_t n_blocks, int32_t n_shards, int64_t *bounds);
 
+/* ---- touching pairs (host) ---------------------------------------------------
+ * The case test of bem_mesh_upload (Section 2.2: pairs of triangles that share
+ * one, two or three vertex indices are common-vertex, common-edge and
+ * identical pairs; Section 3 / Algorithm 3 sorts pairs by this test), run on
+ * the host without a device.  tris: HOST, nt x 3 vertex indices in [0, nv),
+ * distinct within each triangle.  Lists every ordered pair (a, b) of triangles
+ * sharing at least one vertex index, a == b included, ascending in (a, b):
+ * src[k] = a, dst[k] = b, cas[k] = number of shared indices (1 vertex, 2 edge,
+ * 3 identical) and ord[6k .. 6k+5] = the vertex orders the Sauter-Schwab maps
+ * use, a's local indices at positions 0, 1, 2 followed by b's: the shared
+ * vertex first; a shared edge as positions 0 -> 1 in the direction it has in
+ * a, with b's same two vertices in the same order; identical pairs with b in
+ * a's order; the remaining vertices in cyclic order.  *n_pairs receives the
+ * number of pairs and min(cap, *n_pairs) are written (cap = 0 sizes the
+ * arrays; they may then be NULL).  All arrays are HOST memory owned by the
+ * caller.  Errors: BEM_ERR_INVALID_ARG (NULL pointers, an index out of
+ * range), BEM_ERR_DEGENERATE (a triangle with a repeated index, two triangles
+ * with the same three indices), BEM_ERR_UNSUPPORTED (beyond 32-bit indices).
+ * Needs no context and no device. */
+int bem_touching_pairs(const int32_t *tris, int64_t nt, int64_t nv, int32_t *src, int32_t *dst,
+                       int32_t *cas, int32_t *ord, int64_t cap, int64_t *n_pairs);
+
 /* ---- GCA pivots (host) -------------------------------------------------------
  * Pivot rows t~ of every cluster for the H^2 coupling matrices G|t~ x s~
  * (Sections 2.3-2.4).  For a cluster t: B_t = bounding box of the supports

@@ -428,6 +428,19 @@ int orc_classify(const int32_t *ta, const int32_t *tb)
     return classify(ta, tb, oa, ob);
 }
 
+/* Case and the local vertex orders of a triangle pair (exported for tests):
+ * ord[0..2] = a's order, ord[3..5] = b's. */
+int orc_classify_orders(const int32_t *ta, const int32_t *tb, int32_t *ord)
+{
+    int oa[3], ob[3];
+    const int c = classify(ta, tb, oa, ob);
+    for (int k = 0; k < 3; ++k) {
+        ord[k] = oa[k];
+        ord[3 + k] = ob[k];
+    }
+    return c;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Mesh with vertex -> triangle adjacency                                    */
 /* ------------------------------------------------------------------------ */

@@ -49,6 +49,7 @@ def _get():
             lib.orc_rule_points.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             _d, _d, _d, _d, _d, ctypes.c_int]
             lib.orc_classify.argtypes = [_i32, _i32]
+            lib.orc_classify_orders.argtypes = [_i32, _i32, _i32]
             lib.orc_entries.argtypes = [_d, ctypes.c_int64, _i32, ctypes.c_int64,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -101,6 +102,15 @@ def classify(ta, tb) -> str:
     b = np.ascontiguousarray(tb, np.int32)
     c = _get().orc_classify(_p(a, _i32), _p(b, _i32))
     return {v: k for k, v in CASES.items()}[c]
+
+
+def classify_orders(ta, tb):
+    """(case, a's vertex order, b's vertex order) of a triangle pair."""
+    a = np.ascontiguousarray(ta, np.int32)
+    b = np.ascontiguousarray(tb, np.int32)
+    o = np.zeros(6, np.int32)
+    c = _get().orc_classify_orders(_p(a, _i32), _p(b, _i32), _p(o, _i32))
+    return {v: k for k, v in CASES.items()}[c], o[:3].copy(), o[3:].copy()
 
 
 def _mesh(verts, tris):

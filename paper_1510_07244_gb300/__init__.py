@@ -8,9 +8,11 @@ this package only marshals arguments to it (``_binding``) and, in
 from ._binding import (Context, BlockJob, BemError, kernel_desc, quad_desc, load, LIB_PATH,
                        EXPORTS, KERNELS, BASES, RULES, bem_rule_points, PLAN_GRAPH,
                        PLAN_AUTOTUNE, PLAN_PROFILE, ORDER_CLASSES,
-                       ORDER_CLASS_POINTS, bem_shard_blocks, bem_gca_pivots)
+                       ORDER_CLASS_POINTS, bem_shard_blocks, bem_gca_pivots,
+                       bem_touching_pairs)
 
 __all__ = ["Context", "BlockJob", "BemError", "kernel_desc", "quad_desc", "load", "LIB_PATH",
            "EXPORTS", "KERNELS", "BASES", "RULES", "bem_rule_points",
            "PLAN_GRAPH", "PLAN_AUTOTUNE", "PLAN_PROFILE", "ORDER_CLASSES",
-           "ORDER_CLASS_POINTS", "bem_shard_blocks", "bem_gca_pivots"]
+           "ORDER_CLASS_POINTS", "bem_shard_blocks", "bem_gca_pivots",
+           "bem_touching_pairs"]

@@ -31,7 +31,7 @@ EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_
            "bem_pivot_entries_absolute", "bem_mlp_create", "bem_mlp_destroy", "bem_mlp_num_params",
            "bem_mlp_set_params", "bem_mlp_get_params", "bem_mlp_gradients", "bem_mlp_train_step",
            "bem_mlp_infer", "bem_pair_features", "bem_set_order_model", "bem_learned_counts",
-           "bem_shard_blocks", "bem_gca_pivots"]
+           "bem_shard_blocks", "bem_gca_pivots", "bem_touching_pairs"]
 ORDER_CLASSES = [("duffy", 2), ("tri7", 1), ("duffy", 4), ("duffy", 5), ("duffy", 6), ("duffy", 8)]
 ORDER_CLASS_POINTS = [16, 49, 256, 625, 1296, 4096]
 PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE = 1, 2, 4
@@ -122,6 +122,8 @@ def load():
                                       ctypes.c_int64, _vp]
     lib.bem_set_order_model.argtypes = [_vp, _vp, ctypes.c_float]
     lib.bem_shard_blocks.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, _vp]
+    lib.bem_touching_pairs.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp,
+                                       ctypes.c_int64, P(ctypes.c_int64)]
     lib.bem_gca_pivots.argtypes = [_vp, ctypes.c_int64, _vp, ctypes.c_int64, ctypes.c_int32,
                                    ctypes.c_double, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
@@ -171,6 +173,28 @@ def bem_shard_blocks(cost, n_shards: int) -> np.ndarray:
     if rc != BEM_OK:
         raise BemError(rc, "bad shard arguments")
     return bounds
+
+
+def bem_touching_pairs(tris, nv: int):
+    """Touching triangle pairs of a mesh (host only), ascending in (a, b):
+    dict of src, dst (int32), case (1 vertex, 2 edge, 3 identical) and ord
+    (n x 6: a's canonical vertex order, then b's)."""
+    t = np.ascontiguousarray(tris, np.int32)
+    nt = t.shape[0]
+    n = ctypes.c_int64(0)
+    lib = load()
+    rc = lib.bem_touching_pairs(t.ctypes.data_as(_vp), nt, int(nv), None, None, None, None, 0,
+                                ctypes.byref(n))
+    if rc != BEM_OK:
+        raise BemError(rc, "bem_touching_pairs: bad mesh")
+    src, dst, cas = (np.zeros(n.value, np.int32) for _ in range(3))
+    ord_ = np.zeros((n.value, 6), np.int32)
+    rc = lib.bem_touching_pairs(t.ctypes.data_as(_vp), nt, int(nv), src.ctypes.data_as(_vp),
+                                dst.ctypes.data_as(_vp), cas.ctypes.data_as(_vp),
+                                ord_.ctypes.data_as(_vp), n.value, ctypes.byref(n))
+    if rc != BEM_OK:
+        raise BemError(rc, "bem_touching_pairs: bad mesh")
+    return {"src": src, "dst": dst, "case": cas, "ord": ord_}
 
 
 def bem_gca_pivots(verts, tris, basis: str, cl_ptr, cl_idx, cl_son, kappa: float = 0.0,

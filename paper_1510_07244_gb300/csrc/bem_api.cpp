@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "bem_internal.h"
+#include "bem_mesh_plan.h"
 
 using namespace bem;
 
@@ -80,58 +81,6 @@ void free_mesh(Mesh *m)
 {
     for (void *p : m->allocs) cudaFree(p);
     delete m;
-}
-
-int perm_code(const int o[3])
-{
-    for (int c = 0; c < 6; ++c)
-        if (kPerm[c][0] == o[0] && kPerm[c][1] == o[1] && kPerm[c][2] == o[2]) return c;
-    return -1;
-}
-
-// Case of the pair (A, B) by shared vertex indices, and the vertex orders the
-// Sauter-Schwab maps expect (shared vertex first; shared edge as local v0->v1
-// in the direction it has in A; identical: B follows A).  These conventions
-// fix which points the rules evaluate, so results are reproducible bit for bit
-// only with the same orders.
-int classify_pair(const int A[3], const int B[3], int &code_a, int &code_b)
-{
-    int ia[3], ib[3], ns = 0;
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            if (A[i] == B[j]) {
-                ia[ns] = i;
-                ib[ns] = j;
-                ++ns;
-            }
-    int oa[3] = {0, 1, 2}, ob[3] = {0, 1, 2};
-    int cas = kRegular;
-    if (ns == 3) {
-        cas = kIdentical;
-        for (int k = 0; k < 3; ++k)
-            for (int j = 0; j < 3; ++j)
-                if (B[j] == A[k]) ob[k] = j;
-    } else if (ns == 2) {
-        cas = kEdge;
-        // the shared position of A whose cyclic successor is the other shared one
-        const int f = ((ia[0] + 1) % 3 == ia[1]) ? ia[0] : ia[1];
-        oa[0] = f;
-        oa[1] = (f + 1) % 3;
-        oa[2] = (f + 2) % 3;
-        for (int k = 0; k < 2; ++k)
-            for (int j = 0; j < 3; ++j)
-                if (B[j] == A[oa[k]]) ob[k] = j;
-        ob[2] = 3 - ob[0] - ob[1];
-    } else if (ns == 1) {
-        cas = kVertex;
-        for (int k = 0; k < 3; ++k) {
-            oa[k] = (ia[0] + k) % 3;
-            ob[k] = (ib[0] + k) % 3;
-        }
-    }
-    code_a = perm_code(oa);
-    code_b = perm_code(ob);
-    return cas;
 }
 
 Mesh *get_mesh(bem_ctx *ctx, int id)
@@ -494,45 +443,19 @@ int bem_mesh_upload(bem_ctx *ctx, const double *verts, int64_t nv, const int32_t
         f[30] = (float)g[12];
     }
 
-    // vertex -> triangle adjacency (ascending triangle ids)
-    std::vector<int> vt_ptr((size_t)nv + 1, 0), vt_tri((size_t)(3 * nt));
-    for (int64_t k = 0; k < 3 * nt; ++k) vt_ptr[tris[k] + 1]++;
-    for (int64_t v = 0; v < nv; ++v) vt_ptr[v + 1] += vt_ptr[v];
+    // vertex -> triangle adjacency and the touching pairs of every triangle
+    // with case and vertex orders (a2, mesh part; bem_mesh_plan.cpp)
+    TouchPlan P;
     {
-        std::vector<int> fill(vt_ptr.begin(), vt_ptr.end() - 1);
-        for (int64_t t = 0; t < nt; ++t)
-            for (int k = 0; k < 3; ++k) vt_tri[fill[tris[3 * t + k]]++] = (int)t;
+        const char *err = nullptr;
+        const int rc = plan_touching(tris, nt, nv, P, &err);
+        if (rc != BEM_OK) return fail(ctx, rc, err ? err : "touching pairs");
     }
-    int maxdeg = 0;
-    for (int64_t v = 0; v < nv; ++v) maxdeg = std::max(maxdeg, vt_ptr[v + 1] - vt_ptr[v]);
-
-    // a2 (mesh part): touching neighbours of each triangle, case and vertex orders
-    std::vector<int> nb_ptr((size_t)nt + 1, 0), nb_tri, nb_src;
-    std::vector<unsigned char> nb_case, nb_perm;
-    std::vector<int> lists[4];
-    std::vector<int> cand;
-    for (int64_t a = 0; a < nt; ++a) {
-        cand.clear();
-        for (int k = 0; k < 3; ++k) {
-            const int v = tris[3 * a + k];
-            for (int u = vt_ptr[v]; u < vt_ptr[v + 1]; ++u) cand.push_back(vt_tri[u]);
-        }
-        std::sort(cand.begin(), cand.end());
-        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-        for (int b : cand) {
-            int ca, cb;
-            const int cas = classify_pair(tris + 3 * a, tris + 3 * (int64_t)b, ca, cb);
-            if (cas == kRegular) continue;
-            if (cas == kIdentical && b != a)
-                return fail(ctx, BEM_ERR_DEGENERATE, "two triangles with the same vertices");
-            lists[cas].push_back((int)nb_tri.size());
-            nb_tri.push_back(b);
-            nb_src.push_back((int)a);
-            nb_case.push_back((unsigned char)cas);
-            nb_perm.push_back((unsigned char)(ca * 6 + cb));
-        }
-        nb_ptr[a + 1] = (int)nb_tri.size();
-    }
+    const std::vector<int> &vt_ptr = P.vt_ptr, &vt_tri = P.vt_tri;
+    const std::vector<int> &nb_ptr = P.nb_ptr, &nb_tri = P.nb_tri, &nb_src = P.nb_src;
+    const std::vector<unsigned char> &nb_case = P.nb_case, &nb_perm = P.nb_perm;
+    const int maxdeg = P.maxdeg;
+    std::vector<int> *lists = P.lists;
     // reject coordinates shared by two different vertex indices (such pairs
     // would be treated as disjoint although their triangles touch)
     {
