@@ -29,6 +29,11 @@
  *
  * Everything is evaluated in double precision with plain sums in the nested
  * point order (subdomain, xi, eta1, eta2, eta3).
+ *
+ * It also computes the entries of the Green quadrature matrices A_t of
+ * Section 2.3 (orc_green_entries): integrals of one basis function against
+ * the Green function and its normal derivative at a point off the surface,
+ * with a triangle rule on each support triangle.
  */
 #include <math.h>
 #include <stdint.h>
@@ -700,4 +705,94 @@ int orc_pair(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, i
     mesh_free(&M);
     setup_free(&S);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Green quadrature entries (Section 2.3: the matrices A_t of Green's        */
+/* representation formula).  For basis function i (P0: triangle i; P1: the  */
+/* hat function of vertex i) and a point z with unit normal nz off the      */
+/* surface:                                                                  */
+/*   plus  = int phi_i(x) g(x, z) dx,                                        */
+/*   minus = int phi_i(x) d/dn(z) g(x, z) dx                                 */
+/* with g(x, z) = exp(i kappa r)/(4 pi r), r = |x - z| (kappa = 0: Laplace). */
+/* The normal derivative is taken in z: grad_z r = (z - x)/r and            */
+/* dg/dr = (i kappa r - 1) exp(i kappa r)/(4 pi r^2), so                     */
+/*   nz . grad_z g = (x - z).nz (1 - i kappa r) exp(i kappa r)/(4 pi r^3).   */
+/* Each support triangle is integrated with a triangle rule on D: Radon's   */
+/* 7 points (rule 1) or the Duffy square (s, t) = (xi1, xi1 xi2) with q     */
+/* Gauss points per axis and weight xi1 (rule 0), times sqrt(g).  The       */
+/* sqrt(w_nu) and delta_t scalings of A_t are left to the caller.  plus and  */
+/* minus are complex, interleaved (re, im), one per entry.                   */
+/* ------------------------------------------------------------------------ */
+int orc_green_entries(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                      int basis, double kappa, int rule, int q, const int64_t *idx,
+                      const double *z, const double *nz, int64_t n, double *plus, double *minus)
+{
+    double s[ORC_MAXQ * ORC_MAXQ], t[ORC_MAXQ * ORC_MAXQ], w[ORC_MAXQ * ORC_MAXQ];
+    int np = 0;
+    if (rule == 1) {
+        orc_radon7(s, t, w);
+        np = 7;
+    } else {
+        if (q < 1 || q > ORC_MAXQ) return -1;
+        double g[ORC_MAXQ], gw[ORC_MAXQ];
+        orc_gauss_legendre01(q, g, gw);
+        for (int a = 0; a < q; ++a)
+            for (int b = 0; b < q; ++b) {
+                s[np] = g[a];
+                t[np] = g[a] * g[b];
+                w[np] = gw[a] * gw[b] * g[a];
+                ++np;
+            }
+    }
+    orc_mesh m;
+    mesh_init(&m, verts, nv, tris, nt);
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t e = 0; e < n; ++e) {
+        const int64_t i = idx[e];
+        double pr = 0.0, pi = 0.0, mr = 0.0, mi = 0.0;
+        if ((basis == 0 && (i < 0 || i >= nt)) || (basis == 1 && (i < 0 || i >= nv))) {
+            bad = 1;
+        } else {
+            const int64_t lo = basis == 0 ? i : m.vt_ptr[i];
+            const int64_t hi = basis == 0 ? i + 1 : m.vt_ptr[i + 1];
+            for (int64_t k = lo; k < hi; ++k) {
+                const int64_t T = basis == 0 ? i : m.vt_tri[k];
+                double v[3][3], e1[3], e2[3], c[3];
+                int loc = -1;
+                for (int a = 0; a < 3; ++a) {
+                    const int32_t vi = tris[3 * T + a];
+                    if (basis == 1 && vi == i) loc = a;
+                    for (int d = 0; d < 3; ++d) v[a][d] = verts[3 * (int64_t)vi + d];
+                }
+                sub3(v[1], v[0], e1);
+                sub3(v[2], v[1], e2);
+                cross3(e1, e2, c);
+                const double sg = norm3(c);
+                for (int p = 0; p < np; ++p) {
+                    double x[3], d[3];
+                    affine_map(v, s[p], t[p], x);
+                    sub3(x, &z[3 * e], d);
+                    const double r = norm3(d);
+                    const double phi = basis == 0 ? 1.0 : lambda_ref(loc, s[p], t[p]);
+                    const double f = w[p] * sg * phi / (4.0 * ORC_PI * r);
+                    const double dn = (d[0] * nz[3 * e] + d[1] * nz[3 * e + 1] +
+                                       d[2] * nz[3 * e + 2]) / (r * r);
+                    const double cr = cos(kappa * r), ci = sin(kappa * r);
+                    /* plus: f exp(i kappa r); minus: f dn (1 - i kappa r) exp(i kappa r) */
+                    pr += f * cr;
+                    pi += f * ci;
+                    mr += f * dn * (cr + kappa * r * ci);
+                    mi += f * dn * (ci - kappa * r * cr);
+                }
+            }
+        }
+        plus[2 * e] = pr;
+        plus[2 * e + 1] = pi;
+        minus[2 * e] = mr;
+        minus[2 * e + 1] = mi;
+    }
+    mesh_free(&m);
+    return bad ? -1 : 0;
 }

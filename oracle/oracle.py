@@ -50,6 +50,10 @@ def _get():
                                             _d, _d, _d, _d, _d, ctypes.c_int]
             lib.orc_classify.argtypes = [_i32, _i32]
             lib.orc_classify_orders.argtypes = [_i32, _i32, _i32]
+            lib.orc_green_entries.argtypes = [_d, ctypes.c_int64, _i32, ctypes.c_int64,
+                                              ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                              ctypes.c_int, _i64, _d, _d, ctypes.c_int64,
+                                              _d, _d]
             lib.orc_entries.argtypes = [_d, ctypes.c_int64, _i32, ctypes.c_int64,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -111,6 +115,28 @@ def classify_orders(ta, tb):
     o = np.zeros(6, np.int32)
     c = _get().orc_classify_orders(_p(a, _i32), _p(b, _i32), _p(o, _i32))
     return {v: k for k, v in CASES.items()}[c], o[:3].copy(), o[3:].copy()
+
+
+def green_entries(verts, tris, basis, idx, z, nz, kappa=0.0, rule="tri7", q=0):
+    """Green quadrature entries (plus, minus), complex arrays: for each k,
+    int phi_idx[k] g(x, z_k) dx and int phi_idx[k] d/dn(z_k) g(x, z_k) dx
+    (nz_k the unit normal at z_k), with Radon's 7-point rule ("tri7") or a
+    Duffy square of q Gauss points per axis ("duffy") on every support
+    triangle."""
+    v, t = _mesh(verts, tris)
+    i = np.ascontiguousarray(idx, np.int64)
+    zz = np.ascontiguousarray(z, np.float64).reshape(-1, 3)
+    nn = np.ascontiguousarray(nz, np.float64).reshape(-1, 3)
+    n = len(i)
+    assert zz.shape[0] == n and nn.shape[0] == n
+    plus = np.zeros(2 * n)
+    minus = np.zeros(2 * n)
+    rc = _get().orc_green_entries(_p(v, _d), len(v), _p(t, _i32), len(t), BASES[basis],
+                                  float(kappa), RULES[rule], int(q), _p(i, _i64), _p(zz, _d),
+                                  _p(nn, _d), n, _p(plus, _d), _p(minus, _d))
+    if rc != 0:
+        raise ValueError("green_entries: bad index or order")
+    return plus[0::2] + 1j * plus[1::2], minus[0::2] + 1j * minus[1::2]
 
 
 def _mesh(verts, tris):
