@@ -373,6 +373,63 @@ int bem_gca_pivots(const double *verts, int64_t nv, const int32_t *tris, int64_t
                    int32_t max_rank, int32_t n_threads, int32_t *piv_ptr, int32_t *piv_idx,
                    int64_t cap);
 
+/* ---- Green quadrature matrices (device) --------------------------------------
+ * The matrices A_t = (A_t+, A_t-) of Green's representation formula that the
+ * cross approximation above works on (Section 2.3), for a list of clusters in
+ * one launch.  Cluster c has rows r_k = row_idx[row_ptr[c] + k], k < n_c
+ * (n_c = row_ptr[c+1] - row_ptr[c]; P0: triangles, P1: vertices of the mesh)
+ * and points z_nu with unit normals n_nu, nu = pt_ptr[c] + l, l < m_c
+ * (m_c = pt_ptr[c+1] - pt_ptr[c]).  Its block, column-major with leading
+ * dimension n_c, n_c x 2 m_c, at element offset out_off[c] of `out`, holds
+ *   column l        A_t+[k, l] = sp_nu int phi_{r_k}(x) g(x, z_nu) dx
+ *   column m_c + l  A_t-[k, l] = sm_nu int phi_{r_k}(x) d/dn(z_nu) g(x, z_nu) dx
+ * with g(x, z) = exp(i kappa r)/(4 pi r), r = |x - z| (kappa = 0 for
+ * BEM_LAPLACE_SLP and BEM_LAPLACE_DLP, which share Green's function) and
+ * n . grad_z g = (x - z).n (1 - i kappa r) exp(i kappa r)/(4 pi r^3).  The GCA
+ * takes sp = sqrt(w_nu), sm = sqrt(w_nu) delta_t (quadrature weights w_nu on
+ * the boundary of omega_t, delta_t = diam of the cluster's box).  Every
+ * support triangle is integrated in FP64 by a rule on the reference triangle
+ * (Section 2.2): BEM_RULE_TRI7 (Radon's 7 points) or BEM_RULE_DUFFY with q in
+ * [1, 5] Gauss points per axis of the Duffy square.  The integrands are smooth
+ * only for points away from the supports (the GCA keeps them delta_t / 2 away);
+ * this is not checked, and a point on a support gives non-finite entries.
+ *   All pointers are DEVICE arrays owned by the caller:
+ *     row_ptr, pt_ptr  int32[n_clusters + 1], non-decreasing
+ *     row_idx          int32[n_row_idx]
+ *     z, nz            double[n_points][3]
+ *     sp, sm           double[n_points], or NULL for a factor of 1
+ *     out_off          int64[n_clusters]
+ *     out              double[out_len] (Laplace) or 16-byte aligned (re, im)
+ *                      double pairs [out_len] (Helmholtz); blocks must not
+ *                      overlap.
+ * Asynchronous on the context's stream.  Host errors: BEM_ERR_INVALID_ARG
+ * (unknown mesh, bad kernel, rule or counts, NULL pointers, misaligned
+ * complex output).  Found on the device and reported by bem_sync as
+ * BEM_ERR_INVALID_ARG: pointer ranges beyond n_row_idx / n_points or
+ * decreasing, a block beyond out_len (that cluster is skipped), a row index
+ * out of range (that row is skipped). */
+typedef struct {
+    int32_t mesh_id;
+    bem_kernel_desc kernel;
+    int32_t rule;                /* BEM_RULE_TRI7 or BEM_RULE_DUFFY */
+    int32_t q;                   /* Gauss points per axis (BEM_RULE_DUFFY) */
+    int32_t n_clusters;
+    const int32_t *row_ptr;
+    const int32_t *row_idx;
+    int64_t n_row_idx;
+    const int32_t *pt_ptr;
+    const double *z;
+    const double *nz;
+    const double *sp;
+    const double *sm;
+    int64_t n_points;
+    const int64_t *out_off;
+    void *out;
+    int64_t out_len;
+} bem_green_job;
+
+int bem_green_matrices(bem_ctx *ctx, const bem_green_job *job);
+
 /* ---- quadrature rules ------------------------------------------------------
  * Copies the library's 4D rule on D x D for a case (Section 2.2; case 0 =
  * disjoint pairs with regular_rule BEM_RULE_DUFFY / BEM_RULE_TRI7, 1 = common

@@ -5,14 +5,14 @@ The compute path is the CUDA library built by ``paper_1510_07244_gb300.build``;
 this package only marshals arguments to it (``_binding``) and, in
 ``workloads``, assembles the synthetic benchmark inputs.
 """
-from ._binding import (Context, BlockJob, BemError, kernel_desc, quad_desc, load, LIB_PATH,
-                       EXPORTS, KERNELS, BASES, RULES, bem_rule_points, PLAN_GRAPH,
+from ._binding import (Context, BlockJob, GreenJob, BemError, kernel_desc, quad_desc, load,
+                       LIB_PATH, EXPORTS, KERNELS, BASES, RULES, bem_rule_points, PLAN_GRAPH,
                        PLAN_AUTOTUNE, PLAN_PROFILE, ORDER_CLASSES,
                        ORDER_CLASS_POINTS, bem_shard_blocks, bem_gca_pivots,
                        bem_touching_pairs)
 
-__all__ = ["Context", "BlockJob", "BemError", "kernel_desc", "quad_desc", "load", "LIB_PATH",
-           "EXPORTS", "KERNELS", "BASES", "RULES", "bem_rule_points",
+__all__ = ["Context", "BlockJob", "GreenJob", "BemError", "kernel_desc", "quad_desc", "load",
+           "LIB_PATH", "EXPORTS", "KERNELS", "BASES", "RULES", "bem_rule_points",
            "PLAN_GRAPH", "PLAN_AUTOTUNE", "PLAN_PROFILE", "ORDER_CLASSES",
            "ORDER_CLASS_POINTS", "bem_shard_blocks", "bem_gca_pivots",
            "bem_touching_pairs"]

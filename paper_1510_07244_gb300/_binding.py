@@ -31,7 +31,7 @@ EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_
            "bem_pivot_entries_absolute", "bem_mlp_create", "bem_mlp_destroy", "bem_mlp_num_params",
            "bem_mlp_set_params", "bem_mlp_get_params", "bem_mlp_gradients", "bem_mlp_train_step",
            "bem_mlp_infer", "bem_pair_features", "bem_set_order_model", "bem_learned_counts",
-           "bem_shard_blocks", "bem_gca_pivots", "bem_touching_pairs"]
+           "bem_shard_blocks", "bem_gca_pivots", "bem_touching_pairs", "bem_green_matrices"]
 ORDER_CLASSES = [("duffy", 2), ("tri7", 1), ("duffy", 4), ("duffy", 5), ("duffy", 6), ("duffy", 8)]
 ORDER_CLASS_POINTS = [16, 49, 256, 625, 1296, 4096]
 PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE = 1, 2, 4
@@ -64,6 +64,15 @@ class bem_block_job(ctypes.Structure):
                 ("col_ptr", _vp), ("col_idx", _vp), ("n_col_clusters", ctypes.c_int32),
                 ("blk_row", _vp), ("blk_col", _vp), ("blk_off", _vp),
                 ("n_blocks", ctypes.c_int64), ("out", _vp)]
+
+
+class bem_green_job(ctypes.Structure):
+    _fields_ = [("mesh_id", ctypes.c_int32), ("kernel", bem_kernel_desc),
+                ("rule", ctypes.c_int32), ("q", ctypes.c_int32), ("n_clusters", ctypes.c_int32),
+                ("row_ptr", _vp), ("row_idx", _vp), ("n_row_idx", ctypes.c_int64),
+                ("pt_ptr", _vp), ("z", _vp), ("nz", _vp), ("sp", _vp), ("sm", _vp),
+                ("n_points", ctypes.c_int64), ("out_off", _vp), ("out", _vp),
+                ("out_len", ctypes.c_int64)]
 
 
 class bem_mesh_stats(ctypes.Structure):
@@ -107,6 +116,7 @@ def load():
     lib.bem_assemble_dense.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc),
                                        P(bem_quad_desc), ctypes.c_int32, _vp]
     lib.bem_near_field_noalloc.argtypes = [_vp, P(bem_block_job)]
+    lib.bem_green_matrices.argtypes = [_vp, P(bem_green_job)]
     lib.bem_pivot_entries_absolute.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc),
                                                P(bem_quad_desc), _vp, _vp, ctypes.c_int64, _vp]
     lib.bem_mlp_create.argtypes = [_vp, ctypes.c_uint64, P(_vp)]
@@ -271,6 +281,51 @@ class BlockJob:
                              self.blk_row.numel(), _ptr(self.out))
 
 
+@dataclass
+class GreenJob:
+    """Green quadrature matrices A_t = (A_t+, A_t-) of a list of clusters
+    (CUDA tensors): rows row_idx[row_ptr[c]:row_ptr[c+1]], points z / normals nz
+    [pt_ptr[c]:pt_ptr[c+1]] (float64, shape (n, 3)), optional per-point factors
+    sp / sm, block c written column-major (n_c x 2 m_c) at out_off[c] of out."""
+    mesh_id: int
+    row_ptr: object
+    row_idx: object
+    pt_ptr: object
+    z: object
+    nz: object
+    out_off: object
+    out: object
+    sp: object = None
+    sm: object = None
+    kernel: bem_kernel_desc = field(default_factory=kernel_desc)
+    rule: str = "tri7"
+    q: int = 0
+
+    def to_c(self) -> bem_green_job:
+        import torch
+        for n in ("row_ptr", "row_idx", "pt_ptr"):
+            _check_dev(getattr(self, n), torch.int32, n)
+        for n in ("z", "nz"):
+            _check_dev(getattr(self, n), torch.float64, n)
+        for n in ("sp", "sm"):
+            if getattr(self, n) is not None:
+                _check_dev(getattr(self, n), torch.float64, n)
+        _check_dev(self.out_off, torch.int64, "out_off")
+        cplx = self.kernel.kind == KERNELS["helmholtz_slp"]
+        _check_dev(self.out, torch.complex128 if cplx else torch.float64, "out")
+        n_clusters = self.row_ptr.numel() - 1
+        n_points = self.z.numel() // 3
+        if (self.pt_ptr.numel() != n_clusters + 1 or self.out_off.numel() != n_clusters
+                or self.nz.numel() != self.z.numel()
+                or any(t is not None and t.numel() != n_points for t in (self.sp, self.sm))):
+            raise ValueError("GreenJob: inconsistent array sizes")
+        return bem_green_job(self.mesh_id, self.kernel, RULES[self.rule], int(self.q), n_clusters,
+                             _ptr(self.row_ptr), _ptr(self.row_idx), self.row_idx.numel(),
+                             _ptr(self.pt_ptr), _ptr(self.z), _ptr(self.nz), _ptr(self.sp),
+                             _ptr(self.sm), n_points, _ptr(self.out_off), _ptr(self.out),
+                             self.out.numel())
+
+
 class Context:
     """Owns a bem_ctx.  Methods mirror the C entry points."""
 
@@ -333,6 +388,10 @@ class Context:
         """Near field of one job without any device allocation (static scratch)."""
         c = job.to_c()
         self._check(self.lib.bem_near_field_noalloc(self.h, ctypes.byref(c)))
+
+    def bem_green_matrices(self, job):
+        c = job.to_c()
+        self._check(self.lib.bem_green_matrices(self.h, ctypes.byref(c)))
 
     def bem_coupling_blocks(self, jobs):
         arr = (bem_block_job * len(jobs))(*[j.to_c() for j in jobs])

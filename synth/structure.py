@@ -10,6 +10,10 @@ build_block_partition: the recursive block tree over (root, root) with the
   far blocks, leaf x leaf inadmissible blocks are near blocks.
 seeded_pivots: a seeded stand-in for the cross-approximation pivots, at most
   `rank` indices per cluster.
+green_box_points: the point sets of the Green quadrature matrices (Section
+  2.3): points, outward normals and weights of a tensor Gauss-Legendre rule
+  (numpy's nodes) on the six faces of a cluster's auxiliary box omega_t.  They
+  are inputs of the library's call; the integrals over the mesh are not here.
 
 Everything is returned as plain int32/int64 numpy arrays in the cluster-CSR
 form that the library's block-list calls take: clusters (ptr, idx), blocks
@@ -180,3 +184,53 @@ def seeded_pivots(part: BlockPartition, rank: int, seed: int):
 def coupling_blocks(part: BlockPartition, piv_ptr):
     """(blk_row, blk_col, blk_off, total) for the far blocks over pivot sets."""
     return _blocks(part.far, lambda c: int(piv_ptr[c + 1] - piv_ptr[c]))
+
+
+def green_box_points(bmin, bmax, gauss_per_face: int):
+    """Points on the boundary of the auxiliary box omega_t of a cluster whose
+    supports lie in the box [bmin, bmax] (Section 2.3): omega_t is that box
+    grown by delta / 2 on every side, delta = diam [bmin, bmax], so the points
+    stay delta / 2 away from the supports.  Each face carries the tensor
+    product of two gauss_per_face-point Gauss-Legendre rules.
+
+    Returns (z (m, 3), outward unit normals (m, 3), weights (m,), delta) with
+    m = 6 gauss_per_face^2, faces in the order -x, +x, -y, +y, -z, +z."""
+    bmin = np.asarray(bmin, np.float64)
+    bmax = np.asarray(bmax, np.float64)
+    delta = float(np.linalg.norm(bmax - bmin))
+    lo, hi = bmin - 0.5 * delta, bmax + 0.5 * delta
+    x, w = np.polynomial.legendre.leggauss(int(gauss_per_face))
+    z, nz, wt = [], [], []
+    for ax in range(3):
+        a, b = [d for d in range(3) if d != ax]
+        ua = 0.5 * (lo[a] + hi[a]) + 0.5 * (hi[a] - lo[a]) * x
+        ub = 0.5 * (lo[b] + hi[b]) + 0.5 * (hi[b] - lo[b]) * x
+        wab = np.outer(w * 0.5 * (hi[a] - lo[a]), w * 0.5 * (hi[b] - lo[b])).ravel()
+        for side, val in ((-1.0, lo[ax]), (1.0, hi[ax])):
+            p = np.zeros((len(x) * len(x), 3))
+            p[:, ax] = val
+            p[:, a] = np.repeat(ua, len(x))
+            p[:, b] = np.tile(ub, len(x))
+            n = np.zeros_like(p)
+            n[:, ax] = side
+            z.append(p)
+            nz.append(n)
+            wt.append(wab)
+    return np.concatenate(z), np.concatenate(nz), np.concatenate(wt), delta
+
+
+def green_point_sets(tree: ClusterTree, clusters, gauss_per_face: int):
+    """Green point sets of the given clusters in the CSR form the library's
+    Green-matrix call takes: (pt_ptr int32, z (m, 3), nz (m, 3), sp, sm) with
+    sp = sqrt(w) and sm = sqrt(w) delta_t, the factors of A_t+ and A_t-."""
+    ptr = [0]
+    zs, ns, sps, sms = [], [], [], []
+    for c in clusters:
+        z, n, w, delta = green_box_points(tree.bmin[c], tree.bmax[c], gauss_per_face)
+        zs.append(z)
+        ns.append(n)
+        sps.append(np.sqrt(w))
+        sms.append(np.sqrt(w) * delta)
+        ptr.append(ptr[-1] + len(z))
+    return (np.array(ptr, np.int32), np.concatenate(zs), np.concatenate(ns),
+            np.concatenate(sps), np.concatenate(sms))

@@ -61,3 +61,34 @@ def test_create_without_gpu_is_an_error(lib):
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     assert lib.bem_create(ctypes.byref(h), 0, None) != 0
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """Every struct the binding passes through the C ABI has the size and field
+    offsets that the C compiler gives the declarations in include/bem.h."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1510_07244_gb300 import _binding as b
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"bem_kernel_desc": b.bem_kernel_desc, "bem_quad_desc": b.bem_quad_desc,
+               "bem_block_job": b.bem_block_job, "bem_green_job": b.bem_green_job,
+               "bem_mesh_stats": b.bem_mesh_stats, "bem_kernel_time": b.bem_kernel_time}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "bem.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field_name, _ in cls._fields_:
+            lines.append(f'printf("{name} {field_name} %zu\\n", offsetof({name}, {field_name}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field_name, _ in cls._fields_:
+            assert got[(name, field_name)] == getattr(cls, field_name).offset, (name, field_name)
