@@ -1050,6 +1050,191 @@ def run_c5(args):
     ctx.close()
 
 
+# FP64 operations of the Green-matrix kernel (FMA = 2, rsqrt = 1, sincos = 2):
+# per rule point the basis weight 2, the point x - z 12, r^2 5, rsqrt 1,
+# (x - z).n 5, r^-3 and its products 4, two accumulations 3 (Laplace: 32);
+# Helmholtz adds kappa r 2, sincos 2 and the phase products and two more
+# accumulations 11 (47).  Per support triangle and point: edge vectors and
+# z offset 9, scaled accumulation 4 (8 for Helmholtz).
+def green_flops(helm: bool, np_rule: int) -> float:
+    return (47.0 if helm else 32.0) * np_rule + (17.0 if helm else 13.0)
+
+
+def green_workload(pkg, w, gauss_per_face=4, eps=1e-6):
+    """The Green quadrature matrices the host GCA forms (Section 2.3) for the
+    workload's cluster tree: leaves with all their indices, every other cluster
+    with the rows t^ = pivots of its sons (nested bases), each against its
+    6 gauss_per_face^2 box points.  Returns the cluster-CSR arrays of
+    bem_green_matrices and the GCA's own wall time."""
+    from synth.structure import green_point_sets
+    part = w.partition
+    tree = part.tree
+    ptr, idx = part.cluster_csr()
+    t0 = time.perf_counter()
+    pp, pi = pkg.bem_gca_pivots(w.mesh.verts, w.mesh.tris, w.basis, ptr, idx, part.son_array(),
+                                kappa=0.0, gauss_per_face=gauss_per_face, eps=eps,
+                                max_rank=w.meta["rank"])
+    gca_s = time.perf_counter() - t0
+    clusters = list(range(tree.n_clusters))
+    rows = []
+    for c in clusters:
+        if tree.is_leaf(c):
+            rows.append(np.asarray(tree.indices(c), np.int64))
+        else:
+            rows.append(np.unique(np.concatenate([pi[pp[s]:pp[s + 1]] for s in tree.sons[c]])))
+    row_ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    pt_ptr, z, nz, sp, sm = green_point_sets(tree, clusters, gauss_per_face)
+    sizes = 2 * np.diff(row_ptr).astype(np.int64) * np.diff(pt_ptr).astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    return {"row_ptr": row_ptr, "rows": np.concatenate(rows).astype(np.int32), "pt_ptr": pt_ptr,
+            "z": z, "nz": nz, "sp": sp, "sm": sm, "off": off, "total": int(sizes.sum()),
+            "gca_s": gca_s}
+
+
+def run_green(args):
+    """Green quadrature matrices A_t of the GCA (Section 2.3) on the device:
+    one bem_green_matrices launch per step over every cluster of the
+    20480-triangle P1 icosphere's tree, FP64, Radon's 7 points per support
+    triangle; L2 flushed (256 MiB write, untimed) before each step."""
+    import torch
+    import synth
+    import paper_1510_07244_gb300 as pkg
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    w = synth.workloads.config2(args.levels)
+    G = green_workload(pkg, w)
+    stream = torch.cuda.current_stream(dev)
+    ctx = pkg.Context(0, stream)
+    mid = ctx.bem_mesh_upload(w.mesh.verts, w.mesh.tris, w.basis)
+    d = {k: torch.as_tensor(G[k], device=dev) for k in ("row_ptr", "rows", "pt_ptr")}
+    d.update({k: torch.as_tensor(G[k], dtype=torch.float64, device=dev)
+              for k in ("z", "nz", "sp", "sm")})
+    d["off"] = torch.as_tensor(G["off"], dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # support triangles per row: 1 (P0) or the vertex degree (P1)
+    deg = (np.bincount(w.mesh.tris.ravel(), minlength=w.mesh.nv) if w.basis == "p1"
+           else np.ones(w.mesh.nt, np.int64))
+    m_c = np.diff(G["pt_ptr"]).astype(np.int64)
+    tri_pts = float(sum(deg[G["rows"][G["row_ptr"][c]:G["row_ptr"][c + 1]]].sum() * m_c[c]
+                        for c in range(len(m_c))))
+    results = {}
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    for kernel, kappa in (("laplace_slp", 0.0), ("helmholtz_slp", 8.0)):
+        helm = kernel == "helmholtz_slp"
+        out = torch.empty(G["total"], dtype=torch.complex128 if helm else torch.float64,
+                          device=dev)
+        job = pkg.GreenJob(mid, d["row_ptr"], d["rows"], d["pt_ptr"], d["z"], d["nz"], d["off"],
+                           out, sp=d["sp"], sm=d["sm"], kernel=pkg.kernel_desc(kernel, kappa),
+                           rule="tri7")
+        for _ in range(args.warmup):
+            ctx.bem_green_matrices(job)
+        ctx.bem_sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            ctx.bem_green_matrices(job)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.bem_sync()
+        ms = float(sum(a.elapsed_time(b) for a, b in evs))
+        flops = tri_pts * green_flops(helm, 7)
+        ach = flops * args.steps / (ms / 1e3) / 1e12
+        results[kernel] = {"value": G["total"] * args.steps / (ms / 1e3),
+                           "ms_per_step": ms / args.steps,
+                           "roofline": {"bound": "alu", "achieved": round(ach, 4),
+                                        "peak": round(PEAK_FP64, 4), "unit": "TFLOP/s",
+                                        "frac": round(ach / PEAK_FP64, 4), "traffic": None,
+                                        "kernel": "green", "pipe": "fp64",
+                                        "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x "
+                                                       "2.07 GHz"}}
+        del out
+    clk = clocks.stop()
+
+    # end to end through the C ABI: host (pinned) inputs in, the matrices out
+    host = {k: torch.as_tensor(G[k]).pin_memory() for k in ("row_ptr", "rows", "pt_ptr")}
+    host.update({k: torch.as_tensor(G[k], dtype=torch.float64).pin_memory()
+                 for k in ("z", "nz", "sp", "sm")})
+    host["off"] = torch.as_tensor(G["off"], dtype=torch.int64).pin_memory()
+    hout = torch.empty(G["total"], dtype=torch.float64).pin_memory()
+    dd = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    dout = torch.empty(G["total"], dtype=torch.float64, device=dev)
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    job = pkg.GreenJob(mid, dd["row_ptr"], dd["rows"], dd["pt_ptr"], dd["z"], dd["nz"],
+                       dd["off"], dout, sp=dd["sp"], sm=dd["sm"], rule="tri7")
+    e2e_steps = max(1, args.e2e_steps)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for k, v in host.items():
+            dd[k].copy_(v, non_blocking=True)
+        ctx.bem_green_matrices(job)
+        hout.copy_(dout, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    ctx.bem_sync()
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = green_cpu_baseline(w, G, args.cpu_seconds)
+    lap = results["laplace_slp"]
+    n_rows = int(G["row_ptr"][-1])
+    line = {"metric": "Green quadrature matrix entries/s (A_t of the GCA, FP64)",
+            "value": lap["value"], "unit": "entries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": lap["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"A_t = (A_t+, A_t-) of all {len(m_c)} clusters of the "
+                                   f"{w.mesh.nt}-triangle icosphere's P1 tree (leaf 32; leaves "
+                                   f"with their indices, others with their sons' GCA pivots): "
+                                   f"{n_rows} rows x 96 box points (4 x 4 Gauss per face), "
+                                   f"Radon 7 per support triangle, Laplace",
+                       "entries_per_step": G["total"], "l2": "flushed (256 MiB write) "
+                                                             "before each step"},
+            "roofline": lap["roofline"],
+            "helmholtz_kappa8": results["helmholtz_slp"],
+            "e2e": {"value": G["total"] / e2e_s, "unit": "entries/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": G["total"] * 8},
+            "host_gca_s": G["gca_s"],
+            "gpu_launches": args.steps,
+            "cpu_baseline": cpu,
+            "clocks": clk}
+    ctx.bem_mesh_free(mid)
+    ctx.close()
+    print(json.dumps(line))
+
+
+def green_cpu_baseline(w, G, budget_s):
+    """The oracle's Green entries on a seeded sample of the workload's (row,
+    point) pairs, all host cores; entries/s counts plus and minus as two."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(151007244)
+    n_cl = len(G["row_ptr"]) - 1
+    row_cl = np.repeat(np.arange(n_cl), np.diff(G["row_ptr"]))
+
+    def sample(n):
+        r = rng.integers(0, len(G["rows"]), n)
+        c = row_cl[r]
+        p = G["pt_ptr"][c] + rng.integers(0, np.diff(G["pt_ptr"])[c])
+        t0 = time.perf_counter()
+        oracle.green_entries(w.mesh.verts, w.mesh.tris, w.basis, G["rows"][r], G["z"][p],
+                             G["nz"][p], kappa=0.0, rule="tri7")
+        return time.perf_counter() - t0
+
+    n0 = 20000
+    t0 = sample(n0)
+    n = int(max(n0, min(50_000_000, n0 * budget_s / max(t0, 1e-3))))
+    t = sample(n)
+    return {"value": 2 * n / t, "unit": "entries/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} seeded (row, point) pairs of the step (two entries each); {t:.1f} s "
+                      f"on {os.cpu_count()} OpenMP threads"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1070,9 +1255,10 @@ def main():
                          "reports the fastest within 1e-6 of the FP64 form")
     ap.add_argument("--pivots", default="gca", choices=["gca", "seeded"],
                     help="coupling pivots from the host GCA (default) or seeded per cluster")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "green"],
                     help="c2 (default): the 20480-triangle P1 benchmark line; c3 / c4: the "
-                         "49152-triangle Helmholtz cube / the 48-mesh batch, measured the same way")
+                         "49152-triangle Helmholtz cube / the 48-mesh batch, measured the same "
+                         "way; green: the GCA's Green quadrature matrices A_t of the c2 tree")
     ap.add_argument("--c5-n", type=int, default=128,
                     help="C5 sphere subdivision (8 n^2 triangles; 128 = the 131072-triangle "
                          "workload, smaller values only for profiling captures)")
@@ -1086,6 +1272,8 @@ def main():
         run_reference(args)
     elif args.workload == "c5":
         run_c5(args)
+    elif args.workload == "green":
+        run_green(args)
     elif args.workload != "c2":
         run_extra(args)
     else:

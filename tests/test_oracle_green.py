@@ -8,7 +8,12 @@ A_t of Green's representation formula), independent of the oracle itself:
 * Helmholtz: the normal derivative equals the z-derivative of the oracle's
   own first entry (a wrong sign, a dropped (1 - i kappa r) factor or a
   transposed argument fails), and kappa -> 0 reproduces Laplace;
-* the two triangle rules agree where the integrand is smooth."""
+* the two triangle rules agree where the integrand is smooth;
+* Green's representation formula on the auxiliary box omega_t (Section 2.3,
+  G|_{t x s} ~ A_t B_ts): the oracle's entries, scaled as the paper scales
+  a_{t+}, a_{t-}, b_{ts+}, b_{ts-}, reproduce the Galerkin entries of an
+  admissible block, with an error that falls geometrically as the Gauss rule
+  on the box faces is refined; with the minus part's sign flipped it does not."""
 import numpy as np
 import pytest
 
@@ -167,3 +172,70 @@ def test_rules_agree_on_smooth_integrands(mesh):
 def test_bad_index_is_rejected(mesh):
     with pytest.raises(ValueError):
         oracle.green_entries(mesh.verts, mesh.tris, "p1", [mesh.nv], [[3.0, 0, 0]], [[1.0, 0, 0]])
+
+
+def _box_gap(amin, amax, bmin, bmax):
+    gap = np.maximum(0.0, np.maximum(np.asarray(amin) - bmax, np.asarray(bmin) - amax))
+    return float(np.linalg.norm(gap))
+
+
+@pytest.mark.parametrize("basis", ["p0", "p1"])
+@pytest.mark.parametrize("kernel,kappa", [("laplace_slp", 0.0), ("helmholtz_slp", 3.0)])
+def test_representation_formula_reproduces_admissible_blocks(basis, kernel, kappa):
+    """For x in B_t and y outside omega_t, Green's representation formula on
+    the boundary of omega_t gives g(x, y) = int [g(x, z) dg/dn(z)(z, y) -
+    dg/dn(z)(x, z) g(z, y)] dz; a Gauss rule (z_nu, w_nu) on the faces turns
+    it into g_ij ~ sum_nu a_{t+,i nu} b_{ts+,j nu} - a_{t-,i nu} b_{ts-,j nu}
+    with a_{t+} = sqrt(w) int phi_i g, a_{t-} = sqrt(w) delta_t int phi_i dg/dn,
+    b_{ts+} = sqrt(w) int psi_j dg/dn, b_{ts-} = sqrt(w) / delta_t int psi_j g.
+    With Radon's 7 points on every triangle on both sides, the Galerkin entry
+    of the admissible block uses the same points, so only the box rule's error
+    remains.  Blocks are taken with B_s at least delta_t / 2 away from omega_t
+    (the paper's bound on the distance to the boundary)."""
+    from synth.structure import build_block_partition, green_box_points
+    mesh = synth.jitter(synth.icosphere(3), 0.05, 7)
+    part = build_block_partition(mesh, basis, leaf_size=32, eta=2.0)
+    tree = part.tree
+    best = None
+    for t, s in part.far:
+        lo, hi = np.asarray(tree.bmin[t]), np.asarray(tree.bmax[t])
+        d = float(np.linalg.norm(hi - lo))
+        ratio = _box_gap(lo - d / 2, hi + d / 2, tree.bmin[s], tree.bmax[s]) / d
+        size = min(len(tree.indices(t)), len(tree.indices(s)))
+        if ratio >= 0.5 and size >= 8 and (best is None or size > best[0]):
+            best = (size, t, s)
+    assert best is not None
+    _, t, s = best
+    rt, cs = tree.indices(t), tree.indices(s)
+    G = oracle.entries(mesh.verts, mesh.tris, np.repeat(rt, len(cs)), np.tile(cs, len(rt)),
+                       kernel=kernel, kappa=kappa, basis=basis, q_regular=3,
+                       regular_rule="tri7", q_identical=5, q_edge=5, q_vertex=5)
+    G = np.asarray(G).reshape(len(rt), len(cs))
+    errs, wrong = [], []
+    for g in (4, 8, 12):
+        z, nz, w, delta = green_box_points(tree.bmin[t], tree.bmax[t], g)
+        m = len(z)
+
+        def ent(idx):
+            ii = np.repeat(idx, m)
+            zz = np.tile(np.arange(m), len(idx))
+            P, M = oracle.green_entries(mesh.verts, mesh.tris, basis, ii, z[zz], nz[zz],
+                                        kappa=kappa, rule="tri7")
+            return P.reshape(len(idx), m), M.reshape(len(idx), m)
+
+        Pt, Mt = ent(rt)
+        Ps, Ms = ent(cs)
+        sw = np.sqrt(w)
+        a_plus, a_minus = Pt * sw, Mt * (sw * delta)
+        b_plus, b_minus = Ms * sw, Ps * (sw / delta)
+        approx = a_plus @ b_plus.T - a_minus @ b_minus.T
+        flipped = a_plus @ b_plus.T + a_minus @ b_minus.T
+        if kernel != "helmholtz_slp":
+            assert np.abs(approx.imag).max() == 0.0
+            approx, flipped = approx.real, flipped.real
+        scale = np.abs(G).max()
+        errs.append(np.abs(G - approx).max() / scale)
+        wrong.append(np.abs(G - flipped).max() / scale)
+    assert errs[0] < 5e-2 and errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10, errs
+    assert errs[2] < 2e-5, errs
+    assert min(wrong) > 0.1, wrong
