@@ -406,8 +406,9 @@ int bem_gca_pivots(const double *verts, int64_t nv, const int32_t *tris, int64_t
  * (unknown mesh, bad kernel, rule or counts, NULL pointers, misaligned
  * complex output).  Found on the device and reported by bem_sync as
  * BEM_ERR_INVALID_ARG: pointer ranges beyond n_row_idx / n_points or
- * decreasing, a block beyond out_len (that cluster is skipped), a row index
- * out of range (that row is skipped). */
+ * decreasing, a cluster with 2^30 or more rows or points, a block beyond
+ * out_len (that cluster is skipped), a row index out of range (that row is
+ * skipped). */
 typedef struct {
     int32_t mesh_id;
     bem_kernel_desc kernel;

@@ -102,8 +102,9 @@ __global__ void __launch_bounds__(kGreenThreads) k_green(MeshView m, GreenArgs a
         const int32_t rb = a.row_ptr[c], re = a.row_ptr[c + 1];
         const int32_t pb = a.pt_ptr[c], pe = a.pt_ptr[c + 1];
         const int64_t off = a.out_off[c];
+        // the row and point loops step in int: a cluster holds fewer than 2^30 of each
         bool ok = rb >= 0 && re >= rb && re <= a.n_row_idx && pb >= 0 && pe >= pb &&
-                  pe <= a.n_points;
+                  pe <= a.n_points && re - rb < (1 << 30) && pe - pb < (1 << 30);
         if (ok && re > rb && pe > pb) {
             // both factors are below 2^31, so the block size fits in int64
             const int64_t need = 2 * (int64_t)(re - rb) * (int64_t)(pe - pb);
