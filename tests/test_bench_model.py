@@ -63,3 +63,36 @@ def test_committed_traffic_figures():
     t = bench.profiled_traffic("coupling_p1")
     assert isinstance(t, int) and 1_000_000 < t < 100_000_000
     assert bench.profiled_traffic("no_such_kernel") is None
+
+
+def test_green_workload_is_the_gcas_row_sets(small_c2):
+    """The Green-matrix workload holds, per cluster, the rows the host GCA
+    forms A_t on (leaves: all indices; other clusters: the union of their sons'
+    pivots, nested), 96 box points each, and non-overlapping blocks."""
+    import numpy as np
+    import paper_1510_07244_gb300 as pkg
+    w, _ = small_c2
+    G = bench.green_workload(pkg, w)
+    tree = w.partition.tree
+    ptr, idx = w.partition.cluster_csr()
+    pp, pi = pkg.bem_gca_pivots(w.mesh.verts, w.mesh.tris, w.basis, ptr, idx,
+                                w.partition.son_array(), kappa=0.0, gauss_per_face=4, eps=1e-6,
+                                max_rank=w.meta["rank"])
+    rp, rows = G["row_ptr"], G["rows"]
+    assert len(rp) == tree.n_clusters + 1 and rp[0] == 0 and rp[-1] == len(rows)
+    for c in range(tree.n_clusters):
+        r = rows[rp[c]:rp[c + 1]]
+        if tree.is_leaf(c):
+            assert np.array_equal(np.sort(r), np.sort(tree.indices(c)))
+        else:
+            sons = np.concatenate([pi[pp[s]:pp[s + 1]] for s in tree.sons[c]])
+            assert np.array_equal(r, np.unique(sons))
+            # nested bases: a cluster's pivots are rows of its A_t
+            assert np.isin(pi[pp[c]:pp[c + 1]], r).all()
+    m = np.diff(G["pt_ptr"])
+    assert (m == 96).all() and len(G["z"]) == m.sum() == len(G["sp"]) == len(G["sm"])
+    sizes = 2 * np.diff(rp).astype(np.int64) * m
+    assert np.array_equal(G["off"], np.concatenate([[0], np.cumsum(sizes)[:-1]]))
+    assert G["total"] == sizes.sum()
+    # operation count: a rule point costs more with the Helmholtz phase
+    assert bench.green_flops(True, 7) > bench.green_flops(False, 7) > 7 * 30
