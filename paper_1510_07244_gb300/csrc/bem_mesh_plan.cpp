@@ -12,6 +12,9 @@
 
 #include <algorithm>
 #include <array>
+#include <climits>
+#include <thread>
+#include <vector>
 
 #include "bem_internal.h"
 
@@ -19,18 +22,115 @@ namespace bem {
 
 namespace {
 
-// kPerm code of the permutation whose first two entries are (o0, o1)
-int perm_code2(int o0, int o1)
+int pos_in(const int32_t *B, int v) { return B[0] == v ? 0 : (B[1] == v ? 1 : 2); }
+
+// The fans of a triangle's three vertices are ascending lists of triangles; a
+// three-way merge visits every neighbour b once, in ascending order, and
+// calls f(b, m) with bit k of m set when b is in the fan of the triangle's
+// vertex k (so the bit count of m is the number of shared indices).
+template <class F>
+inline void for_each_neighbour(const int *vp, const int *vt, const int32_t *A, F &&f)
 {
-    static const std::array<int, 9> table = [] {
-        std::array<int, 9> t{};
-        for (int c = 0; c < 6; ++c) t[kPerm[c][0] * 3 + kPerm[c][1]] = c;
-        return t;
-    }();
-    return table[o0 * 3 + o1];
+    int i[3], e[3];
+    for (int k = 0; k < 3; ++k) {
+        i[k] = vp[A[k]];
+        e[k] = vp[A[k] + 1];
+    }
+    for (;;) {
+        int b = INT32_MAX;
+        for (int k = 0; k < 3; ++k)
+            if (i[k] < e[k] && vt[i[k]] < b) b = vt[i[k]];
+        if (b == INT32_MAX) return;
+        int m = 0;
+        for (int k = 0; k < 3; ++k)
+            if (i[k] < e[k] && vt[i[k]] == b) {
+                m |= 1 << k;
+                ++i[k];
+            }
+        f(b, m);
+    }
 }
 
-int pos_in(const int32_t *B, int v) { return B[0] == v ? 0 : (B[1] == v ? 1 : 2); }
+// Case of a pair from its mask of shared positions of a.
+inline int mask_case(int m) { return m == 7 ? kIdentical : (m == 3 || m == 5 || m == 6 ? kEdge : kVertex); }
+
+// Pass 1 over the triangles [lo, hi): neighbour counts per triangle (into
+// cnt[a]) and per case for the range; flags two distinct triangles with the
+// same three vertices.
+struct RangeCount {
+    int64_t per_case[4] = {0, 0, 0, 0};
+    bool degenerate = false;
+};
+
+void count_range(const int32_t *tris, const TouchPlan &P, int64_t lo, int64_t hi, int *cnt,
+                 RangeCount &C)
+{
+    const int *vp = P.vt_ptr.data(), *vt = P.vt_tri.data();
+    for (int64_t a = lo; a < hi; ++a) {
+        int n = 0;
+        for_each_neighbour(vp, vt, tris + 3 * a, [&](int b, int m) {
+            if (m == 7 && b != (int)a) C.degenerate = true;
+            ++C.per_case[mask_case(m)];
+            ++n;
+        });
+        cnt[a] = n;
+    }
+}
+
+// Pass 2: the pairs of [lo, hi) at their final positions nb_ptr[a] ..., and
+// their indices into the case lists from the range's offsets case_at[].
+void fill_range(const int32_t *tris, TouchPlan &P, const int *perm2, int64_t lo, int64_t hi,
+                int64_t case_at[4])
+{
+    const int *vp = P.vt_ptr.data(), *vt = P.vt_tri.data();
+    for (int64_t a = lo; a < hi; ++a) {
+        const int32_t *A = tris + 3 * a;
+        int k = P.nb_ptr[(size_t)a];
+        for_each_neighbour(vp, vt, A, [&](int b, int m) {
+            const int32_t *B = tris + 3 * (int64_t)b;
+            const int cas = mask_case(m);
+            int o0, o1, p0, p1;   // a's order starts (o0, o1), b's (p0, p1)
+            if (cas == kIdentical) {
+                o0 = 0;
+                o1 = 1;
+                p0 = pos_in(B, A[0]);
+                p1 = pos_in(B, A[1]);
+            } else if (cas == kEdge) {
+                // shared positions i0 < i1 of a; the edge starts at the one whose
+                // cyclic successor is the other
+                const int i0 = (m & 1) ? 0 : 1, i1 = (m & 4) ? 2 : 1;
+                const int f = (i0 + 1) % 3 == i1 ? i0 : i1;
+                o0 = f;
+                o1 = (f + 1) % 3;
+                p0 = pos_in(B, A[o0]);
+                p1 = pos_in(B, A[o1]);
+            } else {
+                const int i0 = m == 1 ? 0 : (m == 2 ? 1 : 2);
+                o0 = i0;
+                o1 = (i0 + 1) % 3;
+                p0 = pos_in(B, A[i0]);
+                p1 = (p0 + 1) % 3;
+            }
+            P.lists[cas][(size_t)case_at[cas]++] = k;
+            P.nb_tri[(size_t)k] = b;
+            P.nb_src[(size_t)k] = (int)a;
+            P.nb_case[(size_t)k] = (unsigned char)cas;
+            P.nb_perm[(size_t)k] = (unsigned char)(perm2[o0 * 3 + o1] * 6 + perm2[p0 * 3 + p1]);
+            ++k;
+        });
+    }
+}
+
+// Runs body(r) for r = 0 .. n-1, ranges 1.. on host threads and range 0 on
+// the calling thread.
+template <class F>
+void run_ranges(int n, F &&body)
+{
+    std::vector<std::thread> pool;
+    for (int r = 1; r < n; ++r) pool.emplace_back([&body, r] { body(r); });
+    body(0);
+    for (auto &t : pool) t.join();
+}
 
 }  // namespace
 
@@ -47,92 +147,53 @@ int plan_touching(const int32_t *tris, int64_t nt, int64_t nv, TouchPlan &P, con
             for (int k = 0; k < 3; ++k) P.vt_tri[fill[tris[3 * t + k]]++] = (int)t;
     }
     P.maxdeg = 0;
-    size_t bound = 0;     // sum over triangles of their vertices' degrees
-    for (int64_t v = 0; v < nv; ++v) {
-        const int d = P.vt_ptr[v + 1] - P.vt_ptr[v];
-        P.maxdeg = std::max(P.maxdeg, d);
-        bound += (size_t)d * d;
-    }
+    for (int64_t v = 0; v < nv; ++v) P.maxdeg = std::max(P.maxdeg, P.vt_ptr[v + 1] - P.vt_ptr[v]);
 
+    // kPerm code of the permutation whose first two entries are (o0, o1)
+    int perm2[9] = {};
+    for (int c = 0; c < 6; ++c) perm2[kPerm[c][0] * 3 + kPerm[c][1]] = c;
+
+    // Contiguous triangle ranges on host threads (one range below 4096
+    // triangles).  Pass 1 counts, a prefix sum places every pair and every
+    // case-list entry, pass 2 writes them: the result is the same for any
+    // number of ranges.
+    const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+    const int n_ranges = (int)std::max<int64_t>(1, std::min<int64_t>({hw, 64, nt / 2048}));
+    auto range_lo = [&](int r) { return nt * r / n_ranges; };
     P.nb_ptr.assign((size_t)nt + 1, 0);
-    for (auto *v : {&P.nb_tri, &P.nb_src}) {
-        v->clear();
-        v->reserve(bound);
-    }
-    P.nb_case.clear();
-    P.nb_case.reserve(bound);
-    P.nb_perm.clear();
-    P.nb_perm.reserve(bound);
-    for (auto &l : P.lists) l.clear();
-
-    // For triangle a, walk the triangle fans of its three vertices: stamp[b] == a
-    // marks b as collected, mask[b] has bit k set when a's vertex k is one of
-    // b's (so the number of set bits is the number of shared indices).
-    std::vector<int> stamp((size_t)nt, -1), cand;
-    std::vector<unsigned char> mask((size_t)nt, 0);
-    cand.reserve(64);
+    std::vector<RangeCount> C((size_t)n_ranges);
+    run_ranges(n_ranges, [&](int r) {
+        count_range(tris, P, range_lo(r), range_lo(r + 1), P.nb_ptr.data() + 1, C[(size_t)r]);
+    });
+    for (const auto &c : C)
+        if (c.degenerate) {
+            *err = "two triangles with the same vertices";
+            return BEM_ERR_DEGENERATE;
+        }
     for (int64_t a = 0; a < nt; ++a) {
-        const int32_t *A = tris + 3 * a;
-        cand.clear();
-        for (int k = 0; k < 3; ++k) {
-            const int v = A[k];
-            for (int u = P.vt_ptr[v]; u < P.vt_ptr[v + 1]; ++u) {
-                const int b = P.vt_tri[u];
-                if (stamp[b] != (int)a) {
-                    stamp[b] = (int)a;
-                    mask[b] = 0;
-                    cand.push_back(b);
-                }
-                mask[b] |= (unsigned char)(1 << k);
-            }
+        if ((int64_t)P.nb_ptr[(size_t)a] + P.nb_ptr[(size_t)a + 1] > (int64_t)INT32_MAX) {
+            *err = "more than 2^31 touching pairs";
+            return BEM_ERR_UNSUPPORTED;
         }
-        // ascending b (a few dozen candidates: insertion sort)
-        for (size_t i = 1; i < cand.size(); ++i) {
-            const int x = cand[i];
-            size_t j = i;
-            for (; j > 0 && cand[j - 1] > x; --j) cand[j] = cand[j - 1];
-            cand[j] = x;
-        }
-        for (const int b : cand) {
-            const int32_t *B = tris + 3 * (int64_t)b;
-            const int m = mask[b];
-            int cas, o0, o1, p0, p1;   // a's order starts (o0, o1), b's (p0, p1)
-            if (m == 7) {
-                if (b != (int)a) {
-                    *err = "two triangles with the same vertices";
-                    return BEM_ERR_DEGENERATE;
-                }
-                cas = kIdentical;
-                o0 = 0;
-                o1 = 1;
-                p0 = pos_in(B, A[0]);
-                p1 = pos_in(B, A[1]);
-            } else if (m == 3 || m == 5 || m == 6) {
-                cas = kEdge;
-                // shared positions i0 < i1 of a; the edge starts at the one whose
-                // cyclic successor is the other
-                const int i0 = (m & 1) ? 0 : 1, i1 = (m & 4) ? 2 : 1;
-                const int f = (i0 + 1) % 3 == i1 ? i0 : i1;
-                o0 = f;
-                o1 = (f + 1) % 3;
-                p0 = pos_in(B, A[o0]);
-                p1 = pos_in(B, A[o1]);
-            } else {
-                cas = kVertex;
-                const int i0 = m == 1 ? 0 : (m == 2 ? 1 : 2);
-                o0 = i0;
-                o1 = (i0 + 1) % 3;
-                p0 = pos_in(B, A[i0]);
-                p1 = (p0 + 1) % 3;
-            }
-            P.lists[cas].push_back((int)P.nb_tri.size());
-            P.nb_tri.push_back(b);
-            P.nb_src.push_back((int)a);
-            P.nb_case.push_back((unsigned char)cas);
-            P.nb_perm.push_back((unsigned char)(perm_code2(o0, o1) * 6 + perm_code2(p0, p1)));
-        }
-        P.nb_ptr[a + 1] = (int)P.nb_tri.size();
+        P.nb_ptr[(size_t)a + 1] += P.nb_ptr[(size_t)a];
     }
+    const size_t total = (size_t)P.nb_ptr[(size_t)nt];
+    P.nb_tri.resize(total);
+    P.nb_src.resize(total);
+    P.nb_case.resize(total);
+    P.nb_perm.resize(total);
+    std::vector<std::array<int64_t, 4>> case_at((size_t)n_ranges);
+    for (int c = 0; c < 4; ++c) {
+        int64_t at = 0;
+        for (int r = 0; r < n_ranges; ++r) {
+            case_at[(size_t)r][c] = at;
+            at += C[(size_t)r].per_case[c];
+        }
+        P.lists[c].resize((size_t)at);
+    }
+    run_ranges(n_ranges, [&](int r) {
+        fill_range(tris, P, perm2, range_lo(r), range_lo(r + 1), case_at[(size_t)r].data());
+    });
     return BEM_OK;
 }
 

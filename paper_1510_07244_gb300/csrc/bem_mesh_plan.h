@@ -22,9 +22,10 @@ struct TouchPlan {
 };
 
 // Fills P from the triangles tris (nt x 3, indices already checked to lie in
-// [0, nv) and to be distinct within each triangle).  Returns 0, or
-// BEM_ERR_DEGENERATE with a message in *err when two triangles have the same
-// three vertices.
+// [0, nv) and to be distinct within each triangle), on up to one host thread
+// per hardware thread for contiguous triangle ranges (the result does not
+// depend on their number).  Returns 0, or BEM_ERR_DEGENERATE with a message in
+// *err when two triangles have the same three vertices.
 int plan_touching(const int32_t *tris, int64_t nt, int64_t nv, TouchPlan &P, const char **err);
 
 }  // namespace bem

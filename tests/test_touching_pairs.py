@@ -119,3 +119,41 @@ def test_bad_meshes_are_rejected():
     with pytest.raises(pkg.BemError) as e:
         pkg.bem_touching_pairs(np.array([[0, 1, 3]]), 3)             # index out of range
     assert e.value.code == -1
+
+
+def _fan_reference(tris, nv):
+    """Every touching pair in ascending (a, b), found through the vertex fans
+    and classified by the oracle (for meshes too large for _brute_force)."""
+    fans = [[] for _ in range(nv)]
+    for t, row in enumerate(tris):
+        for v in row:
+            fans[v].append(t)
+    out = []
+    for a, row in enumerate(tris):
+        for b in sorted(set(fans[row[0]]) | set(fans[row[1]]) | set(fans[row[2]])):
+            case, oa, ob = oracle.classify_orders(row, tris[b])
+            out.append((a, b, CASE_ID[case], *oa, *ob))
+    return np.array(out, np.int64)
+
+
+def test_large_mesh_split_over_host_threads():
+    """5120 triangles are planned in contiguous triangle ranges on host
+    threads; shuffled and relabelled variants put neighbours in other ranges.
+    The joined result equals the oracle's classification of every pair."""
+    m = sm.icosphere(4)
+    for k, tris in enumerate(_variants(m, 5)):
+        tris = np.asarray(tris)
+        got = pkg.bem_touching_pairs(tris, m.nv)
+        lib = np.column_stack([got["src"], got["dst"], got["case"], got["ord"]]).astype(np.int64)
+        want = _fan_reference(tris, m.nv)
+        assert np.array_equal(lib, want), k
+
+
+def test_duplicate_found_in_any_range():
+    """Two triangles with the same vertices at the end of a large mesh (both
+    in the last host range) are rejected like the small case."""
+    m = sm.icosphere(4)
+    tris = np.vstack([m.tris, m.tris[-1][::-1]])
+    with pytest.raises(pkg.BemError) as e:
+        pkg.bem_touching_pairs(tris, m.nv)
+    assert e.value.code == -5
