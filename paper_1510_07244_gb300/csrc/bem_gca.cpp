@@ -65,11 +65,28 @@ void radon7(HostMesh &M)
     }
 }
 
-// int phi_i(x) g(x, z) dx and int phi_i(x) d/dn(z) g(x, z) dx.
-void basis_integrals(const HostMesh &M, int index, const double *z, const double *nz, cplx &gp,
-                     cplx &gm)
+// Points z_nu (with unit normals) of a cluster's box, one array per coordinate.
+struct BoxPoints {
+    int m = 0;
+    std::vector<double> x, y, z, nx, ny, nz;
+};
+
+// For one basis function and all m points of a box at once:
+//   gp[nu] = int phi_i(x) g(x, z_nu) dx,  gm[nu] = int phi_i(x) d/dn(z_nu) g(x, z_nu) dx.
+// The support triangles' rule points and weights are formed once per basis
+// function and the innermost loop runs over the points.  Every entry is the
+// sum over support triangles, then rule points, with the same operations as
+// evaluating one entry at a time.
+void basis_integrals(const HostMesh &M, int index, const BoxPoints &Z, cplx *gp, cplx *gm)
 {
-    gp = gm = 0.0;
+    const int m = Z.m;
+    std::fill(gp, gp + m, cplx(0.0));
+    std::fill(gm, gm + m, cplx(0.0));
+    std::vector<double> pr, mr;
+    if (M.kappa == 0.0) {
+        pr.assign(m, 0.0);
+        mr.assign(m, 0.0);
+    }
     auto tri = [&](int64_t tr, int local) {
         const int32_t *tv = M.t + 3 * tr;
         const double *v0 = M.v + 3 * (int64_t)tv[0], *v1 = M.v + 3 * (int64_t)tv[1],
@@ -83,23 +100,37 @@ void basis_integrals(const HostMesh &M, int index, const double *z, const double
                      cz = e1[0] * e2[1] - e1[1] * e2[0];
         const double sg = std::sqrt(cx * cx + cy * cy + cz * cz);
         for (int k = 0; k < 7; ++k) {
-            double d[3];
-            for (int c = 0; c < 3; ++c) d[c] = v0[c] + M.S[k] * e1[c] + M.T[k] * e2[c] - z[c];
-            const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double x[3];
+            for (int c = 0; c < 3; ++c) x[c] = v0[c] + M.S[k] * e1[c] + M.T[k] * e2[c];
             const double lam = local < 0 ? 1.0
                                          : (local == 0 ? 1.0 - M.S[k]
                                                        : (local == 1 ? M.S[k] - M.T[k] : M.T[k]));
-            const double f = M.W[k] * sg * lam / (4.0 * kPi * r);
-            // n(z) . grad_z of exp(i kappa r)/r with r = |x - z|:
-            //   (x - z).n / r^2 * (1 - i kappa r) exp(i kappa r) / r
-            const double dn = (d[0] * nz[0] + d[1] * nz[1] + d[2] * nz[2]) / (r * r);
+            const double wk = M.W[k] * sg * lam;
+            const double *zx = Z.x.data(), *zy = Z.y.data(), *zz = Z.z.data();
+            const double *nx = Z.nx.data(), *ny = Z.ny.data(), *nz = Z.nz.data();
             if (M.kappa == 0.0) {
-                gp += f;
-                gm += f * dn;
+                double *p = pr.data(), *q = mr.data();
+                for (int nu = 0; nu < m; ++nu) {
+                    const double d0 = x[0] - zx[nu], d1 = x[1] - zy[nu], d2 = x[2] - zz[nu];
+                    const double r = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                    const double f = wk / (4.0 * kPi * r);
+                    // n(z) . grad_z of 1/r with r = |x - z|: (x - z).n / r^2 / r
+                    const double dn = (d0 * nx[nu] + d1 * ny[nu] + d2 * nz[nu]) / (r * r);
+                    p[nu] += f;
+                    q[nu] += f * dn;
+                }
             } else {
-                const cplx e = std::polar(1.0, M.kappa * r);
-                gp += f * e;
-                gm += f * dn * cplx(1.0, -M.kappa * r) * e;
+                for (int nu = 0; nu < m; ++nu) {
+                    const double d0 = x[0] - zx[nu], d1 = x[1] - zy[nu], d2 = x[2] - zz[nu];
+                    const double r = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                    const double f = wk / (4.0 * kPi * r);
+                    // n(z) . grad_z of exp(i kappa r)/r with r = |x - z|:
+                    //   (x - z).n / r^2 * (1 - i kappa r) exp(i kappa r) / r
+                    const double dn = (d0 * nx[nu] + d1 * ny[nu] + d2 * nz[nu]) / (r * r);
+                    const cplx e = std::polar(1.0, M.kappa * r);
+                    gp[nu] += f * e;
+                    gm[nu] += f * dn * cplx(1.0, -M.kappa * r) * e;
+                }
             }
         }
     };
@@ -112,6 +143,11 @@ void basis_integrals(const HostMesh &M, int index, const double *z, const double
             tri(tr, tv[0] == index ? 0 : (tv[1] == index ? 1 : 2));
         }
     }
+    if (M.kappa == 0.0)
+        for (int nu = 0; nu < m; ++nu) {
+            gp[nu] += pr[nu];
+            gm[nu] += mr[nu];
+        }
 }
 
 void grow_box(const HostMesh &M, int index, double *lo, double *hi)
@@ -193,7 +229,8 @@ std::vector<int32_t> cluster_pivots(const HostMesh &M, const Tree &T, int c,
         whi[d] = hi[d] + 0.5 * delta;
     }
     const int q = (int)g.size();
-    std::vector<double> Z, N, Wq;
+    BoxPoints Z;
+    std::vector<double> Wq;
     for (int ax = 0; ax < 3; ++ax)
         for (int side = 0; side < 2; ++side) {
             const int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
@@ -205,21 +242,26 @@ std::vector<int32_t> cluster_pivots(const HostMesh &M, const Tree &T, int c,
                     z[a1] = wlo[a1] + g[i] * len1;
                     z[a2] = wlo[a2] + g[j] * len2;
                     n[ax] = side ? 1.0 : -1.0;
-                    Z.insert(Z.end(), z, z + 3);
-                    N.insert(N.end(), n, n + 3);
+                    Z.x.push_back(z[0]);
+                    Z.y.push_back(z[1]);
+                    Z.z.push_back(z[2]);
+                    Z.nx.push_back(n[0]);
+                    Z.ny.push_back(n[1]);
+                    Z.nz.push_back(n[2]);
                     Wq.push_back(gw[i] * gw[j] * len1 * len2);
                 }
         }
     const int m = (int)Wq.size(), rn = (int)rows.size();
-    std::vector<cplx> A((size_t)rn * 2 * m);
-    for (int i = 0; i < rn; ++i)
+    Z.m = m;
+    std::vector<cplx> A((size_t)rn * 2 * m), gp(m), gm(m);
+    for (int i = 0; i < rn; ++i) {
+        basis_integrals(M, rows[i], Z, gp.data(), gm.data());
         for (int nu = 0; nu < m; ++nu) {
-            cplx gp, gm;
-            basis_integrals(M, rows[i], &Z[3 * nu], &N[3 * nu], gp, gm);
             const double sw = std::sqrt(Wq[nu]);
-            A[(size_t)i * 2 * m + nu] = sw * gp;
-            A[(size_t)i * 2 * m + m + nu] = sw * delta * gm;
+            A[(size_t)i * 2 * m + nu] = sw * gp[nu];
+            A[(size_t)i * 2 * m + m + nu] = sw * delta * gm[nu];
         }
+    }
     std::vector<int32_t> out;
     for (int r : aca_complete(A, rn, 2 * m, eps, max_rank)) out.push_back(rows[r]);
     std::sort(out.begin(), out.end());
