@@ -165,31 +165,69 @@ void grow_box(const HostMesh &M, int index, double *lo, double *hi)
         for (int64_t k = M.vt_ptr[index]; k < M.vt_ptr[index + 1]; ++k) add_tri(M.vt_tri[k]);
 }
 
+// Position of the entry of largest magnitude, the first in row-major order
+// among equals (bi = -1 if every entry is zero).  Real entries compare by
+// fabs.  Complex entries compare by std::abs (hypot); a first pass over the
+// squared magnitudes finds the largest, and only entries within a relative
+// 1e-12 of it (the hypot maximum is among them: hypot and the square root of
+// the squared magnitude differ by a few ulps) are compared by std::abs, in
+// the same order, so the choice is the one of a full std::abs scan.
+void largest(const std::vector<double> &A, int rows, int cols, int &bi, int &bj, double &best)
+{
+    bi = bj = -1;
+    best = 0.0;
+    for (int i = 0; i < rows; ++i)
+        for (int j = 0; j < cols; ++j) {
+            const double a = std::fabs(A[(size_t)i * cols + j]);
+            if (a > best) {
+                best = a;
+                bi = i;
+                bj = j;
+            }
+        }
+}
+
+void largest(const std::vector<cplx> &A, int rows, int cols, int &bi, int &bj, double &best)
+{
+    const size_t n = (size_t)rows * cols;
+    double top = 0.0;
+    for (size_t k = 0; k < n; ++k) top = std::max(top, std::norm(A[k]));
+    // squared magnitudes that underflow: compare every entry by std::abs
+    const double floor = top > 1e-280 ? top * (1.0 - 1e-12) : 0.0;
+    bi = bj = -1;
+    best = 0.0;
+    for (int i = 0; i < rows; ++i)
+        for (int j = 0; j < cols; ++j) {
+            const cplx &x = A[(size_t)i * cols + j];
+            if (std::norm(x) < floor) continue;
+            const double a = std::abs(x);
+            if (a > best) {
+                best = a;
+                bi = i;
+                bj = j;
+            }
+        }
+}
+
 // Cross approximation with complete pivoting of the rows x cols matrix A
 // (row-major, overwritten by its residual); returns the pivot rows in the
-// order they were chosen.
-std::vector<int> aca_complete(std::vector<cplx> &A, int rows, int cols, double eps, int max_rank)
+// order they were chosen.  T = double for real matrices (kappa = 0), whose
+// arithmetic is that of the complex form with zero imaginary parts.
+template <class T>
+std::vector<int> aca_complete(std::vector<T> &A, int rows, int cols, double eps, int max_rank)
 {
     std::vector<int> piv;
     double first = 0.0;
-    std::vector<cplx> colv(rows), rowv(cols);
+    std::vector<T> colv(rows), rowv(cols);
     for (int k = 0; k < std::min(max_rank, std::min(rows, cols)); ++k) {
-        int bi = -1, bj = -1;
-        double best = 0.0;
-        for (int i = 0; i < rows; ++i)
-            for (int j = 0; j < cols; ++j) {
-                const double a = std::abs(A[(size_t)i * cols + j]);
-                if (a > best) {
-                    best = a;
-                    bi = i;
-                    bj = j;
-                }
-            }
+        int bi, bj;
+        double best;
+        largest(A, rows, cols, bi, bj, best);
         if (bi < 0) break;
         if (k == 0) first = best;
         else if (best <= eps * first) break;
         piv.push_back(bi);
-        const cplx p = A[(size_t)bi * cols + bj];
+        const T p = A[(size_t)bi * cols + bj];
         for (int i = 0; i < rows; ++i) colv[i] = A[(size_t)i * cols + bj] / p;
         for (int j = 0; j < cols; ++j) rowv[j] = A[(size_t)bi * cols + j];
         for (int i = 0; i < rows; ++i) {
@@ -262,8 +300,17 @@ std::vector<int32_t> cluster_pivots(const HostMesh &M, const Tree &T, int c,
             A[(size_t)i * 2 * m + m + nu] = sw * delta * gm[nu];
         }
     }
+    std::vector<int> chosen;
+    if (M.kappa == 0.0) {
+        // real matrix: the same values as the real parts of the complex form
+        std::vector<double> Ar(A.size());
+        for (size_t k = 0; k < A.size(); ++k) Ar[k] = A[k].real();
+        chosen = aca_complete(Ar, rn, 2 * m, eps, max_rank);
+    } else {
+        chosen = aca_complete(A, rn, 2 * m, eps, max_rank);
+    }
     std::vector<int32_t> out;
-    for (int r : aca_complete(A, rn, 2 * m, eps, max_rank)) out.push_back(rows[r]);
+    for (int r : chosen) out.push_back(rows[r]);
     std::sort(out.begin(), out.end());
     return out;
 }
