@@ -1099,14 +1099,17 @@ def green_workload(pkg, w, gauss_per_face=4, eps=1e-6):
     off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
     return {"row_ptr": row_ptr, "rows": np.concatenate(rows).astype(np.int32), "pt_ptr": pt_ptr,
             "z": z, "nz": nz, "sp": sp, "sm": sm, "off": off, "total": int(sizes.sum()),
-            "gca_s": gca_s}
+            "gca_s": gca_s, "piv_ptr": pp, "piv_idx": pi}
 
 
 def measure_green(torch, pkg, ctx, mid, w, dev, stream, steps, warmup):
     """Times bem_green_matrices on the A_t the host GCA forms for the
     workload's tree (green_workload), Laplace and Helmholtz kappa = 8: `warmup`
     untimed launches, then `steps` launches, each bracketed by CUDA events on
-    the context's stream, L2 flushed (256 MiB write, untimed) before each."""
+    the context's stream, L2 flushed (256 MiB write, untimed) before each.
+    Then the whole GCA with its A_t from the device (bem_gca_pivots_device,
+    wall time, best of 3) beside the host GCA's time, and the number of
+    clusters whose pivots differ from the host GCA's."""
     G = green_workload(pkg, w)
     d = {k: torch.as_tensor(G[k], device=dev) for k in ("row_ptr", "rows", "pt_ptr")}
     d.update({k: torch.as_tensor(G[k], dtype=torch.float64, device=dev)
@@ -1154,6 +1157,22 @@ def measure_green(torch, pkg, ctx, mid, w, dev, stream, steps, warmup):
                                     "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz"}}
         del out
     del flush
+    # the GCA with every level's A_t from the device and the cross approximation
+    # on the host (bem_gca_pivots_device), beside the host GCA's own time
+    part = w.partition
+    ptr, idx = part.cluster_csr()
+    times = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        dpp, dpi = ctx.bem_gca_pivots_device(mid, w.mesh.verts, w.mesh.tris, w.basis, ptr, idx,
+                                             part.son_array(), kappa=0.0, gauss_per_face=4,
+                                             eps=1e-6, max_rank=w.meta["rank"])
+        times.append(time.perf_counter() - t0)
+    hpp, hpi = G["piv_ptr"], G["piv_idx"]
+    differ = sum(1 for c in range(len(hpp) - 1)
+                 if not np.array_equal(hpi[hpp[c]:hpp[c + 1]], dpi[dpp[c]:dpp[c + 1]]))
+    res["gca_device"] = {"seconds": min(times), "host_gca_seconds": G["gca_s"],
+                         "clusters": len(hpp) - 1, "clusters_with_other_pivots": differ}
     n_rows = int(G["row_ptr"][-1])
     res["workload"] = (f"A_t = (A_t+, A_t-) of all {len(m_c)} clusters of the {w.mesh.nt}-triangle "
                        f"{w.basis.upper()} tree (leaves with their indices, other clusters with "

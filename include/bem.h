@@ -431,6 +431,28 @@ typedef struct {
 
 int bem_green_matrices(bem_ctx *ctx, const bem_green_job *job);
 
+/* GCA pivots with the Green matrices on the device: the pivots of
+ * bem_gca_pivots (same arguments, same host arrays and outputs), with every
+ * A_t assembled by the kernel of bem_green_matrices (FP64, Radon's 7 points
+ * per support triangle) instead of on the host.  The tree is processed level by
+ * level from the deepest: a level's A_t in one launch, copied back, and their
+ * cross approximation on host threads, as in bem_gca_pivots.  The pivots equal
+ * those of bem_gca_pivots except where rounding of A_t's entries decides between
+ * two candidates of equal magnitude.
+ *   ctx, mesh_id  the context and the id of the same mesh uploaded with
+ *                 bem_mesh_upload (vertex and triangle counts and basis must
+ *                 match; the host arrays give the clusters' boxes)
+ * Synchronises the context's stream once per level.  Allocates one device
+ * buffer for the largest level and frees it before returning.  Errors: those
+ * of bem_gca_pivots; BEM_ERR_INVALID_ARG for an unknown or different mesh;
+ * BEM_ERR_CUDA / BEM_ERR_OOM from the device. */
+int bem_gca_pivots_device(bem_ctx *ctx, int32_t mesh_id, const double *verts, int64_t nv,
+                          const int32_t *tris, int64_t nt, int32_t basis, double kappa,
+                          const int32_t *cl_ptr, const int32_t *cl_idx, const int32_t *cl_son,
+                          int32_t n_clusters, int32_t gauss_per_face, double eps,
+                          int32_t max_rank, int32_t n_threads, int32_t *piv_ptr, int32_t *piv_idx,
+                          int64_t cap);
+
 /* ---- quadrature rules ------------------------------------------------------
  * Copies the library's 4D rule on D x D for a case (Section 2.2; case 0 =
  * disjoint pairs with regular_rule BEM_RULE_DUFFY / BEM_RULE_TRI7, 1 = common

@@ -31,7 +31,8 @@ EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_
            "bem_pivot_entries_absolute", "bem_mlp_create", "bem_mlp_destroy", "bem_mlp_num_params",
            "bem_mlp_set_params", "bem_mlp_get_params", "bem_mlp_gradients", "bem_mlp_train_step",
            "bem_mlp_infer", "bem_pair_features", "bem_set_order_model", "bem_learned_counts",
-           "bem_shard_blocks", "bem_gca_pivots", "bem_touching_pairs", "bem_green_matrices"]
+           "bem_shard_blocks", "bem_gca_pivots", "bem_touching_pairs", "bem_green_matrices",
+           "bem_gca_pivots_device"]
 ORDER_CLASSES = [("duffy", 2), ("tri7", 1), ("duffy", 4), ("duffy", 5), ("duffy", 6), ("duffy", 8)]
 ORDER_CLASS_POINTS = [16, 49, 256, 625, 1296, 4096]
 PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE = 1, 2, 4
@@ -138,6 +139,7 @@ def load():
                                    ctypes.c_double, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
                                    ctypes.c_int64]
+    lib.bem_gca_pivots_device.argtypes = [_vp, ctypes.c_int32] + lib.bem_gca_pivots.argtypes
     lib.bem_learned_counts.argtypes = [_vp, P(ctypes.c_int64)]
     lib.bem_plan_create.argtypes = [_vp, P(bem_block_job), ctypes.c_int32, P(bem_block_job),
                                     ctypes.c_int32, ctypes.c_int32, P(_vp)]
@@ -209,8 +211,10 @@ def bem_touching_pairs(tris, nv: int):
 
 def bem_gca_pivots(verts, tris, basis: str, cl_ptr, cl_idx, cl_son, kappa: float = 0.0,
                    gauss_per_face: int = 4, eps: float = 1e-6, max_rank: int = 16,
-                   n_threads: int = 0):
-    """GCA pivots of every cluster (host only): cluster CSR (piv_ptr, piv_idx) int32."""
+                   n_threads: int = 0, _device_gca=None):
+    """GCA pivots of every cluster (host only): cluster CSR (piv_ptr, piv_idx) int32.
+    (Context.bem_gca_pivots_device passes _device_gca: the same call with the
+    Green matrices on the device.)"""
     v = np.ascontiguousarray(verts, np.float64)
     t = np.ascontiguousarray(tris, np.int32)
     ptr = np.ascontiguousarray(cl_ptr, np.int32)
@@ -221,12 +225,12 @@ def bem_gca_pivots(verts, tris, basis: str, cl_ptr, cl_idx, cl_son, kappa: float
         raise BemError(-1, "cl_son must be (n_clusters, 2)")
     piv_ptr = np.zeros(nc + 1, np.int32)
     piv_idx = np.zeros(max(1, nc * max_rank), np.int32)
-    rc = load().bem_gca_pivots(v.ctypes.data_as(_vp), len(v), t.ctypes.data_as(_vp), len(t),
-                               BASES[basis], float(kappa), ptr.ctypes.data_as(_vp),
-                               idx.ctypes.data_as(_vp), son.ctypes.data_as(_vp), nc,
-                               int(gauss_per_face), float(eps), int(max_rank), int(n_threads),
-                               piv_ptr.ctypes.data_as(_vp), piv_idx.ctypes.data_as(_vp),
-                               piv_idx.size)
+    args = (v.ctypes.data_as(_vp), len(v), t.ctypes.data_as(_vp), len(t), BASES[basis],
+            float(kappa), ptr.ctypes.data_as(_vp), idx.ctypes.data_as(_vp),
+            son.ctypes.data_as(_vp), nc, int(gauss_per_face), float(eps), int(max_rank),
+            int(n_threads), piv_ptr.ctypes.data_as(_vp), piv_idx.ctypes.data_as(_vp),
+            piv_idx.size)
+    rc = _device_gca(*args) if _device_gca is not None else load().bem_gca_pivots(*args)
     if rc != BEM_OK:
         raise BemError(rc, "bad GCA arguments")
     return piv_ptr, piv_idx[: piv_ptr[-1]].copy()
@@ -392,6 +396,20 @@ class Context:
     def bem_green_matrices(self, job):
         c = job.to_c()
         self._check(self.lib.bem_green_matrices(self.h, ctypes.byref(c)))
+
+    def bem_gca_pivots_device(self, mesh_id, verts, tris, basis: str, cl_ptr, cl_idx, cl_son,
+                              kappa: float = 0.0, gauss_per_face: int = 4, eps: float = 1e-6,
+                              max_rank: int = 16, n_threads: int = 0):
+        """bem_gca_pivots with every Green matrix A_t assembled on the device
+        (mesh_id: the same mesh, uploaded); cluster CSR (piv_ptr, piv_idx)."""
+        def call(*args):
+            return self.lib.bem_gca_pivots_device(self.h, int(mesh_id), *args)
+        try:
+            return bem_gca_pivots(verts, tris, basis, cl_ptr, cl_idx, cl_son, kappa=kappa,
+                                  gauss_per_face=gauss_per_face, eps=eps, max_rank=max_rank,
+                                  n_threads=n_threads, _device_gca=call)
+        except BemError as e:
+            raise BemError(e.code, self.lib.bem_last_error(self.h).decode() or str(e)) from None
 
     def bem_coupling_blocks(self, jobs):
         arr = (bem_block_job * len(jobs))(*[j.to_c() for j in jobs])

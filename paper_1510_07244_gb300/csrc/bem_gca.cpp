@@ -28,6 +28,7 @@
 #include <atomic>
 #include <cmath>
 #include <complex>
+#include <functional>
 #include <thread>
 #include <vector>
 
@@ -242,33 +243,43 @@ struct Tree {
     const int32_t *ptr, *idx, *son;
 };
 
-// Pivots of cluster c, given its sons' pivots.
-std::vector<int32_t> cluster_pivots(const HostMesh &M, const Tree &T, int c,
-                                    const std::vector<std::vector<int32_t>> &piv,
-                                    const std::vector<double> &g, const std::vector<double> &gw,
-                                    double eps, int max_rank)
-{
+// The Green problem of cluster c (Section 2.3): its rows (all indices of a
+// leaf; otherwise its sons' pivots, first son first), the points z_nu of the
+// boundary of omega_t with outward normals and weights w_nu, and delta_t.
+// A cluster without rows gets no points.
+struct ClusterGreen {
     std::vector<int32_t> rows;
+    BoxPoints Z;
+    std::vector<double> Wq;
+    double delta = 0.0;
+};
+
+ClusterGreen cluster_green(const HostMesh &M, const Tree &T, int c,
+                           const std::vector<std::vector<int32_t>> &piv,
+                           const std::vector<double> &g, const std::vector<double> &gw)
+{
+    ClusterGreen G;
+    std::vector<int32_t> &rows = G.rows;
     const int s0 = T.son[2 * c], s1 = T.son[2 * c + 1];
     if (s0 < 0 && s1 < 0) rows.assign(T.idx + T.ptr[c], T.idx + T.ptr[c + 1]);
     else
         for (int s : {s0, s1})
             if (s >= 0) rows.insert(rows.end(), piv[s].begin(), piv[s].end());
-    if (rows.empty()) return rows;
+    if (rows.empty()) return G;
 
     double lo[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL}, hi[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
     for (int32_t k = T.ptr[c]; k < T.ptr[c + 1]; ++k) grow_box(M, T.idx[k], lo, hi);
     const double delta = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) +
                                    (hi[1] - lo[1]) * (hi[1] - lo[1]) +
                                    (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    G.delta = delta;
     double wlo[3], whi[3];
     for (int d = 0; d < 3; ++d) {
         wlo[d] = lo[d] - 0.5 * delta;
         whi[d] = hi[d] + 0.5 * delta;
     }
     const int q = (int)g.size();
-    BoxPoints Z;
-    std::vector<double> Wq;
+    BoxPoints &Z = G.Z;
     for (int ax = 0; ax < 3; ++ax)
         for (int side = 0; side < 2; ++side) {
             const int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
@@ -286,20 +297,35 @@ std::vector<int32_t> cluster_pivots(const HostMesh &M, const Tree &T, int c,
                     Z.nx.push_back(n[0]);
                     Z.ny.push_back(n[1]);
                     Z.nz.push_back(n[2]);
-                    Wq.push_back(gw[i] * gw[j] * len1 * len2);
+                    G.Wq.push_back(gw[i] * gw[j] * len1 * len2);
                 }
         }
-    const int m = (int)Wq.size(), rn = (int)rows.size();
-    Z.m = m;
-    std::vector<cplx> A((size_t)rn * 2 * m), gp(m), gm(m);
+    Z.m = (int)G.Wq.size();
+    return G;
+}
+
+// A_t = (A_t+, A_t-) on the host, row-major rows x 2m: sqrt(w_nu) int phi_i g,
+// then sqrt(w_nu) delta_t int phi_i dg/dn(z_nu).
+void host_green_matrix(const HostMesh &M, const ClusterGreen &G, std::vector<cplx> &A)
+{
+    const int m = G.Z.m, rn = (int)G.rows.size();
+    A.assign((size_t)rn * 2 * m, cplx(0.0));
+    std::vector<cplx> gp(m), gm(m);
     for (int i = 0; i < rn; ++i) {
-        basis_integrals(M, rows[i], Z, gp.data(), gm.data());
+        basis_integrals(M, G.rows[i], G.Z, gp.data(), gm.data());
         for (int nu = 0; nu < m; ++nu) {
-            const double sw = std::sqrt(Wq[nu]);
+            const double sw = std::sqrt(G.Wq[nu]);
             A[(size_t)i * 2 * m + nu] = sw * gp[nu];
-            A[(size_t)i * 2 * m + m + nu] = sw * delta * gm[nu];
+            A[(size_t)i * 2 * m + m + nu] = sw * G.delta * gm[nu];
         }
     }
+}
+
+// The cluster's pivots (ascending indices) by cross approximation on A_t.
+std::vector<int32_t> pivots_of(const HostMesh &M, const ClusterGreen &G, std::vector<cplx> &A,
+                               double eps, int max_rank)
+{
+    const int m = G.Z.m, rn = (int)G.rows.size();
     std::vector<int> chosen;
     if (M.kappa == 0.0) {
         // real matrix: the same values as the real parts of the complex form
@@ -310,18 +336,54 @@ std::vector<int32_t> cluster_pivots(const HostMesh &M, const Tree &T, int c,
         chosen = aca_complete(A, rn, 2 * m, eps, max_rank);
     }
     std::vector<int32_t> out;
-    for (int r : chosen) out.push_back(rows[r]);
+    for (int r : chosen) out.push_back(G.rows[r]);
     std::sort(out.begin(), out.end());
     return out;
 }
 
-}  // namespace
+// Pivots of cluster c, given its sons' pivots.
+std::vector<int32_t> cluster_pivots(const HostMesh &M, const Tree &T, int c,
+                                    const std::vector<std::vector<int32_t>> &piv,
+                                    const std::vector<double> &g, const std::vector<double> &gw,
+                                    double eps, int max_rank)
+{
+    const ClusterGreen G = cluster_green(M, T, c, piv, g, gw);
+    if (G.rows.empty()) return {};
+    std::vector<cplx> A;
+    host_green_matrix(M, G, A);
+    return pivots_of(M, G, A, eps, max_rank);
+}
 
-extern "C" int bem_gca_pivots(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
-                              int32_t basis, double kappa, const int32_t *cl_ptr,
-                              const int32_t *cl_idx, const int32_t *cl_son, int32_t n_clusters,
-                              int32_t gauss_per_face, double eps, int32_t max_rank,
-                              int32_t n_threads, int32_t *piv_ptr, int32_t *piv_idx, int64_t cap)
+// Runs body(k) for k = 0 .. n-1 on up to nthr threads (the calling one included).
+template <class F>
+void parallel_for(size_t n, int nthr, F &&body)
+{
+    std::atomic<size_t> next(0);
+    auto work = [&]() {
+        for (size_t k; (k = next.fetch_add(1)) < n;) body(k);
+    };
+    const int t = (int)std::min<size_t>((size_t)std::max(1, nthr), n);
+    std::vector<std::thread> pool;
+    for (int k = 1; k < t; ++k) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
+}
+
+// Checked inputs of a GCA run: the mesh, the tree, every cluster's depth.
+struct GcaRun {
+    HostMesh M;
+    Tree T{nullptr, nullptr, nullptr};
+    std::vector<int> depth;
+    int max_depth = 0;
+    std::vector<double> g, gw;
+    int nthr = 1;
+};
+
+int gca_setup(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, int32_t basis,
+              double kappa, const int32_t *cl_ptr, const int32_t *cl_idx, const int32_t *cl_son,
+              int32_t n_clusters, int32_t gauss_per_face, double eps, int32_t max_rank,
+              int32_t n_threads, const int32_t *piv_ptr, const int32_t *piv_idx, int64_t cap,
+              GcaRun &R)
 {
     if (!verts || !tris || nv < 1 || nt < 1 || (basis != BEM_P0 && basis != BEM_P1) ||
         !std::isfinite(kappa) || kappa < 0.0 || !cl_ptr || !cl_idx || !cl_son || n_clusters < 1 ||
@@ -345,7 +407,8 @@ extern "C" int bem_gca_pivots(const double *verts, int64_t nv, const int32_t *tr
         if (cl_idx[k] < 0 || cl_idx[k] >= nidx) return BEM_ERR_INVALID_ARG;
 
     // depth of every cluster; a cluster with two parents or a cycle is an error
-    std::vector<int> depth(n_clusters, -1), parent(n_clusters, -1);
+    R.depth.assign(n_clusters, -1);
+    std::vector<int> parent(n_clusters, -1);
     for (int c = 0; c < n_clusters; ++c)
         for (int s = 0; s < 2; ++s) {
             const int x = cl_son[2 * c + s];
@@ -353,18 +416,18 @@ extern "C" int bem_gca_pivots(const double *verts, int64_t nv, const int32_t *tr
             if (parent[x] >= 0) return BEM_ERR_INVALID_ARG;
             parent[x] = c;
         }
-    int max_depth = 0;
+    R.max_depth = 0;
     for (int c = 0; c < n_clusters; ++c) {
         int d = 0, x = c;
         while (parent[x] >= 0) {
             x = parent[x];
             if (++d > n_clusters) return BEM_ERR_INVALID_ARG;
         }
-        depth[c] = d;
-        max_depth = std::max(max_depth, d);
+        R.depth[c] = d;
+        R.max_depth = std::max(R.max_depth, d);
     }
 
-    HostMesh M;
+    HostMesh &M = R.M;
     M.v = verts;
     M.t = tris;
     M.nv = nv;
@@ -381,34 +444,119 @@ extern "C" int bem_gca_pivots(const double *verts, int64_t nv, const int32_t *tr
         for (int64_t t = 0; t < nt; ++t)
             for (int k = 0; k < 3; ++k) M.vt_tri[fill[tris[3 * t + k]]++] = (int32_t)t;
     }
-    std::vector<double> g, gw;
-    bem::gauss_legendre_unit(gauss_per_face, g, gw);
+    bem::gauss_legendre_unit(gauss_per_face, R.g, R.gw);
+    R.T = Tree{cl_ptr, cl_idx, cl_son};
+    R.nthr = n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+    return BEM_OK;
+}
 
-    const Tree T{cl_ptr, cl_idx, cl_son};
-    std::vector<std::vector<int32_t>> piv(n_clusters);
-    const int nthr =
-        n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
-    for (int d = max_depth; d >= 0; --d) {
-        std::vector<int> level;
-        for (int c = 0; c < n_clusters; ++c)
-            if (depth[c] == d) level.push_back(c);
-        std::atomic<size_t> next(0);
-        auto work = [&]() {
-            for (size_t k; (k = next.fetch_add(1)) < level.size();)
-                piv[level[k]] = cluster_pivots(M, T, level[k], piv, g, gw, eps, max_rank);
-        };
-        const int n_level = std::min<int>(nthr, (int)level.size());
-        std::vector<std::thread> pool;
-        for (int k = 1; k < n_level; ++k) pool.emplace_back(work);
-        work();
-        for (auto &th : pool) th.join();
-    }
+std::vector<int> level_clusters(const GcaRun &R, int d)
+{
+    std::vector<int> level;
+    for (int c = 0; c < (int)R.depth.size(); ++c)
+        if (R.depth[c] == d) level.push_back(c);
+    return level;
+}
+
+int gca_write(const std::vector<std::vector<int32_t>> &piv, int32_t *piv_ptr, int32_t *piv_idx,
+              int64_t cap)
+{
     int64_t at = 0;
     piv_ptr[0] = 0;
-    for (int c = 0; c < n_clusters; ++c) {
+    for (size_t c = 0; c < piv.size(); ++c) {
         if (at + (int64_t)piv[c].size() > cap) return BEM_ERR_INVALID_ARG;
         for (int32_t v : piv[c]) piv_idx[at++] = v;
         piv_ptr[c + 1] = (int32_t)at;
     }
     return BEM_OK;
 }
+
+}  // namespace
+
+extern "C" int bem_gca_pivots(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                              int32_t basis, double kappa, const int32_t *cl_ptr,
+                              const int32_t *cl_idx, const int32_t *cl_son, int32_t n_clusters,
+                              int32_t gauss_per_face, double eps, int32_t max_rank,
+                              int32_t n_threads, int32_t *piv_ptr, int32_t *piv_idx, int64_t cap)
+{
+    GcaRun R;
+    const int rc = gca_setup(verts, nv, tris, nt, basis, kappa, cl_ptr, cl_idx, cl_son, n_clusters,
+                             gauss_per_face, eps, max_rank, n_threads, piv_ptr, piv_idx, cap, R);
+    if (rc != BEM_OK) return rc;
+    std::vector<std::vector<int32_t>> piv(n_clusters);
+    for (int d = R.max_depth; d >= 0; --d) {
+        const std::vector<int> level = level_clusters(R, d);
+        parallel_for(level.size(), R.nthr, [&](size_t k) {
+            piv[level[k]] = cluster_pivots(R.M, R.T, level[k], piv, R.g, R.gw, eps, max_rank);
+        });
+    }
+    return gca_write(piv, piv_ptr, piv_idx, cap);
+}
+
+namespace bem {
+
+int gca_pivots_levels(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                      int32_t basis, double kappa, const int32_t *cl_ptr, const int32_t *cl_idx,
+                      const int32_t *cl_son, int32_t n_clusters, int32_t gauss_per_face,
+                      double eps, int32_t max_rank, int32_t n_threads,
+                      const GreenLevelProducer &produce, int32_t *piv_ptr, int32_t *piv_idx,
+                      int64_t cap)
+{
+    GcaRun R;
+    int rc = gca_setup(verts, nv, tris, nt, basis, kappa, cl_ptr, cl_idx, cl_son, n_clusters,
+                       gauss_per_face, eps, max_rank, n_threads, piv_ptr, piv_idx, cap, R);
+    if (rc != BEM_OK) return rc;
+    const bool cplx_out = kappa != 0.0;
+    std::vector<std::vector<int32_t>> piv(n_clusters);
+    for (int d = R.max_depth; d >= 0; --d) {
+        const std::vector<int> level = level_clusters(R, d);
+        std::vector<ClusterGreen> G(level.size());
+        parallel_for(level.size(), R.nthr, [&](size_t k) {
+            G[k] = cluster_green(R.M, R.T, level[k], piv, R.g, R.gw);
+        });
+        // the level in the layout of bem_green_matrices: rows and points per
+        // cluster, factors sqrt(w) and sqrt(w) delta_t, one block per cluster
+        GreenLevel L;
+        L.row_ptr.push_back(0);
+        L.pt_ptr.push_back(0);
+        for (const ClusterGreen &C : G) {
+            L.rows.insert(L.rows.end(), C.rows.begin(), C.rows.end());
+            L.row_ptr.push_back((int32_t)L.rows.size());
+            for (int nu = 0; nu < C.Z.m; ++nu) {
+                L.z.insert(L.z.end(), {C.Z.x[nu], C.Z.y[nu], C.Z.z[nu]});
+                L.nz.insert(L.nz.end(), {C.Z.nx[nu], C.Z.ny[nu], C.Z.nz[nu]});
+                const double sw = std::sqrt(C.Wq[nu]);
+                L.sp.push_back(sw);
+                L.sm.push_back(sw * C.delta);
+            }
+            L.pt_ptr.push_back((int32_t)(L.z.size() / 3));
+            L.off.push_back(L.total);
+            L.total += 2 * (int64_t)C.rows.size() * C.Z.m;
+        }
+        std::vector<double> out;
+        if (L.total > 0) {
+            out.assign((size_t)L.total * (cplx_out ? 2 : 1), 0.0);
+            if ((rc = produce(L, cplx_out, out)) != BEM_OK) return rc;
+        }
+        parallel_for(level.size(), R.nthr, [&](size_t k) {
+            const ClusterGreen &C = G[k];
+            const int rn = (int)C.rows.size(), m = C.Z.m;
+            if (rn == 0) {
+                piv[level[k]].clear();
+                return;
+            }
+            // block k: column-major rn x 2m at off[k] -> row-major A_t
+            std::vector<cplx> A((size_t)rn * 2 * m);
+            for (int col = 0; col < 2 * m; ++col)
+                for (int i = 0; i < rn; ++i) {
+                    const size_t e = (size_t)L.off[k] + (size_t)i + (size_t)col * rn;
+                    A[(size_t)i * 2 * m + col] =
+                        cplx_out ? cplx(out[2 * e], out[2 * e + 1]) : cplx(out[e], 0.0);
+                }
+            piv[level[k]] = pivots_of(R.M, C, A, eps, max_rank);
+        });
+    }
+    return gca_write(piv, piv_ptr, piv_idx, cap);
+}
+
+}  // namespace bem

@@ -253,3 +253,88 @@ extern "C" int bem_green_matrices(bem_ctx *ctx, const bem_green_job *job)
     if (e != cudaSuccess) return api_cuda_fail(ctx, e, "green kernel");
     return BEM_OK;
 }
+
+extern "C" int bem_gca_pivots_device(bem_ctx *ctx, int32_t mesh_id, const double *verts,
+                                     int64_t nv, const int32_t *tris, int64_t nt, int32_t basis,
+                                     double kappa, const int32_t *cl_ptr, const int32_t *cl_idx,
+                                     const int32_t *cl_son, int32_t n_clusters,
+                                     int32_t gauss_per_face, double eps, int32_t max_rank,
+                                     int32_t n_threads, int32_t *piv_ptr, int32_t *piv_idx,
+                                     int64_t cap)
+{
+    using namespace bem;
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    auto it = ctx->meshes.find(mesh_id);
+    if (it == ctx->meshes.end()) return api_fail(ctx, BEM_ERR_INVALID_ARG, "unknown mesh id");
+    const Mesh *mesh = it->second;
+    if (mesh->v.nv != nv || mesh->v.nt != nt || mesh->v.basis != basis)
+        return api_fail(ctx, BEM_ERR_INVALID_ARG,
+                        "bem_gca_pivots_device: the host mesh is not the uploaded one "
+                        "(vertex or triangle count, or basis)");
+    Rule2D R;
+    std::memset(&R, 0, sizeof R);
+    make_rule2d(BEM_RULE_TRI7, 0, R);
+    // one device buffer for a level's inputs and blocks, grown for the largest level
+    struct Scratch {
+        char *p = nullptr;
+        size_t bytes = 0;
+        ~Scratch()
+        {
+            if (p) cudaFree(p);
+        }
+    } S;
+    auto produce = [&](const GreenLevel &L, bool cplx_out, std::vector<double> &out) -> int {
+        auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+        const size_t n_cl = L.off.size();
+        const size_t parts[9] = {L.row_ptr.size() * 4, L.pt_ptr.size() * 4, L.rows.size() * 4,
+                                 L.z.size() * 8,       L.nz.size() * 8,     L.sp.size() * 8,
+                                 L.sm.size() * 8,      n_cl * 8,            out.size() * 8};
+        const void *src[8] = {L.row_ptr.data(), L.pt_ptr.data(), L.rows.data(), L.z.data(),
+                              L.nz.data(),      L.sp.data(),     L.sm.data(),   L.off.data()};
+        size_t at[9], need = 0;
+        for (int k = 0; k < 9; ++k) {
+            at[k] = need;
+            need += al(std::max<size_t>(parts[k], 1));
+        }
+        cudaError_t e = cudaSuccess;
+        if (need > S.bytes) {
+            if (S.p) cudaFree(S.p);
+            S.p = nullptr;
+            S.bytes = 0;
+            e = cudaMalloc((void **)&S.p, need);
+            if (e != cudaSuccess) return api_cuda_fail(ctx, e, "cudaMalloc(GCA level)");
+            S.bytes = need;
+        }
+        for (int k = 0; k < 8 && e == cudaSuccess; ++k)
+            if (parts[k] > 0)
+                e = cudaMemcpyAsync(S.p + at[k], src[k], parts[k], cudaMemcpyHostToDevice,
+                                    ctx->stream);
+        if (e != cudaSuccess) return api_cuda_fail(ctx, e, "GCA level upload");
+        GreenArgs a;
+        a.row_ptr = reinterpret_cast<const int32_t *>(S.p + at[0]);
+        a.pt_ptr = reinterpret_cast<const int32_t *>(S.p + at[1]);
+        a.row_idx = reinterpret_cast<const int32_t *>(S.p + at[2]);
+        a.z = reinterpret_cast<const double *>(S.p + at[3]);
+        a.nz = reinterpret_cast<const double *>(S.p + at[4]);
+        a.sp = reinterpret_cast<const double *>(S.p + at[5]);
+        a.sm = reinterpret_cast<const double *>(S.p + at[6]);
+        a.out_off = reinterpret_cast<const int64_t *>(S.p + at[7]);
+        a.out = S.p + at[8];
+        a.n_row_idx = (int64_t)L.rows.size();
+        a.n_points = (int64_t)L.sp.size();
+        a.out_len = L.total;
+        a.kappa = cplx_out ? kappa : 0.0;
+        {
+            ProfScope ps(ctx, "green");
+            e = cplx_out ? launch_green<true>(mesh->v, a, (int)n_cl, R, ctx->status, ctx->stream)
+                         : launch_green<false>(mesh->v, a, (int)n_cl, R, ctx->status, ctx->stream);
+        }
+        if (e != cudaSuccess) return api_cuda_fail(ctx, e, "green kernel");
+        e = cudaMemcpyAsync(out.data(), S.p + at[8], parts[8], cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess) return api_cuda_fail(ctx, e, "GCA level download");
+        return bem_sync(ctx);
+    };
+    return gca_pivots_levels(verts, nv, tris, nt, basis, kappa, cl_ptr, cl_idx, cl_son, n_clusters,
+                             gauss_per_face, eps, max_rank, n_threads, produce, piv_ptr, piv_idx,
+                             cap);
+}

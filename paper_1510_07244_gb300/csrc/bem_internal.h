@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <map>
 #include <string>
 #include <tuple>
@@ -135,6 +136,29 @@ void prof_accumulate(bem_ctx *ctx, const bem_prof_rec &r);
 // bem_plan.cpp: adds the unread launch times of plans run since the last read
 void plan_drain_profile(bem_ctx *ctx);
 void plan_forget(bem_ctx *ctx);   // context teardown
+
+// bem_gca.cpp: the GCA of a cluster tree level by level (deepest first), the
+// Green matrices A_t of each level from a producer.  A level is given in the
+// cluster-CSR layout of bem_green_matrices: cluster k's rows
+// rows[row_ptr[k] .. row_ptr[k+1]) (all indices of a leaf, the sons' pivots
+// otherwise), its box points z / normals nz (3 doubles each) with factors sp =
+// sqrt(w), sm = sqrt(w) delta_t, and its block at element off[k].
+struct GreenLevel {
+    std::vector<int32_t> row_ptr, rows, pt_ptr;
+    std::vector<double> z, nz, sp, sm;
+    std::vector<int64_t> off;
+    int64_t total = 0;
+};
+// Fills out (total doubles, or total (re, im) pairs when cplx_out) with the
+// level's blocks as bem_green_matrices writes them; returns BEM_OK or an error.
+using GreenLevelProducer =
+    std::function<int(const GreenLevel &L, bool cplx_out, std::vector<double> &out)>;
+int gca_pivots_levels(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                      int32_t basis, double kappa, const int32_t *cl_ptr, const int32_t *cl_idx,
+                      const int32_t *cl_son, int32_t n_clusters, int32_t gauss_per_face,
+                      double eps, int32_t max_rank, int32_t n_threads,
+                      const GreenLevelProducer &produce, int32_t *piv_ptr, int32_t *piv_idx,
+                      int64_t cap);
 
 // bem_rules.cpp
 bool gauss_legendre_unit(int q, std::vector<double> &x, std::vector<double> &w);

@@ -312,3 +312,42 @@ def _layout_one(lay, k):
     m = pt_ptr[k + 1] - pt_ptr[k]
     return (np.array([0, len(r)], np.int32), r, np.array([0, m], np.int32), z[p], nz[p], sp[p],
             sm[p], np.zeros(1, np.int64), 2 * len(r) * m)
+
+
+@pytest.mark.parametrize("basis,kappa", [("p0", 0.0), ("p1", 0.0), ("p0", 3.0), ("p1", 3.0)])
+def test_gca_with_device_green_matrices(ctx, pkg, basis, kappa):
+    """bem_gca_pivots_device (every level's A_t from the device, cross
+    approximation on the host) picks the pivots of the host GCA.  The mesh is
+    jittered, and on it the host pivots stay the same when every entry of A_t
+    is perturbed by 1e-14 relative, so rounding differences decide nothing."""
+    from synth.structure import build_block_partition
+    mesh = synth.jitter(synth.icosphere(3), 0.1, 11)
+    part = build_block_partition(mesh, basis, 16, 2.0)
+    ptr, idx = part.cluster_csr()
+    son = part.son_array()
+    host = pkg.bem_gca_pivots(mesh.verts, mesh.tris, basis, ptr, idx, son, kappa=kappa,
+                              gauss_per_face=3)
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, basis)
+    try:
+        dev = ctx.bem_gca_pivots_device(mid, mesh.verts, mesh.tris, basis, ptr, idx, son,
+                                        kappa=kappa, gauss_per_face=3)
+    finally:
+        ctx.bem_mesh_free(mid)
+    assert np.array_equal(host[0], dev[0]) and np.array_equal(host[1], dev[1])
+
+
+def test_gca_device_rejects_another_mesh(ctx, pkg):
+    """The uploaded mesh must be the one whose host arrays are passed."""
+    from synth.structure import build_block_partition
+    mesh = synth.icosphere(2)
+    part = build_block_partition(mesh, "p0", 16, 2.0)
+    ptr, idx = part.cluster_csr()
+    other = synth.icosphere(1)
+    mid = ctx.bem_mesh_upload(other.verts, other.tris, "p0")
+    try:
+        with pytest.raises(pkg.BemError) as e:
+            ctx.bem_gca_pivots_device(mid, mesh.verts, mesh.tris, "p0", ptr, idx,
+                                      part.son_array())
+        assert e.value.code == -1
+    finally:
+        ctx.bem_mesh_free(mid)
