@@ -458,17 +458,8 @@ int bem_mesh_upload(bem_ctx *ctx, const double *verts, int64_t nv, const int32_t
     std::vector<int> *lists = P.lists;
     // reject coordinates shared by two different vertex indices (such pairs
     // would be treated as disjoint although their triangles touch)
-    {
-        std::vector<int64_t> ord((size_t)nv);
-        for (int64_t v = 0; v < nv; ++v) ord[v] = v;
-        std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) {
-            return std::lexicographical_compare(verts + 3 * x, verts + 3 * x + 3, verts + 3 * y,
-                                                verts + 3 * y + 3);
-        });
-        for (int64_t k = 1; k < nv; ++k)
-            if (std::equal(verts + 3 * ord[k - 1], verts + 3 * ord[k - 1] + 3, verts + 3 * ord[k]))
-                return fail(ctx, BEM_ERR_DEGENERATE, "two vertex indices with equal coordinates");
-    }
+    if (find_duplicate_vertex(verts, nv) >= 0)
+        return fail(ctx, BEM_ERR_DEGENERATE, "two vertex indices with equal coordinates");
 
     cudaSetDevice(ctx->device);
     Mesh *m = new Mesh();

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <array>
 #include <climits>
+#include <cstring>
 #include <thread>
 #include <vector>
 
@@ -195,6 +196,38 @@ int plan_touching(const int32_t *tris, int64_t nt, int64_t nv, TouchPlan &P, con
         fill_range(tris, P, perm2, range_lo(r), range_lo(r + 1), case_at[(size_t)r].data());
     });
     return BEM_OK;
+}
+
+// Open addressing over the exact coordinate triples (linear probing, at most
+// half full).  -0.0 and +0.0 are equal under == and hash alike (x + 0.0 maps
+// -0.0 to +0.0); equal triples always probe the same chain, and a match is
+// confirmed by == on the coordinates themselves.
+int64_t find_duplicate_vertex(const double *verts, int64_t nv)
+{
+    size_t cap = 16;
+    while (cap < 2 * (size_t)nv) cap <<= 1;
+    std::vector<int64_t> slot(cap, -1);
+    auto bits = [](double x) {
+        x += 0.0;
+        uint64_t u;
+        std::memcpy(&u, &x, sizeof u);
+        return u;
+    };
+    auto mix = [](uint64_t z) {   // splitmix64 finaliser
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        return z ^ (z >> 31);
+    };
+    for (int64_t v = 0; v < nv; ++v) {
+        const double *p = verts + 3 * v;
+        size_t k = (size_t)mix(bits(p[0]) ^ mix(bits(p[1]) ^ mix(bits(p[2])))) & (cap - 1);
+        for (; slot[k] >= 0; k = (k + 1) & (cap - 1)) {
+            const double *q = verts + 3 * slot[k];
+            if (q[0] == p[0] && q[1] == p[1] && q[2] == p[2]) return v;
+        }
+        slot[k] = v;
+    }
+    return -1;
 }
 
 }  // namespace bem

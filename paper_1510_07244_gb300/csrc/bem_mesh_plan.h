@@ -28,4 +28,9 @@ struct TouchPlan {
 // *err when two triangles have the same three vertices.
 int plan_touching(const int32_t *tris, int64_t nt, int64_t nv, TouchPlan &P, const char **err);
 
+// The smallest vertex index v whose coordinates (verts[3v .. 3v+2], finite)
+// equal, coordinate by coordinate under ==, those of a vertex u < v, or -1 if
+// every vertex index has coordinates of its own.
+int64_t find_duplicate_vertex(const double *verts, int64_t nv);
+
 }  // namespace bem

@@ -157,3 +157,25 @@ def test_duplicate_found_in_any_range():
     with pytest.raises(pkg.BemError) as e:
         pkg.bem_touching_pairs(tris, m.nv)
     assert e.value.code == -5
+
+
+def test_duplicate_vertex_finder_against_brute_force(tmp_path):
+    """The upload's test for two vertex indices with equal coordinates (a
+    hash of the exact triples) agrees with a pairwise comparison on seeded
+    random vertex sets with planted duplicates and signed zeros
+    (tests/dup_vertex_check.cpp, built here with the host compiler)."""
+    import os
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(root, "paper_1510_07244_gb300", "csrc")
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None or not os.path.exists("/usr/local/cuda/include/cuda_runtime.h"):
+        pytest.skip("no host C++ compiler or CUDA headers")
+    exe = str(tmp_path / "dup_vertex_check")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I", os.path.join(root, "include"), "-I", csrc,
+                    "-I", "/usr/local/cuda/include", os.path.join(root, "tests", "dup_vertex_check.cpp"),
+                    os.path.join(csrc, "bem_mesh_plan.cpp"), os.path.join(csrc, "bem_rules.cpp"),
+                    "-o", exe, "-lpthread"], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
