@@ -131,6 +131,30 @@ def kernel_flops(w, counts, stats, precision):
     return {k: (f, p, PEAK_FP32 if p == "fp32" else PEAK_FP64) for k, (f, p) in out.items()}
 
 
+def step_rates(w, counts, stats, precision, ms_per_step):
+    """Triangle-pair integrals and quadrature points one step evaluates, and
+    their rates: regular pairs as the chosen form's kernels evaluate them (once
+    per block pair in the tile engines; once per entry and pair in the coupling
+    engine of the float forms on the piecewise-linear basis), touching pairs
+    once per mesh pair and case, for every operator."""
+    q = w.quad
+    npts_reg = (q.q_regular ** 2) ** 2 if q.regular_rule == "duffy" else 49
+    mixed = precision in ("mixed", "mixed_full")
+    laplace = all(o.kernel != "helmholtz_slp" for o in w.operators)
+    coupling = mixed and w.basis == "p1" and laplace
+    far = counts["far_entry_pairs"] if coupling else counts["far_regular_pairs"]
+    regular = counts["near_regular_pairs"] + far
+    touch_pairs = stats["n_vertex"] + stats["n_edge"] + stats["n_identical"]
+    touch_points = (stats["n_vertex"] * 2 * q.q_vertex ** 4 + stats["n_edge"] * 4 * q.q_edge ** 4 +
+                    stats["n_identical"] * 6 * q.q_identical ** 4)
+    n_ops = len(w.operators)
+    pairs = n_ops * (regular + touch_pairs)
+    points = n_ops * (regular * npts_reg + touch_points)
+    sec = ms_per_step / 1e3
+    return {"pair_integrals_per_step": pairs, "quadrature_points_per_step": points,
+            "pair_integrals_per_s": pairs / sec, "quadrature_points_per_s": points / sec}
+
+
 def block_costs(bs):
     """Cost of each block of a block set: its number of entries."""
     rs = np.diff(bs.row_ptr)[bs.blk_row]
@@ -581,6 +605,7 @@ def run_ours(args):
                              "max_row_scaled_err": rowerr,
                              "row_scaled": "|g - g_fp64| / max(|g_fp64|, 1e-3 row max)",
                              "entries_compared": entries_per_step},
+                "rates": step_rates(w, counts, stats, chosen, total_ms / steps_used),
                 "fp64_form": {"value": value64, "ms_per_step": ms64 / args.fp64_steps,
                               "steps": args.fp64_steps, "roofline": roof64, "kernels": per64},
                 "other_forms": other_forms,

@@ -96,3 +96,26 @@ def test_green_workload_is_the_gcas_row_sets(small_c2):
     assert G["total"] == sizes.sum()
     # operation count: a rule point costs more with the Helmholtz phase
     assert bench.green_flops(True, 7) > bench.green_flops(False, 7) > 7 * 30
+
+
+def test_step_rates_count_pairs_and_points(small_c2):
+    """Pair integrals and quadrature points per step: per operator, the regular
+    pairs as the form's kernels evaluate them plus every touching pair, each
+    with its rule's points; rates divide by the step time."""
+    w, counts = small_c2
+    stats = {"n_vertex": 30, "n_edge": 12, "n_identical": 5}
+    q = w.quad
+    touch = 30 + 12 + 5
+    tpts = 30 * 2 * q.q_vertex ** 4 + 12 * 4 * q.q_edge ** 4 + 5 * 6 * q.q_identical ** 4
+    npts = (q.q_regular ** 2) ** 2 if q.regular_rule == "duffy" else 49
+    n_ops = len(w.operators)
+    r64 = bench.step_rates(w, counts, stats, "fp64", 2.0)
+    reg64 = counts["near_regular_pairs"] + counts["far_regular_pairs"]
+    assert r64["pair_integrals_per_step"] == n_ops * (reg64 + touch)
+    assert r64["quadrature_points_per_step"] == n_ops * (reg64 * npts + tpts)
+    assert r64["pair_integrals_per_s"] == pytest.approx(r64["pair_integrals_per_step"] / 2e-3)
+    # the float forms evaluate P1 coupling entries pair by pair
+    rmx = bench.step_rates(w, counts, stats, "mixed_full", 2.0)
+    regmx = counts["near_regular_pairs"] + counts["far_entry_pairs"]
+    assert rmx["pair_integrals_per_step"] == n_ops * (regmx + touch)
+    assert counts["far_entry_pairs"] >= counts["far_regular_pairs"]
