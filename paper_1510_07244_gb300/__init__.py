@@ -2,8 +2,9 @@
 field and H2 coupling/pivot entries behind the C ABI of include/bem.h.
 
 The compute path is the CUDA library built by ``paper_1510_07244_gb300.build``;
-this package only marshals arguments to it (``_binding``) and, in
-``workloads``, assembles the synthetic benchmark inputs.
+this package only marshals arguments to it (``_binding``) and orchestrates the
+training of the quadrature-order model (``order_model``).  The synthetic
+inputs live in the separate ``synth`` package.
 """
 from ._binding import (Context, BlockJob, GreenJob, BemError, kernel_desc, quad_desc, load,
                        LIB_PATH, EXPORTS, KERNELS, BASES, RULES, bem_rule_points, PLAN_GRAPH,

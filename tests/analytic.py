@@ -167,3 +167,86 @@ def pair_reference(tri_a, tri_b, kernel, la=-1, lb=-1, n=64, p=5):
     assert np.sum(W[bad]) < 1e-30, "non-finite potential at a point with weight"
     val = np.where(bad, 0.0, val)
     return float(np.sum(W * fa * val))
+
+
+# ---------------------------------------------------------------------------
+# Odd powers of the distance, for the real part of the Helmholtz kernel.
+#
+# cos(kappa r)/r - 1/r = sum_{k>=1} (-1)^k kappa^(2k) r^(2k-1) / (2k)!, so the
+# real part of a Helmholtz single-layer integral minus the Laplace one is a
+# series of potentials P_n = int_T r^n dA with odd n >= 1.  With rho' = y - rho
+# in T's plane and r^2 = |rho'|^2 + w^2 the divergence theorem gives
+#     div(rho' r^n) = (n + 2) r^n - n w^2 r^(n-2)
+#  => (n + 2) P_n = n w^2 P_(n-2) + sum_e t0_e E_n(e),
+# and grad(r^(n+2)) = (n + 2) r^n rho' gives the first moment
+#     int_T rho' r^n dA = sum_e u_e E_(n+2)(e) / (n + 2),
+# where the edge integrals E_n = int_e r^n dl (r^2 = R0^2 + l^2 along the edge)
+# follow from d/dl (l r^n) = (n + 1) r^n - n R0^2 r^(n-2):
+#     E_n = ([l r^n] + n R0^2 E_(n-2)) / (n + 1),  E_(-1) = L_e.
+# The recursion starts from the closed forms above (n = -1).
+# ---------------------------------------------------------------------------
+def odd_power_potentials(x, tri, kmax):
+    """For points x (m,3): lists P, V with P[k] = int_T r^(2k-1) dA (m,) and
+    V[k] = int_T (y - rho) r^(2k-1) dA (m,3), k = 0..kmax."""
+    tri = np.asarray(tri, float)
+    n, _ = _geom(tri)
+    S, G, _, _, w, rho = potentials(x, tri)
+    w2 = w * w
+    edges = []
+    for Pm, Pp, le, ue in _edges(tri, n):
+        t0 = (Pm - rho) @ ue
+        lp = (Pp - rho) @ le
+        lm = (Pm - rho) @ le
+        R02 = t0 * t0 + w2
+        Rp = np.linalg.norm(x - Pp, axis=1)
+        Rm = np.linalg.norm(x - Pm, axis=1)
+        L = np.where(np.abs(t0) + np.abs(w) > 0, _log_ratio(Rp, lp, Rm, lm, R02), 0.0)
+        # E[j] = int_e r^(2j-1) dl for j = 0..kmax+1
+        E = [L]
+        for j in range(1, kmax + 2):
+            m_ = 2 * j - 1
+            E.append((lp * Rp ** m_ - lm * Rm ** m_ + m_ * R02 * E[-1]) / (m_ + 1))
+        edges.append((t0, ue, E))
+    P = [S]
+    V = [G]
+    for k in range(1, kmax + 1):
+        m_ = 2 * k - 1
+        acc = m_ * w2 * P[-1]
+        vec = np.zeros((len(x), 3))
+        for t0, ue, E in edges:
+            acc = acc + t0 * E[k]
+            vec += (E[k + 1] / (m_ + 2))[:, None] * ue[None, :]
+        P.append(acc / (m_ + 2))
+        V.append(vec)
+    return P, V
+
+
+def helmholtz_real_excess(x, tri, kappa, lb=-1, kmax=24):
+    """int_T (cos(kappa r) - 1)/(4 pi r) psi(y) dy at points x, psi = 1 (lb = -1)
+    or the hat function of local vertex lb, summed from the odd-power series."""
+    P, V = odd_power_potentials(x, tri, kmax)
+    if lb < 0:
+        lam = np.ones(len(x))
+        beta = np.zeros(3)
+    else:
+        alpha, beta = affine_basis(tri, lb)
+        _, _, _, _, _, rho = potentials(x, tri)
+        lam = alpha + rho @ beta
+    out = np.zeros(len(x))
+    coef = 1.0
+    for k in range(1, kmax + 1):
+        coef *= -kappa * kappa / ((2 * k - 1) * (2 * k))
+        out += coef * (lam * P[k] + V[k] @ beta)
+    return out / FOUR_PI
+
+
+def helmholtz_real_excess_pair(tri_a, tri_b, kappa, la=-1, lb=-1, n=64, p=5, kmax=24):
+    """int_{T_a} phi(x) int_{T_b} (cos(kappa r) - 1)/(4 pi r) psi(y) dy dx."""
+    X, W, s, t = outer_rule(tri_a, n, p)
+    fa = 1.0 if la < 0 else [1.0 - s, s - t, t][la]
+    with np.errstate(all="ignore"):
+        val = helmholtz_real_excess(X, tri_b, kappa, lb, kmax)
+    bad = ~np.isfinite(val)
+    assert np.sum(W[bad]) < 1e-30, "non-finite potential at a point with weight"
+    val = np.where(bad, 0.0, val)
+    return float(np.sum(W * fa * val))
