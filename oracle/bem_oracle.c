@@ -25,7 +25,9 @@
  *     own derivation (6, 4 and 2 subdomains), explained at each function.
  * Kernels (Eq. 2 and Section 4): Laplace single layer 1/(4 pi r), Laplace
  * double layer (x-y).n_y/(4 pi r^3), Helmholtz single layer
- * exp(i kappa r)/(4 pi r).
+ * exp(i kappa r)/(4 pi r), and the Helmholtz double layer of the
+ * Brakhage-Werner formulation (Section 4), the normal derivative in y of the
+ * Helmholtz kernel: (x-y).n_y (1 - i kappa r) exp(i kappa r)/(4 pi r^3).
  *
  * Everything is evaluated in double precision with plain sums in the nested
  * point order (subdomain, xi, eta1, eta2, eta3).
@@ -45,7 +47,7 @@
 
 #define ORC_PI 3.14159265358979323846
 
-enum { ORC_LAPLACE_SLP = 0, ORC_LAPLACE_DLP = 1, ORC_HELMHOLTZ_SLP = 2 };
+enum { ORC_LAPLACE_SLP = 0, ORC_LAPLACE_DLP = 1, ORC_HELMHOLTZ_SLP = 2, ORC_HELMHOLTZ_DLP = 3 };
 enum { ORC_P0 = 0, ORC_P1 = 1 };
 enum { ORC_RULE_DUFFY = 0, ORC_RULE_TRI7 = 1 };
 enum { ORC_CASE_REGULAR = 0, ORC_CASE_VERTEX = 1, ORC_CASE_EDGE = 2, ORC_CASE_IDENTICAL = 3 };
@@ -375,9 +377,18 @@ static void kernel_eval(int kind, double kappa, const double *x, const double *y
         double dn = d[0] * ny[0] + d[1] * ny[1] + d[2] * ny[2];
         *re = dn / (4.0 * ORC_PI * r * r * r);
         *im = 0.0;
-    } else {
+    } else if (kind == ORC_HELMHOLTZ_SLP) {
         *re = cos(kappa * r) / (4.0 * ORC_PI * r);
         *im = sin(kappa * r) / (4.0 * ORC_PI * r);
+    } else {
+        /* d/dn_y exp(i kappa r)/(4 pi r): dr/dn_y = -(x-y).n_y / r and
+         * d/dr [exp(i kappa r)/r] = (i kappa r - 1) exp(i kappa r)/r^2, so the
+         * value is (x-y).n_y (1 - i kappa r) exp(i kappa r)/(4 pi r^3) */
+        double dn = d[0] * ny[0] + d[1] * ny[1] + d[2] * ny[2];
+        double kr = kappa * r, c = cos(kr), sn = sin(kr);
+        double f = dn / (4.0 * ORC_PI * r * r * r);
+        *re = f * (c + kr * sn);
+        *im = f * (sn - kr * c);
     }
 }
 
@@ -558,6 +569,7 @@ static int setup_init(orc_setup *S, int kernel, double kappa, int regular_rule, 
                       int q_identical, int q_edge, int q_vertex)
 {
     memset(S, 0, sizeof(*S));
+    if (kernel < ORC_LAPLACE_SLP || kernel > ORC_HELMHOLTZ_DLP) return -1;
     S->kernel = kernel; S->kappa = kappa; S->regular_rule = regular_rule;
     S->q_regular = q_regular; S->q_identical = q_identical;
     S->q_edge = q_edge; S->q_vertex = q_vertex;
@@ -590,7 +602,7 @@ static int entries_impl(const double *verts, int64_t nv, const int32_t *tris, in
                         double *out, int64_t *npoints, int nthreads, int absolute)
 {
     if (nv <= 0 || nt <= 0 || n < 0) return -1;
-    if (kernel < 0 || kernel > 2) return -1;
+    if (kernel < 0 || kernel > 3) return -1;
     for (int64_t t = 0; t < 3 * nt; ++t)
         if (tris[t] < 0 || tris[t] >= nv) return -1;
     for (int64_t t = 0; t < nt; ++t) {

@@ -19,7 +19,7 @@ _lock = threading.Lock()
 _lib = None
 
 CASES = {"regular": 0, "vertex": 1, "edge": 2, "identical": 3}
-KERNELS = {"laplace_slp": 0, "laplace_dlp": 1, "helmholtz_slp": 2}
+KERNELS = {"laplace_slp": 0, "laplace_dlp": 1, "helmholtz_slp": 2, "helmholtz_dlp": 3}
 BASES = {"p0": 0, "p1": 1}
 RULES = {"duffy": 0, "tri7": 1}
 

@@ -250,3 +250,39 @@ def helmholtz_real_excess_pair(tri_a, tri_b, kappa, la=-1, lb=-1, n=64, p=5, kma
     assert np.sum(W[bad]) < 1e-30, "non-finite potential at a point with weight"
     val = np.where(bad, 0.0, val)
     return float(np.sum(W * fa * val))
+
+
+def helmholtz_dlp_real_excess(x, tri, kappa, lb=-1, kmax=24):
+    """int_T [Re dg_kappa/dn_y - dg_0/dn_y] psi(y) dy at points x.
+
+    The Helmholtz double layer is w (1 - i kappa r) exp(i kappa r)/(4 pi r^3)
+    with w = (x - y).n_y, the height of x above T's plane (constant over T).
+    Its real part minus the Laplace one is w (cos z + z sin z - 1)/(4 pi r^3),
+    z = kappa r, and cos z + z sin z - 1 = sum_{k>=1} (-1)^(k+1) (2k-1)
+    z^(2k)/(2k)!, so the excess is w/(4 pi) sum_k c_k kappa^(2k) P_(2k-3)."""
+    P, V = odd_power_potentials(x, tri, kmax)
+    _, _, _, _, w, rho = potentials(x, tri)
+    if lb < 0:
+        lam = np.ones(len(x))
+        beta = np.zeros(3)
+    else:
+        alpha, beta = affine_basis(tri, lb)
+        lam = alpha + rho @ beta
+    out = np.zeros(len(x))
+    fact = 1.0                        # (2k)!
+    for k in range(1, kmax + 1):
+        fact *= (2 * k - 1) * (2 * k)
+        c = (-1) ** (k + 1) * (2 * k - 1) * kappa ** (2 * k) / fact
+        out += c * (lam * P[k - 1] + V[k - 1] @ beta)
+    return w * out / FOUR_PI
+
+
+def helmholtz_dlp_real_excess_pair(tri_a, tri_b, kappa, la=-1, lb=-1, n=64, p=5, kmax=24):
+    X, W, s, t = outer_rule(tri_a, n, p)
+    fa = 1.0 if la < 0 else [1.0 - s, s - t, t][la]
+    with np.errstate(all="ignore"):
+        val = helmholtz_dlp_real_excess(X, tri_b, kappa, lb, kmax)
+    bad = ~np.isfinite(val)
+    assert np.sum(W[bad]) < 1e-30, "non-finite potential at a point with weight"
+    val = np.where(bad, 0.0, val)
+    return float(np.sum(W * fa * val))
