@@ -474,16 +474,31 @@ int64_t bem_rule_points(int32_t cas, int32_t regular_rule, int32_t q, double *ou
  *
  * Computes the same near-field blocks as bem_near_field for ONE job, with the
  * same kernels, but calls no cudaMalloc, cudaFree or other allocating routine.
- * Its scratch (singular-case rule tables and per-block tile sums) is a static
- * device array of 1,395,200 bytes inside the library, present on every GPU
- * that loads the library until the process exits.  Limits: at most 65536
- * blocks and singular orders q_vertex, q_edge, q_identical <= 6; larger
- * requests fail with BEM_ERR_INVALID_ARG and a message naming the limit.
- * The mesh, the context's status word and the outputs are the ones set up
- * by earlier calls (bem_create, bem_mesh_upload) and by the caller.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ * Its scratch (the singular-case rule tables of every order 1..6 and the
+ * per-block tile sums) is a static device array of 2,053,088 bytes inside the
+ * library, present on every GPU that loads the library until the process
+ * exits.  The mesh, the context's status word and the outputs are the ones
+ * set up by earlier calls (bem_create, bem_mesh_upload) and by the caller.
+ *
+ * Supported: the FP64 form (precision BEM_FP64) with fixed orders
+ * (BEM_ORDER_FIXED), regular rule BEM_RULE_TRI7 or BEM_RULE_DUFFY with
+ * q_regular in [2, 4], singular orders q_vertex, q_edge, q_identical in
+ * [1, 6], at most 65536 blocks.  Rejections (nothing is launched):
+ *   BEM_ERR_INVALID_ARG  null context or job, unknown mesh id, bad kernel
+ *                        descriptor, a singular order outside [1, 6] or more
+ *                        than 65536 blocks (the message names the static
+ *                        scratch's limit), negative block count, null pointer
+ *                        or empty cluster list, complex output not 16-byte
+ *                        aligned;
+ *   BEM_ERR_UNSUPPORTED  the mixed or float-full forms, learned orders, any
+ *                        other regular rule or order, piecewise-linear meshes
+ *                        with a vertex of degree above 16;
+ *   BEM_ERR_CUDA         a failed CUDA call (message from the runtime).
+ *   - The first call on a device sets the array up with that device current:
+ *     it looks up the array's device address (cudaGetSymbolAddress) and
+ *     copies the rule tables into it (synchronous host-to-device copies).
+ *     Make that first call before any stream capture.  Later calls copy
+ *     nothing from the host and only launch kernels on the context's stream.
  *   - Every call shares the one array and the mesh's touching table, and
  *     leaves its contents behind: calls on the same stream are ordered, but
  *     calls that overlap on the GPU (other streams or contexts on the same

@@ -9,6 +9,13 @@
 // singular-case quadrature tables and the per-block tile prefix sums) lives in
 // the file-scope array g_noalloc_scratch below, which every GPU that loads the
 // library holds until the process exits.  Nothing here allocates.
+//
+// Layout of the array: kMaxBlocks int64 tile prefix slots, then the rule
+// tables of every singular case (vertex, edge, identical) at every order
+// q = 1..kMaxOrder, back to back.  The tables are written once per device, by
+// the first call on that device (a synchronous copy from host memory); later
+// calls only pick the offsets of the tables they need, so they copy nothing
+// from the host and do not wait for the device.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -21,32 +28,62 @@ namespace {
 
 constexpr int64_t kMaxBlocks = 65536;   // tile prefix slots (int64 each)
 constexpr int kMaxOrder = 6;            // singular orders q <= 6
-// vertex 2 q^4 + edge 4 q^4 + identical 6 q^4 points, 7 doubles per point
-constexpr int64_t kRuleDoubles = 7LL * 12 * kMaxOrder * kMaxOrder * kMaxOrder * kMaxOrder;
-constexpr int64_t kScratchDoubles = kMaxBlocks + kRuleDoubles;   // 1,395,200 B in all
+// points of the three singular cases at order q: vertex 2 q^4 + edge 4 q^4 +
+// identical 6 q^4; the tables of all orders 1..6 hold 12 (1 + 16 + 81 + 256 +
+// 625 + 1296) = 27,300 points of kRuleCols = 7 doubles
+constexpr int64_t kSumQ4 = 1 + 16 + 81 + 256 + 625 + 1296;
+constexpr int64_t kRuleDoubles = 7LL * 12 * kSumQ4;                // 191,100
+constexpr int64_t kScratchDoubles = kMaxBlocks + kRuleDoubles;     // 2,053,088 B in all
 
 // One copy per device of every process that loads the library.  In host code
 // this name is only a host-side stand-in: the device address comes from
-// cudaGetSymbolAddress (scratch_address below).
+// cudaGetSymbolAddress (scratch_setup below).
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double *g_addr[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on `device` (set up once per device,
-// with that device current).
-cudaError_t scratch_address(int device, double **out)
+struct DeviceScratch {
+    double *base = nullptr;                  // device address of g_noalloc_scratch
+    bem::Rule4D rule[4][kMaxOrder + 1];           // [case][q], views into the array
+};
+DeviceScratch *g_dev[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on `device` and its rule tables, set up
+// once per device with that device current: the address lookup, then every
+// singular rule of order 1..kMaxOrder built on the host and copied into the
+// array with one synchronous cudaMemcpy per table.
+cudaError_t scratch_setup(int device, const DeviceScratch **out)
 {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[device]) {
+    if (!g_dev[device]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_addr[device] = static_cast<double *>(p);
+        auto *S = new DeviceScratch;
+        S->base = static_cast<double *>(p);
+        int64_t at = kMaxBlocks;
+        for (int c = bem::kVertex; c <= bem::kIdentical; ++c)
+            for (int q = 1; q <= kMaxOrder; ++q) {
+                std::vector<double> soa;
+                if (!bem::make_rule4d_host(c, 0, q, soa) || at + (int64_t)soa.size() > kScratchDoubles) {
+                    delete S;
+                    return cudaErrorInvalidValue;
+                }
+                bem::Rule4D &r = S->rule[c][q];
+                r.n = (int)(soa.size() / bem::kRuleCols);
+                r.d = S->base + at;
+                e = cudaMemcpy(r.d, soa.data(), soa.size() * sizeof(double), cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) {
+                    delete S;
+                    return e;
+                }
+                at += (int64_t)soa.size();
+            }
+        g_dev[device] = S;
     }
-    *out = g_addr[device];
+    *out = g_dev[device];
     return cudaSuccess;
 }
 
@@ -97,27 +134,16 @@ extern "C" int bem_near_field_noalloc(bem_ctx *ctx, const bem_block_job *job)
         return noalloc_fail(ctx, BEM_ERR_UNSUPPORTED, "vertex degree above 16 (piecewise linear)");
 
     cudaError_t e = cudaSetDevice(ctx->device);
-    double *scratch = nullptr;
-    if (e == cudaSuccess) e = scratch_address(ctx->device, &scratch);
+    const DeviceScratch *S = nullptr;
+    if (e == cudaSuccess) e = scratch_setup(ctx->device, &S);
     if (e != cudaSuccess) return noalloc_fail(ctx, BEM_ERR_CUDA, cudaGetErrorString(e));
-    int64_t *prefix = reinterpret_cast<int64_t *>(scratch);
-    double *rules = scratch + kMaxBlocks;
+    int64_t *prefix = reinterpret_cast<int64_t *>(S->base);
 
-    // singular-case rules into the static array (host tables, no device allocation)
-    int64_t at = 0;
+    // touching pairs of the mesh from the resident singular rules
     for (int c = kVertex; c <= kIdentical; ++c) {
         if (m->nlist[c] == 0) continue;
-        std::vector<double> soa;
-        if (!make_rule4d_host(c, 0, qs[c], soa)) return noalloc_fail(ctx, BEM_ERR_INVALID_ARG, "bad rule");
-        Rule4D r;
-        r.n = (int)(soa.size() / kRuleCols);
-        r.d = rules + at;
-        at += (int64_t)soa.size();
-        e = cudaMemcpyAsync(r.d, soa.data(), soa.size() * sizeof(double), cudaMemcpyHostToDevice,
-                            ctx->stream);
-        if (e == cudaSuccess)
-            e = launch_touching(m->v, c, m->list[c], m->nlist[c], r, J.kernel.kind, J.kernel.kappa,
-                                0, ctx->stream);
+        e = launch_touching(m->v, c, m->list[c], m->nlist[c], S->rule[c][qs[c]], J.kernel.kind,
+                            J.kernel.kappa, 0, ctx->stream);
         if (e != cudaSuccess) return noalloc_fail(ctx, BEM_ERR_CUDA, cudaGetErrorString(e));
     }
 
