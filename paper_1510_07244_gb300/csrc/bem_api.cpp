@@ -27,7 +27,7 @@ static cudaEvent_t prof_event(bem_ctx *c)
     return e;
 }
 
-ProfScope::ProfScope(bem_ctx *c, const char *name) : ctx(c), on(c->profile)
+ProfScope::ProfScope(bem_ctx *c, const char *name) : ctx(c), on(c && c->profile)
 {
     if (!on) return;
     rec.name = name;
@@ -143,6 +143,13 @@ int get_rule4(bem_ctx *ctx, int cas, int rule, int q, Rule4D &out)
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(rule)");
     e = cudaMemcpy(r.f, sf.data(), sf.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(rule)");
+    // the rounding remainders: (f, fl) is the rule as double-float pairs
+    std::vector<float> sl(soa.size());
+    for (size_t k = 0; k < soa.size(); ++k) sl[k] = (float)(soa[k] - (double)sf[k]);
+    e = cudaMalloc((void **)&r.fl, sl.size() * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(rule)");
+    e = cudaMemcpy(r.fl, sl.data(), sl.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy(rule)");
     ctx->rules4[key] = r;
     out = r;
     return BEM_OK;
@@ -182,6 +189,41 @@ int ensure_prefix(bem_ctx *ctx, int64_t n)
         return cuda_fail(ctx, e, "cudaMalloc(tile prefix)");
     }
     ctx->tile_prefix_cap = cap;
+    return BEM_OK;
+}
+
+// Guard pass of one guarded job (bem_guard.cu) in the context's scratch.
+int run_guard(bem_ctx *ctx, Mesh *m, const BlockLaunch &L, const bem_quad_desc &q,
+              const Rule2D &r2)
+{
+    GuardSet g;
+    g.r2 = r2;
+    const int rr[4] = {q.regular_rule, 0, 0, 0};
+    const int qq[4] = {q.q_regular, q.q_vertex, q.q_edge, q.q_identical};
+    for (int c = 0; c < 4; ++c) {
+        int rc = get_rule4(ctx, c, rr[c], qq[c], g.rules[c]);
+        if (rc) return rc;
+    }
+    cudaError_t e = guard_add(g, m->v, L, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "guard set-up");
+    const size_t bytes = guard_bytes(g);
+    if (bytes > ctx->guard_cap) {
+        if (ctx->guard_buf) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->guard_buf);
+            ctx->guard_buf = nullptr;
+            ctx->guard_cap = 0;
+        }
+        e = cudaMalloc(&ctx->guard_buf, bytes);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(guard)");
+        ctx->guard_cap = bytes;
+    }
+    e = guard_layout(g, ctx->guard_buf, ctx->stream);
+    if (e == cudaSuccess) {
+        ProfScope ps(ctx, "guard");
+        e = guard_run(g, ctx->num_sms, ctx->status, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "guard pass");
     return BEM_OK;
 }
 
@@ -260,11 +302,18 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
             continue;
         }
         const int grid = ctx->num_sms * (m->v.basis == BEM_P0 ? 8 : 2);
+        // cancellation guard of the float double layer (not for the lower
+        // triangle alone: the guard pass reads every entry of the blocks)
+        L.guard = m->v.basis == BEM_P0 && L.kind == BEM_LAPLACE_DLP && L.mixed && !lower_only;
         {
             ProfScope ps(ctx, m->v.basis == BEM_P0 ? "block_p0" : "block_p1");
             e = launch_block_engine(m->v, L, r2, ctx->tile_prefix, ctx->status, grid, ctx->stream);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "block kernel");
+        if (L.guard) {
+            rc = run_guard(ctx, m, L, J.quad, r2);
+            if (rc) return rc;
+        }
     }
     return BEM_OK;
 }
@@ -274,6 +323,7 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
 namespace bem {
 
 int api_fail(bem_ctx *ctx, int code, const char *msg) { return fail(ctx, code, msg); }
+int api_ensure_prefix(bem_ctx *ctx, int64_t n) { return ensure_prefix(ctx, n); }
 int api_cuda_fail(bem_ctx *ctx, cudaError_t e, const char *where) { return cuda_fail(ctx, e, where); }
 int api_get_rule4(bem_ctx *ctx, int cas, int rule, int q, Rule4D &out)
 {
@@ -347,6 +397,7 @@ int bem_destroy(bem_ctx *ctx)
     for (auto &kv : ctx->rules4) {
         cudaFree(kv.second.d);
         cudaFree(kv.second.f);
+        cudaFree(kv.second.fl);
     }
     for (auto &r : ctx->prof_pending) {
         cudaEventDestroy(r.a);
@@ -355,9 +406,8 @@ int bem_destroy(bem_ctx *ctx)
     for (cudaEvent_t e : ctx->prof_free) cudaEventDestroy(e);
     cudaFree(ctx->status);
     cudaFree(ctx->tile_prefix);
-    cudaFree(ctx->learned_cls);
-    cudaFree(ctx->learned_rec);
-    cudaFree(ctx->learned_small);
+    cudaFree(ctx->guard_buf);
+    learned_free(ctx->learned);
     delete ctx;
     return BEM_OK;
 }

@@ -427,9 +427,12 @@ __device__ __forceinline__ void regular_p0_f32_helm(const TriF &A, const TriF &B
     out_im = si * sc;
 }
 
-// Regular pair, piecewise constant, float (Laplace kernels).
-template <int KIND, int NP>
-__device__ __forceinline__ float regular_p0_f32(const TriF &A, const TriF &B, const Rule2D &R)
+// Regular pair, piecewise constant, float (Laplace kernels).  With ABS the
+// double layer also returns in *abs_out the sum of the magnitudes of its terms
+// (the scale of its rounding error, for the cancellation guard).
+template <int KIND, int NP, bool ABS = false>
+__device__ __forceinline__ float regular_p0_f32(const TriF &A, const TriF &B, const Rule2D &R,
+                                                float *abs_out = nullptr)
 {
     float d0[3], yx[NP], yy[NP], yz[NP];
 #pragma unroll
@@ -444,7 +447,7 @@ __device__ __forceinline__ float regular_p0_f32(const TriF &A, const TriF &B, co
     if (KIND == BEM_LAPLACE_DLP)
         H = make_height(A.vh[0], A.vl[0], A.vh[1], A.vl[1], A.vh[2], A.vl[2], B.vh[0], B.vl[0],
                         B.nh, B.nl);
-    float sum = 0.0f, comp = 0.0f;
+    float sum = 0.0f, comp = 0.0f, asum = 0.0f;
     auto outer = [&](int i) {
         const float xx = fmaf(R.sf[i], A.e1[0], fmaf(R.tf[i], A.e2[0], d0[0]));
         const float xy = fmaf(R.sf[i], A.e1[1], fmaf(R.tf[i], A.e2[1], d0[1]));
@@ -454,6 +457,7 @@ __device__ __forceinline__ float regular_p0_f32(const TriF &A, const TriF &B, co
 #pragma unroll
         for (int j = 0; j < NP; ++j)
             inner = fmaf(R.wf[j], kvalf_r<KIND>(xx - yx[j], xy - yy[j], xz - yz[j]), inner);
+        if (ABS) asum = fmaf(R.wf[i], inner * fabsf(dn), asum);
         if (KIND == BEM_LAPLACE_DLP) inner *= dn;
         // compensated outer sum (Kahan)
         const float y = fmaf(R.wf[i], inner, -comp);
@@ -469,6 +473,7 @@ __device__ __forceinline__ float regular_p0_f32(const TriF &A, const TriF &B, co
 #pragma unroll
         for (int i = 0; i < NP; ++i) outer(i);
     }
+    if (ABS) *abs_out = asum * (A.sg * B.sg * (float)kInv4Pi);
     return sum * (A.sg * B.sg * (float)kInv4Pi);
 }
 
@@ -842,6 +847,11 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
     // compensation, which keeps the compensated accuracy at a quarter of the
     // additions.
     constexpr int KB = 4;
+    // piecewise-constant double layer: the sum of |terms| goes to the unused
+    // imaginary part of the table entry (scale of the rounding error, read by
+    // the cancellation guard)
+    constexpr bool ABS = KIND == BEM_LAPLACE_DLP && BASIS == BEM_P0;
+    float asum = 0.0f;
     for (int p0 = lane; p0 < np && !zero; p0 += 32 * KB) {
         float br[NACC], bi[NACC];
 #pragma unroll
@@ -882,6 +892,7 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
             } else {
                 wk = w * kvalf<KIND>(dx, dy, dz, dn);
             }
+            if (ABS) asum += fabsf(wk);
             const float mx[3] = {1.0f, x1, x2}, my[3] = {1.0f, y1, y2};
 #pragma unroll
             for (int i = 0; i < (BASIS == BEM_P0 ? 1 : 3); ++i)
@@ -920,11 +931,13 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
             warp_sum2f(mi[k].h, mi[k].l);
         }
     }
+    if (ABS) asum = warp_sumf(asum);
     if (BASIS == BEM_P0) {
         if (lane == 0) {
             const double scale = (double)A.sg * (double)B.sg * kInv4Pi;
             m.table[idx] = make_double2(((double)mr[0].h + (double)mr[0].l) * scale,
-                                        ((double)mi[0].h + (double)mi[0].l) * scale);
+                                        ABS ? (double)asum * scale
+                                            : ((double)mi[0].h + (double)mi[0].l) * scale);
         }
     } else {
         FF hr[9], hi[9];
@@ -1129,6 +1142,8 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
         }
         if (L.lower_only && a < b) return;
         double re, im;
+        float absum = 0.0f;   // guarded double layer: sum of |terms|
+        const bool guard = MIXED && KIND == BEM_LAPLACE_DLP && L.guard;
         const int4 va = __ldg(m.tvid + a), vb = __ldg(m.tvid + b);
         if (touching(va, vb)) {
             const int k = L.allow_touching ? find_touching(m, a, b) : -1;
@@ -1138,7 +1153,8 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
             }
             const double2 v = m.table[k];
             re = v.x;
-            im = v.y;
+            im = v.y;     // the double layer's float touching kernels put A here
+            if (guard) absum = (float)v.y;
         } else if (MIXED) {
             TriF A, B;
             load_trif(m.geomf, a, A);
@@ -1148,6 +1164,9 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
                 regular_p0_f32_helm<NP>(A, B, R, L.kappa, fr, fi);
                 re = (double)fr;
                 im = (double)fi;
+            } else if (guard) {
+                re = (double)regular_p0_f32<BEM_LAPLACE_DLP, NP, true>(A, B, R, &absum);
+                im = 0.0;
             } else {
                 re = (double)regular_p0_f32<KIND, NP>(A, B, R);
                 im = 0.0;
@@ -1160,6 +1179,7 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
         }
         const int64_t o = bi.off + (int64_t)r + (int64_t)c * bi.nr;
         if (KIND == BEM_HELMHOLTZ_SLP) reinterpret_cast<double2 *>(L.out)[o] = make_double2(re, im);
+        else if (guard) reinterpret_cast<float2 *>(L.out)[o] = make_float2((float)re, absum);
         else reinterpret_cast<double *>(L.out)[o] = re;
     }
 }

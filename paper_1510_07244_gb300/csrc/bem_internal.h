@@ -48,6 +48,7 @@ struct Rule4D {
     int n = 0;
     double *d = nullptr;   // device, kRuleCols n doubles
     float *f = nullptr;    // device, kRuleCols n floats (mixed form), may be null
+    float *fl = nullptr;   // device, kRuleCols n floats: d - f (double-float form), may be null
 };
 
 // Device view of an uploaded mesh.
@@ -67,6 +68,15 @@ struct MeshView {
     const unsigned char *nb_perm;   // ntouch: code_a * 6 + code_b
     double2 *table;            // ntouch * (1 or 9): touching-pair integrals
     int64_t ntouch;
+};
+
+// Scratch of one learned-order job: class per tile slot, records grouped by
+// class, counters (int [8] + fill [8]) and class offsets (int64 [7]).
+struct LearnedScratch {
+    unsigned char *cls = nullptr;
+    void *rec = nullptr;
+    int64_t *small = nullptr;
+    int64_t cap = 0;
 };
 
 struct Mesh {
@@ -94,6 +104,8 @@ struct bem_ctx {
     int *status = nullptr;                 // device status word
     int64_t *tile_prefix = nullptr;        // scratch: per-block tile prefix sums
     int64_t tile_prefix_cap = 0;
+    void *guard_buf = nullptr;             // scratch: cancellation guard of one call
+    size_t guard_cap = 0;
     int num_sms = 0;
     std::map<int, bem::Mesh *> meshes;
     int next_mesh = 1;
@@ -107,10 +119,7 @@ struct bem_ctx {
     // learned order selection
     struct bem_mlp *order_model = nullptr;
     float order_conf = 0.0f;
-    unsigned char *learned_cls = nullptr;        // scratch: class per tile slot
-    void *learned_rec = nullptr;                 // scratch: records grouped by class
-    int64_t learned_cap = 0;
-    int64_t *learned_small = nullptr;            // counters / offsets
+    bem::LearnedScratch learned;                 // scratch of the per-call learned path
     int64_t learned_counts[6] = {0, 0, 0, 0, 0, 0};
 };
 
@@ -129,6 +138,7 @@ namespace bem {
 
 // bem_api.cpp helpers shared with the plan driver
 int api_fail(bem_ctx *ctx, int code, const char *msg);
+int api_ensure_prefix(bem_ctx *ctx, int64_t n);   // grows the tile-prefix scratch
 int api_cuda_fail(bem_ctx *ctx, cudaError_t e, const char *where);
 int api_check_job(bem_ctx *ctx, const bem_block_job &J, Rule2D &r2, Mesh **mesh);
 int api_get_rule4(bem_ctx *ctx, int cas, int rule, int q, Rule4D &out);
@@ -189,6 +199,10 @@ struct BlockLaunch {
     // double layer's touching table (the single layer's is the mesh view's)
     void *out2 = nullptr;
     const double2 *table2 = nullptr;
+    // cancellation guard (piecewise-constant double layer, float forms): the
+    // engine writes each entry as the float pair (value, sum of |terms|) for
+    // the guard pass (bem_guard.cu), which widens or recomputes it
+    int guard = 0;
 };
 
 // Internal kernel id of the fused single + double layer (never a public kind).
@@ -216,6 +230,51 @@ struct BatchJob {
     BlockLaunch L;
     const int64_t *prefix;     // per-block tile prefix sums of this list
 };
+
+// One guarded job (bem_guard.cu): its mesh and blocks, and a per-row maximum
+// (float bits of |value|, zeroed before every pass) over n_rows row indices.
+struct GuardJob {
+    MeshView m;
+    BlockLaunch L;
+    unsigned *rowmax;
+    int64_t n_rows;
+};
+
+// An entry of a guarded job recomputed in FP64: row and column triangles and
+// the output offset.
+struct GuardItem {
+    int32_t job, row, col, pad;
+    int64_t off;
+};
+
+// Forward-error bound of the float forms' double-layer entries, relative to the
+// sum of the magnitudes of the quadrature terms; entries whose bound can exceed
+// the relative-error bar are recomputed in FP64.
+constexpr float kGuardRel = 8e-7f;
+
+// Guarded jobs with the same orders, and their device buffers.  Built on the
+// host (guard_add reads each job's cluster and block arrays once to count its
+// entries), laid out in one device allocation by guard_layout, run by
+// guard_run: zero the row maxima and the list counter, row maxima, selection,
+// FP64 recomputation (rules: the FP64 rules of the jobs' orders).
+struct GuardSet {
+    std::vector<GuardJob> host;
+    std::vector<int64_t> blk_end;        // inclusive prefix of the block counts
+    int64_t rows = 0, entries = 0, cap = 0, cap_t = 0;
+    Rule4D rules[4];                     // FP64 rules: regular, vertex, edge, identical
+    Rule2D r2;                           // the regular rule's 2D points (one per set)
+    GuardJob *d_jobs = nullptr;
+    int64_t *d_blk_end = nullptr;
+    unsigned *d_rowmax = nullptr;
+    unsigned long long *d_count = nullptr;   // [0]: disjoint entries listed, [1]: touching
+    GuardItem *d_list = nullptr;             // disjoint pairs (capacity cap)
+    GuardItem *d_list_t = nullptr;           // touching pairs (capacity cap_t)
+};
+cudaError_t guard_add(GuardSet &g, const MeshView &m, const BlockLaunch &L, cudaStream_t st);
+size_t guard_bytes(const GuardSet &g);
+// buf: guard_bytes(g) bytes, 256-byte aligned; uploads the job table on st
+cudaError_t guard_layout(GuardSet &g, void *buf, cudaStream_t st);
+cudaError_t guard_run(const GuardSet &g, int num_sms, int *status, cudaStream_t st);
 
 // One mesh / kernel of a batched touching launch.
 struct TouchJob {
@@ -284,6 +343,13 @@ cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const i
                                  double kappa, int *status, cudaStream_t st, bool absolute);
 
 // bem_order.cu: learned-order near field of one piecewise-constant job
+cudaError_t learned_alloc(LearnedScratch &S, int64_t tiles);
+void learned_free(LearnedScratch &S);
+int learned_rules(bem_ctx *ctx, Rule4D *rules);   // the 6 classes' FP64 4D rules
+cudaError_t learned_launches(const MeshView &mv, const BlockLaunch &L, const int64_t *prefix,
+                             const ::bem_mlp *model, float conf, const LearnedScratch &S,
+                             const Rule4D *rules, int precision, int num_sms, int *status,
+                             cudaStream_t st, bem_ctx *prof_ctx);
 int run_learned_p0(bem_ctx *ctx, const MeshView &mv, const BlockLaunch &L, const int64_t *prefix,
                    int precision);
 

@@ -64,6 +64,20 @@ struct bem_plan {
     std::vector<TouchBucket> tb;
     std::vector<BlockBucket> bb;
     std::vector<SupTable> sup;
+    std::vector<GuardSet> guards;     // cancellation guard per set of orders
+    // learned-order jobs (piecewise constant): each with its tile prefix sums
+    // and scratch; the order model and confidence captured at creation
+    struct Learned {
+        MeshView m;
+        BlockLaunch L;
+        int64_t *prefix = nullptr;
+        LearnedScratch S;
+        int precision = 0;
+    };
+    std::vector<Learned> learned;
+    const ::bem_mlp *model = nullptr;
+    float conf = 0.0f;
+    Rule4D lrules[6];
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<bem_prof_rec> prof;   // event pairs recorded around each launch
@@ -98,6 +112,7 @@ void plan_free(bem_plan *p)
         cudaEventDestroy(r.b);
     }
     for (void *a : p->allocs) cudaFree(a);
+    for (auto &l : p->learned) learned_free(l.S);
     if (p->cap) cudaStreamDestroy(p->cap);
     delete p;
 }
@@ -204,6 +219,21 @@ cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
     for (auto &b : p->bb) {
         ev_begin();
         e = launch_bucket(ctx, b, b.grid_mult, st);
+        ev_end();
+        if (e != cudaSuccess) return e;
+    }
+    for (auto &l : p->learned) {
+        ev_begin();
+        e = launch_tile_prefix(l.L, kTile, 8, l.prefix, ctx->status, st);
+        if (e == cudaSuccess)
+            e = learned_launches(l.m, l.L, l.prefix, p->model, p->conf, l.S, p->lrules, l.precision,
+                                 ctx->num_sms, ctx->status, st, nullptr);
+        ev_end();
+        if (e != cudaSuccess) return e;
+    }
+    for (auto &g : p->guards) {
+        ev_begin();
+        e = guard_run(g, ctx->num_sms, ctx->status, st);
         ev_end();
         if (e != cudaSuccess) return e;
     }
@@ -316,10 +346,12 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         ji.near = k < n_near;
         ji.touch_job = -1;
         int rc = api_check_job(ctx, J, ji.r2, &ji.m);
-        if (rc == BEM_OK && J.quad.order_mode != BEM_ORDER_FIXED)
-            rc = api_fail(ctx, BEM_ERR_UNSUPPORTED,
-                          "plans run fixed orders; learned orders go through bem_near_field / "
-                          "bem_coupling_blocks");
+        if (rc == BEM_OK && J.quad.order_mode == BEM_ORDER_LEARNED) {
+            if (ji.m->v.basis != BEM_P0)
+                rc = api_fail(ctx, BEM_ERR_UNSUPPORTED, "learned orders need the piecewise-constant basis");
+            else if (!ctx->order_model)
+                rc = api_fail(ctx, BEM_ERR_INVALID_ARG, "order_mode LEARNED needs bem_set_order_model");
+        }
         if (rc) {
             plan_free(p);
             return rc;
@@ -411,10 +443,48 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
 
     // block buckets
     std::map<std::string, int> bindex;
+    std::map<std::string, int> gindex;   // guard sets by orders
     for (size_t jx = 0; jx < jobs.size(); ++jx) {
         auto &ji = jobs[jx];
         const bem_block_job &J = *ji.J;
         if (J.n_blocks == 0 || absorbed[jx]) continue;
+        if (J.quad.order_mode == BEM_ORDER_LEARNED) {
+            bem_plan::Learned l;
+            l.m = ji.m->v;
+            l.m.table = ji.touch_job >= 0 ? tj[ji.touch_job].m.table : nullptr;
+            BlockLaunch &L = l.L;
+            L.row_ptr = J.row_ptr;
+            L.row_idx = J.row_idx;
+            L.col_ptr = J.col_ptr;
+            L.col_idx = J.col_idx;
+            L.n_row_clusters = J.n_row_clusters;
+            L.n_col_clusters = J.n_col_clusters;
+            L.blk_row = J.blk_row;
+            L.blk_col = J.blk_col;
+            L.blk_off = J.blk_off;
+            L.n_blocks = J.n_blocks;
+            L.out = J.out;
+            L.kind = J.kernel.kind;
+            L.kappa = J.kernel.kappa;
+            L.lower_only = 0;
+            L.allow_touching = ji.near ? 1 : 0;
+            L.mixed = is_mixed(J.quad.precision) ? 1 : 0;
+            l.precision = J.quad.precision;
+            // the tile count sizes the job's scratch: one prefix pass now
+            int64_t tiles = 0;
+            if ((e = plan_alloc(p, &l.prefix, (size_t)J.n_blocks)) != cudaSuccess ||
+                (e = launch_tile_prefix(L, kTile, 8, l.prefix, ctx->status, p->cap)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(&tiles, l.prefix + (J.n_blocks - 1), sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, p->cap)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(p->cap)) != cudaSuccess ||
+                (e = learned_alloc(l.S, tiles)) != cudaSuccess) {
+                learned_free(l.S);
+                plan_free(p);
+                return api_cuda_fail(ctx, e, "learned plan job");
+            }
+            p->learned.push_back(l);
+            continue;
+        }
         const int mixed = is_mixed(J.quad.precision) &&
                           !(J.kernel.kind == BEM_HELMHOLTZ_SLP && ji.m->v.basis == BEM_P1);
         const bool coupling = use_coupling_engine(ji.m->v.basis, J.kernel.kind, mixed, ji.near ? 1 : 0);
@@ -462,6 +532,36 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         L.lower_only = 0;
         L.allow_touching = ji.near ? 1 : 0;
         L.mixed = mixed;
+        if (b.basis == BEM_P0 && b.kind == BEM_LAPLACE_DLP && mixed) {
+            // cancellation guard: packed (value, sum of |terms|) outputs, then
+            // the guard pass of this job's orders
+            L.guard = 1;
+            char gk[64];
+            std::snprintf(gk, sizeof gk, "%d %d %d %d %d", J.quad.regular_rule, J.quad.q_regular,
+                          J.quad.q_vertex, J.quad.q_edge, J.quad.q_identical);
+            auto gi = gindex.find(gk);
+            if (gi == gindex.end()) {
+                GuardSet g;
+                g.r2 = ji.r2;
+                const int rr[4] = {J.quad.regular_rule, 0, 0, 0};
+                const int qq[4] = {J.quad.q_regular, J.quad.q_vertex, J.quad.q_edge, J.quad.q_identical};
+                for (int c = 0; c < 4; ++c) {
+                    int rc = api_get_rule4(ctx, c, rr[c], qq[c], g.rules[c]);
+                    if (rc) {
+                        plan_free(p);
+                        return rc;
+                    }
+                }
+                gindex[gk] = (int)p->guards.size();
+                p->guards.push_back(g);
+                gi = gindex.find(gk);
+            }
+            cudaError_t eg = guard_add(p->guards[gi->second], bj.m, L, p->cap);
+            if (eg != cudaSuccess) {
+                plan_free(p);
+                return api_cuda_fail(ctx, eg, "guard set-up");
+            }
+        }
         if (b.basis == BEM_P1 && !b.coupling) {
             // the tile engine reads per-slice support records built once per run
             int rows = -1, cols = -1;
@@ -496,16 +596,37 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
             return api_cuda_fail(ctx, e, "plan upload");
         }
     }
-    // profiling events: one pair per launch of issue()
-    const size_t nt = p->tb.size(), ns = p->sup.size(), nb = p->bb.size();
-    for (size_t k = 0; k < nt + ns + 2 * nb; ++k) {
+    if (!p->learned.empty()) {
+        p->model = ctx->order_model;
+        p->conf = ctx->order_conf;
+        int rc = learned_rules(ctx, p->lrules);
+        if (rc) {
+            plan_free(p);
+            return rc;
+        }
+    }
+    for (auto &g : p->guards) {
+        char *buf = nullptr;
+        if ((e = plan_alloc(p, &buf, guard_bytes(g))) != cudaSuccess ||
+            (e = guard_layout(g, buf, p->cap)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(p->cap)) != cudaSuccess) {
+            plan_free(p);
+            return api_cuda_fail(ctx, e, "guard buffers");
+        }
+    }
+    // profiling events: one pair per launch group of issue()
+    const size_t nt = p->tb.size(), ns = p->sup.size(), nb = p->bb.size(), ng = p->guards.size();
+    const size_t nl = p->learned.size();
+    for (size_t k = 0; k < nt + ns + 2 * nb + nl + ng; ++k) {
         bem_prof_rec r;
         cudaEventCreate(&r.a);
         cudaEventCreate(&r.b);
         if (k < nt) r.name = p->tb[k].name;
         else if (k < nt + ns) r.name = "supports";
         else if (k < nt + ns + nb) r.name = "tile_prefix";
-        else r.name = p->bb[k - nt - ns - nb].name;
+        else if (k < nt + ns + 2 * nb) r.name = p->bb[k - nt - ns - nb].name;
+        else if (k < nt + ns + 2 * nb + nl) r.name = "learned";
+        else r.name = "guard";
         p->prof.push_back(r);
     }
 
@@ -581,9 +702,46 @@ int bem_plan_info(bem_ctx *ctx, bem_plan *p, int32_t *n_touch_launches, int32_t 
     if (n_touch_launches) *n_touch_launches = (int32_t)p->tb.size();
     if (n_block_launches) *n_block_launches = (int32_t)p->bb.size();
     // per block bucket: tile prefix sums and job scan; per support table:
-    // slice prefix and record build
-    if (n_aux_launches) *n_aux_launches = (int32_t)(2 * p->bb.size() + 2 * p->sup.size());
+    // slice prefix and record build; per guard set: row maxima, selection and
+    // the FP64 pass
+    // per learned job: tile prefix, selection, offsets, compaction and one
+    // evaluation per class
+    if (n_aux_launches)
+        *n_aux_launches = (int32_t)(2 * p->bb.size() + 2 * p->sup.size() + 3 * p->guards.size() +
+                                    10 * p->learned.size());
     for (int k = 0; grid_mult && k < cap && k < (int)p->bb.size(); ++k) grid_mult[k] = p->bb[k].grid_mult;
+    return BEM_OK;
+}
+
+int bem_plan_learned_counts(bem_ctx *ctx, bem_plan *p, int64_t *counts)
+{
+    if (!ctx || !p || !counts) return BEM_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    for (int c = 0; c < 6; ++c) counts[c] = 0;
+    for (auto &l : p->learned) {
+        int k[8] = {0};
+        if (e == cudaSuccess) e = cudaMemcpy(k, l.S.small, sizeof(k), cudaMemcpyDeviceToHost);
+        for (int c = 0; c < 6; ++c) counts[c] += k[c];
+    }
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned counts");
+    return BEM_OK;
+}
+
+int bem_plan_guard_stats(bem_ctx *ctx, bem_plan *p, int64_t *guarded_entries, int64_t *recomputed)
+{
+    if (!ctx || !p || !guarded_entries || !recomputed) return BEM_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    int64_t n = 0, r = 0;
+    for (auto &g : p->guards) {
+        unsigned long long c[2] = {0, 0};   // disjoint and touching entries listed
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c, g.d_count, sizeof(c), cudaMemcpyDeviceToHost);
+        n += g.entries;
+        r += std::min<int64_t>((int64_t)c[0], g.cap) + std::min<int64_t>((int64_t)c[1], g.cap_t);
+    }
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "guard statistics");
+    *guarded_entries = n;
+    *recomputed = r;
     return BEM_OK;
 }
 

@@ -289,7 +289,9 @@ def test_mixed_dense_matches_oracle(ctx, pkg, meshname, kernel, kappa, basis, fo
     absint = oracle_absolute(mesh, basis, rows, cols, kernel, kappa, QUADS["paper"])
     err = rel_err_abs(got.ravel(), ref.ravel(), absint, rows)
     assert err.max() <= MIXED_TOL
-    if kernel == "laplace_slp":
+    # the row-scaled measure too: the single layer has no cancellation, and
+    # the piecewise-constant double layer has the cancellation guard
+    if kernel == "laplace_slp" or basis == "p0":
         assert rel_err(got.ravel(), ref.ravel(), rows).max() <= MIXED_TOL
     # and it is not the FP64 result in disguise
     assert err.max() > 1e-12
@@ -314,6 +316,42 @@ def test_mixed_near_field_and_coupling(ctx, pkg, basis, kernel, kappa, form):
         ref = oracle_entries(mesh, basis, r, c, kernel, kappa, QUADS["paper"])
         absint = oracle_absolute(mesh, basis, r, c, kernel, kappa, QUADS["paper"])
         assert rel_err_abs(got, ref, absint, r).max() <= MIXED_TOL
+        if kernel == "laplace_slp" or basis == "p0":
+            assert rel_err(got, ref.real, r).max() <= MIXED_TOL
+    ctx.bem_mesh_free(mid)
+
+
+@pytest.mark.parametrize("form", MIXED_FORMS)
+def test_cancellation_guard_row_scaled(ctx, pkg, form):
+    """Jittered flat faces make many double-layer pairs straddle each other's
+    planes.  With the guard the float forms meet the row-scaled bar on every
+    near-field and coupling entry, through the per-call entry points and
+    through a plan (batched, CUDA graph), and they agree bit for bit."""
+    import torch
+    quad = dict(QUADS["paper"], precision=form)
+    mesh = synth.jitter(synth.cube_surface(8), 0.05, 29)
+    part, near, far = h2_blocks(mesh, "p0", leaf_size=32, eta=2.0, rank=8, pivot_seed=5)
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p0")
+    outs = {nm: (_out(bs.n_entries, "laplace_dlp"), _out(bs.n_entries, "laplace_dlp"))
+            for nm, bs in (("near", near), ("far", far))}
+    ctx.bem_near_field([block_job(pkg, mid, near, "laplace_dlp", 0.0, quad, outs["near"][0])])
+    ctx.bem_coupling_blocks([block_job(pkg, mid, far, "laplace_dlp", 0.0, quad, outs["far"][0])])
+    plan = ctx.bem_plan_create([block_job(pkg, mid, near, "laplace_dlp", 0.0, quad, outs["near"][1])],
+                               [block_job(pkg, mid, far, "laplace_dlp", 0.0, quad, outs["far"][1])],
+                               pkg.PLAN_GRAPH)
+    ctx.bem_plan_run(plan)
+    ctx.bem_plan_run(plan)          # a second replay starts from clean guard state
+    ctx.bem_sync()
+    stats = ctx.bem_plan_guard_stats(plan)
+    ctx.bem_plan_destroy(plan)
+    assert stats["recomputed"] > 0 and stats["recomputed"] < stats["entries"] // 16
+    for nm, bs in (("near", near), ("far", far)):
+        r, c = bs.entry_indices()
+        ref = oracle_entries(mesh, "p0", r, c, "laplace_dlp", 0.0, QUADS["paper"])
+        a = outs[nm][0].cpu().numpy()[: bs.n_entries]
+        b = outs[nm][1].cpu().numpy()[: bs.n_entries]
+        assert np.array_equal(a, b), nm
+        assert rel_err(a, ref, r).max() <= MIXED_TOL, nm
     ctx.bem_mesh_free(mid)
 
 
