@@ -1,15 +1,24 @@
 #!/usr/bin/env python
-"""Benchmark: Galerkin entries/s of the near field + coupling (pivot) blocks.
+"""Benchmark: Galerkin entries/s of near-field + coupling (pivot) blocks.
 
-Workload (one step): the 20480-triangle icosphere with the piecewise-linear
-basis, H2 block partition (leaf 32, eta 2, at most 16 pivots per cluster);
-the Laplace single- and double-layer near-field blocks (Sauter-Schwab order
-5, Duffy order 3) and coupling blocks, FP64.  Inputs are resident on the
-device before the timed region; L2 is flushed (256 MiB write) between timed
-steps.  `e2e` repeats the step through the same C ABI from host buffers:
-mesh upload, block lists host->device, outputs device->host.
+Default line (--workload all): the largest configuration, C4 -- 48 closed
+meshes (16 spheres, 16 cubes, 16 tori; 500 to 30000 triangles each, 389804
+in all), piecewise-constant basis, the Laplace double layer and the
+Helmholtz single layer (kappa ~ U[1, 10]) of every mesh, H2 blocks (leaf 32,
+eta 2, at most 16 host-GCA pivots per cluster), Sauter-Schwab order 5 and
+Duffy order 3: 576 M entries per step, all of them in one persistent plan
+(one CUDA graph replay per step).  The plain FP64 form and the float forms
+are timed; every entry of each float form is compared with the FP64 form on
+both error measures, and the headline is the fastest form within 1e-6 on
+both.  Inputs are resident on the device before the timed region; L2 is
+flushed (256 MiB write) between timed steps.  `e2e` repeats the step through
+the per-call entry points from pinned host buffers (mesh upload and host
+planning, block lists in, all outputs out).  The roofline divides by peaks
+measured in the same run (bem_peak_probe).  C1, C2, C3 and C5 are measured
+in the same run under `configs`, the GCA's Green matrices of C2's tree under
+`green_matrices`.
 
---impl reference runs the plain FP64 CPU oracle on a bounded sample of the
+--impl reference runs the plain FP64 CPU oracle on bounded samples of the
 same workload's entries (the slow baseline arm).
 """
 import argparse
@@ -84,6 +93,40 @@ def flops_per_point_ss(case: str, kernel: str, basis: str) -> float:
 
 PEAK_FP64 = 152 * 2.07e9 * 4.0 / 1e12     # TFLOP/s: 152 SM x 2 FMA/clk x 2.07 GHz
 PEAK_FP32 = 152 * 2.07e9 * 256.0 / 1e12   # TFLOP/s: 152 SM x 128 FMA/clk x 2.07 GHz
+# the denominators of the rooflines: the measured rates once measure_peaks has
+# run (its FP32 and FP64 FMA probes), the unit-count products before
+PEAKS = {"fp32": PEAK_FP32, "fp64": PEAK_FP64,
+         "source": "derived: 152 SM x (2 FP64 | 128 FP32) FMA/clk x 2.07 GHz"}
+
+
+def measure_peaks(torch, ctx, stream):
+    """Measured arithmetic peaks of this GPU (bem_peak_probe): FP32 and FP64 FMA
+    rates and the special-function unit's reciprocal square root and sine/cosine
+    rates, each the best of three launches of about 20 ms timed with CUDA events
+    on the library's stream (after one warm-up launch)."""
+    trips = {0: 20000, 1: 300, 2: 2500, 3: 1250}
+    names = {0: "fp32_fma_tflops", 1: "fp64_fma_tflops", 2: "mufu_rsqrt_tops",
+             3: "mufu_sincos_tops"}
+    out = {}
+    for kind, n in trips.items():
+        ctx.bem_peak_probe(kind, n)
+        best = 0.0
+        for _ in range(3):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ops = ctx.bem_peak_probe(kind, n)
+            b.record(stream)
+            b.synchronize()
+            best = max(best, ops / (a.elapsed_time(b) / 1e3) / 1e12)
+        out[names[kind]] = round(best, 3)
+    ctx.bem_sync()
+    PEAKS.update({"fp32": out["fp32_fma_tflops"], "fp64": out["fp64_fma_tflops"],
+                  "mufu_rsqrt_tops": out["mufu_rsqrt_tops"],
+                  "source": "measured on this GPU (bem_peak_probe), see peaks"})
+    out["how"] = ("bem_peak_probe: 8 CTAs x 256 threads per SM, 8 independent chains per "
+                  "thread; FMA = 2 operations, sine and cosine = 2; best of 3 launches")
+    return out
 
 
 def kernel_flops(w, counts, stats, precision):
@@ -128,7 +171,7 @@ def kernel_flops(w, counts, stats, precision):
         f32 = precision == "mixed_full" or (mixed and cas == "touching_vertex")
         p = "fp32" if f32 else "fp64"
         out[cas] = (f, p)
-    return {k: (f, p, PEAK_FP32 if p == "fp32" else PEAK_FP64) for k, (f, p) in out.items()}
+    return {k: (f, p, PEAKS[p]) for k, (f, p) in out.items()}
 
 
 def step_rates(w, counts, stats, precision, ms_per_step):
@@ -439,6 +482,7 @@ def run_ours(args):
         prof = ctx.bem_profile_read()
         ctx.bem_profile_enable(False)
         info = ctx.bem_plan_info(plan)
+        info["guard"] = ctx.bem_plan_guard_stats(plan)
         ctx.bem_plan_destroy(plan)
         total = reduce_over_ranks(float(sum(a.elapsed_time(b) for a, b in evs)), "max", dev)
         # kernels per replay: touching buckets, block engines, prefix sums and support builds
@@ -663,34 +707,54 @@ def cpu_baseline(w, budget_s):
 
 
 def run_reference(args):
+    """The oracle (plain FP64 C, OpenMP on all host cores) timed as it stands on
+    the default line's workload, C4: each step a bounded seeded sample of the
+    48 meshes' near-field and coupling entries of both operators (seeded pivot
+    sets of the same sizes, so no oracle input comes from the library)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
+    import types
     import synth
     import oracle
     oracle.build()
-    w = synth.workloads.config2(args.levels)
-    entries_per_step = len(w.operators) * (w.near.n_entries + w.far.n_entries)
-    t0 = time_oracle(w, 1000, 3)
+    bw = synth.workloads.config4()
+    views = [types.SimpleNamespace(mesh=it.mesh, basis=bw.basis, quad=bw.quad,
+                                   operators=it.operators, near=it.near, far=it.far)
+             for it in bw.items]
+    entries_per_step = bw.n_entries
+    n0, t0 = batch_cpu_baseline(views, 0.0, seed=3)      # calibration sample
     per_step = args.ref_seconds_per_step
-    n = int(max(1000, 1000 * per_step / max(t0, 1e-3)))
-    times = []
+    n = int(max(2000, n0 * per_step / max(t0, 1e-3)))
+    tot = np.array([len(v.operators) * (v.near.n_entries + v.far.n_entries) for v in views],
+                   float)
+    frac = tot / tot.sum()
+    times, counts = [], []
     for k in range(args.warmup + args.steps):
-        t = time_oracle(w, n, 100 + k)
+        t, done = 0.0, 0
+        for m, v in enumerate(views):
+            c = int(round(n * frac[m]))
+            if c > 0:
+                t += time_oracle(v, c, 100 + 1000 * k + m)
+                done += c
         if k >= args.warmup:
             times.append(t)
-    value = n * len(times) / sum(times)
-    sample = (f"each step: {n} of the {entries_per_step} entries of the workload, drawn uniformly "
-              f"(seeded) from near-field and coupling entries of both operators")
+            counts.append(done)
+    value = sum(counts) / sum(times)
+    sample = (f"each step: {counts[0]} of the {entries_per_step} entries of the workload, drawn "
+              f"uniformly (seeded) from every mesh's near-field and coupling entries of both "
+              f"operators in proportion to its entries")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": w.name, "entries_per_step": entries_per_step, "precision": "fp64",
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": bw.name, "entries_per_step": int(entries_per_step),
+                       "precision": "fp64",
                        "pivots": "seeded, rank <= 16 (per-cluster counts as the host GCA's)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -784,6 +848,7 @@ def run_extra(args):
         prof = ctx.bem_profile_read()
         ctx.bem_profile_enable(False)
         info = ctx.bem_plan_info(plan)
+        info["guard"] = ctx.bem_plan_guard_stats(plan)
         ctx.bem_plan_destroy(plan)
         ms = float(sum(a.elapsed_time(b) for a, b in evs))
         info["kernels_per_step"] = (info["touch_launches"] + info["block_launches"] +
@@ -829,7 +894,8 @@ def run_extra(args):
         o = alloc_outs()
         ms, prof, info = run_form(f, o, args.steps, args.warmup)
         res[f] = {"value": entries * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
-                  "kernels": roofline(prof, f, args.steps), "launches": info["kernels_per_step"]}
+                  "kernels": roofline(prof, f, args.steps), "launches": info["kernels_per_step"],
+                  "guard": info["guard"]}
         # accuracy outside the timed region, against the FP64 form on every entry
         res[f]["max_rel_err_vs_fp64_form"], res[f]["max_row_scaled_err"] = max_rel_err(o, outs64)
         del o
@@ -858,13 +924,325 @@ def run_extra(args):
             "fp64_form": {"value": value64, "ms_per_step": ms64 / args.fp64_steps,
                           "steps": args.fp64_steps, "kernels": roofline(prof64, "fp64", args.fp64_steps)},
             "forms": {f: {k: r[k] for k in ("value", "ms_per_step", "max_rel_err_vs_fp64_form",
-                                            "max_row_scaled_err")}
+                                            "max_row_scaled_err", "guard")}
                       for f, r in res.items()},
             "accuracy": {"measure": "|g - g_fp64| / max(A, 1e-3 row max A), A = sum of |quadrature "
                                     "terms| (forward-error scale), every entry", "bound": 1e-6},
             "clocks": clk}
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# Plan-driven workloads (C2, C3, C4): the FP64 form and the float forms, each
+# one persistent plan (one CUDA graph replay per step) over all meshes of the
+# workload, every entry of every float form compared with the FP64 form on
+# both error measures; the chosen form is the fastest within 1e-6 on both.
+# ---------------------------------------------------------------------------
+# special-function operations per quadrature point of the float kernels:
+# rsqrt for the Laplace kernels; Helmholtz adds the reciprocal of the phase
+# offset and its sine and cosine (__fdividef, __sincosf)
+def mufu_per_point(kernel: str, kclass: str, precision: str) -> float:
+    if precision == "fp64":
+        return 1.0
+    if kernel == "helmholtz_slp" and kclass.startswith("block"):
+        return 4.0
+    return 1.0
+
+
+def kernel_points(v, counts, stats):
+    """{kernel class: quadrature points per step per operator} of one view."""
+    q = v.quad
+    npts = (q.q_regular ** 2) ** 2 if q.regular_rule == "duffy" else 49
+    out = {}
+    reg = counts["near_regular_pairs"] + counts["far_regular_pairs"]
+    out["block_p1" if v.basis == "p1" else "block_p0"] = reg * npts
+    for cas, nsub, qq, key in (("touching_vertex", 2, q.q_vertex, "n_vertex"),
+                               ("touching_edge", 4, q.q_edge, "n_edge"),
+                               ("touching_identical", 6, q.q_identical, "n_identical")):
+        out[cas] = stats[key] * nsub * qq ** 4
+    return out
+
+
+def plan_workload(torch, pkg, ctx, dev, stream, name, basis, quad, items, forms, steps,
+                  fp64_steps, warmup, gca=True, e2e_steps=0, flush=None, barrier=None,
+                  reduce_ms=None):
+    """Runs one plan-driven workload (items: mesh, operators, near, far,
+    partition) in the FP64 form and the given float forms; returns a dict with
+    the chosen form's value and per-kernel rooflines, every form's value and
+    errors, the guard's statistics, and (e2e_steps > 0) the chosen form end to
+    end through the per-call entry points with pinned host buffers."""
+    import types
+    from synth import structure, workloads
+    gca_s = 0.0
+    if gca:
+        for it in items:
+            ptr, idx = it.partition.cluster_csr()
+            kappa = max(op.kappa for op in it.operators)
+            t0 = time.perf_counter()
+            pp, pi = pkg.bem_gca_pivots(it.mesh.verts, it.mesh.tris, basis, ptr, idx,
+                                        it.partition.son_array(), kappa=kappa, gauss_per_face=4,
+                                        eps=1e-6, max_rank=16)
+            gca_s += time.perf_counter() - t0
+            fr, fc, foff, ftot = structure.coupling_blocks(it.partition, pp)
+            it.far = workloads.BlockSet(pp, pi, pp, pi, fr, fc, foff, ftot)
+    views, mids, sets, counts, stats = [], [], [], [], []
+    for it in items:
+        v = types.SimpleNamespace(mesh=it.mesh, basis=basis, quad=quad, operators=it.operators,
+                                  near=it.near, far=it.far)
+        views.append(v)
+        mids.append(ctx.bem_mesh_upload(it.mesh.verts, it.mesh.tris, basis))
+        sets.append(build_device_inputs(torch, pkg, v, dev))
+        counts.append(pair_counts(v))
+        stats.append(ctx.bem_mesh_info(mids[-1]))
+    entries = sum(len(v.operators) * (v.near.n_entries + v.far.n_entries) for v in views)
+    if flush is None:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def alloc_outs():
+        o = []
+        for v in views:
+            d = {}
+            for op in v.operators:
+                dt = torch.complex128 if op.kernel == "helmholtz_slp" else torch.float64
+                for nm in ("near", "far"):
+                    d[(op.kernel, nm)] = torch.zeros(max(1, getattr(v, nm).n_entries), dtype=dt,
+                                                     device=dev)
+            o.append(d)
+        return o
+
+    def run_form(precision, outs, n_steps, n_warm):
+        near, far = [], []
+        for v, mid, st, o in zip(views, mids, sets, outs):
+            j = make_jobs(torch, pkg, mid, v, st, o, precision)
+            near += j["near"]
+            far += j["far"]
+        plan = ctx.bem_plan_create(near, far, pkg.PLAN_GRAPH | pkg.PLAN_AUTOTUNE | pkg.PLAN_PROFILE)
+        for _ in range(n_warm):
+            ctx.bem_plan_run(plan)
+        ctx.bem_sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n_steps)]
+        ctx.bem_profile_reset()
+        ctx.bem_profile_enable(True)
+        if barrier:
+            barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(n_steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            ctx.bem_plan_run(plan)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.bem_sync()
+        if barrier:
+            barrier()
+        prof = ctx.bem_profile_read()
+        ctx.bem_profile_enable(False)
+        info = ctx.bem_plan_info(plan)
+        info["guard"] = ctx.bem_plan_guard_stats(plan)
+        ctx.bem_plan_destroy(plan)
+        ms = float(sum(a.elapsed_time(b) for a, b in evs))
+        if reduce_ms:
+            ms = reduce_ms(ms)          # the slowest rank's time
+        info["kernels_per_step"] = (info["touch_launches"] + info["block_launches"] +
+                                    info["aux_launches"])
+        return ms, prof, info
+
+    def roofline(prof, precision, n_steps):
+        model, mufu = {}, {}
+        for v, c, st in zip(views, counts, stats):
+            pts = kernel_points(v, c, st)
+            for k, (f, pipe, peak) in kernel_flops(v, c, st, precision).items():
+                f0 = model.get(k, (0.0, pipe, peak))[0]
+                model[k] = (f0 + f, pipe, peak)
+            for k, n in pts.items():
+                mufu[k] = mufu.get(k, 0.0) + sum(n * mufu_per_point(o.kernel, k, precision)
+                                                 for o in v.operators)
+        per = {}
+        for kname, (launches, ms) in prof.items():
+            if kname in model:
+                f, pipe, peak = model[kname]
+                ach = f * n_steps / (ms / 1e3) / 1e12
+                per[kname] = {"achieved": round(ach, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                              "pipe": pipe, "frac": round(ach / peak, 4), "ms": round(ms, 3),
+                              "launches": launches, "avg_launch_ms": round(ms / launches, 4)}
+                if kname in mufu and PEAKS.get("mufu_rsqrt_tops"):
+                    mach = mufu[kname] * n_steps / (ms / 1e3) / 1e12
+                    per[kname]["mufu"] = {"achieved": round(mach, 4),
+                                          "peak": PEAKS["mufu_rsqrt_tops"], "unit": "Tops/s",
+                                          "frac": round(mach / PEAKS["mufu_rsqrt_tops"], 4)}
+            else:
+                per[kname] = {"ms": round(ms, 3), "launches": launches}
+        return per
+
+    def errors(outs, outs64):
+        ea = er = 0.0
+        for v, mid, o, o64 in zip(views, mids, outs, outs64):
+            sc = error_scales(torch, pkg, ctx, dev, mid, v, quad.kw(), o64)
+            a, r = entry_errors(o, o64, sc)
+            ea, er = max(ea, a), max(er, r)
+            del sc
+        return ea, er
+
+    outs64 = alloc_outs()
+    ms64, prof64, info64 = run_form("fp64", outs64, fp64_steps, 1)
+    res = {}
+    keep = {}
+    for f in forms:
+        o = alloc_outs()
+        ms, prof, info = run_form(f, o, steps, warmup)
+        res[f] = {"value": entries * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                  "kernels": roofline(prof, f, steps), "launches": info["kernels_per_step"],
+                  "guard": info["guard"], "grid_mult": info["grid_mult"]}
+        res[f]["max_rel_err_vs_fp64_form"], res[f]["max_row_scaled_err"] = errors(o, outs64)
+        keep[f] = o
+    ok = [f for f in forms if max(res[f]["max_rel_err_vs_fp64_form"],
+                                  res[f]["max_row_scaled_err"]) <= 1e-6]
+    chosen = max(ok, key=lambda f: res[f]["value"]) if ok else None
+    for f in forms:
+        if f != chosen:
+            del keep[f]
+    value64 = entries * fp64_steps / (ms64 / 1e3)
+    out = {"workload": name, "meshes": len(items),
+           "triangles": int(sum(v.mesh.nt for v in views)), "basis": basis,
+           "operators": sorted({o.kernel for v in views for o in v.operators}),
+           "entries_per_step": int(entries), "quadrature": quad.kw(),
+           "pivots": ("host GCA per mesh (4x4 Gauss points per face, eps 1e-6, rank <= 16)"
+                      if gca else "seeded, rank <= 16"),
+           "gca_setup_s": gca_s if gca else None,
+           "chosen_form": chosen or "fp64",
+           "fp64_form": {"value": value64, "ms_per_step": ms64 / fp64_steps, "steps": fp64_steps,
+                         "kernels": roofline(prof64, "fp64", fp64_steps)},
+           "forms": {f: {k: r[k] for k in ("value", "ms_per_step", "max_rel_err_vs_fp64_form",
+                                           "max_row_scaled_err", "guard")}
+                     for f, r in res.items()}}
+    head = res[chosen] if chosen else None
+    out["value"] = head["value"] if head else value64
+    out["ms_per_step"] = head["ms_per_step"] if head else ms64 / fp64_steps
+    out["kernels"] = head["kernels"] if head else out["fp64_form"]["kernels"]
+    out["kernels_per_step"] = head["launches"] if head else info64["kernels_per_step"]
+    out["grid_mult"] = head["grid_mult"] if head else info64["grid_mult"]
+    out["steps"] = steps if head else fp64_steps
+    out["speedup_vs_fp64_form"] = out["value"] / value64
+    out["max_rel_err_vs_fp64_form"] = head["max_rel_err_vs_fp64_form"] if head else 0.0
+    out["max_row_scaled_err"] = head["max_row_scaled_err"] if head else 0.0
+
+    if e2e_steps > 0:
+        # end to end through the per-call entry points, host buffers in and out
+        outs = keep[chosen] if chosen else outs64
+        prec = chosen or "fp64"
+        pin, host_out = [], []
+        h2d = d2h = 0
+        for v, st, o in zip(views, sets, outs):
+            ph = {}
+            for nm in ("near", "far"):
+                bs = getattr(v, nm)
+                keys = ["row_ptr", "row_idx", "blk_row", "blk_col", "blk_off"]
+                if st[nm]["col_ptr"] is not st[nm]["row_ptr"]:
+                    keys += ["col_ptr", "col_idx"]
+                ph[nm] = {k: torch.from_numpy(np.ascontiguousarray(
+                    getattr(bs, k), np.int64 if k == "blk_off" else np.int32)).pin_memory()
+                    for k in keys}
+                h2d += sum(t.numel() * t.element_size() for t in ph[nm].values())
+            pin.append(ph)
+            ho = {k: torch.empty(t.shape, dtype=t.dtype).pin_memory() for k, t in o.items()}
+            d2h += sum(t.numel() * t.element_size() for t in ho.values())
+            host_out.append(ho)
+            h2d += v.mesh.verts.nbytes + v.mesh.tris.nbytes
+        times = []
+        for k in range(e2e_steps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            mids2 = []
+            for v, st, o, ph, ho in zip(views, sets, outs, pin, host_out):
+                mid2 = ctx.bem_mesh_upload(v.mesh.verts, v.mesh.tris, basis)
+                mids2.append(mid2)
+                for nm in ("near", "far"):
+                    for key, t in ph[nm].items():
+                        st[nm][key].copy_(t, non_blocking=True)
+                j2 = make_jobs(torch, pkg, mid2, v, st, o, prec)
+                ctx.bem_near_field(j2["near"])
+                ctx.bem_coupling_blocks(j2["far"])
+                for key, t in o.items():
+                    ho[key].copy_(t, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            ctx.bem_sync()
+            t1 = time.perf_counter()
+            for m2 in mids2:
+                ctx.bem_mesh_free(m2)
+            if k > 0:
+                times.append(t1 - t0)
+        out["e2e"] = {"value": entries / statistics.mean(times), "unit": UNIT,
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                      "steps": len(times),
+                      "includes": "per mesh: upload + host planning, block lists H2D, "
+                                  "bem_near_field + bem_coupling_blocks, all outputs D2H"}
+    for mid in mids:
+        ctx.bem_mesh_free(mid)
+    out["_views"] = views
+    return out
+
+
+def measure_c1(torch, pkg, ctx, dev, stream, steps, warmup, flush):
+    """C1: the dense 1280 x 1280 Laplace single-layer matrix (P0, SS q=4, Radon
+    7 x 7) through bem_assemble_dense, in the FP64 form and the float forms;
+    every entry of each float form against the FP64 form (both measures)."""
+    import synth
+    w = synth.workloads.config1()
+    n = w.mesh.nt
+    mid = ctx.bem_mesh_upload(w.mesh.verts, w.mesh.tris, "p0")
+    kd = pkg.kernel_desc("laplace_slp")
+
+    def run(prec):
+        qd = pkg.quad_desc(**w.quad.kw(), precision=prec)
+        out = torch.zeros(n * n, dtype=torch.float64, device=dev)
+        for _ in range(warmup):
+            ctx.bem_assemble_dense(mid, kd, qd, 0, out)
+        ctx.bem_sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            ctx.bem_assemble_dense(mid, kd, qd, 0, out)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.bem_sync()
+        return float(sum(a.elapsed_time(b) for a, b in evs)) / steps, out
+
+    ms64, o64 = run("fp64")
+    rows = torch.arange(n, dtype=torch.int32, device=dev).repeat_interleave(n)
+    cols = torch.arange(n, dtype=torch.int32, device=dev).repeat(n)
+    A = torch.empty(n * n, dtype=torch.float64, device=dev)
+    ctx.bem_pivot_entries_absolute(mid, kd, pkg.quad_desc(**w.quad.kw()), rows, cols, A)
+    ctx.bem_sync()
+    # column-major output: entry (i, j) at j n + i; rows/cols above are row-major
+    A = A.view(n, n).t().reshape(-1)
+    g64 = o64.view(n, n)                      # [j, i]
+    rmax = g64.abs().max(dim=0).values        # per row i
+    row_scale = torch.maximum(g64.abs(), 1e-3 * rmax[None, :]).reshape(-1)
+    Am = A.view(n, n)
+    a_scale = torch.maximum(Am, 1e-3 * Am.max(dim=0).values[None, :]).reshape(-1)
+    forms = {}
+    for f in ("mixed_full", "mixed"):
+        ms, o = run(f)
+        d = (o - o64).abs()
+        forms[f] = {"value": n * n / (ms / 1e3), "ms_per_step": ms,
+                    "max_rel_err_vs_fp64_form": (d / a_scale).max().item(),
+                    "max_row_scaled_err": (d / row_scale).max().item()}
+    ctx.bem_mesh_free(mid)
+    ok = [f for f in forms if max(forms[f]["max_rel_err_vs_fp64_form"],
+                                  forms[f]["max_row_scaled_err"]) <= 1e-6]
+    chosen = max(ok, key=lambda f: forms[f]["value"]) if ok else None
+    head = forms[chosen] if chosen else {"value": n * n / (ms64 / 1e3), "ms_per_step": ms64}
+    return {"workload": w.name, "triangles": n, "entries_per_step": n * n,
+            "quadrature": w.quad.kw(), "call": "bem_assemble_dense (full matrix)",
+            "chosen_form": chosen or "fp64", "value": head["value"],
+            "ms_per_step": head["ms_per_step"], "steps": steps,
+            "fp64_form": {"value": n * n / (ms64 / 1e3), "ms_per_step": ms64},
+            "forms": forms}
 
 
 # ---------------------------------------------------------------------------
@@ -876,7 +1254,7 @@ def run_extra(args):
 # judged on seeded sampled blocks against FP64 pivot entries at Duffy order 10
 # (forward-error scale).
 # ---------------------------------------------------------------------------
-def run_c5(args):
+def run_c5(args, emit=True):
     import types
     import torch
     import synth
@@ -1087,8 +1465,10 @@ def run_c5(args):
                                     "|quadrature terms of g_ref|",
                          "sampled_entries": n_cmp, "max_err": acc, "bound": 1e-6},
             "clocks": clk}
-    print(json.dumps(line), flush=True)
     ctx.close()
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 # FP64 operations of the Green-matrix kernel (FMA = 2, rsqrt = 1, sincos = 2):
@@ -1180,11 +1560,11 @@ def measure_green(torch, pkg, ctx, mid, w, dev, stream, steps, warmup):
         res[kernel] = {"value": G["total"] * steps / (ms / 1e3), "unit": "entries/s",
                        "ms_per_step": ms / steps, "steps": steps,
                        "roofline": {"bound": "alu", "achieved": round(ach, 4),
-                                    "peak": round(PEAK_FP64, 4), "unit": "TFLOP/s",
-                                    "frac": round(ach / PEAK_FP64, 4), "traffic": None,
+                                    "peak": round(PEAKS["fp64"], 4), "unit": "TFLOP/s",
+                                    "frac": round(ach / PEAKS["fp64"], 4), "traffic": None,
                                     "kernel": "green", "pipe": "fp64",
                                     "flops_per_step": flops,
-                                    "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz"}}
+                                    "peak_source": PEAKS["source"]}}
         del out
     del flush
     # the GCA with every level's A_t from the device and the cross approximation
@@ -1308,6 +1688,197 @@ def green_cpu_baseline(w, G, budget_s):
                       f"on {os.cpu_count()} OpenMP threads"}
 
 
+def batch_cpu_baseline(views, budget_s, seed=1):
+    """The oracle on a seeded sample of a batch's entries (all meshes, operators,
+    near field and coupling blocks), sampled in proportion to each mesh's
+    entries, on all host cores; entries/s."""
+    import oracle
+    oracle.build()
+    tot = np.array([len(v.operators) * (v.near.n_entries + v.far.n_entries) for v in views],
+                   float)
+    frac = tot / tot.sum()
+
+    def run(n, sd):
+        t = 0.0
+        done = 0
+        for k, v in enumerate(views):
+            m = int(round(n * frac[k]))
+            if m <= 0:
+                continue
+            t += time_oracle(v, m, sd + k)
+            done += m
+        return done, t
+
+    n0, t0 = run(4000, seed)
+    if budget_s <= 0:
+        return n0, t0
+    # grow the sample until it takes about the budget (the first samples are
+    # dominated by the per-mesh set-up of the oracle's calls)
+    n, t, k = n0, t0, 0
+    while t < 0.5 * budget_s and n < 50_000_000 and k < 4:
+        n = int(min(50_000_000, max(2 * n, n * budget_s / max(t, 1e-3))))
+        n, t = run(n, seed + 1000 * (k + 1))
+        k += 1
+    return n, t
+
+
+def shard_items(items, rank, ws):
+    """Contiguous cost-balanced ranges of a batch's meshes, one per rank (cost:
+    entries x operators), from the library's shard planner (bem_shard_blocks)."""
+    import paper_1510_07244_gb300 as pkg
+    cost = np.array([len(it.operators) * (it.near.n_entries + it.far.n_entries) for it in items],
+                    np.int64)
+    b = pkg.bem_shard_blocks(cost, ws)
+    return items[int(b[rank]):int(b[rank + 1])]
+
+
+def run_all(args):
+    """The default line: the largest configuration, C4 (48 meshes, 576 M entries
+    per step, one plan), as the headline, with its roofline against measured
+    peaks, the oracle on the host cores and the end-to-end figure; C1, C2, C3
+    and C5 measured in the same run under `configs`; the Green matrices of
+    C2's tree under `green_matrices`."""
+    import torch
+    import synth
+    import paper_1510_07244_gb300 as pkg
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = pkg.Context(local, stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks = measure_peaks(torch, ctx, stream)
+    bw = synth.workloads.config4()
+    items = shard_items(bw.items, rank, ws) if ws > 1 else bw.items
+    barrier = (lambda: torch.distributed.barrier()) if ws > 1 else None
+    reduce_ms = (lambda ms: reduce_over_ranks(ms, "max", dev)) if ws > 1 else None
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    forms = ["mixed_full", "mixed"] if args.form == "auto" else [args.form]
+    r4 = plan_workload(torch, pkg, ctx, dev, stream, bw.name, bw.basis, bw.quad, items, forms,
+                       args.steps, args.fp64_steps, args.warmup, gca=args.pivots == "gca",
+                       e2e_steps=args.e2e_steps if ws == 1 else 0, flush=flush,
+                       barrier=barrier, reduce_ms=reduce_ms)
+    clk = clocks.stop()
+    views = r4.pop("_views")
+    entries_all = reduce_over_ranks(r4["entries_per_step"], "sum", dev) if ws > 1 else \
+        r4["entries_per_step"]
+    value = entries_all / (r4["ms_per_step"] / 1e3)
+
+    # roofline of the dominant kernel of the chosen form
+    kern = r4["kernels"]
+    dom = max((k for k in kern if "ms" in kern[k]), key=lambda k: kern[k]["ms"])
+    roof = dict(kern[dom])
+    roof.update({"bound": "alu", "kernel": dom, "traffic": None,
+                 "peak_source": PEAKS["source"] + " (FP32 FMA probe; 'mufu': the reciprocal "
+                                                  "square root probe)"})
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        n, t = batch_cpu_baseline(views, args.cpu_seconds)
+        cpu = {"value": n / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} entries drawn uniformly (seeded) from the 48 meshes' near-field "
+                         f"and coupling entries of both operators, in proportion to each mesh's "
+                         f"entries; {t:.1f} s on {os.cpu_count()} OpenMP threads"}
+
+    configs = {}
+    if ws == 1 and not args.headline_only:
+        steps_x = max(3, args.steps // 2)
+        for key, fn in (("C1", lambda: measure_c1(torch, pkg, ctx, dev, stream, steps_x,
+                                                  args.warmup, flush)),
+                        ("C2", lambda: _config_plan(torch, pkg, ctx, dev, stream, flush, args,
+                                                    synth.workloads.config2(args.levels),
+                                                    steps_x)),
+                        ("C3", lambda: _config_plan(torch, pkg, ctx, dev, stream, flush, args,
+                                                    synth.workloads.config3(), steps_x)),
+                        ("C5", lambda: _config_c5(args, steps_x))):
+            try:
+                configs[key] = fn()
+            except Exception as e:      # recorded beside the headline, already measured
+                configs[key] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
+
+    green = None
+    if rank == 0 and ws == 1 and not args.no_green and not args.headline_only:
+        try:
+            w2 = synth.workloads.config2(args.levels)
+            use_gca_pivots(pkg, w2)
+            mid = ctx.bem_mesh_upload(w2.mesh.verts, w2.mesh.tris, w2.basis)
+            green, _ = measure_green(torch, pkg, ctx, mid, w2, dev, stream, args.steps,
+                                     args.warmup)
+            ctx.bem_mesh_free(mid)
+        except Exception as e:
+            green = {"error": f"{type(e).__name__}: {e}"}
+
+    if rank == 0:
+        chosen = r4["chosen_form"]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": r4["steps"], "warmup": args.warmup, "ms_per_step": r4["ms_per_step"],
+                "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak",
+                "vs_baseline": None,
+                "dtype": "f32+f64 (mixed)" if chosen != "fp64" else "f64", "data": "synthetic",
+                "config": {"workload": r4["workload"], "meshes": len(bw.items),
+                           "triangles": int(sum(it.mesh.nt for it in bw.items)),
+                           "basis": bw.basis, "operators": r4["operators"],
+                           "entries_per_step": int(entries_all), "quadrature": r4["quadrature"],
+                           "precision": chosen, "order_mode": "fixed",
+                           "pivots": r4["pivots"], "gca_setup_s": r4["gca_setup_s"],
+                           "sharding": (f"{ws} ranks, contiguous cost-balanced mesh ranges"
+                                        if ws > 1 else None),
+                           "l2": "flushed between timed steps (256 MiB write, untimed)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": r4.get("e2e"),
+                "gpu_launches": int(r4["kernels_per_step"] * r4["steps"]),
+                "peaks": peaks,
+                "accuracy": {"max_rel_err_vs_fp64_form": r4["max_rel_err_vs_fp64_form"],
+                             "max_row_scaled_err": r4["max_row_scaled_err"], "bound": 1e-6,
+                             "forward_error_scale": "|g - g_fp64| / max(A, 1e-3 row max A), "
+                                                    "A = sum of |quadrature terms|",
+                             "row_scaled": "|g - g_fp64| / max(|g_fp64|, 1e-3 row max |g_fp64|)"
+                                           ", rows per mesh, operator and block set",
+                             "entries_compared": int(r4["entries_per_step"])},
+                "kernels": kern, "fp64_form": r4["fp64_form"], "forms": r4["forms"],
+                "speedup_vs_fp64_form": r4["speedup_vs_fp64_form"],
+                "driver": {"kind": "persistent batched plan, one CUDA graph replay per step",
+                           "autotuned_ctas_per_sm": r4["grid_mult"]},
+                "configs": configs, "green_matrices": green, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _config_plan(torch, pkg, ctx, dev, stream, flush, args, w, steps):
+    """One single-mesh workload (C2, C3) as a plan, with the oracle's rate."""
+    from synth import workloads
+    it = workloads.BatchItem(w.mesh, w.operators, w.near, w.far, w.partition)
+    r = plan_workload(torch, pkg, ctx, dev, stream, w.name, w.basis, w.quad, [it],
+                      ["mixed_full", "mixed"], steps, max(1, args.fp64_steps - 1), args.warmup,
+                      gca=args.pivots == "gca", flush=flush)
+    views = r.pop("_views")
+    if not args.no_cpu_baseline:
+        n, t = batch_cpu_baseline(views, 4.0)
+        r["cpu_baseline"] = {"value": n / t, "unit": UNIT, "cores": os.cpu_count(),
+                             "sample": f"{n} seeded entries, {t:.1f} s"}
+    return r
+
+
+def _config_c5(args, steps):
+    """C5 (learned orders) through run_c5 with fewer timed steps."""
+    a = copy.copy(args)
+    a.steps = steps
+    a.fp64_steps = 1
+    line = run_c5(a, emit=False)
+    for k in ("metric", "unit", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data",
+              "clocks"):
+        line.pop(k, None)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1330,10 +1901,14 @@ def main():
                          "reports the fastest within 1e-6 of the FP64 form")
     ap.add_argument("--pivots", default="gca", choices=["gca", "seeded"],
                     help="coupling pivots from the host GCA (default) or seeded per cluster")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "green"],
-                    help="c2 (default): the 20480-triangle P1 benchmark line; c3 / c4: the "
-                         "49152-triangle Helmholtz cube / the 48-mesh batch, measured the same "
-                         "way; green: the GCA's Green quadrature matrices A_t of the c2 tree")
+    ap.add_argument("--workload", default="all",
+                    choices=["all", "c2", "c3", "c4", "c5", "green"],
+                    help="all (default): the C4 headline (48 meshes) with C1, C2, C3 and C5 "
+                         "under 'configs'; c2: the 20480-triangle P1 line alone; c3 / c4: the "
+                         "49152-triangle Helmholtz cube / the 48-mesh batch alone; c5: learned "
+                         "orders; green: the GCA's Green quadrature matrices A_t of the c2 tree")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="with --workload all: only the C4 headline (no configs, no green)")
     ap.add_argument("--c5-n", type=int, default=128,
                     help="C5 sphere subdivision (8 n^2 triangles; 128 = the 131072-triangle "
                          "workload, smaller values only for profiling captures)")
@@ -1343,8 +1918,23 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
+    ws_env = os.environ.get("WORLD_SIZE")
+    if ws_env is None and args.gpus > 1:
+        # start one rank per GPU on this node and hand back the launcher's status
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+               f"--nproc-per-node={args.gpus}", "--master-addr=127.0.0.1",
+               f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+        raise SystemExit(subprocess.call(cmd))
+    if ws_env is not None and int(ws_env) != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={ws_env}: launch one rank per GPU")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "all":
+        run_all(args)
     elif args.workload == "c5":
         run_c5(args)
     elif args.workload == "green":

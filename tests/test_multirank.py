@@ -31,7 +31,11 @@ def _rank_main(rank, ws, port, out):
     mine = int(bench.block_costs(w.near)[lo:hi].sum())
     total = bench.reduce_over_ranks(mine, "sum")
     slowest = bench.reduce_over_ranks(10.0 + rank, "max")
-    out[rank] = (lo, hi, mine, total, slowest)
+    # the default line's sharding: contiguous cost-balanced ranges of a batch's meshes
+    batch = synth.workloads.config4(count=6, lo=200.0, hi=800.0)
+    ids = [id(it) for it in bench.shard_items(batch.items, rank, ws)]
+    pos = [k for k, it in enumerate(batch.items) if id(it) in ids]
+    out[rank] = (lo, hi, mine, total, slowest, pos)
     tdist.barrier()
     tdist.destroy_process_group()
 
@@ -50,6 +54,7 @@ def test_two_rank_sharding_and_reductions():
     assert r0[2] + r1[2] == costs.sum() == r0[3] == r1[3]                # summed entries
     assert r0[4] == r1[4] == 11.0                                         # max over ranks
     assert abs(r0[2] - r1[2]) <= costs.max()                              # balanced
+    assert r0[5] + r1[5] == list(range(6)) and r0[5] and r1[5]           # meshes split, once
 
 
 def test_shard_planner_properties():
