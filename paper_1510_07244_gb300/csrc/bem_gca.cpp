@@ -215,7 +215,8 @@ void largest(const std::vector<cplx> &A, int rows, int cols, int &bi, int &bj, d
 // order they were chosen.  T = double for real matrices (kappa = 0), whose
 // arithmetic is that of the complex form with zero imaginary parts.
 template <class T>
-std::vector<int> aca_complete(std::vector<T> &A, int rows, int cols, double eps, int max_rank)
+std::vector<int> aca_complete(std::vector<T> &A, int rows, int cols, double eps, int max_rank,
+                              std::vector<int> *piv_cols = nullptr)
 {
     std::vector<int> piv;
     double first = 0.0;
@@ -228,6 +229,7 @@ std::vector<int> aca_complete(std::vector<T> &A, int rows, int cols, double eps,
         if (k == 0) first = best;
         else if (best <= eps * first) break;
         piv.push_back(bi);
+        if (piv_cols) piv_cols->push_back(bj);
         const T p = A[(size_t)bi * cols + bj];
         for (int i = 0; i < rows; ++i) colv[i] = A[(size_t)i * cols + bj] / p;
         for (int j = 0; j < cols; ++j) rowv[j] = A[(size_t)bi * cols + j];
@@ -339,6 +341,76 @@ std::vector<int32_t> pivots_of(const HostMesh &M, const ClusterGreen &G, std::ve
     for (int r : chosen) out.push_back(G.rows[r]);
     std::sort(out.begin(), out.end());
     return out;
+}
+
+// The cluster's interpolation matrix (Section 2.3): with the pivot rows t~
+// (ascending) and the pivot columns tau that the cross approximation chose,
+//     V = (A_t)|rows x tau  ((A_t)|t~ x tau)^-1,
+// rows x K row-major (K = |t~|, columns in the order of t~), so that
+// A_t ~ V (A_t)|t~ x all and the rows of V at t~ form the identity.  Solved by
+// Gaussian elimination with partial pivoting on the K x K system.
+struct ClusterBasis {
+    std::vector<int32_t> piv;    // ascending
+    std::vector<cplx> V;         // rows x K
+};
+
+ClusterBasis basis_of(const HostMesh &M, const ClusterGreen &G, std::vector<cplx> &A, double eps,
+                      int max_rank)
+{
+    const int m = G.Z.m, rn = (int)G.rows.size(), cols = 2 * m;
+    const std::vector<cplx> A0 = A;
+    std::vector<int> chosen, tau;
+    if (M.kappa == 0.0) {
+        std::vector<double> Ar(A.size());
+        for (size_t k = 0; k < A.size(); ++k) Ar[k] = A[k].real();
+        chosen = aca_complete(Ar, rn, cols, eps, max_rank, &tau);
+    } else {
+        chosen = aca_complete(A, rn, cols, eps, max_rank, &tau);
+    }
+    const int K = (int)chosen.size();
+    // pivot rows in ascending index order
+    std::vector<int> order(K);
+    for (int k = 0; k < K; ++k) order[k] = k;
+    std::sort(order.begin(), order.end(),
+              [&](int x, int y) { return G.rows[chosen[x]] < G.rows[chosen[y]]; });
+    ClusterBasis B;
+    for (int k = 0; k < K; ++k) B.piv.push_back(G.rows[chosen[order[k]]]);
+    if (K == 0) return B;
+    // P[k][l] = A0[row chosen[order[k]], col tau[l]]; V P = C with C = A0[:, tau]
+    // <=> P^T V^T = C^T: factor Q = P^T (K x K) once, solve for every row of C
+    std::vector<cplx> Q((size_t)K * K);
+    for (int k = 0; k < K; ++k)
+        for (int l = 0; l < K; ++l) Q[(size_t)l * K + k] = A0[(size_t)chosen[order[k]] * cols + tau[l]];
+    std::vector<int> pr(K);
+    for (int k = 0; k < K; ++k) pr[k] = k;
+    for (int k = 0; k < K; ++k) {
+        int best = k;
+        for (int i = k + 1; i < K; ++i)
+            if (std::abs(Q[(size_t)i * K + k]) > std::abs(Q[(size_t)best * K + k])) best = i;
+        if (best != k) {
+            for (int j = 0; j < K; ++j) std::swap(Q[(size_t)k * K + j], Q[(size_t)best * K + j]);
+            std::swap(pr[k], pr[best]);
+        }
+        for (int i = k + 1; i < K; ++i) {
+            const cplx f = Q[(size_t)i * K + k] / Q[(size_t)k * K + k];
+            Q[(size_t)i * K + k] = f;
+            for (int j = k + 1; j < K; ++j) Q[(size_t)i * K + j] -= f * Q[(size_t)k * K + j];
+        }
+    }
+    B.V.assign((size_t)rn * K, cplx(0.0));
+    std::vector<cplx> b(K);
+    for (int r = 0; r < rn; ++r) {
+        // right-hand side: row r of C, i.e. A0[r, tau[l]] for l < K, permuted
+        for (int k = 0; k < K; ++k) b[k] = A0[(size_t)r * cols + tau[pr[k]]];
+        for (int i = 1; i < K; ++i)
+            for (int j = 0; j < i; ++j) b[i] -= Q[(size_t)i * K + j] * b[j];
+        for (int i = K - 1; i >= 0; --i) {
+            for (int j = i + 1; j < K; ++j) b[i] -= Q[(size_t)i * K + j] * b[j];
+            b[i] /= Q[(size_t)i * K + i];
+        }
+        for (int k = 0; k < K; ++k) B.V[(size_t)r * K + k] = b[k];
+    }
+    return B;
 }
 
 // Pivots of cluster c, given its sons' pivots.
@@ -489,6 +561,52 @@ extern "C" int bem_gca_pivots(const double *verts, int64_t nv, const int32_t *tr
         parallel_for(level.size(), R.nthr, [&](size_t k) {
             piv[level[k]] = cluster_pivots(R.M, R.T, level[k], piv, R.g, R.gw, eps, max_rank);
         });
+    }
+    return gca_write(piv, piv_ptr, piv_idx, cap);
+}
+
+extern "C" int bem_gca_bases(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                             int32_t basis, double kappa, const int32_t *cl_ptr,
+                             const int32_t *cl_idx, const int32_t *cl_son, int32_t n_clusters,
+                             int32_t gauss_per_face, double eps, int32_t max_rank,
+                             int32_t n_threads, int32_t *piv_ptr, int32_t *piv_idx, int64_t cap,
+                             int64_t *v_off, double *V, int64_t v_cap)
+{
+    if (!v_off || !V || v_cap < 0) return BEM_ERR_INVALID_ARG;
+    GcaRun R;
+    const int rc = gca_setup(verts, nv, tris, nt, basis, kappa, cl_ptr, cl_idx, cl_son, n_clusters,
+                             gauss_per_face, eps, max_rank, n_threads, piv_ptr, piv_idx, cap, R);
+    if (rc != BEM_OK) return rc;
+    std::vector<std::vector<int32_t>> piv(n_clusters);
+    std::vector<std::vector<cplx>> mats(n_clusters);
+    for (int d = R.max_depth; d >= 0; --d) {
+        const std::vector<int> level = level_clusters(R, d);
+        parallel_for(level.size(), R.nthr, [&](size_t k) {
+            const int c = level[k];
+            const ClusterGreen G = cluster_green(R.M, R.T, c, piv, R.g, R.gw);
+            if (G.rows.empty()) {
+                piv[c].clear();
+                mats[c].clear();
+                return;
+            }
+            std::vector<cplx> A;
+            host_green_matrix(R.M, G, A);
+            ClusterBasis B = basis_of(R.M, G, A, eps, max_rank);
+            piv[c] = std::move(B.piv);
+            mats[c] = std::move(B.V);
+        });
+    }
+    const int w = kappa != 0.0 ? 2 : 1;   // doubles per element
+    int64_t at = 0;
+    v_off[0] = 0;
+    for (int c = 0; c < n_clusters; ++c) {
+        if (at + (int64_t)mats[c].size() > v_cap) return BEM_ERR_INVALID_ARG;
+        for (size_t k = 0; k < mats[c].size(); ++k) {
+            V[w * (at + (int64_t)k)] = mats[c][k].real();
+            if (w == 2) V[2 * (at + (int64_t)k) + 1] = mats[c][k].imag();
+        }
+        at += (int64_t)mats[c].size();
+        v_off[c + 1] = at;
     }
     return gca_write(piv, piv_ptr, piv_idx, cap);
 }
