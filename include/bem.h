@@ -238,6 +238,28 @@ int bem_mlp_gradients(bem_ctx *ctx, bem_mlp *mlp, const float *X, const int32_t 
 /* one Adam step (beta 0.9 / 0.999) on the n rows; loss = mean loss before the step */
 int bem_mlp_train_step(bem_ctx *ctx, bem_mlp *mlp, const float *X, const int32_t *y, int32_t n,
                        float lr, float *loss);
+/* Normalisation from raw features: the mean and population standard
+ * deviation of each of the 8 columns of X (device, n x 8 raw features), in
+ * FP64 with a fixed reduction order; stored as the model's mean and 1/std
+ * (a standard deviation below 1e-6 counts as 1). */
+int bem_mlp_fit_norm(bem_ctx *ctx, bem_mlp *mlp, const float *X, int64_t n);
+/* One epoch of training on RAW features: for every minibatch of `batch` rows
+ * of the permutation perm (device int64[n], row indices of X and y), the rows
+ * are gathered and normalised with the model's mean / std, then one Adam step
+ * as bem_mlp_train_step.  mean_loss (may be NULL) = the per-row mean of the
+ * minibatch losses, each taken before its step; waits for the stream once. */
+int bem_mlp_train_epoch(bem_ctx *ctx, bem_mlp *mlp, const float *X, const int32_t *y, int64_t n,
+                        const int64_t *perm, int32_t batch, float lr, float *mean_loss);
+/* Training labels from the method itself, for disjoint pairs (a[k], b[k]) of a
+ * piecewise-constant mesh (device int32 arrays): the pair is integrated with
+ * the six classes' rules and with Duffy q_ref (FP64, bem_pivot_entries), and
+ * err_c = |g_c - g_ref| / A_ref (A_ref: the sum of the magnitudes of the
+ * reference's terms, the forward-error scale); labels[k] (device int32) = the
+ * cheapest class with err_c <= tol, else class 5.  errors (device n x 6
+ * floats, may be NULL) receives err_c.  Waits for the stream. */
+int bem_order_labels(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
+                     const int32_t *a, const int32_t *b, int64_t n, float tol, int32_t q_ref,
+                     int32_t *labels, float *errors);
 /* logits (n x 6, device) of the BF16 tensor-core inference */
 int bem_mlp_infer(bem_ctx *ctx, bem_mlp *mlp, const float *X, int64_t n, float *logits);
 /* features of pairs (a[k], b[k]) of a piecewise-constant mesh (normalised by the
@@ -280,8 +302,14 @@ int bem_learned_counts(bem_ctx *ctx, int64_t *counts /* [6] */);
  * distinct cluster list; their storage is sized from the lists' total length
  * at creation (one device read), and a later run whose lists need more
  * records reports BEM_ERR_INVALID_ARG through the status word.
- * Plans run the fixed orders of each job's bem_quad_desc: a job with
- * order_mode BEM_ORDER_LEARNED is rejected with BEM_ERR_UNSUPPORTED.
+ * A job with order_mode BEM_ORDER_LEARNED (piecewise-constant basis only,
+ * else BEM_ERR_UNSUPPORTED) runs the learned path of bem_near_field inside the
+ * plan (tile prefix sums, selection by the order model, compaction by class,
+ * one evaluation per class), with the order model and confidence set by
+ * bem_set_order_model at plan creation (BEM_ERR_INVALID_ARG if none): the
+ * model must stay alive until bem_plan_destroy.  Its scratch is sized from
+ * the job's tile count at creation; its results equal bem_near_field's.
+ * The cancellation guard below covers fixed-order jobs only.
  * In the float forms a piecewise-linear Laplace single-layer job and a
  * double-layer job of the same kind (both near field or both coupling) with
  * the same mesh, the same block-list pointers and the same regular rule,
@@ -306,6 +334,29 @@ int bem_plan_destroy(bem_ctx *ctx, bem_plan *plan);
 int bem_plan_info(bem_ctx *ctx, bem_plan *plan, int32_t *n_touch_launches,
                   int32_t *n_block_launches, int32_t *n_aux_launches, int32_t *grid_mult,
                   int32_t cap);
+
+/* Cancellation guard of the float forms (piecewise-constant double layer).
+ * A double-layer entry whose test triangle straddles the trial triangle's
+ * plane sums terms of both signs (Eq. 1 with the kernel of Section 4's K);
+ * its float value then carries an error of a few float ulps of the sum of
+ * the magnitudes of its terms, A, which can exceed 1e-6 of the entry or of a
+ * thousandth of the largest entry of its row.  Plans (and bem_near_field /
+ * bem_coupling_blocks) running a BEM_LAPLACE_DLP job in BEM_MIXED or
+ * BEM_MIXED_FULL on a BEM_P0 mesh therefore check every entry after the float
+ * pass: if 8e-7 A > 1e-6 max(|g|, 1e-3 max over the job's row of |g|), the
+ * entry is recomputed with the FP64 form's rules in double-float arithmetic
+ * (float hi + lo pairs, about 44 bits).  This call waits for
+ * the context's stream and returns the number of guarded entries of the plan
+ * and how many of them the last run recomputed.  The per-call entry points
+ * read the job's cluster and block arrays to size the guard's scratch, so a
+ * guarded job makes them wait for the stream. */
+int bem_plan_guard_stats(bem_ctx *ctx, bem_plan *plan, int64_t *guarded_entries,
+                         int64_t *recomputed);
+
+/* Rule-class counts of the plan's learned-order jobs in its last run (HOST
+ * int64[6], classes in the order of bem_learned_counts); waits for the
+ * context's stream. */
+int bem_plan_learned_counts(bem_ctx *ctx, bem_plan *plan, int64_t *counts);
 
 /* ---- sharding (multi-GPU) ----------------------------------------------------
  * Every matrix entry is independent (Section 3: the work lists need no
@@ -372,6 +423,26 @@ int bem_gca_pivots(const double *verts, int64_t nv, const int32_t *tris, int64_t
                    const int32_t *cl_son, int32_t n_clusters, int32_t gauss_per_face, double eps,
                    int32_t max_rank, int32_t n_threads, int32_t *piv_ptr, int32_t *piv_idx,
                    int64_t cap);
+
+/* GCA pivots and interpolation matrices (Section 2.3: V_t = (A_t)|rows x tau
+ * ((A_t)|t~ x tau)^-1 with the pivot rows t~ and pivot columns tau that the
+ * cross approximation chose; Section 2.4: nested bases).  Same arguments and
+ * pivots as bem_gca_pivots, plus the matrices: cluster c's matrix has one row
+ * per row of its Green problem -- every index of a leaf in cl_idx order, or
+ * for a cluster with sons the sons' pivots (first son first, each ascending),
+ * the rows t^ of its transfer matrix V^_t -- and one column per pivot of c
+ * (ascending), row-major, at element offset v_off[c] of V (v_off HOST
+ * int64[n_clusters + 1], v_off[c + 1] - v_off[c] = rows x K_c).  V is a HOST
+ * array of v_cap elements: doubles for kappa = 0, (re, im) double pairs
+ * otherwise; (n_indices + 2 max_rank n_clusters) max_rank elements always
+ * suffice.  The rows at the pivots form the identity (the interpolation
+ * property R_t V_t = I), up to rounding.  Errors as bem_gca_pivots, and
+ * BEM_ERR_INVALID_ARG for NULL v_off or V or v_cap too small. */
+int bem_gca_bases(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, int32_t basis,
+                  double kappa, const int32_t *cl_ptr, const int32_t *cl_idx,
+                  const int32_t *cl_son, int32_t n_clusters, int32_t gauss_per_face, double eps,
+                  int32_t max_rank, int32_t n_threads, int32_t *piv_ptr, int32_t *piv_idx,
+                  int64_t cap, int64_t *v_off, double *V, int64_t v_cap);
 
 /* ---- Green quadrature matrices (device) --------------------------------------
  * The matrices A_t = (A_t+, A_t-) of Green's representation formula that the
@@ -504,6 +575,66 @@ int64_t bem_rule_points(int32_t cas, int32_t regular_rule, int32_t q, double *ou
  *     calls that overlap on the GPU (other streams or contexts on the same
  *     device) race and may produce wrong entries. */
 int bem_near_field_noalloc(bem_ctx *ctx, const bem_block_job *job);
+
+/* ---- H2 matrix-vector product and conjugate gradients -----------------------
+ * The H2 matrix of Section 2.4 built from the blocks this library assembles,
+ * and the solve of Section 4 (the interior Dirichlet problem V a = (1/2 M + K) b
+ * by conjugate gradients, V symmetric positive definite):
+ *     G ~ sum over near blocks (t, s) of N_ts  +  sum over admissible blocks of
+ *         V_t S_ts V_s^T,   S_ts = G|t~ x s~ (coupling entries at the pivots),
+ * with the nested cluster bases of bem_gca_bases (V_t = diag(V_t1, V_t2) V^_t
+ * for a cluster with sons).  Real (FP64) matrices: the Laplace kernels.
+ *   n             number of indices (basis functions)
+ *   cl_ptr, cl_idx, cl_son, n_clusters  HOST cluster tree as for bem_gca_pivots
+ *   piv_ptr, piv_idx, v_off, V          HOST output of bem_gca_bases (kappa = 0;
+ *                                        at most 32 pivots per cluster)
+ *   near_row, near_col, near_off  HOST near blocks (row cluster, column cluster,
+ *                 element offset): leaves only, column-major |t| x |s| over the
+ *                 clusters' index sets at near_vals + near_off (DEVICE, the
+ *                 output of bem_near_field for the same blocks)
+ *   far_row, far_col, far_off     HOST admissible blocks, column-major
+ *                 |t~| x |s~| over the pivots at far_vals + far_off (DEVICE, the
+ *                 output of bem_coupling_blocks over the pivot sets)
+ *   diag          HOST double[n] added to the diagonal (Section 4's 1/2 M for
+ *                 the operator 1/2 M + K of the right-hand side), or NULL
+ * The library copies the tree, the bases, the block lists and diag to the
+ * device; near_vals and far_vals stay the caller's and must outlive the
+ * handle.
+ * bem_h2_matvec: y = G x for DEVICE vectors of n doubles (x != y),
+ * asynchronous on the context's stream; bitwise reproducible (no atomics).
+ * bem_h2_cg: conjugate gradients (Hestenes-Stiefel) from x = 0 until
+ * |r| <= tol |b| or maxit iterations; b, x DEVICE vectors of n doubles; waits
+ * for the stream once per iteration (the residual check); returns the
+ * iterations and |r|/|b|.  Errors: BEM_ERR_INVALID_ARG (bad tree, bases of the
+ * wrong shape, a block out of range or a near block on a non-leaf row
+ * cluster), BEM_ERR_UNSUPPORTED (more than 32 pivots in a cluster),
+ * BEM_ERR_DEGENERATE (a non-finite residual: the matrix is not positive
+ * definite), BEM_ERR_CUDA. */
+typedef struct bem_h2 bem_h2;
+int bem_h2_create(bem_ctx *ctx, int64_t n, int32_t n_clusters, const int32_t *cl_ptr,
+                  const int32_t *cl_idx, const int32_t *cl_son, const int32_t *piv_ptr,
+                  const int32_t *piv_idx, const int64_t *v_off, const double *V, int64_t n_near,
+                  const int32_t *near_row, const int32_t *near_col, const int64_t *near_off,
+                  const double *near_vals, int64_t n_far, const int32_t *far_row,
+                  const int32_t *far_col, const int64_t *far_off, const double *far_vals,
+                  const double *diag, bem_h2 **out);
+int bem_h2_matvec(bem_ctx *ctx, bem_h2 *h2, const double *x, double *y);
+int bem_h2_cg(bem_ctx *ctx, bem_h2 *h2, const double *b, double *x, double tol, int32_t maxit,
+              int32_t *iters, double *rel_res);
+int bem_h2_destroy(bem_ctx *ctx, bem_h2 *h2);
+
+/* ---- arithmetic-pipe probes -------------------------------------------------
+ * Not part of the paper's method: measurement kernels that give the
+ * quadrature kernels' rooflines a measured denominator on the GPU at hand.
+ * Launches one probe on the context's stream (asynchronously) and stores in
+ * *ops the number of operations that launch performs; the caller times the
+ * launch with CUDA events on that stream.  kind: 0 = FP32 FMA (2 operations
+ * each), 1 = FP64 FMA (2 each), 2 = reciprocal square root of the special
+ * function unit (rsqrt.approx.ftz.f32, 1 each), 3 = its sine and cosine
+ * (2 per argument).  Every thread of 8 CTAs of 256 threads per SM runs 8
+ * independent chains of 16 operations per trip, `trips` times.  Errors:
+ * BEM_ERR_INVALID_ARG for a kind outside [0, 3] or trips outside [1, 2^30]. */
+int bem_peak_probe(bem_ctx *ctx, int32_t kind, int64_t trips, double *ops);
 
 /* ---- launch profiling (tracing) ------------------------------------------
  * When enabled, every kernel launch of the context is bracketed by CUDA

@@ -32,7 +32,9 @@ EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_
            "bem_mlp_set_params", "bem_mlp_get_params", "bem_mlp_gradients", "bem_mlp_train_step",
            "bem_mlp_infer", "bem_pair_features", "bem_set_order_model", "bem_learned_counts",
            "bem_shard_blocks", "bem_gca_pivots", "bem_touching_pairs", "bem_green_matrices",
-           "bem_gca_pivots_device"]
+           "bem_gca_pivots_device", "bem_plan_guard_stats", "bem_peak_probe", "bem_gca_bases", "bem_h2_create", "bem_h2_matvec",
+           "bem_h2_cg", "bem_h2_destroy", "bem_plan_learned_counts", "bem_mlp_fit_norm",
+           "bem_mlp_train_epoch", "bem_order_labels"]
 ORDER_CLASSES = [("duffy", 2), ("tri7", 1), ("duffy", 4), ("duffy", 5), ("duffy", 6), ("duffy", 8)]
 ORDER_CLASS_POINTS = [16, 49, 256, 625, 1296, 4096]
 PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE = 1, 2, 4
@@ -140,6 +142,14 @@ def load():
                                    ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
                                    ctypes.c_int64]
     lib.bem_gca_pivots_device.argtypes = [_vp, ctypes.c_int32] + lib.bem_gca_pivots.argtypes
+    lib.bem_gca_bases.argtypes = lib.bem_gca_pivots.argtypes + [_vp, _vp, ctypes.c_int64]
+    lib.bem_h2_create.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp,
+                                  _vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, ctypes.c_int64,
+                                  _vp, _vp, _vp, _vp, _vp, P(_vp)]
+    lib.bem_h2_matvec.argtypes = [_vp, _vp, _vp, _vp]
+    lib.bem_h2_cg.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int32,
+                              P(ctypes.c_int32), P(ctypes.c_double)]
+    lib.bem_h2_destroy.argtypes = [_vp, _vp]
     lib.bem_learned_counts.argtypes = [_vp, P(ctypes.c_int64)]
     lib.bem_plan_create.argtypes = [_vp, P(bem_block_job), ctypes.c_int32, P(bem_block_job),
                                     ctypes.c_int32, ctypes.c_int32, P(_vp)]
@@ -147,6 +157,14 @@ def load():
     lib.bem_plan_destroy.argtypes = [_vp, _vp]
     lib.bem_plan_info.argtypes = [_vp, _vp, P(ctypes.c_int32), P(ctypes.c_int32),
                                   P(ctypes.c_int32), P(ctypes.c_int32), ctypes.c_int32]
+    lib.bem_plan_guard_stats.argtypes = [_vp, _vp, P(ctypes.c_int64), P(ctypes.c_int64)]
+    lib.bem_peak_probe.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64, P(ctypes.c_double)]
+    lib.bem_plan_learned_counts.argtypes = [_vp, _vp, P(ctypes.c_int64)]
+    lib.bem_mlp_fit_norm.argtypes = [_vp, _vp, _vp, ctypes.c_int64]
+    lib.bem_mlp_train_epoch.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int32,
+                                        ctypes.c_float, P(ctypes.c_float)]
+    lib.bem_order_labels.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc), _vp, _vp,
+                                     ctypes.c_int64, ctypes.c_float, ctypes.c_int32, _vp, _vp]
     lib.bem_rule_points.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
                                     ctypes.c_int64]
     lib.bem_profile_enable.argtypes = [_vp, ctypes.c_int32]
@@ -234,6 +252,45 @@ def bem_gca_pivots(verts, tris, basis: str, cl_ptr, cl_idx, cl_son, kappa: float
     if rc != BEM_OK:
         raise BemError(rc, "bad GCA arguments")
     return piv_ptr, piv_idx[: piv_ptr[-1]].copy()
+
+
+def bem_gca_bases(verts, tris, basis: str, cl_ptr, cl_idx, cl_son, kappa: float = 0.0,
+                  gauss_per_face: int = 4, eps: float = 1e-6, max_rank: int = 16,
+                  n_threads: int = 0):
+    """GCA pivots and interpolation matrices (host only): (piv_ptr, piv_idx,
+    mats) with mats[c] the rows x K_c matrix of cluster c (float64, complex128
+    for kappa > 0): V_t of a leaf (rows = its indices), the transfer matrix of
+    a cluster with sons (rows = the sons' pivots, first son first)."""
+    v = np.ascontiguousarray(verts, np.float64)
+    t = np.ascontiguousarray(tris, np.int32)
+    ptr = np.ascontiguousarray(cl_ptr, np.int32)
+    idx = np.ascontiguousarray(cl_idx, np.int32)
+    son = np.ascontiguousarray(cl_son, np.int32)
+    nc = len(ptr) - 1
+    if son.shape != (nc, 2):
+        raise BemError(-1, "cl_son must be (n_clusters, 2)")
+    piv_ptr = np.zeros(nc + 1, np.int32)
+    piv_idx = np.zeros(max(1, nc * max_rank), np.int32)
+    cplx = kappa != 0.0
+    v_cap = (int(ptr[-1]) + 2 * max_rank * nc) * max_rank
+    v_off = np.zeros(nc + 1, np.int64)
+    V = np.zeros(max(1, v_cap * (2 if cplx else 1)), np.float64)
+    rc = load().bem_gca_bases(v.ctypes.data_as(_vp), len(v), t.ctypes.data_as(_vp), len(t),
+                              BASES[basis], float(kappa), ptr.ctypes.data_as(_vp),
+                              idx.ctypes.data_as(_vp), son.ctypes.data_as(_vp), nc,
+                              int(gauss_per_face), float(eps), int(max_rank), int(n_threads),
+                              piv_ptr.ctypes.data_as(_vp), piv_idx.ctypes.data_as(_vp),
+                              piv_idx.size, v_off.ctypes.data_as(_vp), V.ctypes.data_as(_vp),
+                              v_cap)
+    if rc != BEM_OK:
+        raise BemError(rc, "bad GCA arguments")
+    vals = V.view(np.complex128) if cplx else V
+    mats = []
+    for c in range(nc):
+        k = int(piv_ptr[c + 1] - piv_ptr[c])
+        blk = vals[v_off[c]:v_off[c + 1]]
+        mats.append(blk.reshape(-1, k).copy() if k > 0 else np.zeros((0, 0), vals.dtype))
+    return piv_ptr, piv_idx[: piv_ptr[-1]].copy(), mats
 
 
 def kernel_desc(kind="laplace_slp", kappa=0.0) -> bem_kernel_desc:
@@ -480,6 +537,77 @@ class Context:
         return {"touch_launches": nt.value, "block_launches": nb.value, "aux_launches": na.value,
                 "grid_mult": [g[k] for k in range(min(64, nb.value))]}
 
+    # ---- H2 matrix-vector product and conjugate gradients -------------------
+    def bem_h2_create(self, n, cl_ptr, cl_idx, cl_son, piv_ptr, piv_idx, mats, near, near_vals,
+                      far, far_vals, diag=None):
+        """H2 matrix from the tree (host), the bases of bem_gca_bases (host:
+        piv_ptr, piv_idx and the list of matrices) and the near / coupling
+        blocks: near, far = (blk_row, blk_col, blk_off) host arrays with their
+        device values (float64 tensors that must outlive the handle); diag:
+        optional host array added to the diagonal."""
+        import torch
+        _check_dev(near_vals, torch.float64, "near_vals")
+        _check_dev(far_vals, torch.float64, "far_vals")
+        ptr = np.ascontiguousarray(cl_ptr, np.int32)
+        idx = np.ascontiguousarray(cl_idx, np.int32)
+        son = np.ascontiguousarray(cl_son, np.int32)
+        pp = np.ascontiguousarray(piv_ptr, np.int32)
+        pi = np.ascontiguousarray(piv_idx, np.int32)
+        sizes = [np.asarray(m).size for m in mats]
+        v_off = np.zeros(len(mats) + 1, np.int64)
+        v_off[1:] = np.cumsum(sizes)
+        V = np.ascontiguousarray(np.concatenate([np.asarray(m, np.float64).ravel() for m in mats])
+                                 if sizes else np.zeros(1), np.float64)
+        nr, nc_, no = (np.ascontiguousarray(a, t) for a, t in zip(near, (np.int32, np.int32, np.int64)))
+        fr, fc, fo = (np.ascontiguousarray(a, t) for a, t in zip(far, (np.int32, np.int32, np.int64)))
+        h = _vp()
+        dg = None if diag is None else np.ascontiguousarray(diag, np.float64)
+        if dg is not None and dg.shape != (int(n),):
+            raise BemError(-1, "diag must have n entries")
+        keep = (ptr, idx, son, pp, pi, v_off, V, nr, nc_, no, fr, fc, fo, dg)
+        self._check(self.lib.bem_h2_create(
+            self.h, int(n), len(ptr) - 1, *[a.ctypes.data_as(_vp) for a in keep[:7]],
+            len(nr), nr.ctypes.data_as(_vp), nc_.ctypes.data_as(_vp), no.ctypes.data_as(_vp),
+            _ptr(near_vals), len(fr), fr.ctypes.data_as(_vp), fc.ctypes.data_as(_vp),
+            fo.ctypes.data_as(_vp), _ptr(far_vals),
+            None if dg is None else dg.ctypes.data_as(_vp), ctypes.byref(h)))
+        return h
+
+    def bem_h2_matvec(self, h2, x, y):
+        import torch
+        _check_dev(x, torch.float64, "x")
+        _check_dev(y, torch.float64, "y")
+        self._check(self.lib.bem_h2_matvec(self.h, h2, _ptr(x), _ptr(y)))
+
+    def bem_h2_cg(self, h2, b, x, tol=1e-8, maxit=1000):
+        import torch
+        _check_dev(b, torch.float64, "b")
+        _check_dev(x, torch.float64, "x")
+        it, res = ctypes.c_int32(0), ctypes.c_double(0.0)
+        self._check(self.lib.bem_h2_cg(self.h, h2, _ptr(b), _ptr(x), float(tol), int(maxit),
+                                       ctypes.byref(it), ctypes.byref(res)))
+        return it.value, res.value
+
+    def bem_h2_destroy(self, h2):
+        self._check(self.lib.bem_h2_destroy(self.h, h2))
+
+    def bem_peak_probe(self, kind: int, trips: int) -> float:
+        """Launches one arithmetic-pipe probe on the context's stream; returns
+        the number of operations the launch performs."""
+        ops = ctypes.c_double(0.0)
+        self._check(self.lib.bem_peak_probe(self.h, int(kind), int(trips), ctypes.byref(ops)))
+        return ops.value
+
+    def bem_plan_learned_counts(self, plan):
+        c = (ctypes.c_int64 * 6)()
+        self._check(self.lib.bem_plan_learned_counts(self.h, plan, c))
+        return [c[k] for k in range(6)]
+
+    def bem_plan_guard_stats(self, plan):
+        n, r = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._check(self.lib.bem_plan_guard_stats(self.h, plan, ctypes.byref(n), ctypes.byref(r)))
+        return {"entries": n.value, "recomputed": r.value}
+
     # ---- pivots (absolute sums) and the order model --------------------------
     def bem_pivot_entries_absolute(self, mesh_id, kernel, quad, rows, cols, out):
         import torch
@@ -530,6 +658,33 @@ class Context:
         self._check(self.lib.bem_mlp_train_step(self.h, mlp, _ptr(X), _ptr(y), y.numel(),
                                                 ctypes.c_float(lr), ctypes.byref(loss)))
         return loss.value
+
+    def bem_mlp_fit_norm(self, mlp, X):
+        import torch
+        _check_dev(X, torch.float32, "X")
+        self._check(self.lib.bem_mlp_fit_norm(self.h, mlp, _ptr(X), X.shape[0]))
+
+    def bem_mlp_train_epoch(self, mlp, X, y, perm, batch, lr):
+        import torch
+        _check_dev(X, torch.float32, "X")
+        _check_dev(y, torch.int32, "y")
+        _check_dev(perm, torch.int64, "perm")
+        loss = ctypes.c_float(0.0)
+        self._check(self.lib.bem_mlp_train_epoch(self.h, mlp, _ptr(X), _ptr(y), X.shape[0],
+                                                 _ptr(perm), int(batch), ctypes.c_float(lr),
+                                                 ctypes.byref(loss)))
+        return loss.value
+
+    def bem_order_labels(self, mesh_id, kernel, a, b, labels, errors=None, tol=1e-7, q_ref=12):
+        import torch
+        _check_dev(a, torch.int32, "a")
+        _check_dev(b, torch.int32, "b")
+        _check_dev(labels, torch.int32, "labels")
+        if errors is not None:
+            _check_dev(errors, torch.float32, "errors")
+        self._check(self.lib.bem_order_labels(self.h, mesh_id, ctypes.byref(kernel), _ptr(a),
+                                              _ptr(b), a.numel(), ctypes.c_float(tol), int(q_ref),
+                                              _ptr(labels), _ptr(errors)))
 
     def bem_mlp_infer(self, mlp, X, logits):
         import torch

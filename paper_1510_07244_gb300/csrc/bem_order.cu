@@ -404,6 +404,10 @@ __global__ void k_mlp_infer(MlpDev P, const float *__restrict__ X, int64_t n, fl
 //   eval:    one warp per record with the class's rule.
 // ---------------------------------------------------------------------------
 constexpr int kClasses = 6;
+// the classes' regular rules: (rule, q)
+static const int kClassRule[kClasses][2] = {{BEM_RULE_DUFFY, 2}, {BEM_RULE_TRI7, 1},
+                                            {BEM_RULE_DUFFY, 4}, {BEM_RULE_DUFFY, 5},
+                                            {BEM_RULE_DUFFY, 6}, {BEM_RULE_DUFFY, 8}};
 
 __device__ __forceinline__ void select_entry(const MeshView &m, const BlockLaunch &L,
                                              const int64_t *prefix, int64_t tile, int *status,
@@ -842,6 +846,10 @@ struct bem_mlp {
     float *norm = nullptr;     // mean[8], inv_std[8]
     int64_t step = 0;
     // training scratch
+    float *xb = nullptr;       // minibatch of normalised features (bem_mlp_train_epoch)
+    int32_t *yb = nullptr;
+    float *loss_acc = nullptr;
+    int64_t bcap = 0;
     int64_t cap = 0;
     float *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *z3 = nullptr, *dz3 = nullptr,
           *dz2 = nullptr, *dz1 = nullptr, *loss = nullptr, *loss_sum = nullptr;
@@ -898,6 +906,91 @@ cudaError_t mlp_forward_backward(bem_mlp *m, const float *X, const int32_t *y, i
     k_back_act<<<nblk((int64_t)n * kHid), 256, 0, st>>>(m->dz2, P + kOffW2, m->z1, n, kHid, kHid, m->dz1);
     k_weight_grad<<<nblk(kHid * kIn + kHid), 256, 0, st>>>(m->dz1, X, n, kHid, kIn, G + kOffW1, G + kOffB1);
     return cudaGetLastError();
+}
+
+// Per-feature mean and standard deviation (population) of X (n x 8) in FP64:
+// one block per feature, fixed strided partial sums and a fixed tree, so the
+// result does not depend on timing.  norm = (mean[8], 1 / std[8]), with std
+// below 1e-6 taken as 1 (a constant feature).
+__global__ void __launch_bounds__(256) k_norm_stats(const float *__restrict__ X, int64_t n,
+                                                    float *norm)
+{
+    __shared__ double s1[256], s2[256];
+    const int f = blockIdx.x;
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += (double)X[i * kIn + f];
+    s1[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s1[threadIdx.x] += s1[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double mean = s1[0] / (double)n;
+    double b = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double d = (double)X[i * kIn + f] - mean;
+        b += d * d;
+    }
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s2[threadIdx.x] += s2[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double sd = sqrt(s2[0] / (double)n);
+        norm[f] = (float)mean;
+        norm[kIn + f] = (float)(sd > 1e-6 ? 1.0 / sd : 1.0);
+    }
+}
+
+// rows perm[0..b) of the raw features, normalised with the model's (mean,
+// 1/std), and their labels
+__global__ void __launch_bounds__(256) k_gather_norm(const float *__restrict__ X,
+                                                     const int32_t *__restrict__ y,
+                                                     const int64_t *__restrict__ perm, int b,
+                                                     const float *__restrict__ norm, float *xb,
+                                                     int32_t *yb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b * kIn) return;
+    const int r = i / kIn, f = i % kIn;
+    const int64_t src = perm[r];
+    xb[i] = (X[src * kIn + f] - norm[f]) * norm[kIn + f];
+    if (f == 0) yb[r] = y[src];
+}
+
+__global__ void k_loss_acc(const float *loss_sum, float *acc, int reset)
+{
+    acc[0] = (reset ? 0.0f : acc[0]) + loss_sum[0];
+}
+
+// Order-class labels from the method's own errors (Section 2.2 rules against a
+// high Duffy order): err_c = |v_c - v_ref| / A_ref for each class c (A_ref the
+// sum of the magnitudes of the reference's terms), label = the cheapest class
+// with err_c <= tol, else the most accurate one.
+__global__ void __launch_bounds__(256) k_class_error(int64_t n, int cls, int cplx,
+                                                     const double *__restrict__ v,
+                                                     const double *__restrict__ ref,
+                                                     const double *__restrict__ A, float *err)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d;
+    if (cplx) d = hypot(v[2 * i] - ref[2 * i], v[2 * i + 1] - ref[2 * i + 1]);
+    else d = fabs(v[i] - ref[i]);
+    err[i * kOut + cls] = (float)(d / fmax(A[i], 1e-300));
+}
+
+__global__ void __launch_bounds__(256) k_class_label(int64_t n, const float *__restrict__ err,
+                                                     float tol, int32_t *label)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int l = kOut - 1;
+    for (int c = kOut - 1; c >= 0; --c)
+        if (err[i * kOut + c] <= tol) l = c;
+    label[i] = l;
 }
 
 MlpDev mlp_dev(const bem_mlp *m)
@@ -977,7 +1070,8 @@ int bem_mlp_destroy(bem_ctx *ctx, bem_mlp *m)
     cudaStreamSynchronize(ctx->stream);
     mlp_free_scratch(m);
     for (void *p : {(void *)m->params, (void *)m->grads, (void *)m->m1, (void *)m->m2, (void *)m->pbf,
-                    (void *)m->norm, (void *)m->loss_sum})
+                    (void *)m->norm, (void *)m->loss_sum, (void *)m->xb, (void *)m->yb,
+                    (void *)m->loss_acc})
         cudaFree(p);
     delete m;
     return BEM_OK;
@@ -1047,6 +1141,61 @@ int bem_mlp_train_step(bem_ctx *ctx, bem_mlp *m, const float *X, const int32_t *
     return BEM_OK;
 }
 
+int bem_mlp_fit_norm(bem_ctx *ctx, bem_mlp *m, const float *X, int64_t n)
+{
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (!m || !X || n < 1) return api_fail(ctx, BEM_ERR_INVALID_ARG, "bem_mlp_fit_norm: bad arguments");
+    k_norm_stats<<<kIn, 256, 0, ctx->stream>>>(X, n, m->norm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "bem_mlp_fit_norm");
+    return BEM_OK;
+}
+
+int bem_mlp_train_epoch(bem_ctx *ctx, bem_mlp *m, const float *X, const int32_t *y, int64_t n,
+                        const int64_t *perm, int32_t batch, float lr, float *mean_loss)
+{
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (!m || !X || !y || !perm || n < 1 || batch < 1)
+        return api_fail(ctx, BEM_ERR_INVALID_ARG, "bem_mlp_train_epoch: bad arguments");
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    if (batch > m->bcap) {
+        cudaStreamSynchronize(st);
+        cudaFree(m->xb);
+        cudaFree(m->yb);
+        m->xb = nullptr;
+        m->yb = nullptr;
+        m->bcap = 0;
+        e = cudaMalloc((void **)&m->xb, sizeof(float) * (size_t)batch * kIn);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&m->yb, sizeof(int32_t) * (size_t)batch);
+        if (e != cudaSuccess) return api_cuda_fail(ctx, e, "cudaMalloc(minibatch)");
+        m->bcap = batch;
+    }
+    if (!m->loss_acc) {
+        e = cudaMalloc((void **)&m->loss_acc, sizeof(float));
+        if (e != cudaSuccess) return api_cuda_fail(ctx, e, "cudaMalloc(loss)");
+    }
+    const float b1 = 0.9f, b2 = 0.999f;
+    for (int64_t s = 0; s < n; s += batch) {
+        const int b = (int)std::min<int64_t>(batch, n - s);
+        k_gather_norm<<<nblk((int64_t)b * kIn), 256, 0, st>>>(X, y, perm + s, b, m->norm, m->xb, m->yb);
+        e = mlp_forward_backward(m, m->xb, m->yb, b, st);
+        if (e != cudaSuccess) return api_cuda_fail(ctx, e, "bem_mlp_train_epoch");
+        m->step += 1;
+        const float c1 = 1.0f - std::pow(b1, (float)m->step), c2 = 1.0f - std::pow(b2, (float)m->step);
+        k_adam<<<nblk(kNParams), 256, 0, st>>>(m->params, m->grads, m->m1, m->m2, kNParams, lr,
+                                               b1, b2, 1e-8f, c1, c2);
+        k_to_bf16<<<nblk(kNParams), 256, 0, st>>>(m->params, kNParams, m->pbf);
+        k_loss_acc<<<1, 1, 0, st>>>(m->loss_sum, m->loss_acc, s == 0 ? 1 : 0);
+    }
+    float tot = 0.0f;
+    e = cudaMemcpyAsync(&tot, m->loss_acc, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "bem_mlp_train_epoch");
+    if (mean_loss) *mean_loss = tot / (float)n;
+    return BEM_OK;
+}
+
 int bem_mlp_infer(bem_ctx *ctx, bem_mlp *m, const float *X, int64_t n, float *logits)
 {
     if (!ctx || !m || (n > 0 && (!X || !logits)) || n < 0) return BEM_ERR_INVALID_ARG;
@@ -1072,6 +1221,69 @@ int bem_learned_counts(bem_ctx *ctx, int64_t *counts)
 {
     if (!ctx || !counts) return BEM_ERR_INVALID_ARG;
     for (int c = 0; c < kClasses; ++c) counts[c] = ctx->learned_counts[c];
+    return BEM_OK;
+}
+
+int bem_order_labels(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel,
+                     const int32_t *a, const int32_t *b, int64_t n, float tol, int32_t q_ref,
+                     int32_t *labels, float *errors)
+{
+    if (!ctx || !kernel) return BEM_ERR_INVALID_ARG;
+    auto it = ctx->meshes.find(mesh_id);
+    if (it == ctx->meshes.end()) return api_fail(ctx, BEM_ERR_INVALID_ARG, "unknown mesh id");
+    const MeshView &mv = it->second->v;
+    if (mv.basis != BEM_P0) return api_fail(ctx, BEM_ERR_UNSUPPORTED, "labels need a P0 mesh");
+    if (kernel->kind < BEM_LAPLACE_SLP || kernel->kind > BEM_HELMHOLTZ_SLP || q_ref < 1 ||
+        q_ref > 20 || !(tol > 0.0f) || n < 0)
+        return api_fail(ctx, BEM_ERR_INVALID_ARG, "bem_order_labels: bad arguments");
+    if (n == 0) return BEM_OK;
+    if (!a || !b || !labels) return api_fail(ctx, BEM_ERR_INVALID_ARG, "null pointer");
+    const int cplx = kernel->kind == BEM_HELMHOLTZ_SLP ? 1 : 0;
+    Rule4D rules[4];
+    for (int c = kVertex; c <= kIdentical; ++c) {
+        int rc = api_get_rule4(ctx, c, 0, 5, rules[c]);
+        if (rc) return rc;
+    }
+    cudaStream_t st = ctx->stream;
+    double *ref = nullptr, *A = nullptr, *v = nullptr;
+    float *err = nullptr;
+    cudaError_t e = cudaMalloc((void **)&ref, sizeof(double) * n * (1 + cplx));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&A, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&v, sizeof(double) * n * (1 + cplx));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&err, sizeof(float) * n * kOut);
+    int rc = BEM_OK;
+    if (e == cudaSuccess) {
+        // the reference: Duffy q_ref, its value and the sum of |terms|
+        rc = api_get_rule4(ctx, kRegular, BEM_RULE_DUFFY, q_ref, rules[kRegular]);
+        if (!rc) e = launch_pivot_entries(mv, a, b, n, ref, rules, kernel->kind, kernel->kappa,
+                                          ctx->status, st, false);
+        if (!rc && e == cudaSuccess)
+            e = launch_pivot_entries(mv, a, b, n, A, rules, kernel->kind, kernel->kappa,
+                                     ctx->status, st, true);
+        for (int c = 0; c < kClasses && !rc && e == cudaSuccess; ++c) {
+            rc = api_get_rule4(ctx, kRegular, kClassRule[c][0], kClassRule[c][1], rules[kRegular]);
+            if (rc) break;
+            e = launch_pivot_entries(mv, a, b, n, v, rules, kernel->kind, kernel->kappa,
+                                     ctx->status, st, false);
+            if (e == cudaSuccess) {
+                k_class_error<<<nblk(n), 256, 0, st>>>(n, c, cplx, v, ref, A, err);
+                e = cudaGetLastError();
+            }
+        }
+        if (!rc && e == cudaSuccess) {
+            k_class_label<<<nblk(n), 256, 0, st>>>(n, err, tol, labels);
+            e = cudaGetLastError();
+        }
+        if (!rc && e == cudaSuccess && errors)
+            e = cudaMemcpyAsync(errors, err, sizeof(float) * n * kOut, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFree(ref);
+    cudaFree(A);
+    cudaFree(v);
+    cudaFree(err);
+    if (rc) return rc;
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "bem_order_labels");
     return BEM_OK;
 }
 
@@ -1114,10 +1326,114 @@ int bem_pair_features(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kern
 // ---------------------------------------------------------------------------
 namespace bem {
 
-// the classes' regular rules: (rule, q)
-static const int kClassRule[kClasses][2] = {{BEM_RULE_DUFFY, 2}, {BEM_RULE_TRI7, 1},
-                                            {BEM_RULE_DUFFY, 4}, {BEM_RULE_DUFFY, 5},
-                                            {BEM_RULE_DUFFY, 6}, {BEM_RULE_DUFFY, 8}};
+
+// Scratch of one learned job for `tiles` tiles: class per tile slot, records
+// grouped by class, counters and class offsets.
+cudaError_t learned_alloc(LearnedScratch &S, int64_t tiles)
+{
+    const int64_t slots = std::max<int64_t>(1, tiles * 256);
+    cudaError_t e = cudaMalloc((void **)&S.cls, slots);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S.rec, slots * sizeof(int4));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S.small, 64 * sizeof(int64_t));
+    if (e == cudaSuccess) S.cap = slots;
+    return e;
+}
+
+void learned_free(LearnedScratch &S)
+{
+    cudaFree(S.cls);
+    cudaFree(S.rec);
+    cudaFree(S.small);
+    S = LearnedScratch{};
+}
+
+// The launches of one learned job (the touching table and the tile prefix
+// sums are already on the stream): select (features, MLP, class per entry),
+// offsets, compaction by class, one evaluation per class.  `rules` holds the
+// classes' FP64 4D rules (for the classes without a product-rule kernel).
+// Errors are CUDA launch errors.
+cudaError_t learned_launches(const MeshView &mv, const BlockLaunch &L, const int64_t *prefix,
+                             const bem_mlp *model, float conf, const LearnedScratch &S,
+                             const Rule4D *rules, int precision, int num_sms, int *status,
+                             cudaStream_t st, bem_ctx *prof_ctx)
+{
+    LearnedArgs A;
+    A.P = mlp_dev(model);
+    A.mean = model->norm;
+    A.inv_std = model->norm + 8;
+    A.conf = conf;
+    A.cls = S.cls;
+    A.counts = reinterpret_cast<int *>(S.small);
+    A.fill = A.counts + 8;
+    A.offs = S.small + 8;
+    A.rec = reinterpret_cast<int4 *>(S.rec);
+    cudaError_t e = cudaMemsetAsync(A.counts, 0, 16 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const int grid = num_sms * 8;
+    {
+        ProfScope ps(prof_ctx, "learned_select");
+        k_learned_select<<<grid, 256, 0, st>>>(mv, L, prefix, A, status);
+        k_learned_offsets<<<1, 32, 0, st>>>(A);
+        k_learned_compact<<<grid, 256, 0, st>>>(mv, L, prefix, A);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    static const char *kEvalName[kClasses] = {"learned_eval_duffy2", "learned_eval_tri7",
+                                              "learned_eval_duffy4", "learned_eval_duffy5",
+                                              "learned_eval_duffy6", "learned_eval_duffy8"};
+    const bool mixed = is_mixed(precision);
+    for (int c = 0; c < kClasses; ++c) {
+        ProfScope ps(prof_ctx, kEvalName[c]);
+        Rule2D r2;
+        if (mixed && make_rule2d(kClassRule[c][0], kClassRule[c][1], r2) &&
+            (r2.np == 4 || r2.np == 7 || r2.np == 16 || r2.np == 25)) {
+            // thread per pair on the 2D product rule
+            e = L.kind == BEM_LAPLACE_SLP
+                    ? launch_learned_tp<BEM_LAPLACE_SLP>(mv, A.rec, A.offs, c, r2, L.kappa, L.out, grid, st)
+                    : L.kind == BEM_LAPLACE_DLP
+                          ? launch_learned_tp<BEM_LAPLACE_DLP>(mv, A.rec, A.offs, c, r2, L.kappa, L.out, grid, st)
+                          : launch_learned_tp<BEM_HELMHOLTZ_SLP>(mv, A.rec, A.offs, c, r2, L.kappa, L.out, grid, st);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        if (mixed && kClassRule[c][0] == BEM_RULE_DUFFY &&
+            (kClassRule[c][1] == 6 || kClassRule[c][1] == 8)) {
+            // thread per pair, trial points in chunks
+            const int q = kClassRule[c][1];
+            e = L.kind == BEM_LAPLACE_SLP
+                    ? launch_learned_big<BEM_LAPLACE_SLP>(mv, A.rec, A.offs, c, q, L.kappa, L.out, grid, st)
+                    : L.kind == BEM_LAPLACE_DLP
+                          ? launch_learned_big<BEM_LAPLACE_DLP>(mv, A.rec, A.offs, c, q, L.kappa, L.out, grid, st)
+                          : launch_learned_big<BEM_HELMHOLTZ_SLP>(mv, A.rec, A.offs, c, q, L.kappa, L.out, grid, st);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        const Rule4D &r = rules[c];
+        switch (L.kind) {
+        case BEM_LAPLACE_SLP:
+            if (mixed) k_learned_eval<BEM_LAPLACE_SLP, true><<<grid, 256, 0, st>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+            else k_learned_eval<BEM_LAPLACE_SLP, false><<<grid, 256, 0, st>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+            break;
+        case BEM_LAPLACE_DLP:
+            if (mixed) k_learned_eval<BEM_LAPLACE_DLP, true><<<grid, 256, 0, st>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+            else k_learned_eval<BEM_LAPLACE_DLP, false><<<grid, 256, 0, st>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+            break;
+        default:
+            if (mixed) k_learned_eval<BEM_HELMHOLTZ_SLP, true><<<grid, 256, 0, st>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+            else k_learned_eval<BEM_HELMHOLTZ_SLP, false><<<grid, 256, 0, st>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int learned_rules(bem_ctx *ctx, Rule4D *rules)
+{
+    for (int c = 0; c < kClasses; ++c) {
+        int rc = api_get_rule4(ctx, kRegular, kClassRule[c][0], kClassRule[c][1], rules[c]);
+        if (rc) return rc;
+    }
+    return BEM_OK;
+}
 
 int run_learned_p0(bem_ctx *ctx, const MeshView &mv, const BlockLaunch &L, const int64_t *prefix,
                    int precision)
@@ -1130,90 +1446,24 @@ int run_learned_p0(bem_ctx *ctx, const MeshView &mv, const BlockLaunch &L, const
                                     cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned: tile count");
-    const int64_t slots = std::max<int64_t>(1, tiles * 256);
-    if (slots > ctx->learned_cap) {
-        cudaFree(ctx->learned_cls);
-        cudaFree(ctx->learned_rec);
-        ctx->learned_cls = nullptr;
-        ctx->learned_rec = nullptr;
-        ctx->learned_cap = 0;
-        e = cudaMalloc((void **)&ctx->learned_cls, slots);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->learned_rec, slots * sizeof(int4));
-        if (e != cudaSuccess) return api_cuda_fail(ctx, e, "cudaMalloc(learned scratch)");
-        ctx->learned_cap = slots;
-    }
-    if (!ctx->learned_small) {
-        e = cudaMalloc((void **)&ctx->learned_small, 64 * sizeof(int64_t));
-        if (e != cudaSuccess) return api_cuda_fail(ctx, e, "cudaMalloc(learned counters)");
-    }
-    LearnedArgs A;
-    A.P = mlp_dev(model);
-    A.mean = model->norm;
-    A.inv_std = model->norm + 8;
-    A.conf = ctx->order_conf;
-    A.cls = ctx->learned_cls;
-    A.counts = reinterpret_cast<int *>(ctx->learned_small);
-    A.fill = A.counts + 8;
-    A.offs = ctx->learned_small + 8;
-    A.rec = reinterpret_cast<int4 *>(ctx->learned_rec);
-    cudaMemsetAsync(A.counts, 0, 16 * sizeof(int), ctx->stream);
-    const int grid = ctx->num_sms * 8;
-    {
-        ProfScope ps(ctx, "learned_select");
-        k_learned_select<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A, ctx->status);
-        k_learned_offsets<<<1, 32, 0, ctx->stream>>>(A);
-        k_learned_compact<<<grid, 256, 0, ctx->stream>>>(mv, L, prefix, A);
-    }
-    static const char *kEvalName[kClasses] = {"learned_eval_duffy2", "learned_eval_tri7",
-                                              "learned_eval_duffy4", "learned_eval_duffy5",
-                                              "learned_eval_duffy6", "learned_eval_duffy8"};
-    const bool mixed = is_mixed(precision);
-    for (int c = 0; c < kClasses; ++c) {
-        ProfScope ps(ctx, kEvalName[c]);
-        Rule2D r2;
-        if (mixed && make_rule2d(kClassRule[c][0], kClassRule[c][1], r2) &&
-            (r2.np == 4 || r2.np == 7 || r2.np == 16 || r2.np == 25)) {
-            // thread per pair on the 2D product rule
-            e = L.kind == BEM_LAPLACE_SLP
-                    ? launch_learned_tp<BEM_LAPLACE_SLP>(mv, A.rec, A.offs, c, r2, L.kappa, L.out, grid, ctx->stream)
-                    : L.kind == BEM_LAPLACE_DLP
-                          ? launch_learned_tp<BEM_LAPLACE_DLP>(mv, A.rec, A.offs, c, r2, L.kappa, L.out, grid, ctx->stream)
-                          : launch_learned_tp<BEM_HELMHOLTZ_SLP>(mv, A.rec, A.offs, c, r2, L.kappa, L.out, grid, ctx->stream);
-            if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned evaluation");
-            continue;
-        }
-        if (mixed && kClassRule[c][0] == BEM_RULE_DUFFY &&
-            (kClassRule[c][1] == 6 || kClassRule[c][1] == 8)) {
-            // thread per pair, trial points in chunks
-            const int q = kClassRule[c][1];
-            e = L.kind == BEM_LAPLACE_SLP
-                    ? launch_learned_big<BEM_LAPLACE_SLP>(mv, A.rec, A.offs, c, q, L.kappa, L.out, grid, ctx->stream)
-                    : L.kind == BEM_LAPLACE_DLP
-                          ? launch_learned_big<BEM_LAPLACE_DLP>(mv, A.rec, A.offs, c, q, L.kappa, L.out, grid, ctx->stream)
-                          : launch_learned_big<BEM_HELMHOLTZ_SLP>(mv, A.rec, A.offs, c, q, L.kappa, L.out, grid, ctx->stream);
-            if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned evaluation");
-            continue;
-        }
-        Rule4D r;
-        int rc = api_get_rule4(ctx, kRegular, kClassRule[c][0], kClassRule[c][1], r);
-        if (rc) return rc;
-        switch (L.kind) {
-        case BEM_LAPLACE_SLP:
-            if (mixed) k_learned_eval<BEM_LAPLACE_SLP, true><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
-            else k_learned_eval<BEM_LAPLACE_SLP, false><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
-            break;
-        case BEM_LAPLACE_DLP:
-            if (mixed) k_learned_eval<BEM_LAPLACE_DLP, true><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
-            else k_learned_eval<BEM_LAPLACE_DLP, false><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
-            break;
-        default:
-            if (mixed) k_learned_eval<BEM_HELMHOLTZ_SLP, true><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
-            else k_learned_eval<BEM_HELMHOLTZ_SLP, false><<<grid, 256, 0, ctx->stream>>>(mv, A.rec, A.offs, c, r.d, r.f, r.n, L.kappa, L.out);
+    if (std::max<int64_t>(1, tiles * 256) > ctx->learned.cap) {
+        learned_free(ctx->learned);
+        e = learned_alloc(ctx->learned, tiles);
+        if (e != cudaSuccess) {
+            learned_free(ctx->learned);
+            return api_cuda_fail(ctx, e, "cudaMalloc(learned scratch)");
         }
     }
+    Rule4D rules[kClasses];
+    int rc = learned_rules(ctx, rules);
+    if (rc) return rc;
+    e = learned_launches(mv, L, prefix, model, ctx->order_conf, ctx->learned, rules, precision,
+                         ctx->num_sms, ctx->status, ctx->stream, ctx);
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned evaluation");
     // class counts of this call (for reports): read after the launches
     int counts[8] = {0};
-    e = cudaMemcpyAsync(counts, A.counts, 8 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    e = cudaMemcpyAsync(counts, ctx->learned.small, 8 * sizeof(int), cudaMemcpyDeviceToHost,
+                        ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned path");
     for (int c = 0; c < kClasses; ++c) ctx->learned_counts[c] = counts[c];

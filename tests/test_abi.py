@@ -20,7 +20,7 @@ def lib():
 def declared():
     src = open(os.path.join(ROOT, "include", "bem.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(bem_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(bem_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():

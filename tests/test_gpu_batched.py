@@ -182,15 +182,16 @@ def test_shards_reproduce_unsharded_run(env):
     ctx.bem_mesh_free(mid)
 
 
-def test_plan_rejects_learned_orders(env, small_batch):
-    """Plans run fixed orders: a learned-order job is refused, not silently
-    evaluated at the fixed orders."""
+def test_plan_rejects_learned_orders_without_model(env, small_batch):
+    """A learned-order job needs an order model: without one the plan is
+    refused, not silently evaluated at the fixed orders."""
     pkg, ctx = env
+    ctx.bem_set_order_model(None, 0.0)
     mids, near, far, outs = _jobs(pkg, ctx, small_batch, "mixed_full")
     near[0].quad = pkg.quad_desc(**QUAD, precision="mixed_full", order_mode="learned")
     with pytest.raises(pkg.BemError) as ei:
         ctx.bem_plan_create(near, far, 0)
-    assert ei.value.code == -6
+    assert ei.value.code == -1
     for m in mids:
         ctx.bem_mesh_free(m)
 

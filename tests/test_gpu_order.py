@@ -172,3 +172,96 @@ def test_learned_near_field_meets_target_with_gain(env, trained, kernel, kappa, 
           f"max error {err:.2e} (target 1e-6)")
     ctx.bem_set_order_model(None, 0.0)
     ctx.bem_mesh_free(mid)
+
+
+def test_learned_jobs_in_a_plan_equal_per_call_results(env, trained):
+    """Learned-order jobs inside a plan (one CUDA graph with fixed-order jobs
+    beside them) give the per-call learned results bit for bit, with the same
+    class counts."""
+    import torch
+    from parity_util import block_job
+    pkg, ctx, om = env
+    mlp, _ = trained
+    ctx.bem_set_order_model(mlp, 0.99)
+    mesh = synth.jitter(synth.octasphere(24), 0.05, 151007244 + 5098)
+    _, near, far = synth.workloads.h2_blocks(mesh, "p0", 32, 2.0, 16, 8)
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p0")
+    ql = dict(q_regular=3, regular_rule="duffy", q_identical=5, q_edge=5, q_vertex=5,
+              order_mode="learned", precision="mixed_full")
+    qf = dict(ql, order_mode="fixed")
+    res = {}
+    for how in ("calls", "plan"):
+        outs = {}
+        jobs = {"near": [], "far": []}
+        for kernel, kappa in KERNELS:
+            dt = torch.complex128 if kernel == "helmholtz_slp" else torch.float64
+            for nm, bs in (("near", near), ("far", far)):
+                o = torch.full((bs.n_entries,), float("nan"), dtype=dt, device="cuda")
+                outs[(kernel, nm)] = o
+                jobs[nm].append(block_job(pkg, mid, bs, kernel, kappa, ql, o))
+        # a fixed-order job beside the learned ones
+        fixed = torch.full((near.n_entries,), float("nan"), dtype=torch.float64, device="cuda")
+        outs["fixed"] = fixed
+        counts = np.zeros(6, np.int64)
+        if how == "calls":
+            for nm in ("near", "far"):
+                for j in jobs[nm]:
+                    (ctx.bem_near_field if nm == "near" else ctx.bem_coupling_blocks)([j])
+                    counts += ctx.bem_learned_counts()
+            ctx.bem_near_field([block_job(pkg, mid, near, "laplace_slp", 0.0, qf, fixed)])
+        else:
+            plan = ctx.bem_plan_create(jobs["near"] + [block_job(pkg, mid, near, "laplace_slp",
+                                                                 0.0, qf, fixed)],
+                                       jobs["far"], pkg.PLAN_GRAPH)
+            ctx.bem_plan_run(plan)
+            counts += np.array(ctx.bem_plan_learned_counts(plan))
+            ctx.bem_plan_destroy(plan)
+        ctx.bem_sync()
+        res[how] = ({k: v.cpu() for k, v in outs.items()}, counts)
+    for k in res["calls"][0]:
+        assert torch.isfinite(res["plan"][0][k]).all()
+        assert torch.equal(res["calls"][0][k], res["plan"][0][k]), k
+    assert np.array_equal(res["calls"][1], res["plan"][1]) and res["plan"][1].sum() > 0
+    ctx.bem_set_order_model(None, 0.0)
+    ctx.bem_mesh_free(mid)
+
+
+def test_labels_and_normalisation_in_the_library(env):
+    """bem_order_labels against the oracle's own class errors (the same rules,
+    the same reference order and scale), and bem_mlp_fit_norm against the
+    features' mean and standard deviation."""
+    import torch
+    import oracle
+    pkg, ctx, om = env
+    mesh = synth.jitter(synth.octasphere(12), 0.05, 151007244 + 5097)
+    _, near, far = synth.workloads.h2_blocks(mesh, "p0", 32, 2.0, 16, 7)
+    rng = synth.SplitMix64(11)
+    a, b = _regular_pairs(mesh, (near, far), 400, rng)
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p0")
+    ad, bd = to_dev(a, torch.int32), to_dev(b, torch.int32)
+    classes = [("duffy", 2), ("tri7", 3), ("duffy", 4), ("duffy", 5), ("duffy", 6), ("duffy", 8)]
+    for kernel, kappa in KERNELS:
+        lab, err = om.labels(ctx, mid, pkg.kernel_desc(kernel, kappa), ad, bd, tol=1e-7)
+        got_err = err.cpu().numpy()
+        q12 = dict(q_regular=12, regular_rule="duffy", q_identical=5, q_edge=5, q_vertex=5)
+        ref = oracle.entries(mesh.verts, mesh.tris, a, b, kernel=kernel, kappa=kappa, **q12)
+        A = oracle.entries_absolute(mesh.verts, mesh.tris, a, b, kernel=kernel, kappa=kappa, **q12)
+        E = np.stack([np.abs(oracle.entries(mesh.verts, mesh.tris, a, b, kernel=kernel,
+                                            kappa=kappa, **dict(q12, regular_rule=r, q_regular=q))
+                             - ref) / A for r, q in classes], axis=1)
+        assert np.allclose(got_err, E, rtol=1e-4, atol=1e-12)
+        ok = E <= 1e-7
+        exp = np.where(ok.any(axis=1), np.argmax(ok, axis=1), 5)
+        clear = np.all(np.abs(E / 1e-7 - 1.0) > 1e-3, axis=1)   # no error at the threshold
+        assert np.array_equal(lab.cpu().numpy()[clear], exp[clear])
+        X = om.raw_features(ctx, mid, pkg.kernel_desc(kernel, kappa), ad, bd)
+        mlp = ctx.bem_mlp_create(1)
+        ctx.bem_mlp_fit_norm(mlp, X)
+        _, norm = ctx.bem_mlp_get_params(mlp)
+        Xh = X.cpu().numpy().astype(np.float64)
+        sd = Xh.std(axis=0)
+        assert np.allclose(norm[:8], Xh.mean(axis=0), rtol=1e-5, atol=1e-6)
+        assert np.allclose(norm[8:], np.where(sd > 1e-6, 1.0 / np.where(sd > 0, sd, 1), 1.0),
+                           rtol=1e-5)
+        ctx.bem_mlp_destroy(mlp)
+    ctx.bem_mesh_free(mid)
