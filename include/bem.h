@@ -53,7 +53,8 @@ extern "C" {
 #define BEM_ERR_UNSUPPORTED (-6)  /* option combination not implemented          */
 
 /* ---- enumerations -------------------------------------------------------- */
-enum { BEM_LAPLACE_SLP = 0, BEM_LAPLACE_DLP = 1, BEM_HELMHOLTZ_SLP = 2 };
+enum { BEM_LAPLACE_SLP = 0, BEM_LAPLACE_DLP = 1, BEM_HELMHOLTZ_SLP = 2, BEM_HELMHOLTZ_DLP = 3,
+       BEM_HELMHOLTZ_BW = 4 };
 enum { BEM_P0 = 0, BEM_P1 = 1 };
 enum { BEM_RULE_DUFFY = 0, BEM_RULE_TRI7 = 1 };
 enum { BEM_FP64 = 0, BEM_MIXED = 1, BEM_MIXED_FULL = 2 };
@@ -61,10 +62,25 @@ enum { BEM_ORDER_FIXED = 0, BEM_ORDER_LEARNED = 1 };
 
 typedef struct bem_ctx bem_ctx;
 
-/* Kernel function (Eq. 2).  kappa: wave number, used by BEM_HELMHOLTZ_SLP. */
+/* Kernel function (Eq. 2 and Section 4), k(x, y) with r = |x - y|:
+ *   BEM_LAPLACE_SLP    1 / (4 pi r)
+ *   BEM_LAPLACE_DLP    (x - y).n_y / (4 pi r^3)
+ *   BEM_HELMHOLTZ_SLP  exp(i kappa r) / (4 pi r)
+ *   BEM_HELMHOLTZ_DLP  d/dn_y exp(i kappa r)/(4 pi r)
+ *                      = (x - y).n_y (1 - i kappa r) exp(i kappa r) / (4 pi r^3)
+ *   BEM_HELMHOLTZ_BW   the Brakhage-Werner combination of Section 4, the
+ *                      double layer minus i eta times the single layer.
+ * kappa: wave number (Helmholtz kinds); eta: coupling parameter of
+ * BEM_HELMHOLTZ_BW (ignored by the others).  The Helmholtz kinds give complex
+ * entries ((re, im) double pairs, 16-byte aligned outputs).
+ * BEM_HELMHOLTZ_DLP and BEM_HELMHOLTZ_BW run in FP64 in every precision (the
+ * float forms cover the first three kinds), take fixed orders only, and are not
+ * kernels of the Green matrices (bem_green_matrices) or of the allocation-free
+ * call. */
 typedef struct {
     int32_t kind;
     double kappa;
+    double eta;
 } bem_kernel_desc;
 
 /* Quadrature orders (Section 2.2 and the "higher quadrature orders" study of
@@ -622,6 +638,32 @@ int bem_h2_matvec(bem_ctx *ctx, bem_h2 *h2, const double *x, double *y);
 int bem_h2_cg(bem_ctx *ctx, bem_h2 *h2, const double *b, double *x, double tol, int32_t maxit,
               int32_t *iters, double *rel_res);
 int bem_h2_destroy(bem_ctx *ctx, bem_h2 *h2);
+
+/* ---- potentials and the exterior Helmholtz problem -----------------------
+ * Section 4's exterior Dirichlet problem in the Brakhage-Werner form: the
+ * density w on the surface solves (1/2 M + K - i eta V) w = F, F_i = int phi_i f,
+ * and the field outside is u(z) = sum_j w_j int_{T_j} (dg/dn_y - i eta g)(z, y) dy.
+ * bem_potentials: u(z_k) = sum_j w_j int_{T_j} k(z_k, y) dy for n_points points
+ *   z (DEVICE double[n_points][3], off the surface: the integrands must be
+ *   smooth) and a piecewise-constant complex density (DEVICE (re, im) double
+ *   pairs, one per triangle), with the kernel of `kernel` (any kind) and a
+ *   Duffy q x q rule per triangle (q in [1, 5]), FP64; out: DEVICE complex
+ *   [n_points].  Asynchronous.  Errors: BEM_ERR_INVALID_ARG (unknown mesh, bad
+ *   kernel, order or pointers, complex arrays not 16-byte aligned),
+ *   BEM_ERR_UNSUPPORTED (a piecewise-linear mesh).
+ * bem_dense_gmres: restarted GMRES for (A + diag(d)) x = b with A a DEVICE
+ *   column-major complex n x n matrix (e.g. from bem_assemble_dense), d a
+ *   DEVICE complex vector or NULL, b and x DEVICE complex vectors (x is
+ *   overwritten, starting from 0); classical Gram-Schmidt applied twice,
+ *   `restart` Krylov vectors per cycle (<= 500), at most maxit iterations,
+ *   until |b - (A + D) x| <= tol |b|.  Allocates (restart + 1) n complex
+ *   values of scratch per call and waits for the stream at every Arnoldi
+ *   step.  Returns the iterations and the relative residual. */
+int bem_potentials(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kernel, int32_t q,
+                   const double *points, int64_t n_points, const double *density, double *out);
+int bem_dense_gmres(bem_ctx *ctx, int64_t n, const double *A, const double *diag,
+                    const double *b, double *x, double tol, int32_t restart, int32_t maxit,
+                    int32_t *iters, double *rel_res);
 
 /* ---- arithmetic-pipe probes -------------------------------------------------
  * Not part of the paper's method: measurement kernels that give the

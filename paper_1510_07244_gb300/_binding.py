@@ -18,7 +18,10 @@ LIB_PATH = os.path.join(_PKG, "_build", "libbem_gb300.so")
 BEM_OK = 0
 ERRORS = {-1: "BEM_ERR_INVALID_ARG", -2: "BEM_ERR_CUDA", -3: "BEM_ERR_OOM",
           -4: "BEM_ERR_TIMEOUT", -5: "BEM_ERR_DEGENERATE", -6: "BEM_ERR_UNSUPPORTED"}
-KERNELS = {"laplace_slp": 0, "laplace_dlp": 1, "helmholtz_slp": 2}
+KERNELS = {"laplace_slp": 0, "laplace_dlp": 1, "helmholtz_slp": 2, "helmholtz_dlp": 3,
+           "helmholtz_bw": 4}
+COMPLEX_KERNELS = ("helmholtz_slp", "helmholtz_dlp", "helmholtz_bw")
+_COMPLEX_IDS = tuple(KERNELS[k] for k in COMPLEX_KERNELS)
 BASES = {"p0": 0, "p1": 1}
 RULES = {"duffy": 0, "tri7": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_full": 2}
@@ -34,7 +37,7 @@ EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_
            "bem_shard_blocks", "bem_gca_pivots", "bem_touching_pairs", "bem_green_matrices",
            "bem_gca_pivots_device", "bem_plan_guard_stats", "bem_peak_probe", "bem_gca_bases", "bem_h2_create", "bem_h2_matvec",
            "bem_h2_cg", "bem_h2_destroy", "bem_plan_learned_counts", "bem_mlp_fit_norm",
-           "bem_mlp_train_epoch", "bem_order_labels"]
+           "bem_mlp_train_epoch", "bem_order_labels", "bem_potentials", "bem_dense_gmres"]
 ORDER_CLASSES = [("duffy", 2), ("tri7", 1), ("duffy", 4), ("duffy", 5), ("duffy", 6), ("duffy", 8)]
 ORDER_CLASS_POINTS = [16, 49, 256, 625, 1296, 4096]
 PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE = 1, 2, 4
@@ -47,7 +50,7 @@ class BemError(RuntimeError):
 
 
 class bem_kernel_desc(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("kappa", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int32), ("kappa", ctypes.c_double), ("eta", ctypes.c_double)]
 
 
 class bem_quad_desc(ctypes.Structure):
@@ -160,6 +163,11 @@ def load():
     lib.bem_plan_guard_stats.argtypes = [_vp, _vp, P(ctypes.c_int64), P(ctypes.c_int64)]
     lib.bem_peak_probe.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64, P(ctypes.c_double)]
     lib.bem_plan_learned_counts.argtypes = [_vp, _vp, P(ctypes.c_int64)]
+    lib.bem_potentials.argtypes = [_vp, ctypes.c_int32, P(bem_kernel_desc), ctypes.c_int32, _vp,
+                                   ctypes.c_int64, _vp, _vp]
+    lib.bem_dense_gmres.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, ctypes.c_double,
+                                    ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32),
+                                    P(ctypes.c_double)]
     lib.bem_mlp_fit_norm.argtypes = [_vp, _vp, _vp, ctypes.c_int64]
     lib.bem_mlp_train_epoch.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int32,
                                         ctypes.c_float, P(ctypes.c_float)]
@@ -293,8 +301,8 @@ def bem_gca_bases(verts, tris, basis: str, cl_ptr, cl_idx, cl_son, kappa: float 
     return piv_ptr, piv_idx[: piv_ptr[-1]].copy(), mats
 
 
-def kernel_desc(kind="laplace_slp", kappa=0.0) -> bem_kernel_desc:
-    return bem_kernel_desc(KERNELS[kind], float(kappa))
+def kernel_desc(kind="laplace_slp", kappa=0.0, eta=0.0) -> bem_kernel_desc:
+    return bem_kernel_desc(KERNELS[kind], float(kappa), float(eta))
 
 
 def quad_desc(q_regular=3, regular_rule="duffy", q_identical=5, q_edge=5, q_vertex=5,
@@ -333,7 +341,7 @@ class BlockJob:
         for n in ("row_ptr", "row_idx", "col_ptr", "col_idx", "blk_row", "blk_col"):
             _check_dev(getattr(self, n), torch.int32, n)
         _check_dev(self.blk_off, torch.int64, "blk_off")
-        cplx = self.kernel.kind == KERNELS["helmholtz_slp"]
+        cplx = self.kernel.kind in _COMPLEX_IDS
         _check_dev(self.out, torch.complex128 if cplx else torch.float64, "out")
         return bem_block_job(self.mesh_id, self.kernel, self.quad,
                              _ptr(self.row_ptr), _ptr(self.row_idx), self.row_ptr.numel() - 1,
@@ -372,7 +380,7 @@ class GreenJob:
             if getattr(self, n) is not None:
                 _check_dev(getattr(self, n), torch.float64, n)
         _check_dev(self.out_off, torch.int64, "out_off")
-        cplx = self.kernel.kind == KERNELS["helmholtz_slp"]
+        cplx = self.kernel.kind in _COMPLEX_IDS
         _check_dev(self.out, torch.complex128 if cplx else torch.float64, "out")
         n_clusters = self.row_ptr.numel() - 1
         n_points = self.z.numel() // 3
@@ -476,7 +484,7 @@ class Context:
         import torch
         _check_dev(rows, torch.int32, "rows")
         _check_dev(cols, torch.int32, "cols")
-        cplx = kernel.kind == KERNELS["helmholtz_slp"]
+        cplx = kernel.kind in _COMPLEX_IDS
         _check_dev(out, torch.complex128 if cplx else torch.float64, "out")
         if rows.numel() != cols.numel() or out.numel() < rows.numel():
             raise ValueError("rows/cols/out size mismatch")
@@ -486,7 +494,7 @@ class Context:
 
     def bem_assemble_dense(self, mesh_id, kernel, quad, lower_only, out):
         import torch
-        cplx = kernel.kind == KERNELS["helmholtz_slp"]
+        cplx = kernel.kind in _COMPLEX_IDS
         _check_dev(out, torch.complex128 if cplx else torch.float64, "out")
         info = self.bem_mesh_info(mesh_id)
         n = info["n_triangles"] if info["basis"] == 0 else info["n_vertices"]
@@ -597,6 +605,32 @@ class Context:
         ops = ctypes.c_double(0.0)
         self._check(self.lib.bem_peak_probe(self.h, int(kind), int(trips), ctypes.byref(ops)))
         return ops.value
+
+    def bem_potentials(self, mesh_id, kernel, points, density, out, q=4):
+        """Potentials of a piecewise-constant complex density at points off the
+        surface (device tensors: points (m, 3) float64, density (nt,) and out (m,)
+        complex128)."""
+        import torch
+        _check_dev(points, torch.float64, "points")
+        _check_dev(density, torch.complex128, "density")
+        _check_dev(out, torch.complex128, "out")
+        self._check(self.lib.bem_potentials(self.h, mesh_id, ctypes.byref(kernel), int(q),
+                                            _ptr(points), points.shape[0], _ptr(density),
+                                            _ptr(out)))
+
+    def bem_dense_gmres(self, A, b, x, diag=None, tol=1e-8, restart=100, maxit=1000):
+        """GMRES for (A + diag(diag)) x = b; A column-major complex (n*n,) device
+        tensor, b, x, diag complex (n,).  Returns (iterations, relative residual)."""
+        import torch
+        for t, nm in ((A, "A"), (b, "b"), (x, "x")):
+            _check_dev(t, torch.complex128, nm)
+        if diag is not None:
+            _check_dev(diag, torch.complex128, "diag")
+        it, res = ctypes.c_int32(0), ctypes.c_double(0.0)
+        self._check(self.lib.bem_dense_gmres(self.h, b.numel(), _ptr(A), _ptr(diag), _ptr(b),
+                                             _ptr(x), float(tol), int(restart), int(maxit),
+                                             ctypes.byref(it), ctypes.byref(res)))
+        return it.value, res.value
 
     def bem_plan_learned_counts(self, plan):
         c = (ctypes.c_int64 * 6)()

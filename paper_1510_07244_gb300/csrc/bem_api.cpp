@@ -116,9 +116,10 @@ int check_quad(bem_ctx *ctx, const bem_quad_desc *q, Rule2D &r2, bool block_rule
 int check_kernel(bem_ctx *ctx, const bem_kernel_desc *k)
 {
     if (!k) return fail(ctx, BEM_ERR_INVALID_ARG, "null kernel descriptor");
-    if (k->kind < BEM_LAPLACE_SLP || k->kind > BEM_HELMHOLTZ_SLP)
+    if (k->kind < BEM_LAPLACE_SLP || k->kind > BEM_HELMHOLTZ_BW)
         return fail(ctx, BEM_ERR_INVALID_ARG, "unknown kernel kind");
     if (!std::isfinite(k->kappa)) return fail(ctx, BEM_ERR_INVALID_ARG, "kappa is not finite");
+    if (!std::isfinite(k->eta)) return fail(ctx, BEM_ERR_INVALID_ARG, "eta is not finite");
     return BEM_OK;
 }
 
@@ -168,7 +169,8 @@ int run_touching(bem_ctx *ctx, Mesh *m, const bem_kernel_desc *k, const bem_quad
                                        "touching_identical"};
         ProfScope ps(ctx, names[cas]);
         cudaError_t e = launch_touching(m->v, cas, m->list[cas], m->nlist[cas], r, k->kind,
-                                        k->kappa, touch_in_float(q->precision, cas), ctx->stream);
+                                        k->kappa, touch_in_float(q->precision, cas, k->kind),
+                                        ctx->stream, k->eta);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "touching kernel");
     }
     return BEM_OK;
@@ -246,7 +248,7 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
         if (!J.row_ptr || !J.row_idx || !J.col_ptr || !J.col_idx || !J.blk_row || !J.blk_col ||
             !J.blk_off || !J.out || J.n_row_clusters < 1 || J.n_col_clusters < 1)
             return fail(ctx, BEM_ERR_INVALID_ARG, "null pointer or empty cluster list");
-        if (J.kernel.kind == BEM_HELMHOLTZ_SLP && (reinterpret_cast<uintptr_t>(J.out) & 15))
+        if (kind_complex(J.kernel.kind) && (reinterpret_cast<uintptr_t>(J.out) & 15))
             return fail(ctx, BEM_ERR_INVALID_ARG, "complex output must be 16-byte aligned");
         if (m->v.basis == BEM_P1 && m->v.maxdeg > kMaxDegP1)
             return fail(ctx, BEM_ERR_UNSUPPORTED, "vertex degree above 16 (piecewise linear)");
@@ -272,7 +274,8 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
         L.kappa = J.kernel.kappa;
         L.lower_only = lower_only;
         L.allow_touching = allow_touching ? 1 : 0;
-        L.mixed = is_mixed(J.quad.precision) ? 1 : 0;
+        L.mixed = is_mixed(J.quad.precision) && !kind_fp64_only(L.kind) ? 1 : 0;
+        L.eta = J.kernel.eta;
         const bool coupling = J.quad.order_mode == BEM_ORDER_FIXED &&
                               use_coupling_engine(m->v.basis, L.kind, L.mixed, L.allow_touching);
         const int tr = coupling ? kCouplingRows : kTile;
@@ -284,6 +287,9 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "tile prefix kernel");
         if (J.quad.order_mode == BEM_ORDER_LEARNED) {
+            if (kind_fp64_only(J.kernel.kind))
+                return fail(ctx, BEM_ERR_UNSUPPORTED,
+                            "learned orders cover the Laplace kernels and the Helmholtz single layer");
             if (m->v.basis != BEM_P0)
                 return fail(ctx, BEM_ERR_UNSUPPORTED, "learned orders need the piecewise-constant basis");
             if (lower_only)
@@ -343,7 +349,7 @@ int api_check_job(bem_ctx *ctx, const bem_block_job &J, Rule2D &r2, Mesh **mesh)
         (!J.row_ptr || !J.row_idx || !J.col_ptr || !J.col_idx || !J.blk_row || !J.blk_col ||
          !J.blk_off || !J.out || J.n_row_clusters < 1 || J.n_col_clusters < 1))
         return fail(ctx, BEM_ERR_INVALID_ARG, "null pointer or empty cluster list");
-    if (J.kernel.kind == BEM_HELMHOLTZ_SLP && (reinterpret_cast<uintptr_t>(J.out) & 15))
+    if (kind_complex(J.kernel.kind) && (reinterpret_cast<uintptr_t>(J.out) & 15))
         return fail(ctx, BEM_ERR_INVALID_ARG, "complex output must be 16-byte aligned");
     if (m->v.basis == BEM_P1 && m->v.maxdeg > kMaxDegP1)
         return fail(ctx, BEM_ERR_UNSUPPORTED, "vertex degree above 16 (piecewise linear)");
@@ -630,7 +636,7 @@ static int pivot_impl(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kern
     if (n < 0) return fail(ctx, BEM_ERR_INVALID_ARG, "negative entry count");
     if (n == 0) return BEM_OK;
     if (!rows || !cols || !out) return fail(ctx, BEM_ERR_INVALID_ARG, "null pointer");
-    if (!absolute && kernel->kind == BEM_HELMHOLTZ_SLP && (reinterpret_cast<uintptr_t>(out) & 15))
+    if (!absolute && kind_complex(kernel->kind) && (reinterpret_cast<uintptr_t>(out) & 15))
         return fail(ctx, BEM_ERR_INVALID_ARG, "complex output must be 16-byte aligned");
     Rule4D rules[4];
     if ((rc = get_rule4(ctx, kRegular, quad->regular_rule, quad->q_regular, rules[kRegular])) ||
@@ -642,7 +648,7 @@ static int pivot_impl(bem_ctx *ctx, int32_t mesh_id, const bem_kernel_desc *kern
     {
         ProfScope ps(ctx, "pivot");
         e = launch_pivot_entries(m->v, rows, cols, n, out, rules, kernel->kind, kernel->kappa,
-                                 ctx->status, ctx->stream, absolute);
+                                 ctx->status, ctx->stream, absolute, kernel->eta);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pivot kernel");
     return BEM_OK;

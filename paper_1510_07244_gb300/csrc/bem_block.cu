@@ -244,7 +244,8 @@ size_t p1_smem_bytes(bool cplx, bool mixed, bool fused)
 template <int KIND, bool ABS>
 __global__ void __launch_bounds__(256) k_pivot(MeshView m, const int32_t *__restrict__ rows,
                                                const int32_t *__restrict__ cols, int64_t n,
-                                               void *out, RuleSet rs, double kappa, int *status)
+                                               void *out, RuleSet rs, double kappa, int *status,
+                                               double eta)
 {
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(256) k_pivot(MeshView m, const int32_t *__rest
                 const double dy = d0[1] + x1 * e1a[1] + x2 * e2a[1] - y1 * e1b[1] - y2 * e2b[1];
                 const double dz = d0[2] + x1 * e1a[2] + x2 * e2a[2] - y1 * e1b[2] - y2 * e2b[2];
                 double kr, ki;
-                kval<KIND>(dx, dy, dz, B.n, kappa, kr, ki);
+                kval<KIND>(dx, dy, dz, B.n, kappa, kr, ki, eta);
                 double f = w;
                 if (ca >= 0) f *= (ca == 0 ? 1.0 - x1 : (ca == 1 ? x1 - x2 : x2));
                 if (cb >= 0) f *= (cb == 0 ? 1.0 - y1 : (cb == 1 ? y1 - y2 : y2));
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(256) k_pivot(MeshView m, const int32_t *__rest
                     pr += fabs(f) * sqrt(kr * kr + ki * ki);
                 } else {
                     pr += f * kr;
-                    if (KIND == BEM_HELMHOLTZ_SLP) pi += f * ki;
+                    if (kind_complex(KIND)) pi += f * ki;
                 }
             }
             const double scale = A.sg * B.sg * kInv4Pi;
@@ -324,9 +325,9 @@ __global__ void __launch_bounds__(256) k_pivot(MeshView m, const int32_t *__rest
         }
     }
     sr = warp_sum(sr);
-    if (KIND == BEM_HELMHOLTZ_SLP) si = warp_sum(si);
+    if (kind_complex(KIND)) si = warp_sum(si);
     if (lane == 0) {
-        if (KIND == BEM_HELMHOLTZ_SLP && !ABS) reinterpret_cast<double2 *>(out)[wid] = make_double2(sr, si);
+        if (kind_complex(KIND) && !ABS) reinterpret_cast<double2 *>(out)[wid] = make_double2(sr, si);
         else reinterpret_cast<double *>(out)[wid] = sr;
     }
 }
@@ -377,6 +378,10 @@ cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const R
     case BEM_LAPLACE_DLP:
         return L.mixed ? block_kind<BEM_LAPLACE_DLP, true>(m, L, R, prefix, status, grid, st)
                        : block_kind<BEM_LAPLACE_DLP, false>(m, L, R, prefix, status, grid, st);
+    case BEM_HELMHOLTZ_DLP:   // FP64 in every precision
+        return block_kind<BEM_HELMHOLTZ_DLP, false>(m, L, R, prefix, status, grid, st);
+    case BEM_HELMHOLTZ_BW:
+        return block_kind<BEM_HELMHOLTZ_BW, false>(m, L, R, prefix, status, grid, st);
     default:
         // the mixed Helmholtz form covers piecewise-constant pairs
         return (L.mixed && m.basis == BEM_P0)
@@ -387,7 +392,8 @@ cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const R
 
 cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const int32_t *cols,
                                  int64_t n, void *out, const Rule4D *rules, int kind,
-                                 double kappa, int *status, cudaStream_t st, bool absolute)
+                                 double kappa, int *status, cudaStream_t st, bool absolute,
+                                 double eta)
 {
     if (n <= 0) return cudaSuccess;
     RuleSet rs;
@@ -396,10 +402,12 @@ cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const i
         rs.n[c] = rules[c].n;
     }
     const int64_t blocks = (n + 7) / 8;
-#define BEM_PIV(K, A) k_pivot<K, A><<<(unsigned)blocks, 256, 0, st>>>(m, rows, cols, n, out, rs, kappa, status)
+#define BEM_PIV(K, A) k_pivot<K, A><<<(unsigned)blocks, 256, 0, st>>>(m, rows, cols, n, out, rs, kappa, status, eta)
     switch (kind) {
     case BEM_LAPLACE_SLP: if (absolute) BEM_PIV(BEM_LAPLACE_SLP, true); else BEM_PIV(BEM_LAPLACE_SLP, false); break;
     case BEM_LAPLACE_DLP: if (absolute) BEM_PIV(BEM_LAPLACE_DLP, true); else BEM_PIV(BEM_LAPLACE_DLP, false); break;
+    case BEM_HELMHOLTZ_DLP: if (absolute) BEM_PIV(BEM_HELMHOLTZ_DLP, true); else BEM_PIV(BEM_HELMHOLTZ_DLP, false); break;
+    case BEM_HELMHOLTZ_BW: if (absolute) BEM_PIV(BEM_HELMHOLTZ_BW, true); else BEM_PIV(BEM_HELMHOLTZ_BW, false); break;
     default: if (absolute) BEM_PIV(BEM_HELMHOLTZ_SLP, true); else BEM_PIV(BEM_HELMHOLTZ_SLP, false); break;
     }
 #undef BEM_PIV
@@ -457,6 +465,10 @@ cudaError_t launch_block_batch(const BatchJob *jobs, int n_jobs, const int64_t *
     case BEM_LAPLACE_DLP:
         return mixed ? batch_kind<BEM_LAPLACE_DLP, true>(jobs, n_jobs, job_end, basis, R, status, grid, st)
                      : batch_kind<BEM_LAPLACE_DLP, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
+    case BEM_HELMHOLTZ_DLP:   // FP64 in every precision
+        return batch_kind<BEM_HELMHOLTZ_DLP, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
+    case BEM_HELMHOLTZ_BW:
+        return batch_kind<BEM_HELMHOLTZ_BW, false>(jobs, n_jobs, job_end, basis, R, status, grid, st);
     default:
         return (mixed && basis == BEM_P0)
                    ? batch_kind<BEM_HELMHOLTZ_SLP, true>(jobs, n_jobs, job_end, basis, R, status, grid, st)

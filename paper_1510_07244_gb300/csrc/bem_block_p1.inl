@@ -54,7 +54,7 @@ cudaError_t single(const MeshView &m, const BlockLaunch &L, const Rule2D &R, con
                    int *status, int grid, cudaStream_t st)
 {
     constexpr bool MIXED = BEM_P1_MIXED;
-    const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP, MIXED, KIND == kFusedLaplace);
+    const size_t sm = p1_smem_bytes(kind_complex(KIND), MIXED, KIND == kFusedLaplace);
     cudaError_t e = cudaFuncSetAttribute(k_block_p1<KIND, NP, MIXED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -67,7 +67,7 @@ cudaError_t batch(const BatchJob *jobs, int n_jobs, const int64_t *job_end, cons
                   int *status, int grid, cudaStream_t st)
 {
     constexpr bool MIXED = BEM_P1_MIXED;
-    const size_t sm = p1_smem_bytes(KIND == BEM_HELMHOLTZ_SLP, MIXED, KIND == kFusedLaplace);
+    const size_t sm = p1_smem_bytes(kind_complex(KIND), MIXED, KIND == kFusedLaplace);
     // set once (outside any stream capture: plans issue once before capturing)
     static bool attr_done = false;
     if (!attr_done) {
@@ -89,6 +89,8 @@ cudaError_t single_kind(int kind, const MeshView &m, const BlockLaunch &L, const
     if (kind == BEM_LAPLACE_SLP) return single<BEM_LAPLACE_SLP, NP>(m, L, R, prefix, status, grid, st);
     if (kind == BEM_LAPLACE_DLP) return single<BEM_LAPLACE_DLP, NP>(m, L, R, prefix, status, grid, st);
 #if !BEM_P1_MIXED
+    if (kind == BEM_HELMHOLTZ_DLP) return single<BEM_HELMHOLTZ_DLP, NP>(m, L, R, prefix, status, grid, st);
+    if (kind == BEM_HELMHOLTZ_BW) return single<BEM_HELMHOLTZ_BW, NP>(m, L, R, prefix, status, grid, st);
     return single<BEM_HELMHOLTZ_SLP, NP>(m, L, R, prefix, status, grid, st);
 #else
     return cudaErrorInvalidValue;
@@ -102,6 +104,8 @@ cudaError_t batch_kind(int kind, const BatchJob *jobs, int n_jobs, const int64_t
     if (kind == BEM_LAPLACE_SLP) return batch<BEM_LAPLACE_SLP, NP>(jobs, n_jobs, job_end, R, status, grid, st);
     if (kind == BEM_LAPLACE_DLP) return batch<BEM_LAPLACE_DLP, NP>(jobs, n_jobs, job_end, R, status, grid, st);
 #if !BEM_P1_MIXED
+    if (kind == BEM_HELMHOLTZ_DLP) return batch<BEM_HELMHOLTZ_DLP, NP>(jobs, n_jobs, job_end, R, status, grid, st);
+    if (kind == BEM_HELMHOLTZ_BW) return batch<BEM_HELMHOLTZ_BW, NP>(jobs, n_jobs, job_end, R, status, grid, st);
     return batch<BEM_HELMHOLTZ_SLP, NP>(jobs, n_jobs, job_end, R, status, grid, st);
 #else
     if (kind == kFusedLaplace) return batch<kFusedLaplace, NP>(jobs, n_jobs, job_end, R, status, grid, st);

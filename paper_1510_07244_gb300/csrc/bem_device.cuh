@@ -41,7 +41,7 @@ __device__ __forceinline__ void load_tri(const double *__restrict__ geom, int64_
 // Kernel value without the 1/(4 pi) factor; d = x - y, nb = trial normal.
 template <int KIND>
 __device__ __forceinline__ void kval(double dx, double dy, double dz, const double *nb,
-                                     double kappa, double &re, double &im)
+                                     double kappa, double &re, double &im, double eta = 0.0)
 {
     const double r2 = dx * dx + dy * dy + dz * dz;
     const double ri = rsqrt(r2);
@@ -52,11 +52,25 @@ __device__ __forceinline__ void kval(double dx, double dy, double dz, const doub
         const double dn = dx * nb[0] + dy * nb[1] + dz * nb[2];
         re = dn * ri * ri * ri;
         im = 0.0;
-    } else {
+    } else if (KIND == BEM_HELMHOLTZ_SLP) {
         double s, c;
         sincos(kappa * (r2 * ri), &s, &c);
         re = c * ri;
         im = s * ri;
+    } else {
+        // (x-y).n_y (1 - i kappa r) exp(i kappa r) / r^3, and for the
+        // Brakhage-Werner combination minus i eta exp(i kappa r) / r
+        const double dn = dx * nb[0] + dy * nb[1] + dz * nb[2];
+        const double kr = kappa * (r2 * ri);
+        double s, c;
+        sincos(kr, &s, &c);
+        const double f = dn * ri * ri * ri;
+        re = f * (c + kr * s);
+        im = f * (s - kr * c);
+        if (KIND == BEM_HELMHOLTZ_BW) {
+            re += eta * s * ri;
+            im -= eta * c * ri;
+        }
     }
 }
 
@@ -578,14 +592,15 @@ __device__ __forceinline__ FF operator-(FF a, FF b)
 
 template <int KIND, int BASIS, int CAS>
 __device__ __forceinline__ void touch_pair(const MeshView &m, int idx, const double *__restrict__ rule,
-                                           int np, double kappa, int lane)
+                                           int np, double kappa, int lane, double eta = 0.0)
 {
     const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);
     const int pc = __ldg(m.nb_perm + idx);
     const int *pa = c_perm[pc / 6], *pb = c_perm[pc % 6];
     constexpr int NACC = BASIS == BEM_P0 ? 1 : 9;
-    constexpr bool CPLX = KIND == BEM_HELMHOLTZ_SLP;
-    constexpr bool ZERO = KIND == BEM_LAPLACE_DLP && CAS == kIdentical;   // flat pair
+    constexpr bool CPLX = kind_complex(KIND);
+    // a flat identical pair has no double layer (the height vanishes)
+    constexpr bool ZERO = (KIND == BEM_LAPLACE_DLP || KIND == BEM_HELMHOLTZ_DLP) && CAS == kIdentical;
     double accr[NACC], acci[NACC];
 #pragma unroll
     for (int k = 0; k < NACC; ++k) accr[k] = acci[k] = 0.0;
@@ -646,11 +661,26 @@ __device__ __forceinline__ void touch_pair(const MeshView &m, int idx, const dou
             } else if (KIND == BEM_LAPLACE_DLP) {
                 const double dn = CAS == kEdge ? x2 * H : dx * nb[0] + dy * nb[1] + dz * nb[2];
                 kr = dn * ri * ri * ri;
-            } else {
+            } else if (KIND == BEM_HELMHOLTZ_SLP) {
                 double sn, cs;
                 sincos(kappa * (r2 * ri), &sn, &cs);
                 kr = cs * ri;
                 ki = sn * ri;
+            } else {
+                // Helmholtz double layer (and Brakhage-Werner): the height is
+                // zero on an identical flat pair, x2 H on a common edge
+                const double dn = CAS == kIdentical ? 0.0
+                                  : (CAS == kEdge ? x2 * H : dx * nb[0] + dy * nb[1] + dz * nb[2]);
+                const double kd = kappa * (r2 * ri);
+                double sn, cs;
+                sincos(kd, &sn, &cs);
+                const double f = dn * ri * ri * ri;
+                kr = f * (cs + kd * sn);
+                ki = f * (sn - kd * cs);
+                if (KIND == BEM_HELMHOLTZ_BW) {
+                    kr += eta * sn * ri;
+                    ki -= eta * cs * ri;
+                }
             }
             const double wr = w * kr, wi = w * ki;
             if (BASIS == BEM_P0) {
@@ -773,7 +803,7 @@ template <int CAS, int KIND, int BASIS>
 __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const float *__restrict__ rule,
                                           int np, int lane, float kappa = 0.0f)
 {
-    constexpr bool CPLX = KIND == BEM_HELMHOLTZ_SLP;
+    constexpr bool CPLX = kind_complex(KIND);
     const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);
     const int pc = __ldg(m.nb_perm + idx);
     const int *pa = c_perm[pc / 6], *pb = c_perm[pc % 6];
@@ -964,7 +994,8 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
 // ---------------------------------------------------------------------------
 template <int KIND, int NP>
 __device__ __forceinline__ void regular_p0(const Tri &A, const Tri &B, const Rule2D &R,
-                                           double kappa, double &out_re, double &out_im)
+                                           double kappa, double &out_re, double &out_im,
+                                           double eta = 0.0)
 {
     double e1a[3], e2a[3], d0[3], yx[NP], yy[NP], yz[NP];
 #pragma unroll
@@ -995,12 +1026,12 @@ __device__ __forceinline__ void regular_p0(const Tri &A, const Tri &B, const Rul
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             double kr, ki;
-            kval<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], B.n, kappa, kr, ki);
+            kval<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], B.n, kappa, kr, ki, eta);
             ir += R.w[j] * kr;
-            if (KIND == BEM_HELMHOLTZ_SLP) ii += R.w[j] * ki;
+            if (kind_complex(KIND)) ii += R.w[j] * ki;
         }
         sr += R.w[i] * ir;
-        if (KIND == BEM_HELMHOLTZ_SLP) si += R.w[i] * ii;
+        if (kind_complex(KIND)) si += R.w[i] * ii;
     }
     const double scale = A.sg * B.sg * kInv4Pi;
     out_re = sr * scale;
@@ -1009,7 +1040,8 @@ __device__ __forceinline__ void regular_p0(const Tri &A, const Tri &B, const Rul
 
 template <int KIND, int NP>
 __device__ __forceinline__ void regular_p1(const Tri &A, const Tri &B, const Rule2D &R,
-                                           double kappa, double *accr, double *acci)
+                                           double kappa, double *accr, double *acci,
+                                           double eta = 0.0)
 {
     double e1a[3], e2a[3], d0[3], yx[NP], yy[NP], yz[NP];
 #pragma unroll
@@ -1041,14 +1073,14 @@ __device__ __forceinline__ void regular_p1(const Tri &A, const Tri &B, const Rul
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             double kr, ki;
-            kval<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], B.n, kappa, kr, ki);
+            kval<KIND>(xx - yx[j], xy - yy[j], xz - yz[j], B.n, kappa, kr, ki, eta);
             const double lb[3] = {1.0 - R.s[j], R.s[j] - R.t[j], R.t[j]};
             const double wr = R.w[j] * kr;
             const double wi = R.w[j] * ki;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 ir[q] += wr * lb[q];
-                if (KIND == BEM_HELMHOLTZ_SLP) ii[q] += wi * lb[q];
+                if (kind_complex(KIND)) ii[q] += wi * lb[q];
             }
         }
         const double la[3] = {1.0 - R.s[i], R.s[i] - R.t[i], R.t[i]};
@@ -1058,7 +1090,7 @@ __device__ __forceinline__ void regular_p1(const Tri &A, const Tri &B, const Rul
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 accr[p * 3 + q] += f * ir[q];
-                if (KIND == BEM_HELMHOLTZ_SLP) acci[p * 3 + q] += f * ii[q];
+                if (kind_complex(KIND)) acci[p * 3 + q] += f * ii[q];
             }
         }
     }
@@ -1175,10 +1207,10 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
             Tri A, B;
             load_tri(m.geom, a, A);
             load_tri(m.geom, b, B);
-            regular_p0<KIND, NP>(A, B, R, L.kappa, re, im);
+            regular_p0<KIND, NP>(A, B, R, L.kappa, re, im, L.eta);
         }
         const int64_t o = bi.off + (int64_t)r + (int64_t)c * bi.nr;
-        if (KIND == BEM_HELMHOLTZ_SLP) reinterpret_cast<double2 *>(L.out)[o] = make_double2(re, im);
+        if (kind_complex(KIND)) reinterpret_cast<double2 *>(L.out)[o] = make_double2(re, im);
         else if (guard) reinterpret_cast<float2 *>(L.out)[o] = make_float2((float)re, absum);
         else reinterpret_cast<double *>(L.out)[o] = re;
     }
@@ -1339,7 +1371,7 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
                                         const int64_t *__restrict__ prefix, int64_t tile,
                                         int *status, unsigned char *smem_raw)
 {
-    constexpr bool CPLX = KIND == BEM_HELMHOLTZ_SLP;
+    constexpr bool CPLX = kind_complex(KIND);
     // fused: single layer in the real slots, double layer in the second ones
     constexpr bool FUSED = KIND == kFusedLaplace;
     constexpr bool TWO = CPLX || FUSED;
@@ -1463,7 +1495,7 @@ __device__ __forceinline__ void p1_tile(const MeshView &m, const BlockLaunch &L,
                     load_tri(m.geom, a, A);
                     load_tri(m.geom, b, B);
                     double dr[9], di[9];
-                    regular_p1<KIND, NP>(A, B, R, L.kappa, dr, di);
+                    regular_p1<KIND, NP>(A, B, R, L.kappa, dr, di, L.eta);
 #pragma unroll
                     for (int q = 0; q < 9; ++q) {
                         vr[q] = (Val)dr[q];

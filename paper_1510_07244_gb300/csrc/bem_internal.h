@@ -185,6 +185,7 @@ struct BlockLaunch {
     void *out;
     int kind;
     double kappa;
+    double eta = 0.0;   // Brakhage-Werner coupling (BEM_HELMHOLTZ_BW)
     int lower_only;
     int allow_touching;
     int mixed;        // 1: regular pairs in FP32 (BEM_MIXED, BEM_MIXED_FULL)
@@ -206,7 +207,7 @@ struct BlockLaunch {
 };
 
 // Internal kernel id of the fused single + double layer (never a public kind).
-constexpr int kFusedLaplace = 3;
+constexpr int kFusedLaplace = 16;
 
 // One support record (int32 words, 16-byte multiple): list lengths [kTile],
 // per-vertex lists [kMaxDegP1][kTile], triangles [kTile * kMaxDegP1], count.
@@ -219,8 +220,23 @@ constexpr int kSupInts = (kSupCount + 1 + 3) & ~3;
 // Precision forms: float arithmetic for disjoint pairs, and for the touching
 // pairs of case `cas`.
 inline bool is_mixed(int precision) { return precision == BEM_MIXED || precision == BEM_MIXED_FULL; }
-inline int touch_in_float(int precision, int cas)
+// kernels with complex values, and kernels that run in FP64 in every precision
+__host__ __device__ constexpr bool kind_complex(int kind)
 {
+    return kind == BEM_HELMHOLTZ_SLP || kind == BEM_HELMHOLTZ_DLP || kind == BEM_HELMHOLTZ_BW;
+}
+__host__ __device__ constexpr bool kind_fp64_only(int kind)
+{
+    return kind == BEM_HELMHOLTZ_DLP || kind == BEM_HELMHOLTZ_BW;
+}
+// kernels whose numerator is the height (x - y).n_y of x above the trial plane
+__host__ __device__ constexpr bool kind_has_height(int kind)
+{
+    return kind == BEM_LAPLACE_DLP || kind == BEM_HELMHOLTZ_DLP || kind == BEM_HELMHOLTZ_BW;
+}
+inline int touch_in_float(int precision, int cas, int kind)
+{
+    if (kind_fp64_only(kind)) return 0;
     return precision == BEM_MIXED_FULL || (precision == BEM_MIXED && cas == kVertex);
 }
 
@@ -280,6 +296,7 @@ cudaError_t guard_run(const GuardSet &g, int num_sms, int *status, cudaStream_t 
 struct TouchJob {
     MeshView m;                // m.table = this job's touching table
     double kappa;
+    double eta = 0.0;
 };
 
 // Launch shape of a block-engine bucket (autotuned).
@@ -291,7 +308,7 @@ cudaError_t launch_tile_prefix(const BlockLaunch &L, int tr, int tc, int64_t *pr
                                int *status, cudaStream_t st);
 cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
                             const Rule4D &rule, int kind, double kappa, int f32,
-                            cudaStream_t st);
+                            cudaStream_t st, double eta = 0.0);
 cudaError_t launch_block_engine(const MeshView &m, const BlockLaunch &L, const Rule2D &rule,
                                 const int64_t *prefix, int *status, int grid, cudaStream_t st);
 size_t p1_smem_bytes(bool cplx, bool mixed, bool fused = false);
@@ -340,7 +357,8 @@ cudaError_t launch_block_batch(const BatchJob *jobs, int n_jobs, const int64_t *
                                cudaStream_t st);
 cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const int32_t *cols,
                                  int64_t n, void *out, const Rule4D *rules /*[4]*/, int kind,
-                                 double kappa, int *status, cudaStream_t st, bool absolute);
+                                 double kappa, int *status, cudaStream_t st, bool absolute,
+                                 double eta = 0.0);
 
 // bem_order.cu: learned-order near field of one piecewise-constant job
 cudaError_t learned_alloc(LearnedScratch &S, int64_t tiles);

@@ -349,6 +349,9 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         if (rc == BEM_OK && J.quad.order_mode == BEM_ORDER_LEARNED) {
             if (ji.m->v.basis != BEM_P0)
                 rc = api_fail(ctx, BEM_ERR_UNSUPPORTED, "learned orders need the piecewise-constant basis");
+            else if (kind_fp64_only(J.kernel.kind))
+                rc = api_fail(ctx, BEM_ERR_UNSUPPORTED,
+                              "learned orders cover the Laplace kernels and the Helmholtz single layer");
             else if (!ctx->order_model)
                 rc = api_fail(ctx, BEM_ERR_INVALID_ARG, "order_mode LEARNED needs bem_set_order_model");
         }
@@ -375,12 +378,14 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         t.m = mv;
         t.m.table = table;
         t.kappa = ji.J->kernel.kappa;
+        t.eta = ji.J->kernel.eta;
         ji.touch_job = (int)tj.size();
         tj.push_back(t);
         const int qs[4] = {0, ji.J->quad.q_vertex, ji.J->quad.q_edge, ji.J->quad.q_identical};
         for (int c = kVertex; c <= kIdentical; ++c) {
             auto &v = titems[std::make_tuple(mv.basis, ji.J->kernel.kind, c,
-                                             touch_in_float(ji.J->quad.precision, c), qs[c])];
+                                             touch_in_float(ji.J->quad.precision, c,
+                                                            ji.J->kernel.kind), qs[c])];
             for (int idx : ji.m->hlist[c]) v.push_back(make_int2(ji.touch_job, idx));
         }
     }
@@ -485,7 +490,7 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
             p->learned.push_back(l);
             continue;
         }
-        const int mixed = is_mixed(J.quad.precision) &&
+        const int mixed = is_mixed(J.quad.precision) && !kind_fp64_only(J.kernel.kind) &&
                           !(J.kernel.kind == BEM_HELMHOLTZ_SLP && ji.m->v.basis == BEM_P1);
         const bool coupling = use_coupling_engine(ji.m->v.basis, J.kernel.kind, mixed, ji.near ? 1 : 0);
         const bool fused = out2[jx] != nullptr;
@@ -532,6 +537,7 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         L.lower_only = 0;
         L.allow_touching = ji.near ? 1 : 0;
         L.mixed = mixed;
+        L.eta = J.kernel.eta;
         if (b.basis == BEM_P0 && b.kind == BEM_LAPLACE_DLP && mixed) {
             // cancellation guard: packed (value, sum of |terms|) outputs, then
             // the guard pass of this job's orders

@@ -9,11 +9,11 @@ namespace bem {
 template <int KIND, int BASIS, int CAS>
 __global__ void __launch_bounds__(256) k_touching(MeshView m, const int *__restrict__ list,
                                                   int64_t n, const double *__restrict__ rule,
-                                                  int np, double kappa)
+                                                  int np, double kappa, double eta)
 {
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wid >= n) return;
-    touch_pair<KIND, BASIS, CAS>(m, __ldg(list + wid), rule, np, kappa, threadIdx.x & 31);
+    touch_pair<KIND, BASIS, CAS>(m, __ldg(list + wid), rule, np, kappa, threadIdx.x & 31, eta);
 }
 
 // Batched: items[k] = (job, touching index) over many meshes / kernels.
@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(256) k_touching_batch(const TouchJob *__restri
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wid >= n) return;
     const int2 it = items[wid];
-    touch_pair<KIND, BASIS, CAS>(jobs[it.x].m, it.y, rule, np, jobs[it.x].kappa, threadIdx.x & 31);
+    touch_pair<KIND, BASIS, CAS>(jobs[it.x].m, it.y, rule, np, jobs[it.x].kappa, threadIdx.x & 31,
+                                 jobs[it.x].eta);
 }
 
 template <int CAS, int KIND, int BASIS>
@@ -52,12 +53,13 @@ __global__ void __launch_bounds__(256) k_touching_f32_batch(const TouchJob *__re
 }
 
 cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
-                            const Rule4D &rule, int kind, double kappa, int f32, cudaStream_t st)
+                            const Rule4D &rule, int kind, double kappa, int f32, cudaStream_t st,
+                            double eta)
 {
     if (n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + 7) / 8);
     const bool p1 = m.basis == BEM_P1;
-    if (f32 && rule.f) {
+    if (f32 && rule.f && !kind_fp64_only(kind)) {
         const float kf = (float)kappa;
 #define BEM_TV(K, B)                                                                          \
     do {                                                                                      \
@@ -71,7 +73,7 @@ cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t
 #undef BEM_TV
         return cudaGetLastError();
     }
-#define BEM_TOUCH(K, B, C) k_touching<K, B, C><<<blocks, 256, 0, st>>>(m, list, n, rule.d, rule.n, kappa)
+#define BEM_TOUCH(K, B, C) k_touching<K, B, C><<<blocks, 256, 0, st>>>(m, list, n, rule.d, rule.n, kappa, eta)
 #define BEM_TOUCH_CASE(K, B)                                   \
     do {                                                       \
         if (cas == kIdentical) BEM_TOUCH(K, B, kIdentical);    \
@@ -81,6 +83,8 @@ cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t
     switch (kind) {
     case BEM_LAPLACE_SLP: if (p1) BEM_TOUCH_CASE(BEM_LAPLACE_SLP, BEM_P1); else BEM_TOUCH_CASE(BEM_LAPLACE_SLP, BEM_P0); break;
     case BEM_LAPLACE_DLP: if (p1) BEM_TOUCH_CASE(BEM_LAPLACE_DLP, BEM_P1); else BEM_TOUCH_CASE(BEM_LAPLACE_DLP, BEM_P0); break;
+    case BEM_HELMHOLTZ_DLP: if (p1) BEM_TOUCH_CASE(BEM_HELMHOLTZ_DLP, BEM_P1); else BEM_TOUCH_CASE(BEM_HELMHOLTZ_DLP, BEM_P0); break;
+    case BEM_HELMHOLTZ_BW: if (p1) BEM_TOUCH_CASE(BEM_HELMHOLTZ_BW, BEM_P1); else BEM_TOUCH_CASE(BEM_HELMHOLTZ_BW, BEM_P0); break;
     default: if (p1) BEM_TOUCH_CASE(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TOUCH_CASE(BEM_HELMHOLTZ_SLP, BEM_P0); break;
     }
 #undef BEM_TOUCH_CASE
@@ -94,7 +98,7 @@ cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int
     if (n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((n + 7) / 8);
     const bool p1 = basis == BEM_P1;
-    if (f32 && rule.f) {
+    if (f32 && rule.f && !kind_fp64_only(kind)) {
 #define BEM_TVB(K, B)                                                                          \
     do {                                                                                       \
         if (cas == kIdentical) k_touching_f32_batch<kIdentical, K, B><<<blocks, 256, 0, st>>>(jobs, items, n, rule.f, rule.n); \
@@ -117,6 +121,8 @@ cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int
     switch (kind) {
     case BEM_LAPLACE_SLP: if (p1) BEM_TB_CASE(BEM_LAPLACE_SLP, BEM_P1); else BEM_TB_CASE(BEM_LAPLACE_SLP, BEM_P0); break;
     case BEM_LAPLACE_DLP: if (p1) BEM_TB_CASE(BEM_LAPLACE_DLP, BEM_P1); else BEM_TB_CASE(BEM_LAPLACE_DLP, BEM_P0); break;
+    case BEM_HELMHOLTZ_DLP: if (p1) BEM_TB_CASE(BEM_HELMHOLTZ_DLP, BEM_P1); else BEM_TB_CASE(BEM_HELMHOLTZ_DLP, BEM_P0); break;
+    case BEM_HELMHOLTZ_BW: if (p1) BEM_TB_CASE(BEM_HELMHOLTZ_BW, BEM_P1); else BEM_TB_CASE(BEM_HELMHOLTZ_BW, BEM_P0); break;
     default: if (p1) BEM_TB_CASE(BEM_HELMHOLTZ_SLP, BEM_P1); else BEM_TB_CASE(BEM_HELMHOLTZ_SLP, BEM_P0); break;
     }
 #undef BEM_TB_CASE

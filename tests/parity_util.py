@@ -80,4 +80,4 @@ def block_job(pkg, mesh_id, bs, kernel, kappa, quad, out):
 def oracle_entries(mesh, basis, rows, cols, kernel, kappa, quad):
     z = oracle.entries(mesh.verts, mesh.tris, rows, cols, kernel=kernel, kappa=kappa,
                        basis=basis, **quad)
-    return z if kernel == "helmholtz_slp" else z.real
+    return z if kernel.startswith("helmholtz") else z.real
