@@ -95,6 +95,17 @@ PEAK_FP64 = 152 * 2.07e9 * 4.0 / 1e12     # TFLOP/s: 152 SM x 2 FMA/clk x 2.07 G
 PEAK_FP32 = 152 * 2.07e9 * 256.0 / 1e12   # TFLOP/s: 152 SM x 128 FMA/clk x 2.07 GHz
 # the denominators of the rooflines: the measured rates once measure_peaks has
 # run (its FP32 and FP64 FMA probes), the unit-count products before
+def _measured_hbm():
+    """The HBM copy rate measured on this machine (MEASURED_PEAKS.json), else the
+    pool's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+MEASURED_HBM_GBS = _measured_hbm()
 PEAKS = {"fp32": PEAK_FP32, "fp64": PEAK_FP64,
          "source": "derived: 152 SM x (2 FP64 | 128 FP32) FMA/clk x 2.07 GHz"}
 
@@ -764,14 +775,14 @@ def run_reference(args):
 # by entry.  These lines are measurements of the other configurations, not the
 # default benchmark line.
 # ---------------------------------------------------------------------------
-def extra_items(name):
+def extra_items(name, args):
     """(workload name, basis, Quad, items); an item has mesh, operators, near, far,
     partition (for the host GCA)."""
     import synth
     if name == "c3":
         w = synth.workloads.config3()
         return w.name, w.basis, w.quad, [w]
-    bw = synth.workloads.config4()
+    bw = synth.workloads.config4(args.c4_meshes)
     return bw.name, bw.basis, bw.quad, bw.items
 
 
@@ -783,7 +794,7 @@ def run_extra(args):
 
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
-    name, basis, quad, items = extra_items(args.workload)
+    name, basis, quad, items = extra_items(args.workload, args)
     # host GCA pivots per mesh, with the largest wave number of its operators
     gca_s = 0.0
     if args.pivots == "gca":
@@ -1346,6 +1357,8 @@ def run_c5(args, emit=True):
         return ms
 
     def learned_form(outs, steps, conf):
+        """The chosen form: learned orders + float arithmetic + one persistent
+        plan (CUDA graph) over all four jobs."""
         ctx.bem_set_order_model(mlp, conf)
         quad = pkg.quad_desc(**w.quad.kw(), precision="mixed_full", order_mode="learned")
         near, far = [], []
@@ -1356,25 +1369,19 @@ def run_c5(args, emit=True):
                 lst.append(pkg.BlockJob(mid, st["row_ptr"], st["row_idx"], st["col_ptr"],
                                         st["col_idx"], st["blk_row"], st["blk_col"],
                                         st["blk_off"], outs[(op.kernel, nm)], kd, quad))
-        totals = np.zeros(6, np.int64)
-
-        def step():
-            # one learned call per job; class counts summed over the jobs
-            for j in near:
-                ctx.bem_near_field([j])
-                totals[:] += ctx.bem_learned_counts()
-            for j in far:
-                ctx.bem_coupling_blocks([j])
-                totals[:] += ctx.bem_learned_counts()
-        totals[:] = 0
+        plan = ctx.bem_plan_create(near, far, pkg.PLAN_GRAPH | pkg.PLAN_AUTOTUNE | pkg.PLAN_PROFILE)
         ctx.bem_profile_reset()
         ctx.bem_profile_enable(True)
-        ms = timed(step, steps)
+        ms = timed(lambda: ctx.bem_plan_run(plan), steps)
         prof = ctx.bem_profile_read()
         ctx.bem_profile_enable(False)
+        counts = ctx.bem_plan_learned_counts(plan)
+        info = ctx.bem_plan_info(plan)
+        ctx.bem_plan_destroy(plan)
         runs = args.warmup + steps
-        counts = [int(v) // runs for v in totals]
         per_step = {k: round(v[1] / runs, 3) for k, v in prof.items()}
+        per_step["kernels_per_step"] = info["touch_launches"] + info["block_launches"] + \
+            info["aux_launches"]
         return ms, counts, per_step
 
     clocks = Clocks(0)
@@ -1447,6 +1454,7 @@ def run_c5(args, emit=True):
                        "entries_per_step": int(entries), "quadrature": w.quad.kw(),
                        "precision": "mixed_full", "order_mode": "learned for every disjoint "
                        "pair (near field and coupling blocks); touching pairs at the fixed orders",
+                       "driver": "one persistent plan (CUDA graph) over the four learned jobs",
                        "pivots": "host GCA (kappa 16)", "gca_setup_s": gca_s,
                        "l2": "flushed between timed steps (256 MiB write, untimed)"},
             "learned": {"class_counts": counts, "class_points": pkg.ORDER_CLASS_POINTS,
@@ -1688,6 +1696,167 @@ def green_cpu_baseline(w, G, budget_s):
                       f"on {os.cpu_count()} OpenMP threads"}
 
 
+def measure_h2_solve(torch, pkg, ctx, dev, stream, k=64, warmup=3, reps=20):
+    """The interior Dirichlet problem of Section 4 on the octahedral sphere with
+    8 k^2 triangles (P0; f1 = x1^2 - x3^2, Neumann data 2 f1): GCA bases on
+    the host (at most 32 pivots per cluster, tolerance 1e-8), the single- and
+    double-layer near-field and coupling blocks assembled on the device (FP64
+    form), V in H2 form solved by conjugate gradients for the right-hand side
+    (1/2 M + K) f1 (an H2 product).  Reports the H2 product's time and
+    bandwidth (it is memory-bound: every stored entry is read once), the
+    solve, and the Neumann error."""
+    import synth
+    from synth import structure, workloads
+    mesh = synth.octasphere(k)
+    n = mesh.nt
+    v = mesh.verts[mesh.tris]
+    area = 0.5 * np.linalg.norm(np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 1]), axis=1)
+    c = v.mean(axis=1)
+    f1 = c[:, 0] ** 2 - c[:, 2] ** 2
+    part = structure.build_block_partition(mesh, "p0", 32, 2.0)
+    ptr, idx = part.cluster_csr()
+    son = part.son_array()
+    t0 = time.perf_counter()
+    pp, pi, mats = pkg.bem_gca_bases(mesh.verts, mesh.tris, "p0", ptr, idx, son, eps=1e-8,
+                                     max_rank=32)
+    gca_s = time.perf_counter() - t0
+    nr, nc, no, ntot = part.near_blocks()
+    fr, fc, fo, ftot = structure.coupling_blocks(part, pp)
+    near = workloads.BlockSet(ptr, idx, ptr, idx, nr, nc, no, ntot)
+    far = workloads.BlockSet(pp, pi, pp, pi, fr, fc, fo, ftot)
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p0")
+    quad = pkg.quad_desc(q_regular=3, regular_rule="duffy", q_identical=5, q_edge=5, q_vertex=5)
+
+    def dev_arr(a, dt):
+        return torch.as_tensor(np.ascontiguousarray(a)).to(device=dev, dtype=dt)
+
+    rp, ri = dev_arr(ptr, torch.int32), dev_arr(idx, torch.int32)
+    pr, pq = dev_arr(pp, torch.int32), dev_arr(pi, torch.int32)
+    vals, hs = {}, {}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for kern in ("laplace_slp", "laplace_dlp"):
+        kd = pkg.kernel_desc(kern)
+        nv_ = torch.zeros(max(1, ntot), dtype=torch.float64, device=dev)
+        fv_ = torch.zeros(max(1, ftot), dtype=torch.float64, device=dev)
+        ctx.bem_near_field([pkg.BlockJob(mid, rp, ri, rp, ri, dev_arr(nr, torch.int32),
+                                         dev_arr(nc, torch.int32), dev_arr(no, torch.int64), nv_,
+                                         kd, quad)])
+        ctx.bem_coupling_blocks([pkg.BlockJob(mid, pr, pq, pr, pq, dev_arr(fr, torch.int32),
+                                              dev_arr(fc, torch.int32), dev_arr(fo, torch.int64),
+                                              fv_, kd, quad)])
+        vals[kern] = (nv_, fv_)
+    ev1.record(stream)
+    ctx.bem_sync()
+    assembly_ms = ev0.elapsed_time(ev1)
+    hs["V"] = ctx.bem_h2_create(n, ptr, idx, son, pp, pi, mats, (nr, nc, no), vals["laplace_slp"][0],
+                                (fr, fc, fo), vals["laplace_slp"][1])
+    hs["K"] = ctx.bem_h2_create(n, ptr, idx, son, pp, pi, mats, (nr, nc, no), vals["laplace_dlp"][0],
+                                (fr, fc, fo), vals["laplace_dlp"][1], diag=0.5 * area)
+    x = torch.as_tensor(f1).to(dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    for _ in range(warmup):
+        ctx.bem_h2_matvec(hs["V"], x, y)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    torch.cuda.synchronize(dev)
+    for a, b in evs:
+        a.record(stream)
+        ctx.bem_h2_matvec(hs["V"], x, y)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    mv_ms = min(a.elapsed_time(b) for a, b in evs)
+    basis_elems = sum(np.asarray(m).size for m in mats)
+    bytes_mv = 8.0 * (ntot + ftot + basis_elems) + 8.0 * 4 * n
+    rhs = torch.empty(n, dtype=torch.float64, device=dev)
+    ctx.bem_h2_matvec(hs["K"], x, rhs)
+    alpha = torch.empty(n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    it, res = ctx.bem_h2_cg(hs["V"], rhs, alpha, tol=1e-8, maxit=5000)
+    solve_s = time.perf_counter() - t0
+    a_h = alpha.cpu().numpy()
+    err = float(np.sqrt(np.sum(area * (a_h - 2 * f1) ** 2) / np.sum(area * (2 * f1) ** 2)))
+    for h in hs.values():
+        ctx.bem_h2_destroy(h)
+    ctx.bem_mesh_free(mid)
+    bw = bytes_mv / (mv_ms / 1e3) / 1e9
+    return {"workload": f"interior Dirichlet problem, octahedral sphere {n} triangles, P0, "
+                        f"f1 = x1^2 - x3^2 (Neumann data 2 f1)",
+            "gca_bases_s": gca_s, "assembly_ms": assembly_ms,
+            "near_entries": int(ntot), "coupling_entries": int(ftot),
+            "basis_entries": int(basis_elems), "max_rank": int(np.diff(pp).max()),
+            "matvec": {"ms": mv_ms, "bytes": bytes_mv, "achieved_gbs": bw,
+                       "peak_gbs": MEASURED_HBM_GBS, "frac": bw / MEASURED_HBM_GBS,
+                       "bound": "hbm", "note": "every stored entry read once per product"},
+            "cg": {"iterations": it, "rel_residual": res, "seconds": solve_s, "tol": 1e-8},
+            "neumann_rel_error_vs_2f1": err}
+
+
+def measure_bw_solve(torch, pkg, ctx, dev, stream, ks=(16, 32), kappa=3.0, eta=3.0):
+    """The exterior Helmholtz problem of Section 4 in the Brakhage-Werner form on
+    the octahedral spheres with 8 k^2 triangles: f = g(x, (0, 0, 0.2)), kappa 3,
+    eta 3.  The dense matrix K - i eta V (FP64, bem_assemble_dense), F by the
+    Green-matrix call, (1/2 M + K - i eta V) w = F by GMRES, and the field at 24
+    seeded exterior points against f.  Times the assembly and the solve."""
+    import synth
+    out = {"problem": "exterior Dirichlet problem, Brakhage-Werner form, f = g(x, (0,0,0.2)), "
+                      "kappa 3, eta 3, P0, octahedral spheres", "meshes": []}
+    z0 = np.array([0.0, 0.0, 0.2])
+    for k in ks:
+        mesh = synth.octasphere(k)
+        n = mesh.nt
+        mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p0")
+        quad = pkg.quad_desc(q_regular=3, regular_rule="duffy", q_identical=5, q_edge=5, q_vertex=5)
+        A = torch.empty(n * n, dtype=torch.complex128, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx.bem_assemble_dense(mid, pkg.kernel_desc("helmholtz_bw", kappa, eta), quad, 0, A)
+        ctx.bem_sync()
+        e0.record(stream)
+        ctx.bem_assemble_dense(mid, pkg.kernel_desc("helmholtz_bw", kappa, eta), quad, 0, A)
+        e1.record(stream)
+        ctx.bem_sync()
+        asm_ms = e0.elapsed_time(e1)
+        v = mesh.verts[mesh.tris]
+        area = 0.5 * np.linalg.norm(np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 1]), axis=1)
+
+        def d(a, dt):
+            return torch.as_tensor(np.ascontiguousarray(a)).to(device=dev, dtype=dt)
+
+        F = torch.empty(2 * n, dtype=torch.complex128, device=dev)
+        job = pkg.GreenJob(mid, d([0, n], torch.int32), torch.arange(n, dtype=torch.int32,
+                                                                       device=dev),
+                           d([0, 1], torch.int32), d(z0[None, :], torch.float64),
+                           d([[0.0, 0.0, 1.0]], torch.float64), d([0], torch.int64), F,
+                           kernel=pkg.kernel_desc("helmholtz_slp", kappa), rule="duffy", q=5)
+        ctx.bem_green_matrices(job)
+        w = torch.empty(n, dtype=torch.complex128, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        it, res = ctx.bem_dense_gmres(A, F[:n].contiguous(), w, diag=d(0.5 * area + 0j,
+                                                                        torch.complex128),
+                                      tol=1e-10, restart=100)
+        solve_s = time.perf_counter() - t0
+        rng = np.random.default_rng(3)
+        dz = rng.standard_normal((24, 3))
+        z = dz / np.linalg.norm(dz, axis=1)[:, None] * rng.uniform(1.5, 3.0, 24)[:, None]
+        u = torch.empty(24, dtype=torch.complex128, device=dev)
+        ctx.bem_potentials(mid, pkg.kernel_desc("helmholtz_bw", kappa, eta), d(z, torch.float64),
+                           w, u, q=5)
+        ctx.bem_sync()
+        r = np.linalg.norm(z - z0, axis=1)
+        f = np.exp(1j * kappa * r) / (4 * np.pi * r)
+        err = float(np.abs(u.cpu().numpy() - f).max() / np.abs(f).max())
+        ctx.bem_mesh_free(mid)
+        out["meshes"].append({"triangles": n, "assembly_ms": asm_ms,
+                              "entries_per_s": n * n / (asm_ms / 1e3),
+                              "gmres_iterations": it, "gmres_rel_residual": res,
+                              "solve_s": solve_s, "max_rel_field_error": err})
+        del A
+        torch.cuda.empty_cache()
+    return out
+
+
 def batch_cpu_baseline(views, budget_s, seed=1):
     """The oracle on a seeded sample of a batch's entries (all meshes, operators,
     near field and coupling blocks), sampled in proportion to each mesh's
@@ -1752,7 +1921,7 @@ def run_all(args):
     ctx = pkg.Context(local, stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     peaks = measure_peaks(torch, ctx, stream)
-    bw = synth.workloads.config4()
+    bw = synth.workloads.config4(args.c4_meshes)
     items = shard_items(bw.items, rank, ws) if ws > 1 else bw.items
     barrier = (lambda: torch.distributed.barrier()) if ws > 1 else None
     reduce_ms = (lambda ms: reduce_over_ranks(ms, "max", dev)) if ws > 1 else None
@@ -1796,7 +1965,9 @@ def run_all(args):
                                                     steps_x)),
                         ("C3", lambda: _config_plan(torch, pkg, ctx, dev, stream, flush, args,
                                                     synth.workloads.config3(), steps_x)),
-                        ("C5", lambda: _config_c5(args, steps_x))):
+                        ("C5", lambda: _config_c5(args, steps_x)),
+                        ("H2_solve", lambda: measure_h2_solve(torch, pkg, ctx, dev, stream)),
+                        ("BW_solve", lambda: measure_bw_solve(torch, pkg, ctx, dev, stream))):
             try:
                 configs[key] = fn()
             except Exception as e:      # recorded beside the headline, already measured
@@ -1912,6 +2083,9 @@ def main():
     ap.add_argument("--c5-n", type=int, default=128,
                     help="C5 sphere subdivision (8 n^2 triangles; 128 = the 131072-triangle "
                          "workload, smaller values only for profiling captures)")
+    ap.add_argument("--c4-meshes", type=int, default=48,
+                    help="meshes of the C4 batch (48 = the workload; fewer only for profiling "
+                         "captures)")
     ap.add_argument("--levels", type=int, default=5,
                     help="icosphere refinement levels (5 = the 20480-triangle workload; "
                          "smaller values only for profiling captures)")

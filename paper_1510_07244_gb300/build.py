@@ -17,7 +17,7 @@ LIB = os.path.join(OUT_DIR, "libbem_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["bem_api.cpp", "bem_rules.cpp", "bem_plan.cpp", "bem_touch.cu", "bem_block.cu",
            "bem_block_p1_fp64.cu", "bem_block_p1_mixed.cu", "bem_order.cu", "bem_static.cu",
-           "bem_gca.cpp", "bem_coupling.cu", "bem_mesh_plan.cpp", "bem_green.cu", "bem_guard.cu", "bem_peaks.cu", "bem_h2.cu"]
+           "bem_gca.cpp", "bem_coupling.cu", "bem_mesh_plan.cpp", "bem_green.cu", "bem_guard.cu", "bem_peaks.cu", "bem_h2.cu", "bem_solve.cu"]
 
 
 def nvcc() -> str:

@@ -5,9 +5,9 @@
 // V_t S_ts V_s^T with nested cluster bases: V_t of a leaf is its
 // interpolation matrix, V_t of a cluster with sons is diag(V_t1, V_t2) V^_t
 // (transfer matrix V^_t, rows = the sons' pivots).  y = G x runs as
-//   near     y|t = sum_s N_ts x|s                 one warp per leaf, row per lane
+//   near     y|t = sum_s N_ts x|s                 one CTA per leaf, row per lane
 //   forward  x^_s = V_s^T x|s (leaf) or V^_s^T (x^_s1; x^_s2), deepest level first
-//   coupling y^_t = sum_s S_ts x^_s               one warp per cluster
+//   coupling y^_t = sum_s S_ts x^_s               one CTA per cluster
 //   backward (y^_t1; y^_t2) += V^_t y^_t, y|t += V_t y^_t (leaf), top level first
 // Every output element is written by one lane in a fixed order (no atomics),
 // so products are bitwise reproducible.  All arithmetic is FP64.  The matrix
@@ -77,30 +77,40 @@ struct H2View {
     const double *diag;
 };
 
-// near field: one warp per leaf row cluster, lane i = row i (clusters of at
-// most 32 indices per warp pass)
+// near field: one CTA per leaf row cluster; its 8 warps take every 8th near
+// block, lane i = row i (rows in passes of 32), and the warps' partial sums
+// are added in warp order (fixed, so the result is reproducible)
+constexpr int kH2Warps = 8;
+
 __global__ void __launch_bounds__(256) k_h2_near(H2View H, const int32_t *leaves, int n_leaves,
                                                  const double *__restrict__ x, double *y)
 {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (w >= n_leaves) return;
-    const int t = leaves[w];
+    __shared__ double part[kH2Warps][32];
+    const int t = leaves[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = H.cl_ptr[t], nr = H.cl_ptr[t + 1] - r0;
     for (int i0 = 0; i0 < nr; i0 += 32) {
         const int i = i0 + lane;
         double acc = 0.0;
-        for (int b = H.near_ptr[t]; b < H.near_ptr[t + 1]; ++b) {
-            const int s = H.near_col[b];
-            const int c0 = H.cl_ptr[s], ncl = H.cl_ptr[s + 1] - c0;
-            const double *N = H.near_vals + H.near_off[b];
-            if (i < nr)
-                for (int j = 0; j < ncl; ++j) acc = fma(N[i + (int64_t)j * nr], x[H.cl_idx[c0 + j]], acc);
-        }
-        if (i < nr) {
+        if (i < nr)
+            for (int b = H.near_ptr[t] + warp; b < H.near_ptr[t + 1]; b += kH2Warps) {
+                const int s = H.near_col[b];
+                const int c0 = H.cl_ptr[s], ncl = H.cl_ptr[s + 1] - c0;
+                const double *N = H.near_vals + H.near_off[b] + i;
+#pragma unroll 4
+                for (int j = 0; j < ncl; ++j) acc = fma(N[(int64_t)j * nr], x[H.cl_idx[c0 + j]], acc);
+            }
+        part[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0 && i < nr) {
+            double sum = 0.0;
+#pragma unroll
+            for (int k = 0; k < kH2Warps; ++k) sum += part[k][lane];
             const int gi = H.cl_idx[r0 + i];
-            if (H.diag) acc = fma(H.diag[gi], x[gi], acc);
-            y[gi] = acc;
+            if (H.diag) sum = fma(H.diag[gi], x[gi], sum);
+            y[gi] = sum;
         }
+        __syncthreads();
     }
 }
 
@@ -124,22 +134,34 @@ __global__ void __launch_bounds__(256) k_h2_forward(H2View H, const int32_t *lev
 }
 
 // coupling: y^_t = sum over t's admissible blocks of S_ts x^_s (column-major
-// K_t x K_s); every cluster's y^ is written here, zero without blocks
+// K_t x K_s); one CTA per cluster, its 8 warps over every 8th block, lane =
+// row, partial sums added in warp order; every cluster's y^ is written here,
+// zero without blocks
 __global__ void __launch_bounds__(256) k_h2_coupling(H2View H, int nc, const double *__restrict__ xhat,
                                                      double *yhat)
 {
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (t >= nc) return;
+    __shared__ double part[kH2Warps][32];
+    const int t = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = H.rank[t];
-    if (lane >= K) return;
+    if (K == 0) return;                 // uniform across the CTA
     double acc = 0.0;
-    for (int b = H.far_ptr[t]; b < H.far_ptr[t + 1]; ++b) {
-        const int s = H.far_col[b], Ks = H.rank[s];
-        const double *S = H.far_vals + H.far_off[b];
-        const double *xs = xhat + H.hat_off[s];
-        for (int l = 0; l < Ks; ++l) acc = fma(S[lane + (int64_t)l * K], xs[l], acc);
+    if (lane < K)
+        for (int b = H.far_ptr[t] + warp; b < H.far_ptr[t + 1]; b += kH2Warps) {
+            const int s = H.far_col[b], Ks = H.rank[s];
+            const double *S = H.far_vals + H.far_off[b] + lane;
+            const double *xs = xhat + H.hat_off[s];
+#pragma unroll 4
+            for (int l = 0; l < Ks; ++l) acc = fma(S[(int64_t)l * K], xs[l], acc);
+        }
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && lane < K) {
+        double sum = 0.0;
+#pragma unroll
+        for (int k = 0; k < kH2Warps; ++k) sum += part[k][lane];
+        yhat[H.hat_off[t] + lane] = sum;
     }
-    yhat[H.hat_off[t] + lane] = acc;
 }
 
 // backward transformation of one level: every row i of V_c (lane per row)
@@ -252,13 +274,12 @@ unsigned warps_grid(int64_t warps) { return (unsigned)((warps * 32 + 255) / 256)
 cudaError_t matvec(const bem_h2 *h, const double *x, double *y, cudaStream_t st)
 {
     const H2View H = view(h);
-    if (h->n_leaves > 0)
-        k_h2_near<<<warps_grid(h->n_leaves), 256, 0, st>>>(H, h->leaves, h->n_leaves, x, y);
+    if (h->n_leaves > 0) k_h2_near<<<h->n_leaves, 256, 0, st>>>(H, h->leaves, h->n_leaves, x, y);
     for (int d = (int)h->level.size() - 1; d >= 0; --d)
         if (h->level_n[d] > 0)
             k_h2_forward<<<warps_grid(h->level_n[d]), 256, 0, st>>>(H, h->level[d], h->level_n[d],
                                                                      x, h->xhat);
-    k_h2_coupling<<<warps_grid(h->nc), 256, 0, st>>>(H, h->nc, h->xhat, h->yhat);
+    k_h2_coupling<<<h->nc, 256, 0, st>>>(H, h->nc, h->xhat, h->yhat);
     for (size_t d = 0; d < h->level.size(); ++d)
         if (h->level_n[d] > 0)
             k_h2_backward<<<warps_grid(h->level_n[d]), 256, 0, st>>>(H, h->level[d], h->level_n[d],
