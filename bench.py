@@ -1067,9 +1067,15 @@ def plan_workload(torch, pkg, ctx, dev, stream, name, basis, quad, items, forms,
             for k, (f, pipe, peak) in kernel_flops(v, c, st, precision).items():
                 f0 = model.get(k, (0.0, pipe, peak))[0]
                 model[k] = (f0 + f, pipe, peak)
+            # plans fuse the two Laplace layers of the same P1 blocks in the float
+            # forms: one reciprocal square root per point serves both
+            kinds = sorted(o.kernel for o in v.operators)
+            fused = (precision in ("mixed", "mixed_full") and v.basis == "p1" and
+                     kinds == ["laplace_dlp", "laplace_slp"])
             for k, n in pts.items():
+                ops = v.operators[:1] if (fused and k == "block_p1") else v.operators
                 mufu[k] = mufu.get(k, 0.0) + sum(n * mufu_per_point(o.kernel, k, precision)
-                                                 for o in v.operators)
+                                                 for o in ops)
         per = {}
         for kname, (launches, ms) in prof.items():
             if kname in model:
