@@ -7,7 +7,8 @@
 //  k_block_p0/p1   block engine for near-field, coupling and dense blocks
 //                  (Section 2.3 blocks t x s; Section 3 per-case lists are
 //                  replaced by classifying each pair on the fly): one CTA per
-//                  tile of a block, one thread per disjoint triangle pair
+//                  tile (P1: 32 x 32 of a block; P0: 256 consecutive entries
+//                  of the list), one thread per disjoint triangle pair
 //                  (product rule of a 2D triangle rule, Section 2.2 Duffy),
 //                  touching pairs read from the touching table.
 //  k_pivot         one warp per requested entry g_ij (pivot rows/columns).
@@ -72,15 +73,17 @@ __global__ void __launch_bounds__(1024) k_tile_prefix_batch(BatchJob *jobs, int 
     tile_prefix_cta(J.L, tr, tc, const_cast<int64_t *>(J.prefix), status, job_total + blockIdx.x);
 }
 
-// inclusive scan of the job totals (single CTA)
-__global__ void __launch_bounds__(1024) k_job_scan(const int64_t *job_total, int n, int64_t *job_end)
+// inclusive scan of the job totals in tiles of `unit` (single CTA): the
+// piecewise-constant engine counts entries per job, kP0Tile to a tile
+__global__ void __launch_bounds__(1024) k_job_scan(const int64_t *job_total, int n, int unit,
+                                                   int64_t *job_end)
 {
     __shared__ int64_t part[1024];
     const int chunk = (n + blockDim.x - 1) / blockDim.x;
     const int lo = threadIdx.x * chunk, hi = min(n, lo + chunk);
     int64_t sum = 0;
     for (int k = lo; k < hi; ++k) {
-        sum += job_total[k];
+        sum += (job_total[k] + unit - 1) / unit;
         job_end[k] = sum;
     }
     part[threadIdx.x] = sum;
@@ -95,12 +98,15 @@ __global__ void __launch_bounds__(1024) k_job_scan(const int64_t *job_total, int
     for (int k = lo; k < hi; ++k) job_end[k] += base;
 }
 
+// The float form is capped at 64 registers (four CTAs, 32 warps per SM): the
+// tiles' dependent loads (block, cluster, index, geometry) want the warps.
 template <int KIND, int NP, bool MIXED>
-__global__ void __launch_bounds__(256) k_block_p0(MeshView m, BlockLaunch L, Rule2D R,
+__global__ void __launch_bounds__(256, MIXED ? 4 : 1) k_block_p0(MeshView m, BlockLaunch L, Rule2D R,
                                                   const int64_t *__restrict__ prefix,
                                                   int *status)
 {
-    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
+    // prefix counts entries; a tile is kP0Tile of them
+    const int64_t total = L.n_blocks > 0 ? (prefix[L.n_blocks - 1] + kP0Tile - 1) / kP0Tile : 0;
     for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x)
         p0_tile<KIND, NP, MIXED>(m, L, R, prefix, tile, status);
 }
@@ -113,7 +119,7 @@ __global__ void __launch_bounds__(256) k_block_p0(MeshView m, BlockLaunch L, Rul
 // same tile body as the single-list kernels, so the results are identical.
 // ---------------------------------------------------------------------------
 template <int KIND, int NP, bool MIXED>
-__global__ void __launch_bounds__(256) k_batch_p0(const BatchJob *__restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(256, MIXED ? 4 : 1) k_batch_p0(const BatchJob *__restrict__ jobs, int n_jobs,
                                                   const int64_t *__restrict__ job_end, Rule2D R,
                                                   int *status)
 {
@@ -414,12 +420,13 @@ cudaError_t launch_pivot_entries(const MeshView &m, const int32_t *rows, const i
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_prefix_batch(BatchJob *jobs, int n_jobs, int tr, int tc, int64_t *job_total,
-                                     int64_t *job_end, int *status, cudaStream_t st)
+cudaError_t launch_tile_prefix_batch(BatchJob *jobs, int n_jobs, int tr, int tc, int unit,
+                                     int64_t *job_total, int64_t *job_end, int *status,
+                                     cudaStream_t st)
 {
     if (n_jobs <= 0) return cudaSuccess;
     k_tile_prefix_batch<<<n_jobs, 1024, 0, st>>>(jobs, tr, tc, job_total, status);
-    k_job_scan<<<1, 1024, 0, st>>>(job_total, n_jobs, job_end);
+    k_job_scan<<<1, 1024, 0, st>>>(job_total, n_jobs, unit, job_end);
     return cudaGetLastError();
 }
 

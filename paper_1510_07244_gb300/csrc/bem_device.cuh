@@ -294,9 +294,11 @@ __device__ __forceinline__ float kvalf_r(float dx, float dy, float dz)
 // Helmholtz in the mixed form.  exp(i kappa r) = exp(i kappa r0) exp(i kappa
 // (r - r0)) with r0 = the distance of the two centroids: r0, kappa r0 and its
 // reduction modulo 2 pi are formed in double-float arithmetic once per pair;
-// per point only the small offset r - r0 = ((2 d_c + e) . e) / (r + r0), with
-// e = (x - x_c) - (y - y_c) from centroid-relative offsets, is evaluated in
-// float, so the phase keeps ~1e-7 absolute accuracy for kappa r of order 10^2.
+// per point only the small offset r - r0 (from q = (2 d_c + e) . e, with
+// e = (x - x_c) - (y - y_c) from centroid-relative offsets, see helm_offset)
+// is evaluated in float, so the phase keeps ~1e-7 absolute accuracy for
+// kappa r of order 10^2.  The sums run over exp(i kappa (r - r0)) / r and are
+// rotated by exp(i kappa r0) once per pair.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void dd_add(float ah, float al, float bh, float bl, float &h, float &l)
 {
@@ -318,7 +320,9 @@ __device__ __forceinline__ void dd_mul(float ah, float al, float bh, float bl, f
 // phase data of a pair: cos/sin of kappa r0 and the float quantities per point
 struct HelmPhase {
     float dcx, dcy, dcz;   // centroid difference d_c (float)
-    float r0, r0sq;        // r0 and r0^2 (float)
+    float r0h, r0l;        // r0 as an unevaluated hi + lo pair
+    float r0sqh, r0sql;    // r0^2 as an unevaluated hi + lo pair
+    float m2r0l;           // -2 r0l
     float c0, s0;          // cos, sin of kappa r0
     float kap;
 };
@@ -369,25 +373,46 @@ __device__ __forceinline__ HelmPhase helm_phase(const TriF &A, const TriF &B, do
     P.dcx = dh[0] + dl[0];
     P.dcy = dh[1] + dl[1];
     P.dcz = dh[2] + dl[2];
-    P.r0 = r0h + r0l;
-    P.r0sq = sh + sl;
+    P.r0h = r0h;
+    P.r0l = r0l;
+    P.m2r0l = -2.0f * r0l;
+    P.r0sqh = sh;
+    P.r0sql = sl;
     P.kap = kh;
     return P;
 }
 
-// exp(i kappa r) / r (times nothing else) at offset e = d - d_c
-__device__ __forceinline__ void helm_value(const HelmPhase &P, float ex, float ey, float ez,
-                                           float &re, float &im)
+// At the offset e = d - d_c: cos and sin of kappa (r - r0), and 1/r.  The
+// factor exp(i kappa r0) is common to every point of the pair and is applied
+// to the pair's sum by helm_rotate.
+//
+// r - r0 without a division: q = r^2 - r0^2 = (2 d_c + e) . e is formed in
+// float (accurate relative to q, not to r^2); r_a = r2 / sqrt(r2) from the
+// rounded r2 = r0^2 + q carries the roundings of r2 and of the reciprocal
+// square root, and the residual r^2 - r_a^2 = (r0sq_hi - r_a^2) + (r0sq_lo + q)
+// (one FMA) corrects it to first order, r = r_a + res / (2 r_a).  r_a - r0_hi
+// is exact while r_a is within a factor 2 of r0, so r - r0 keeps an error of
+// a few float ulps of itself plus that of q.  Three special-function
+// operations per point (rsqrt, sin, cos).
+__device__ __forceinline__ void helm_offset(const HelmPhase &P, float ex, float ey, float ez,
+                                            float &c, float &s, float &ri)
 {
     const float q = fmaf(fmaf(2.0f, P.dcx, ex), ex,
                          fmaf(fmaf(2.0f, P.dcy, ey), ey, fmaf(2.0f, P.dcz, ez) * ez));
-    const float r2 = P.r0sq + q;
-    const float ri = rsqrt_fast(r2);
-    const float delta = __fdividef(q, fmaf(r2, ri, P.r0));
-    float s, c;
+    const float r2 = P.r0sqh + q;
+    ri = rsqrt_fast(r2);
+    const float ra = r2 * ri;
+    const float res = fmaf(-ra, ra, P.r0sqh) + (q + P.r0sql);
+    const float delta = fmaf(0.5f, fmaf(res, ri, P.m2r0l), ra - P.r0h);
     __sincosf(P.kap * delta, &s, &c);
-    re = (P.c0 * c - P.s0 * s) * ri;
-    im = (P.s0 * c + P.c0 * s) * ri;
+}
+
+// (re, im) = exp(i kappa r0) (sr + i si)
+__device__ __forceinline__ void helm_rotate(const HelmPhase &P, float sr, float si, float &re,
+                                            float &im)
+{
+    re = P.c0 * sr - P.s0 * si;
+    im = P.s0 * sr + P.c0 * si;
 }
 
 // Regular pair, piecewise constant, Helmholtz single layer, float.
@@ -414,10 +439,11 @@ __device__ __forceinline__ void regular_p0_f32_helm(const TriF &A, const TriF &B
         float ir = 0.0f, ii = 0.0f;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            float kr, ki;
-            helm_value(P, xx - yx[j], xy - yy[j], xz - yz[j], kr, ki);
-            ir = fmaf(R.wf[j], kr, ir);
-            ii = fmaf(R.wf[j], ki, ii);
+            float c, s, ri;
+            helm_offset(P, xx - yx[j], xy - yy[j], xz - yz[j], c, s, ri);
+            const float wr = R.wf[j] * ri;
+            ir = fmaf(c, wr, ir);
+            ii = fmaf(s, wr, ii);
         }
         // compensated outer sums
         float y = fmaf(R.wf[i], ir, -cr), t = sr + y;
@@ -428,17 +454,20 @@ __device__ __forceinline__ void regular_p0_f32_helm(const TriF &A, const TriF &B
         ci = (t - si) - y;
         si = t;
     };
-    // larger rules keep the outer loop rolled (code size)
-    if (NP > 9) {
+    // the outer loop stays rolled from 9 points on: the unrolled body of
+    // 81 points overflows the instruction cache
+    if (NP >= 9) {
 #pragma unroll 1
         for (int i = 0; i < NP; ++i) outer(i);
     } else {
 #pragma unroll
         for (int i = 0; i < NP; ++i) outer(i);
     }
+    float re, im;
+    helm_rotate(P, sr, si, re, im);
     const float sc = A.sg * B.sg * (float)kInv4Pi;
-    out_re = sr * sc;
-    out_im = si * sc;
+    out_re = re * sc;
+    out_im = im * sc;
 }
 
 // Regular pair, piecewise constant, float (Laplace kernels).  With ABS the
@@ -1149,71 +1178,100 @@ __device__ __forceinline__ BlockInfo block_info(const BlockLaunch &L, const int6
 }
 
 // ---------------------------------------------------------------------------
-// Block engine, piecewise constant: tile = 32 rows x 8 columns, one thread per entry.
+// Block engine, piecewise constant.  The entries of a block list are numbered
+// block after block, each block column-major (rows fastest, the order of its
+// output); a tile is kP0Tile consecutive entries, one thread each, and may
+// span several blocks, so that small blocks (coupling blocks of a few pivots,
+// leaves of a few triangles) leave no lane idle.  prefix[b] = entries of
+// blocks 0..b (inclusive).
 // ---------------------------------------------------------------------------
-constexpr int kP0Cols = 8;
-
-// One tile (32 rows x 8 columns) of one block list; `tile` indexes the list's tiles.
+// One tile of one block list; `tile` indexes the list's tiles (called by
+// every thread of the CTA with the same `tile`; the warps run independently).
 template <int KIND, int NP, bool MIXED>
 __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
                                         const int64_t *__restrict__ prefix, int64_t tile,
                                         int *status)
 {
-    const int lr = threadIdx.x & 31, lc = threadIdx.x >> 5;
-    {
-        const BlockInfo bi = block_info(L, prefix, tile, status);
-        if (!bi.ok) return;
-        const int ntr = (bi.nr + kTile - 1) / kTile;
-        const int r = (bi.tile_in_blk % ntr) * kTile + lr;
-        const int c = (bi.tile_in_blk / ntr) * kP0Cols + lc;
-        if (r >= bi.nr || c >= bi.nc) return;
-        const int a = L.row_idx[bi.r_lo + r], b = L.col_idx[bi.c_lo + c];
-        if (a < 0 || a >= m.nt || b < 0 || b >= m.nt) {
+    static_assert(kP0Tile == 256, "one thread per entry of a tile");
+    // Each warp finds the blocks of its 32 entries by itself (no CTA barrier):
+    // one search for the block of its first entry, then the inclusive sums of
+    // the 32 blocks from there, one per lane; an entry's block is the first
+    // of them whose sum exceeds it (a ballot), unless more than 32 of the
+    // blocks are empty.
+    const int lane = threadIdx.x & 31;
+    const int64_t ew = tile * kP0Tile + (threadIdx.x & ~31);
+    const int64_t total = prefix[L.n_blocks - 1];
+    if (ew >= total) return;   // the whole warp
+    const int64_t e = ew + lane;
+    const int64_t b0 = find_block(prefix, L.n_blocks, ew);
+    const int64_t pw = b0 + lane < L.n_blocks ? prefix[b0 + lane] : INT64_MAX;
+    const int64_t p_before = b0 > 0 ? prefix[b0 - 1] : 0;
+    const int k = __popc(__ballot_sync(0xffffffffu, pw <= e));
+    const int64_t p_prev = __shfl_sync(0xffffffffu, pw, k > 0 ? k - 1 : 0);
+    int64_t b, before;
+    if (k < 32) {
+        b = b0 + k;
+        before = k > 0 ? p_prev : p_before;
+    } else {
+        b = find_block(prefix, L.n_blocks, e);
+        before = b > 0 ? prefix[b - 1] : 0;
+    }
+    if (e >= total) return;
+    const int t = L.blk_row[b], s = L.blk_col[b];
+    if (t < 0 || t >= L.n_row_clusters || s < 0 || s >= L.n_col_clusters) {
+        set_status(status, BEM_ERR_INVALID_ARG);
+        return;
+    }
+    const int r_lo = L.row_ptr[t], nr = L.row_ptr[t + 1] - r_lo;
+    const int c_lo = L.col_ptr[s];
+    const int64_t le = e - before;          // 0 <= le < nr * nc
+    const int c = (int)(le / nr), r = (int)(le - (int64_t)c * nr);
+    const int a = L.row_idx[r_lo + r], bb = L.col_idx[c_lo + c];
+    if (a < 0 || a >= m.nt || bb < 0 || bb >= m.nt) {
+        set_status(status, BEM_ERR_INVALID_ARG);
+        return;
+    }
+    if (L.lower_only && a < bb) return;
+    double re, im;
+    float absum = 0.0f;   // guarded double layer: sum of |terms|
+    const bool guard = MIXED && KIND == BEM_LAPLACE_DLP && L.guard;
+    const int4 va = __ldg(m.tvid + a), vb = __ldg(m.tvid + bb);
+    if (touching(va, vb)) {
+        const int k = L.allow_touching ? find_touching(m, a, bb) : -1;
+        if (k < 0) {
             set_status(status, BEM_ERR_INVALID_ARG);
             return;
         }
-        if (L.lower_only && a < b) return;
-        double re, im;
-        float absum = 0.0f;   // guarded double layer: sum of |terms|
-        const bool guard = MIXED && KIND == BEM_LAPLACE_DLP && L.guard;
-        const int4 va = __ldg(m.tvid + a), vb = __ldg(m.tvid + b);
-        if (touching(va, vb)) {
-            const int k = L.allow_touching ? find_touching(m, a, b) : -1;
-            if (k < 0) {
-                set_status(status, BEM_ERR_INVALID_ARG);
-                return;
-            }
-            const double2 v = m.table[k];
-            re = v.x;
-            im = v.y;     // the double layer's float touching kernels put A here
-            if (guard) absum = (float)v.y;
-        } else if (MIXED) {
-            TriF A, B;
-            load_trif(m.geomf, a, A);
-            load_trif(m.geomf, b, B);
-            if (KIND == BEM_HELMHOLTZ_SLP) {
-                float fr, fi;
-                regular_p0_f32_helm<NP>(A, B, R, L.kappa, fr, fi);
-                re = (double)fr;
-                im = (double)fi;
-            } else if (guard) {
-                re = (double)regular_p0_f32<BEM_LAPLACE_DLP, NP, true>(A, B, R, &absum);
-                im = 0.0;
-            } else {
-                re = (double)regular_p0_f32<KIND, NP>(A, B, R);
-                im = 0.0;
-            }
+        const double2 v = m.table[k];
+        re = v.x;
+        im = v.y;     // the double layer's float touching kernels put A here
+        if (guard) absum = (float)v.y;
+    } else if (MIXED) {
+        TriF A, B;
+        load_trif(m.geomf, a, A);
+        load_trif(m.geomf, bb, B);
+        if (KIND == BEM_HELMHOLTZ_SLP) {
+            float fr, fi;
+            regular_p0_f32_helm<NP>(A, B, R, L.kappa, fr, fi);
+            re = (double)fr;
+            im = (double)fi;
+        } else if (guard) {
+            re = (double)regular_p0_f32<BEM_LAPLACE_DLP, NP, true>(A, B, R, &absum);
+            im = 0.0;
         } else {
-            Tri A, B;
-            load_tri(m.geom, a, A);
-            load_tri(m.geom, b, B);
-            regular_p0<KIND, NP>(A, B, R, L.kappa, re, im, L.eta);
+            re = (double)regular_p0_f32<KIND, NP>(A, B, R);
+            im = 0.0;
         }
-        const int64_t o = bi.off + (int64_t)r + (int64_t)c * bi.nr;
-        if (kind_complex(KIND)) reinterpret_cast<double2 *>(L.out)[o] = make_double2(re, im);
-        else if (guard) reinterpret_cast<float2 *>(L.out)[o] = make_float2((float)re, absum);
-        else reinterpret_cast<double *>(L.out)[o] = re;
+    } else {
+        Tri A, B;
+        load_tri(m.geom, a, A);
+        load_tri(m.geom, bb, B);
+        regular_p0<KIND, NP>(A, B, R, L.kappa, re, im, L.eta);
     }
+    const int64_t o = L.blk_off[b] + le;
+    if (kind_complex(KIND)) reinterpret_cast<double2 *>(L.out)[o] = make_double2(re, im);
+    else if (guard) reinterpret_cast<float2 *>(L.out)[o] = make_float2((float)re, absum);
+    else reinterpret_cast<double *>(L.out)[o] = re;
 }
 
 // ---------------------------------------------------------------------------

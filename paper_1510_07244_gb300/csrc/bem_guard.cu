@@ -75,26 +75,39 @@ __device__ __forceinline__ GBlock guard_block(const GuardJob *jobs, const int64_
     return g;
 }
 
+// One warp per block (blocks hold a few hundred entries, so a CTA per block
+// would leave the passes waiting on each block's index loads): lanes take
+// the block's rows, the maximum over the row's columns goes out with one
+// atomic per (block, row).
 __global__ void __launch_bounds__(256) k_guard_rowmax(const GuardJob *__restrict__ jobs,
                                                       const int64_t *__restrict__ blk_end,
                                                       int n_jobs)
 {
     const int64_t nb = blk_end[n_jobs - 1];
-    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nw) {
         const GBlock g = guard_block(jobs, blk_end, n_jobs, b);
         if (!g.ok) continue;
         const GuardJob &G = jobs[g.job];
         const float2 *o = reinterpret_cast<const float2 *>(G.L.out) + g.off;
-        const int n = g.nr * g.nc;
-        for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            const int row = G.L.row_idx[g.r_lo + e % g.nr];
-            if (row < 0 || row >= G.n_rows) continue;
+        for (int r = lane; r < g.nr; r += 32) {
+            const int row = G.L.row_idx[g.r_lo + r];
+            float m0 = 0.0f, m1 = 0.0f;
+            int c = 0;
+            for (; c + 1 < g.nc; c += 2) {
+                m0 = fmaxf(m0, fabsf(o[r + (int64_t)c * g.nr].x));
+                m1 = fmaxf(m1, fabsf(o[r + (int64_t)(c + 1) * g.nr].x));
+            }
+            if (c < g.nc) m0 = fmaxf(m0, fabsf(o[r + (int64_t)c * g.nr].x));
             // |value| >= 0, so its bit pattern orders like the value
-            atomicMax(G.rowmax + row, __float_as_uint(fabsf(o[e].x)));
+            if (row >= 0 && row < G.n_rows)
+                atomicMax(G.rowmax + row, __float_as_uint(fmaxf(m0, m1)));
         }
     }
 }
 
+// One warp per block, lanes over its entries (column-major, coalesced).
 __global__ void __launch_bounds__(256) k_guard_select(const GuardJob *__restrict__ jobs,
                                                       const int64_t *__restrict__ blk_end,
                                                       int n_jobs, GuardItem *list,
@@ -106,31 +119,33 @@ __global__ void __launch_bounds__(256) k_guard_select(const GuardJob *__restrict
     // list_t (count[1], capacity cap_t: every touching pair of the jobs)
     const int64_t nb = blk_end[n_jobs - 1];
     const int lane = threadIdx.x & 31;
-    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nw) {
         const GBlock g = guard_block(jobs, blk_end, n_jobs, b);
-        if (!g.ok) continue;
+        if (!g.ok) continue;   // uniform across the warp
         const GuardJob &G = jobs[g.job];
         float2 *o2 = reinterpret_cast<float2 *>(G.L.out) + g.off;
         double *od = reinterpret_cast<double *>(G.L.out) + g.off;
         const int n = g.nr * g.nc;
-        // whole warps iterate together, so the ballot below sees every lane
-        const int n_up = (n + 31) & ~31;
-        for (int e = threadIdx.x; e < n_up; e += blockDim.x) {
+        // the whole warp iterates together, so the ballot below sees every lane
+        for (int e0 = 0; e0 < n; e0 += 32) {
+            const int e = e0 + lane;
             bool redo = false;
             int row = 0, col = 0;
             if (e < n) {
                 const float2 v = o2[e];
-                row = G.L.row_idx[g.r_lo + e % g.nr];
-                col = G.L.col_idx[g.c_lo + e / g.nr];
+                const int c = e / g.nr;
+                row = G.L.row_idx[g.r_lo + e - c * g.nr];
+                col = G.L.col_idx[g.c_lo + c];
                 float rmax = 0.0f;
                 if (row >= 0 && row < G.n_rows) rmax = __uint_as_float(G.rowmax[row]);
                 const float scale = fmaxf(fabsf(v.x), kRowFloor * rmax);
                 redo = rel * v.y > kRelBound * scale;
                 // entries kept in float are widened in place; the listed ones
-                // keep the pair until the FP64 pass overwrites them
+                // keep the pair until the recomputation overwrites them
                 if (!redo) od[e] = (double)v.x;
             }
-            // touching pairs (shared vertex index) go to the FP64 list
+            // touching pairs (shared vertex index) go to their own list
             bool touch = false;
             if (redo) touch = touching(__ldg(G.m.tvid + row), __ldg(G.m.tvid + col));
             for (int side = 0; side < 2; ++side) {

@@ -22,6 +22,8 @@ constexpr int kGeomFStride = 32;     // floats per triangle record of the mixed 
 //         (FP64 differences rounded once) | n hi[3] | n lo[3] | sqrt_g | pad
 constexpr int kMaxDegP1 = 16;        // vertex degree bound of the P1 block engine
 constexpr int kTile = 32;            // rows / columns of one block tile
+constexpr int kP0Tile = 256;         // entries of one piecewise-constant tile (one per thread)
+constexpr int kP0Cols = 8;           // columns of a learned-order tile (32 rows x 8 columns)
 constexpr int kMaxNp = 25;           // points of a 2D regular rule (Duffy q <= 5)
 
 enum Case { kRegular = 0, kVertex = 1, kEdge = 2, kIdentical = 3 };
@@ -325,11 +327,26 @@ cudaError_t launch_p1_batch_fp64(int kind, int np, const BatchJob *jobs, int n_j
 cudaError_t launch_p1_batch_mixed(int kind, int np, const BatchJob *jobs, int n_jobs,
                                   const int64_t *job_end, const Rule2D &R, int *status, int grid,
                                   cudaStream_t st);
-cudaError_t launch_tile_prefix_batch(BatchJob *jobs, int n_jobs, int tr, int tc, int64_t *job_total,
-                                     int64_t *job_end, int *status, cudaStream_t st);
+// Per-job block prefix sums of tiles tr x tc (tr = tc = 1: entries) and the
+// inclusive scan of the job totals in units of `unit` per tile.
+cudaError_t launch_tile_prefix_batch(BatchJob *jobs, int n_jobs, int tr, int tc, int unit,
+                                     int64_t *job_total, int64_t *job_end, int *status,
+                                     cudaStream_t st);
 // bem_coupling.cu: coupling blocks of the piecewise-linear basis, mixed form
 // (Laplace kernels), one entry per lane in warp tiles of 16 rows x 2 columns.
 constexpr int kCouplingRows = 16, kCouplingCols = 2;
+// Tile shape of the block engines: rows x columns per tile for the prefix
+// sums, and prefix units per tile (the piecewise-constant engine counts
+// entries and takes kP0Tile consecutive ones per tile).
+struct TileShape {
+    int tr, tc, unit;
+};
+inline TileShape block_tile_shape(int basis, bool coupling)
+{
+    if (coupling) return {kCouplingRows, kCouplingCols, 1};
+    if (basis == BEM_P0) return {1, 1, kP0Tile};
+    return {kTile, kTile, 1};
+}
 bool use_coupling_engine(int basis, int kind, int mixed, int allow_touching);
 cudaError_t launch_coupling_p1(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
                                const int64_t *prefix, int *status, int grid, cudaStream_t st);

@@ -420,7 +420,7 @@ __device__ __forceinline__ void select_entry(const MeshView &m, const BlockLaunc
     const int lr = threadIdx.x & 31, lc = threadIdx.x >> 5;
     const int ntr = (bi.nr + kTile - 1) / kTile;
     const int r = (bi.tile_in_blk % ntr) * kTile + lr;
-    const int c = (bi.tile_in_blk / ntr) * 8 + lc;
+    const int c = (bi.tile_in_blk / ntr) * kP0Cols + lc;
     if (r >= bi.nr || c >= bi.nc) return;
     a = L.row_idx[bi.r_lo + r];
     b = L.col_idx[bi.c_lo + c];
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(256) k_learned_compact(MeshView m, BlockLaunch
         const int lr = threadIdx.x & 31, lc = threadIdx.x >> 5;
         const int ntr = (bi.nr + kTile - 1) / kTile;
         const int r = (bi.tile_in_blk % ntr) * kTile + lr;
-        const int c = (bi.tile_in_blk / ntr) * 8 + lc;
+        const int c = (bi.tile_in_blk / ntr) * kP0Cols + lc;
         // slots within the class: one atomic per class and warp, lanes in order
 #pragma unroll
         for (int cc = 0; cc < kClasses; ++cc) {
@@ -661,10 +661,11 @@ __global__ void __launch_bounds__(256) k_learned_eval_big(MeshView m, const int4
 #pragma unroll
                 for (int j = 0; j < CH; ++j) {
                     if (CPLX) {
-                        float kr, ki;
-                        helm_value(P, xx - yx[j], xy - yy[j], xz - yz[j], kr, ki);
-                        ir = fmaf(R.w[jc + j], kr, ir);
-                        ii = fmaf(R.w[jc + j], ki, ii);
+                        float c, s, ri;
+                        helm_offset(P, xx - yx[j], xy - yy[j], xz - yz[j], c, s, ri);
+                        const float wr = R.w[jc + j] * ri;
+                        ir = fmaf(c, wr, ir);
+                        ii = fmaf(s, wr, ii);
                     } else {
                         ir = fmaf(R.w[jc + j], kvalf_r<KIND>(xx - yx[j], xy - yy[j], xz - yz[j]), ir);
                     }
@@ -683,9 +684,11 @@ __global__ void __launch_bounds__(256) k_learned_eval_big(MeshView m, const int4
             }
         }
         const float sc = A.sg * B.sg * (float)kInv4Pi;
-        if (CPLX)
-            reinterpret_cast<double2 *>(out)[pos] = make_double2((double)(sr * sc), (double)(si * sc));
-        else
+        if (CPLX) {
+            float re, im;
+            helm_rotate(P, sr, si, re, im);
+            reinterpret_cast<double2 *>(out)[pos] = make_double2((double)(re * sc), (double)(im * sc));
+        } else
             reinterpret_cast<double *>(out)[pos] = (double)(sr * sc);
     }
 }
@@ -775,12 +778,12 @@ __global__ void __launch_bounds__(256) k_learned_eval(MeshView m, const int4 *__
                     // centroid-relative offsets (see helm_phase)
                     const float ax = x1 - 0.666666687f, at = x2 - 0.333333343f;
                     const float bx = y1 - 0.666666687f, bt = y2 - 0.333333343f;
-                    float kr, ki;
-                    helm_value(P, fmaf(ax, A.e1[0], at * A.e2[0]) - fmaf(bx, B.e1[0], bt * B.e2[0]),
-                               fmaf(ax, A.e1[1], at * A.e2[1]) - fmaf(bx, B.e1[1], bt * B.e2[1]),
-                               fmaf(ax, A.e1[2], at * A.e2[2]) - fmaf(bx, B.e1[2], bt * B.e2[2]), kr, ki);
-                    acc = fmaf(w, kr, acc);
-                    acci = fmaf(w, ki, acci);
+                    float c, s, ri;
+                    helm_offset(P, fmaf(ax, A.e1[0], at * A.e2[0]) - fmaf(bx, B.e1[0], bt * B.e2[0]),
+                                fmaf(ax, A.e1[1], at * A.e2[1]) - fmaf(bx, B.e1[1], bt * B.e2[1]),
+                                fmaf(ax, A.e1[2], at * A.e2[2]) - fmaf(bx, B.e1[2], bt * B.e2[2]), c, s, ri);
+                    acc = fmaf(c, w * ri, acc);
+                    acci = fmaf(s, w * ri, acci);
                 } else {
                     const float dx = fmaf(x1, A.e1[0], fmaf(x2, A.e2[0], d0[0])) - fmaf(y1, B.e1[0], y2 * B.e2[0]);
                     const float dy = fmaf(x1, A.e1[1], fmaf(x2, A.e2[1], d0[1])) - fmaf(y1, B.e1[1], y2 * B.e2[1]);
@@ -790,7 +793,13 @@ __global__ void __launch_bounds__(256) k_learned_eval(MeshView m, const int4 *__
                 }
             }
             acc = warp_sumf(acc);
-            if (KIND == BEM_HELMHOLTZ_SLP) acci = warp_sumf(acci);
+            if (KIND == BEM_HELMHOLTZ_SLP) {
+                acci = warp_sumf(acci);
+                float re, im;
+                helm_rotate(P, acc, acci, re, im);
+                acc = re;
+                acci = im;
+            }
             const double sc = (double)A.sg * (double)B.sg * kInv4Pi;
             sr = (double)acc * sc;
             si = (double)acci * sc;

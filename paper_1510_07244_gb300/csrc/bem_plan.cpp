@@ -159,8 +159,12 @@ cudaError_t plan_support(bem_plan *p, const MeshView &m, const int32_t *ptr, con
     return cudaSuccess;
 }
 
-int tile_rows(const BlockBucket &b) { return b.coupling ? kCouplingRows : kTile; }
-int tile_cols(const BlockBucket &b) { return b.coupling ? kCouplingCols : (b.basis == BEM_P0 ? 8 : kTile); }
+cudaError_t bucket_prefix(bem_ctx *ctx, const BlockBucket &b, cudaStream_t st)
+{
+    const TileShape ts = block_tile_shape(b.basis, b.coupling);
+    return launch_tile_prefix_batch(b.jobs, (int)b.host_jobs.size(), ts.tr, ts.tc, ts.unit,
+                                    b.job_total, b.job_end, ctx->status, st);
+}
 
 cudaError_t launch_bucket(bem_ctx *ctx, const BlockBucket &b, int mult, cudaStream_t st)
 {
@@ -211,8 +215,7 @@ cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
     }
     for (auto &b : p->bb) {
         ev_begin();
-        e = launch_tile_prefix_batch(b.jobs, (int)b.host_jobs.size(), tile_rows(b), tile_cols(b),
-                                     b.job_total, b.job_end, ctx->status, st);
+        e = bucket_prefix(ctx, b, st);
         ev_end();
         if (e != cudaSuccess) return e;
     }
@@ -224,7 +227,7 @@ cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
     }
     for (auto &l : p->learned) {
         ev_begin();
-        e = launch_tile_prefix(l.L, kTile, 8, l.prefix, ctx->status, st);
+        e = launch_tile_prefix(l.L, kTile, kP0Cols, l.prefix, ctx->status, st);
         if (e == cudaSuccess)
             e = learned_launches(l.m, l.L, l.prefix, p->model, p->conf, l.S, p->lrules, l.precision,
                                  ctx->num_sms, ctx->status, st, nullptr);
@@ -253,8 +256,7 @@ int autotune(bem_ctx *ctx, bem_plan *p)
         launch_build_supports(s.m, s.ptr, s.idx, s.n, s.slice, s.sup, s.cap, ctx->status,
                               ctx->num_sms * 4, st);
     for (auto &bk : p->bb)
-        launch_tile_prefix_batch(bk.jobs, (int)bk.host_jobs.size(), tile_rows(bk), tile_cols(bk),
-                                 bk.job_total, bk.job_end, ctx->status, st);
+        bucket_prefix(ctx, bk, st);
     cudaError_t e = cudaStreamSynchronize(st);
     for (auto &bk : p->bb) {
         if (e != cudaSuccess) break;
@@ -478,7 +480,7 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
             // the tile count sizes the job's scratch: one prefix pass now
             int64_t tiles = 0;
             if ((e = plan_alloc(p, &l.prefix, (size_t)J.n_blocks)) != cudaSuccess ||
-                (e = launch_tile_prefix(L, kTile, 8, l.prefix, ctx->status, p->cap)) != cudaSuccess ||
+                (e = launch_tile_prefix(L, kTile, kP0Cols, l.prefix, ctx->status, p->cap)) != cudaSuccess ||
                 (e = cudaMemcpyAsync(&tiles, l.prefix + (J.n_blocks - 1), sizeof(int64_t),
                                      cudaMemcpyDeviceToHost, p->cap)) != cudaSuccess ||
                 (e = cudaStreamSynchronize(p->cap)) != cudaSuccess ||

@@ -164,8 +164,8 @@ extern "C" int bem_near_field_noalloc(bem_ctx *ctx, const bem_block_job *job)
     L.lower_only = 0;
     L.allow_touching = 1;
     L.mixed = 0;
-    const int tc = m->v.basis == BEM_P0 ? 8 : kTile;
-    e = launch_tile_prefix(L, kTile, tc, prefix, ctx->status, ctx->stream);
+    const TileShape ts = block_tile_shape(m->v.basis, false);
+    e = launch_tile_prefix(L, ts.tr, ts.tc, prefix, ctx->status, ctx->stream);
     if (e == cudaSuccess)
         e = launch_block_engine(m->v, L, r2, prefix, ctx->status,
                                 ctx->num_sms * (m->v.basis == BEM_P0 ? 8 : 2), ctx->stream);
