@@ -91,6 +91,38 @@ def flops_per_point_ss(case: str, kernel: str, basis: str) -> float:
     return f
 
 
+def touch_rule_xi(kernel: str, basis: str, q: int, f32: bool) -> bool:
+    """Whether the library evaluates a touching case with xi integrated out
+    (bem_rule_points_xi): the Laplace kernels where the q-point Gauss rule in
+    xi is exact for the integrand's degree in xi, the float Helmholtz single
+    layer with its xi sums."""
+    if kernel == "helmholtz_slp":
+        return f32 and q <= 20
+    if kernel not in ("laplace_slp", "laplace_dlp"):
+        return False
+    deg = (2 if kernel == "laplace_slp" else 1) + (2 if basis == "p1" else 0)
+    return 2 * q - 1 >= deg
+
+
+def touch_cost(case: str, kernel: str, basis: str, q: int, f32: bool):
+    """(evaluation points per touching pair, algorithmic flops per point).
+    With xi integrated out the points are the q^3 per subdomain at xi = 1;
+    the float Helmholtz single layer then costs, per point, the distance part
+    once (difference, r^2 5, rsqrt 1, kappa |u| 2, weight 1, accumulation 2),
+    per node pair a sine/cosine (2) and two FMAs per moment power, and the
+    middle node and the rotation by exp(i th / 2) (sincos 2, 8 per power)."""
+    nsub = {"vertex": 2, "edge": 4, "identical": 6}[case]
+    xi = touch_rule_xi(kernel, basis, q, f32)
+    pts = nsub * q ** (3 if xi else 4)
+    f = flops_per_point_ss(case, kernel, basis)
+    if xi and kernel == "helmholtz_slp":
+        mm = 3 if basis == "p1" else 1
+        geo = {"identical": 9.0, "edge": 15.0, "vertex": 21.0}[case]
+        f = (geo + 11.0 + (q // 2) * (2.0 + 4.0 * mm) + 2.0 + 8.0 * mm +
+             (20.0 if basis == "p1" else 0.0))
+    return pts, f
+
+
 PEAK_FP64 = 152 * 2.07e9 * 4.0 / 1e12     # TFLOP/s: 152 SM x 2 FMA/clk x 2.07 GHz
 PEAK_FP32 = 152 * 2.07e9 * 256.0 / 1e12   # TFLOP/s: 152 SM x 128 FMA/clk x 2.07 GHz
 # the denominators of the rooflines: the measured rates once measure_peaks has
@@ -174,14 +206,15 @@ def kernel_flops(w, counts, stats, precision):
     if fused:
         f_blk -= reg * npts_reg * 9.0
     out["block_p1" if w.basis == "p1" else "block_p0"] = (f_blk, pipe)
-    for cas, nsub, qq, key in (("touching_vertex", 2, q.q_vertex, "n_vertex"),
-                               ("touching_edge", 4, q.q_edge, "n_edge"),
-                               ("touching_identical", 6, q.q_identical, "n_identical")):
-        f = sum(stats[key] * nsub * qq ** 4 * flops_per_point_ss(cas.split("_")[1], o.kernel, w.basis)
-                for o in w.operators)
+    for cas, qq, key in (("touching_vertex", q.q_vertex, "n_vertex"),
+                         ("touching_edge", q.q_edge, "n_edge"),
+                         ("touching_identical", q.q_identical, "n_identical")):
         f32 = precision == "mixed_full" or (mixed and cas == "touching_vertex")
-        p = "fp32" if f32 else "fp64"
-        out[cas] = (f, p)
+        f = 0.0
+        for o in w.operators:
+            pts, fpp = touch_cost(cas.split("_")[1], o.kernel, w.basis, qq, f32)
+            f += stats[key] * pts * fpp
+        out[cas] = (f, "fp32" if f32 else "fp64")
     return {k: (f, p, PEAKS[p]) for k, (f, p) in out.items()}
 
 
@@ -956,22 +989,26 @@ def run_extra(args):
 def mufu_per_point(kernel: str, kclass: str, precision: str) -> float:
     if precision == "fp64":
         return 1.0
+    # the float Helmholtz pair: reciprocal square root, sine and cosine
     if kernel == "helmholtz_slp" and kclass.startswith("block"):
-        return 4.0
+        return 3.0
     return 1.0
 
 
-def kernel_points(v, counts, stats):
-    """{kernel class: quadrature points per step per operator} of one view."""
+def kernel_points(v, counts, stats, kernel, precision):
+    """{kernel class: evaluation points per step} of one view and operator
+    (touching cases as touch_cost counts them)."""
     q = v.quad
     npts = (q.q_regular ** 2) ** 2 if q.regular_rule == "duffy" else 49
+    mixed = precision in ("mixed", "mixed_full")
     out = {}
     reg = counts["near_regular_pairs"] + counts["far_regular_pairs"]
     out["block_p1" if v.basis == "p1" else "block_p0"] = reg * npts
-    for cas, nsub, qq, key in (("touching_vertex", 2, q.q_vertex, "n_vertex"),
-                               ("touching_edge", 4, q.q_edge, "n_edge"),
-                               ("touching_identical", 6, q.q_identical, "n_identical")):
-        out[cas] = stats[key] * nsub * qq ** 4
+    for cas, qq, key in (("touching_vertex", q.q_vertex, "n_vertex"),
+                         ("touching_edge", q.q_edge, "n_edge"),
+                         ("touching_identical", q.q_identical, "n_identical")):
+        f32 = precision == "mixed_full" or (mixed and cas == "touching_vertex")
+        out[cas] = stats[key] * touch_cost(cas.split("_")[1], kernel, v.basis, qq, f32)[0]
     return out
 
 
@@ -1063,7 +1100,6 @@ def plan_workload(torch, pkg, ctx, dev, stream, name, basis, quad, items, forms,
     def roofline(prof, precision, n_steps):
         model, mufu = {}, {}
         for v, c, st in zip(views, counts, stats):
-            pts = kernel_points(v, c, st)
             for k, (f, pipe, peak) in kernel_flops(v, c, st, precision).items():
                 f0 = model.get(k, (0.0, pipe, peak))[0]
                 model[k] = (f0 + f, pipe, peak)
@@ -1072,10 +1108,11 @@ def plan_workload(torch, pkg, ctx, dev, stream, name, basis, quad, items, forms,
             kinds = sorted(o.kernel for o in v.operators)
             fused = (precision in ("mixed", "mixed_full") and v.basis == "p1" and
                      kinds == ["laplace_dlp", "laplace_slp"])
-            for k, n in pts.items():
-                ops = v.operators[:1] if (fused and k == "block_p1") else v.operators
-                mufu[k] = mufu.get(k, 0.0) + sum(n * mufu_per_point(o.kernel, k, precision)
-                                                 for o in ops)
+            for i, o in enumerate(v.operators):
+                for k, n in kernel_points(v, c, st, o.kernel, precision).items():
+                    if fused and k == "block_p1" and i > 0:
+                        continue
+                    mufu[k] = mufu.get(k, 0.0) + n * mufu_per_point(o.kernel, k, precision)
         per = {}
         for kname, (launches, ms) in prof.items():
             if kname in model:
@@ -1949,7 +1986,10 @@ def run_all(args):
     kern = r4["kernels"]
     dom = max((k for k in kern if "ms" in kern[k]), key=lambda k: kern[k]["ms"])
     roof = dict(kern[dom])
-    roof.update({"bound": "alu", "kernel": dom, "traffic": None,
+    # DRAM bytes per launch from the committed ncu summary (taken on 6 meshes,
+    # scaled to the 48 by the entries; see its file), for the full workload only
+    traffic = profiled_traffic(dom) if args.c4_meshes == 48 and ws == 1 else None
+    roof.update({"bound": "alu", "kernel": dom, "traffic": traffic,
                  "peak_source": PEAKS["source"] + " (FP32 FMA probe; 'mufu': the reciprocal "
                                                   "square root probe)"})
 

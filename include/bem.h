@@ -552,6 +552,21 @@ int bem_gca_pivots_device(bem_ctx *ctx, int32_t mesh_id, const double *verts, in
  * Needs no device and no context. */
 int64_t bem_rule_points(int32_t cas, int32_t regular_rule, int32_t q, double *out, int64_t cap);
 
+/* The touching rule of case cas (1 = common vertex, 2 = common edge,
+ * 3 = identical) and order q with xi integrated out, in the layout of
+ * bem_rule_points: the q^3 points per subdomain at xi = 1, weight J(eta)
+ * times the Gauss weights of (eta1, eta2, eta3).  Under the Sauter-Schwab
+ * maps of Section 2.2 every coordinate and difference is xi times a function
+ * of eta and the weight xi^3 times one, so for the Laplace kernels the
+ * integrand of a moment is xi^n times a function of eta (single layer n = 2,
+ * double layer n = 1, one more per piecewise-linear coordinate factor); where
+ * the q-point Gauss rule in xi is exact for degree n, the q^4-point sum equals
+ * 1/(n+1) times the sum over these points.  The library evaluates Laplace
+ * touching pairs this way wherever that holds (2q - 1 >= n); the Helmholtz
+ * kernels keep the q^4 rule.  Returns n, or a negative BEM_ERR_* for another
+ * case or order.  Needs no device and no context. */
+int64_t bem_rule_points_xi(int32_t cas, int32_t q, double *out, int64_t cap);
+
 /* ---- allocation-free near field --------------------------------------------
  * The paper has no counterpart of this call; it exists for callers that must
  * not allocate device memory (a service whose device memory belongs to its own

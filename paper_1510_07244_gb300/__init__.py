@@ -7,13 +7,13 @@ training of the quadrature-order model (``order_model``).  The synthetic
 inputs live in the separate ``synth`` package.
 """
 from ._binding import (Context, BlockJob, GreenJob, BemError, kernel_desc, quad_desc, load,
-                       LIB_PATH, EXPORTS, KERNELS, BASES, RULES, bem_rule_points, PLAN_GRAPH,
+                       LIB_PATH, EXPORTS, KERNELS, BASES, RULES, bem_rule_points, bem_rule_points_xi, PLAN_GRAPH,
                        PLAN_AUTOTUNE, PLAN_PROFILE, ORDER_CLASSES,
                        ORDER_CLASS_POINTS, bem_shard_blocks, bem_gca_pivots,
                        bem_touching_pairs, bem_gca_bases)
 
 __all__ = ["Context", "BlockJob", "GreenJob", "BemError", "kernel_desc", "quad_desc", "load",
-           "LIB_PATH", "EXPORTS", "KERNELS", "BASES", "RULES", "bem_rule_points",
+           "LIB_PATH", "EXPORTS", "KERNELS", "BASES", "RULES", "bem_rule_points", "bem_rule_points_xi",
            "PLAN_GRAPH", "PLAN_AUTOTUNE", "PLAN_PROFILE", "ORDER_CLASSES",
            "ORDER_CLASS_POINTS", "bem_shard_blocks", "bem_gca_pivots",
            "bem_touching_pairs", "bem_gca_bases"]

@@ -37,7 +37,8 @@ EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_
            "bem_shard_blocks", "bem_gca_pivots", "bem_touching_pairs", "bem_green_matrices",
            "bem_gca_pivots_device", "bem_plan_guard_stats", "bem_peak_probe", "bem_gca_bases", "bem_h2_create", "bem_h2_matvec",
            "bem_h2_cg", "bem_h2_destroy", "bem_plan_learned_counts", "bem_mlp_fit_norm",
-           "bem_mlp_train_epoch", "bem_order_labels", "bem_potentials", "bem_dense_gmres"]
+           "bem_mlp_train_epoch", "bem_order_labels", "bem_potentials", "bem_dense_gmres",
+           "bem_rule_points_xi"]
 ORDER_CLASSES = [("duffy", 2), ("tri7", 1), ("duffy", 4), ("duffy", 5), ("duffy", 6), ("duffy", 8)]
 ORDER_CLASS_POINTS = [16, 49, 256, 625, 1296, 4096]
 PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE = 1, 2, 4
@@ -175,14 +176,16 @@ def load():
                                      ctypes.c_int64, ctypes.c_float, ctypes.c_int32, _vp, _vp]
     lib.bem_rule_points.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
                                     ctypes.c_int64]
+    lib.bem_rule_points_xi.argtypes = [ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int64]
     lib.bem_profile_enable.argtypes = [_vp, ctypes.c_int32]
     lib.bem_profile_reset.argtypes = [_vp]
     lib.bem_profile_read.argtypes = [_vp, P(bem_kernel_time), ctypes.c_int32,
                                      P(ctypes.c_int32)]
     for name in EXPORTS:
-        if name not in ("bem_last_error", "bem_rule_points"):
+        if name not in ("bem_last_error", "bem_rule_points", "bem_rule_points_xi"):
             getattr(lib, name).restype = ctypes.c_int
     lib.bem_rule_points.restype = ctypes.c_int64
+    lib.bem_rule_points_xi.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -198,6 +201,19 @@ def bem_rule_points(case: str, q: int, regular_rule: str = "duffy"):
         raise BemError(int(n), "bad rule")
     out = np.zeros(7 * n)
     lib.bem_rule_points(CASES[case], RULES[regular_rule], q, out.ctypes.data_as(_vp), out.size)
+    cols = out.reshape(7, n)
+    return dict(zip(("x1", "x2", "y1", "y2", "w", "d1", "d2"), cols))
+
+
+def bem_rule_points_xi(case: str, q: int):
+    """A touching case's rule with xi integrated out (q^3 points per subdomain
+    at xi = 1): dict of numpy columns x1, x2, y1, y2, w, d1, d2."""
+    lib = load()
+    n = lib.bem_rule_points_xi(CASES[case], q, None, 0)
+    if n < 0:
+        raise BemError(int(n), "bad rule")
+    out = np.zeros(7 * n)
+    lib.bem_rule_points_xi(CASES[case], q, out.ctypes.data_as(_vp), out.size)
     cols = out.reshape(7, n)
     return dict(zip(("x1", "x2", "y1", "y2", "w", "d1", "d2"), cols))
 

@@ -123,17 +123,22 @@ int check_kernel(bem_ctx *ctx, const bem_kernel_desc *k)
     return BEM_OK;
 }
 
+// Rules of the context, built on first use: regular rules by (rule, q),
+// touching rules by q with rule 0 (q^4 points) or kRuleXiOut (xi integrated out).
 int get_rule4(bem_ctx *ctx, int cas, int rule, int q, Rule4D &out)
 {
-    auto key = std::make_tuple(cas, cas == kRegular ? rule : 0, q);
+    const bool xi = cas != kRegular && rule == kRuleXiOut;
+    auto key = std::make_tuple(cas, cas == kRegular || xi ? rule : 0, q);
     auto it = ctx->rules4.find(key);
     if (it != ctx->rules4.end()) {
         out = it->second;
         return BEM_OK;
     }
     std::vector<double> soa;
-    if (!make_rule4d_host(cas, rule, q, soa)) return fail(ctx, BEM_ERR_INVALID_ARG, "bad rule");
+    if (!make_rule4d_host(cas, rule, q, soa, xi)) return fail(ctx, BEM_ERR_INVALID_ARG, "bad rule");
     Rule4D r;
+    r.xi = xi ? 1 : 0;
+    r.q = q;
     r.n = (int)(soa.size() / kRuleCols);
     cudaError_t e = cudaMalloc((void **)&r.d, soa.size() * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(rule)");
@@ -156,6 +161,11 @@ int get_rule4(bem_ctx *ctx, int cas, int rule, int q, Rule4D &out)
     return BEM_OK;
 }
 
+int touch_rule(bem_ctx *ctx, int cas, int q, int kind, int basis, bool f32, Rule4D &out)
+{
+    return get_rule4(ctx, cas, touch_xi_out(kind, basis, q, f32) ? kRuleXiOut : 0, q, out);
+}
+
 // Evaluates every touching pair of the mesh into its touching table.
 int run_touching(bem_ctx *ctx, Mesh *m, const bem_kernel_desc *k, const bem_quad_desc *q)
 {
@@ -163,14 +173,14 @@ int run_touching(bem_ctx *ctx, Mesh *m, const bem_kernel_desc *k, const bem_quad
     for (int cas = kVertex; cas <= kIdentical; ++cas) {
         if (m->nlist[cas] == 0) continue;
         Rule4D r;
-        int rc = get_rule4(ctx, cas, 0, qs[cas], r);
+        const int f32 = touch_in_float(q->precision, cas, k->kind);
+        int rc = touch_rule(ctx, cas, qs[cas], k->kind, m->v.basis, f32 != 0, r);
         if (rc) return rc;
         static const char *names[4] = {"", "touching_vertex", "touching_edge",
                                        "touching_identical"};
         ProfScope ps(ctx, names[cas]);
         cudaError_t e = launch_touching(m->v, cas, m->list[cas], m->nlist[cas], r, k->kind,
-                                        k->kappa, touch_in_float(q->precision, cas, k->kind),
-                                        ctx->stream, k->eta);
+                                        k->kappa, f32, ctx->stream, k->eta);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "touching kernel");
     }
     return BEM_OK;
@@ -200,10 +210,10 @@ int run_guard(bem_ctx *ctx, Mesh *m, const BlockLaunch &L, const bem_quad_desc &
 {
     GuardSet g;
     g.r2 = r2;
-    const int rr[4] = {q.regular_rule, 0, 0, 0};
     const int qq[4] = {q.q_regular, q.q_vertex, q.q_edge, q.q_identical};
     for (int c = 0; c < 4; ++c) {
-        int rc = get_rule4(ctx, c, rr[c], qq[c], g.rules[c]);
+        int rc = c == kRegular ? get_rule4(ctx, c, q.regular_rule, qq[c], g.rules[c])
+                               : touch_rule(ctx, c, qq[c], L.kind, m->v.basis, true, g.rules[c]);
         if (rc) return rc;
     }
     cudaError_t e = guard_add(g, m->v, L, ctx->stream);
@@ -334,6 +344,11 @@ namespace bem {
 int api_fail(bem_ctx *ctx, int code, const char *msg) { return fail(ctx, code, msg); }
 int api_ensure_prefix(bem_ctx *ctx, int64_t n) { return ensure_prefix(ctx, n); }
 int api_cuda_fail(bem_ctx *ctx, cudaError_t e, const char *where) { return cuda_fail(ctx, e, where); }
+int api_touch_rule(bem_ctx *ctx, int cas, int q, int kind, int basis, bool f32, Rule4D &out)
+{
+    return touch_rule(ctx, cas, q, kind, basis, f32, out);
+}
+
 int api_get_rule4(bem_ctx *ctx, int cas, int rule, int q, Rule4D &out)
 {
     return get_rule4(ctx, cas, rule, q, out);
@@ -755,6 +770,16 @@ int64_t bem_rule_points(int32_t cas, int32_t regular_rule, int32_t q, double *ou
     if (cas < kRegular || cas > kIdentical || q < 1 || q > 20) return BEM_ERR_INVALID_ARG;
     std::vector<double> soa;
     if (!make_rule4d_host(cas, regular_rule, q, soa)) return BEM_ERR_INVALID_ARG;
+    const int64_t n = (int64_t)(soa.size() / kRuleCols);
+    if (out && cap >= (int64_t)soa.size()) std::memcpy(out, soa.data(), soa.size() * sizeof(double));
+    return n;
+}
+
+int64_t bem_rule_points_xi(int32_t cas, int32_t q, double *out, int64_t cap)
+{
+    if (cas < kVertex || cas > kIdentical || q < 1 || q > 20) return BEM_ERR_INVALID_ARG;
+    std::vector<double> soa;
+    if (!make_rule4d_host(cas, 0, q, soa, true)) return BEM_ERR_INVALID_ARG;
     const int64_t n = (int64_t)(soa.size() / kRuleCols);
     if (out && cap >= (int64_t)soa.size()) std::memcpy(out, soa.data(), soa.size() * sizeof(double));
     return n;

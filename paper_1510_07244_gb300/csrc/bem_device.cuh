@@ -212,6 +212,29 @@ __device__ __forceinline__ void warp_sum2f(float &hi, float &lo)
     }
 }
 
+// The same over aligned groups of W lanes (W a power of two up to 32).
+template <int W>
+__device__ __forceinline__ void group_sum2f(float &hi, float &lo)
+{
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        float sh, e;
+        two_sum(hi, h2, sh, e);
+        hi = sh;
+        lo = (lo + l2) + e;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ float group_sumf(float v)
+{
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // heights of the test triangle's vertices k0, k1, k2 above the trial plane
 // (through the trial vertex bh/bl with normal nh/nl) as affine coefficients
 __device__ __forceinline__ Height make_height(const float *a0h, const float *a0l,
@@ -619,9 +642,12 @@ __device__ __forceinline__ FF operator-(FF a, FF b)
     return r;
 }
 
+// xi = 1: the rule has xi integrated out (Laplace kernels only, see
+// touch_xi_out); the moments take their xi_moment factors at the end.
 template <int KIND, int BASIS, int CAS>
 __device__ __forceinline__ void touch_pair(const MeshView &m, int idx, const double *__restrict__ rule,
-                                           int np, double kappa, int lane, double eta = 0.0)
+                                           int np, double kappa, int lane, double eta = 0.0,
+                                           int xi = 0)
 {
     const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);
     const int pc = __ldg(m.nb_perm + idx);
@@ -741,6 +767,10 @@ __device__ __forceinline__ void touch_pair(const MeshView &m, int idx, const dou
         }
     }
     if (lane == 0) {
+        if (!CPLX && xi) {
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) accr[k] *= xi_moment(KIND, k / 3, k % 3);
+        }
         const double scale = __ldg(g_a + 12) * __ldg(g_b + 12) * kInv4Pi;
         if (BASIS == BEM_P0) {
             m.table[idx] = make_double2(accr[0] * scale, acci[0] * scale);
@@ -828,10 +858,22 @@ __device__ __forceinline__ void regular_p1_f32_fused(const TriF &A, const TriF &
 // from the FP64 records (neighbours can be nearly coplanar): h(x) for a common
 // vertex, x2 h(a2) for a common edge (the shared vertices lie in the plane), 0
 // for identical pairs.  Every lane sums its points with Kahan compensation.
-template <int CAS, int KIND, int BASIS>
+// With xi = 1 the rule holds the points at xi = 1 (xi integrated out): the
+// Laplace moments take their xi_moment factors at the end, and the Helmholtz
+// single layer sums over the Gauss nodes of xi (XR) at each point, sharing the
+// distance and its reciprocal square root.
+// A pair takes an aligned group of LPP lanes (sub = lane within the group):
+// 32 for the q^4 rules, fewer for the shorter xi-integrated ones, so that the
+// per-pair set-up and reduction are shared by fewer points.  Every lane of the
+// warp calls this (the group reductions shuffle across the warp); a group
+// without a pair of its own repeats another and passes store = false.
+template <int CAS, int KIND, int BASIS, int LPP = 32>
 __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const float *__restrict__ rule,
-                                          int np, int lane, float kappa = 0.0f)
+                                          int np, int sub, float kappa, int xi, const XiRule &XR,
+                                          bool store = true)
 {
+    static_assert(LPP == 8 || LPP == 16 || LPP == 32, "lanes per pair");
+    static_assert(BASIS == BEM_P0 || LPP >= 16, "nine hats need nine lanes");
     constexpr bool CPLX = kind_complex(KIND);
     const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);
     const int pc = __ldg(m.nb_perm + idx);
@@ -868,7 +910,7 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
     float h2 = 0.0f;
     if (KIND == BEM_LAPLACE_DLP && CAS != kIdentical) {
         double d1 = 0.0, d2 = 0.0;
-        if (lane == 0) {
+        if (sub == 0) {
             const double *ga = m.geom + (int64_t)a * kGeomStride;
             const double *gb = m.geom + (int64_t)b * kGeomStride;
 #pragma unroll
@@ -878,8 +920,8 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
                 d2 = fma(__ldg(ga + 3 * pa[2] + c) - b0, n, d2);
             }
         }
-        d1 = __shfl_sync(0xffffffffu, d1, 0);
-        d2 = __shfl_sync(0xffffffffu, d2, 0);
+        d1 = __shfl_sync(0xffffffffu, d1, 0, LPP);
+        d2 = __shfl_sync(0xffffffffu, d2, 0, LPP);
         if (CAS == kEdge) {
             h2 = (float)d2;
         } else {
@@ -893,6 +935,7 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
         }
     }
     constexpr int NACC = BASIS == BEM_P0 ? 1 : 9;
+    constexpr int MM = BASIS == BEM_P0 ? 1 : 3;   // moment powers 0, 1, 2
     float acc[NACC], cmp[NACC], acci[NACC], cmpi[NACC];
 #pragma unroll
     for (int k = 0; k < NACC; ++k) acc[k] = cmp[k] = acci[k] = cmpi[k] = 0.0f;
@@ -900,7 +943,7 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
     const bool zero = KIND == BEM_LAPLACE_DLP && CAS == kIdentical;
     const float *X1 = rule, *X2 = rule + np, *Y1 = rule + 2 * np, *Y2 = rule + 3 * np,
                 *W = rule + 4 * np, *D1 = rule + 5 * np, *D2 = rule + 6 * np;
-    // Each lane takes its points in blocks of KB (stride 32): the terms of a
+    // Each lane takes its points in blocks of KB (stride LPP): the terms of a
     // block are added plainly (error at most KB - 1 ulps of the block's
     // magnitudes) and each block sum enters the lane's sums with Kahan
     // compensation, which keeps the compensated accuracy at a quarter of the
@@ -911,13 +954,13 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
     // the cancellation guard)
     constexpr bool ABS = KIND == BEM_LAPLACE_DLP && BASIS == BEM_P0;
     float asum = 0.0f;
-    for (int p0 = lane; p0 < np && !zero; p0 += 32 * KB) {
+    for (int p0 = sub; p0 < np && !zero; p0 += LPP * KB) {
         float br[NACC], bi[NACC];
 #pragma unroll
         for (int k = 0; k < NACC; ++k) br[k] = bi[k] = 0.0f;
 #pragma unroll
         for (int u = 0; u < KB; ++u) {
-            const int p = p0 + 32 * u;
+            const int p = p0 + LPP * u;
             if (p >= np) break;
             const float x1 = __ldg(X1 + p), x2 = __ldg(X2 + p), y1 = __ldg(Y1 + p),
                         y2 = __ldg(Y2 + p), w = __ldg(W + p);
@@ -939,27 +982,69 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
                 dy = fmaf(d1, e1a[1], d2 * e2a[1]);
                 dz = fmaf(d1, e1a[2], d2 * e2a[2]);
             }
-            float wk, wki = 0.0f;
+            // term of moment power m (the number of coordinate factors x, y):
+            // one value for all m unless the Helmholtz xi sum runs here
+            float wk[MM], wki[MM];
             if (CPLX) {
                 // the pair touches: kappa r stays below kappa times two diameters
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 const float ri = rsqrt_fast(r2);
-                float sn, cs;
-                sincosf(kappa * (r2 * ri), &sn, &cs);
-                wk = w * cs * ri;
-                wki = w * sn * ri;
+                if (xi) {
+                    // (dx, dy, dz) = u(eta) at xi = 1: the Gauss sum over xi of
+                    // w_k xi_k^(2+m) exp(i kappa xi_k |u|) / |u| in pairs of
+                    // nodes 1/2 -+ t, one sine and cosine per pair (XiRule)
+                    const float th = kappa * (r2 * ri);
+                    float sr[MM], si[MM];
+#pragma unroll
+                    for (int q = 0; q < MM; ++q) {
+                        sr[q] = XR.cmid[q];
+                        si[q] = 0.0f;
+                    }
+#pragma unroll 1
+                    for (int jp = 0; jp < XR.npair; ++jp) {
+                        float sn, cs;
+                        sincosf(th * XR.t[jp], &sn, &cs);
+#pragma unroll
+                        for (int q = 0; q < MM; ++q) {
+                            sr[q] = fmaf(XR.cp[jp][q], cs, sr[q]);
+                            si[q] = fmaf(XR.cm[jp][q], sn, si[q]);
+                        }
+                    }
+                    float s0, c0;
+                    sincosf(0.5f * th, &s0, &c0);
+                    const float wr = w * ri;
+#pragma unroll
+                    for (int q = 0; q < MM; ++q) {
+                        wk[q] = wr * (sr[q] * c0 - si[q] * s0);
+                        wki[q] = wr * (sr[q] * s0 + si[q] * c0);
+                    }
+                } else {
+                    float sn, cs;
+                    sincosf(kappa * (r2 * ri), &sn, &cs);
+#pragma unroll
+                    for (int q = 0; q < MM; ++q) {
+                        wk[q] = w * cs * ri;
+                        wki[q] = w * sn * ri;
+                    }
+                }
             } else {
-                wk = w * kvalf<KIND>(dx, dy, dz, dn);
+                const float v = w * kvalf<KIND>(dx, dy, dz, dn);
+#pragma unroll
+                for (int q = 0; q < MM; ++q) {
+                    wk[q] = v;
+                    wki[q] = 0.0f;
+                }
             }
-            if (ABS) asum += fabsf(wk);
+            if (ABS) asum += fabsf(wk[0]);
             const float mx[3] = {1.0f, x1, x2}, my[3] = {1.0f, y1, y2};
 #pragma unroll
             for (int i = 0; i < (BASIS == BEM_P0 ? 1 : 3); ++i)
 #pragma unroll
                 for (int j = 0; j < (BASIS == BEM_P0 ? 1 : 3); ++j) {
                     const int k = BASIS == BEM_P0 ? 0 : i * 3 + j;
-                    br[k] += BASIS == BEM_P0 ? wk : wk * mx[i] * my[j];
-                    if (CPLX) bi[k] += BASIS == BEM_P0 ? wki : wki * mx[i] * my[j];
+                    const int q = BASIS == BEM_P0 ? 0 : (i > 0) + (j > 0);
+                    br[k] += BASIS == BEM_P0 ? wk[q] : wk[q] * mx[i] * my[j];
+                    if (CPLX) bi[k] += BASIS == BEM_P0 ? wki[q] : wki[q] * mx[i] * my[j];
                 }
         }
 #pragma unroll
@@ -983,35 +1068,46 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
 #pragma unroll
     for (int k = 0; k < NACC; ++k) {
         mr[k] = FF{acc[k], -cmp[k]};
-        warp_sum2f(mr[k].h, mr[k].l);
+        group_sum2f<LPP>(mr[k].h, mr[k].l);
         mi[k] = FF{0.0f, 0.0f};
         if (CPLX) {
             mi[k] = FF{acci[k], -cmpi[k]};
-            warp_sum2f(mi[k].h, mi[k].l);
+            group_sum2f<LPP>(mi[k].h, mi[k].l);
         }
     }
-    if (ABS) asum = warp_sumf(asum);
+    if (ABS) asum = group_sumf<LPP>(asum);
+    if (!store) return;
     if (BASIS == BEM_P0) {
-        if (lane == 0) {
-            const double scale = (double)A.sg * (double)B.sg * kInv4Pi;
+        if (sub == 0) {
+            // xi integrated out: every term (and so the sum of |terms|) takes one factor
+            const double scale = (double)A.sg * (double)B.sg * kInv4Pi *
+                                 (!CPLX && xi ? xi_moment(KIND, 0, 0) : 1.0);
             m.table[idx] = make_double2(((double)mr[0].h + (double)mr[0].l) * scale,
                                         ABS ? (double)asum * scale
                                             : ((double)mi[0].h + (double)mi[0].l) * scale);
         }
     } else {
+        if (!CPLX && xi) {
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) {
+                const double c = xi_moment(KIND, k / 3, k % 3);
+                const float ch = (float)c, cl = (float)(c - (double)ch);
+                dd_mul(mr[k].h, mr[k].l, ch, cl, mr[k].h, mr[k].l);
+            }
+        }
         FF hr[9], hi[9];
         moments_to_hats(mr, hr);
         if (CPLX) moments_to_hats(mi, hi);
         FF vr = hr[0], vi = CPLX ? hi[0] : FF{0.0f, 0.0f};
 #pragma unroll
         for (int q = 1; q < 9; ++q)
-            if (lane == q) {
+            if (sub == q) {
                 vr = hr[q];
                 if (CPLX) vi = hi[q];
             }
-        if (lane < 9) {
+        if (sub < 9) {
             const double scale = (double)A.sg * (double)B.sg * kInv4Pi;
-            m.table[(int64_t)idx * 9 + pa[lane / 3] * 3 + pb[lane % 3]] =
+            m.table[(int64_t)idx * 9 + pa[sub / 3] * 3 + pb[sub % 3]] =
                 make_double2(((double)vr.h + (double)vr.l) * scale,
                              ((double)vi.h + (double)vi.l) * scale);
         }
@@ -1196,8 +1292,8 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
     // Each warp finds the blocks of its 32 entries by itself (no CTA barrier):
     // one search for the block of its first entry, then the inclusive sums of
     // the 32 blocks from there, one per lane; an entry's block is the first
-    // of them whose sum exceeds it (a ballot), unless more than 32 of the
-    // blocks are empty.
+    // of them whose sum exceeds it (a search over the lanes by shuffles),
+    // unless more than 32 of the blocks are empty.
     const int lane = threadIdx.x & 31;
     const int64_t ew = tile * kP0Tile + (threadIdx.x & ~31);
     const int64_t total = prefix[L.n_blocks - 1];
@@ -1206,7 +1302,19 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
     const int64_t b0 = find_block(prefix, L.n_blocks, ew);
     const int64_t pw = b0 + lane < L.n_blocks ? prefix[b0 + lane] : INT64_MAX;
     const int64_t p_before = b0 > 0 ? prefix[b0 - 1] : 0;
-    const int k = __popc(__ballot_sync(0xffffffffu, pw <= e));
+    // k = first window slot with a sum above e (32 if none); six steps
+    // narrow [0, 32] to one slot, every lane shuffling in every step
+    int lo = 0, hi = 32;
+#pragma unroll
+    for (int step = 0; step < 6; ++step) {
+        const int mid = (lo + hi) >> 1;
+        const int64_t v = __shfl_sync(0xffffffffu, pw, mid & 31);
+        if (lo < hi) {
+            if (v > e) hi = mid;
+            else lo = mid + 1;
+        }
+    }
+    const int k = lo;
     const int64_t p_prev = __shfl_sync(0xffffffffu, pw, k > 0 ? k - 1 : 0);
     int64_t b, before;
     if (k < 32) {
@@ -1223,8 +1331,12 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
         return;
     }
     const int r_lo = L.row_ptr[t], nr = L.row_ptr[t + 1] - r_lo;
-    const int c_lo = L.col_ptr[s];
-    const int64_t le = e - before;          // 0 <= le < nr * nc
+    const int c_lo = L.col_ptr[s], nc = L.col_ptr[s + 1] - c_lo;
+    const int64_t le = e - before;
+    if (le < 0 || nr <= 0 || le >= (int64_t)nr * nc) {   // the prefix and the blocks disagree
+        set_status(status, BEM_ERR_INVALID_ARG);
+        return;
+    }
     const int c = (int)(le / nr), r = (int)(le - (int64_t)c * nr);
     const int a = L.row_idx[r_lo + r], bb = L.col_idx[c_lo + c];
     if (a < 0 || a >= m.nt || bb < 0 || bb >= m.nt) {

@@ -217,6 +217,7 @@ struct GuardRule {
 struct TouchRules {
     const float *h[4], *l[4];   // [case]: kRuleCols n floats each, hi and lo parts
     int n[4];
+    int xi[4];                  // 1: xi integrated out (the double layer's factor 1/2)
 };
 
 // One warp per listed touching entry (common vertex or common edge; a flat
@@ -331,7 +332,9 @@ __global__ void __launch_bounds__(256) k_guard_redo_touch(const GuardJob *__rest
         if (lane == 0) {
             const double sa = __ldg(m.geom + (int64_t)a * kGeomStride + 12);
             const double sb = __ldg(m.geom + (int64_t)b * kGeomStride + 12);
-            reinterpret_cast<double *>(G.L.out)[it.off] = ((double)gh + (double)gl) * (sa * sb * kInv4Pi);
+            const double xs = cas >= kVertex && R.xi[cas] ? xi_moment(BEM_LAPLACE_DLP, 0, 0) : 1.0;
+            reinterpret_cast<double *>(G.L.out)[it.off] =
+                ((double)gh + (double)gl) * (sa * sb * kInv4Pi) * xs;
         }
     }
 }
@@ -562,6 +565,7 @@ cudaError_t guard_run(const GuardSet &g, int num_sms, int *status, cudaStream_t 
         tr.h[c] = g.rules[c].f;
         tr.l[c] = g.rules[c].fl;
         tr.n[c] = g.rules[c].n;
+        tr.xi[c] = g.rules[c].xi;
     }
     if (g.cap_t > 0)
         k_guard_redo_touch<<<num_sms * 4, 256, 0, st>>>(g.d_jobs, g.d_list_t, g.d_count + 1,

@@ -48,10 +48,28 @@ struct Rule2D {
 constexpr int kRuleCols = 7;
 struct Rule4D {
     int n = 0;
+    int q = 0;             // Gauss points per axis (touching rules)
     double *d = nullptr;   // device, kRuleCols n doubles
     float *f = nullptr;    // device, kRuleCols n floats (mixed form), may be null
     float *fl = nullptr;   // device, kRuleCols n floats: d - f (double-float form), may be null
+    int xi = 0;            // 1: a touching rule with xi integrated out (at xi = 1)
 };
+// Rule id of the touching rules with xi integrated out (the rule cache's key).
+constexpr int kRuleXiOut = 1;
+
+// The q-point Gauss rule in xi on [0, 1] for the Helmholtz sums at fixed eta:
+// sum_k w_k xi_k^(2+m) exp(i th xi_k) = exp(i th / 2) (cmid[m] + sum_j
+// (cp[j][m] cos(th t_j) + i cm[j][m] sin(th t_j))) over the node pairs
+// xi = 1/2 -+ t_j (the nodes and weights are symmetric about 1/2), cmid the
+// middle node's term for odd q; m = 0, 1, 2.
+constexpr int kMaxXiPairs = 10;
+struct XiRule {
+    int npair = 0;
+    float t[kMaxXiPairs];
+    float cp[kMaxXiPairs][3], cm[kMaxXiPairs][3];
+    float cmid[3] = {0.0f, 0.0f, 0.0f};
+};
+bool make_xi_rule(int q, XiRule &out);
 
 // Device view of an uploaded mesh.
 struct MeshView {
@@ -144,6 +162,10 @@ int api_ensure_prefix(bem_ctx *ctx, int64_t n);   // grows the tile-prefix scrat
 int api_cuda_fail(bem_ctx *ctx, cudaError_t e, const char *where);
 int api_check_job(bem_ctx *ctx, const bem_block_job &J, Rule2D &r2, Mesh **mesh);
 int api_get_rule4(bem_ctx *ctx, int cas, int rule, int q, Rule4D &out);
+// The touching rule of case cas and order q for a kernel, basis and
+// precision of the touching kernel (f32): xi integrated out where
+// touch_xi_out allows it, else the q^4 rule.
+int api_touch_rule(bem_ctx *ctx, int cas, int q, int kind, int basis, bool f32, Rule4D &out);
 void prof_accumulate(bem_ctx *ctx, const bem_prof_rec &r);
 // bem_plan.cpp: adds the unread launch times of plans run since the last read
 void plan_drain_profile(bem_ctx *ctx);
@@ -175,7 +197,8 @@ int gca_pivots_levels(const double *verts, int64_t nv, const int32_t *tris, int6
 // bem_rules.cpp
 bool gauss_legendre_unit(int q, std::vector<double> &x, std::vector<double> &w);
 bool make_rule2d(int regular_rule, int q, Rule2D &out);
-bool make_rule4d_host(int cas, int regular_rule, int q, std::vector<double> &soa);
+bool make_rule4d_host(int cas, int regular_rule, int q, std::vector<double> &soa,
+                      bool xi_out = false);
 
 // bem_kernels.cu: launchers (return a cudaError_t of the launch)
 struct BlockLaunch {
@@ -235,6 +258,28 @@ __host__ __device__ constexpr bool kind_fp64_only(int kind)
 __host__ __device__ constexpr bool kind_has_height(int kind)
 {
     return kind == BEM_LAPLACE_DLP || kind == BEM_HELMHOLTZ_DLP || kind == BEM_HELMHOLTZ_BW;
+}
+// Touching pairs with xi integrated out.  Under the Sauter-Schwab maps the
+// Laplace integrands are xi^n times a function of (eta1, eta2, eta3): the
+// single layer xi^2 (Jacobian xi^3 over r = xi |u|), the double layer xi
+// (height xi h over r^3 = xi^3 |u|^3), and each piecewise-linear moment
+// (1, x1, x2) x (1, y1, y2) one more power per factor x or y.  The q-point
+// Gauss rule in xi integrates degree 2q - 1 exactly, so where n stays within
+// it the sum over xi is 1 / (n + 1), and the rule at xi = 1 with that factor
+// gives the q^4-point result (up to rounding) with q^3 points per subdomain.
+__host__ __device__ constexpr int xi_base(int kind) { return kind == BEM_LAPLACE_SLP ? 2 : 1; }
+inline bool touch_xi_out(int kind, int basis, int q, bool f32)
+{
+    // the float Helmholtz single layer sums over xi at each point (XiRule)
+    if (kind == BEM_HELMHOLTZ_SLP) return f32 && q <= 2 * kMaxXiPairs;
+    if (kind != BEM_LAPLACE_SLP && kind != BEM_LAPLACE_DLP) return false;
+    const int deg = xi_base(kind) + (basis == BEM_P1 ? 2 : 0);
+    return 2 * q - 1 >= deg;
+}
+// factor of the moment with i (test) and j (trial) coordinate factors
+__host__ __device__ constexpr double xi_moment(int kind, int i, int j)
+{
+    return 1.0 / (double)(xi_base(kind) + (i > 0 ? 1 : 0) + (j > 0 ? 1 : 0) + 1);
 }
 inline int touch_in_float(int precision, int cas, int kind)
 {

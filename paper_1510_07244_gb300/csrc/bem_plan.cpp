@@ -401,7 +401,7 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         TouchBucket t;
         std::tie(t.basis, t.kind, t.cas, t.mixed, std::ignore) = kv.first;
         const int q = std::get<4>(kv.first);
-        int rc = api_get_rule4(ctx, t.cas, 0, q, t.rule);
+        int rc = api_touch_rule(ctx, t.cas, q, t.kind, t.basis, t.mixed != 0, t.rule);
         if (rc) {
             plan_free(p);
             return rc;
@@ -551,10 +551,11 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
             if (gi == gindex.end()) {
                 GuardSet g;
                 g.r2 = ji.r2;
-                const int rr[4] = {J.quad.regular_rule, 0, 0, 0};
                 const int qq[4] = {J.quad.q_regular, J.quad.q_vertex, J.quad.q_edge, J.quad.q_identical};
                 for (int c = 0; c < 4; ++c) {
-                    int rc = api_get_rule4(ctx, c, rr[c], qq[c], g.rules[c]);
+                    int rc = c == kRegular
+                                 ? api_get_rule4(ctx, c, J.quad.regular_rule, qq[c], g.rules[c])
+                                 : api_touch_rule(ctx, c, qq[c], L.kind, b.basis, true, g.rules[c]);
                     if (rc) {
                         plan_free(p);
                         return rc;

@@ -25,6 +25,14 @@
 //                                                    J = xi^3 eta1 (1-eta1)
 //    Every piece is used as is and with x and y exchanged (R- = swap of R+):
 //    2, 4 and 6 subdomains with q^4 points each.
+//  * In every piece x1, x2, y1, y2 and the differences are xi times a function
+//    of (eta1, eta2, eta3), and the weight is xi^3 times one.  For the Laplace
+//    kernels on flat triangles the integrand is then a monomial in xi times a
+//    function of eta (r = xi |u(eta)|, heights xi h(eta), the hats' arguments
+//    xi times ...), so a Gauss rule in xi that is exact for that degree sums
+//    to the monomial's integral 1 / (n + 1): the same rule with xi integrated
+//    out has q^3 points per subdomain, taken at xi = 1 with weight
+//    J(eta) w(eta) (xi_moment gives the factor of each moment).
 #include <cmath>
 #include <functional>
 #include <vector>
@@ -129,6 +137,28 @@ bool make_rule2d(int regular_rule, int q, Rule2D &out)
     return true;
 }
 
+bool make_xi_rule(int q, XiRule &out)
+{
+    std::vector<double> g, gw;
+    if (q < 1 || q > 2 * kMaxXiPairs || !gauss_legendre_unit(q, g, gw)) return false;
+    out = XiRule();
+    // nodes ascend: g[k] = 1/2 - t, g[q-1-k] = 1/2 + t with equal weights
+    for (int k = 0; k < q / 2; ++k) {
+        const double a = g[q - 1 - k], b = g[k];
+        const double w = 0.5 * (gw[k] + gw[q - 1 - k]);
+        out.t[k] = (float)(a - 0.5);
+        for (int m = 0; m < 3; ++m) {
+            const double pa = std::pow(a, 2 + m), pb = std::pow(b, 2 + m);
+            out.cp[k][m] = (float)(w * (pa + pb));
+            out.cm[k][m] = (float)(w * (pa - pb));
+        }
+    }
+    out.npair = q / 2;
+    if (q % 2)
+        for (int m = 0; m < 3; ++m) out.cmid[m] = (float)(gw[q / 2] * std::pow(0.5, 2 + m));
+    return true;
+}
+
 namespace {
 
 struct Pt {
@@ -178,8 +208,9 @@ std::vector<Piece> pieces(int cas)
 
 }  // namespace
 
-bool make_rule4d_host(int cas, int regular_rule, int q, std::vector<double> &soa)
+bool make_rule4d_host(int cas, int regular_rule, int q, std::vector<double> &soa, bool xi_out)
 {
+    if (xi_out && cas == kRegular) return false;
     std::vector<Pt> pts;
     if (cas == kRegular) {
         // 2D rule on D (any Duffy order here; the block engine's Rule2D holds <= 25 points)
@@ -206,14 +237,16 @@ bool make_rule4d_host(int cas, int regular_rule, int q, std::vector<double> &soa
     } else {
         std::vector<double> g, gw;
         if (!gauss_legendre_unit(q, g, gw)) return false;
+        // xi integrated out: one node xi = 1 with weight 1
+        const int nxi = xi_out ? 1 : q;
         for (const Piece &f : pieces(cas))
             for (int swap = 0; swap < 2; ++swap)
-                for (int i = 0; i < q; ++i)
+                for (int i = 0; i < nxi; ++i)
                     for (int j = 0; j < q; ++j)
                         for (int k = 0; k < q; ++k)
                             for (int l = 0; l < q; ++l) {
-                                Pt p = f(g[i], g[j], g[k], g[l]);
-                                p.w *= gw[i] * gw[j] * gw[k] * gw[l];
+                                Pt p = f(xi_out ? 1.0 : g[i], g[j], g[k], g[l]);
+                                p.w *= (xi_out ? 1.0 : gw[i]) * gw[j] * gw[k] * gw[l];
                                 if (swap) {
                                     std::swap(p.x1, p.y1);
                                     std::swap(p.x2, p.y2);
