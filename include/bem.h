@@ -688,9 +688,10 @@ int bem_dense_gmres(bem_ctx *ctx, int64_t n, const double *A, const double *diag
  * launch with CUDA events on that stream.  kind: 0 = FP32 FMA (2 operations
  * each), 1 = FP64 FMA (2 each), 2 = reciprocal square root of the special
  * function unit (rsqrt.approx.ftz.f32, 1 each), 3 = its sine and cosine
- * (2 per argument).  Every thread of 8 CTAs of 256 threads per SM runs 8
- * independent chains of 16 operations per trip, `trips` times.  Errors:
- * BEM_ERR_INVALID_ARG for a kind outside [0, 3] or trips outside [1, 2^30]. */
+ * (2 per argument), 4 = packed FP32 pair FMA (fma.rn.f32x2, 4 each).  Every
+ * thread of 8 CTAs of 256 threads per SM runs 8 independent chains of 16
+ * instructions per trip, `trips` times.  Errors: BEM_ERR_INVALID_ARG for a
+ * kind outside [0, 4] or trips outside [1, 2^30]. */
 int bem_peak_probe(bem_ctx *ctx, int32_t kind, int64_t trips, double *ops);
 
 /* ---- launch profiling (tracing) ------------------------------------------

@@ -99,6 +99,39 @@ __global__ void __launch_bounds__(256) k_peak_sincos(int64_t trips, float *sink)
     if (s == 12345.678f) sink[blockIdx.x] = s;
 }
 
+// Packed FP32 pairs: one fma.rn.f32x2 is two FMAs on the two halves of a
+// 64-bit register pair (sm_100 and later).
+__device__ __forceinline__ unsigned long long pack_f32x2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_peak_ffma2(int64_t trips, float a, float b, float *sink)
+{
+    unsigned long long x[kChains];
+    const unsigned long long aa = pack_f32x2(a, a), bb = pack_f32x2(b, b);
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+        x[c] = pack_f32x2((float)(threadIdx.x + c) * 1e-3f, (float)(threadIdx.x + c) * 2e-3f);
+    for (int64_t t = 0; t < trips; ++t) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c)
+                asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[c]) : "l"(aa), "l"(bb));
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x[c]));
+        s += lo + hi;
+    }
+    if (s == 12345.678f) sink[blockIdx.x] = s;
+}
+
 }  // namespace
 
 }  // namespace bem
@@ -107,8 +140,8 @@ extern "C" int bem_peak_probe(bem_ctx *ctx, int32_t kind, int64_t trips, double 
 {
     using namespace bem;
     if (!ctx) return BEM_ERR_INVALID_ARG;
-    if (!ops || kind < 0 || kind > 3 || trips < 1 || trips > (int64_t)1 << 30)
-        return api_fail(ctx, BEM_ERR_INVALID_ARG, "bem_peak_probe: kind in [0, 3], trips in [1, 2^30]");
+    if (!ops || kind < 0 || kind > 4 || trips < 1 || trips > (int64_t)1 << 30)
+        return api_fail(ctx, BEM_ERR_INVALID_ARG, "bem_peak_probe: kind in [0, 4], trips in [1, 2^30]");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return api_cuda_fail(ctx, e, "cudaSetDevice");
     const int blocks = ctx->num_sms * 8, threads = 256;
@@ -132,9 +165,13 @@ extern "C" int bem_peak_probe(bem_ctx *ctx, int32_t kind, int64_t trips, double 
         k_peak_rsqrt<<<blocks, threads, 0, ctx->stream>>>(trips, (float *)sink);
         *ops = n;
         break;
-    default:
+    case 3:
         k_peak_sincos<<<blocks, threads, 0, ctx->stream>>>(trips, (float *)sink);
         *ops = 2.0 * n;          // sine and cosine
+        break;
+    default:
+        k_peak_ffma2<<<blocks, threads, 0, ctx->stream>>>(trips, 0.999f, 1e-3f, (float *)sink);
+        *ops = 4.0 * n;          // two FMAs per instruction
         break;
     }
     e = cudaGetLastError();
