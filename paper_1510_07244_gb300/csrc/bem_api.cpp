@@ -288,11 +288,10 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
         L.eta = J.kernel.eta;
         const bool coupling = J.quad.order_mode == BEM_ORDER_FIXED &&
                               use_coupling_engine(m->v.basis, L.kind, L.mixed, L.allow_touching);
-        // learned orders take their own tiles (32 rows x 8 columns)
+        // learned orders run on the piecewise-constant engine's flat tiles
         const bool learned = J.quad.order_mode == BEM_ORDER_LEARNED;
-        const TileShape ts = block_tile_shape(m->v.basis, coupling);
-        const int tr = learned ? kTile : ts.tr;
-        const int tc = learned ? kP0Cols : ts.tc;
+        const TileShape ts = block_tile_shape(learned ? BEM_P0 : m->v.basis, coupling);
+        const int tr = ts.tr, tc = ts.tc;
         cudaError_t e;
         {
             ProfScope ps(ctx, "tile_prefix");

@@ -15,7 +15,11 @@ static __constant__ int c_perm[6][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {0, 2, 
 
 constexpr double kInv4Pi = 0.079577471545947667884441881686257181;
 
-__device__ __forceinline__ void set_status(int *st, int code) { atomicCAS(st, 0, code); }
+// First error wins; a null status word (passes that repeat a checked pass) drops it.
+__device__ __forceinline__ void set_status(int *st, int code)
+{
+    if (st) atomicCAS(st, 0, code);
+}
 
 struct Tri {
     double v[3][3];
@@ -1281,23 +1285,34 @@ __device__ __forceinline__ BlockInfo block_info(const BlockLaunch &L, const int6
 // leaves of a few triangles) leave no lane idle.  prefix[b] = entries of
 // blocks 0..b (inclusive).
 // ---------------------------------------------------------------------------
-// One tile of one block list; `tile` indexes the list's tiles (called by
-// every thread of the CTA with the same `tile`; the warps run independently).
-template <int KIND, int NP, bool MIXED>
-__device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
-                                        const int64_t *__restrict__ prefix, int64_t tile,
-                                        int *status)
+// Entry threadIdx.x of flat tile `tile` of a block list (prefix = inclusive
+// entry counts per block): its triangle pair (a, b) and output position.
+// Each warp finds the blocks of its 32 entries by itself (no CTA barrier):
+// one search for the block of its first entry, then the inclusive sums of the
+// 32 blocks from there, one per lane; an entry's block is the first of them
+// whose sum exceeds it (a search over the lanes by shuffles), unless more than
+// 32 of the blocks are empty.  Every lane of a warp whose first entry lies
+// within the list must call this (shuffles); ok = false past the list's end
+// and for invalid blocks or indices (these set the status word).
+struct FlatEntry {
+    bool ok;
+    int a, b;        // test and trial triangle
+    int64_t pos;     // output position: block offset + row + column * rows
+};
+
+__device__ __forceinline__ FlatEntry flat_entry(const MeshView &m, const BlockLaunch &L,
+                                                const int64_t *__restrict__ prefix, int64_t tile,
+                                                int *status)
 {
     static_assert(kP0Tile == 256, "one thread per entry of a tile");
-    // Each warp finds the blocks of its 32 entries by itself (no CTA barrier):
-    // one search for the block of its first entry, then the inclusive sums of
-    // the 32 blocks from there, one per lane; an entry's block is the first
-    // of them whose sum exceeds it (a search over the lanes by shuffles),
-    // unless more than 32 of the blocks are empty.
+    FlatEntry fe;
+    fe.ok = false;
+    fe.a = fe.b = 0;
+    fe.pos = 0;
     const int lane = threadIdx.x & 31;
     const int64_t ew = tile * kP0Tile + (threadIdx.x & ~31);
     const int64_t total = prefix[L.n_blocks - 1];
-    if (ew >= total) return;   // the whole warp
+    if (ew >= total) return fe;   // the whole warp
     const int64_t e = ew + lane;
     const int64_t b0 = find_block(prefix, L.n_blocks, ew);
     const int64_t pw = b0 + lane < L.n_blocks ? prefix[b0 + lane] : INT64_MAX;
@@ -1324,25 +1339,41 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
         b = find_block(prefix, L.n_blocks, e);
         before = b > 0 ? prefix[b - 1] : 0;
     }
-    if (e >= total) return;
+    if (e >= total) return fe;
     const int t = L.blk_row[b], s = L.blk_col[b];
     if (t < 0 || t >= L.n_row_clusters || s < 0 || s >= L.n_col_clusters) {
         set_status(status, BEM_ERR_INVALID_ARG);
-        return;
+        return fe;
     }
     const int r_lo = L.row_ptr[t], nr = L.row_ptr[t + 1] - r_lo;
     const int c_lo = L.col_ptr[s], nc = L.col_ptr[s + 1] - c_lo;
     const int64_t le = e - before;
     if (le < 0 || nr <= 0 || le >= (int64_t)nr * nc) {   // the prefix and the blocks disagree
         set_status(status, BEM_ERR_INVALID_ARG);
-        return;
+        return fe;
     }
     const int c = (int)(le / nr), r = (int)(le - (int64_t)c * nr);
-    const int a = L.row_idx[r_lo + r], bb = L.col_idx[c_lo + c];
-    if (a < 0 || a >= m.nt || bb < 0 || bb >= m.nt) {
+    fe.a = L.row_idx[r_lo + r];
+    fe.b = L.col_idx[c_lo + c];
+    if (fe.a < 0 || fe.a >= m.nt || fe.b < 0 || fe.b >= m.nt) {
         set_status(status, BEM_ERR_INVALID_ARG);
-        return;
+        return fe;
     }
+    fe.pos = L.blk_off[b] + le;
+    fe.ok = true;
+    return fe;
+}
+
+// One tile of one block list; `tile` indexes the list's tiles (called by
+// every thread of the CTA with the same `tile`; the warps run independently).
+template <int KIND, int NP, bool MIXED>
+__device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
+                                        const int64_t *__restrict__ prefix, int64_t tile,
+                                        int *status)
+{
+    const FlatEntry fe = flat_entry(m, L, prefix, tile, status);
+    if (!fe.ok) return;
+    const int a = fe.a, bb = fe.b;
     if (L.lower_only && a < bb) return;
     double re, im;
     float absum = 0.0f;   // guarded double layer: sum of |terms|
@@ -1380,7 +1411,7 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
         load_tri(m.geom, bb, B);
         regular_p0<KIND, NP>(A, B, R, L.kappa, re, im, L.eta);
     }
-    const int64_t o = L.blk_off[b] + le;
+    const int64_t o = fe.pos;
     if (kind_complex(KIND)) reinterpret_cast<double2 *>(L.out)[o] = make_double2(re, im);
     else if (guard) reinterpret_cast<float2 *>(L.out)[o] = make_float2((float)re, absum);
     else reinterpret_cast<double *>(L.out)[o] = re;

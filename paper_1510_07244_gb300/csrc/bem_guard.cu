@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(256) k_guard_rowmax(const GuardJob *__restrict
     }
 }
 
-// One warp per block, lanes over its entries (column-major, coalesced).
+// One warp per block, lanes over its entries (column-major, coalesced), four
+// entries per lane in flight.
 __global__ void __launch_bounds__(256) k_guard_select(const GuardJob *__restrict__ jobs,
                                                       const int64_t *__restrict__ blk_end,
                                                       int n_jobs, GuardItem *list,
@@ -127,47 +128,63 @@ __global__ void __launch_bounds__(256) k_guard_select(const GuardJob *__restrict
         float2 *o2 = reinterpret_cast<float2 *>(G.L.out) + g.off;
         double *od = reinterpret_cast<double *>(G.L.out) + g.off;
         const int n = g.nr * g.nc;
-        // the whole warp iterates together, so the ballot below sees every lane
-        for (int e0 = 0; e0 < n; e0 += 32) {
-            const int e = e0 + lane;
-            bool redo = false;
-            int row = 0, col = 0;
-            if (e < n) {
-                const float2 v = o2[e];
-                const int c = e / g.nr;
-                row = G.L.row_idx[g.r_lo + e - c * g.nr];
-                col = G.L.col_idx[g.c_lo + c];
-                float rmax = 0.0f;
-                if (row >= 0 && row < G.n_rows) rmax = __uint_as_float(G.rowmax[row]);
-                const float scale = fmaxf(fabsf(v.x), kRowFloor * rmax);
-                redo = rel * v.y > kRelBound * scale;
-                // entries kept in float are widened in place; the listed ones
-                // keep the pair until the recomputation overwrites them
-                if (!redo) od[e] = (double)v.x;
+        // four entries per lane and trip, their loads issued together; the
+        // whole warp iterates together, so the ballots below see every lane
+        constexpr int U = 4;
+        for (int e0 = 0; e0 < n; e0 += 32 * U) {
+            float2 v[U];
+            int row[U], col[U];
+            bool redo[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + 32 * u + lane;
+                v[u] = e < n ? o2[e] : make_float2(0.0f, 0.0f);
+                const int c = e < n ? e / g.nr : 0;
+                row[u] = e < n ? G.L.row_idx[g.r_lo + e - c * g.nr] : 0;
+                col[u] = e < n ? G.L.col_idx[g.c_lo + c] : 0;
             }
-            // touching pairs (shared vertex index) go to their own list
-            bool touch = false;
-            if (redo) touch = touching(__ldg(G.m.tvid + row), __ldg(G.m.tvid + col));
-            for (int side = 0; side < 2; ++side) {
-                const bool mine = redo && (side == 1) == touch;
-                const unsigned mask = __ballot_sync(0xffffffffu, mine);
-                if (!mask) continue;
-                unsigned long long base = 0;
-                const int leader = __ffs(mask) - 1;
-                if (lane == leader) base = atomicAdd(count + side, (unsigned long long)__popc(mask));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (mine) {
-                    const unsigned long long k = base + __popc(mask & ((1u << lane) - 1u));
-                    if ((int64_t)k < (side == 0 ? cap : cap_t)) {
-                        GuardItem it;
-                        it.job = g.job;
-                        it.row = row;
-                        it.col = col;
-                        it.off = g.off + e;
-                        (side == 0 ? list : list_t)[k] = it;
-                    } else {
-                        set_status(status, BEM_ERR_OOM);
-                        od[e] = (double)o2[e].x;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + 32 * u + lane;
+                redo[u] = false;
+                if (e < n) {
+                    float rmax = 0.0f;
+                    if (row[u] >= 0 && row[u] < G.n_rows) rmax = __uint_as_float(G.rowmax[row[u]]);
+                    const float scale = fmaxf(fabsf(v[u].x), kRowFloor * rmax);
+                    redo[u] = rel * v[u].y > kRelBound * scale;
+                    // entries kept in float are widened in place; the listed
+                    // ones keep the pair until the recomputation overwrites them
+                    if (!redo[u]) od[e] = (double)v[u].x;
+                }
+            }
+            if (!__any_sync(0xffffffffu, redo[0] || redo[1] || redo[2] || redo[3])) continue;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + 32 * u + lane;
+                // touching pairs (shared vertex index) go to their own list
+                bool touch = false;
+                if (redo[u]) touch = touching(__ldg(G.m.tvid + row[u]), __ldg(G.m.tvid + col[u]));
+                for (int side = 0; side < 2; ++side) {
+                    const bool mine = redo[u] && (side == 1) == touch;
+                    const unsigned mask = __ballot_sync(0xffffffffu, mine);
+                    if (!mask) continue;
+                    unsigned long long base = 0;
+                    const int leader = __ffs(mask) - 1;
+                    if (lane == leader) base = atomicAdd(count + side, (unsigned long long)__popc(mask));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (mine) {
+                        const unsigned long long k = base + __popc(mask & ((1u << lane) - 1u));
+                        if ((int64_t)k < (side == 0 ? cap : cap_t)) {
+                            GuardItem it;
+                            it.job = g.job;
+                            it.row = row[u];
+                            it.col = col[u];
+                            it.off = g.off + e;
+                            (side == 0 ? list : list_t)[k] = it;
+                        } else {
+                            set_status(status, BEM_ERR_OOM);
+                            od[e] = (double)v[u].x;
+                        }
                     }
                 }
             }

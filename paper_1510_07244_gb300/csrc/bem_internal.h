@@ -23,7 +23,6 @@ constexpr int kGeomFStride = 32;     // floats per triangle record of the mixed 
 constexpr int kMaxDegP1 = 16;        // vertex degree bound of the P1 block engine
 constexpr int kTile = 32;            // rows / columns of one block tile
 constexpr int kP0Tile = 256;         // entries of one piecewise-constant tile (one per thread)
-constexpr int kP0Cols = 8;           // columns of a learned-order tile (32 rows x 8 columns)
 constexpr int kMaxNp = 25;           // points of a 2D regular rule (Duffy q <= 5)
 
 enum Case { kRegular = 0, kVertex = 1, kEdge = 2, kIdentical = 3 };
@@ -93,10 +92,11 @@ struct MeshView {
 // Scratch of one learned-order job: class per tile slot, records grouped by
 // class, counters (int [8] + fill [8]) and class offsets (int64 [7]).
 struct LearnedScratch {
-    unsigned char *cls = nullptr;
-    void *rec = nullptr;
-    int64_t *small = nullptr;
-    int64_t cap = 0;
+    unsigned char *cls = nullptr;   // class per entry slot (cap slots)
+    void *rec = nullptr;            // records by class (cap int4)
+    int64_t *small = nullptr;       // class counts and offsets
+    int *tcount = nullptr;          // per class and tile: count, then scanned offset
+    int64_t cap = 0;                // entry slots: a multiple of the flat tile
 };
 
 struct Mesh {

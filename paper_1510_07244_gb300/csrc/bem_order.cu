@@ -409,26 +409,19 @@ static const int kClassRule[kClasses][2] = {{BEM_RULE_DUFFY, 2}, {BEM_RULE_TRI7,
                                             {BEM_RULE_DUFFY, 4}, {BEM_RULE_DUFFY, 5},
                                             {BEM_RULE_DUFFY, 6}, {BEM_RULE_DUFFY, 8}};
 
+// Entry threadIdx.x of flat tile `tile` (flat_entry; every lane of the warp
+// calls this).
 __device__ __forceinline__ void select_entry(const MeshView &m, const BlockLaunch &L,
                                              const int64_t *prefix, int64_t tile, int *status,
                                              int &a, int &b, int64_t &pos, int &state)
 {
     // state: 0 = no entry, 1 = done (touching, written), 2 = regular pair
     state = 0;
-    const BlockInfo bi = block_info(L, prefix, tile, status);
-    if (!bi.ok) return;
-    const int lr = threadIdx.x & 31, lc = threadIdx.x >> 5;
-    const int ntr = (bi.nr + kTile - 1) / kTile;
-    const int r = (bi.tile_in_blk % ntr) * kTile + lr;
-    const int c = (bi.tile_in_blk / ntr) * kP0Cols + lc;
-    if (r >= bi.nr || c >= bi.nc) return;
-    a = L.row_idx[bi.r_lo + r];
-    b = L.col_idx[bi.c_lo + c];
-    if (a < 0 || a >= m.nt || b < 0 || b >= m.nt) {
-        set_status(status, BEM_ERR_INVALID_ARG);
-        return;
-    }
-    pos = bi.off + (int64_t)r + (int64_t)c * bi.nr;
+    const FlatEntry fe = flat_entry(m, L, prefix, tile, status);
+    if (!fe.ok) return;
+    a = fe.a;
+    b = fe.b;
+    pos = fe.pos;
     const int4 va = __ldg(m.tvid + a), vb = __ldg(m.tvid + b);
     if (touching(va, vb)) {
         // near field: the touching table's value; a touching pair in a coupling
@@ -450,10 +443,20 @@ struct LearnedArgs {
     float conf;                  // confidence level of the cumulative class probability
     unsigned char *cls;          // per tile slot: class (255 = no regular pair)
     int *counts;                 // [kClasses]
-    int *fill;                   // [kClasses]
     int64_t *offs;               // [kClasses + 1]
     int4 *rec;                   // records: (pos lo, pos hi, a, b)
+    int *tcount;                 // [kClasses][ntile]: per tile, then its exclusive offset in the class
+    int64_t ntile;               // tiles the scratch holds
 };
+
+// Tiles of a learned job: the list's entries in flat tiles of kP0Tile, at most
+// the scratch's capacity (a list that outgrew it is reported by the selection).
+__device__ __forceinline__ int64_t learned_tiles(const BlockLaunch &L, const int64_t *prefix,
+                                                 int64_t cap)
+{
+    const int64_t t = L.n_blocks > 0 ? (prefix[L.n_blocks - 1] + kP0Tile - 1) / kP0Tile : 0;
+    return t < cap ? t : cap;
+}
 
 __global__ void __launch_bounds__(256, 2) k_learned_select(MeshView m, BlockLaunch L,
                                                            const int64_t *__restrict__ prefix,
@@ -461,9 +464,14 @@ __global__ void __launch_bounds__(256, 2) k_learned_select(MeshView m, BlockLaun
 {
     __shared__ float xs[8][2][16][8];
     __shared__ MlpFrag F;
+    __shared__ int wcount[8][kClasses];
     mlp_stage(A.P, F);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
+    // prefix counts entries; a tile is kP0Tile of them
+    const int64_t total = learned_tiles(L, prefix, A.ntile);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && L.n_blocks > 0 &&
+        (prefix[L.n_blocks - 1] + kP0Tile - 1) / kP0Tile > A.ntile)
+        set_status(status, BEM_ERR_INVALID_ARG);   // the lists outgrew the scratch
     for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
         int a = 0, b = 0, state = 0;
         int64_t pos = 0;
@@ -518,14 +526,53 @@ __global__ void __launch_bounds__(256, 2) k_learned_select(MeshView m, BlockLaun
                 }
             }
         }
-        // class counts: one atomic per class and warp
+        // the tile's class counts (no atomics: a scan over the tiles follows)
 #pragma unroll
         for (int cc = 0; cc < kClasses; ++cc) {
             const unsigned mk = __ballot_sync(0xffffffffu, cls == cc);
-            if (mk && lane == 0) atomicAdd(&A.counts[cc], __popc(mk));
+            if (lane == 0) wcount[w][cc] = __popc(mk);
         }
         A.cls[tile * 256 + threadIdx.x] = (unsigned char)cls;
+        __syncthreads();
+        if (threadIdx.x < kClasses) {
+            int n = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) n += wcount[k][threadIdx.x];
+            A.tcount[threadIdx.x * A.ntile + tile] = n;
+        }
+        __syncthreads();   // wcount is rewritten by the next tile
     }
+}
+
+// Per class (one CTA each): the exclusive scan of the tiles' counts in place,
+// and the class total.
+__global__ void __launch_bounds__(1024) k_learned_scan(BlockLaunch L,
+                                                       const int64_t *__restrict__ prefix,
+                                                       LearnedArgs A)
+{
+    __shared__ int part[1024];
+    const int c = blockIdx.x;
+    const int64_t n = learned_tiles(L, prefix, A.ntile);
+    int *t = A.tcount + c * A.ntile;
+    const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = min(n, (int64_t)threadIdx.x * chunk), hi = min(n, lo + chunk);
+    int sum = 0;
+    for (int64_t k = lo; k < hi; ++k) sum += t[k];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
+    for (int64_t k = lo; k < hi; ++k) {
+        const int v = t[k];
+        t[k] = run;
+        run += v;
+    }
+    if (threadIdx.x == blockDim.x - 1) A.counts[c] = part[threadIdx.x];
 }
 
 __global__ void k_learned_offsets(LearnedArgs A)
@@ -535,44 +582,47 @@ __global__ void k_learned_offsets(LearnedArgs A)
         for (int c = 0; c < kClasses; ++c) {
             A.offs[c] = s;
             s += A.counts[c];
-            A.fill[c] = 0;
         }
         A.offs[kClasses] = s;
     }
 }
 
+// Records by class at the scanned offsets: tile offset (k_learned_scan) +
+// the counts of the tile's earlier warps + the lane's rank in its warp, so
+// the records of a class come in entry order and no atomics are needed.
 __global__ void __launch_bounds__(256) k_learned_compact(MeshView m, BlockLaunch L,
                                                          const int64_t *__restrict__ prefix,
                                                          LearnedArgs A)
 {
-    const int64_t total = L.n_blocks > 0 ? prefix[L.n_blocks - 1] : 0;
-    const int lane = threadIdx.x & 31;
+    __shared__ int wcount[8][kClasses];
+    const int64_t total = learned_tiles(L, prefix, A.ntile);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
         // the loop is uniform across the CTA: every warp takes part in the ballots
         const int cls = A.cls[tile * 256 + threadIdx.x];
-        const unsigned any = __ballot_sync(0xffffffffu, cls < kClasses);
-        if (!any) continue;
-        const BlockInfo bi = block_info(L, prefix, tile, nullptr);
-        const int lr = threadIdx.x & 31, lc = threadIdx.x >> 5;
-        const int ntr = (bi.nr + kTile - 1) / kTile;
-        const int r = (bi.tile_in_blk % ntr) * kTile + lr;
-        const int c = (bi.tile_in_blk / ntr) * kP0Cols + lc;
-        // slots within the class: one atomic per class and warp, lanes in order
+        unsigned mk[kClasses];
 #pragma unroll
         for (int cc = 0; cc < kClasses; ++cc) {
-            const unsigned mk = __ballot_sync(0xffffffffu, cls == cc);
-            if (!mk) continue;
-            const int leader = __ffs(mk) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(&A.fill[cc], __popc(mk));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (cls == cc) {
-                const int64_t pos = bi.off + (int64_t)r + (int64_t)c * bi.nr;
-                const int k = base + __popc(mk & ((1u << lane) - 1u));
-                A.rec[A.offs[cc] + k] = make_int4((int)(pos & 0xffffffff), (int)(pos >> 32),
-                                                  L.row_idx[bi.r_lo + r], L.col_idx[bi.c_lo + c]);
+            mk[cc] = __ballot_sync(0xffffffffu, cls == cc);
+            if (lane == 0) wcount[w][cc] = __popc(mk[cc]);
+        }
+        __syncthreads();
+        if (__ballot_sync(0xffffffffu, cls < kClasses)) {
+            // the selection pass already checked the indices (status not set twice)
+            const FlatEntry fe = flat_entry(m, L, prefix, tile, nullptr);
+            if (cls < kClasses) {
+                int k = A.tcount[cls * A.ntile + tile];
+                for (int v = 0; v < w; ++v) k += wcount[v][cls];
+                unsigned mine = 0;
+#pragma unroll
+                for (int cc = 0; cc < kClasses; ++cc)
+                    if (cls == cc) mine = mk[cc];
+                k += __popc(mine & ((1u << lane) - 1u));
+                A.rec[A.offs[cls] + k] = make_int4((int)(fe.pos & 0xffffffff), (int)(fe.pos >> 32),
+                                                   fe.a, fe.b);
             }
         }
+        __syncthreads();   // wcount is rewritten by the next tile
     }
 }
 
@@ -1340,10 +1390,12 @@ namespace bem {
 // grouped by class, counters and class offsets.
 cudaError_t learned_alloc(LearnedScratch &S, int64_t tiles)
 {
-    const int64_t slots = std::max<int64_t>(1, tiles * 256);
+    tiles = std::max<int64_t>(1, tiles);
+    const int64_t slots = tiles * kP0Tile;
     cudaError_t e = cudaMalloc((void **)&S.cls, slots);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S.rec, slots * sizeof(int4));
     if (e == cudaSuccess) e = cudaMalloc((void **)&S.small, 64 * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S.tcount, tiles * kClasses * sizeof(int));
     if (e == cudaSuccess) S.cap = slots;
     return e;
 }
@@ -1353,6 +1405,7 @@ void learned_free(LearnedScratch &S)
     cudaFree(S.cls);
     cudaFree(S.rec);
     cudaFree(S.small);
+    cudaFree(S.tcount);
     S = LearnedScratch{};
 }
 
@@ -1373,8 +1426,9 @@ cudaError_t learned_launches(const MeshView &mv, const BlockLaunch &L, const int
     A.conf = conf;
     A.cls = S.cls;
     A.counts = reinterpret_cast<int *>(S.small);
-    A.fill = A.counts + 8;
     A.offs = S.small + 8;
+    A.tcount = S.tcount;
+    A.ntile = S.cap / kP0Tile;
     A.rec = reinterpret_cast<int4 *>(S.rec);
     cudaError_t e = cudaMemsetAsync(A.counts, 0, 16 * sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -1382,6 +1436,7 @@ cudaError_t learned_launches(const MeshView &mv, const BlockLaunch &L, const int
     {
         ProfScope ps(prof_ctx, "learned_select");
         k_learned_select<<<grid, 256, 0, st>>>(mv, L, prefix, A, status);
+        k_learned_scan<<<kClasses, 1024, 0, st>>>(L, prefix, A);
         k_learned_offsets<<<1, 32, 0, st>>>(A);
         k_learned_compact<<<grid, 256, 0, st>>>(mv, L, prefix, A);
     }
@@ -1449,12 +1504,13 @@ int run_learned_p0(bem_ctx *ctx, const MeshView &mv, const BlockLaunch &L, const
 {
     bem_mlp *model = ctx->order_model;
     if (!model) return api_fail(ctx, BEM_ERR_INVALID_ARG, "order_mode LEARNED needs bem_set_order_model");
-    // the number of tiles sizes the scratch: one read back per call
-    int64_t tiles = 0;
-    cudaError_t e = cudaMemcpyAsync(&tiles, prefix + (L.n_blocks - 1), sizeof(int64_t),
+    // the number of entries sizes the scratch: one read back per call
+    int64_t entries = 0;
+    cudaError_t e = cudaMemcpyAsync(&entries, prefix + (L.n_blocks - 1), sizeof(int64_t),
                                     cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned: tile count");
+    if (e != cudaSuccess) return api_cuda_fail(ctx, e, "learned: entry count");
+    const int64_t tiles = (entries + kP0Tile - 1) / kP0Tile;
     if (std::max<int64_t>(1, tiles * 256) > ctx->learned.cap) {
         learned_free(ctx->learned);
         e = learned_alloc(ctx->learned, tiles);

@@ -227,7 +227,7 @@ cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
     }
     for (auto &l : p->learned) {
         ev_begin();
-        e = launch_tile_prefix(l.L, kTile, kP0Cols, l.prefix, ctx->status, st);
+        e = launch_tile_prefix(l.L, 1, 1, l.prefix, ctx->status, st);
         if (e == cudaSuccess)
             e = learned_launches(l.m, l.L, l.prefix, p->model, p->conf, l.S, p->lrules, l.precision,
                                  ctx->num_sms, ctx->status, st, nullptr);
@@ -477,14 +477,14 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
             L.allow_touching = ji.near ? 1 : 0;
             L.mixed = is_mixed(J.quad.precision) ? 1 : 0;
             l.precision = J.quad.precision;
-            // the tile count sizes the job's scratch: one prefix pass now
-            int64_t tiles = 0;
+            // the entry count sizes the job's scratch: one prefix pass now
+            int64_t entries = 0;
             if ((e = plan_alloc(p, &l.prefix, (size_t)J.n_blocks)) != cudaSuccess ||
-                (e = launch_tile_prefix(L, kTile, kP0Cols, l.prefix, ctx->status, p->cap)) != cudaSuccess ||
-                (e = cudaMemcpyAsync(&tiles, l.prefix + (J.n_blocks - 1), sizeof(int64_t),
+                (e = launch_tile_prefix(L, 1, 1, l.prefix, ctx->status, p->cap)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(&entries, l.prefix + (J.n_blocks - 1), sizeof(int64_t),
                                      cudaMemcpyDeviceToHost, p->cap)) != cudaSuccess ||
                 (e = cudaStreamSynchronize(p->cap)) != cudaSuccess ||
-                (e = learned_alloc(l.S, tiles)) != cudaSuccess) {
+                (e = learned_alloc(l.S, (entries + kP0Tile - 1) / kP0Tile)) != cudaSuccess) {
                 learned_free(l.S);
                 plan_free(p);
                 return api_cuda_fail(ctx, e, "learned plan job");
