@@ -1647,6 +1647,23 @@ def measure_green(torch, pkg, ctx, mid, w, dev, stream, steps, warmup):
     return res, G
 
 
+def run_solves(args):
+    """The Section 4 solves alone (the H2 product and CG, the Brakhage-Werner
+    exterior problem), as they run under configs in the default line; one JSON
+    line with both results."""
+    import torch
+    import paper_1510_07244_gb300 as pkg
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = pkg.Context(0, stream)
+    out = {"workload": "solves", "H2_solve": measure_h2_solve(torch, pkg, ctx, dev, stream),
+           "BW_solve": measure_bw_solve(torch, pkg, ctx, dev, stream)}
+    ctx.close()
+    print(json.dumps(out))
+
+
 def run_green(args):
     """Green quadrature matrices A_t of the GCA (Section 2.3) on the device:
     one bem_green_matrices launch per step over every cluster of the
@@ -2122,7 +2139,7 @@ def main():
     ap.add_argument("--pivots", default="gca", choices=["gca", "seeded"],
                     help="coupling pivots from the host GCA (default) or seeded per cluster")
     ap.add_argument("--workload", default="all",
-                    choices=["all", "c2", "c3", "c4", "c5", "green"],
+                    choices=["all", "c2", "c3", "c4", "c5", "green", "solves"],
                     help="all (default): the C4 headline (48 meshes) with C1, C2, C3 and C5 "
                          "under 'configs'; c2: the 20480-triangle P1 line alone; c3 / c4: the "
                          "49152-triangle Helmholtz cube / the 48-mesh batch alone; c5: learned "
@@ -2162,6 +2179,8 @@ def main():
         run_c5(args)
     elif args.workload == "green":
         run_green(args)
+    elif args.workload == "solves":
+        run_solves(args)
     elif args.workload != "c2":
         run_extra(args)
     else:

@@ -442,6 +442,126 @@ __device__ __forceinline__ void helm_rotate(const HelmPhase &P, float sr, float 
     im = P.s0 * sr + P.c0 * si;
 }
 
+// Packed FP32 pairs (sm_100 and later): sub/add/mul/fma .f32x2 apply the scalar
+// operation, with its rounding, to both halves of a 64-bit register pair in
+// one instruction.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// The float Helmholtz pair of regular_p0_f32_helm with two trial points per
+// packed instruction: the same operations per point (helm_offset), each rounded
+// as there; the reciprocal square roots, sines and cosines stay scalar.  The
+// inner sums run as two partial sums (even and odd trial points) added per
+// test point; an odd rule's last pair repeats its last point with weight 0.
+template <int NP>
+__device__ __forceinline__ void regular_p0_f32_helm_x2(const TriF &A, const TriF &B,
+                                                       const Rule2D &R, double kappa,
+                                                       float &out_re, float &out_im)
+{
+    constexpr int NQ = (NP + 1) / 2;
+    const HelmPhase P = helm_phase(A, B, kappa);
+    f32x2 yx[NQ], yy[NQ], yz[NQ], w2[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int j0 = 2 * q, j1 = 2 * q + 1 < NP ? 2 * q + 1 : NP - 1;
+        const float a0 = R.sf[j0] - 0.666666687f, b0 = R.tf[j0] - 0.333333343f;
+        const float a1 = R.sf[j1] - 0.666666687f, b1 = R.tf[j1] - 0.333333343f;
+        yx[q] = f2_pack(fmaf(a0, B.e1[0], b0 * B.e2[0]), fmaf(a1, B.e1[0], b1 * B.e2[0]));
+        yy[q] = f2_pack(fmaf(a0, B.e1[1], b0 * B.e2[1]), fmaf(a1, B.e1[1], b1 * B.e2[1]));
+        yz[q] = f2_pack(fmaf(a0, B.e1[2], b0 * B.e2[2]), fmaf(a1, B.e1[2], b1 * B.e2[2]));
+        w2[q] = f2_pack(R.wf[j0], 2 * q + 1 < NP ? R.wf[j1] : 0.0f);
+    }
+    const f32x2 tdx = f2_pack(2.0f * P.dcx, 2.0f * P.dcx), tdy = f2_pack(2.0f * P.dcy, 2.0f * P.dcy),
+                tdz = f2_pack(2.0f * P.dcz, 2.0f * P.dcz);
+    const f32x2 r0sqh = f2_pack(P.r0sqh, P.r0sqh), nr0sqh = f2_pack(-P.r0sqh, -P.r0sqh),
+                r0sql = f2_pack(P.r0sql, P.r0sql), r0h = f2_pack(P.r0h, P.r0h),
+                m2r0l = f2_pack(P.m2r0l, P.m2r0l), kap = f2_pack(P.kap, P.kap),
+                half = f2_pack(0.5f, 0.5f);
+    float sr = 0.0f, si = 0.0f, cr = 0.0f, ci = 0.0f;
+#pragma unroll 1
+    for (int i = 0; i < NP; ++i) {
+        const float a = R.sf[i] - 0.666666687f, b = R.tf[i] - 0.333333343f;
+        const float xx = fmaf(a, A.e1[0], b * A.e2[0]);
+        const float xy = fmaf(a, A.e1[1], b * A.e2[1]);
+        const float xz = fmaf(a, A.e1[2], b * A.e2[2]);
+        const f32x2 X = f2_pack(xx, xx), Y = f2_pack(xy, xy), Z = f2_pack(xz, xz);
+        f32x2 ir = f2_pack(0.0f, 0.0f), ii = ir;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const f32x2 ex = f2_sub(X, yx[q]), ey = f2_sub(Y, yy[q]), ez = f2_sub(Z, yz[q]);
+            // q = (2 d_c + e) . e, r^2 = r0^2 + q (helm_offset)
+            const f32x2 qq = f2_fma(f2_add(tdx, ex), ex,
+                                    f2_fma(f2_add(tdy, ey), ey, f2_mul(f2_add(tdz, ez), ez)));
+            const f32x2 r2 = f2_add(r0sqh, qq);
+            float r2a, r2b;
+            f2_unpack(r2, r2a, r2b);
+            const f32x2 ri = f2_pack(rsqrt_fast(r2a), rsqrt_fast(r2b));
+            const f32x2 ra = f2_mul(r2, ri);
+            // (r0sq_hi - ra^2) + (q + r0sq_lo), with ra^2 - r0sq_hi from one FMA
+            const f32x2 res = f2_sub(f2_add(qq, r0sql), f2_fma(ra, ra, nr0sqh));
+            const f32x2 delta = f2_fma(half, f2_fma(res, ri, m2r0l), f2_sub(ra, r0h));
+            float ta, tb;
+            f2_unpack(f2_mul(kap, delta), ta, tb);
+            float sa, ca, sb, cb;
+            __sincosf(ta, &sa, &ca);
+            __sincosf(tb, &sb, &cb);
+            const f32x2 wr = f2_mul(w2[q], ri);
+            ir = f2_fma(f2_pack(ca, cb), wr, ir);
+            ii = f2_fma(f2_pack(sa, sb), wr, ii);
+        }
+        float ir0, ir1, ii0, ii1;
+        f2_unpack(ir, ir0, ir1);
+        f2_unpack(ii, ii0, ii1);
+        // compensated outer sums
+        float y = fmaf(R.wf[i], ir0 + ir1, -cr), t = sr + y;
+        cr = (t - sr) - y;
+        sr = t;
+        y = fmaf(R.wf[i], ii0 + ii1, -ci);
+        t = si + y;
+        ci = (t - si) - y;
+        si = t;
+    }
+    float re, im;
+    helm_rotate(P, sr, si, re, im);
+    const float sc = A.sg * B.sg * (float)kInv4Pi;
+    out_re = re * sc;
+    out_im = im * sc;
+}
+
 // Regular pair, piecewise constant, Helmholtz single layer, float.
 template <int NP>
 __device__ __forceinline__ void regular_p0_f32_helm(const TriF &A, const TriF &B, const Rule2D &R,
@@ -1395,7 +1515,7 @@ __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L,
         load_trif(m.geomf, bb, B);
         if (KIND == BEM_HELMHOLTZ_SLP) {
             float fr, fi;
-            regular_p0_f32_helm<NP>(A, B, R, L.kappa, fr, fi);
+            regular_p0_f32_helm_x2<NP>(A, B, R, L.kappa, fr, fi);
             re = (double)fr;
             im = (double)fi;
         } else if (guard) {

@@ -10,7 +10,8 @@
 //   coupling y^_t = sum_s S_ts x^_s               one CTA per cluster
 //   backward (y^_t1; y^_t2) += V^_t y^_t, y|t += V_t y^_t (leaf), top level first
 // Every output element is written by one lane in a fixed order (no atomics),
-// so products are bitwise reproducible.  All arithmetic is FP64.  The matrix
+// so products are bitwise reproducible.  The near field runs on a second
+// stream beside the forward and coupling passes.  All arithmetic is FP64.  The matrix
 // is memory- and latency-bound: per product it reads every near-field and
 // coupling entry once (8 bytes each) and does 2 flops per entry.
 #include <cuda_runtime.h>
@@ -34,6 +35,7 @@ struct bem_h2 {
     int32_t *leaf = nullptr;       // 1 for leaves
     int32_t *src = nullptr;        // row sources: vector index (leaf) or hat index (else)
     double *vals = nullptr;        // basis matrices
+    double *valsT = nullptr;       // the same, each transposed (K_c x R_c row-major)
     // near blocks by leaf row cluster (CSR over nc), far blocks by row cluster
     int32_t *near_ptr = nullptr, *near_col = nullptr;
     int64_t *near_off = nullptr;
@@ -52,6 +54,10 @@ struct bem_h2 {
     double *diag = nullptr;        // added to the diagonal (null: none)
     // conjugate gradients: vectors and scalars
     double *r = nullptr, *p = nullptr, *q = nullptr, *part = nullptr, *scal = nullptr;
+    // the near field runs on a second stream beside the forward and coupling
+    // passes (it writes y, the backward pass then adds to it)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace bem {
@@ -70,7 +76,7 @@ __device__ __forceinline__ double warp_sum_d(double v)
 struct H2View {
     const int32_t *rows, *rank, *leaf, *src;
     const int64_t *v_off, *src_off, *hat_off;
-    const double *vals;
+    const double *vals, *valsT;
     const int32_t *near_ptr, *near_col, *far_ptr, *far_col, *cl_ptr, *cl_idx;
     const int64_t *near_off, *far_off;
     const double *near_vals, *far_vals;
@@ -115,22 +121,35 @@ __global__ void __launch_bounds__(256) k_h2_near(H2View H, const int32_t *leaves
 }
 
 // forward transformation of one level: x^_c = V_c^T v, v = x at the leaf's
-// indices or the sons' x^ entries; lane k = column k (K_c <= 32)
+// indices or the sons' x^ entries.  One CTA per cluster: lane k = column k
+// (K_c <= 32), the 8 warps take every 8th row, and their partial sums are
+// added in warp order (fixed, so the result is reproducible).  A level is
+// latency-bound (a few rows per warp), so the rows are spread over warps.
 __global__ void __launch_bounds__(256) k_h2_forward(H2View H, const int32_t *level, int n,
                                                     const double *__restrict__ x, double *xhat)
 {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (w >= n) return;
-    const int c = level[w];
+    __shared__ double part[kH2Warps][32];
+    const int c = level[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = H.rows[c], K = H.rank[c];
-    if (K == 0) return;
+    if (K == 0) return;                 // uniform across the CTA
     const double *V = H.vals + H.v_off[c];
     const int32_t *src = H.src + H.src_off[c];
     const double *v = H.leaf[c] ? x : xhat;
     double acc = 0.0;
-    if (lane < K)
-        for (int i = 0; i < R; ++i) acc = fma(V[(int64_t)i * K + lane], v[src[i]], acc);
-    if (lane < K) xhat[H.hat_off[c] + lane] = acc;
+    if (lane < K) {
+#pragma unroll 4
+        for (int i = warp; i < R; i += kH2Warps)
+            acc = fma(V[(int64_t)i * K + lane], __ldg(v + __ldg(src + i)), acc);
+    }
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && lane < K) {
+        double sum = 0.0;
+#pragma unroll
+        for (int k = 0; k < kH2Warps; ++k) sum += part[k][lane];
+        xhat[H.hat_off[c] + lane] = sum;
+    }
 }
 
 // coupling: y^_t = sum over t's admissible blocks of S_ts x^_s (column-major
@@ -164,25 +183,39 @@ __global__ void __launch_bounds__(256) k_h2_coupling(H2View H, int nc, const dou
     }
 }
 
-// backward transformation of one level: every row i of V_c (lane per row)
-// adds (V_c y^_c)_i to its target: the vector y at a leaf's index, the son's
-// y^ entry otherwise
+// backward transformation of one level: every row i of V_c adds (V_c y^_c)_i
+// to its target, the vector y at a leaf's index, the son's y^ entry otherwise.
+// One CTA per cluster; rows of at most 64 take four threads each (columns
+// k = part mod 4, combined by two fixed shuffles), longer ones one thread per
+// row.  The transposed basis makes consecutive rows consecutive words.
 __global__ void __launch_bounds__(256) k_h2_backward(H2View H, const int32_t *level, int n,
                                                      double *yhat, double *y)
 {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (w >= n) return;
-    const int c = level[w];
+    const int c = level[blockIdx.x];
     const int R = H.rows[c], K = H.rank[c];
-    if (K == 0) return;
-    const double *V = H.vals + H.v_off[c];
+    if (K == 0) return;                 // uniform across the CTA
+    const double *VT = H.valsT + H.v_off[c];
     const int32_t *src = H.src + H.src_off[c];
     const double *yc = yhat + H.hat_off[c];
     double *dst = H.leaf[c] ? y : yhat;
-    for (int i = lane; i < R; i += 32) {
+    if (R <= 64) {
+        const int i = threadIdx.x >> 2, part = threadIdx.x & 3;
         double acc = 0.0;
-        for (int k = 0; k < K; ++k) acc = fma(V[(int64_t)i * K + k], yc[k], acc);
-        dst[src[i]] += acc;
+        if (i < R) {
+#pragma unroll 4
+            for (int k = part; k < K; k += 4) acc = fma(VT[(int64_t)k * R + i], yc[k], acc);
+        }
+        // the four parts of a row sit in four consecutive lanes
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (i < R && part == 0) dst[src[i]] += acc;
+    } else {
+        for (int i = threadIdx.x; i < R; i += blockDim.x) {
+            double acc = 0.0;
+#pragma unroll 8
+            for (int k = 0; k < K; ++k) acc = fma(VT[(int64_t)k * R + i], yc[k], acc);
+            dst[src[i]] += acc;
+        }
     }
 }
 
@@ -255,6 +288,7 @@ H2View view(const bem_h2 *h)
     v.src_off = h->src_off;
     v.hat_off = h->hat_off;
     v.vals = h->vals;
+    v.valsT = h->valsT;
     v.near_ptr = h->near_ptr;
     v.near_col = h->near_col;
     v.near_off = h->near_off;
@@ -269,21 +303,24 @@ H2View view(const bem_h2 *h)
     return v;
 }
 
-unsigned warps_grid(int64_t warps) { return (unsigned)((warps * 32 + 255) / 256); }
 
 cudaError_t matvec(const bem_h2 *h, const double *x, double *y, cudaStream_t st)
 {
     const H2View H = view(h);
-    if (h->n_leaves > 0) k_h2_near<<<h->n_leaves, 256, 0, st>>>(H, h->leaves, h->n_leaves, x, y);
+    // fork: the near field on the side stream, joined before the backward pass
+    cudaError_t e = cudaEventRecord(h->fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->fork, 0);
+    if (e != cudaSuccess) return e;
+    if (h->n_leaves > 0) k_h2_near<<<h->n_leaves, 256, 0, h->side>>>(H, h->leaves, h->n_leaves, x, y);
+    if ((e = cudaEventRecord(h->join, h->side)) != cudaSuccess) return e;
     for (int d = (int)h->level.size() - 1; d >= 0; --d)
         if (h->level_n[d] > 0)
-            k_h2_forward<<<warps_grid(h->level_n[d]), 256, 0, st>>>(H, h->level[d], h->level_n[d],
-                                                                     x, h->xhat);
+            k_h2_forward<<<h->level_n[d], 256, 0, st>>>(H, h->level[d], h->level_n[d], x, h->xhat);
     k_h2_coupling<<<h->nc, 256, 0, st>>>(H, h->nc, h->xhat, h->yhat);
+    if ((e = cudaStreamWaitEvent(st, h->join, 0)) != cudaSuccess) return e;
     for (size_t d = 0; d < h->level.size(); ++d)
         if (h->level_n[d] > 0)
-            k_h2_backward<<<warps_grid(h->level_n[d]), 256, 0, st>>>(H, h->level[d], h->level_n[d],
-                                                                      h->yhat, y);
+            k_h2_backward<<<h->level_n[d], 256, 0, st>>>(H, h->level[d], h->level_n[d], h->yhat, y);
     return cudaGetLastError();
 }
 
@@ -315,6 +352,9 @@ cudaError_t h2_alloc(bem_h2 *h, T **d, size_t n)
 void h2_free(bem_h2 *h)
 {
     for (void *a : h->allocs) cudaFree(a);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
+    if (h->side) cudaStreamDestroy(h->side);
     delete h;
 }
 
@@ -442,11 +482,19 @@ int bem_h2_create(bem_ctx *ctx, int64_t n, int32_t n_clusters, const int32_t *cl
     cudaSetDevice(ctx->device);
     cudaError_t e = cudaSuccess;
     std::vector<int32_t> cp(cl_ptr, cl_ptr + nc + 1), ci(cl_idx, cl_idx + cl_ptr[nc]);
-    std::vector<double> vals(V, V + v_off[nc]);
+    std::vector<double> vals(V, V + v_off[nc]), valsT(vals.size());
+    for (int c = 0; c < nc; ++c)
+        for (int i = 0; i < rows[c]; ++i)
+            for (int k = 0; k < rank[c]; ++k)
+                valsT[voff[c] + (int64_t)k * rows[c] + i] = vals[voff[c] + (int64_t)i * rank[c] + k];
     if ((e = h2_upload(h, &h->rows, rows)) || (e = h2_upload(h, &h->rank, rank)) ||
         (e = h2_upload(h, &h->leaf, leaf)) || (e = h2_upload(h, &h->src, src)) ||
         (e = h2_upload(h, &h->v_off, voff)) || (e = h2_upload(h, &h->src_off, soff)) ||
         (e = h2_upload(h, &h->hat_off, hoff)) || (e = h2_upload(h, &h->vals, vals)) ||
+        (e = h2_upload(h, &h->valsT, valsT)) ||
+        (e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming)) ||
         (e = h2_upload(h, &h->near_ptr, nptr)) || (e = h2_upload(h, &h->near_col, ncol)) ||
         (e = h2_upload(h, &h->near_off, noff)) || (e = h2_upload(h, &h->far_ptr, fptr)) ||
         (e = h2_upload(h, &h->far_col, fcol)) || (e = h2_upload(h, &h->far_off, foff)) ||
