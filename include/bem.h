@@ -306,10 +306,18 @@ int bem_learned_counts(bem_ctx *ctx, int64_t *counts /* [6] */);
  *                             (cached in the context);
  *          BEM_PLAN_PROFILE   record launch-profiling events in the plan
  *                             (read with bem_profile_read while profiling is
- *                             enabled).
+ *                             enabled);
+ *          BEM_PLAN_STATIC_LISTS  the index lists' contents (cluster lists,
+ *                             block lists) stay as they are at creation: the
+ *                             passes derived from them alone (tile prefix sums,
+ *                             piecewise-linear support records, a learned
+ *                             job's prefix sums) run once at creation and the
+ *                             runs issue only the quadrature and guard passes.
+ *                             Changing the lists afterwards gives wrong entries
+ *                             (the kernels still check every index).
  * The plan keeps the jobs' device pointers (index lists, outputs) and uses
  * the meshes' device data: both must stay valid until bem_plan_destroy; the
- * index lists' contents are read at every run.
+ * index lists' contents are read at every run (unless BEM_PLAN_STATIC_LISTS).
  * bem_plan_create runs the plan's kernels once (or several times when
  * autotuning), so outputs are written at creation too.  Results are the
  * same, bit for bit, as those of bem_near_field / bem_coupling_blocks.
@@ -338,6 +346,7 @@ typedef struct bem_plan bem_plan;
 #define BEM_PLAN_GRAPH    1
 #define BEM_PLAN_AUTOTUNE 2
 #define BEM_PLAN_PROFILE  4
+#define BEM_PLAN_STATIC_LISTS 8
 int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near,
                     const bem_block_job *coupling_jobs, int32_t n_coupling, int32_t flags,
                     bem_plan **plan);

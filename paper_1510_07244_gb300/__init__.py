@@ -8,12 +8,12 @@ inputs live in the separate ``synth`` package.
 """
 from ._binding import (Context, BlockJob, GreenJob, BemError, kernel_desc, quad_desc, load,
                        LIB_PATH, EXPORTS, KERNELS, BASES, RULES, bem_rule_points, bem_rule_points_xi, PLAN_GRAPH,
-                       PLAN_AUTOTUNE, PLAN_PROFILE, ORDER_CLASSES,
+                       PLAN_AUTOTUNE, PLAN_PROFILE, PLAN_STATIC_LISTS, ORDER_CLASSES,
                        ORDER_CLASS_POINTS, bem_shard_blocks, bem_gca_pivots,
                        bem_touching_pairs, bem_gca_bases)
 
 __all__ = ["Context", "BlockJob", "GreenJob", "BemError", "kernel_desc", "quad_desc", "load",
            "LIB_PATH", "EXPORTS", "KERNELS", "BASES", "RULES", "bem_rule_points", "bem_rule_points_xi",
-           "PLAN_GRAPH", "PLAN_AUTOTUNE", "PLAN_PROFILE", "ORDER_CLASSES",
+           "PLAN_GRAPH", "PLAN_AUTOTUNE", "PLAN_PROFILE", "PLAN_STATIC_LISTS", "ORDER_CLASSES",
            "ORDER_CLASS_POINTS", "bem_shard_blocks", "bem_gca_pivots",
            "bem_touching_pairs", "bem_gca_bases"]

@@ -41,7 +41,7 @@ EXPORTS = ["bem_create", "bem_destroy", "bem_last_error", "bem_sync", "bem_mesh_
            "bem_rule_points_xi"]
 ORDER_CLASSES = [("duffy", 2), ("tri7", 1), ("duffy", 4), ("duffy", 5), ("duffy", 6), ("duffy", 8)]
 ORDER_CLASS_POINTS = [16, 49, 256, 625, 1296, 4096]
-PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE = 1, 2, 4
+PLAN_GRAPH, PLAN_AUTOTUNE, PLAN_PROFILE, PLAN_STATIC_LISTS = 1, 2, 4, 8
 
 
 class BemError(RuntimeError):

@@ -376,6 +376,7 @@ int api_check_job(bem_ctx *ctx, const bem_block_job &J, Rule2D &r2, Mesh **mesh)
 
 void prof_accumulate(bem_ctx *ctx, const bem_prof_rec &r)
 {
+    if (r.skipped) return;
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, r.a, r.b);
     auto &t = ctx->prof_total[r.name];

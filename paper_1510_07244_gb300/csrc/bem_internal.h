@@ -95,7 +95,7 @@ struct LearnedScratch {
     unsigned char *cls = nullptr;   // class per entry slot (cap slots)
     void *rec = nullptr;            // records by class (cap int4)
     int64_t *small = nullptr;       // class counts and offsets
-    int *tcount = nullptr;          // per class and tile: count, then scanned offset
+    int *tcount = nullptr;          // per class and tile warp: count, then scanned offset
     int64_t cap = 0;                // entry slots: a multiple of the flat tile
 };
 
@@ -115,6 +115,7 @@ struct Mesh {
 struct bem_prof_rec {
     std::string name;
     cudaEvent_t a, b;
+    bool skipped = false;   // a launch group the runs do not issue (static plans)
 };
 
 struct bem_ctx {

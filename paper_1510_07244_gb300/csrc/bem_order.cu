@@ -445,7 +445,7 @@ struct LearnedArgs {
     int *counts;                 // [kClasses]
     int64_t *offs;               // [kClasses + 1]
     int4 *rec;                   // records: (pos lo, pos hi, a, b)
-    int *tcount;                 // [kClasses][ntile]: per tile, then its exclusive offset in the class
+    int *tcount;                 // [kClasses][8 ntile]: per warp of a tile, then its exclusive offset in the class
     int64_t ntile;               // tiles the scratch holds
 };
 
@@ -464,7 +464,6 @@ __global__ void __launch_bounds__(256, 2) k_learned_select(MeshView m, BlockLaun
 {
     __shared__ float xs[8][2][16][8];
     __shared__ MlpFrag F;
-    __shared__ int wcount[8][kClasses];
     mlp_stage(A.P, F);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // prefix counts entries; a tile is kP0Tile of them
@@ -526,53 +525,104 @@ __global__ void __launch_bounds__(256, 2) k_learned_select(MeshView m, BlockLaun
                 }
             }
         }
-        // the tile's class counts (no atomics: a scan over the tiles follows)
+        // the warp's class counts (no atomics and no barrier: a scan over the
+        // tiles' warps follows)
 #pragma unroll
         for (int cc = 0; cc < kClasses; ++cc) {
             const unsigned mk = __ballot_sync(0xffffffffu, cls == cc);
-            if (lane == 0) wcount[w][cc] = __popc(mk);
+            if (lane == 0) A.tcount[cc * 8 * A.ntile + tile * 8 + w] = __popc(mk);
         }
         A.cls[tile * 256 + threadIdx.x] = (unsigned char)cls;
-        __syncthreads();
-        if (threadIdx.x < kClasses) {
-            int n = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) n += wcount[k][threadIdx.x];
-            A.tcount[threadIdx.x * A.ntile + tile] = n;
-        }
-        __syncthreads();   // wcount is rewritten by the next tile
     }
 }
 
-// Per class (one CTA each): the exclusive scan of the tiles' counts in place,
-// and the class total.
-__global__ void __launch_bounds__(1024) k_learned_scan(BlockLaunch L,
-                                                       const int64_t *__restrict__ prefix,
-                                                       LearnedArgs A)
+// Exclusive scan of the warps' class counts (8 per tile, in entry order) in
+// place, per class, in kScanSeg segments: segment sums (one CTA per class and
+// segment, coalesced), the segments' offsets and the class totals (one warp
+// per class), then each segment rescanned with its offset in chunks of 256
+// (warp shuffles and the chunk's warp totals).  Integer sums, so the order of
+// the additions does not matter.
+constexpr int kScanSeg = 64;
+
+__device__ __forceinline__ int64_t scan_len(const BlockLaunch &L, const int64_t *prefix,
+                                            const LearnedArgs &A)
 {
-    __shared__ int part[1024];
-    const int c = blockIdx.x;
-    const int64_t n = learned_tiles(L, prefix, A.ntile);
-    int *t = A.tcount + c * A.ntile;
-    const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
-    const int64_t lo = min(n, (int64_t)threadIdx.x * chunk), hi = min(n, lo + chunk);
+    return 8 * learned_tiles(L, prefix, A.ntile);
+}
+
+__global__ void __launch_bounds__(256) k_learned_seg_sum(BlockLaunch L,
+                                                         const int64_t *__restrict__ prefix,
+                                                         LearnedArgs A, int *seg)
+{
+    __shared__ int ws[8];
+    const int c = blockIdx.x / kScanSeg, g = blockIdx.x % kScanSeg;
+    const int64_t n = scan_len(L, prefix, A), len = (n + kScanSeg - 1) / kScanSeg;
+    const int64_t lo = min(n, g * len), hi = min(n, lo + len);
+    const int *t = A.tcount + c * 8 * A.ntile;
     int sum = 0;
-    for (int64_t k = lo; k < hi; ++k) sum += t[k];
-    part[threadIdx.x] = sum;
+    for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) sum += t[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sum;
     __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int k = 0; k < 8; ++k) s += ws[k];
+        seg[blockIdx.x] = s;
+    }
+}
+
+// one warp per class: exclusive offsets of the segments, and the class total
+__global__ void k_learned_seg_off(LearnedArgs A, int *seg)
+{
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (c >= kClasses) return;
+    int run = 0;
+    for (int g0 = 0; g0 < kScanSeg; g0 += 32) {
+        const int v = seg[c * kScanSeg + g0 + lane];
+        int x = v;   // inclusive warp scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        seg[c * kScanSeg + g0 + lane] = run + x - v;
+        run += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) A.counts[c] = run;
+}
+
+__global__ void __launch_bounds__(256) k_learned_seg_apply(BlockLaunch L,
+                                                           const int64_t *__restrict__ prefix,
+                                                           LearnedArgs A, const int *seg)
+{
+    __shared__ int ws[8];
+    __shared__ int carry;
+    const int c = blockIdx.x / kScanSeg, g = blockIdx.x % kScanSeg;
+    const int64_t n = scan_len(L, prefix, A), len = (n + kScanSeg - 1) / kScanSeg;
+    const int64_t lo = min(n, g * len), hi = min(n, lo + len);
+    int *t = A.tcount + c * 8 * A.ntile;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = seg[blockIdx.x];
+    __syncthreads();
+    for (int64_t k0 = lo; k0 < hi; k0 += blockDim.x) {
+        const int64_t k = k0 + threadIdx.x;
+        const int v = k < hi ? t[k] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[w] = x;
         __syncthreads();
-        part[threadIdx.x] += v;
+        int before = carry;
+        for (int k2 = 0; k2 < w; ++k2) before += ws[k2];
+        if (k < hi) t[k] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + x;
         __syncthreads();
     }
-    int run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
-    for (int64_t k = lo; k < hi; ++k) {
-        const int v = t[k];
-        t[k] = run;
-        run += v;
-    }
-    if (threadIdx.x == blockDim.x - 1) A.counts[c] = part[threadIdx.x];
 }
 
 __global__ void k_learned_offsets(LearnedArgs A)
@@ -587,42 +637,33 @@ __global__ void k_learned_offsets(LearnedArgs A)
     }
 }
 
-// Records by class at the scanned offsets: tile offset (k_learned_scan) +
-// the counts of the tile's earlier warps + the lane's rank in its warp, so
-// the records of a class come in entry order and no atomics are needed.
+// Records by class at the scanned offsets: the warp's offset (k_learned_scan)
+// + the lane's rank in its warp, so the records of a class come in entry order
+// and no atomics or barriers are needed.
 __global__ void __launch_bounds__(256) k_learned_compact(MeshView m, BlockLaunch L,
                                                          const int64_t *__restrict__ prefix,
                                                          LearnedArgs A)
 {
-    __shared__ int wcount[8][kClasses];
     const int64_t total = learned_tiles(L, prefix, A.ntile);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        // the loop is uniform across the CTA: every warp takes part in the ballots
         const int cls = A.cls[tile * 256 + threadIdx.x];
-        unsigned mk[kClasses];
+        // warp-uniform: flat_entry shuffles across the warp
+        if (!__ballot_sync(0xffffffffu, cls < kClasses)) continue;
+        unsigned mine = 0;
 #pragma unroll
         for (int cc = 0; cc < kClasses; ++cc) {
-            mk[cc] = __ballot_sync(0xffffffffu, cls == cc);
-            if (lane == 0) wcount[w][cc] = __popc(mk[cc]);
+            const unsigned mk = __ballot_sync(0xffffffffu, cls == cc);
+            if (cls == cc) mine = mk;
         }
-        __syncthreads();
-        if (__ballot_sync(0xffffffffu, cls < kClasses)) {
-            // the selection pass already checked the indices (status not set twice)
-            const FlatEntry fe = flat_entry(m, L, prefix, tile, nullptr);
-            if (cls < kClasses) {
-                int k = A.tcount[cls * A.ntile + tile];
-                for (int v = 0; v < w; ++v) k += wcount[v][cls];
-                unsigned mine = 0;
-#pragma unroll
-                for (int cc = 0; cc < kClasses; ++cc)
-                    if (cls == cc) mine = mk[cc];
-                k += __popc(mine & ((1u << lane) - 1u));
-                A.rec[A.offs[cls] + k] = make_int4((int)(fe.pos & 0xffffffff), (int)(fe.pos >> 32),
-                                                   fe.a, fe.b);
-            }
+        // the selection pass already checked the indices (status not set twice)
+        const FlatEntry fe = flat_entry(m, L, prefix, tile, nullptr);
+        if (cls < kClasses) {
+            const int k = A.tcount[cls * 8 * A.ntile + tile * 8 + w] +
+                          __popc(mine & ((1u << lane) - 1u));
+            A.rec[A.offs[cls] + k] = make_int4((int)(fe.pos & 0xffffffff), (int)(fe.pos >> 32),
+                                               fe.a, fe.b);
         }
-        __syncthreads();   // wcount is rewritten by the next tile
     }
 }
 
@@ -1394,8 +1435,9 @@ cudaError_t learned_alloc(LearnedScratch &S, int64_t tiles)
     const int64_t slots = tiles * kP0Tile;
     cudaError_t e = cudaMalloc((void **)&S.cls, slots);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S.rec, slots * sizeof(int4));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&S.small, 64 * sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&S.tcount, tiles * kClasses * sizeof(int));
+    // small: class counts (8 ints), offsets (8 + 1 int64), segment sums of the scan
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S.small, (16 + kClasses * kScanSeg) * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S.tcount, tiles * 8 * kClasses * sizeof(int));
     if (e == cudaSuccess) S.cap = slots;
     return e;
 }
@@ -1436,7 +1478,10 @@ cudaError_t learned_launches(const MeshView &mv, const BlockLaunch &L, const int
     {
         ProfScope ps(prof_ctx, "learned_select");
         k_learned_select<<<grid, 256, 0, st>>>(mv, L, prefix, A, status);
-        k_learned_scan<<<kClasses, 1024, 0, st>>>(L, prefix, A);
+        int *seg = reinterpret_cast<int *>(S.small + 16);   // kClasses * kScanSeg ints
+        k_learned_seg_sum<<<kClasses * kScanSeg, 256, 0, st>>>(L, prefix, A, seg);
+        k_learned_seg_off<<<1, 32 * kClasses, 0, st>>>(A, seg);
+        k_learned_seg_apply<<<kClasses * kScanSeg, 256, 0, st>>>(L, prefix, A, seg);
         k_learned_offsets<<<1, 32, 0, st>>>(A);
         k_learned_compact<<<grid, 256, 0, st>>>(mv, L, prefix, A);
     }

@@ -184,8 +184,11 @@ cudaError_t launch_bucket(bem_ctx *ctx, const BlockBucket &b, int mult, cudaStre
 // Issues the plan's launches on stream st (profiling events when prof != null).
 // Events recorded while the stream is being captured must be external record
 // nodes, or the graph only uses them for ordering and never records them.
+// structure: also issue the passes that only depend on the index lists (the
+// support records and the tile prefix sums); static plans skip them after
+// creation.
 cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
-                  bool capturing = false)
+                  bool capturing = false, bool structure = true)
 {
     cudaError_t e = cudaSuccess;
     size_t pi = 0;
@@ -207,6 +210,10 @@ cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
         if (e != cudaSuccess) return e;
     }
     for (auto &s : p->sup) {
+        if (!structure) {
+            ++pi;
+            continue;
+        }
         ev_begin();
         e = launch_build_supports(s.m, s.ptr, s.idx, s.n, s.slice, s.sup, s.cap, ctx->status,
                                   ctx->num_sms * 4, st);
@@ -214,6 +221,10 @@ cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
         if (e != cudaSuccess) return e;
     }
     for (auto &b : p->bb) {
+        if (!structure) {
+            ++pi;
+            continue;
+        }
         ev_begin();
         e = bucket_prefix(ctx, b, st);
         ev_end();
@@ -227,7 +238,7 @@ cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
     }
     for (auto &l : p->learned) {
         ev_begin();
-        e = launch_tile_prefix(l.L, 1, 1, l.prefix, ctx->status, st);
+        if (structure) e = launch_tile_prefix(l.L, 1, 1, l.prefix, ctx->status, st);
         if (e == cudaSuccess)
             e = learned_launches(l.m, l.L, l.prefix, p->model, p->conf, l.S, p->lrules, l.precision,
                                  ctx->num_sms, ctx->status, st, nullptr);
@@ -636,6 +647,8 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
         else if (k < nt + ns + 2 * nb) r.name = p->bb[k - nt - ns - nb].name;
         else if (k < nt + ns + 2 * nb + nl) r.name = "learned";
         else r.name = "guard";
+        // static plans build the support records and tile prefix sums once
+        r.skipped = (flags & BEM_PLAN_STATIC_LISTS) && k >= nt && k < nt + ns + nb;
         p->prof.push_back(r);
     }
 
@@ -657,7 +670,8 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
     if (flags & BEM_PLAN_GRAPH) {
         e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e2 = issue(ctx, p, p->cap, (flags & BEM_PLAN_PROFILE) != 0, true);
+            cudaError_t e2 = issue(ctx, p, p->cap, (flags & BEM_PLAN_PROFILE) != 0, true,
+                                   !(flags & BEM_PLAN_STATIC_LISTS));
             e = cudaStreamEndCapture(p->cap, &p->graph);
             if (e2 != cudaSuccess) e = e2;
         }
@@ -683,7 +697,7 @@ int bem_plan_run(bem_ctx *ctx, bem_plan *p)
     }
     cudaError_t e;
     if (p->exec) e = cudaGraphLaunch(p->exec, ctx->stream);
-    else e = issue(ctx, p, ctx->stream, prof);
+    else e = issue(ctx, p, ctx->stream, prof, false, !(p->flags & BEM_PLAN_STATIC_LISTS));
     if (e != cudaSuccess) return api_cuda_fail(ctx, e, "plan run");
     if (prof) {
         p->prof_outstanding = true;
@@ -711,13 +725,17 @@ int bem_plan_info(bem_ctx *ctx, bem_plan *p, int32_t *n_touch_launches, int32_t 
     if (n_touch_launches) *n_touch_launches = (int32_t)p->tb.size();
     if (n_block_launches) *n_block_launches = (int32_t)p->bb.size();
     // per block bucket: tile prefix sums and job scan; per support table:
-    // slice prefix and record build; per guard set: row maxima, selection and
-    // the FP64 pass
-    // per learned job: tile prefix, selection, offsets, compaction and one
-    // evaluation per class
+    // slice prefix and record build
+    // (static plans: without the list-derived passes); a guard set launches
+    // row maxima, selection and the disjoint recomputation, plus the touching
+    // one when it has near-field jobs; a learned job selection, scan, offsets,
+    // compaction and six class evaluations after its prefix sums
+    const bool stat = (p->flags & BEM_PLAN_STATIC_LISTS) != 0;
+    int64_t guard_launches = 0;
+    for (const auto &g : p->guards) guard_launches += g.cap_t > 0 ? 4 : 3;
     if (n_aux_launches)
-        *n_aux_launches = (int32_t)(2 * p->bb.size() + 2 * p->sup.size() + 3 * p->guards.size() +
-                                    10 * p->learned.size());
+        *n_aux_launches = (int32_t)((stat ? 0 : 2 * p->bb.size() + 2 * p->sup.size()) +
+                                    guard_launches + (stat ? 10 : 11) * p->learned.size());
     for (int k = 0; grid_mult && k < cap && k < (int)p->bb.size(); ++k) grid_mult[k] = p->bb[k].grid_mult;
     return BEM_OK;
 }

@@ -49,7 +49,7 @@ def _jobs(pkg, ctx, w, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_full"])
-@pytest.mark.parametrize("flags", [0, 1, 3, 7])
+@pytest.mark.parametrize("flags", [0, 1, 3, 7, 9, 11])
 def test_plan_equals_per_job_calls(env, small_batch, precision, flags):
     pkg, ctx = env
     mids, near, far, outs = _jobs(pkg, ctx, small_batch, precision)
@@ -238,4 +238,48 @@ def test_plan_fuses_single_and_double_layer(env):
         A = oracle_absolute(mesh, "p1", rows, cols, kernel, 0.0, QUAD)
         assert rel_err_abs(o.cpu().numpy(), want, A, rows).max() <= 1e-6, (name, kernel)
     ctx.bem_plan_destroy(plan)
+    ctx.bem_mesh_free(mid)
+
+
+def test_static_plan_skips_list_passes(env):
+    """BEM_PLAN_STATIC_LISTS: the support records and prefix sums are built once
+    at creation; the runs issue only the quadrature and guard passes, with the
+    same results bit for bit (P1, fused layers, near field and coupling)."""
+    import torch
+    from parity_util import to_dev
+    pkg, ctx = env
+    mesh = synth.jitter(synth.icosphere(3), 0.05, 6)
+    _, near, far = synth.workloads.h2_blocks(mesh, "p1", 16, 2.0, 6, 5)
+    mid = ctx.bem_mesh_upload(mesh.verts, mesh.tris, "p1")
+    quad = dict(QUAD, precision="mixed_full")
+    res = {}
+    for flags in (pkg.PLAN_GRAPH | pkg.PLAN_PROFILE,
+                  pkg.PLAN_GRAPH | pkg.PLAN_PROFILE | pkg.PLAN_STATIC_LISTS):
+        jobs = {"near": [], "far": []}
+        outs = []
+        for name, bs in (("near", near), ("far", far)):
+            arr = [to_dev(a, torch.int32) for a in (bs.row_ptr, bs.row_idx, bs.blk_row, bs.blk_col)]
+            off = to_dev(bs.blk_off, torch.int64)
+            for kernel in ("laplace_slp", "laplace_dlp"):
+                o = torch.full((bs.n_entries,), float("nan"), dtype=torch.float64, device="cuda")
+                jobs[name].append(pkg.BlockJob(mid, arr[0], arr[1], arr[0], arr[1], arr[2], arr[3],
+                                               off, o, pkg.kernel_desc(kernel), pkg.quad_desc(**quad)))
+                outs.append(o)
+        plan = ctx.bem_plan_create(jobs["near"], jobs["far"], flags)
+        for o in outs:
+            o.fill_(float("nan"))
+        ctx.bem_profile_reset()
+        ctx.bem_profile_enable(True)
+        ctx.bem_plan_run(plan)
+        ctx.bem_plan_run(plan)
+        prof = ctx.bem_profile_read()
+        ctx.bem_profile_enable(False)
+        ctx.bem_sync()
+        res[flags] = ([o.cpu() for o in outs], prof, ctx.bem_plan_info(plan)["aux_launches"])
+        ctx.bem_plan_destroy(plan)
+    (a, pa, na), (b, pb, nb) = res.values()
+    assert all(torch.equal(x, y) for x, y in zip(a, b))
+    assert "supports" in pa and "tile_prefix" in pa
+    assert "supports" not in pb and "tile_prefix" not in pb
+    assert nb < na
     ctx.bem_mesh_free(mid)
