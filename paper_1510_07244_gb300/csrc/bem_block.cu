@@ -105,10 +105,15 @@ __global__ void __launch_bounds__(256, MIXED ? 4 : 1) k_block_p0(MeshView m, Blo
                                                   const int64_t *__restrict__ prefix,
                                                   int *status)
 {
-    // prefix counts entries; a tile is kP0Tile of them
+    // prefix counts entries; a tile is kP0Tile of them.  Each CTA takes a
+    // contiguous run of tiles, so every warp finds its next tile's blocks
+    // from the previous one's (flat_entry's hint).
     const int64_t total = L.n_blocks > 0 ? (prefix[L.n_blocks - 1] + kP0Tile - 1) / kP0Tile : 0;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x)
-        p0_tile<KIND, NP, MIXED>(m, L, R, prefix, tile, status);
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(total, t0 + per);
+    int64_t hint = -1;
+    for (int64_t tile = t0; tile < t1; ++tile)
+        p0_tile<KIND, NP, MIXED>(m, L, R, prefix, tile, status, hint);
 }
 
 // ---------------------------------------------------------------------------
@@ -123,12 +128,22 @@ __global__ void __launch_bounds__(256, MIXED ? 4 : 1) k_batch_p0(const BatchJob 
                                                   const int64_t *__restrict__ job_end, Rule2D R,
                                                   int *status)
 {
+    // contiguous runs of tiles per CTA (see k_block_p0); the block hint is
+    // kept while the run stays in one job
     const int64_t total = n_jobs > 0 ? job_end[n_jobs - 1] : 0;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(total, t0 + per);
+    int64_t hint = -1;
+    int jprev = -1;
+    for (int64_t tile = t0; tile < t1; ++tile) {
         const int j = find_job(job_end, n_jobs, tile);
+        if (j != jprev) {
+            hint = -1;
+            jprev = j;
+        }
         const int64_t local = tile - (j > 0 ? job_end[j - 1] : 0);
         const BatchJob &J = jobs[j];
-        p0_tile<KIND, NP, MIXED>(J.m, J.L, R, J.prefix, local, status);
+        p0_tile<KIND, NP, MIXED>(J.m, J.L, R, J.prefix, local, status, hint);
     }
 }
 

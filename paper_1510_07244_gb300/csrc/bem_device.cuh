@@ -1420,9 +1420,13 @@ struct FlatEntry {
     int64_t pos;     // output position: block offset + row + column * rows
 };
 
+// hint (warp-uniform, in and out): a block index at or before the block of the
+// warp's first entry, from the warp's previous tile of the same list (-1:
+// none).  Tiles taken in increasing order then find their first block after a
+// step or two forward instead of a binary search.
 __device__ __forceinline__ FlatEntry flat_entry(const MeshView &m, const BlockLaunch &L,
                                                 const int64_t *__restrict__ prefix, int64_t tile,
-                                                int *status)
+                                                int *status, int64_t &hint)
 {
     static_assert(kP0Tile == 256, "one thread per entry of a tile");
     FlatEntry fe;
@@ -1434,7 +1438,14 @@ __device__ __forceinline__ FlatEntry flat_entry(const MeshView &m, const BlockLa
     const int64_t total = prefix[L.n_blocks - 1];
     if (ew >= total) return fe;   // the whole warp
     const int64_t e = ew + lane;
-    const int64_t b0 = find_block(prefix, L.n_blocks, ew);
+    int64_t b0 = -1;
+    if (hint >= 0 && hint < L.n_blocks) {
+        int64_t h = hint;
+        for (int step = 0; step < 8 && h < L.n_blocks - 1 && prefix[h] <= ew; ++step) ++h;
+        if (prefix[h] > ew && (h == 0 || prefix[h - 1] <= ew)) b0 = h;
+    }
+    if (b0 < 0) b0 = find_block(prefix, L.n_blocks, ew);
+    hint = b0;
     const int64_t pw = b0 + lane < L.n_blocks ? prefix[b0 + lane] : INT64_MAX;
     const int64_t p_before = b0 > 0 ? prefix[b0 - 1] : 0;
     // k = first window slot with a sum above e (32 if none); six steps
@@ -1485,13 +1496,14 @@ __device__ __forceinline__ FlatEntry flat_entry(const MeshView &m, const BlockLa
 }
 
 // One tile of one block list; `tile` indexes the list's tiles (called by
-// every thread of the CTA with the same `tile`; the warps run independently).
+// every thread of the CTA with the same `tile`; the warps run independently;
+// hint as flat_entry's).
 template <int KIND, int NP, bool MIXED>
 __device__ __forceinline__ void p0_tile(const MeshView &m, const BlockLaunch &L, const Rule2D &R,
                                         const int64_t *__restrict__ prefix, int64_t tile,
-                                        int *status)
+                                        int *status, int64_t &hint)
 {
-    const FlatEntry fe = flat_entry(m, L, prefix, tile, status);
+    const FlatEntry fe = flat_entry(m, L, prefix, tile, status, hint);
     if (!fe.ok) return;
     const int a = fe.a, bb = fe.b;
     if (L.lower_only && a < bb) return;

@@ -413,11 +413,12 @@ static const int kClassRule[kClasses][2] = {{BEM_RULE_DUFFY, 2}, {BEM_RULE_TRI7,
 // calls this).
 __device__ __forceinline__ void select_entry(const MeshView &m, const BlockLaunch &L,
                                              const int64_t *prefix, int64_t tile, int *status,
-                                             int &a, int &b, int64_t &pos, int &state)
+                                             int &a, int &b, int64_t &pos, int &state,
+                                             int64_t &hint)
 {
     // state: 0 = no entry, 1 = done (touching, written), 2 = regular pair
     state = 0;
-    const FlatEntry fe = flat_entry(m, L, prefix, tile, status);
+    const FlatEntry fe = flat_entry(m, L, prefix, tile, status, hint);
     if (!fe.ok) return;
     a = fe.a;
     b = fe.b;
@@ -471,10 +472,15 @@ __global__ void __launch_bounds__(256, 2) k_learned_select(MeshView m, BlockLaun
     if (blockIdx.x == 0 && threadIdx.x == 0 && L.n_blocks > 0 &&
         (prefix[L.n_blocks - 1] + kP0Tile - 1) / kP0Tile > A.ntile)
         set_status(status, BEM_ERR_INVALID_ARG);   // the lists outgrew the scratch
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    // contiguous runs of tiles per CTA: the block search starts from the
+    // previous tile's block
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(total, t0 + per);
+    int64_t hint = -1;
+    for (int64_t tile = t0; tile < t1; ++tile) {
         int a = 0, b = 0, state = 0;
         int64_t pos = 0;
-        select_entry(m, L, prefix, tile, status, a, b, pos, state);
+        select_entry(m, L, prefix, tile, status, a, b, pos, state, hint);
         float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (state == 2) pair_features(m, a, b, L.kind, L.kappa, A.mean, A.inv_std, f);
 #pragma unroll
@@ -646,7 +652,10 @@ __global__ void __launch_bounds__(256) k_learned_compact(MeshView m, BlockLaunch
 {
     const int64_t total = learned_tiles(L, prefix, A.ntile);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(total, t0 + per);
+    int64_t hint = -1;
+    for (int64_t tile = t0; tile < t1; ++tile) {
         const int cls = A.cls[tile * 256 + threadIdx.x];
         // warp-uniform: flat_entry shuffles across the warp
         if (!__ballot_sync(0xffffffffu, cls < kClasses)) continue;
@@ -657,7 +666,7 @@ __global__ void __launch_bounds__(256) k_learned_compact(MeshView m, BlockLaunch
             if (cls == cc) mine = mk;
         }
         // the selection pass already checked the indices (status not set twice)
-        const FlatEntry fe = flat_entry(m, L, prefix, tile, nullptr);
+        const FlatEntry fe = flat_entry(m, L, prefix, tile, nullptr, hint);
         if (cls < kClasses) {
             const int k = A.tcount[cls * 8 * A.ntile + tile * 8 + w] +
                           __popc(mine & ((1u << lane) - 1u));
