@@ -537,6 +537,7 @@ int bem_mesh_upload(bem_ctx *ctx, const double *verts, int64_t nv, const int32_t
 
     cudaSetDevice(ctx->device);
     Mesh *m = new Mesh();
+    m->host_hash = mesh_hash(verts, nv, tris, nt);
     MeshView &V = m->v;
     V.nv = nv;
     V.nt = nt;

@@ -267,10 +267,11 @@ extern "C" int bem_gca_pivots_device(bem_ctx *ctx, int32_t mesh_id, const double
     auto it = ctx->meshes.find(mesh_id);
     if (it == ctx->meshes.end()) return api_fail(ctx, BEM_ERR_INVALID_ARG, "unknown mesh id");
     const Mesh *mesh = it->second;
-    if (mesh->v.nv != nv || mesh->v.nt != nt || mesh->v.basis != basis)
+    if (mesh->v.nv != nv || mesh->v.nt != nt || mesh->v.basis != basis || !verts || !tris ||
+        mesh_hash(verts, nv, tris, nt) != mesh->host_hash)
         return api_fail(ctx, BEM_ERR_INVALID_ARG,
                         "bem_gca_pivots_device: the host mesh is not the uploaded one "
-                        "(vertex or triangle count, or basis)");
+                        "(coordinates, connectivity or basis)");
     Rule2D R;
     std::memset(&R, 0, sizeof R);
     make_rule2d(BEM_RULE_TRI7, 0, R);

@@ -108,7 +108,25 @@ struct Mesh {
     std::vector<int> hlist[4];                              // host copies of the lists
     int *iota = nullptr;       // 0 .. n-1 (dense calls)
     int *dense_csr = nullptr;  // {0, n} and the block {0, 0, off 0}
+    uint64_t host_hash = 0;    // mesh_hash of the uploaded vertex and triangle arrays
 };
+
+// FNV-1a over the bytes of the vertex and triangle arrays: calls that take the
+// host mesh again (bem_gca_pivots_device) check it is the uploaded one.
+inline uint64_t mesh_hash(const double *verts, int64_t nv, const int32_t *tris, int64_t nt)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto add = [&h](const void *p, size_t n) {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        for (size_t k = 0; k < n; ++k) {
+            h ^= c[k];
+            h *= 1099511628211ull;
+        }
+    };
+    add(verts, (size_t)nv * 3 * sizeof(double));
+    add(tris, (size_t)nt * 3 * sizeof(int32_t));
+    return h;
+}
 
 }  // namespace bem
 

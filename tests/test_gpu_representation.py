@@ -344,13 +344,18 @@ def test_gca_device_rejects_another_mesh(ctx, pkg):
     ptr, idx = part.cluster_csr()
     other = synth.icosphere(1)
     mid = ctx.bem_mesh_upload(other.verts, other.tris, "p0")
+    # same counts, moved coordinates: caught by the upload's hash
+    moved = synth.jitter(mesh, 0.05, 3)
+    mid2 = ctx.bem_mesh_upload(moved.verts, moved.tris, "p0")
     try:
-        with pytest.raises(pkg.BemError) as e:
-            ctx.bem_gca_pivots_device(mid, mesh.verts, mesh.tris, "p0", ptr, idx,
-                                      part.son_array())
-        assert e.value.code == -1
+        for m in (mid, mid2):
+            with pytest.raises(pkg.BemError) as e:
+                ctx.bem_gca_pivots_device(m, mesh.verts, mesh.tris, "p0", ptr, idx,
+                                          part.son_array())
+            assert e.value.code == -1
     finally:
         ctx.bem_mesh_free(mid)
+        ctx.bem_mesh_free(mid2)
 
 
 @pytest.mark.parametrize("basis,kernel,kappa", [("p0", "laplace_slp", 0.0),
