@@ -31,19 +31,34 @@ __device__ void tile_prefix_cta(const BlockLaunch &L, int tr, int tc, int64_t *p
     const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
     const int64_t lo = threadIdx.x * chunk, hi = min(n, lo + chunk);
     int64_t sum = 0;
-    for (int64_t b = lo; b < hi; ++b) {
-        const int t = L.blk_row[b], s = L.blk_col[b];
-        int64_t tiles = 0;
-        if (t >= 0 && t < L.n_row_clusters && s >= 0 && s < L.n_col_clusters) {
-            const int nr = L.row_ptr[t + 1] - L.row_ptr[t];
-            const int nc = L.col_ptr[s + 1] - L.col_ptr[s];
-            if (nr < 0 || nc < 0) set_status(status, BEM_ERR_INVALID_ARG);
-            else tiles = (int64_t)((nr + tr - 1) / tr) * ((nc + tc - 1) / tc);
-        } else {
-            set_status(status, BEM_ERR_INVALID_ARG);
+    // U blocks at a time: their cluster and size loads do not depend on one
+    // another, so they are in flight together
+    constexpr int U = 8;
+    for (int64_t b0 = lo; b0 < hi; b0 += U) {
+        int t[U], s[U], nr[U], nc[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool in = b0 + u < hi;
+            t[u] = in ? L.blk_row[b0 + u] : 0;
+            s[u] = in ? L.blk_col[b0 + u] : 0;
         }
-        sum += tiles;
-        prefix[b] = sum;   // local inclusive sum, fixed below
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ok[u] = b0 + u < hi && t[u] >= 0 && t[u] < L.n_row_clusters && s[u] >= 0 &&
+                    s[u] < L.n_col_clusters;
+            nr[u] = ok[u] ? L.row_ptr[t[u] + 1] - L.row_ptr[t[u]] : 0;
+            nc[u] = ok[u] ? L.col_ptr[s[u] + 1] - L.col_ptr[s[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (b0 + u >= hi) break;
+            int64_t tiles = 0;
+            if (!ok[u] || nr[u] < 0 || nc[u] < 0) set_status(status, BEM_ERR_INVALID_ARG);
+            else tiles = (int64_t)((nr[u] + tr - 1) / tr) * ((nc[u] + tc - 1) / tc);
+            sum += tiles;
+            prefix[b0 + u] = sum;   // local inclusive sum, fixed below
+        }
     }
     part[threadIdx.x] = sum;
     __syncthreads();

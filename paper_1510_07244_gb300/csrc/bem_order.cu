@@ -33,16 +33,13 @@ namespace bem {
 // by the model's mean and standard deviation.  Float arithmetic (a feature
 // only has to place the pair among the classes).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void pair_features(const MeshView &m, int a, int b, int kind,
-                                              double kappa, const float *mean, const float *inv_std,
-                                              float *f)
+__device__ __forceinline__ void pair_features_rec(const TriF &A, const TriF &B, int kind,
+                                                  double kappa, const float *mean,
+                                                  const float *inv_std, float *f)
 {
     // float arithmetic on the double-float records: vertex offsets from each
     // triangle's vertex 0, and the offset between the two vertices 0 formed from
     // the hi + lo pairs, so every difference keeps float precision
-    TriF A, B;
-    load_trif(m.geomf, a, A);
-    load_trif(m.geomf, b, B);
     float oa[3][3], ob[3][3], d0[3], na[3], nb[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -102,6 +99,16 @@ __device__ __forceinline__ void pair_features(const MeshView &m, int a, int b, i
     raw[7] = __log2f(ar);
 #pragma unroll
     for (int k = 0; k < 8; ++k) f[k] = (raw[k] - mean[k]) * inv_std[k];
+}
+
+__device__ __forceinline__ void pair_features(const MeshView &m, int a, int b, int kind,
+                                              double kappa, const float *mean, const float *inv_std,
+                                              float *f)
+{
+    TriF A, B;
+    load_trif(m.geomf, a, A);
+    load_trif(m.geomf, b, B);
+    pair_features_rec(A, B, kind, kappa, mean, inv_std, f);
 }
 
 __global__ void k_features(MeshView m, const int32_t *__restrict__ a_idx,
@@ -309,19 +316,18 @@ __device__ __forceinline__ void mlp_tile(const MlpFrag &F, const float (*X16)[8]
     a[1] = pack_bf16(X16[r + 8][cq], X16[r + 8][cq + 1]);
     a[2] = 0u;   // columns 8..15 are padding
     a[3] = 0u;
-    float h1[8][4];
+    // layer 1, its ReLU outputs packed at once into layer 2's A fragments: n tile
+    // 2kt fills registers 0 and 1 of k tile kt, n tile 2kt + 1 registers 2 and 3
+    unsigned a1[4][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const uint2 bw = F.w1[nt][lane];
         const unsigned b[2] = {bw.x, bw.y};
         const int col = nt * 8 + cq;
-        h1[nt][0] = F.b1[col];
-        h1[nt][1] = F.b1[col + 1];
-        h1[nt][2] = F.b1[col];
-        h1[nt][3] = F.b1[col + 1];
-        mma_bf16(h1[nt], a, b);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) h1[nt][q] = fmaxf(h1[nt][q], 0.0f);
+        float h[4] = {F.b1[col], F.b1[col + 1], F.b1[col], F.b1[col + 1]};
+        mma_bf16(h, a, b);
+        a1[nt / 2][2 * (nt % 2)] = pack_bf16(fmaxf(h[0], 0.0f), fmaxf(h[1], 0.0f));
+        a1[nt / 2][2 * (nt % 2) + 1] = pack_bf16(fmaxf(h[2], 0.0f), fmaxf(h[3], 0.0f));
     }
     // layer 2: K = 64 (4 k tiles), N = 64 (8 n tiles)
     float h2[8][4];
@@ -335,16 +341,11 @@ __device__ __forceinline__ void mlp_tile(const MlpFrag &F, const float (*X16)[8]
     }
 #pragma unroll
     for (int kt = 0; kt < 4; ++kt) {
-        unsigned ak[4];
-        ak[0] = pack_bf16(h1[2 * kt][0], h1[2 * kt][1]);
-        ak[1] = pack_bf16(h1[2 * kt][2], h1[2 * kt][3]);
-        ak[2] = pack_bf16(h1[2 * kt + 1][0], h1[2 * kt + 1][1]);
-        ak[3] = pack_bf16(h1[2 * kt + 1][2], h1[2 * kt + 1][3]);
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
             const uint2 bw = F.w2[nt][kt][lane];
             const unsigned b[2] = {bw.x, bw.y};
-            mma_bf16(h2[nt], ak, b);
+            mma_bf16(h2[nt], a1[kt], b);
         }
     }
     // layer 3: K = 64, N = 6 (one 8-column tile)
@@ -410,11 +411,15 @@ static const int kClassRule[kClasses][2] = {{BEM_RULE_DUFFY, 2}, {BEM_RULE_TRI7,
                                             {BEM_RULE_DUFFY, 6}, {BEM_RULE_DUFFY, 8}};
 
 // Entry threadIdx.x of flat tile `tile` (flat_entry; every lane of the warp
-// calls this).
+// calls this), with both triangles' records.  The records are loaded beside
+// the vertex ids and the features are formed before the touching test, so the
+// loads of a tile wait once.  A touching pair is written from the touching
+// table; its features are unused.
 __device__ __forceinline__ void select_entry(const MeshView &m, const BlockLaunch &L,
                                              const int64_t *prefix, int64_t tile, int *status,
+                                             const float *mean, const float *inv_std,
                                              int &a, int &b, int64_t &pos, int &state,
-                                             int64_t &hint)
+                                             int64_t &hint, float *f)
 {
     // state: 0 = no entry, 1 = done (touching, written), 2 = regular pair
     state = 0;
@@ -424,6 +429,10 @@ __device__ __forceinline__ void select_entry(const MeshView &m, const BlockLaunc
     b = fe.b;
     pos = fe.pos;
     const int4 va = __ldg(m.tvid + a), vb = __ldg(m.tvid + b);
+    TriF A, B;
+    load_trif(m.geomf, a, A);
+    load_trif(m.geomf, b, B);
+    pair_features_rec(A, B, L.kind, L.kappa, mean, inv_std, f);
     if (touching(va, vb)) {
         // near field: the touching table's value; a touching pair in a coupling
         // block (no table) means the block was not admissible
@@ -459,13 +468,19 @@ __device__ __forceinline__ int64_t learned_tiles(const BlockLaunch &L, const int
     return t < cap ? t : cap;
 }
 
-__global__ void __launch_bounds__(256, 2) k_learned_select(MeshView m, BlockLaunch L,
+// Capped at 64 registers (four CTAs, 32 warps per SM): the tiles' dependent
+// loads want the warps, and the two MLP tiles run one after the other to fit.
+__global__ void __launch_bounds__(256, 4) k_learned_select(MeshView m, BlockLaunch L,
                                                            const int64_t *__restrict__ prefix,
                                                            LearnedArgs A, int *status)
 {
-    __shared__ float xs[8][2][16][8];
+    // xs: per warp its 32 rows of features, then (same place) their logits
+    __shared__ __align__(16) float xs[8][2][16][8];
+    __shared__ float norm[2][8];
     __shared__ MlpFrag F;
-    mlp_stage(A.P, F);
+    if (threadIdx.x < 16) norm[threadIdx.x / 8][threadIdx.x % 8] =
+        threadIdx.x < 8 ? A.mean[threadIdx.x] : A.inv_std[threadIdx.x - 8];
+    mlp_stage(A.P, F);   // ends with a barrier
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // prefix counts entries; a tile is kP0Tile of them
     const int64_t total = learned_tiles(L, prefix, A.ntile);
@@ -477,37 +492,31 @@ __global__ void __launch_bounds__(256, 2) k_learned_select(MeshView m, BlockLaun
     const int64_t per = (total + gridDim.x - 1) / gridDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(total, t0 + per);
     int64_t hint = -1;
+    const int my_t = lane / 16, my_r = lane % 16;   // this lane's row: tile, row in tile
+    const int r = lane / 4, cq = 2 * (lane % 4);    // mma fragment: row, class pair
     for (int64_t tile = t0; tile < t1; ++tile) {
         int a = 0, b = 0, state = 0;
         int64_t pos = 0;
-        select_entry(m, L, prefix, tile, status, a, b, pos, state, hint);
         float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (state == 2) pair_features(m, a, b, L.kind, L.kappa, A.mean, A.inv_std, f);
+        select_entry(m, L, prefix, tile, status, norm[0], norm[1], a, b, pos, state, hint, f);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) xs[w][lane / 16][lane % 16][k] = f[k];
+        for (int k = 0; k < 8; ++k) xs[w][my_t][my_r][k] = state == 2 ? f[k] : 0.0f;
         __syncwarp();
-        // logits of the warp's 32 rows: two 16-row tiles
-        float lo[2][2], hi[2][2];
-        mlp_tile(F, xs[w][0], lane, lo[0], hi[0]);
-        mlp_tile(F, xs[w][1], lane, lo[1], hi[1]);
-        __syncwarp();
-        // gather this lane's row logits: row = lane; tile = lane / 16, r = lane % 16
-        float logit[kClasses];
-        {
-            const int my_t = lane / 16, my_r = lane % 16;
-#pragma unroll
-            for (int cc = 0; cc < 8; ++cc) {
-                // class cc of row my_r in tile my_t lives in lane 4 * (my_r % 8) + cc / 2,
-                // register lo (rows < 8) or hi (rows >= 8), element cc % 2
-                const int src = 4 * (my_r % 8) + cc / 2;
-                float v0 = __shfl_sync(0xffffffffu, lo[0][cc % 2], src);
-                float v1 = __shfl_sync(0xffffffffu, hi[0][cc % 2], src);
-                float v2 = __shfl_sync(0xffffffffu, lo[1][cc % 2], src);
-                float v3 = __shfl_sync(0xffffffffu, hi[1][cc % 2], src);
-                const float v = my_t == 0 ? (my_r < 8 ? v0 : v1) : (my_r < 8 ? v2 : v3);
-                if (cc < kClasses) logit[cc] = v;
-            }
+        // logits of the warp's 32 rows: two 16-row tiles, one after the other,
+        // each written back over its features once every lane has read them
+#pragma unroll 1
+        for (int t = 0; t < 2; ++t) {
+            float lo[2], hi[2];
+            mlp_tile(F, xs[w][t], lane, lo, hi);
+            __syncwarp();
+            *reinterpret_cast<float2 *>(&xs[w][t][r][cq]) = make_float2(lo[0], lo[1]);
+            *reinterpret_cast<float2 *>(&xs[w][t][r + 8][cq]) = make_float2(hi[0], hi[1]);
         }
+        __syncwarp();
+        const float4 l0 = *reinterpret_cast<const float4 *>(&xs[w][my_t][my_r][0]);
+        const float4 l1 = *reinterpret_cast<const float4 *>(&xs[w][my_t][my_r][4]);
+        __syncwarp();   // the next tile's features overwrite xs
+        const float logit[kClasses] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y};
         int cls = 255;
         if (state == 2) {
             float mx = logit[0];
