@@ -1184,6 +1184,19 @@ def plan_workload(torch, pkg, ctx, dev, stream, name, basis, quad, items, forms,
     out["speedup_vs_fp64_form"] = out["value"] / value64
     out["max_rel_err_vs_fp64_form"] = head["max_rel_err_vs_fp64_form"] if head else 0.0
     out["max_row_scaled_err"] = head["max_row_scaled_err"] if head else 0.0
+    # triangle-pair integrals and quadrature points of one step of the reported form
+    pairs = points = 0
+    for v, c, st in zip(views, counts, stats):
+        touch = st["n_vertex"] + st["n_edge"] + st["n_identical"]
+        for o in v.operators:
+            pairs += c["near_regular_pairs"] + c["far_regular_pairs"] + touch
+            points += sum(kernel_points(v, c, st, o.kernel, chosen or "fp64").values())
+    sec = out["ms_per_step"] / 1e3
+    out["work"] = {"pair_integrals_per_step": int(pairs), "points_per_step": int(points),
+                   "pair_integrals_per_s": pairs / sec, "points_per_s": points / sec,
+                   "counted": "per operator: the regular pairs of the block kernels and the "
+                              "touching pairs of the mesh's table; points of the rules as the "
+                              "kernels run them; the guard's recomputations not counted"}
 
     if e2e_steps > 0:
         # end to end through the per-call entry points, host buffers in and out
@@ -1492,6 +1505,18 @@ def run_c5(args, emit=True):
     conf = max(ok, key=lambda c: sweep[str(c)]["value"]) if ok else \
         min(confs, key=lambda c: acc[f"learned_{c}"])
     mslrn, counts, pts = lrn[conf]["ms"], lrn[conf]["counts"], sweep[str(conf)]["points_per_disjoint_pair"]
+    # triangle-pair integrals and quadrature points of one learned step: the
+    # disjoint pairs at their classes' rules, the touching pairs of the mesh's
+    # table at the fixed singular rules, per operator
+    st = ctx.bem_mesh_info(mid)
+    tpairs = tpts = 0
+    for op in w.operators:
+        for cas, qq in (("vertex", w.quad.q_vertex), ("edge", w.quad.q_edge),
+                        ("identical", w.quad.q_identical)):
+            tpairs += st[f"n_{cas}"]
+            tpts += st[f"n_{cas}"] * touch_cost(cas, op.kernel, "p0", qq, True)[0]
+    wpairs = int(sum(counts) + tpairs)
+    wpoints = int(float(np.dot(counts, pkg.ORDER_CLASS_POINTS)) + tpts)
     line = {"metric": METRIC, "value": entries / (mslrn / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mslrn,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1514,6 +1539,9 @@ def run_c5(args, emit=True):
                       "mixed_full_fixed": {"value": entries / (msfix / 1e3), "ms_per_step": msfix},
                       "learned_mixed_full": {"value": entries / (mslrn / 1e3),
                                              "ms_per_step": mslrn, "confidence": conf}},
+            "work": {"pair_integrals_per_step": wpairs, "points_per_step": wpoints,
+                     "pair_integrals_per_s": wpairs / (mslrn / 1e3),
+                     "points_per_s": wpoints / (mslrn / 1e3)},
             "accuracy": {"reference": "FP64 pivot entries at Duffy q=10 (same singular rules)",
                          "measure": "|g - g_ref| / max(A, 1e-3 row max A), A = sum of "
                                     "|quadrature terms of g_ref|",
@@ -2001,6 +2029,11 @@ def run_all(args):
     entries_all = reduce_over_ranks(r4["entries_per_step"], "sum", dev) if ws > 1 else \
         r4["entries_per_step"]
     value = entries_all / (r4["ms_per_step"] / 1e3)
+    if ws > 1:   # every rank's pairs and points over the slowest rank's time
+        w4 = r4["work"]
+        for k in ("pair_integrals", "points"):
+            w4[f"{k}_per_step"] = int(reduce_over_ranks(w4[f"{k}_per_step"], "sum", dev))
+            w4[f"{k}_per_s"] = w4[f"{k}_per_step"] / (r4["ms_per_step"] / 1e3)
 
     # roofline of the dominant kernel of the chosen form
     kern = r4["kernels"]
@@ -2079,7 +2112,7 @@ def run_all(args):
                                            ", rows per mesh, operator and block set",
                              "entries_compared": int(r4["entries_per_step"])},
                 "kernels": kern, "fp64_form": r4["fp64_form"], "forms": r4["forms"],
-                "speedup_vs_fp64_form": r4["speedup_vs_fp64_form"],
+                "speedup_vs_fp64_form": r4["speedup_vs_fp64_form"], "work": r4.get("work"),
                 "driver": {"kind": "persistent batched plan, one CUDA graph replay per step",
                            "autotuned_ctas_per_sm": r4["grid_mult"]},
                 "configs": configs, "green_matrices": green, "clocks": clk}
