@@ -996,7 +996,7 @@ __device__ __forceinline__ void touch_f32(const MeshView &m, int idx, const floa
                                           int np, int sub, float kappa, int xi, const XiRule &XR,
                                           bool store = true)
 {
-    static_assert(LPP == 8 || LPP == 16 || LPP == 32, "lanes per pair");
+    static_assert(LPP == 4 || LPP == 8 || LPP == 16 || LPP == 32, "lanes per pair");
     static_assert(BASIS == BEM_P0 || LPP >= 16, "nine hats need nine lanes");
     constexpr bool CPLX = kind_complex(KIND);
     const int a = __ldg(m.nb_src + idx), b = __ldg(m.nb_tri + idx);

@@ -66,12 +66,13 @@ __global__ void __launch_bounds__(256) k_touching_f32_batch(const TouchJob *__re
 
 // Lanes per pair of the float kernels: the xi-integrated Laplace rules are
 // short (q^3 points per subdomain), the Helmholtz xi sums cost a few sines
-// per point, the q^4 rules fill a warp.
+// per point, the q^4 rules fill a warp.  Every lane of a group repeats the
+// pair's set-up, so the shorter rules take fewer lanes.
 static int lanes_per_pair(const Rule4D &rule, int kind, int basis)
 {
     if (!rule.xi) return 32;
-    if (kind_complex(kind)) return 16;
-    return basis == BEM_P1 ? 16 : 8;
+    if (basis == BEM_P1) return 16;
+    return kind_complex(kind) ? 8 : 4;
 }
 
 cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
@@ -95,7 +96,8 @@ cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t
 #define BEM_TV(K, B)                                                                            \
     do {                                                                                        \
         const int lp = lanes_per_pair(rule, K, B);                                              \
-        if (lp == 8) BEM_TVL(K, B, (B == BEM_P0 ? 8 : 16));                                         \
+        if (lp == 4) BEM_TVL(K, B, (B == BEM_P0 ? 4 : 16));                                         \
+        else if (lp == 8) BEM_TVL(K, B, (B == BEM_P0 ? 8 : 16));                                    \
         else if (lp == 16) BEM_TVL(K, B, 16);                                                   \
         else BEM_TVL(K, B, 32);                                                                 \
     } while (0)
@@ -144,7 +146,8 @@ cudaError_t launch_touching_batch(const TouchJob *jobs, int basis, int kind, int
 #define BEM_TVB(K, B)                                                                           \
     do {                                                                                        \
         const int lp = lanes_per_pair(rule, K, B);                                              \
-        if (lp == 8) BEM_TVBL(K, B, (B == BEM_P0 ? 8 : 16));                                         \
+        if (lp == 4) BEM_TVBL(K, B, (B == BEM_P0 ? 4 : 16));                                        \
+        else if (lp == 8) BEM_TVBL(K, B, (B == BEM_P0 ? 8 : 16));                                   \
         else if (lp == 16) BEM_TVBL(K, B, 16);                                                  \
         else BEM_TVBL(K, B, 32);                                                                \
     } while (0)
