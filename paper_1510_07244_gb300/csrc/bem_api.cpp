@@ -266,7 +266,7 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
             rc = run_touching(ctx, m, &J.kernel, &J.quad);
             if (rc) return rc;
         }
-        rc = ensure_prefix(ctx, J.n_blocks);
+        rc = ensure_prefix(ctx, J.n_blocks + prefix_chunks(J.n_blocks));   // + chunk totals
         if (rc) return rc;
         BlockLaunch L;
         L.row_ptr = J.row_ptr;
@@ -295,7 +295,8 @@ int run_blocks(bem_ctx *ctx, const bem_block_job *jobs, int32_t n_jobs, bool all
         cudaError_t e;
         {
             ProfScope ps(ctx, "tile_prefix");
-            e = launch_tile_prefix(L, tr, tc, ctx->tile_prefix, ctx->status, ctx->stream);
+            e = launch_tile_prefix_wide(L, tr, tc, ctx->tile_prefix, ctx->tile_prefix + J.n_blocks,
+                                        ctx->status, ctx->stream);
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "tile prefix kernel");
         if (J.quad.order_mode == BEM_ORDER_LEARNED) {

@@ -22,14 +22,15 @@
 
 namespace bem {
 
-// Tiles per block -> inclusive prefix sums (single CTA, chunked).
-__device__ void tile_prefix_cta(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
-                                int *status, int64_t *total)
+// Tiles per block of blocks [first, end) -> inclusive prefix sums from `first`
+// (one CTA, a contiguous run of blocks per thread).
+__device__ void tile_prefix_range(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
+                                  int *status, int64_t *total, int64_t first, int64_t end)
 {
     __shared__ int64_t part[1024];
-    const int64_t n = L.n_blocks;
+    const int64_t n = end - first;
     const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
-    const int64_t lo = threadIdx.x * chunk, hi = min(n, lo + chunk);
+    const int64_t lo = first + threadIdx.x * chunk, hi = min(end, lo + chunk);
     int64_t sum = 0;
     // U blocks at a time: their cluster and size loads do not depend on one
     // another, so they are in flight together
@@ -72,6 +73,13 @@ __device__ void tile_prefix_cta(const BlockLaunch &L, int tr, int tc, int64_t *p
     for (int64_t b = lo; b < hi; ++b) prefix[b] += base;
     if (total && threadIdx.x == blockDim.x - 1) *total = part[threadIdx.x];
     __syncthreads();
+}
+
+// Tiles per block -> inclusive prefix sums (single CTA).
+__device__ void tile_prefix_cta(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
+                                int *status, int64_t *total)
+{
+    tile_prefix_range(L, tr, tc, prefix, status, total, 0, L.n_blocks);
 }
 
 __global__ void __launch_bounds__(1024) k_tile_prefix(BlockLaunch L, int tr, int tc,
@@ -373,6 +381,47 @@ cudaError_t launch_tile_prefix(const BlockLaunch &L, int tr, int tc, int64_t *pr
 {
     if (L.n_blocks <= 0) return cudaSuccess;
     k_tile_prefix<<<1, 1024, 0, st>>>(L, tr, tc, prefix, status);
+    return cudaGetLastError();
+}
+
+// Long block lists over many CTAs: CTA c scans blocks [c K, (c + 1) K) in place
+// (K = kPrefixChunk) and leaves the chunk's total; then every later chunk adds
+// the totals of the chunks before it.  Integer sums: the same prefix as the
+// single-CTA pass.
+__global__ void __launch_bounds__(1024) k_tile_prefix_chunk(BlockLaunch L, int tr, int tc,
+                                                            int64_t *prefix, int64_t *chunk_total,
+                                                            int *status)
+{
+    const int64_t lo = (int64_t)blockIdx.x * kPrefixChunk;
+    tile_prefix_range(L, tr, tc, prefix, status, chunk_total + blockIdx.x, lo,
+                      min(L.n_blocks, lo + kPrefixChunk));
+}
+
+// CTA c adds the totals of chunks 0 .. c to chunk c + 1
+__global__ void __launch_bounds__(1024) k_tile_prefix_add(BlockLaunch L, int64_t *prefix,
+                                                          const int64_t *__restrict__ chunk_total)
+{
+    __shared__ int64_t ws[32];
+    const int c = blockIdx.x + 1;
+    int64_t s = 0;
+    for (int k = threadIdx.x; k < c; k += blockDim.x) s += chunk_total[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    int64_t base = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) base += ws[k];
+    const int64_t lo = (int64_t)c * kPrefixChunk, hi = min(L.n_blocks, lo + kPrefixChunk);
+    for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x) prefix[b] += base;
+}
+
+cudaError_t launch_tile_prefix_wide(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
+                                    int64_t *chunk_total, int *status, cudaStream_t st)
+{
+    if (L.n_blocks <= kPrefixChunk) return launch_tile_prefix(L, tr, tc, prefix, status, st);
+    const int64_t nch = prefix_chunks(L.n_blocks);
+    k_tile_prefix_chunk<<<(unsigned)nch, 1024, 0, st>>>(L, tr, tc, prefix, chunk_total, status);
+    k_tile_prefix_add<<<(unsigned)(nch - 1), 1024, 0, st>>>(L, prefix, chunk_total);
     return cudaGetLastError();
 }
 

@@ -372,6 +372,14 @@ struct Shape {
 
 cudaError_t launch_tile_prefix(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
                                int *status, cudaStream_t st);
+// Blocks per CTA of the many-CTA prefix pass, and its chunk count (the
+// chunk_total scratch holds one int64 per chunk).
+constexpr int64_t kPrefixChunk = 8192;
+inline int64_t prefix_chunks(int64_t n_blocks) { return (n_blocks + kPrefixChunk - 1) / kPrefixChunk; }
+// The same prefix sums as launch_tile_prefix; lists longer than one chunk take
+// two launches over many CTAs.
+cudaError_t launch_tile_prefix_wide(const BlockLaunch &L, int tr, int tc, int64_t *prefix,
+                                    int64_t *chunk_total, int *status, cudaStream_t st);
 cudaError_t launch_touching(const MeshView &m, int cas, const int *list, int64_t n,
                             const Rule4D &rule, int kind, double kappa, int f32,
                             cudaStream_t st, double eta = 0.0);

@@ -238,7 +238,9 @@ cudaError_t issue(bem_ctx *ctx, bem_plan *p, cudaStream_t st, bool record_prof,
     }
     for (auto &l : p->learned) {
         ev_begin();
-        if (structure) e = launch_tile_prefix(l.L, 1, 1, l.prefix, ctx->status, st);
+        if (structure)
+            e = launch_tile_prefix_wide(l.L, 1, 1, l.prefix, l.prefix + l.L.n_blocks, ctx->status,
+                                        st);
         if (e == cudaSuccess)
             e = learned_launches(l.m, l.L, l.prefix, p->model, p->conf, l.S, p->lrules, l.precision,
                                  ctx->num_sms, ctx->status, st, nullptr);
@@ -490,8 +492,11 @@ int bem_plan_create(bem_ctx *ctx, const bem_block_job *near_jobs, int32_t n_near
             l.precision = J.quad.precision;
             // the entry count sizes the job's scratch: one prefix pass now
             int64_t entries = 0;
-            if ((e = plan_alloc(p, &l.prefix, (size_t)J.n_blocks)) != cudaSuccess ||
-                (e = launch_tile_prefix(L, 1, 1, l.prefix, ctx->status, p->cap)) != cudaSuccess ||
+            // prefix sums, then the many-CTA pass's chunk totals
+            if ((e = plan_alloc(p, &l.prefix, (size_t)(J.n_blocks + prefix_chunks(J.n_blocks)))) !=
+                    cudaSuccess ||
+                (e = launch_tile_prefix_wide(L, 1, 1, l.prefix, l.prefix + J.n_blocks, ctx->status,
+                                             p->cap)) != cudaSuccess ||
                 (e = cudaMemcpyAsync(&entries, l.prefix + (J.n_blocks - 1), sizeof(int64_t),
                                      cudaMemcpyDeviceToHost, p->cap)) != cudaSuccess ||
                 (e = cudaStreamSynchronize(p->cap)) != cudaSuccess ||
@@ -728,14 +733,18 @@ int bem_plan_info(bem_ctx *ctx, bem_plan *p, int32_t *n_touch_launches, int32_t 
     // slice prefix and record build
     // (static plans: without the list-derived passes); a guard set launches
     // row maxima, selection and the disjoint recomputation, plus the touching
-    // one when it has near-field jobs; a learned job selection, scan, offsets,
-    // compaction and six class evaluations after its prefix sums
+    // one when it has near-field jobs; a learned job selection, scan (three
+    // launches), offsets, compaction and six class evaluations after its prefix
+    // sums
     const bool stat = (p->flags & BEM_PLAN_STATIC_LISTS) != 0;
     int64_t guard_launches = 0;
     for (const auto &g : p->guards) guard_launches += g.cap_t > 0 ? 4 : 3;
+    int64_t n_learned = 12 * (int64_t)p->learned.size();
+    if (!stat)   // prefix sums: one CTA, or two launches over many CTAs for long lists
+        for (const auto &l : p->learned) n_learned += l.L.n_blocks > kPrefixChunk ? 2 : 1;
     if (n_aux_launches)
         *n_aux_launches = (int32_t)((stat ? 0 : 2 * p->bb.size() + 2 * p->sup.size()) +
-                                    guard_launches + (stat ? 10 : 11) * p->learned.size());
+                                    guard_launches + n_learned);
     for (int k = 0; grid_mult && k < cap && k < (int)p->bb.size(); ++k) grid_mult[k] = p->bb[k].grid_mult;
     return BEM_OK;
 }
