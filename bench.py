@@ -1220,13 +1220,16 @@ def plan_workload(torch, pkg, ctx, dev, stream, name, basis, quad, items, forms,
             d2h += sum(t.numel() * t.element_size() for t in ho.values())
             host_out.append(ho)
             h2d += v.mesh.verts.nbytes + v.mesh.tris.nbytes
-        times = []
+        times, uploads = [], []
         for k in range(e2e_steps + 1):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             mids2 = []
+            t_up = 0.0
             for v, st, o, ph, ho in zip(views, sets, outs, pin, host_out):
+                tu = time.perf_counter()
                 mid2 = ctx.bem_mesh_upload(v.mesh.verts, v.mesh.tris, basis)
+                t_up += time.perf_counter() - tu
                 mids2.append(mid2)
                 for nm in ("near", "far"):
                     for key, t in ph[nm].items():
@@ -1243,9 +1246,11 @@ def plan_workload(torch, pkg, ctx, dev, stream, name, basis, quad, items, forms,
                 ctx.bem_mesh_free(m2)
             if k > 0:
                 times.append(t1 - t0)
+                uploads.append(t_up)
         out["e2e"] = {"value": entries / statistics.mean(times), "unit": UNIT,
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                      "steps": len(times),
+                      "steps": len(times), "s_per_step": statistics.mean(times),
+                      "mesh_upload_s_per_step": statistics.mean(uploads),
                       "includes": "per mesh: upload + host planning, block lists H2D, "
                                   "bem_near_field + bem_coupling_blocks, all outputs D2H"}
     for mid in mids:
