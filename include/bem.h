@@ -354,8 +354,11 @@ int bem_plan_run(bem_ctx *ctx, bem_plan *plan);
 int bem_plan_destroy(bem_ctx *ctx, bem_plan *plan);
 /* Kernel launches of one plan run: touching buckets, block buckets, and the
  * auxiliary launches (per block bucket its tile prefix sums, per distinct
- * piecewise-linear cluster list its support records); the chosen CTAs per SM
- * of up to `cap` block buckets.  Any pointer may be NULL. */
+ * piecewise-linear cluster list its support records, per guard set its three
+ * or four passes, per learned job its prefix sums (one launch, two above 8192
+ * blocks), selection, three scan passes, offsets, compaction and six class
+ * evaluations; BEM_PLAN_STATIC_LISTS leaves out the list-derived passes); the
+ * chosen CTAs per SM of up to `cap` block buckets.  Any pointer may be NULL. */
 int bem_plan_info(bem_ctx *ctx, bem_plan *plan, int32_t *n_touch_launches,
                   int32_t *n_block_launches, int32_t *n_aux_launches, int32_t *grid_mult,
                   int32_t cap);
