@@ -119,3 +119,30 @@ def test_step_rates_count_pairs_and_points(small_c2):
     regmx = counts["near_regular_pairs"] + counts["far_entry_pairs"]
     assert rmx["pair_integrals_per_step"] == n_ops * (regmx + touch)
     assert counts["far_entry_pairs"] >= counts["far_regular_pairs"]
+
+
+def test_p0_pair_integrals_equal_entries():
+    """Piecewise-constant bases: every entry is one triangle pair, so the
+    regular pairs of the block sets plus the mesh's touching pairs (each one
+    lies in exactly one near-field block) are the entries; the touching
+    pairs' points are the rules' points as the float kernels run them."""
+    import numpy as np
+    import paper_1510_07244_gb300 as pkg
+    w = synth.workloads.config3(n=8)          # 768 triangles, P0
+    counts = bench.pair_counts(w)
+    tp = pkg.bem_touching_pairs(w.mesh.tris, w.mesh.nv)
+    stats = {f"n_{c}": int(np.sum(tp["case"] == k))
+             for k, c in ((1, "vertex"), (2, "edge"), (3, "identical"))}
+    assert stats["n_identical"] == w.mesh.nt
+    pairs = (counts["near_regular_pairs"] + counts["far_regular_pairs"] + stats["n_vertex"] +
+             stats["n_edge"] + stats["n_identical"])
+    assert pairs == w.near.n_entries + w.far.n_entries
+    for op in w.operators:
+        pts = bench.kernel_points(w, counts, stats, op.kernel, "mixed_full")
+        reg = counts["near_regular_pairs"] + counts["far_regular_pairs"]
+        assert pts["block_p0"] == reg * 81
+        for cas, q in (("vertex", w.quad.q_vertex), ("edge", w.quad.q_edge),
+                       ("identical", w.quad.q_identical)):
+            nsub = {"vertex": 2, "edge": 4, "identical": 6}[cas]
+            # the float Helmholtz kernels sum xi in node pairs: q^3 points per subdomain
+            assert pts[f"touching_{cas}"] == stats[f"n_{cas}"] * nsub * q ** 3
